@@ -1,0 +1,219 @@
+/*
+ * pd.h -- C ABI of the GB300 (sm_103a) HOG+LBP sliding-window SVM pedestrian
+ * detector (arXiv 1611.01642, "GPU-based pedestrian detection for autonomous
+ * driving").
+ *
+ * The detector (Section 4.1, steps 2-5) builds an image pyramid of every
+ * frame, extracts uniform-LBP and HOG cell histograms on every level,
+ * normalises 2x2-cell blocks, scores every 64x128 window (stride 8) with a
+ * linear SVM and finishes with non-maximum suppression. All of it runs in
+ * this library's CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions
+ *  - Every call returns an int status: PD_OK (0) or a negative PD_E* code.
+ *    No C++ exception crosses this boundary. Calls that take a handle record
+ *    a message retrievable with pd_last_error().
+ *  - "device" pointers are CUDA global-memory addresses of the current
+ *    device; "host" pointers are ordinary CPU memory. The caller owns every
+ *    pointer it passes; the library never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Device work is stream-ordered and asynchronous unless a
+ *    function says it synchronises.
+ *  - Images are 8-bit grayscale, row-major, `pitch` bytes between rows.
+ *
+ * Method constants (Sections 4.2-4.4): 8x8-pixel cells, 2x2-cell blocks at
+ * a one-cell stride, 64x128-pixel windows = 7x15 blocks at an 8-pixel
+ * stride, 9 unsigned orientation bins, 59 uniform-LBP bins, a 95-value
+ * block feature (36 HOG then 59 LBP).
+ */
+#ifndef PD_H
+#define PD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PD_ABI_VERSION 1
+
+#define PD_OK 0
+#define PD_EINVAL (-1)    /* bad argument, size or layout */
+#define PD_ENOMEM (-2)    /* device or pinned-host allocation failed */
+#define PD_ECUDA (-3)     /* a CUDA runtime call or kernel launch failed */
+#define PD_ETIMEOUT (-4)  /* a bounded device-side wait ran out; results invalid */
+#define PD_EBOUNDS (-5)   /* a device-side bounds check fired; results invalid */
+#define PD_ESTATE (-6)    /* call out of order (e.g. results before pd_sync) */
+#define PD_EOVERFLOW (-7) /* more NMS candidates in a frame than max_candidates */
+
+#define PD_HOG_BINS 9
+#define PD_LBP_BINS 59
+#define PD_FEAT 95
+#define PD_WIN_BW 7   /* window width in blocks  (64 px) */
+#define PD_WIN_BH 15  /* window height in blocks (128 px) */
+#define PD_TEMPLATE_SIZE (PD_WIN_BH * PD_WIN_BW * PD_FEAT) /* 9975 */
+#define PD_MAX_LEVELS 96
+
+typedef struct pd_handle pd_handle;
+
+/* Detector parameters. Fill with pd_params_default() and then override.
+ * struct_size must be sizeof(pd_params) (ABI versioning). */
+typedef struct pd_params {
+    uint32_t struct_size;
+    float pyr_factor;        /* scale step between pyramid levels, > 1 (1.05 or 1.2) */
+    float l2hys_clip;        /* HOG L2-Hys clipping value, 0.2 */
+    float threshold;         /* a window is a detection iff score > threshold (0) */
+    float nms_iou;           /* NMS suppresses when IoU > nms_iou (0.5) */
+    int32_t max_boxes_per_frame;      /* NMS output cap per frame (4096) */
+    int32_t max_candidates_per_frame; /* windows above threshold per frame, <= 16384 */
+    int32_t max_frames;      /* frames per pd_detect call (arena sizing) */
+    int32_t max_width;       /* largest frame width  (arena sizing) */
+    int32_t max_height;      /* largest frame height (arena sizing) */
+    int32_t flags;           /* reserved, 0 */
+} pd_params;
+
+/* One detection: a window in frame coordinates. */
+typedef struct pd_box {
+    float x, y, w, h;  /* top-left and size in frame pixels */
+    float score;       /* SVM score (float32) */
+    int32_t level;     /* pyramid level */
+    int32_t wx, wy;    /* window position in cells on that level */
+} pd_box;
+
+/* Geometry of one pyramid level of one frame. */
+typedef struct pd_level_info {
+    int32_t width, height;   /* level size in pixels */
+    int32_t cells_x, cells_y;/* floor(width/8), floor(height/8) */
+    int32_t rows, cols;      /* score map size: cells_y-15 by cells_x-7 (0 if none) */
+    int64_t score_offset;    /* float offset of this map in the handle's score buffer */
+} pd_level_info;
+
+/* Defaults: factor 1.05, clip 0.2, threshold 0, IoU 0.5, 4096 boxes,
+ * 16384 candidates, 1 frame of 1242x375. */
+int pd_params_default(pd_params *p);
+
+/* Pyramid level sizes of a W x H frame (Section 4.4, pyramidal sliding
+ * window; the level rule is this library's reading: level k has scale
+ * factor^k, size floor(W/factor^k) x floor(H/factor^k), and levels are kept
+ * while a 64x128 window fits). Host only. Wk/Hk: host arrays of max_levels
+ * entries. Returns the number of levels (>= 0) or PD_EINVAL. */
+int pd_pyramid(int W, int H, float factor, int max_levels, int32_t *Wk, int32_t *Hk);
+
+/* Creates a detector. svm_w: host float[15][7][95] template in window order
+ * (block row i, block column j, feature t: 36 HOG values = 4 cells x 9 bins
+ * in the order top-left, top-right, bottom-left, bottom-right, then 59 LBP
+ * values); svm_b: bias (Section 4.4: distance to the SVM hyper-plane). The
+ * handle allocates its device arena (cudaMalloc) sized by params, on the
+ * current device, and owns it until pd_destroy. Errors: PD_EINVAL,
+ * PD_ENOMEM, PD_ECUDA; *out is NULL on error. */
+int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handle **out);
+
+/* Frees the arena and the handle (synchronises the device first). NULL is a no-op. */
+void pd_destroy(pd_handle *h);
+
+/* Last error message recorded on the handle ("" if none). Valid until the next call. */
+const char *pd_last_error(const pd_handle *h);
+
+/* Runs the whole plain path on n_frames frames (Section 4.1 steps 2-5):
+ * pyramid (K1), LBP and HOG cell histograms (K2/K3), block normalisation fused
+ * with the window scores (K4), NMS (K5). d_frames: host array of n_frames
+ * DEVICE pointers to u8 frames; widths/heights/pitches: host arrays. Frames
+ * smaller than 64x128 have no level and no detection (not an error).
+ * Asynchronous on `stream`; the frames must stay valid until pd_sync
+ * returns. Results live in the handle until the next pd_detect.
+ * Errors: PD_EINVAL (n_frames > max_frames, a frame larger than
+ * max_width x max_height, NULL pointer, pitch < width), PD_ECUDA. */
+int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_frames,
+              const int32_t *widths, const int32_t *heights, const int32_t *pitches);
+
+/* Waits for the last pd_detect, then surfaces device-side status: PD_OK,
+ * PD_EOVERFLOW (a frame had more candidates than max_candidates_per_frame;
+ * its boxes are invalid), PD_ETIMEOUT / PD_EBOUNDS (results invalid), or
+ * PD_ECUDA. Copies the per-frame box lists to host memory owned by the
+ * handle. Synchronous. */
+int pd_sync(pd_handle *h);
+
+/* Level geometry of frame `frame` of the last pd_detect (host). info: host
+ * array of PD_MAX_LEVELS entries. Available right after pd_detect. */
+int pd_frame_levels(const pd_handle *h, int frame, int *n_levels, pd_level_info *info);
+
+/* Device pointer to all score maps of the last pd_detect (float32; map of
+ * (frame, level) at pd_level_info.score_offset, row-major rows x cols;
+ * window (wx, wy) scores the 64x128 window whose top-left pixel is
+ * (8wx, 8wy) on that level). Valid until the next pd_detect / pd_destroy;
+ * read it after pd_sync or on the same stream. *total = number of floats. */
+int pd_scores(const pd_handle *h, const float **d_scores, int64_t *total);
+
+/* Host copy of frame `frame`'s kept boxes, in NMS order (score descending,
+ * ties by level, wy, wx ascending). Requires pd_sync first (else PD_ESTATE).
+ * out: host array of cap entries; *count = number of boxes (may exceed cap;
+ * only min(count, cap) are written). */
+int pd_boxes(const pd_handle *h, int frame, pd_box *out, int cap, int *count);
+
+/* Number of this library's kernel launches issued by the last pd_detect. */
+int pd_last_launch_count(const pd_handle *h);
+
+/* Same as pd_detect with frames in HOST memory (h_frames: host array of host
+ * pointers; pinned memory gives the fastest copies): the library copies each
+ * frame into its arena on `stream` (Section 4.1 step 1) and runs pd_detect.
+ * The host frames may be reused once pd_sync returns. Errors as pd_detect. */
+int pd_detect_host(pd_handle *h, void *stream, int n_frames, const uint8_t *const *h_frames,
+                   const int32_t *widths, const int32_t *heights, const int32_t *pitches);
+
+/* ---------------------------------------------------------------------------
+ * Stage entry points (the same kernels pd_detect runs, one level at a time),
+ * for parity tests and for callers that keep intermediates. All pointers are
+ * DEVICE pointers owned by the caller; all calls are asynchronous on `stream`.
+ * They use the handle's small descriptor scratch, so calls on one handle must
+ * not overlap on the GPU with each other or with pd_detect.
+ * ------------------------------------------------------------------------- */
+
+/* K1, Section 4.4 pyramid: writes levels 0..n_levels-1 of one W x H frame
+ * (fixed-point bilinear, 11-bit weights, each level resampled straight from
+ * the frame; the frame is read once). Level k is Wk[k] x Hk[k] (host arrays)
+ * at d_levels + level_offsets[k] (host array, bytes) with pitch
+ * level_pitches[k] (host array, >= Wk[k]). n_levels <= PD_MAX_LEVELS.
+ * Errors: PD_EINVAL, PD_ECUDA. */
+int pd_resize_levels(pd_handle *h, void *stream, const uint8_t *d_frame, int W, int H, int pitch, int n_levels,
+                     const int32_t *Wk, const int32_t *Hk, uint8_t *d_levels,
+                     const int64_t *level_offsets, const int32_t *level_pitches);
+
+/* K2 + K3, Sections 4.2-4.3 (Algorithms 1, 2, 4, 5): uniform-LBP cell counts
+ * and soft-binned HOG cell histograms of one Wk x Hk level image.
+ * Outputs are plane-major with `cell_pitch` elements per row
+ * (cell_pitch >= floor(Wk/8), a multiple of 16):
+ *   d_hog  float32 [9][cells_y][cell_pitch]   (plane stride hog_plane elems)
+ *   d_lbp  uint8   [59][cells_y][cell_pitch]  (plane stride lbp_plane elems)
+ * hog_plane / lbp_plane >= cells_y * cell_pitch. Errors: PD_EINVAL, PD_ECUDA. */
+int pd_cell_features(pd_handle *h, void *stream, const uint8_t *d_level, int Wk, int Hk, int pitch, float *d_hog,
+                     int64_t hog_plane, uint8_t *d_lbp, int64_t lbp_plane, int cell_pitch);
+
+/* K4, Section 4.4 (Algorithm 6) with block normalisation: the score map of
+ * one level from its cell planes (layouts of pd_cell_features), using the
+ * handle's template and bias: d_scores float32 [cells_y-15][cells_x-7],
+ * row pitch cells_x-7. The cell planes are read through TMA: d_hog and d_lbp
+ * must be 16-byte aligned and the planes must hold at least 16 rows beyond
+ * cells_y that the caller does not mind being read (their values never reach
+ * a valid window). Errors: PD_EINVAL, PD_ECUDA. */
+int pd_window_scores(pd_handle *h, void *stream, const float *d_hog, int64_t hog_plane,
+                     const uint8_t *d_lbp, int64_t lbp_plane, int cell_pitch, int cells_x,
+                     int cells_y, float *d_scores);
+
+/* K5 (refinement stage, Section 3; greedy NMS) on caller score maps of ONE
+ * frame: n_levels maps laid back to back from d_scores (float32, level k
+ * rows[k] x cols[k], host arrays), level sizes Wk/Hk (host), frame W x H.
+ * Writes the kept boxes in NMS order to d_boxes (device, cap max_boxes) and
+ * the kept / candidate counts to d_counts[0] / d_counts[1] (device int32).
+ * Uses the handle's threshold, nms_iou and caps and its scratch buffers.
+ * Errors: PD_EINVAL, PD_ECUDA; a candidate overflow sets d_counts[1] to
+ * -(number of candidates). */
+int pd_nms_maps(pd_handle *h, void *stream, const float *d_scores, int n_levels, const int32_t *rows,
+                const int32_t *cols, const int32_t *Wk, const int32_t *Hk, int W, int H,
+                pd_box *d_boxes, int max_boxes, int32_t *d_counts);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PD_H */

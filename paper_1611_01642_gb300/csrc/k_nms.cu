@@ -1,0 +1,168 @@
+// K5 -- non-maximum suppression (refinement stage of Section 3, run on the
+// host in the paper; greedy IoU suppression here, on the device).
+//
+// One CTA (1024 threads) per frame:
+//  1. collects every window of every level with score > threshold into a
+//     shared-memory key list (64-bit keys: the float score mapped to an
+//     order-reversing integer in the high word, level/wy/wx in the low word,
+//     so ascending keys = score descending, then level, wy, wx ascending);
+//  2. bitonic-sorts the keys;
+//  3. walks them in order: a key not yet suppressed is kept, and all threads
+//     then suppress the later keys whose IoU with it exceeds the threshold.
+// Boxes and IoU are computed in double precision with explicitly rounded
+// operations (no contraction into FMA), so the keep/suppress decisions are
+// the exact IEEE results of the box definition.
+#include "pd_internal.h"
+
+namespace pd {
+namespace {
+
+constexpr int kThreads = 1024;
+
+__device__ __forceinline__ unsigned long long make_key(float s, int level, int wy, int wx) {
+    const uint32_t u = __float_as_uint(s);
+    const uint32_t ord = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    return ((unsigned long long)(~ord) << 32) |
+           (uint32_t)((level << 24) | (wy << 12) | wx);
+}
+
+__device__ __forceinline__ pd_box decode(unsigned long long key, const FrameDesc &fd,
+                                         const LevelDesc *levels) {
+    const uint32_t hi = (uint32_t)(key >> 32), lo = (uint32_t)key;
+    const uint32_t ord = ~hi;
+    const uint32_t u = (ord & 0x80000000u) ? (ord ^ 0x80000000u) : ~ord;
+    pd_box b;
+    b.score = __uint_as_float(u);
+    b.level = (int)(lo >> 24);
+    b.wy = (int)((lo >> 12) & 4095);
+    b.wx = (int)(lo & 4095);
+    const LevelDesc L = levels[fd.first_level + b.level];
+    const double W = (double)fd.W, H = (double)fd.H, Wk = (double)L.Wk, Hk = (double)L.Hk;
+    b.x = (float)__ddiv_rn(__dmul_rn((double)(8 * b.wx), W), Wk);
+    b.y = (float)__ddiv_rn(__dmul_rn((double)(8 * b.wy), H), Hk);
+    b.w = (float)__ddiv_rn(__dmul_rn(64.0, W), Wk);
+    b.h = (float)__ddiv_rn(__dmul_rn(128.0, H), Hk);
+    return b;
+}
+
+__device__ __forceinline__ double iou(const pd_box &a, const pd_box &b) {
+    const double ax0 = a.x, ay0 = a.y, ax1 = __dadd_rn((double)a.x, (double)a.w),
+                 ay1 = __dadd_rn((double)a.y, (double)a.h);
+    const double bx0 = b.x, by0 = b.y, bx1 = __dadd_rn((double)b.x, (double)b.w),
+                 by1 = __dadd_rn((double)b.y, (double)b.h);
+    const double iw = __dsub_rn(fmin(ax1, bx1), fmax(ax0, bx0));
+    const double ih = __dsub_rn(fmin(ay1, by1), fmax(ay0, by0));
+    if (iw <= 0.0 || ih <= 0.0) return 0.0;
+    const double inter = __dmul_rn(iw, ih);
+    const double ua = __dsub_rn(__dadd_rn(__dmul_rn((double)a.w, (double)a.h),
+                                          __dmul_rn((double)b.w, (double)b.h)),
+                                inter);
+    return __ddiv_rn(inter, ua);
+}
+
+__global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ frames,
+                                                  const LevelDesc *__restrict__ levels,
+                                                  const float *__restrict__ scores, float threshold,
+                                                  float iou_thr, int cap, pd_box *__restrict__ boxes,
+                                                  int max_boxes, int32_t *__restrict__ counts) {
+    extern __shared__ unsigned long long keys[];  // [cap_pow2] then cap bytes of flags
+    __shared__ int n_cand;
+    const int f = blockIdx.x, tid = threadIdx.x;
+    const FrameDesc fd = frames[f];
+    int cap_pow2 = 1;
+    while (cap_pow2 < cap) cap_pow2 <<= 1;
+    uint8_t *supp = reinterpret_cast<uint8_t *>(keys + cap_pow2);
+
+    if (tid == 0) n_cand = 0;
+    __syncthreads();
+    for (int k = 0; k < fd.n_levels; ++k) {
+        const LevelDesc L = levels[fd.first_level + k];
+        const int n = L.rows * L.cols;
+        const float *sc = scores + L.score_off;
+        for (int i = tid; i < n; i += kThreads) {
+            const float s = sc[i];
+            if (s > threshold) {
+                const int idx = atomicAdd(&n_cand, 1);
+                if (idx < cap) {
+                    const int wy = i / L.cols;
+                    keys[idx] = make_key(s, k, wy, i - wy * L.cols);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int n = n_cand;
+    if (n > cap) {
+        if (tid == 0) {
+            counts[2 * f] = 0;
+            counts[2 * f + 1] = -n;
+        }
+        return;
+    }
+    int np = 1;
+    while (np < n) np <<= 1;
+    for (int i = n + tid; i < np; i += kThreads) keys[i] = ~0ull;
+    for (int i = tid; i < n; i += kThreads) supp[i] = 0;
+    __syncthreads();
+    for (int k = 2; k <= np; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < np; i += kThreads) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long a = keys[i], b = keys[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    int kept = 0;
+    pd_box *out = boxes + (size_t)f * max_boxes;
+    for (int i = 0; i < n && kept < max_boxes; ++i) {
+        if (supp[i]) continue;  // uniform: flags only change inside a pass that ends in a barrier
+        const pd_box bi = decode(keys[i], fd, levels);
+        if (tid == 0) out[kept] = bi;
+        ++kept;
+        if (kept == max_boxes) break;
+        for (int j = i + 1 + tid; j < n; j += kThreads) {
+            if (supp[j]) continue;
+            const pd_box bj = decode(keys[j], fd, levels);
+            if (iou(bi, bj) > (double)iou_thr) supp[j] = 1;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        counts[2 * f] = kept;
+        counts[2 * f + 1] = n;
+    }
+}
+
+size_t nms_smem(int cap) {
+    int p = 1;
+    while (p < cap) p <<= 1;
+    return (size_t)p * sizeof(unsigned long long) + (size_t)cap;
+}
+
+}  // namespace
+
+cudaError_t init_nms() {
+    return cudaFuncSetAttribute(k_nms, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)nms_smem(16384));
+}
+
+cudaError_t launch_nms(cudaStream_t s, const FrameDesc *d_frames, const LevelDesc *d_levels,
+                       int n_frames, const float *scores, float threshold, float iou,
+                       unsigned long long *cand, int max_cand, pd_box *boxes, int max_boxes,
+                       int32_t *counts) {
+    (void)cand;
+    if (n_frames <= 0) return cudaSuccess;
+    k_nms<<<n_frames, kThreads, nms_smem(max_cand), s>>>(d_frames, d_levels, scores, threshold, iou,
+                                                         max_cand, boxes, max_boxes, counts);
+    return cudaGetLastError();
+}
+
+}  // namespace pd

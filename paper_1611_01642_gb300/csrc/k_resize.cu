@@ -1,0 +1,101 @@
+// K1 -- image pyramid (Section 4.4, pyramidal sliding window; Section 4.1 step 2).
+//
+// Every pyramid level is a fixed-point bilinear resample (11-bit weights) of
+// the frame itself, not of the previous level. One CTA owns a 128x32 source
+// tile of one frame: it stages the tile (+1 pixel of right/bottom halo) in
+// shared memory once and then writes, for every level of that frame, the
+// output pixels whose top-left source sample falls inside the tile. The
+// frame is therefore read from HBM exactly once for all levels, and each
+// level pixel is written exactly once.
+//
+// Per output coordinate the host planner precomputes the Q11 source index
+// and weight (packed as x0 << 11 | a), so the kernel does only integer
+// multiply-adds:  out = ((2048-ay)*((2048-ax)*I00 + ax*I01)
+//                        + ay*((2048-ax)*I10 + ax*I11) + 2^21) >> 22.
+#include "pd_internal.h"
+
+namespace pd {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kTileW = kResizeTW;       // 128
+constexpr int kTileH = kResizeTH;       // 32
+constexpr int kSmemW = kTileW + 4;      // 129 used, padded
+constexpr int kSmemH = kTileH + 1;      // 33
+
+// First output coordinate whose source index is >= s (table is non-decreasing).
+__device__ __forceinline__ int lower_bound_src(const int32_t *tab, int n, int s) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if ((tab[mid] >> 11) < s) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kThreads) k_resize(const FrameDesc *__restrict__ frames,
+                                                     const LevelDesc *__restrict__ levels,
+                                                     const int32_t *__restrict__ tabs,
+                                                     uint8_t *__restrict__ pyr,
+                                                     const ResizeItem *__restrict__ items) {
+    __shared__ uint8_t tile[kSmemH][kSmemW];
+    __shared__ int4 ranges[PD_MAX_LEVELS];  // xs, xe, ys, ye per level
+
+    const ResizeItem it = items[blockIdx.x];
+    const FrameDesc fd = frames[it.frame];
+    const int tid = threadIdx.x;
+
+    // Stage the source tile [x0, x0+129) x [y0, y0+33) clamped to the frame.
+    for (int i = tid; i < kSmemH * (kTileW + 1); i += kThreads) {
+        int r = i / (kTileW + 1), c = i - r * (kTileW + 1);
+        int y = min(it.y0 + r, fd.H - 1), x = min(it.x0 + c, fd.W - 1);
+        tile[r][c] = fd.ptr[(size_t)y * fd.pitch + x];
+    }
+    // Output ranges of every level (one thread per level).
+    for (int k = tid; k < fd.n_levels; k += kThreads) {
+        const LevelDesc L = levels[fd.first_level + k];
+        const int32_t *xt = tabs + L.xtab_off, *yt = tabs + L.ytab_off;
+        int4 r;
+        r.x = lower_bound_src(xt, L.Wk, it.x0);
+        r.y = lower_bound_src(xt, L.Wk, it.x0 + kTileW);
+        r.z = lower_bound_src(yt, L.Hk, it.y0);
+        r.w = lower_bound_src(yt, L.Hk, it.y0 + kTileH);
+        ranges[k] = r;
+    }
+    __syncthreads();
+
+    const int tx = tid & (kTileW - 1), ty = tid >> 7;  // 128 columns x 2 rows
+    for (int k = 0; k < fd.n_levels; ++k) {
+        const int4 r = ranges[k];
+        const int x = r.x + tx;
+        if (x >= r.y) continue;
+        const LevelDesc L = levels[fd.first_level + k];
+        const int32_t ex = __ldg(tabs + L.xtab_off + x);
+        const int sx0 = (ex >> 11) - it.x0, ax = ex & 2047;
+        const int sx1 = min((ex >> 11) + 1, fd.W - 1) - it.x0;
+        uint8_t *out = pyr + L.img_off + x;
+        for (int y = r.z + ty; y < r.w; y += 2) {
+            const int32_t ey = __ldg(tabs + L.ytab_off + y);
+            const int sy0 = (ey >> 11) - it.y0, ay = ey & 2047;
+            const int sy1 = min((ey >> 11) + 1, fd.H - 1) - it.y0;
+            const int i00 = tile[sy0][sx0], i01 = tile[sy0][sx1];
+            const int i10 = tile[sy1][sx0], i11 = tile[sy1][sx1];
+            const int top = (2048 - ax) * i00 + ax * i01;
+            const int bot = (2048 - ax) * i10 + ax * i11;
+            const int v = ((2048 - ay) * top + ay * bot + (1 << 21)) >> 22;
+            out[(size_t)y * L.img_pitch] = (uint8_t)v;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_resize(cudaStream_t s, const FrameDesc *d_frames, const LevelDesc *d_levels,
+                          const int32_t *d_tabs, uint8_t *pyr, const ResizeItem *d_items,
+                          int n_items) {
+    if (n_items <= 0) return cudaSuccess;
+    k_resize<<<n_items, kThreads, 0, s>>>(d_frames, d_levels, d_tabs, pyr, d_items);
+    return cudaGetLastError();
+}
+
+}  // namespace pd

@@ -1,0 +1,737 @@
+// Host runtime of the detector library: parameter checks, batch planning,
+// the device arena, TMA tensor maps and the C ABI of include/pd.h.
+//
+// A batch plan lists, for every frame, its pyramid levels (Section 4.4) and
+// lays out every intermediate in one device arena allocated at pd_create:
+//   pyramid images      u8, level k of frame f at img_off, pitch round16(Wk)
+//   HOG cell atlas      f32 [9][atlas_rows][P]
+//   LBP cell atlas      u8  [59][atlas_rows][P]   (P = round16(max cells_x))
+//   score maps          f32, map of (f, k) at score_off, rows x cols
+//   boxes / counts      per frame
+// Every level owns a band of atlas rows, so one pair of tensor maps (encoded
+// once) covers all levels of all frames. The plan also carries the work
+// lists of the four kernels and the Q11 resample tables; it is packed into a
+// pinned host buffer and sent with one asynchronous copy per pd_detect.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pd_internal.h"
+
+using namespace pd;
+
+namespace {
+
+constexpr int64_t kAlign = 256;
+
+int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+struct Plan {
+    std::vector<FrameDesc> frames;
+    std::vector<LevelDesc> levels;
+    std::vector<ResizeItem> r_items;
+    std::vector<CellItem> c_items;
+    std::vector<SvmItem> s_items;
+    std::vector<int32_t> tabs;
+    int64_t pyr_bytes = 0;
+    int64_t score_floats = 0;
+    int32_t atlas_rows = 0;
+    int32_t max_wc = 0;
+    // frames of equal size share their Q11 tables: (W, H) -> first level index
+    std::map<std::pair<int, int>, int> tab_owner;
+
+    void clear() {
+        tab_owner.clear();
+        frames.clear();
+        levels.clear();
+        r_items.clear();
+        c_items.clear();
+        s_items.clear();
+        tabs.clear();
+        pyr_bytes = score_floats = 0;
+        atlas_rows = max_wc = 0;
+    }
+};
+
+// Byte offsets of the plan's sections inside the packed descriptor block.
+struct Packed {
+    int64_t frames, levels, r_items, c_items, s_items, tabs, total;
+};
+
+Packed pack_layout(const Plan &p) {
+    Packed o;
+    int64_t off = 0;
+    auto take = [&](int64_t bytes) {
+        int64_t at = off;
+        off = round_up(off + bytes, 16);
+        return at;
+    };
+    o.frames = take((int64_t)p.frames.size() * sizeof(FrameDesc));
+    o.levels = take((int64_t)p.levels.size() * sizeof(LevelDesc));
+    o.r_items = take((int64_t)p.r_items.size() * sizeof(ResizeItem));
+    o.c_items = take((int64_t)p.c_items.size() * sizeof(CellItem));
+    o.s_items = take((int64_t)p.s_items.size() * sizeof(SvmItem));
+    o.tabs = take((int64_t)p.tabs.size() * sizeof(int32_t));
+    o.total = off;
+    return o;
+}
+
+// Q11 source index and weight of destination coordinate x for a resize of
+// n source samples to m: round-half-up of ((x + 0.5) * n / m - 0.5) * 2048,
+// clamped to the first / last sample. Packed as index << 11 | weight.
+int32_t q11_entry(int x, int n, int m) {
+    const int64_t num = ((int64_t)(2 * x + 1) * n - m) * 2048 + m;
+    const int64_t den = 2 * (int64_t)m;
+    int64_t q = num / den;
+    if (num % den != 0 && num < 0) q -= 1;
+    int32_t idx, a;
+    if (q < 0) {
+        idx = 0;
+        a = 0;
+    } else {
+        idx = (int32_t)(q >> 11);
+        a = (int32_t)(q & 2047);
+        if (idx >= n - 1) {
+            idx = n - 1;
+            a = 0;
+        }
+    }
+    return (idx << 11) | a;
+}
+
+int level_sizes(int W, int H, double factor, int max_levels, int32_t *Wk, int32_t *Hk) {
+    if (!(factor > 1.0) || W < 0 || H < 0) return PD_EINVAL;
+    int n = 0;
+    for (int k = 0; n < max_levels; ++k) {
+        const double s = std::pow(factor, (double)k);
+        const int wk = (int)std::floor((double)W / s + 1e-9);
+        const int hk = (int)std::floor((double)H / s + 1e-9);
+        if (wk < 64 || hk < 128) break;
+        Wk[n] = wk;
+        Hk[n] = hk;
+        ++n;
+    }
+    return n;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+}  // namespace
+
+namespace pd {
+
+void build_lbp_bin_table(uint8_t table[256]) {
+    // uniform = at most two 0/1 transitions around the 8-bit circle; uniform
+    // codes are numbered in increasing order, all others share the last bin
+    int rank = 0;
+    for (int c = 0; c < 256; ++c) {
+        const int rot = ((c >> 1) | (c << 7)) & 255;
+        const int transitions = __builtin_popcount((unsigned)(c ^ rot));
+        table[c] = transitions <= 2 ? (uint8_t)rank++ : (uint8_t)(kLbpBins - 1);
+    }
+}
+
+int encode_plane_map(CUtensorMap *map, void *base, CUtensorMapDataType dtype, int elem_bytes,
+                     int64_t pitch, int64_t rows, int64_t planes, int64_t plane_stride_elems,
+                     uint32_t box_x, uint32_t box_y, uint32_t box_planes) {
+    auto fn = get_encode();
+    if (!fn) return PD_ECUDA;
+    cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)rows, (cuuint64_t)planes};
+    cuuint64_t strides[2] = {(cuuint64_t)(pitch * elem_bytes), (cuuint64_t)(plane_stride_elems * elem_bytes)};
+    cuuint32_t box[3] = {box_x, box_y, box_planes};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, dtype, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? PD_OK : PD_ECUDA;
+}
+
+}  // namespace pd
+
+struct pd_handle {
+    pd_params p{};
+    int device = 0;
+    float bias = 0.f;
+    // arena
+    unsigned char *arena = nullptr;
+    size_t arena_bytes = 0;
+    float *d_w = nullptr;          // [95][15][8]
+    uint8_t *d_lbp_map = nullptr;  // [256]
+    unsigned char *d_desc = nullptr;
+    int64_t desc_cap = 0;
+    uint8_t *d_pyr = nullptr;
+    int64_t pyr_cap = 0;
+    CellAtlas atlas{};
+    float *d_scores = nullptr;
+    int64_t score_cap = 0;
+    pd_box *d_boxes = nullptr;
+    int32_t *d_counts = nullptr;  // [2 * max_frames]
+    unsigned *d_err = nullptr;
+    uint8_t *d_frames = nullptr;  // host-input staging for pd_detect_host
+    int64_t frames_cap = 0;
+    int64_t level_cap = 0, r_cap = 0, c_cap = 0, s_cap = 0, tab_cap = 0;
+    // pinned host
+    unsigned char *h_desc = nullptr;
+    pd_box *h_boxes = nullptr;
+    int32_t *h_counts = nullptr;
+    unsigned *h_err = nullptr;
+    cudaEvent_t desc_done = nullptr;
+    // tensor maps over the atlases
+    CUtensorMap hog_map{}, lbp_map{};
+    // last batch
+    Plan plan;
+    cudaStream_t stream = nullptr;
+    bool detected = false, synced = false;
+    int last_launches = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(pd_handle *h, int code, const char *fmt, ...) {
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return code;
+}
+
+#define PD_CUDA(h, call)                                                                     \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) return fail((h), PD_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Adds one level to the plan (tables, descriptor, work items).
+void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int64_t img_off,
+                int32_t img_pitch, const LevelDesc *share = nullptr) {
+    LevelDesc L{};
+    L.img_off = img_off;
+    L.img_pitch = img_pitch;
+    L.frame = frame;
+    L.level = level;
+    L.W = W;
+    L.H = H;
+    L.Wk = Wk;
+    L.Hk = Hk;
+    L.Wc = Wk / 8;
+    L.Hc = Hk / 8;
+    L.cell_row = p.atlas_rows;
+    L.rows = std::max(L.Hc - kWinBH, 0);  // block rows Hc-1, window height 15 blocks
+    L.cols = std::max(L.Wc - kWinBW, 0);
+    if (L.rows == 0 || L.cols == 0) L.rows = L.cols = 0;
+    L.score_off = p.score_floats;
+    if (share) {
+        L.xtab_off = share->xtab_off;
+        L.ytab_off = share->ytab_off;
+    } else {
+        L.xtab_off = (int32_t)p.tabs.size();
+        for (int x = 0; x < Wk; ++x) p.tabs.push_back(q11_entry(x, W, Wk));
+        L.ytab_off = (int32_t)p.tabs.size();
+        for (int y = 0; y < Hk; ++y) p.tabs.push_back(q11_entry(y, H, Hk));
+    }
+    const int li = (int)p.levels.size();
+    for (int cy = 0; cy < L.Hc; cy += kCellTH)
+        for (int cx = 0; cx < L.Wc; cx += kCellTW) p.c_items.push_back({li, cx, cy, 0});
+    for (int wy = 0; wy < L.rows; wy += kSvmTH)
+        for (int wx = 0; wx < L.cols; wx += kSvmTW) p.s_items.push_back({li, wx, wy, 0});
+    p.atlas_rows += L.Hc;
+    p.score_floats += (int64_t)L.rows * L.cols;
+    p.max_wc = std::max(p.max_wc, L.Wc);
+    p.levels.push_back(L);
+}
+
+// Plans one frame with the pyramid rule; returns PD_OK or an error.
+int plan_frame(Plan &p, const pd_params &prm, const uint8_t *ptr, int W, int H, int pitch) {
+    int32_t Wk[PD_MAX_LEVELS], Hk[PD_MAX_LEVELS];
+    int n = level_sizes(W, H, prm.pyr_factor, PD_MAX_LEVELS, Wk, Hk);
+    if (n < 0) return n;
+    FrameDesc fd{};
+    fd.ptr = ptr;
+    fd.W = W;
+    fd.H = H;
+    fd.pitch = pitch;
+    fd.first_level = (int32_t)p.levels.size();
+    fd.n_levels = n;
+    const int f = (int)p.frames.size();
+    auto owner = p.tab_owner.find({W, H});
+    const int first_shared = owner == p.tab_owner.end() ? -1 : owner->second;
+    if (first_shared < 0 && n > 0) p.tab_owner[{W, H}] = (int)p.levels.size();
+    for (int k = 0; k < n; ++k) {
+        const int32_t lp = (int32_t)round_up(Wk[k], 16);
+        const LevelDesc share = first_shared >= 0 ? p.levels[first_shared + k] : LevelDesc{};
+        plan_level(p, f, k, W, H, Wk[k], Hk[k], p.pyr_bytes, lp, first_shared >= 0 ? &share : nullptr);
+        p.pyr_bytes += (int64_t)lp * Hk[k];
+    }
+    if (n > 0)
+        for (int y = 0; y < H; y += kResizeTH)
+            for (int x = 0; x < W; x += kResizeTW) p.r_items.push_back({f, x, y, 0});
+    p.frames.push_back(fd);
+    return PD_OK;
+}
+
+bool params_ok(const pd_params *p) {
+    return p && p->struct_size == sizeof(pd_params) && p->pyr_factor > 1.0f && p->l2hys_clip > 0.f &&
+           p->nms_iou >= 0.f && p->max_boxes_per_frame > 0 && p->max_candidates_per_frame > 0 &&
+           p->max_candidates_per_frame <= 16384 && p->max_frames > 0 && p->max_width > 0 &&
+           p->max_height > 0;
+}
+
+// Packs the plan into the pinned staging buffer and sends it to the device.
+int upload_plan(pd_handle *h, cudaStream_t s, const Plan &p, Packed &o) {
+    o = pack_layout(p);
+    if (o.total > h->desc_cap) return fail(h, PD_EINVAL, "plan descriptors exceed the arena");
+    PD_CUDA(h, cudaEventSynchronize(h->desc_done));  // previous copy has left the staging buffer
+    auto put = [&](int64_t off, const void *src, size_t bytes) {
+        if (bytes) std::memcpy(h->h_desc + off, src, bytes);
+    };
+    put(o.frames, p.frames.data(), p.frames.size() * sizeof(FrameDesc));
+    put(o.levels, p.levels.data(), p.levels.size() * sizeof(LevelDesc));
+    put(o.r_items, p.r_items.data(), p.r_items.size() * sizeof(ResizeItem));
+    put(o.c_items, p.c_items.data(), p.c_items.size() * sizeof(CellItem));
+    put(o.s_items, p.s_items.data(), p.s_items.size() * sizeof(SvmItem));
+    put(o.tabs, p.tabs.data(), p.tabs.size() * sizeof(int32_t));
+    if (o.total) PD_CUDA(h, cudaMemcpyAsync(h->d_desc, h->h_desc, o.total, cudaMemcpyHostToDevice, s));
+    PD_CUDA(h, cudaEventRecord(h->desc_done, s));
+    return PD_OK;
+}
+
+template <class T>
+const T *dptr(pd_handle *h, int64_t off) {
+    return reinterpret_cast<const T *>(h->d_desc + off);
+}
+
+}  // namespace
+
+extern "C" {
+
+int pd_params_default(pd_params *p) {
+    if (!p) return PD_EINVAL;
+    std::memset(p, 0, sizeof *p);
+    p->struct_size = sizeof(pd_params);
+    p->pyr_factor = 1.05f;
+    p->l2hys_clip = 0.2f;
+    p->threshold = 0.0f;
+    p->nms_iou = 0.5f;
+    p->max_boxes_per_frame = 4096;
+    p->max_candidates_per_frame = 16384;
+    p->max_frames = 1;
+    p->max_width = 1242;
+    p->max_height = 375;
+    p->flags = 0;
+    return PD_OK;
+}
+
+int pd_pyramid(int W, int H, float factor, int max_levels, int32_t *Wk, int32_t *Hk) {
+    if (!Wk || !Hk || max_levels < 0) return PD_EINVAL;
+    return level_sizes(W, H, factor, max_levels, Wk, Hk);
+}
+
+const char *pd_last_error(const pd_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+int pd_last_launch_count(const pd_handle *h) { return h ? h->last_launches : 0; }
+
+void pd_destroy(pd_handle *h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    if (h->arena) cudaFree(h->arena);
+    if (h->h_desc) cudaFreeHost(h->h_desc);
+    if (h->h_boxes) cudaFreeHost(h->h_boxes);
+    if (h->h_counts) cudaFreeHost(h->h_counts);
+    if (h->desc_done) cudaEventDestroy(h->desc_done);
+    delete h;
+}
+
+int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handle **out) {
+    if (!out) return PD_EINVAL;
+    *out = nullptr;
+    if (!params_ok(params) || !svm_w) return PD_EINVAL;
+    pd_handle *h = new pd_handle();
+    h->p = *params;
+    h->bias = svm_b;
+    auto bail = [&](int code) {
+        pd_destroy(h);
+        return code;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess) return bail(PD_ECUDA);
+    if (init_cells() != cudaSuccess || init_svm() != cudaSuccess || init_nms() != cudaSuccess)
+        return bail(PD_ECUDA);
+
+    // Worst-case plan: max_frames frames of max_width x max_height.
+    Plan worst;
+    for (int f = 0; f < params->max_frames; ++f)
+        if (plan_frame(worst, *params, nullptr, params->max_width, params->max_height,
+                       params->max_width) != PD_OK)
+            return bail(PD_EINVAL);
+    if (worst.levels.empty()) {
+        // frames too small for any window still get a valid (tiny) arena
+        worst.max_wc = std::max(params->max_width / 8, 1);
+    }
+    const Packed wp = pack_layout(worst);
+    h->desc_cap = round_up(wp.total + 4096, kAlign);
+    h->pyr_cap = round_up(std::max<int64_t>(worst.pyr_bytes, 16), kAlign);
+    const int32_t P = (int32_t)std::max<int64_t>(round_up(std::max(worst.max_wc, 1), 16), 48);
+    const int32_t rows = std::max(worst.atlas_rows, 1);
+    h->atlas.pitch = P;
+    h->atlas.rows = rows;
+    h->atlas.hog_plane = (int64_t)rows * P;
+    h->atlas.lbp_plane = (int64_t)rows * P;
+    h->score_cap = std::max<int64_t>(worst.score_floats, 1);
+    h->frames_cap = (int64_t)params->max_frames * round_up(params->max_width, 16) * params->max_height;
+
+    struct Part {
+        int64_t bytes;
+        int64_t off;
+    };
+    std::vector<Part> parts = {
+        {(int64_t)kFeat * kWinBH * kWPad * 4, 0},                  // 0 template
+        {256, 0},                                                  // 1 lbp map
+        {h->desc_cap, 0},                                          // 2 descriptors
+        {h->pyr_cap, 0},                                           // 3 pyramid
+        {(int64_t)kHogBins * h->atlas.hog_plane * 4, 0},           // 4 hog atlas
+        {(int64_t)kLbpBins * h->atlas.lbp_plane, 0},               // 5 lbp atlas
+        {h->score_cap * 4, 0},                                     // 6 scores
+        {(int64_t)params->max_frames * params->max_boxes_per_frame * (int64_t)sizeof(pd_box), 0},  // 7
+        {(int64_t)params->max_frames * 2 * 4 + 16, 0},             // 8 counts + error word
+        {h->frames_cap, 0},                                        // 9 host-input frames
+    };
+    int64_t total = 0;
+    for (auto &pt : parts) {
+        pt.off = total;
+        total = round_up(total + pt.bytes, kAlign);
+    }
+    h->arena_bytes = (size_t)total;
+    if (cudaMalloc(&h->arena, h->arena_bytes) != cudaSuccess) return bail(PD_ENOMEM);
+    if (cudaMemset(h->arena, 0, h->arena_bytes) != cudaSuccess) return bail(PD_ECUDA);
+    h->d_w = reinterpret_cast<float *>(h->arena + parts[0].off);
+    h->d_lbp_map = h->arena + parts[1].off;
+    h->d_desc = h->arena + parts[2].off;
+    h->d_pyr = h->arena + parts[3].off;
+    h->atlas.hog = reinterpret_cast<float *>(h->arena + parts[4].off);
+    h->atlas.lbp = h->arena + parts[5].off;
+    h->d_scores = reinterpret_cast<float *>(h->arena + parts[6].off);
+    h->d_boxes = reinterpret_cast<pd_box *>(h->arena + parts[7].off);
+    h->d_counts = reinterpret_cast<int32_t *>(h->arena + parts[8].off);
+    h->d_err = reinterpret_cast<unsigned *>(h->d_counts + 2 * params->max_frames);
+    h->d_frames = h->arena + parts[9].off;
+
+    if (cudaMallocHost(&h->h_desc, h->desc_cap) != cudaSuccess) return bail(PD_ENOMEM);
+    if (cudaMallocHost(&h->h_boxes, (size_t)params->max_frames * params->max_boxes_per_frame *
+                                        sizeof(pd_box)) != cudaSuccess)
+        return bail(PD_ENOMEM);
+    if (cudaMallocHost(&h->h_counts, (size_t)params->max_frames * 2 * 4 + 16) != cudaSuccess)
+        return bail(PD_ENOMEM);
+    h->h_err = reinterpret_cast<unsigned *>(h->h_counts + 2 * params->max_frames);
+    if (cudaEventCreateWithFlags(&h->desc_done, cudaEventDisableTiming) != cudaSuccess)
+        return bail(PD_ECUDA);
+    if (cudaEventRecord(h->desc_done, 0) != cudaSuccess) return bail(PD_ECUDA);
+
+    // template -> [t][i][8] (j padded), lbp map
+    std::vector<float> wt((size_t)kFeat * kWinBH * kWPad, 0.f);
+    for (int i = 0; i < kWinBH; ++i)
+        for (int j = 0; j < kWinBW; ++j)
+            for (int t = 0; t < kFeat; ++t)
+                wt[((size_t)t * kWinBH + i) * kWPad + j] = svm_w[((size_t)i * kWinBW + j) * kFeat + t];
+    uint8_t map[256];
+    build_lbp_bin_table(map);
+    if (cudaMemcpy(h->d_w, wt.data(), wt.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_lbp_map, map, 256, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(PD_ECUDA);
+    if (encode_plane_map(&h->hog_map, h->atlas.hog, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, P, rows,
+                         kHogBins, h->atlas.hog_plane, 40, kSvmTH + kWinBH, kHogBins) != PD_OK ||
+        encode_plane_map(&h->lbp_map, h->atlas.lbp, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, P, rows,
+                         kLbpBins, h->atlas.lbp_plane, 48, kSvmTH + kWinBH, kLbpBins) != PD_OK)
+        return bail(PD_ECUDA);
+    *out = h;
+    return PD_OK;
+}
+
+int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_frames,
+              const int32_t *widths, const int32_t *heights, const int32_t *pitches) {
+    if (!h) return PD_EINVAL;
+    h->detected = h->synced = false;
+    h->last_launches = 0;
+    if (n_frames < 0 || n_frames > h->p.max_frames)
+        return fail(h, PD_EINVAL, "n_frames %d outside [0, %d]", n_frames, h->p.max_frames);
+    if (n_frames > 0 && (!d_frames || !widths || !heights || !pitches))
+        return fail(h, PD_EINVAL, "null argument");
+    Plan &p = h->plan;
+    p.clear();
+    for (int f = 0; f < n_frames; ++f) {
+        const int W = widths[f], H = heights[f], pitch = pitches[f];
+        if (W < 1 || H < 1 || W > h->p.max_width || H > h->p.max_height || pitch < W || !d_frames[f])
+            return fail(h, PD_EINVAL, "frame %d: bad size %dx%d pitch %d", f, W, H, pitch);
+        int r = plan_frame(p, h->p, d_frames[f], W, H, pitch);
+        if (r != PD_OK) return fail(h, r, "frame %d: planning failed", f);
+    }
+    if (p.atlas_rows > h->atlas.rows || p.pyr_bytes > h->pyr_cap || p.score_floats > h->score_cap)
+        return fail(h, PD_EINVAL, "batch exceeds the arena");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->stream = s;
+    Packed o;
+    int r = upload_plan(h, s, p, o);
+    if (r != PD_OK) return r;
+    PD_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), s));
+    const FrameDesc *df = dptr<FrameDesc>(h, o.frames);
+    const LevelDesc *dl = dptr<LevelDesc>(h, o.levels);
+    PD_CUDA(h, launch_resize(s, df, dl, dptr<int32_t>(h, o.tabs), h->d_pyr, dptr<ResizeItem>(h, o.r_items),
+                             (int)p.r_items.size()));
+    PD_CUDA(h, launch_cells(s, dl, h->d_pyr, h->atlas, dptr<CellItem>(h, o.c_items), (int)p.c_items.size(),
+                            h->d_lbp_map));
+    PD_CUDA(h, launch_svm(s, &h->hog_map, &h->lbp_map, dl, h->atlas.pitch, h->d_w, h->bias,
+                          h->p.l2hys_clip, h->d_scores, dptr<SvmItem>(h, o.s_items),
+                          (int)p.s_items.size(), h->d_err));
+    PD_CUDA(h, launch_nms(s, df, dl, n_frames, h->d_scores, h->p.threshold, h->p.nms_iou, nullptr,
+                          h->p.max_candidates_per_frame, h->d_boxes, h->p.max_boxes_per_frame,
+                          h->d_counts));
+    h->last_launches = (p.r_items.empty() ? 0 : 1) + (p.c_items.empty() ? 0 : 1) +
+                       (p.s_items.empty() ? 0 : 1) + (n_frames > 0 ? 1 : 0);
+    h->detected = true;
+    return PD_OK;
+}
+
+int pd_detect_host(pd_handle *h, void *stream, int n_frames, const uint8_t *const *h_frames,
+                   const int32_t *widths, const int32_t *heights, const int32_t *pitches) {
+    if (!h) return PD_EINVAL;
+    if (n_frames < 0 || n_frames > h->p.max_frames)
+        return fail(h, PD_EINVAL, "n_frames %d outside [0, %d]", n_frames, h->p.max_frames);
+    if (n_frames > 0 && (!h_frames || !widths || !heights || !pitches))
+        return fail(h, PD_EINVAL, "null argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<const uint8_t *> dev((size_t)n_frames);
+    std::vector<int32_t> dp((size_t)n_frames);
+    int64_t off = 0;
+    for (int f = 0; f < n_frames; ++f) {
+        const int W = widths[f], H = heights[f];
+        if (W < 1 || H < 1 || W > h->p.max_width || H > h->p.max_height || pitches[f] < W || !h_frames[f])
+            return fail(h, PD_EINVAL, "frame %d: bad size %dx%d pitch %d", f, W, H, pitches[f]);
+        dp[f] = (int32_t)round_up(W, 16);
+        dev[f] = h->d_frames + off;
+        PD_CUDA(h, cudaMemcpy2DAsync(h->d_frames + off, dp[f], h_frames[f], pitches[f], W, H,
+                                     cudaMemcpyHostToDevice, s));
+        off += (int64_t)dp[f] * H;
+    }
+    return pd_detect(h, stream, n_frames, dev.data(), widths, heights, dp.data());
+}
+
+int pd_sync(pd_handle *h) {
+    if (!h) return PD_EINVAL;
+    if (!h->detected) return fail(h, PD_ESTATE, "pd_sync without pd_detect");
+    const int nf = (int)h->plan.frames.size();
+    PD_CUDA(h, cudaMemcpyAsync(h->h_counts, h->d_counts, (size_t)nf * 2 * 4, cudaMemcpyDeviceToHost, h->stream));
+    PD_CUDA(h, cudaMemcpyAsync(h->h_err, h->d_err, 4, cudaMemcpyDeviceToHost, h->stream));
+    PD_CUDA(h, cudaStreamSynchronize(h->stream));
+    int status = PD_OK;
+    if (*h->h_err & kErrTimeout) status = fail(h, PD_ETIMEOUT, "device wait timed out");
+    else if (*h->h_err & kErrBounds) status = fail(h, PD_EBOUNDS, "device bounds check fired");
+    for (int f = 0; f < nf; ++f) {
+        const int kept = h->h_counts[2 * f];
+        if (h->h_counts[2 * f + 1] < 0 && status == PD_OK)
+            status = fail(h, PD_EOVERFLOW, "frame %d: %d candidates > %d", f, -h->h_counts[2 * f + 1],
+                          h->p.max_candidates_per_frame);
+        if (kept > 0)
+            PD_CUDA(h, cudaMemcpyAsync(h->h_boxes + (size_t)f * h->p.max_boxes_per_frame,
+                                       h->d_boxes + (size_t)f * h->p.max_boxes_per_frame,
+                                       (size_t)kept * sizeof(pd_box), cudaMemcpyDeviceToHost, h->stream));
+    }
+    PD_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->synced = true;
+    return status;
+}
+
+int pd_frame_levels(const pd_handle *h, int frame, int *n_levels, pd_level_info *info) {
+    if (!h || !n_levels || !info || !h->detected) return PD_EINVAL;
+    if (frame < 0 || frame >= (int)h->plan.frames.size()) return PD_EINVAL;
+    const FrameDesc &fd = h->plan.frames[frame];
+    *n_levels = fd.n_levels;
+    for (int k = 0; k < fd.n_levels; ++k) {
+        const LevelDesc &L = h->plan.levels[fd.first_level + k];
+        info[k].width = L.Wk;
+        info[k].height = L.Hk;
+        info[k].cells_x = L.Wc;
+        info[k].cells_y = L.Hc;
+        info[k].rows = L.rows;
+        info[k].cols = L.cols;
+        info[k].score_offset = L.score_off;
+    }
+    return PD_OK;
+}
+
+int pd_scores(const pd_handle *h, const float **d_scores, int64_t *total) {
+    if (!h || !d_scores || !total) return PD_EINVAL;
+    *d_scores = h->d_scores;
+    *total = h->detected ? h->plan.score_floats : 0;
+    return PD_OK;
+}
+
+int pd_boxes(const pd_handle *h, int frame, pd_box *out, int cap, int *count) {
+    if (!h || !count || (cap > 0 && !out)) return PD_EINVAL;
+    if (!h->synced) return PD_ESTATE;
+    if (frame < 0 || frame >= (int)h->plan.frames.size()) return PD_EINVAL;
+    const int kept = h->h_counts[2 * frame];
+    *count = kept;
+    const int n = std::min(kept, cap);
+    if (n > 0)
+        std::memcpy(out, h->h_boxes + (size_t)frame * h->p.max_boxes_per_frame, (size_t)n * sizeof(pd_box));
+    return PD_OK;
+}
+
+// ----------------------------------------------------------------------------- stage entry points
+int pd_resize_levels(pd_handle *h, void *stream, const uint8_t *d_frame, int W, int H, int pitch,
+                     int n_levels, const int32_t *Wk, const int32_t *Hk, uint8_t *d_levels,
+                     const int64_t *level_offsets, const int32_t *level_pitches) {
+    if (!h) return PD_EINVAL;
+    if (!d_frame || !d_levels || !Wk || !Hk || !level_offsets || !level_pitches || W < 1 || H < 1 ||
+        pitch < W || n_levels < 0 || n_levels > PD_MAX_LEVELS)
+        return fail(h, PD_EINVAL, "pd_resize_levels: bad argument");
+    Plan p;
+    FrameDesc fd{};
+    fd.ptr = d_frame;
+    fd.W = W;
+    fd.H = H;
+    fd.pitch = pitch;
+    fd.first_level = 0;
+    fd.n_levels = n_levels;
+    for (int k = 0; k < n_levels; ++k) {
+        if (Wk[k] < 1 || Hk[k] < 1 || Wk[k] > W || Hk[k] > H || level_pitches[k] < Wk[k])
+            return fail(h, PD_EINVAL, "pd_resize_levels: level %d size %dx%d", k, Wk[k], Hk[k]);
+        plan_level(p, 0, k, W, H, Wk[k], Hk[k], level_offsets[k], level_pitches[k]);
+    }
+    for (int y = 0; y < H; y += kResizeTH)
+        for (int x = 0; x < W; x += kResizeTW) p.r_items.push_back({0, x, y, 0});
+    p.frames.push_back(fd);
+    p.c_items.clear();
+    p.s_items.clear();
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Packed o;
+    int r = upload_plan(h, s, p, o);
+    if (r != PD_OK) return r;
+    PD_CUDA(h, launch_resize(s, dptr<FrameDesc>(h, o.frames), dptr<LevelDesc>(h, o.levels),
+                             dptr<int32_t>(h, o.tabs), d_levels, dptr<ResizeItem>(h, o.r_items),
+                             (int)p.r_items.size()));
+    return PD_OK;
+}
+
+int pd_cell_features(pd_handle *h, void *stream, const uint8_t *d_level, int Wk, int Hk, int pitch,
+                     float *d_hog, int64_t hog_plane, uint8_t *d_lbp, int64_t lbp_plane, int cell_pitch) {
+    if (!h) return PD_EINVAL;
+    const int Wc = Wk / 8, Hc = Hk / 8;
+    if (!d_level || !d_hog || !d_lbp || Wk < 1 || Hk < 1 || pitch < Wk || cell_pitch < Wc ||
+        cell_pitch % 16 != 0 || hog_plane < (int64_t)Hc * cell_pitch || lbp_plane < (int64_t)Hc * cell_pitch)
+        return fail(h, PD_EINVAL, "pd_cell_features: bad argument");
+    Plan p;
+    plan_level(p, 0, 0, Wk, Hk, Wk, Hk, 0, pitch);
+    p.s_items.clear();
+    p.tabs.clear();
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Packed o;
+    int r = upload_plan(h, s, p, o);
+    if (r != PD_OK) return r;
+    CellAtlas a{};
+    a.hog = d_hog;
+    a.lbp = d_lbp;
+    a.hog_plane = hog_plane;
+    a.lbp_plane = lbp_plane;
+    a.pitch = cell_pitch;
+    a.rows = Hc;
+    PD_CUDA(h, launch_cells(s, dptr<LevelDesc>(h, o.levels), d_level, a, dptr<CellItem>(h, o.c_items),
+                            (int)p.c_items.size(), h->d_lbp_map));
+    return PD_OK;
+}
+
+int pd_window_scores(pd_handle *h, void *stream, const float *d_hog, int64_t hog_plane,
+                     const uint8_t *d_lbp, int64_t lbp_plane, int cell_pitch, int cells_x, int cells_y,
+                     float *d_scores) {
+    if (!h) return PD_EINVAL;
+    if (!d_hog || !d_lbp || !d_scores || cells_x < 0 || cells_y < 0 || cell_pitch < cells_x ||
+        cell_pitch % 16 != 0 || hog_plane % 4 != 0 || lbp_plane % 16 != 0 ||
+        hog_plane < (int64_t)cells_y * cell_pitch || lbp_plane < (int64_t)cells_y * cell_pitch ||
+        (reinterpret_cast<uintptr_t>(d_hog) & 15) || (reinterpret_cast<uintptr_t>(d_lbp) & 15))
+        return fail(h, PD_EINVAL, "pd_window_scores: bad argument");
+    Plan p;
+    plan_level(p, 0, 0, 8 * cells_x, 8 * cells_y, 8 * cells_x, 8 * cells_y, 0, 8 * cells_x);
+    p.c_items.clear();
+    p.tabs.clear();
+    if (p.s_items.empty()) return PD_OK;
+    CUtensorMap hm, lm;
+    const int64_t rows = std::max(cells_y, 1);
+    if (encode_plane_map(&hm, const_cast<float *>(d_hog), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, cell_pitch,
+                         rows, kHogBins, hog_plane, 40, kSvmTH + kWinBH, kHogBins) != PD_OK ||
+        encode_plane_map(&lm, const_cast<uint8_t *>(d_lbp), CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, cell_pitch,
+                         rows, kLbpBins, lbp_plane, 48, kSvmTH + kWinBH, kLbpBins) != PD_OK)
+        return fail(h, PD_ECUDA, "pd_window_scores: tensor map encoding failed");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Packed o;
+    int r = upload_plan(h, s, p, o);
+    if (r != PD_OK) return r;
+    PD_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), s));
+    PD_CUDA(h, launch_svm(s, &hm, &lm, dptr<LevelDesc>(h, o.levels), cell_pitch, h->d_w, h->bias,
+                          h->p.l2hys_clip, d_scores, dptr<SvmItem>(h, o.s_items), (int)p.s_items.size(),
+                          h->d_err));
+    return PD_OK;
+}
+
+int pd_nms_maps(pd_handle *h, void *stream, const float *d_scores, int n_levels, const int32_t *rows,
+                const int32_t *cols, const int32_t *Wk, const int32_t *Hk, int W, int H, pd_box *d_boxes,
+                int max_boxes, int32_t *d_counts) {
+    if (!h) return PD_EINVAL;
+    if (!d_scores || !rows || !cols || !Wk || !Hk || !d_boxes || !d_counts || n_levels < 0 ||
+        n_levels > PD_MAX_LEVELS || max_boxes < 1 || W < 1 || H < 1)
+        return fail(h, PD_EINVAL, "pd_nms_maps: bad argument");
+    Plan p;
+    FrameDesc fd{};
+    fd.W = W;
+    fd.H = H;
+    fd.first_level = 0;
+    fd.n_levels = n_levels;
+    int64_t off = 0;
+    for (int k = 0; k < n_levels; ++k) {
+        if (rows[k] < 0 || cols[k] < 0 || rows[k] > 4096 || cols[k] > 4096 || Wk[k] < 1 || Hk[k] < 1)
+            return fail(h, PD_EINVAL, "pd_nms_maps: level %d", k);
+        LevelDesc L{};
+        L.W = W;
+        L.H = H;
+        L.Wk = Wk[k];
+        L.Hk = Hk[k];
+        L.rows = rows[k];
+        L.cols = cols[k];
+        L.score_off = off;
+        off += (int64_t)rows[k] * cols[k];
+        p.levels.push_back(L);
+    }
+    p.frames.push_back(fd);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Packed o;
+    int r = upload_plan(h, s, p, o);
+    if (r != PD_OK) return r;
+    PD_CUDA(h, launch_nms(s, dptr<FrameDesc>(h, o.frames), dptr<LevelDesc>(h, o.levels), 1, d_scores,
+                          h->p.threshold, h->p.nms_iou, nullptr, h->p.max_candidates_per_frame, d_boxes,
+                          max_boxes, d_counts));
+    return PD_OK;
+}
+
+}  // extern "C"
