@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the plain detector path on GB300.
+
+One step = the whole hot path (pyramid, LBP+HOG cell histograms, block
+normalisation + window scores, NMS) over one batch of synthetic 1242x375
+frames (the paper's frame size; pyramid factor 1.05 -> 23 levels, 33,428
+windows per frame). Frames are resident in HBM when the timed region starts;
+L2 is flushed (256 MB write) before every timed step and each step is timed
+with CUDA events on the detector's stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line. Under torchrun (N > 1) every rank runs an independent
+replica on its own frames (frames are independent: weak scaling, no
+collective on the data path); the step time is the max over ranks.
+`--impl reference` times the CPU oracle (test infrastructure) on the host.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WIDTH, HEIGHT = 1242, 375
+FACTOR = float(np.float32(1.05))
+CFG_ID = 2                      # scene recipe of the 1242x375 workload
+FLOP_PER_WINDOW = 2 * 15 * 7 * 95   # 9,975 FMA
+PAPER_FPS_1242x375 = 20.0       # Tegra X1, HOGLBP-SVM (context: another machine)
+L2_FLUSH_BYTES = 256 << 20
+METRIC = "frames/s (1242x375, HOG+LBP+SVM+NMS)"
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--frames-per-step", type=int, default=64)
+    ap.add_argument("--cpu-sample-frames", type=int, default=12,
+                    help="frames the CPU oracle times for cpu_baseline (bounded sample)")
+    return ap.parse_args(argv)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def rank_frame_indices(rank: int, frames_per_rank: int):
+    """Frames of a rank's replica: disjoint seeded scenes per rank."""
+    return list(range(rank * frames_per_rank, (rank + 1) * frames_per_rank))
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max of a per-rank scalar over all ranks (host logic; gloo or nccl)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def load_template():
+    d = np.load(os.path.join(ROOT, "tests", "golden", "svm_template_seed0.npz"))
+    return d["w"], float(d["b"])
+
+
+def make_frames(indices):
+    import synth
+    return [synth.make_scene(WIDTH, HEIGHT, CFG_ID, i) for i in indices]
+
+
+def windows_per_frame() -> int:
+    from paper_1611_01642_gb300 import pd_pyramid
+    return sum(max(hk // 8 - 15, 0) * max(wk // 8 - 7, 0) for wk, hk in pd_pyramid(WIDTH, HEIGHT, FACTOR))
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle samples (200 ms) while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = np.array([float(r[1]) for r in rows])
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        loaded = sm[sm >= 0.5 * sm.max()]
+        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def time_oracle(frames, w, b):
+    """Single-threaded FP64 oracle over `frames` (the full plain path per frame)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    for img in frames:
+        oracle.detect(img, w, b, FACTOR)
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w, b = load_template()
+    frames = make_frames(range(max(args.warmup, 0) + args.steps))
+    for img in frames[:args.warmup]:
+        time_oracle([img], w, b)
+    t = time_oracle(frames[args.warmup:args.warmup + args.steps], w, b)
+    fps = args.steps / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": fps / PAPER_FPS_1242x375, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{WIDTH}x{HEIGHT} u8 frames, pyramid factor 1.05 (23 levels), "
+                               "plain HOG+LBP+SVM+NMS", "frames_per_step": 1},
+        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} seeded {WIDTH}x{HEIGHT} frames, one per step, "
+                                   "single thread"},
+        "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU
+def _file_hash(path: str) -> str:
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per K4 launch from the committed ncu summary, if the kernel is unchanged."""
+    path = os.path.join(ROOT, "profiles", "k_svm_1242x375_b64.txt")
+    src = os.path.join(ROOT, "paper_1611_01642_gb300", "csrc", "k_svm.cu")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    with open(path) as f:
+        for line in f:
+            if "=" in line and line.startswith("@"):
+                k, v = line[1:].split("=", 1)
+                rec[k.strip()] = v.strip()
+    if rec.get("source_sha256_16") != _file_hash(src):
+        return None
+    try:
+        return float(rec["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_1611_01642_gb300 import build as pkg_build
+    pkg_build.build()
+    import paper_1611_01642_gb300 as pd
+
+    B = args.frames_per_step
+    w, b = load_template()
+    imgs = make_frames(rank_frame_indices(rank, B))
+    det = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=B, max_width=WIDTH, max_height=HEIGHT,
+                      flags=pd.PD_FLAG_STAGE_TIMING)
+    stream = torch.cuda.current_stream()
+    frames = [torch.from_numpy(im).cuda() for im in imgs]
+    pinned = [torch.from_numpy(im).pin_memory() for im in imgs]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    wpf = windows_per_frame()
+
+    def step():
+        det.detect(frames)
+        st = det.sync()
+        if st != pd.PD_OK:
+            raise RuntimeError(f"pd_sync: {pd.ERROR_NAMES.get(st, st)} {pd.pd_last_error(det.h)}")
+
+    for _ in range(max(args.warmup, 0)):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    total_ms, stage_ms = 0.0, np.zeros(4)
+    launches = 0
+    for i in range(args.steps):
+        flush.fill_(i & 255)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        det.detect(frames)
+        e1.record(stream)
+        st = det.sync()
+        if st != pd.PD_OK:
+            raise RuntimeError(f"pd_sync: {pd.ERROR_NAMES.get(st, st)} {pd.pd_last_error(det.h)}")
+        total_ms += e0.elapsed_time(e1)
+        stage_ms += np.array(pd.pd_stage_times(det.h))
+        launches += pd.pd_last_launch_count(det.h)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    total_ms = reduce_max(total_ms, world, device="cuda")
+    value = world * B * args.steps / (total_ms / 1e3)
+    ms_step = total_ms / args.steps
+    stage_step = stage_ms / args.steps
+
+    # end to end through the public API: host frames in, host boxes out
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for i in range(args.steps):
+        det.detect_host(pinned)
+        st = det.sync()
+        if st != pd.PD_OK:
+            raise RuntimeError(f"pd_sync: {pd.ERROR_NAMES.get(st, st)}")
+        d2h += 8 * B + 4 + sum(32 * len(det.boxes(f)) for f in range(B))
+    torch.cuda.synchronize()
+    e2e_s = reduce_max(time.perf_counter() - t0, world, device="cuda")
+    e2e = {"value": world * B * args.steps / e2e_s, "unit": "frames/s",
+           "h2d_bytes_per_step": int(sum(im.nbytes for im in imgs)),
+           "d2h_bytes_per_step": int(d2h // max(args.steps, 1))}
+
+    peaks, peak_kind = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = sm_count * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12  # TFLOP/s
+    achieved = B * wpf * FLOP_PER_WINDOW / (stage_step[2] / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": recorded_traffic(),
+                "kernel": "k_svm (block L2-Hys norm + window correlation, FP32 FMA)",
+                "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
+                              f"(max SM clock, {peak_kind})"}
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_sample_frames > 0:
+        n = min(args.cpu_sample_frames, B)
+        t = time_oracle(imgs[:n], w, b)
+        cpu = {"value": n / t, "unit": "frames/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n} of the step's {B} frames through the whole plain path, FP64, one thread"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_FPS_1242x375, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{WIDTH}x{HEIGHT} u8 frames, pyramid factor 1.05 (23 levels), "
+                               "plain HOG+LBP+SVM+NMS",
+                   "frames_per_step": B * world, "frames_per_gpu": B, "windows_per_frame": wpf,
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"{world} independent replicas"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "stage_ms_per_step": {"pyramid": stage_step[0], "cells": stage_step[1], "norm_svm": stage_step[2],
+                              "nms": stage_step[3]},
+        "px_per_ns": B * WIDTH * HEIGHT / (ms_step * 1e6),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    det.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -55,6 +55,9 @@ extern "C" {
 #define PD_TEMPLATE_SIZE (PD_WIN_BH * PD_WIN_BW * PD_FEAT) /* 9975 */
 #define PD_MAX_LEVELS 96
 
+/* pd_params.flags */
+#define PD_FLAG_STAGE_TIMING 1 /* record CUDA events around each kernel of pd_detect */
+
 typedef struct pd_handle pd_handle;
 
 /* Detector parameters. Fill with pd_params_default() and then override.
@@ -70,7 +73,7 @@ typedef struct pd_params {
     int32_t max_frames;      /* frames per pd_detect call (arena sizing) */
     int32_t max_width;       /* largest frame width  (arena sizing) */
     int32_t max_height;      /* largest frame height (arena sizing) */
-    int32_t flags;           /* reserved, 0 */
+    int32_t flags;           /* PD_FLAG_* bits, 0 by default */
 } pd_params;
 
 /* One detection: a window in frame coordinates. */
@@ -153,6 +156,13 @@ int pd_boxes(const pd_handle *h, int frame, pd_box *out, int cap, int *count);
 
 /* Number of this library's kernel launches issued by the last pd_detect. */
 int pd_last_launch_count(const pd_handle *h);
+
+/* Device time in milliseconds of each kernel of the last pd_detect, from CUDA
+ * events recorded on its stream around each launch: ms[0] pyramid (K1),
+ * ms[1] cell histograms (K2/K3), ms[2] block norm + window scores (K4),
+ * ms[3] NMS (K5). Needs PD_FLAG_STAGE_TIMING at pd_create and a pd_sync
+ * after the detect (else PD_ESTATE). */
+int pd_stage_times(const pd_handle *h, float *ms);
 
 /* Same as pd_detect with frames in HOST memory (h_frames: host array of host
  * pointers; pinned memory gives the fastest copies): the library copies each

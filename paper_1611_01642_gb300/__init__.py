@@ -28,10 +28,11 @@ ERROR_NAMES = {0: "PD_OK", -1: "PD_EINVAL", -2: "PD_ENOMEM", -3: "PD_ECUDA", -4:
                -5: "PD_EBOUNDS", -6: "PD_ESTATE", -7: "PD_EOVERFLOW"}
 HOG_BINS, LBP_BINS, FEAT, WIN_BW, WIN_BH = 9, 59, 95, 7, 15
 MAX_LEVELS = 96
+PD_FLAG_STAGE_TIMING = 1
 
 EXPORTED = ["pd_params_default", "pd_pyramid", "pd_create", "pd_destroy", "pd_last_error",
             "pd_detect", "pd_detect_host", "pd_sync", "pd_frame_levels", "pd_scores", "pd_boxes",
-            "pd_last_launch_count", "pd_resize_levels", "pd_cell_features", "pd_window_scores",
+            "pd_last_launch_count", "pd_stage_times", "pd_resize_levels", "pd_cell_features", "pd_window_scores",
             "pd_nms_maps"]
 
 
@@ -96,6 +97,7 @@ def load(path: str | None = None):
         "pd_scores": ([P, P, P], i),
         "pd_boxes": ([P, i, P, i, P], i),
         "pd_last_launch_count": ([P], i),
+        "pd_stage_times": ([P, P], i),
         "pd_resize_levels": ([P, P, P, i, i, i, i, P, P, P, P, P], i),
         "pd_cell_features": ([P, P, P, i, i, i, P, i64, P, i64, i], i),
         "pd_window_scores": ([P, P, P, i64, P, i64, i, i, i, P], i),
@@ -230,6 +232,13 @@ def pd_boxes(h, frame: int, cap: int = 4096) -> np.ndarray:
 
 def pd_last_launch_count(h) -> int:
     return load().pd_last_launch_count(h)
+
+
+def pd_stage_times(h):
+    """[K1, K2/K3, K4, K5] device milliseconds of the last detect (needs PD_FLAG_STAGE_TIMING)."""
+    ms = np.zeros(4, np.float32)
+    _check(load().pd_stage_times(h, ms.ctypes.data_as(ctypes.c_void_p)), h)
+    return [float(v) for v in ms]
 
 
 def pd_resize_levels(h, frame, level_dims, out, offsets, pitches, stream=None) -> None:

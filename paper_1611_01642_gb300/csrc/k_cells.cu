@@ -1,11 +1,13 @@
 // K2 + K3 -- HOG and uniform-LBP cell histograms of one pyramid level
 // (Section 4.2, Algorithms 1-2; Section 4.3, Algorithms 4-5).
 //
-// One CTA of 128 threads owns a tile of 15 x 8 cells (120 x 64 pixels). Thread
-// t owns pixel column x = 8*cx0 - 4 + t, i.e. the tile's columns plus the 4
-// columns on each side whose HOG votes still reach the tile, and walks down
-// the rows [8*cy0 - 4, 8*cy0 + 68) with its 3x3 neighbourhood kept in
-// registers (one new row of 3 bytes per step, coalesced across the warp).
+// One CTA of 128 threads owns a tile of 15 x 8 cells (120 x 64 pixels). It
+// first stages the 130 x 74 pixel region it reads (the tile, the 4 pixels on
+// each side whose HOG votes still reach it, and the 1-pixel gradient halo,
+// with the level's clamp-to-edge border baked in) in shared memory with one
+// burst of coalesced loads. Thread t then owns pixel column
+// x = 8*cx0 - 4 + t and walks down the rows [8*cy0 - 4, 8*cy0 + 68) with its
+// 3x3 neighbourhood kept in registers (one new row of 3 bytes per step).
 //
 // Per pixel:
 //  * LBP (Algorithm 1): 8 comparisons with the clockwise neighbours (a
@@ -32,11 +34,14 @@ constexpr int kThreads = 128;
 constexpr int kTW = kCellTW;   // 15 cells
 constexpr int kTH = kCellTH;   // 8 cells
 constexpr int kCols = 8 * kTW + 8;  // 128 columns (one per thread)
+constexpr int kPixCols = kCols + 2;  // + gradient / LBP halo
+constexpr int kPixRows = 8 * kTH + 10;
 
 struct CellSmem {
     float R[kTH][kHogBins][kCols];       // vertical HOG partial sums per column
     uint32_t cnt[kTH][kTW][kLbpBins];    // LBP counts per cell
     uint8_t map[256];                    // LBP code -> uniform bin
+    uint8_t pix[kPixRows][kPixCols];     // pixels [8cy0-5, 8cy0+69) x [8cx0-5, 8cx0+125), clamped
 };
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
@@ -61,22 +66,34 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
         for (int b = 0; b < kHogBins; ++b) S.R[r][b][tid] = 0.f;
     for (int i = tid; i < kTH * kTW * kLbpBins; i += kThreads) (&S.cnt[0][0][0])[i] = 0u;
     for (int i = tid; i < 256; i += kThreads) S.map[i] = lbp_map[i];
+    const int px0 = 8 * it.cx0 - 5, py0 = 8 * it.cy0 - 5;
+    {
+        const int c0 = tid, c1 = tid + kThreads;
+        const int x0c = clampi(px0 + c0, 0, Wk - 1);
+        const int x1c = clampi(px0 + c1, 0, Wk - 1);
+#pragma unroll 8
+        for (int r = 0; r < kPixRows; ++r) {
+            const uint8_t *p = img + (size_t)clampi(py0 + r, 0, Hk - 1) * pitch;
+            S.pix[r][c0] = p[x0c];
+            if (c1 < kPixCols) S.pix[r][c1] = p[x1c];
+        }
+    }
     __syncthreads();
 
     const int x = 8 * it.cx0 - 4 + tid;
     const int gridW = 8 * Wc, gridH = 8 * Hc;
     if (x >= 0 && x < gridW) {
-        const int xl = clampi(x - 1, 0, Wk - 1), xr = clampi(x + 1, 0, Wk - 1);
+        const int sc = x - px0;  // shared-memory column of x (x-1 and x+1 are its neighbours)
         const bool core_x = (x >= 8 * it.cx0) && (x < 8 * it.cx0 + 8 * kTW);
         const int cxl = (x >> 3) - it.cx0;
         const int y_begin = max(8 * it.cy0 - 4, 0);
         const int y_end = min(8 * it.cy0 + 8 * kTH + 4, gridH);
         // rolling 3x3 neighbourhood: rows y-1 (a), y (b), y+1 (c)
         auto row = [&](int yy, int &l, int &m, int &r) {
-            const uint8_t *p = img + (size_t)clampi(yy, 0, Hk - 1) * pitch;
-            l = p[xl];
-            m = p[x];
-            r = p[xr];
+            const uint8_t *p = &S.pix[yy - py0][sc];
+            l = p[-1];
+            m = p[0];
+            r = p[1];
         };
         int al, am, ar, bl, bm, br, cl, cm, cr;
         row(y_begin - 1, al, am, ar);

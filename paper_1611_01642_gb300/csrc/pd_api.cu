@@ -186,6 +186,7 @@ struct pd_handle {
     int64_t score_cap = 0;
     pd_box *d_boxes = nullptr;
     int32_t *d_counts = nullptr;  // [2 * max_frames]
+    float4 *d_nms_scratch = nullptr;  // [max_frames][max_candidates] decoded candidate boxes
     unsigned *d_err = nullptr;
     uint8_t *d_frames = nullptr;  // host-input staging for pd_detect_host
     int64_t frames_cap = 0;
@@ -196,6 +197,8 @@ struct pd_handle {
     int32_t *h_counts = nullptr;
     unsigned *h_err = nullptr;
     cudaEvent_t desc_done = nullptr;
+    cudaEvent_t stage_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool timed = false;
     // tensor maps over the atlases
     CUtensorMap hog_map{}, lbp_map{};
     // last batch
@@ -363,6 +366,8 @@ void pd_destroy(pd_handle *h) {
     if (h->h_boxes) cudaFreeHost(h->h_boxes);
     if (h->h_counts) cudaFreeHost(h->h_counts);
     if (h->desc_done) cudaEventDestroy(h->desc_done);
+    for (auto &e : h->stage_ev)
+        if (e) cudaEventDestroy(e);
     delete h;
 }
 
@@ -418,6 +423,7 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
         {(int64_t)params->max_frames * params->max_boxes_per_frame * (int64_t)sizeof(pd_box), 0},  // 7
         {(int64_t)params->max_frames * 2 * 4 + 16, 0},             // 8 counts + error word
         {h->frames_cap, 0},                                        // 9 host-input frames
+        {(int64_t)params->max_frames * params->max_candidates_per_frame * 16, 0},  // 10 NMS scratch
     };
     int64_t total = 0;
     for (auto &pt : parts) {
@@ -438,6 +444,7 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
     h->d_counts = reinterpret_cast<int32_t *>(h->arena + parts[8].off);
     h->d_err = reinterpret_cast<unsigned *>(h->d_counts + 2 * params->max_frames);
     h->d_frames = h->arena + parts[9].off;
+    h->d_nms_scratch = reinterpret_cast<float4 *>(h->arena + parts[10].off);
 
     if (cudaMallocHost(&h->h_desc, h->desc_cap) != cudaSuccess) return bail(PD_ENOMEM);
     if (cudaMallocHost(&h->h_boxes, (size_t)params->max_frames * params->max_boxes_per_frame *
@@ -449,6 +456,9 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
     if (cudaEventCreateWithFlags(&h->desc_done, cudaEventDisableTiming) != cudaSuccess)
         return bail(PD_ECUDA);
     if (cudaEventRecord(h->desc_done, 0) != cudaSuccess) return bail(PD_ECUDA);
+    if (params->flags & PD_FLAG_STAGE_TIMING)
+        for (auto &e : h->stage_ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return bail(PD_ECUDA);
 
     // template -> [t][i][8] (j padded), lbp map
     std::vector<float> wt((size_t)kFeat * kWinBH * kWPad, 0.f);
@@ -498,16 +508,23 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
     PD_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), s));
     const FrameDesc *df = dptr<FrameDesc>(h, o.frames);
     const LevelDesc *dl = dptr<LevelDesc>(h, o.levels);
+    const bool timed = (h->p.flags & PD_FLAG_STAGE_TIMING) != 0;
+    h->timed = timed;
+    if (timed) PD_CUDA(h, cudaEventRecord(h->stage_ev[0], s));
     PD_CUDA(h, launch_resize(s, df, dl, dptr<int32_t>(h, o.tabs), h->d_pyr, dptr<ResizeItem>(h, o.r_items),
                              (int)p.r_items.size()));
+    if (timed) PD_CUDA(h, cudaEventRecord(h->stage_ev[1], s));
     PD_CUDA(h, launch_cells(s, dl, h->d_pyr, h->atlas, dptr<CellItem>(h, o.c_items), (int)p.c_items.size(),
                             h->d_lbp_map));
+    if (timed) PD_CUDA(h, cudaEventRecord(h->stage_ev[2], s));
     PD_CUDA(h, launch_svm(s, &h->hog_map, &h->lbp_map, dl, h->atlas.pitch, h->d_w, h->bias,
                           h->p.l2hys_clip, h->d_scores, dptr<SvmItem>(h, o.s_items),
                           (int)p.s_items.size(), h->d_err));
-    PD_CUDA(h, launch_nms(s, df, dl, n_frames, h->d_scores, h->p.threshold, h->p.nms_iou, nullptr,
-                          h->p.max_candidates_per_frame, h->d_boxes, h->p.max_boxes_per_frame,
-                          h->d_counts));
+    if (timed) PD_CUDA(h, cudaEventRecord(h->stage_ev[3], s));
+    PD_CUDA(h, launch_nms(s, df, dl, n_frames, h->d_scores, h->p.threshold, h->p.nms_iou,
+                          h->d_nms_scratch, h->p.max_candidates_per_frame, h->d_boxes,
+                          h->p.max_boxes_per_frame, h->d_counts));
+    if (timed) PD_CUDA(h, cudaEventRecord(h->stage_ev[4], s));
     h->last_launches = (p.r_items.empty() ? 0 : 1) + (p.c_items.empty() ? 0 : 1) +
                        (p.s_items.empty() ? 0 : 1) + (n_frames > 0 ? 1 : 0);
     h->detected = true;
@@ -561,6 +578,14 @@ int pd_sync(pd_handle *h) {
     PD_CUDA(h, cudaStreamSynchronize(h->stream));
     h->synced = true;
     return status;
+}
+
+int pd_stage_times(const pd_handle *h, float *ms) {
+    if (!h || !ms) return PD_EINVAL;
+    if (!h->timed || !h->synced) return PD_ESTATE;
+    for (int i = 0; i < 4; ++i)
+        if (cudaEventElapsedTime(&ms[i], h->stage_ev[i], h->stage_ev[i + 1]) != cudaSuccess) return PD_ECUDA;
+    return PD_OK;
 }
 
 int pd_frame_levels(const pd_handle *h, int frame, int *n_levels, pd_level_info *info) {
@@ -729,8 +754,8 @@ int pd_nms_maps(pd_handle *h, void *stream, const float *d_scores, int n_levels,
     int r = upload_plan(h, s, p, o);
     if (r != PD_OK) return r;
     PD_CUDA(h, launch_nms(s, dptr<FrameDesc>(h, o.frames), dptr<LevelDesc>(h, o.levels), 1, d_scores,
-                          h->p.threshold, h->p.nms_iou, nullptr, h->p.max_candidates_per_frame, d_boxes,
-                          max_boxes, d_counts));
+                          h->p.threshold, h->p.nms_iou, h->d_nms_scratch, h->p.max_candidates_per_frame,
+                          d_boxes, max_boxes, d_counts));
     return PD_OK;
 }
 

@@ -86,7 +86,7 @@ cudaError_t launch_svm(cudaStream_t s, const CUtensorMap *hog_map, const CUtenso
                        unsigned *d_err);
 cudaError_t launch_nms(cudaStream_t s, const FrameDesc *d_frames, const LevelDesc *d_levels,
                        int n_frames, const float *scores, float threshold, float iou,
-                       unsigned long long *cand, int max_cand, pd_box *boxes, int max_boxes,
+                       float4 *scratch, int max_cand, pd_box *boxes, int max_boxes,
                        int32_t *counts);
 
 // Encodes a 3-D tiled tensor map over plane-major cell planes.
