@@ -9,9 +9,9 @@
 //  2. bitonic-sorts the keys;
 //  3. decodes every candidate's box once (double precision, explicitly
 //     rounded, stored as float) into a per-frame global scratch array;
-//  4. walks the candidates in order: one not yet suppressed is kept, and all
+//  4. walks the candidates in order: one not yet suppressed is kept, all
 //     threads then suppress the later candidates whose IoU with it exceeds
-//     the threshold.
+//     the threshold, and the first survivor after it is the next one kept.
 // The IoU test first evaluates the IoU in float; the float value is within
 // 1e-4 of the exact one for boxes of this detector (sides >= 64 px,
 // coordinates < 8192), so a float IoU more than 1e-3 away from the threshold
@@ -156,19 +156,30 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
         bx[i] = make_float4(b.x, b.y, b.w, b.h);
     }
     __syncthreads();
-    int kept = 0;
+    // Greedy walk. `next` (the first candidate after i that survived the
+    // pass) is found with a block-wide atomicMin during the pass, so no
+    // thread rescans the flags; two slots alternate so that resetting one
+    // never races with reading the other.
+    __shared__ int next_slot[2];
+    int kept = 0, i = n > 0 ? 0 : n, parity = 0;
     pd_box *out = boxes + (size_t)f * max_boxes;
-    for (int i = 0; i < n && kept < max_boxes; ++i) {
-        if (supp[i]) continue;  // uniform: flags only change inside a pass that ends in a barrier
+    while (i < n && kept < max_boxes) {
         const float4 bi = bx[i];
-        if (tid == 0) out[kept] = decode(keys[i], fd, levels);
+        if (tid == 0) {
+            out[kept] = decode(keys[i], fd, levels);
+            next_slot[parity] = n;
+        }
         ++kept;
         if (kept == max_boxes) break;
+        __syncthreads();
         for (int j = i + 1 + tid; j < n; j += kThreads) {
             if (supp[j]) continue;
             if (suppresses(bi, bx[j], iou_thr)) supp[j] = 1;
+            else atomicMin(&next_slot[parity], j);
         }
         __syncthreads();
+        i = next_slot[parity];
+        parity ^= 1;
     }
     if (tid == 0) {
         counts[2 * f] = kept;
