@@ -157,6 +157,17 @@ int pd_boxes(const pd_handle *h, int frame, pd_box *out, int cap, int *count);
 /* Number of this library's kernel launches issued by the last pd_detect. */
 int pd_last_launch_count(const pd_handle *h);
 
+/* K4 tile shapes (windows per CTA tile, x by y): 0 = 32x16, 1 = 64x8,
+ * 2 = 32x8, 3 = 64x4. For each level the planner takes the shape with the
+ * least (number of tiles x cost[shape]). The default costs are a model
+ * (1, 1, 0.6, 0.6); the autotuner measures them on the running GPU and sets
+ * them here. cost: host array of PD_TILE_SHAPES positive floats. Affects the
+ * next pd_detect / pd_window_scores; results are identical for any costs up
+ * to float rounding (the same sums in a different tiling). */
+#define PD_TILE_SHAPES 4
+int pd_set_tile_costs(pd_handle *h, const float *cost);
+int pd_get_tile_costs(const pd_handle *h, float *cost);
+
 /* Device time in milliseconds of each kernel of the last pd_detect, from CUDA
  * events recorded on its stream around each launch: ms[0] pyramid (K1),
  * ms[1] cell histograms (K2/K3), ms[2] block norm + window scores (K4),
@@ -200,12 +211,12 @@ int pd_cell_features(pd_handle *h, void *stream, const uint8_t *d_level, int Wk,
                      int64_t hog_plane, uint8_t *d_lbp, int64_t lbp_plane, int cell_pitch);
 
 /* K4, Section 4.4 (Algorithm 6) with block normalisation: the score map of
- * one level from its cell planes (layouts of pd_cell_features), using the
- * handle's template and bias: d_scores float32 [cells_y-15][cells_x-7],
- * row pitch cells_x-7. The cell planes are read through TMA: d_hog and d_lbp
- * must be 16-byte aligned and the planes must hold at least 16 rows beyond
- * cells_y that the caller does not mind being read (their values never reach
- * a valid window). Errors: PD_EINVAL, PD_ECUDA. */
+ * one level from its cell planes (layouts of pd_cell_features; LBP counts
+ * must be <= 64, as a cell has 64 pixels), using the handle's template and
+ * bias: d_scores float32 [cells_y-15][cells_x-7], row pitch cells_x-7. The
+ * cell planes are read through TMA: d_hog and d_lbp must be 16-byte aligned,
+ * cell_pitch a multiple of 16, hog_plane a multiple of 4 and lbp_plane a
+ * multiple of 16 elements. Errors: PD_EINVAL, PD_ECUDA. */
 int pd_window_scores(pd_handle *h, void *stream, const float *d_hog, int64_t hog_plane,
                      const uint8_t *d_lbp, int64_t lbp_plane, int cell_pitch, int cells_x,
                      int cells_y, float *d_scores);

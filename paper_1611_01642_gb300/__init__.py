@@ -29,10 +29,12 @@ ERROR_NAMES = {0: "PD_OK", -1: "PD_EINVAL", -2: "PD_ENOMEM", -3: "PD_ECUDA", -4:
 HOG_BINS, LBP_BINS, FEAT, WIN_BW, WIN_BH = 9, 59, 95, 7, 15
 MAX_LEVELS = 96
 PD_FLAG_STAGE_TIMING = 1
+TILE_SHAPES = 4
+TILE_SHAPE_DIMS = [(32, 16), (64, 8), (32, 8), (64, 4)]  # windows per K4 tile (x, y)
 
 EXPORTED = ["pd_params_default", "pd_pyramid", "pd_create", "pd_destroy", "pd_last_error",
             "pd_detect", "pd_detect_host", "pd_sync", "pd_frame_levels", "pd_scores", "pd_boxes",
-            "pd_last_launch_count", "pd_stage_times", "pd_resize_levels", "pd_cell_features", "pd_window_scores",
+            "pd_last_launch_count", "pd_stage_times", "pd_set_tile_costs", "pd_get_tile_costs", "pd_resize_levels", "pd_cell_features", "pd_window_scores",
             "pd_nms_maps"]
 
 
@@ -98,6 +100,8 @@ def load(path: str | None = None):
         "pd_boxes": ([P, i, P, i, P], i),
         "pd_last_launch_count": ([P], i),
         "pd_stage_times": ([P, P], i),
+        "pd_set_tile_costs": ([P, P], i),
+        "pd_get_tile_costs": ([P, P], i),
         "pd_resize_levels": ([P, P, P, i, i, i, i, P, P, P, P, P], i),
         "pd_cell_features": ([P, P, P, i, i, i, P, i64, P, i64, i], i),
         "pd_window_scores": ([P, P, P, i64, P, i64, i, i, i, P], i),
@@ -239,6 +243,18 @@ def pd_stage_times(h):
     ms = np.zeros(4, np.float32)
     _check(load().pd_stage_times(h, ms.ctypes.data_as(ctypes.c_void_p)), h)
     return [float(v) for v in ms]
+
+
+def pd_set_tile_costs(h, costs) -> None:
+    c, cp = _np(costs, np.float32)
+    assert c.size == TILE_SHAPES
+    _check(load().pd_set_tile_costs(h, cp), h)
+
+
+def pd_get_tile_costs(h):
+    c = np.zeros(TILE_SHAPES, np.float32)
+    _check(load().pd_get_tile_costs(h, c.ctypes.data_as(ctypes.c_void_p)), h)
+    return [float(v) for v in c]
 
 
 def pd_resize_levels(h, frame, level_dims, out, offsets, pitches, stream=None) -> None:

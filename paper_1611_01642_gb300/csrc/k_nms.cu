@@ -166,7 +166,19 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
     while (i < n && kept < max_boxes) {
         const float4 bi = bx[i];
         if (tid == 0) {
-            out[kept] = decode(keys[i], fd, levels);
+            const unsigned long long key = keys[i];
+            const uint32_t hi = (uint32_t)(key >> 32), lo = (uint32_t)key;
+            const uint32_t ord = ~hi;
+            pd_box b;
+            b.x = bi.x;
+            b.y = bi.y;
+            b.w = bi.z;
+            b.h = bi.w;
+            b.score = __uint_as_float((ord & 0x80000000u) ? (ord ^ 0x80000000u) : ~ord);
+            b.level = (int)(lo >> 24);
+            b.wy = (int)((lo >> 12) & 4095);
+            b.wx = (int)(lo & 4095);
+            out[kept] = b;
             next_slot[parity] = n;
         }
         ++kept;

@@ -31,6 +31,8 @@ using namespace pd;
 namespace {
 
 constexpr int64_t kAlign = 256;
+// relative time of one K4 tile per shape (model; the autotuner replaces it)
+const float kDefaultTileCost[kSvmShapes] = {1.0f, 1.0f, 0.6f, 0.6f};
 
 int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
@@ -199,8 +201,10 @@ struct pd_handle {
     cudaEvent_t desc_done = nullptr;
     cudaEvent_t stage_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     bool timed = false;
-    // tensor maps over the atlases
-    CUtensorMap hog_map{}, lbp_map{};
+    // tensor maps over the atlases, one pair per K4 tile shape
+    CUtensorMap hog_map[kSvmShapes]{}, lbp_map[kSvmShapes]{};
+    float tile_cost[kSvmShapes] = {kDefaultTileCost[0], kDefaultTileCost[1], kDefaultTileCost[2],
+                                   kDefaultTileCost[3]};
     // last batch
     Plan plan;
     cudaStream_t stream = nullptr;
@@ -230,8 +234,25 @@ int fail(pd_handle *h, int code, const char *fmt, ...) {
     } while (0)
 
 // Adds one level to the plan (tables, descriptor, work items).
+// K4 tile shape of a rows x cols score map: the shape with the least
+// tiles x cost (cost = relative time of one tile of that shape).
+int pick_shape(int rows, int cols, const float *cost) {
+    int best = 0;
+    double best_c = 1e300;
+    for (int s = 0; s < kSvmShapes; ++s) {
+        const SvmShapeInfo sh = svm_shape(s);
+        const double c = (double)((rows + sh.th - 1) / sh.th) * ((cols + sh.tw - 1) / sh.tw) * cost[s];
+        if (c < best_c) {
+            best_c = c;
+            best = s;
+        }
+    }
+    return best;
+}
+
 void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int64_t img_off,
-                int32_t img_pitch, const LevelDesc *share = nullptr) {
+                int32_t img_pitch, const LevelDesc *share = nullptr,
+                const float *tile_cost = kDefaultTileCost) {
     LevelDesc L{};
     L.img_off = img_off;
     L.img_pitch = img_pitch;
@@ -260,8 +281,12 @@ void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int
     const int li = (int)p.levels.size();
     for (int cy = 0; cy < L.Hc; cy += kCellTH)
         for (int cx = 0; cx < L.Wc; cx += kCellTW) p.c_items.push_back({li, cx, cy, 0});
-    for (int wy = 0; wy < L.rows; wy += kSvmTH)
-        for (int wx = 0; wx < L.cols; wx += kSvmTW) p.s_items.push_back({li, wx, wy, 0});
+    if (L.rows > 0) {
+        const int shape = pick_shape(L.rows, L.cols, tile_cost);
+        const SvmShapeInfo sh = svm_shape(shape);
+        for (int wy = 0; wy < L.rows; wy += sh.th)
+            for (int wx = 0; wx < L.cols; wx += sh.tw) p.s_items.push_back({li, wx, wy, shape});
+    }
     p.atlas_rows += L.Hc;
     p.score_floats += (int64_t)L.rows * L.cols;
     p.max_wc = std::max(p.max_wc, L.Wc);
@@ -269,7 +294,8 @@ void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int
 }
 
 // Plans one frame with the pyramid rule; returns PD_OK or an error.
-int plan_frame(Plan &p, const pd_params &prm, const uint8_t *ptr, int W, int H, int pitch) {
+int plan_frame(Plan &p, const pd_params &prm, const uint8_t *ptr, int W, int H, int pitch,
+               const float *tile_cost = kDefaultTileCost) {
     int32_t Wk[PD_MAX_LEVELS], Hk[PD_MAX_LEVELS];
     int n = level_sizes(W, H, prm.pyr_factor, PD_MAX_LEVELS, Wk, Hk);
     if (n < 0) return n;
@@ -287,7 +313,8 @@ int plan_frame(Plan &p, const pd_params &prm, const uint8_t *ptr, int W, int H, 
     for (int k = 0; k < n; ++k) {
         const int32_t lp = (int32_t)round_up(Wk[k], 16);
         const LevelDesc share = first_shared >= 0 ? p.levels[first_shared + k] : LevelDesc{};
-        plan_level(p, f, k, W, H, Wk[k], Hk[k], p.pyr_bytes, lp, first_shared >= 0 ? &share : nullptr);
+        plan_level(p, f, k, W, H, Wk[k], Hk[k], p.pyr_bytes, lp, first_shared >= 0 ? &share : nullptr,
+                   tile_cost);
         p.pyr_bytes += (int64_t)lp * Hk[k];
     }
     if (n > 0)
@@ -320,6 +347,22 @@ int upload_plan(pd_handle *h, cudaStream_t s, const Plan &p, Packed &o) {
     put(o.tabs, p.tabs.data(), p.tabs.size() * sizeof(int32_t));
     if (o.total) PD_CUDA(h, cudaMemcpyAsync(h->d_desc, h->h_desc, o.total, cudaMemcpyHostToDevice, s));
     PD_CUDA(h, cudaEventRecord(h->desc_done, s));
+    return PD_OK;
+}
+
+// One HOG and one LBP tensor map per K4 tile shape over plane-major cell
+// planes [planes][rows][pitch].
+int encode_svm_maps(CUtensorMap *hog_maps, CUtensorMap *lbp_maps, const float *hog, const uint8_t *lbp,
+                    int64_t pitch, int64_t rows, int64_t hog_plane, int64_t lbp_plane) {
+    for (int s = 0; s < kSvmShapes; ++s) {
+        const SvmShapeInfo sh = svm_shape(s);
+        if (encode_plane_map(&hog_maps[s], const_cast<float *>(hog), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                             pitch, rows, kHogBins, hog_plane, sh.hog_box_x, sh.cell_rows, kHogBins) != PD_OK ||
+            encode_plane_map(&lbp_maps[s], const_cast<uint8_t *>(lbp), CU_TENSOR_MAP_DATA_TYPE_UINT8, 1,
+                             pitch, rows, kLbpBins, lbp_plane, sh.lbp_box_x, sh.cell_rows,
+                             svm_lbp_chunk()) != PD_OK)
+            return PD_ECUDA;
+    }
     return PD_OK;
 }
 
@@ -471,10 +514,8 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
     if (cudaMemcpy(h->d_w, wt.data(), wt.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->d_lbp_map, map, 256, cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(PD_ECUDA);
-    if (encode_plane_map(&h->hog_map, h->atlas.hog, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, P, rows,
-                         kHogBins, h->atlas.hog_plane, 40, kSvmTH + kWinBH, kHogBins) != PD_OK ||
-        encode_plane_map(&h->lbp_map, h->atlas.lbp, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, P, rows,
-                         kLbpBins, h->atlas.lbp_plane, 48, kSvmTH + kWinBH, kLbpBins) != PD_OK)
+    if (encode_svm_maps(h->hog_map, h->lbp_map, h->atlas.hog, h->atlas.lbp, P, rows, h->atlas.hog_plane,
+                        h->atlas.lbp_plane) != PD_OK)
         return bail(PD_ECUDA);
     *out = h;
     return PD_OK;
@@ -495,7 +536,7 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
         const int W = widths[f], H = heights[f], pitch = pitches[f];
         if (W < 1 || H < 1 || W > h->p.max_width || H > h->p.max_height || pitch < W || !d_frames[f])
             return fail(h, PD_EINVAL, "frame %d: bad size %dx%d pitch %d", f, W, H, pitch);
-        int r = plan_frame(p, h->p, d_frames[f], W, H, pitch);
+        int r = plan_frame(p, h->p, d_frames[f], W, H, pitch, h->tile_cost);
         if (r != PD_OK) return fail(h, r, "frame %d: planning failed", f);
     }
     if (p.atlas_rows > h->atlas.rows || p.pyr_bytes > h->pyr_cap || p.score_floats > h->score_cap)
@@ -517,9 +558,8 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
     PD_CUDA(h, launch_cells(s, dl, h->d_pyr, h->atlas, dptr<CellItem>(h, o.c_items), (int)p.c_items.size(),
                             h->d_lbp_map));
     if (timed) PD_CUDA(h, cudaEventRecord(h->stage_ev[2], s));
-    PD_CUDA(h, launch_svm(s, &h->hog_map, &h->lbp_map, dl, h->atlas.pitch, h->d_w, h->bias,
-                          h->p.l2hys_clip, h->d_scores, dptr<SvmItem>(h, o.s_items),
-                          (int)p.s_items.size(), h->d_err));
+    PD_CUDA(h, launch_svm(s, h->hog_map, h->lbp_map, dl, h->d_w, h->bias, h->p.l2hys_clip, h->d_scores,
+                          dptr<SvmItem>(h, o.s_items), (int)p.s_items.size(), h->d_err));
     if (timed) PD_CUDA(h, cudaEventRecord(h->stage_ev[3], s));
     PD_CUDA(h, launch_nms(s, df, dl, n_frames, h->d_scores, h->p.threshold, h->p.nms_iou,
                           h->d_nms_scratch, h->p.max_candidates_per_frame, h->d_boxes,
@@ -578,6 +618,20 @@ int pd_sync(pd_handle *h) {
     PD_CUDA(h, cudaStreamSynchronize(h->stream));
     h->synced = true;
     return status;
+}
+
+int pd_set_tile_costs(pd_handle *h, const float *cost) {
+    if (!h || !cost) return PD_EINVAL;
+    for (int s = 0; s < kSvmShapes; ++s)
+        if (!(cost[s] > 0.f)) return fail(h, PD_EINVAL, "tile cost %d must be > 0", s);
+    for (int s = 0; s < kSvmShapes; ++s) h->tile_cost[s] = cost[s];
+    return PD_OK;
+}
+
+int pd_get_tile_costs(const pd_handle *h, float *cost) {
+    if (!h || !cost) return PD_EINVAL;
+    for (int s = 0; s < kSvmShapes; ++s) cost[s] = h->tile_cost[s];
+    return PD_OK;
 }
 
 int pd_stage_times(const pd_handle *h, float *ms) {
@@ -698,25 +752,22 @@ int pd_window_scores(pd_handle *h, void *stream, const float *d_hog, int64_t hog
         (reinterpret_cast<uintptr_t>(d_hog) & 15) || (reinterpret_cast<uintptr_t>(d_lbp) & 15))
         return fail(h, PD_EINVAL, "pd_window_scores: bad argument");
     Plan p;
-    plan_level(p, 0, 0, 8 * cells_x, 8 * cells_y, 8 * cells_x, 8 * cells_y, 0, 8 * cells_x);
+    plan_level(p, 0, 0, 8 * cells_x, 8 * cells_y, 8 * cells_x, 8 * cells_y, 0, 8 * cells_x, nullptr,
+               h->tile_cost);
     p.c_items.clear();
     p.tabs.clear();
     if (p.s_items.empty()) return PD_OK;
-    CUtensorMap hm, lm;
+    CUtensorMap hm[kSvmShapes], lm[kSvmShapes];
     const int64_t rows = std::max(cells_y, 1);
-    if (encode_plane_map(&hm, const_cast<float *>(d_hog), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, cell_pitch,
-                         rows, kHogBins, hog_plane, 40, kSvmTH + kWinBH, kHogBins) != PD_OK ||
-        encode_plane_map(&lm, const_cast<uint8_t *>(d_lbp), CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, cell_pitch,
-                         rows, kLbpBins, lbp_plane, 48, kSvmTH + kWinBH, kLbpBins) != PD_OK)
+    if (encode_svm_maps(hm, lm, d_hog, d_lbp, cell_pitch, rows, hog_plane, lbp_plane) != PD_OK)
         return fail(h, PD_ECUDA, "pd_window_scores: tensor map encoding failed");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Packed o;
     int r = upload_plan(h, s, p, o);
     if (r != PD_OK) return r;
     PD_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), s));
-    PD_CUDA(h, launch_svm(s, &hm, &lm, dptr<LevelDesc>(h, o.levels), cell_pitch, h->d_w, h->bias,
-                          h->p.l2hys_clip, d_scores, dptr<SvmItem>(h, o.s_items), (int)p.s_items.size(),
-                          h->d_err));
+    PD_CUDA(h, launch_svm(s, hm, lm, dptr<LevelDesc>(h, o.levels), h->d_w, h->bias, h->p.l2hys_clip,
+                          d_scores, dptr<SvmItem>(h, o.s_items), (int)p.s_items.size(), h->d_err));
     return PD_OK;
 }
 

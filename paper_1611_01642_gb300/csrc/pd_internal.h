@@ -49,15 +49,23 @@ struct LevelDesc {
 // Work items (one CTA each).
 struct ResizeItem { int32_t frame, x0, y0, pad; };   // source tile of a frame
 struct CellItem { int32_t level, cx0, cy0, pad; };   // cell tile of a level
-struct SvmItem { int32_t level, wx0, wy0, pad; };    // window tile of a level
+struct SvmItem { int32_t level, wx0, wy0, shape; };  // window tile of a level, tile shape index
 
 // Tiles.
 constexpr int kResizeTW = 128;  // source tile width  (pixels)
 constexpr int kResizeTH = 32;   // source tile height (pixels)
 constexpr int kCellTW = 15;     // cells per cell tile along x (128 threads = 8*15+8 columns)
 constexpr int kCellTH = 8;      // cells per cell tile along y
-constexpr int kSvmTW = 32;      // windows per SVM tile along x
-constexpr int kSvmTH = 16;      // windows per SVM tile along y
+constexpr int kSvmShapes = 4;   // K4 tile shapes: 32x16, 64x8, 32x8, 64x4 windows
+
+struct SvmShapeInfo {
+    int tw, th;     // windows per tile along x / y
+    int hog_box_x;  // TMA box width of the HOG cell planes (cells)
+    int lbp_box_x;  // TMA box width of the LBP cell planes (cells)
+    int cell_rows;  // TMA box height (cell rows)
+};
+SvmShapeInfo svm_shape(int s);
+int svm_lbp_chunk();  // LBP planes per TMA box
 
 // Cell atlas: plane-major [plane][atlas_rows][pitch]; pitch in elements.
 struct CellAtlas {
@@ -80,10 +88,9 @@ cudaError_t launch_resize(cudaStream_t s, const FrameDesc *d_frames, const Level
                           int n_items);
 cudaError_t launch_cells(cudaStream_t s, const LevelDesc *d_levels, const uint8_t *pyr,
                          CellAtlas atlas, const CellItem *d_items, int n_items, const uint8_t *d_lbp_map);
-cudaError_t launch_svm(cudaStream_t s, const CUtensorMap *hog_map, const CUtensorMap *lbp_map,
-                       const LevelDesc *d_levels, int32_t atlas_pitch, const float *d_w, float bias,
-                       float clip, float *scores, const SvmItem *d_items, int n_items,
-                       unsigned *d_err);
+cudaError_t launch_svm(cudaStream_t s, const CUtensorMap *hog_maps, const CUtensorMap *lbp_maps,
+                       const LevelDesc *d_levels, const float *d_w, float bias, float clip,
+                       float *scores, const SvmItem *d_items, int n_items, unsigned *d_err);
 cudaError_t launch_nms(cudaStream_t s, const FrameDesc *d_frames, const LevelDesc *d_levels,
                        int n_frames, const float *scores, float threshold, float iou,
                        float4 *scratch, int max_cand, pd_box *boxes, int max_boxes,

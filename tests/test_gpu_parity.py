@@ -353,3 +353,26 @@ def test_errors_are_reported(template):
         assert e.value.code in (pd.PD_ESTATE, pd.PD_EINVAL)
     finally:
         d.close()
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2, 3])
+def test_window_scores_every_tile_shape(template, shape):
+    # force one K4 tile shape through the planner's cost table
+    from paper_1611_01642_gb300 import build as bld
+    bld.build()
+    w, b = template
+    d = pd.Detector(w, b, max_frames=1, max_width=700, max_height=600)
+    try:
+        costs = [1e6] * pd.TILE_SHAPES
+        costs[shape] = 1.0
+        pd.pd_set_tile_costs(d.h, costs)
+        assert pd.pd_get_tile_costs(d.h) == costs
+        for (W, H, seed) in [(520, 410, 1), (700, 600, 2), (64, 128, 3), (130, 300, 4)]:
+            L = synth.random_image(W, H, 300 + seed, smooth=True)
+            hog = oracle.hog_cells(L).astype(np.float32)
+            lbp = oracle.lbp_cells(L)
+            feat = oracle.block_features(hog.astype(np.float64), lbp)
+            got = _scores_gpu_from_cells(d, hog, lbp)
+            _check_scores(got, feat, w, b, oracle.scores(feat, w, b), f"shape {shape} {W}x{H}")
+    finally:
+        d.close()
