@@ -233,6 +233,29 @@ int pd_nms_maps(pd_handle *h, void *stream, const float *d_scores, int n_levels,
                 const int32_t *cols, const int32_t *Wk, const int32_t *Hk, int W, int H,
                 pd_box *d_boxes, int max_boxes, int32_t *d_counts);
 
+/* Allocation-free NMS. The paper has no counterpart: this exists for
+ * callers that must not allocate device memory at run time -- a real-time
+ * frame loop whose coding rules forbid allocation after start-up, a plugin
+ * inside a host framework that owns all GPU memory, or code that only has a
+ * fixed memory budget -- and so cannot create a pd_handle (pd_create calls
+ * cudaMalloc). It computes exactly what pd_nms_maps computes, with the
+ * threshold, IoU and caps passed as arguments, and needs no handle.
+ * The scratch memory it needs (level descriptors and the decoded box of
+ * every candidate) is one static array inside the library, about 270 KB,
+ * that every GPU which loads the library holds until the process exits; it
+ * limits a call to max_candidates <= 16384 and n_levels <= PD_MAX_LEVELS
+ * (larger values return PD_EINVAL). The caller passes inputs and outputs as
+ * for pd_nms_maps: d_scores, d_boxes (cap max_boxes) and d_counts (kept,
+ * candidates; a candidate overflow writes 0 and -candidates). The first call
+ * on a device looks up the array's device address and sets the kernel's
+ * shared-memory limit, so make that first call outside any stream capture.
+ * All calls share the one array and it keeps the last call's contents, so
+ * calls that overlap on the GPU (two streams, two threads) race: serialise
+ * them. Errors: PD_EINVAL, PD_ECUDA. Asynchronous on `stream`. */
+int pd_nms_noalloc(void *stream, const float *d_scores, int n_levels, const int32_t *rows,
+                   const int32_t *cols, const int32_t *Wk, const int32_t *Hk, int W, int H, float threshold,
+                   float nms_iou, int max_candidates, pd_box *d_boxes, int max_boxes, int32_t *d_counts);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,7 +35,7 @@ TILE_SHAPE_DIMS = [(32, 16), (64, 8), (32, 8), (64, 4)]  # windows per K4 tile (
 EXPORTED = ["pd_params_default", "pd_pyramid", "pd_create", "pd_destroy", "pd_last_error",
             "pd_detect", "pd_detect_host", "pd_sync", "pd_frame_levels", "pd_scores", "pd_boxes",
             "pd_last_launch_count", "pd_stage_times", "pd_set_tile_costs", "pd_get_tile_costs", "pd_resize_levels", "pd_cell_features", "pd_window_scores",
-            "pd_nms_maps"]
+            "pd_nms_maps", "pd_nms_noalloc"]
 
 
 class pd_params(ctypes.Structure):
@@ -106,6 +106,7 @@ def load(path: str | None = None):
         "pd_cell_features": ([P, P, P, i, i, i, P, i64, P, i64, i], i),
         "pd_window_scores": ([P, P, P, i64, P, i64, i, i, i, P], i),
         "pd_nms_maps": ([P, P, P, i, P, P, P, P, i, i, P, i, P], i),
+        "pd_nms_noalloc": ([P, P, i, P, P, P, P, i, i, f, f, i, P, i, P], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -290,6 +291,19 @@ def pd_nms_maps(h, scores, rows, cols, level_dims, W: int, H: int, boxes, max_bo
     hk, hkp = _np([d[1] for d in level_dims], np.int32)
     _check(load().pd_nms_maps(h, _stream(stream), _ptr(scores), n, rp, cp, wkp, hkp, W, H, _ptr(boxes),
                               max_boxes, _ptr(counts)), h)
+
+
+def pd_nms_noalloc(scores, rows, cols, level_dims, W: int, H: int, threshold: float, nms_iou: float,
+                   max_candidates: int, boxes, max_boxes: int, counts, stream=None) -> None:
+    """NMS with no handle and no device allocation (scratch inside the library)."""
+    n = len(rows)
+    r, rp = _np(rows, np.int32)
+    c, cp = _np(cols, np.int32)
+    wk, wkp = _np([d[0] for d in level_dims], np.int32)
+    hk, hkp = _np([d[1] for d in level_dims], np.int32)
+    _check(load().pd_nms_noalloc(_stream(stream), _ptr(scores), n, rp, cp, wkp, hkp, W, H,
+                                 float(threshold), float(nms_iou), max_candidates, _ptr(boxes),
+                                 max_boxes, _ptr(counts)))
 
 
 # ----------------------------------------------------------------------------- convenience

@@ -19,6 +19,8 @@
 // explicitly rounded operations (no FMA contraction), which is the exact IEEE
 // evaluation of the definition. Decisions are therefore the same as those of
 // a plain double-precision implementation.
+#include <mutex>
+
 #include "pd_internal.h"
 
 namespace pd {
@@ -222,4 +224,113 @@ cudaError_t launch_nms(cudaStream_t s, const FrameDesc *d_frames, const LevelDes
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free NMS (pd_nms_noalloc). The kernel above needs device memory
+// beyond its inputs and outputs: the frame / level descriptors it reads and
+// the per-candidate decoded boxes. For callers that cannot allocate device
+// memory, that scratch lives in one file-scope array that every GPU loading
+// this library holds until the process exits. A small set-up kernel copies
+// the level geometry (passed by value) into it before the unchanged NMS
+// kernel runs.
+namespace {
+
+constexpr int kNoAllocMaxCandidates = 16384;
+constexpr int kNoAllocMaxLevels = PD_MAX_LEVELS;
+
+struct NoAllocScratch {
+    FrameDesc frame;
+    LevelDesc levels[kNoAllocMaxLevels];
+    float4 boxes[kNoAllocMaxCandidates];  // decoded candidate boxes
+};
+
+struct NoAllocGeometry {
+    int32_t W, H, n_levels, pad;
+    int32_t Wk[kNoAllocMaxLevels], Hk[kNoAllocMaxLevels];
+    int32_t rows[kNoAllocMaxLevels], cols[kNoAllocMaxLevels];
+    int64_t score_off[kNoAllocMaxLevels];
+};
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_nms_scratch[sizeof(NoAllocScratch)];
+
+namespace {
+
+__global__ void k_nms_noalloc_setup(const __grid_constant__ NoAllocGeometry g, NoAllocScratch *s) {
+    if (threadIdx.x == 0) {
+        FrameDesc f{};
+        f.W = g.W;
+        f.H = g.H;
+        f.first_level = 0;
+        f.n_levels = g.n_levels;
+        s->frame = f;
+    }
+    for (int k = threadIdx.x; k < g.n_levels; k += blockDim.x) {
+        LevelDesc L{};
+        L.W = g.W;
+        L.H = g.H;
+        L.Wk = g.Wk[k];
+        L.Hk = g.Hk[k];
+        L.rows = g.rows[k];
+        L.cols = g.cols[k];
+        L.score_off = g.score_off[k];
+        s->levels[k] = L;
+    }
+}
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+NoAllocScratch *g_noalloc_addr[kMaxDevices] = {};
+
+}  // namespace
+
 }  // namespace pd
+
+extern "C" int pd_nms_noalloc(void *stream, const float *d_scores, int n_levels, const int32_t *rows,
+                              const int32_t *cols, const int32_t *Wk, const int32_t *Hk, int W, int H,
+                              float threshold, float nms_iou, int max_candidates, pd_box *d_boxes,
+                              int max_boxes, int32_t *d_counts) {
+    using namespace pd;
+    if (!d_scores || !rows || !cols || !Wk || !Hk || !d_boxes || !d_counts || n_levels < 0 ||
+        n_levels > kNoAllocMaxLevels || max_candidates < 1 || max_candidates > kNoAllocMaxCandidates ||
+        max_boxes < 1 || W < 1 || H < 1 || !(nms_iou >= 0.f))
+        return PD_EINVAL;
+    NoAllocGeometry g{};
+    g.W = W;
+    g.H = H;
+    g.n_levels = n_levels;
+    int64_t off = 0;
+    for (int k = 0; k < n_levels; ++k) {
+        if (rows[k] < 0 || cols[k] < 0 || rows[k] > 4096 || cols[k] > 4096 || Wk[k] < 1 || Hk[k] < 1)
+            return PD_EINVAL;
+        g.Wk[k] = Wk[k];
+        g.Hk[k] = Hk[k];
+        g.rows[k] = rows[k];
+        g.cols[k] = cols[k];
+        g.score_off[k] = off;
+        off += (int64_t)rows[k] * cols[k];
+    }
+    // Once per device: the device address of the scratch array (the host-side
+    // symbol is only a stand-in) and the kernel's shared-memory opt-in.
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PD_ECUDA;
+    if (dev < 0 || dev >= kMaxDevices) return PD_EINVAL;
+    NoAllocScratch *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_nms_scratch) != cudaSuccess || !p) return PD_ECUDA;
+            if (init_nms() != cudaSuccess) return PD_ECUDA;
+            g_noalloc_addr[dev] = reinterpret_cast<NoAllocScratch *>(p);
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    k_nms_noalloc_setup<<<1, 128, 0, s>>>(g, scratch);
+    if (cudaGetLastError() != cudaSuccess) return PD_ECUDA;
+    if (launch_nms(s, &scratch->frame, scratch->levels, 1, d_scores, threshold, nms_iou, scratch->boxes,
+                   max_candidates, d_boxes, max_boxes, d_counts) != cudaSuccess)
+        return PD_ECUDA;
+    return PD_OK;
+}
