@@ -133,9 +133,14 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
 /* Waits for the last pd_detect, then surfaces device-side status: PD_OK,
  * PD_EOVERFLOW (a frame had more candidates than max_candidates_per_frame;
  * its boxes are invalid), PD_ETIMEOUT / PD_EBOUNDS (results invalid), or
- * PD_ECUDA. Copies the per-frame box lists to host memory owned by the
- * handle. Synchronous. */
+ * PD_ECUDA. The NMS kernel writes the kept boxes and counts straight into
+ * mapped pinned host memory owned by the handle. Synchronous. */
 int pd_sync(pd_handle *h);
+
+/* Number of windows above threshold (NMS candidates) of frame `frame` of the
+ * last detect; negative if it exceeded max_candidates_per_frame. Requires
+ * pd_sync (else PD_ESTATE). */
+int pd_frame_candidates(const pd_handle *h, int frame, int *n);
 
 /* Level geometry of frame `frame` of the last pd_detect (host). info: host
  * array of PD_MAX_LEVELS entries. Available right after pd_detect. */
@@ -176,9 +181,11 @@ int pd_get_tile_costs(const pd_handle *h, float *cost);
 int pd_stage_times(const pd_handle *h, float *ms);
 
 /* Same as pd_detect with frames in HOST memory (h_frames: host array of host
- * pointers; pinned memory gives the fastest copies): the library copies each
- * frame into its arena on `stream` (Section 4.1 step 1) and runs pd_detect.
- * The host frames may be reused once pd_sync returns. Errors as pd_detect. */
+ * pointers; Section 4.1 step 1, the host-to-device transfer). Page-locked
+ * frames (cudaMallocHost / cudaHostRegister / pinned tensors) are read in
+ * place by the pyramid kernel over the host link, once; other host frames are
+ * first copied into the arena on `stream`. The host frames may be reused once
+ * pd_sync returns. Errors as pd_detect. */
 int pd_detect_host(pd_handle *h, void *stream, int n_frames, const uint8_t *const *h_frames,
                    const int32_t *widths, const int32_t *heights, const int32_t *pitches);
 

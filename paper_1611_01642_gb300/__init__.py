@@ -33,7 +33,7 @@ TILE_SHAPES = 4
 TILE_SHAPE_DIMS = [(32, 16), (64, 8), (32, 8), (64, 4)]  # windows per K4 tile (x, y)
 
 EXPORTED = ["pd_params_default", "pd_pyramid", "pd_create", "pd_destroy", "pd_last_error",
-            "pd_detect", "pd_detect_host", "pd_sync", "pd_frame_levels", "pd_scores", "pd_boxes",
+            "pd_detect", "pd_detect_host", "pd_sync", "pd_frame_candidates", "pd_frame_levels", "pd_scores", "pd_boxes",
             "pd_last_launch_count", "pd_stage_times", "pd_set_tile_costs", "pd_get_tile_costs", "pd_resize_levels", "pd_cell_features", "pd_window_scores",
             "pd_nms_maps", "pd_nms_noalloc"]
 
@@ -95,6 +95,7 @@ def load(path: str | None = None):
         "pd_detect": ([P, P, i, P, P, P, P], i),
         "pd_detect_host": ([P, P, i, P, P, P, P], i),
         "pd_sync": ([P], i),
+        "pd_frame_candidates": ([P, i, P], i),
         "pd_frame_levels": ([P, i, P, P], i),
         "pd_scores": ([P, P, P], i),
         "pd_boxes": ([P, i, P, i, P], i),
@@ -208,6 +209,12 @@ def pd_detect_host(h, frames, stream=None) -> None:
 def pd_sync(h) -> int:
     """Waits for the last detect; returns the status code (PD_OK or a PD_E* code)."""
     return load().pd_sync(h)
+
+
+def pd_frame_candidates(h, frame: int) -> int:
+    n = ctypes.c_int(0)
+    _check(load().pd_frame_candidates(h, frame, ctypes.byref(n)), h)
+    return n.value
 
 
 def pd_frame_levels(h, frame: int):

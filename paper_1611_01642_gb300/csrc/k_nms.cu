@@ -7,8 +7,8 @@
 //     order-reversing integer in the high word, level/wy/wx in the low word,
 //     so ascending keys = score descending, then level, wy, wx ascending);
 //  2. bitonic-sorts the keys;
-//  3. decodes every candidate's box once (double precision, explicitly
-//     rounded, stored as float) into a per-frame global scratch array;
+//  3. decodes every candidate's box once (exactly rounded float division)
+//     into a per-frame global scratch array;
 //  4. walks the candidates in order: one not yet suppressed is kept, all
 //     threads then suppress the later candidates whose IoU with it exceeds
 //     the threshold, and the first survivor after it is the next one kept.
@@ -37,8 +37,11 @@ __device__ __forceinline__ unsigned long long make_key(float s, int level, int w
 
 __device__ __forceinline__ bool suppresses(const float4 &a, const float4 &b, float thr);
 
-__device__ __forceinline__ pd_box decode(unsigned long long key, const FrameDesc &fd,
-                                         const LevelDesc *levels) {
+// Box of a key. x = 8*wx*W/Wk etc. are quotients of integers below 2^24, so
+// the correctly rounded float quotient (__fdiv_rn) equals the double quotient
+// rounded to float (a quotient of two such integers cannot lie within 2^-49
+// of a float rounding midpoint without being on it): no double arithmetic.
+__device__ __forceinline__ pd_box decode(unsigned long long key, int W, int H, const int2 *wkhk) {
     const uint32_t hi = (uint32_t)(key >> 32), lo = (uint32_t)key;
     const uint32_t ord = ~hi;
     const uint32_t u = (ord & 0x80000000u) ? (ord ^ 0x80000000u) : ~ord;
@@ -47,12 +50,20 @@ __device__ __forceinline__ pd_box decode(unsigned long long key, const FrameDesc
     b.level = (int)(lo >> 24);
     b.wy = (int)((lo >> 12) & 4095);
     b.wx = (int)(lo & 4095);
-    const LevelDesc L = levels[fd.first_level + b.level];
-    const double W = (double)fd.W, H = (double)fd.H, Wk = (double)L.Wk, Hk = (double)L.Hk;
-    b.x = (float)__ddiv_rn(__dmul_rn((double)(8 * b.wx), W), Wk);
-    b.y = (float)__ddiv_rn(__dmul_rn((double)(8 * b.wy), H), Hk);
-    b.w = (float)__ddiv_rn(__dmul_rn(64.0, W), Wk);
-    b.h = (float)__ddiv_rn(__dmul_rn(128.0, H), Hk);
+    const int2 d = wkhk[b.level];
+    const long long nx = 8LL * b.wx * W, ny = 8LL * b.wy * H;
+    if (nx < (1 << 24) && ny < (1 << 24) && 128LL * H < (1 << 24) && 64LL * W < (1 << 24) &&
+        d.x < (1 << 24) && d.y < (1 << 24)) {
+        b.x = __fdiv_rn((float)nx, (float)d.x);
+        b.y = __fdiv_rn((float)ny, (float)d.y);
+        b.w = __fdiv_rn((float)(64 * W), (float)d.x);
+        b.h = __fdiv_rn((float)(128 * H), (float)d.y);
+    } else {  // operands not exact in float: the double quotient, rounded
+        b.x = (float)__ddiv_rn((double)nx, (double)d.x);
+        b.y = (float)__ddiv_rn((double)ny, (double)d.y);
+        b.w = (float)__ddiv_rn(64.0 * W, (double)d.x);
+        b.h = (float)__ddiv_rn(128.0 * H, (double)d.y);
+    }
     return b;
 }
 
@@ -99,8 +110,13 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
                                                   int32_t *__restrict__ counts) {
     extern __shared__ unsigned long long keys[];  // [cap_pow2] then cap bytes of flags
     __shared__ int n_cand;
+    __shared__ int2 wkhk[PD_MAX_LEVELS];  // level sizes of this frame
     const int f = blockIdx.x, tid = threadIdx.x;
     const FrameDesc fd = frames[f];
+    for (int k = tid; k < fd.n_levels; k += kThreads) {
+        const LevelDesc L = levels[fd.first_level + k];
+        wkhk[k] = make_int2(L.Wk, L.Hk);
+    }
     int cap_pow2 = 1;
     while (cap_pow2 < cap) cap_pow2 <<= 1;
     uint8_t *supp = reinterpret_cast<uint8_t *>(keys + cap_pow2);
@@ -111,10 +127,16 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
         const LevelDesc L = levels[fd.first_level + k];
         const int n = L.rows * L.cols;
         const float *sc = scores + L.score_off;
-        for (int i = tid; i < n; i += kThreads) {
-            const float s = sc[i];
-            if (s > threshold) {
-                const int idx = atomicAdd(&n_cand, 1);
+        for (int i0 = 0; i0 < n; i0 += kThreads) {  // warp-aggregated appends
+            const int i = i0 + tid;
+            const float s = i < n ? sc[i] : 0.f;
+            const bool hit = i < n && s > threshold;
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            int base = 0;
+            if ((tid & 31) == 0 && m) base = atomicAdd(&n_cand, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (hit) {
+                const int idx = base + __popc(m & ((1u << (tid & 31)) - 1u));
                 if (idx < cap) {
                     const int wy = i / L.cols;
                     keys[idx] = make_key(s, k, wy, i - wy * L.cols);
@@ -154,14 +176,14 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
     }
     float4 *bx = scratch + (size_t)f * cap;
     for (int i = tid; i < n; i += kThreads) {
-        const pd_box b = decode(keys[i], fd, levels);
+        const pd_box b = decode(keys[i], fd.W, fd.H, wkhk);
         bx[i] = make_float4(b.x, b.y, b.w, b.h);
     }
     __syncthreads();
     // Greedy walk. `next` (the first candidate after i that survived the
-    // pass) is found with a block-wide atomicMin during the pass, so no
-    // thread rescans the flags; two slots alternate so that resetting one
-    // never races with reading the other.
+    // pass) is found during the pass (per-thread min, warp min, one atomicMin
+    // per warp), so no thread rescans the flags; two slots alternate so that
+    // resetting one never races with reading the other.
     __shared__ int next_slot[2];
     int kept = 0, i = n > 0 ? 0 : n, parity = 0;
     pd_box *out = boxes + (size_t)f * max_boxes;
@@ -186,11 +208,14 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
         ++kept;
         if (kept == max_boxes) break;
         __syncthreads();
+        int first = n;  // first survivor seen by this thread
         for (int j = i + 1 + tid; j < n; j += kThreads) {
             if (supp[j]) continue;
             if (suppresses(bi, bx[j], iou_thr)) supp[j] = 1;
-            else atomicMin(&next_slot[parity], j);
+            else first = min(first, j);
         }
+        first = __reduce_min_sync(0xffffffffu, first);
+        if ((tid & 31) == 0 && first < n) atomicMin(&next_slot[parity], first);
         __syncthreads();
         i = next_slot[parity];
         parity ^= 1;

@@ -45,7 +45,10 @@ __global__ void __launch_bounds__(kThreads) k_resize(const FrameDesc *__restrict
     const FrameDesc fd = frames[it.frame];
     const int tid = threadIdx.x;
 
-    // Stage the source tile [x0, x0+129) x [y0, y0+33) clamped to the frame.
+    // Stage the source tile [x0, x0+129) x [y0, y0+33) clamped to the frame
+    // (independent loads, unrolled so that many are in flight: the frame may
+    // be read straight from pinned host memory).
+#pragma unroll 6
     for (int i = tid; i < kSmemH * (kTileW + 1); i += kThreads) {
         int r = i / (kTileW + 1), c = i - r * (kTileW + 1);
         int y = min(it.y0 + r, fd.H - 1), x = min(it.x0 + c, fd.W - 1);

@@ -195,8 +195,10 @@ struct pd_handle {
     int64_t level_cap = 0, r_cap = 0, c_cap = 0, s_cap = 0, tab_cap = 0;
     // pinned host
     unsigned char *h_desc = nullptr;
-    pd_box *h_boxes = nullptr;
-    int32_t *h_counts = nullptr;
+    pd_box *h_boxes = nullptr;     // mapped: written by the NMS kernel
+    int32_t *h_counts = nullptr;   // mapped: [2 * max_frames] kept / candidates
+    pd_box *m_boxes = nullptr;     // device views of the two mapped buffers
+    int32_t *m_counts = nullptr;
     unsigned *h_err = nullptr;
     cudaEvent_t desc_done = nullptr;
     cudaEvent_t stage_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -207,6 +209,13 @@ struct pd_handle {
                                    kDefaultTileCost[3]};
     // last batch
     Plan plan;
+    // cached plan + captured graph for a repeated batch shape
+    std::vector<int32_t> sig;        // n_frames, then (W, H, pitch) per frame
+    bool cache_valid = false;        // plan + full descriptors on the device match `sig`
+    Packed packed{};
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    cudaEvent_t graph_done = nullptr;
     cudaStream_t stream = nullptr;
     bool detected = false, synced = false;
     int last_launches = 0;
@@ -366,6 +375,15 @@ int encode_svm_maps(CUtensorMap *hog_maps, CUtensorMap *lbp_maps, const float *h
     return PD_OK;
 }
 
+void invalidate_cache(pd_handle *h) {
+    h->cache_valid = false;
+    h->sig.clear();
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+}
+
 template <class T>
 const T *dptr(pd_handle *h, int64_t off) {
     return reinterpret_cast<const T *>(h->d_desc + off);
@@ -409,6 +427,9 @@ void pd_destroy(pd_handle *h) {
     if (h->h_boxes) cudaFreeHost(h->h_boxes);
     if (h->h_counts) cudaFreeHost(h->h_counts);
     if (h->desc_done) cudaEventDestroy(h->desc_done);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->graph_done) cudaEventDestroy(h->graph_done);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (auto &e : h->stage_ev)
         if (e) cudaEventDestroy(e);
     delete h;
@@ -439,8 +460,31 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
         // frames too small for any window still get a valid (tiny) arena
         worst.max_wc = std::max(params->max_width / 8, 1);
     }
-    const Packed wp = pack_layout(worst);
-    h->desc_cap = round_up(wp.total + 4096, kAlign);
+    // Descriptor capacity: per frame, the largest frame's levels, work items
+    // (K4 tiles counted for the shape with the most tiles) and its own Q11
+    // tables (frames of different sizes do not share them).
+    {
+        Plan one;
+        plan_frame(one, *params, nullptr, params->max_width, params->max_height, params->max_width);
+        int64_t s_bound = 0;
+        for (const LevelDesc &L : one.levels) {
+            int64_t most = 0;
+            for (int sh = 0; sh < kSvmShapes; ++sh) {
+                const SvmShapeInfo si = svm_shape(sh);
+                most = std::max<int64_t>(most, (int64_t)((L.rows + si.th - 1) / si.th) *
+                                                   ((L.cols + si.tw - 1) / si.tw));
+            }
+            s_bound += most;
+        }
+        const int64_t F = params->max_frames;
+        h->desc_cap = round_up(F * (int64_t)sizeof(FrameDesc), 16) +
+                      round_up(F * (int64_t)one.levels.size() * (int64_t)sizeof(LevelDesc), 16) +
+                      round_up(F * (int64_t)one.r_items.size() * (int64_t)sizeof(ResizeItem), 16) +
+                      round_up(F * (int64_t)one.c_items.size() * (int64_t)sizeof(CellItem), 16) +
+                      round_up(F * s_bound * (int64_t)sizeof(SvmItem), 16) +
+                      round_up(F * (int64_t)one.tabs.size() * 4, 16) + 4096;
+        h->desc_cap = round_up(h->desc_cap, kAlign);
+    }
     h->pyr_cap = round_up(std::max<int64_t>(worst.pyr_bytes, 16), kAlign);
     const int32_t P = (int32_t)std::max<int64_t>(round_up(std::max(worst.max_wc, 1), 16), 48);
     const int32_t rows = std::max(worst.atlas_rows, 1);
@@ -490,18 +534,27 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
     h->d_nms_scratch = reinterpret_cast<float4 *>(h->arena + parts[10].off);
 
     if (cudaMallocHost(&h->h_desc, h->desc_cap) != cudaSuccess) return bail(PD_ENOMEM);
-    if (cudaMallocHost(&h->h_boxes, (size_t)params->max_frames * params->max_boxes_per_frame *
-                                        sizeof(pd_box)) != cudaSuccess)
+    // Results land in mapped pinned host memory: NMS writes the kept boxes and
+    // counts there directly, so pd_sync needs no device-to-host copies.
+    if (cudaHostAlloc(&h->h_boxes, (size_t)params->max_frames * params->max_boxes_per_frame * sizeof(pd_box),
+                      cudaHostAllocMapped) != cudaSuccess)
         return bail(PD_ENOMEM);
-    if (cudaMallocHost(&h->h_counts, (size_t)params->max_frames * 2 * 4 + 16) != cudaSuccess)
+    if (cudaHostAlloc(&h->h_counts, (size_t)params->max_frames * 2 * 4 + 16, cudaHostAllocMapped) != cudaSuccess)
         return bail(PD_ENOMEM);
     h->h_err = reinterpret_cast<unsigned *>(h->h_counts + 2 * params->max_frames);
+    if (cudaHostGetDevicePointer(reinterpret_cast<void **>(&h->m_boxes), h->h_boxes, 0) != cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void **>(&h->m_counts), h->h_counts, 0) != cudaSuccess)
+        return bail(PD_ECUDA);
     if (cudaEventCreateWithFlags(&h->desc_done, cudaEventDisableTiming) != cudaSuccess)
         return bail(PD_ECUDA);
     if (cudaEventRecord(h->desc_done, 0) != cudaSuccess) return bail(PD_ECUDA);
     if (params->flags & PD_FLAG_STAGE_TIMING)
         for (auto &e : h->stage_ev)
             if (cudaEventCreate(&e) != cudaSuccess) return bail(PD_ECUDA);
+    if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->graph_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(h->graph_done, 0) != cudaSuccess)
+        return bail(PD_ECUDA);
 
     // template -> [t][i][8] (j padded), lbp map
     std::vector<float> wt((size_t)kFeat * kWinBH * kWPad, 0.f);
@@ -530,41 +583,99 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
         return fail(h, PD_EINVAL, "n_frames %d outside [0, %d]", n_frames, h->p.max_frames);
     if (n_frames > 0 && (!d_frames || !widths || !heights || !pitches))
         return fail(h, PD_EINVAL, "null argument");
-    Plan &p = h->plan;
-    p.clear();
+    std::vector<int32_t> sig;
+    sig.reserve(1 + 3 * (size_t)n_frames);
+    sig.push_back(n_frames);
     for (int f = 0; f < n_frames; ++f) {
         const int W = widths[f], H = heights[f], pitch = pitches[f];
         if (W < 1 || H < 1 || W > h->p.max_width || H > h->p.max_height || pitch < W || !d_frames[f])
             return fail(h, PD_EINVAL, "frame %d: bad size %dx%d pitch %d", f, W, H, pitch);
-        int r = plan_frame(p, h->p, d_frames[f], W, H, pitch, h->tile_cost);
-        if (r != PD_OK) return fail(h, r, "frame %d: planning failed", f);
+        sig.push_back(W);
+        sig.push_back(H);
+        sig.push_back(pitch);
     }
-    if (p.atlas_rows > h->atlas.rows || p.pyr_bytes > h->pyr_cap || p.score_floats > h->score_cap)
-        return fail(h, PD_EINVAL, "batch exceeds the arena");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     h->stream = s;
-    Packed o;
-    int r = upload_plan(h, s, p, o);
-    if (r != PD_OK) return r;
-    PD_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), s));
+    Plan &p = h->plan;
+    const bool reuse = h->cache_valid && sig == h->sig;
+    if (!reuse) {
+        invalidate_cache(h);
+        p.clear();
+        for (int f = 0; f < n_frames; ++f) {
+            int r = plan_frame(p, h->p, d_frames[f], widths[f], heights[f], pitches[f], h->tile_cost);
+            if (r != PD_OK) return fail(h, r, "frame %d: planning failed", f);
+        }
+        if (p.atlas_rows > h->atlas.rows || p.pyr_bytes > h->pyr_cap || p.score_floats > h->score_cap)
+            return fail(h, PD_EINVAL, "batch exceeds the arena");
+        // full descriptor upload, once per batch shape
+        int r = upload_plan(h, s, p, h->packed);
+        if (r != PD_OK) return r;
+        h->sig = sig;
+        h->cache_valid = true;
+    }
+    // frame pointers change from call to call: rewrite only that section
+    PD_CUDA(h, cudaEventSynchronize(h->graph_done));
+    PD_CUDA(h, cudaEventSynchronize(h->desc_done));
+    for (int f = 0; f < n_frames; ++f) p.frames[f].ptr = d_frames[f];
+    const Packed &o = h->packed;
+    if (n_frames) std::memcpy(h->h_desc + o.frames, p.frames.data(), p.frames.size() * sizeof(FrameDesc));
     const FrameDesc *df = dptr<FrameDesc>(h, o.frames);
     const LevelDesc *dl = dptr<LevelDesc>(h, o.levels);
     const bool timed = (h->p.flags & PD_FLAG_STAGE_TIMING) != 0;
     h->timed = timed;
-    if (timed) PD_CUDA(h, cudaEventRecord(h->stage_ev[0], s));
-    PD_CUDA(h, launch_resize(s, df, dl, dptr<int32_t>(h, o.tabs), h->d_pyr, dptr<ResizeItem>(h, o.r_items),
-                             (int)p.r_items.size()));
-    if (timed) PD_CUDA(h, cudaEventRecord(h->stage_ev[1], s));
-    PD_CUDA(h, launch_cells(s, dl, h->d_pyr, h->atlas, dptr<CellItem>(h, o.c_items), (int)p.c_items.size(),
-                            h->d_lbp_map));
-    if (timed) PD_CUDA(h, cudaEventRecord(h->stage_ev[2], s));
-    PD_CUDA(h, launch_svm(s, h->hog_map, h->lbp_map, dl, h->d_w, h->bias, h->p.l2hys_clip, h->d_scores,
-                          dptr<SvmItem>(h, o.s_items), (int)p.s_items.size(), h->d_err));
-    if (timed) PD_CUDA(h, cudaEventRecord(h->stage_ev[3], s));
-    PD_CUDA(h, launch_nms(s, df, dl, n_frames, h->d_scores, h->p.threshold, h->p.nms_iou,
-                          h->d_nms_scratch, h->p.max_candidates_per_frame, h->d_boxes,
-                          h->p.max_boxes_per_frame, h->d_counts));
-    if (timed) PD_CUDA(h, cudaEventRecord(h->stage_ev[4], s));
+    // inside a capture an event record must be an external node to be timed
+    bool capturing = false;
+    auto record = [&](cudaEvent_t e, cudaStream_t q) {
+        return capturing ? cudaEventRecordWithFlags(e, q, cudaEventRecordExternal) : cudaEventRecord(e, q);
+    };
+    auto enqueue = [&](cudaStream_t q) -> int {
+        if (n_frames)
+            PD_CUDA(h, cudaMemcpyAsync(h->d_desc + o.frames, h->h_desc + o.frames,
+                                       p.frames.size() * sizeof(FrameDesc), cudaMemcpyHostToDevice, q));
+        PD_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), q));
+        if (timed) PD_CUDA(h, record(h->stage_ev[0], q));
+        PD_CUDA(h, launch_resize(q, df, dl, dptr<int32_t>(h, o.tabs), h->d_pyr, dptr<ResizeItem>(h, o.r_items),
+                                 (int)p.r_items.size()));
+        if (timed) PD_CUDA(h, record(h->stage_ev[1], q));
+        PD_CUDA(h, launch_cells(q, dl, h->d_pyr, h->atlas, dptr<CellItem>(h, o.c_items), (int)p.c_items.size(),
+                                h->d_lbp_map));
+        if (timed) PD_CUDA(h, record(h->stage_ev[2], q));
+        PD_CUDA(h, launch_svm(q, h->hog_map, h->lbp_map, dl, h->d_w, h->bias, h->p.l2hys_clip, h->d_scores,
+                              dptr<SvmItem>(h, o.s_items), (int)p.s_items.size(), h->d_err));
+        if (timed) PD_CUDA(h, record(h->stage_ev[3], q));
+        PD_CUDA(h, launch_nms(q, df, dl, n_frames, h->d_scores, h->p.threshold, h->p.nms_iou,
+                              h->d_nms_scratch, h->p.max_candidates_per_frame, h->m_boxes,
+                              h->p.max_boxes_per_frame, h->m_counts));
+        if (timed) PD_CUDA(h, record(h->stage_ev[4], q));
+        return PD_OK;
+    };
+    if (reuse && !h->graph) {
+        // second call with this batch shape: capture the step once
+        PD_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        capturing = true;
+        int r = enqueue(h->cap_stream);
+        capturing = false;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+        if (r != PD_OK) {
+            if (g) cudaGraphDestroy(g);
+            return r;
+        }
+        if (e != cudaSuccess) return fail(h, PD_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&h->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            h->graph = nullptr;
+            return fail(h, PD_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+    }
+    if (h->graph) {
+        PD_CUDA(h, cudaGraphLaunch(h->graph, s));
+    } else {
+        int r = enqueue(s);
+        if (r != PD_OK) return r;
+    }
+    PD_CUDA(h, cudaEventRecord(h->graph_done, s));
     h->last_launches = (p.r_items.empty() ? 0 : 1) + (p.c_items.empty() ? 0 : 1) +
                        (p.s_items.empty() ? 0 : 1) + (n_frames > 0 ? 1 : 0);
     h->detected = true;
@@ -586,6 +697,16 @@ int pd_detect_host(pd_handle *h, void *stream, int n_frames, const uint8_t *cons
         const int W = widths[f], H = heights[f];
         if (W < 1 || H < 1 || W > h->p.max_width || H > h->p.max_height || pitches[f] < W || !h_frames[f])
             return fail(h, PD_EINVAL, "frame %d: bad size %dx%d pitch %d", f, W, H, pitches[f]);
+        // Pinned (page-locked) host frames are read by the pyramid kernel in
+        // place, over the host link; other host memory is copied first.
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, h_frames[f]) == cudaSuccess && a.type == cudaMemoryTypeHost &&
+            a.devicePointer) {
+            dev[f] = reinterpret_cast<const uint8_t *>(a.devicePointer);
+            dp[f] = pitches[f];
+            continue;
+        }
+        cudaGetLastError();  // clear a failed query on unregistered memory
         dp[f] = (int32_t)round_up(W, 16);
         dev[f] = h->d_frames + off;
         PD_CUDA(h, cudaMemcpy2DAsync(h->d_frames + off, dp[f], h_frames[f], pitches[f], W, H,
@@ -599,25 +720,25 @@ int pd_sync(pd_handle *h) {
     if (!h) return PD_EINVAL;
     if (!h->detected) return fail(h, PD_ESTATE, "pd_sync without pd_detect");
     const int nf = (int)h->plan.frames.size();
-    PD_CUDA(h, cudaMemcpyAsync(h->h_counts, h->d_counts, (size_t)nf * 2 * 4, cudaMemcpyDeviceToHost, h->stream));
     PD_CUDA(h, cudaMemcpyAsync(h->h_err, h->d_err, 4, cudaMemcpyDeviceToHost, h->stream));
-    PD_CUDA(h, cudaStreamSynchronize(h->stream));
+    PD_CUDA(h, cudaStreamSynchronize(h->stream));  // boxes and counts are already in host memory
     int status = PD_OK;
     if (*h->h_err & kErrTimeout) status = fail(h, PD_ETIMEOUT, "device wait timed out");
     else if (*h->h_err & kErrBounds) status = fail(h, PD_EBOUNDS, "device bounds check fired");
-    for (int f = 0; f < nf; ++f) {
-        const int kept = h->h_counts[2 * f];
-        if (h->h_counts[2 * f + 1] < 0 && status == PD_OK)
+    for (int f = 0; f < nf && status == PD_OK; ++f)
+        if (h->h_counts[2 * f + 1] < 0)
             status = fail(h, PD_EOVERFLOW, "frame %d: %d candidates > %d", f, -h->h_counts[2 * f + 1],
                           h->p.max_candidates_per_frame);
-        if (kept > 0)
-            PD_CUDA(h, cudaMemcpyAsync(h->h_boxes + (size_t)f * h->p.max_boxes_per_frame,
-                                       h->d_boxes + (size_t)f * h->p.max_boxes_per_frame,
-                                       (size_t)kept * sizeof(pd_box), cudaMemcpyDeviceToHost, h->stream));
-    }
-    PD_CUDA(h, cudaStreamSynchronize(h->stream));
     h->synced = true;
     return status;
+}
+
+int pd_frame_candidates(const pd_handle *h, int frame, int *n) {
+    if (!h || !n) return PD_EINVAL;
+    if (!h->synced) return PD_ESTATE;
+    if (frame < 0 || frame >= (int)h->plan.frames.size()) return PD_EINVAL;
+    *n = h->h_counts[2 * frame + 1];
+    return PD_OK;
 }
 
 int pd_set_tile_costs(pd_handle *h, const float *cost) {
@@ -625,6 +746,7 @@ int pd_set_tile_costs(pd_handle *h, const float *cost) {
     for (int s = 0; s < kSvmShapes; ++s)
         if (!(cost[s] > 0.f)) return fail(h, PD_EINVAL, "tile cost %d must be > 0", s);
     for (int s = 0; s < kSvmShapes; ++s) h->tile_cost[s] = cost[s];
+    invalidate_cache(h);
     return PD_OK;
 }
 
@@ -684,6 +806,7 @@ int pd_resize_levels(pd_handle *h, void *stream, const uint8_t *d_frame, int W, 
                      int n_levels, const int32_t *Wk, const int32_t *Hk, uint8_t *d_levels,
                      const int64_t *level_offsets, const int32_t *level_pitches) {
     if (!h) return PD_EINVAL;
+    invalidate_cache(h);  // the descriptor region is reused below
     if (!d_frame || !d_levels || !Wk || !Hk || !level_offsets || !level_pitches || W < 1 || H < 1 ||
         pitch < W || n_levels < 0 || n_levels > PD_MAX_LEVELS)
         return fail(h, PD_EINVAL, "pd_resize_levels: bad argument");
@@ -718,6 +841,7 @@ int pd_resize_levels(pd_handle *h, void *stream, const uint8_t *d_frame, int W, 
 int pd_cell_features(pd_handle *h, void *stream, const uint8_t *d_level, int Wk, int Hk, int pitch,
                      float *d_hog, int64_t hog_plane, uint8_t *d_lbp, int64_t lbp_plane, int cell_pitch) {
     if (!h) return PD_EINVAL;
+    invalidate_cache(h);  // the descriptor region is reused below
     const int Wc = Wk / 8, Hc = Hk / 8;
     if (!d_level || !d_hog || !d_lbp || Wk < 1 || Hk < 1 || pitch < Wk || cell_pitch < Wc ||
         cell_pitch % 16 != 0 || hog_plane < (int64_t)Hc * cell_pitch || lbp_plane < (int64_t)Hc * cell_pitch)
@@ -746,6 +870,7 @@ int pd_window_scores(pd_handle *h, void *stream, const float *d_hog, int64_t hog
                      const uint8_t *d_lbp, int64_t lbp_plane, int cell_pitch, int cells_x, int cells_y,
                      float *d_scores) {
     if (!h) return PD_EINVAL;
+    invalidate_cache(h);  // the descriptor region is reused below
     if (!d_hog || !d_lbp || !d_scores || cells_x < 0 || cells_y < 0 || cell_pitch < cells_x ||
         cell_pitch % 16 != 0 || hog_plane % 4 != 0 || lbp_plane % 16 != 0 ||
         hog_plane < (int64_t)cells_y * cell_pitch || lbp_plane < (int64_t)cells_y * cell_pitch ||
@@ -775,6 +900,7 @@ int pd_nms_maps(pd_handle *h, void *stream, const float *d_scores, int n_levels,
                 const int32_t *cols, const int32_t *Wk, const int32_t *Hk, int W, int H, pd_box *d_boxes,
                 int max_boxes, int32_t *d_counts) {
     if (!h) return PD_EINVAL;
+    invalidate_cache(h);  // the descriptor region is reused below
     if (!d_scores || !rows || !cols || !Wk || !Hk || !d_boxes || !d_counts || n_levels < 0 ||
         n_levels > PD_MAX_LEVELS || max_boxes < 1 || W < 1 || H < 1)
         return fail(h, PD_EINVAL, "pd_nms_maps: bad argument");

@@ -327,10 +327,17 @@ def test_detect_host_equals_device(template):
         d.detect([torch.from_numpy(im).cuda() for im in imgs])
         assert d.sync() == pd.PD_OK
         dev = [d.boxes(i) for i in range(3)]
-        d.detect_host(imgs)
+        d.detect_host(imgs)  # pageable numpy frames: copied into the arena
         assert d.sync() == pd.PD_OK
         for i in range(3):
             assert np.array_equal(d.boxes(i), dev[i])
+        pinned = [torch.from_numpy(im).pin_memory() for im in imgs]
+        for _ in range(3):  # pinned frames: read in place (plan, capture, replay)
+            d.detect_host(pinned)
+            assert d.sync() == pd.PD_OK
+            for i in range(3):
+                assert np.array_equal(d.boxes(i), dev[i])
+                assert pd.pd_frame_candidates(d.h, i) > 0
     finally:
         d.close()
 
@@ -376,3 +383,34 @@ def test_window_scores_every_tile_shape(template, shape):
             _check_scores(got, feat, w, b, oracle.scores(feat, w, b), f"shape {shape} {W}x{H}")
     finally:
         d.close()
+
+
+def test_repeated_batch_shape_replays_graph_with_new_frames(template):
+    # calls 1, 2, 3 with one batch shape: plan, capture, replay; each must
+    # equal a fresh handle's result for the same frames
+    from paper_1611_01642_gb300 import build as bld
+    bld.build()
+    w, b = template
+    sizes = [(640, 480), (1242, 375), (333, 200)]
+    batches = [[synth.make_scene(W, H, 3, 100 * k + i) for i, (W, H) in enumerate(sizes)]
+               for k in range(3)]
+    d = pd.Detector(w, b, max_frames=3, max_width=1242, max_height=480)
+    try:
+        got = []
+        for imgs in batches:
+            d.detect([torch.from_numpy(im).cuda() for im in imgs])
+            assert d.sync() == pd.PD_OK
+            got.append(([torch.cat([m.reshape(-1) for m in d.score_maps(i)]).clone() for i in range(3)],
+                        [d.boxes(i) for i in range(3)]))
+    finally:
+        d.close()
+    for imgs, (maps, boxes) in zip(batches, got):
+        f = pd.Detector(w, b, max_frames=3, max_width=1242, max_height=480)
+        try:
+            f.detect([torch.from_numpy(im).cuda() for im in imgs])
+            assert f.sync() == pd.PD_OK
+            for i in range(3):
+                assert torch.equal(torch.cat([m.reshape(-1) for m in f.score_maps(i)]), maps[i])
+                assert np.array_equal(f.boxes(i), boxes[i])
+        finally:
+            f.close()
