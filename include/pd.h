@@ -68,7 +68,7 @@ typedef struct pd_params {
     float l2hys_clip;        /* HOG L2-Hys clipping value, 0.2 */
     float threshold;         /* a window is a detection iff score > threshold (0) */
     float nms_iou;           /* NMS suppresses when IoU > nms_iou (0.5) */
-    int32_t max_boxes_per_frame;      /* NMS output cap per frame (4096) */
+    int32_t max_boxes_per_frame;      /* NMS output cap per frame (4096), <= 16384 */
     int32_t max_candidates_per_frame; /* windows above threshold per frame, <= 16384 */
     int32_t max_frames;      /* frames per pd_detect call (arena sizing) */
     int32_t max_width;       /* largest frame width  (arena sizing) */
@@ -251,7 +251,7 @@ int pd_nms_maps(pd_handle *h, void *stream, const float *d_scores, int n_levels,
  * every candidate) is one static array inside the library, about 270 KB,
  * that every GPU which loads the library holds until the process exits; it
  * limits a call to max_candidates <= 16384 and n_levels <= PD_MAX_LEVELS
- * (larger values return PD_EINVAL). The caller passes inputs and outputs as
+ * (larger values, or max_boxes > 16384, return PD_EINVAL). The caller passes inputs and outputs as
  * for pd_nms_maps: d_scores, d_boxes (cap max_boxes) and d_counts (kept,
  * candidates; a candidate overflow writes 0 and -candidates). The first call
  * on a device looks up the array's device address and sets the kernel's

@@ -8,17 +8,24 @@
 //     so ascending keys = score descending, then level, wy, wx ascending);
 //  2. bitonic-sorts the keys;
 //  3. decodes every candidate's box once (exactly rounded float division)
-//     into a per-frame global scratch array;
+//     into shared memory (over the no longer needed key array, whose keys
+//     move to a per-frame global scratch array) or, for very many
+//     candidates, into that global scratch;
 //  4. walks the candidates in order: one not yet suppressed is kept, all
 //     threads then suppress the later candidates whose IoU with it exceeds
 //     the threshold, and the first survivor after it is the next one kept.
-// The IoU test first evaluates the IoU in float; the float value is within
-// 1e-4 of the exact one for boxes of this detector (sides >= 64 px,
-// coordinates < 8192), so a float IoU more than 1e-3 away from the threshold
+// The IoU test first evaluates the IoU in float. For boxes of this detector
+// (width >= 64, height >= 128, coordinates < 8192) the float value is within
+// 7e-5 of the exact one: each coordinate sum or difference is off by at most
+// 3 float roundings of values < 8192 (1.5e-3 px), which moves the
+// intersection by at most (w + h) * 1.5e-3 px^2 and the IoU by at most
+// 1.5e-3 * (1/w + 1/h) <= 3.5e-5 through the intersection and as much again
+// through the union. So a float IoU more than 2e-4 away from the threshold
 // decides; otherwise the IoU is recomputed in double precision with
 // explicitly rounded operations (no FMA contraction), which is the exact IEEE
 // evaluation of the definition. Decisions are therefore the same as those of
-// a plain double-precision implementation.
+// a plain double-precision implementation, and the slow double path runs
+// only for the rare pairs in the band.
 #include <mutex>
 
 #include "pd_internal.h"
@@ -27,6 +34,8 @@ namespace pd {
 namespace {
 
 constexpr int kThreads = 1024;
+constexpr int kMaxCandidates = 16384;  // keys + flags + kept list fit in shared memory
+constexpr int kMaxBoxes = 16384;
 
 __device__ __forceinline__ unsigned long long make_key(float s, int level, int wy, int wx) {
     const uint32_t u = __float_as_uint(s);
@@ -36,6 +45,13 @@ __device__ __forceinline__ unsigned long long make_key(float s, int level, int w
 }
 
 __device__ __forceinline__ bool suppresses(const float4 &a, const float4 &b, float thr);
+
+__device__ __noinline__ void decode_f64(long long nx, long long ny, int W, int H, int2 d, pd_box &b) {
+    b.x = (float)__ddiv_rn((double)nx, (double)d.x);
+    b.y = (float)__ddiv_rn((double)ny, (double)d.y);
+    b.w = (float)__ddiv_rn(64.0 * W, (double)d.x);
+    b.h = (float)__ddiv_rn(128.0 * H, (double)d.y);
+}
 
 // Box of a key. x = 8*wx*W/Wk etc. are quotients of integers below 2^24, so
 // the correctly rounded float quotient (__fdiv_rn) equals the double quotient
@@ -59,10 +75,7 @@ __device__ __forceinline__ pd_box decode(unsigned long long key, int W, int H, c
         b.w = __fdiv_rn((float)(64 * W), (float)d.x);
         b.h = __fdiv_rn((float)(128 * H), (float)d.y);
     } else {  // operands not exact in float: the double quotient, rounded
-        b.x = (float)__ddiv_rn((double)nx, (double)d.x);
-        b.y = (float)__ddiv_rn((double)ny, (double)d.y);
-        b.w = (float)__ddiv_rn(64.0 * W, (double)d.x);
-        b.h = (float)__ddiv_rn(128.0 * H, (double)d.y);
+        decode_f64(nx, ny, W, H, d, b);
     }
     return b;
 }
@@ -82,7 +95,9 @@ __device__ __forceinline__ double iou(const pd_box &a, const pd_box &b) {
     return __ddiv_rn(inter, ua);
 }
 
-__device__ __forceinline__ double iou4(const float4 &a, const float4 &b) {
+// Out of line on purpose: the double-precision path is rare, and inlined it
+// would be if-converted and executed for every pair.
+__device__ __noinline__ double iou4(const float4 &a, const float4 &b) {
     pd_box x, y;
     x.x = a.x; x.y = a.y; x.w = a.z; x.h = a.w;
     y.x = b.x; y.y = b.y; y.w = b.z; y.h = b.w;
@@ -95,10 +110,10 @@ __device__ __forceinline__ bool suppresses(const float4 &a, const float4 &b, flo
     float fi = 0.f;
     if (iw > 0.f && ih > 0.f) {
         const float inter = iw * ih;
-        fi = inter / (a.z * a.w + b.z * b.w - inter);
+        fi = __fdividef(inter, a.z * a.w + b.z * b.w - inter);
     }
-    if (fi < thr - 1e-3f) return false;
-    if (fi > thr + 1e-3f) return true;
+    if (fi < thr - 2e-4f) return false;
+    if (fi > thr + 2e-4f) return true;
     return iou4(a, b) > (double)thr;
 }
 
@@ -108,7 +123,7 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
                                                   float iou_thr, int cap, float4 *__restrict__ scratch,
                                                   pd_box *__restrict__ boxes, int max_boxes,
                                                   int32_t *__restrict__ counts) {
-    extern __shared__ unsigned long long keys[];  // [cap_pow2] then cap bytes of flags
+    extern __shared__ unsigned long long keys[];  // [cap_pow2], cap bytes of flags, kept list
     __shared__ int n_cand;
     __shared__ int2 wkhk[PD_MAX_LEVELS];  // level sizes of this frame
     const int f = blockIdx.x, tid = threadIdx.x;
@@ -174,51 +189,85 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
             __syncthreads();
         }
     }
-    float4 *bx = scratch + (size_t)f * cap;
-    for (int i = tid; i < n; i += kThreads) {
-        const pd_box b = decode(keys[i], fd.W, fd.H, wkhk);
-        bx[i] = make_float4(b.x, b.y, b.w, b.h);
+    // Decoded boxes: in shared memory when they fit in the key region (the
+    // keys then move to the global scratch, where only kept ones are read
+    // again), otherwise in the global scratch. Each greedy pass reads every
+    // remaining box, so keeping them on chip shortens every pass.
+    float4 *gbx = scratch + (size_t)f * cap;
+    const float4 *bx;
+    const unsigned long long *ksrc;
+    if (2 * n <= cap_pow2) {
+        unsigned long long *gkeys = reinterpret_cast<unsigned long long *>(gbx);
+        for (int i = tid; i < n; i += kThreads) gkeys[i] = keys[i];
+        __syncthreads();
+        float4 *sbx = reinterpret_cast<float4 *>(keys);
+        for (int i = tid; i < n; i += kThreads) {  // each thread re-reads only its own writes
+            const pd_box b = decode(gkeys[i], fd.W, fd.H, wkhk);
+            sbx[i] = make_float4(b.x, b.y, b.w, b.h);
+        }
+        bx = sbx;
+        ksrc = gkeys;
+    } else {
+        for (int i = tid; i < n; i += kThreads) {
+            const pd_box b = decode(keys[i], fd.W, fd.H, wkhk);
+            gbx[i] = make_float4(b.x, b.y, b.w, b.h);
+        }
+        bx = gbx;
+        ksrc = keys;
     }
     __syncthreads();
     // Greedy walk. `next` (the first candidate after i that survived the
     // pass) is found during the pass (per-thread min, warp min, one atomicMin
-    // per warp), so no thread rescans the flags; two slots alternate so that
-    // resetting one never races with reading the other.
-    __shared__ int next_slot[2];
-    int kept = 0, i = n > 0 ? 0 : n, parity = 0;
-    pd_box *out = boxes + (size_t)f * max_boxes;
+    // per warp), so no thread rescans the flags; three slots rotate so that a
+    // pass needs one barrier (the slot reset two passes ahead never races with
+    // a read or an update). Kept indices are recorded on chip and the output
+    // boxes are written after the walk, so each pass only touches shared
+    // memory.
+    __shared__ int next_slot[3];
+    int *kept_idx = reinterpret_cast<int *>(supp + ((cap + 15) & ~15));
+    if (tid == 0) next_slot[0] = next_slot[1] = next_slot[2] = n;
+    __syncthreads();
+    int kept = 0, i = n > 0 ? 0 : n, pass = 0;
     while (i < n && kept < max_boxes) {
-        const float4 bi = bx[i];
-        if (tid == 0) {
-            const unsigned long long key = keys[i];
-            const uint32_t hi = (uint32_t)(key >> 32), lo = (uint32_t)key;
-            const uint32_t ord = ~hi;
-            pd_box b;
-            b.x = bi.x;
-            b.y = bi.y;
-            b.w = bi.z;
-            b.h = bi.w;
-            b.score = __uint_as_float((ord & 0x80000000u) ? (ord ^ 0x80000000u) : ~ord);
-            b.level = (int)(lo >> 24);
-            b.wy = (int)((lo >> 12) & 4095);
-            b.wx = (int)(lo & 4095);
-            out[kept] = b;
-            next_slot[parity] = n;
-        }
+        if (tid == 0) kept_idx[kept] = i;
         ++kept;
         if (kept == max_boxes) break;
-        __syncthreads();
+        const float4 bi = bx[i];
+        const int slot = pass % 3;
         int first = n;  // first survivor seen by this thread
+#pragma unroll 4
         for (int j = i + 1 + tid; j < n; j += kThreads) {
             if (supp[j]) continue;
             if (suppresses(bi, bx[j], iou_thr)) supp[j] = 1;
             else first = min(first, j);
         }
         first = __reduce_min_sync(0xffffffffu, first);
-        if ((tid & 31) == 0 && first < n) atomicMin(&next_slot[parity], first);
-        __syncthreads();
-        i = next_slot[parity];
-        parity ^= 1;
+        if ((tid & 31) == 0 && first < n) atomicMin(&next_slot[slot], first);
+        __syncthreads();  // the one barrier of a pass
+        i = next_slot[slot];
+        // slot (pass+2)%3 was last read in the previous pass, before this
+        // barrier, and is next written in pass+2, after the next barrier
+        if (tid == 0) next_slot[(pass + 2) % 3] = n;
+        ++pass;
+    }
+    __syncthreads();
+    pd_box *out = boxes + (size_t)f * max_boxes;
+    for (int k = tid; k < kept; k += kThreads) {
+        const int c = kept_idx[k];
+        const unsigned long long key = ksrc[c];
+        const float4 bc = bx[c];
+        const uint32_t hi = (uint32_t)(key >> 32), lo = (uint32_t)key;
+        const uint32_t ord = ~hi;
+        pd_box b;
+        b.x = bc.x;
+        b.y = bc.y;
+        b.w = bc.z;
+        b.h = bc.w;
+        b.score = __uint_as_float((ord & 0x80000000u) ? (ord ^ 0x80000000u) : ~ord);
+        b.level = (int)(lo >> 24);
+        b.wy = (int)((lo >> 12) & 4095);
+        b.wx = (int)(lo & 4095);
+        out[k] = b;
     }
     if (tid == 0) {
         counts[2 * f] = kept;
@@ -226,17 +275,17 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
     }
 }
 
-size_t nms_smem(int cap) {
+size_t nms_smem(int cap, int max_boxes) {
     int p = 1;
     while (p < cap) p <<= 1;
-    return (size_t)p * sizeof(unsigned long long) + (size_t)cap;
+    return (size_t)p * sizeof(unsigned long long) + (size_t)((cap + 15) & ~15) + 4 * (size_t)max_boxes;
 }
 
 }  // namespace
 
 cudaError_t init_nms() {
     return cudaFuncSetAttribute(k_nms, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)nms_smem(16384));
+                                (int)nms_smem(kMaxCandidates, kMaxBoxes));
 }
 
 cudaError_t launch_nms(cudaStream_t s, const FrameDesc *d_frames, const LevelDesc *d_levels,
@@ -244,7 +293,9 @@ cudaError_t launch_nms(cudaStream_t s, const FrameDesc *d_frames, const LevelDes
                        float4 *scratch, int max_cand, pd_box *boxes, int max_boxes,
                        int32_t *counts) {
     if (n_frames <= 0) return cudaSuccess;
-    k_nms<<<n_frames, kThreads, nms_smem(max_cand), s>>>(d_frames, d_levels, scores, threshold, iou,
+    if (max_cand < 1 || max_cand > kMaxCandidates || max_boxes < 1 || max_boxes > kMaxBoxes)
+        return cudaErrorInvalidValue;
+    k_nms<<<n_frames, kThreads, nms_smem(max_cand, max_boxes), s>>>(d_frames, d_levels, scores, threshold, iou,
                                                          max_cand, scratch, boxes, max_boxes, counts);
     return cudaGetLastError();
 }
@@ -318,7 +369,7 @@ extern "C" int pd_nms_noalloc(void *stream, const float *d_scores, int n_levels,
     using namespace pd;
     if (!d_scores || !rows || !cols || !Wk || !Hk || !d_boxes || !d_counts || n_levels < 0 ||
         n_levels > kNoAllocMaxLevels || max_candidates < 1 || max_candidates > kNoAllocMaxCandidates ||
-        max_boxes < 1 || W < 1 || H < 1 || !(nms_iou >= 0.f))
+        max_boxes < 1 || max_boxes > kMaxBoxes || W < 1 || H < 1 || !(nms_iou >= 0.f))
         return PD_EINVAL;
     NoAllocGeometry g{};
     g.W = W;

@@ -335,7 +335,8 @@ int plan_frame(Plan &p, const pd_params &prm, const uint8_t *ptr, int W, int H, 
 
 bool params_ok(const pd_params *p) {
     return p && p->struct_size == sizeof(pd_params) && p->pyr_factor > 1.0f && p->l2hys_clip > 0.f &&
-           p->nms_iou >= 0.f && p->max_boxes_per_frame > 0 && p->max_candidates_per_frame > 0 &&
+           p->nms_iou >= 0.f && p->max_boxes_per_frame > 0 && p->max_boxes_per_frame <= 16384 &&
+           p->max_candidates_per_frame > 0 &&
            p->max_candidates_per_frame <= 16384 && p->max_frames > 0 && p->max_width > 0 &&
            p->max_height > 0;
 }
@@ -902,7 +903,7 @@ int pd_nms_maps(pd_handle *h, void *stream, const float *d_scores, int n_levels,
     if (!h) return PD_EINVAL;
     invalidate_cache(h);  // the descriptor region is reused below
     if (!d_scores || !rows || !cols || !Wk || !Hk || !d_boxes || !d_counts || n_levels < 0 ||
-        n_levels > PD_MAX_LEVELS || max_boxes < 1 || W < 1 || H < 1)
+        n_levels > PD_MAX_LEVELS || max_boxes < 1 || max_boxes > 16384 || W < 1 || H < 1)
         return fail(h, PD_EINVAL, "pd_nms_maps: bad argument");
     Plan p;
     FrameDesc fd{};
