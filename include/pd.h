@@ -240,6 +240,48 @@ int pd_nms_maps(pd_handle *h, void *stream, const float *d_scores, int n_levels,
                 const int32_t *cols, const int32_t *Wk, const int32_t *Hk, int W, int H,
                 pd_box *d_boxes, int max_boxes, int32_t *d_counts);
 
+/* ---------------------------------------------------------------------------
+ * Learned window proposal (not in the paper; a small network that predicts
+ * which windows of a pyramid level can score above the SVM threshold, so that
+ * the detector can skip the others). Per level image L:
+ *   x = bf16(L/255 - 0.5); a1 = relu(conv3x3 stride 2 (1 -> 16));
+ *   a2 = relu(conv3x3 s2 (16 -> 32)); a3 = relu(conv3x3 s2 (32 -> 32)), one
+ *   vector per 8x8 cell; h = wh . a3 + bh (1x1 head, one value per cell);
+ *   z[wy][wx] = bv + sum_{r<16, s<8} V[r][s] h[wy+r][wx+s], one keep-logit per
+ *   window (the window pooling lets the logit see the whole 64x128 window).
+ * bf16 inputs, weights and stored activations, fp32 accumulation.
+ * Parameters: PD_CNN_PARAMS floats in the order w1[16][1][3][3], b1[16],
+ * w2[32][16][3][3], b2[32], w3[32][32][3][3], b3[32], wh[32], bh, V[16][8], bv.
+ * ------------------------------------------------------------------------- */
+#define PD_CNN_PARAMS 14210
+
+/* Loads the proposal parameters (host, fp32 master copy) and resets the
+ * optimiser state. Synchronous. Errors: PD_EINVAL, PD_ECUDA. */
+int pd_cnn_set_params(pd_handle *h, const float *params, int n);
+
+/* Host copies of the master parameters and of the gradient of the last
+ * training step (either pointer may be NULL). Synchronous. */
+int pd_cnn_get_params(pd_handle *h, float *params, float *grad, int n);
+
+/* Proposal forward on one level image (device, u8, Wk x Hk, pitch): writes
+ * the per-cell head values to d_h (float, cells_y rows of h_pitch) and the
+ * window keep-logits to d_logits (float [cells_y-15][cells_x-7]). */
+int pd_cnn_forward(pd_handle *h, void *stream, const uint8_t *d_level, int Wk, int Hk, int pitch, float *d_h,
+                   int h_pitch, float *d_logits);
+
+/* One training step on the last pd_detect batch (same stream): every window
+ * of every level is an example, labelled positive iff its SVM score (already
+ * computed by that pd_detect) is > label_threshold; the loss is the mean
+ * binary cross-entropy with logits with positive weight pos_weight over all
+ * windows of the batch; the gradient is computed by this library's backward
+ * kernels (fixed-order reductions: deterministic) and, if lr > 0, Adam
+ * (beta 0.9 / 0.999, eps 1e-8) updates the master parameters. The first call
+ * allocates a training workspace (cudaMalloc). */
+int pd_cnn_train_step(pd_handle *h, void *stream, float pos_weight, float label_threshold, float lr);
+
+/* Loss of the last training step (synchronises the stream). */
+int pd_cnn_train_loss(pd_handle *h, void *stream, float *loss);
+
 /* Allocation-free NMS. The paper has no counterpart: this exists for
  * callers that must not allocate device memory at run time -- a real-time
  * frame loop whose coding rules forbid allocation after start-up, a plugin

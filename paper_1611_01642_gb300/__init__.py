@@ -35,7 +35,8 @@ TILE_SHAPE_DIMS = [(32, 16), (64, 8), (32, 8), (64, 4)]  # windows per K4 tile (
 EXPORTED = ["pd_params_default", "pd_pyramid", "pd_create", "pd_destroy", "pd_last_error",
             "pd_detect", "pd_detect_host", "pd_sync", "pd_frame_candidates", "pd_frame_levels", "pd_scores", "pd_boxes",
             "pd_last_launch_count", "pd_stage_times", "pd_set_tile_costs", "pd_get_tile_costs", "pd_resize_levels", "pd_cell_features", "pd_window_scores",
-            "pd_nms_maps", "pd_nms_noalloc"]
+            "pd_nms_maps", "pd_nms_noalloc", "pd_cnn_set_params", "pd_cnn_get_params", "pd_cnn_forward",
+            "pd_cnn_train_step", "pd_cnn_train_loss"]
 
 
 class pd_params(ctypes.Structure):
@@ -108,6 +109,11 @@ def load(path: str | None = None):
         "pd_window_scores": ([P, P, P, i64, P, i64, i, i, i, P], i),
         "pd_nms_maps": ([P, P, P, i, P, P, P, P, i, i, P, i, P], i),
         "pd_nms_noalloc": ([P, P, i, P, P, P, P, i, i, f, f, i, P, i, P], i),
+        "pd_cnn_set_params": ([P, P, i], i),
+        "pd_cnn_get_params": ([P, P, P, i], i),
+        "pd_cnn_forward": ([P, P, P, i, i, i, P, i, P], i),
+        "pd_cnn_train_step": ([P, P, f, f, f], i),
+        "pd_cnn_train_loss": ([P, P, P], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -311,6 +317,39 @@ def pd_nms_noalloc(scores, rows, cols, level_dims, W: int, H: int, threshold: fl
     _check(load().pd_nms_noalloc(_stream(stream), _ptr(scores), n, rp, cp, wkp, hkp, W, H,
                                  float(threshold), float(nms_iou), max_candidates, _ptr(boxes),
                                  max_boxes, _ptr(counts)))
+
+
+CNN_PARAMS = 14210
+
+
+def pd_cnn_set_params(h, params) -> None:
+    p, pp = _np(params, np.float32)
+    assert p.size == CNN_PARAMS
+    _check(load().pd_cnn_set_params(h, pp, CNN_PARAMS), h)
+
+
+def pd_cnn_get_params(h):
+    """(master parameters, gradient of the last training step) as float32 arrays."""
+    p = np.zeros(CNN_PARAMS, np.float32)
+    g = np.zeros(CNN_PARAMS, np.float32)
+    _check(load().pd_cnn_get_params(h, p.ctypes.data_as(ctypes.c_void_p), g.ctypes.data_as(ctypes.c_void_p),
+                                    CNN_PARAMS), h)
+    return p, g
+
+
+def pd_cnn_forward(h, level, hmap, h_pitch: int, logits, stream=None) -> None:
+    _check(load().pd_cnn_forward(h, _stream(stream), _ptr(level), level.shape[1], level.shape[0], level.stride(0),
+                                 _ptr(hmap), h_pitch, _ptr(logits)), h)
+
+
+def pd_cnn_train_step(h, pos_weight: float, label_threshold: float, lr: float, stream=None) -> None:
+    _check(load().pd_cnn_train_step(h, _stream(stream), float(pos_weight), float(label_threshold), float(lr)), h)
+
+
+def pd_cnn_train_loss(h, stream=None) -> float:
+    v = ctypes.c_float(0)
+    _check(load().pd_cnn_train_loss(h, _stream(stream), ctypes.byref(v)), h)
+    return float(v.value)
 
 
 # ----------------------------------------------------------------------------- convenience

@@ -42,6 +42,7 @@ struct Plan {
     std::vector<ResizeItem> r_items;
     std::vector<CellItem> c_items;
     std::vector<SvmItem> s_items;
+    std::vector<CnnItem> cnn_items;
     std::vector<int32_t> tabs;
     int64_t pyr_bytes = 0;
     int64_t score_floats = 0;
@@ -57,6 +58,7 @@ struct Plan {
         r_items.clear();
         c_items.clear();
         s_items.clear();
+        cnn_items.clear();
         tabs.clear();
         pyr_bytes = score_floats = 0;
         atlas_rows = max_wc = 0;
@@ -65,7 +67,7 @@ struct Plan {
 
 // Byte offsets of the plan's sections inside the packed descriptor block.
 struct Packed {
-    int64_t frames, levels, r_items, c_items, s_items, tabs, total;
+    int64_t frames, levels, r_items, c_items, s_items, cnn_items, tabs, total;
 };
 
 Packed pack_layout(const Plan &p) {
@@ -81,6 +83,7 @@ Packed pack_layout(const Plan &p) {
     o.r_items = take((int64_t)p.r_items.size() * sizeof(ResizeItem));
     o.c_items = take((int64_t)p.c_items.size() * sizeof(CellItem));
     o.s_items = take((int64_t)p.s_items.size() * sizeof(SvmItem));
+    o.cnn_items = take((int64_t)p.cnn_items.size() * sizeof(CnnItem));
     o.tabs = take((int64_t)p.tabs.size() * sizeof(int32_t));
     o.total = off;
     return o;
@@ -203,6 +206,21 @@ struct pd_handle {
     cudaEvent_t desc_done = nullptr;
     cudaEvent_t stage_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     bool timed = false;
+    // learned proposal: parameters (fp32 master + Adam state + rounded copy),
+    // inference fragments, per-cell head values, window logits
+    float *cnn = nullptr;           // [5][kCnnParams]: master, m, v, grad, rounded
+    float *in_tab = nullptr;        // [256]
+    uint32_t *w2frag = nullptr;     // [2304]
+    uint32_t *w3frag = nullptr;     // [4608]
+    float *hmap = nullptr;          // one f32 plane over the cell atlas
+    float *logits = nullptr;        // window logits, score-map layout
+    bool cnn_loaded = false, frag_stale = false;
+    int adam_t = 0;
+    // training workspace (allocated on first use, grown with the batch)
+    unsigned char *train_ws = nullptr;
+    size_t train_ws_bytes = 0;
+    int train_levels = 0;
+    float *train_loss_ptr = nullptr;
     // tensor maps over the atlases, one pair per K4 tile shape
     CUtensorMap hog_map[kSvmShapes]{}, lbp_map[kSvmShapes]{};
     float tile_cost[kSvmShapes] = {kDefaultTileCost[0], kDefaultTileCost[1], kDefaultTileCost[2],
@@ -354,6 +372,7 @@ int upload_plan(pd_handle *h, cudaStream_t s, const Plan &p, Packed &o) {
     put(o.r_items, p.r_items.data(), p.r_items.size() * sizeof(ResizeItem));
     put(o.c_items, p.c_items.data(), p.c_items.size() * sizeof(CellItem));
     put(o.s_items, p.s_items.data(), p.s_items.size() * sizeof(SvmItem));
+    put(o.cnn_items, p.cnn_items.data(), p.cnn_items.size() * sizeof(CnnItem));
     put(o.tabs, p.tabs.data(), p.tabs.size() * sizeof(int32_t));
     if (o.total) PD_CUDA(h, cudaMemcpyAsync(h->d_desc, h->h_desc, o.total, cudaMemcpyHostToDevice, s));
     PD_CUDA(h, cudaEventRecord(h->desc_done, s));
@@ -374,6 +393,33 @@ int encode_svm_maps(CUtensorMap *hog_maps, CUtensorMap *lbp_maps, const float *h
             return PD_ECUDA;
     }
     return PD_OK;
+}
+
+// Round to the nearest bfloat16 (ties to even): 8 significant bits of the
+// exact value, as a float.
+float bf16_round_host(double a) {
+    if (a == 0.0 || !std::isfinite(a)) return (float)a;
+    int e = 0;
+    const double m = std::frexp(a, &e);      // a = m 2^e, 0.5 <= |m| < 1
+    return (float)std::ldexp(std::nearbyint(m * 256.0) / 256.0, e);
+}
+
+uint32_t bf16_bits(float f) {  // f is already a bf16 value: its top 16 bits
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return u >> 16;
+}
+
+// mma.sync m16n8k16 B fragments (B = K x N): lane (g = lane/4, t = lane%4)
+// holds B[2t][g], B[2t+1][g] in register 0 and B[2t+8][g], B[2t+9][g] in
+// register 1 (first element in the low half).
+void pack_frag(const float *W, int cin, int ci0, int tap, int nt, uint32_t *out /* [32][2] */) {
+    for (int lane = 0; lane < 32; ++lane) {
+        const int g = lane >> 2, t = lane & 3, co = nt * 8 + g;
+        auto w = [&](int ci) { return bf16_bits(bf16_round_host(W[((size_t)co * cin + ci) * 9 + tap])); };
+        out[2 * lane] = w(ci0 + 2 * t) | (w(ci0 + 2 * t + 1) << 16);
+        out[2 * lane + 1] = w(ci0 + 2 * t + 8) | (w(ci0 + 2 * t + 9) << 16);
+    }
 }
 
 void invalidate_cache(pd_handle *h) {
@@ -429,6 +475,7 @@ void pd_destroy(pd_handle *h) {
     if (h->h_counts) cudaFreeHost(h->h_counts);
     if (h->desc_done) cudaEventDestroy(h->desc_done);
     if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->train_ws) cudaFree(h->train_ws);
     if (h->graph_done) cudaEventDestroy(h->graph_done);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (auto &e : h->stage_ev)
@@ -448,7 +495,8 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
         return code;
     };
     if (cudaGetDevice(&h->device) != cudaSuccess) return bail(PD_ECUDA);
-    if (init_cells() != cudaSuccess || init_svm() != cudaSuccess || init_nms() != cudaSuccess)
+    if (init_cells() != cudaSuccess || init_svm() != cudaSuccess || init_nms() != cudaSuccess ||
+        init_cnn() != cudaSuccess)
         return bail(PD_ECUDA);
 
     // Worst-case plan: max_frames frames of max_width x max_height.
@@ -512,6 +560,9 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
         {(int64_t)params->max_frames * 2 * 4 + 16, 0},             // 8 counts + error word
         {h->frames_cap, 0},                                        // 9 host-input frames
         {(int64_t)params->max_frames * params->max_candidates_per_frame * 16, 0},  // 10 NMS scratch
+        {(int64_t)5 * kCnnParams * 4 + 1024 + 2304 * 4 + 4608 * 4, 0},             // 11 CNN parameters
+        {(int64_t)rows * P * 4, 0},                                                 // 12 head values
+        {h->score_cap * 4, 0},                                                      // 13 window logits
     };
     int64_t total = 0;
     for (auto &pt : parts) {
@@ -533,6 +584,12 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
     h->d_err = reinterpret_cast<unsigned *>(h->d_counts + 2 * params->max_frames);
     h->d_frames = h->arena + parts[9].off;
     h->d_nms_scratch = reinterpret_cast<float4 *>(h->arena + parts[10].off);
+    h->cnn = reinterpret_cast<float *>(h->arena + parts[11].off);
+    h->in_tab = h->cnn + 5 * kCnnParams;
+    h->w2frag = reinterpret_cast<uint32_t *>(h->in_tab + 256);
+    h->w3frag = h->w2frag + 2304;
+    h->hmap = reinterpret_cast<float *>(h->arena + parts[12].off);
+    h->logits = reinterpret_cast<float *>(h->arena + parts[13].off);
 
     if (cudaMallocHost(&h->h_desc, h->desc_cap) != cudaSuccess) return bail(PD_ENOMEM);
     // Results land in mapped pinned host memory: NMS writes the kept boxes and
@@ -563,6 +620,9 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
         for (int j = 0; j < kWinBW; ++j)
             for (int t = 0; t < kFeat; ++t)
                 wt[((size_t)t * kWinBH + i) * kWPad + j] = svm_w[((size_t)i * kWinBW + j) * kFeat + t];
+    float tab[256];
+    for (int v = 0; v < 256; ++v) tab[v] = bf16_round_host((double)v / 255.0 - 0.5);
+    if (cudaMemcpy(h->in_tab, tab, sizeof tab, cudaMemcpyHostToDevice) != cudaSuccess) return bail(PD_ECUDA);
     uint8_t map[256];
     build_lbp_bin_table(map);
     if (cudaMemcpy(h->d_w, wt.data(), wt.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -754,6 +814,198 @@ int pd_set_tile_costs(pd_handle *h, const float *cost) {
 int pd_get_tile_costs(const pd_handle *h, float *cost) {
     if (!h || !cost) return PD_EINVAL;
     for (int s = 0; s < kSvmShapes; ++s) cost[s] = h->tile_cost[s];
+    return PD_OK;
+}
+
+// ----------------------------------------------------------------------------- learned proposal
+namespace {
+
+CnnWeights cnn_weights(const pd_handle *h) {
+    const float *wr = h->cnn + 4 * kCnnParams;
+    CnnWeights w;
+    w.in_tab = h->in_tab;
+    w.w1 = wr + kOffW1;
+    w.b1 = wr + kOffB1;
+    w.w2frag = h->w2frag;
+    w.b2 = wr + kOffB2;
+    w.w3frag = h->w3frag;
+    w.b3 = wr + kOffB3;
+    w.wh = wr + kOffWh;
+    w.bh = wr + kOffBh;
+    w.v = wr + kOffV;
+    w.bv = wr + kOffBv;
+    return w;
+}
+
+// Inference fragments from the master weights (after set_params or training).
+int refresh_fragments(pd_handle *h) {
+    std::vector<float> p(kCnnParams);
+    PD_CUDA(h, cudaMemcpy(p.data(), h->cnn, kCnnParams * 4, cudaMemcpyDeviceToHost));
+    std::vector<uint32_t> f2(2304), f3(4608);
+    for (int tap = 0; tap < 9; ++tap)
+        for (int nt = 0; nt < 4; ++nt) pack_frag(p.data() + kOffW2, 16, 0, tap, nt, &f2[(tap * 4 + nt) * 64]);
+    for (int tap = 0; tap < 9; ++tap)
+        for (int kh = 0; kh < 2; ++kh)
+            for (int nt = 0; nt < 4; ++nt)
+                pack_frag(p.data() + kOffW3, 32, 16 * kh, tap, nt, &f3[((tap * 2 + kh) * 4 + nt) * 64]);
+    PD_CUDA(h, cudaMemcpy(h->w2frag, f2.data(), f2.size() * 4, cudaMemcpyHostToDevice));
+    PD_CUDA(h, cudaMemcpy(h->w3frag, f3.data(), f3.size() * 4, cudaMemcpyHostToDevice));
+    h->frag_stale = false;
+    return PD_OK;
+}
+
+}  // namespace
+
+int pd_cnn_set_params(pd_handle *h, const float *params, int n) {
+    if (!h || !params || n != kCnnParams) return h ? fail(h, PD_EINVAL, "expected %d parameters", kCnnParams) : PD_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(params[i])) return fail(h, PD_EINVAL, "parameter %d is not finite", i);
+    PD_CUDA(h, cudaDeviceSynchronize());
+    PD_CUDA(h, cudaMemcpy(h->cnn, params, kCnnParams * 4, cudaMemcpyHostToDevice));
+    PD_CUDA(h, cudaMemset(h->cnn + kCnnParams, 0, 3 * kCnnParams * 4));  // Adam m, v and grad
+    PD_CUDA(h, launch_round_params(0, h->cnn, h->cnn + 4 * kCnnParams));
+    PD_CUDA(h, cudaDeviceSynchronize());
+    h->adam_t = 0;
+    h->cnn_loaded = true;
+    return refresh_fragments(h);
+}
+
+int pd_cnn_get_params(pd_handle *h, float *params, float *grad, int n) {
+    if (!h || n != kCnnParams) return PD_EINVAL;
+    PD_CUDA(h, cudaDeviceSynchronize());
+    if (params) PD_CUDA(h, cudaMemcpy(params, h->cnn, kCnnParams * 4, cudaMemcpyDeviceToHost));
+    if (grad) PD_CUDA(h, cudaMemcpy(grad, h->cnn + 3 * kCnnParams, kCnnParams * 4, cudaMemcpyDeviceToHost));
+    return PD_OK;
+}
+
+int pd_cnn_forward(pd_handle *h, void *stream, const uint8_t *d_level, int Wk, int Hk, int pitch, float *d_h,
+                   int h_pitch, float *d_logits) {
+    if (!h) return PD_EINVAL;
+    invalidate_cache(h);  // the descriptor region is reused below
+    const int Wc = Wk / 8, Hc = Hk / 8;
+    if (!d_level || !d_h || !d_logits || Wk < 1 || Hk < 1 || pitch < Wk || h_pitch < Wc)
+        return fail(h, PD_EINVAL, "pd_cnn_forward: bad argument");
+    if (!h->cnn_loaded) return fail(h, PD_ESTATE, "no proposal parameters (pd_cnn_set_params)");
+    if (h->frag_stale) {
+        int r = refresh_fragments(h);
+        if (r != PD_OK) return r;
+    }
+    Plan p;
+    plan_level(p, 0, 0, Wk, Hk, Wk, Hk, 0, pitch);
+    p.c_items.clear();
+    p.s_items.clear();
+    p.tabs.clear();
+    for (int cy = 0; cy < Hc; cy += kCnnTile)
+        for (int cx = 0; cx < Wc; cx += kCnnTile) p.cnn_items.push_back({0, cy, cx, 0});
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Packed o;
+    int r = upload_plan(h, s, p, o);
+    if (r != PD_OK) return r;
+    PD_CUDA(h, launch_cnn(s, dptr<LevelDesc>(h, o.levels), p.levels[0].rows > 0 ? 1 : 0, d_level,
+                          dptr<CnnItem>(h, o.cnn_items), (int)p.cnn_items.size(), cnn_weights(h), d_h, h_pitch,
+                          d_logits));
+    return PD_OK;
+}
+
+int pd_cnn_train_step(pd_handle *h, void *stream, float pos_weight, float label_threshold, float lr) {
+    if (!h) return PD_EINVAL;
+    if (!h->detected || !h->cache_valid) return fail(h, PD_ESTATE, "pd_cnn_train_step needs a pd_detect batch");
+    if (!h->cnn_loaded) return fail(h, PD_ESTATE, "no proposal parameters (pd_cnn_set_params)");
+    if (!(pos_weight > 0.f) || !(lr >= 0.f)) return fail(h, PD_EINVAL, "bad pos_weight / lr");
+    const Plan &p = h->plan;
+    const int nl = (int)p.levels.size();
+    std::vector<TrainLevel> tl(nl);
+    int64_t n16 = 0, n32 = 0, nwin = 0;
+    for (int k = 0; k < nl; ++k) {
+        const LevelDesc &L = p.levels[k];
+        TrainLevel &T = tl[k];
+        T.level = k;
+        T.H1 = (L.Hk + 1) / 2; T.W1 = (L.Wk + 1) / 2;
+        T.H2 = (T.H1 + 1) / 2; T.W2 = (T.W1 + 1) / 2;
+        T.H3 = (T.H2 + 1) / 2; T.W3 = (T.W2 + 1) / 2;
+        T.pad = 0;
+        T.a1 = n16; n16 += (int64_t)16 * T.H1 * T.W1;
+        T.a2 = n16; n16 += (int64_t)32 * T.H2 * T.W2;
+        T.a3 = n32; n32 += (int64_t)32 * T.H3 * T.W3;
+        nwin += (int64_t)L.rows * L.cols;
+    }
+    if (nwin == 0) return fail(h, PD_EINVAL, "batch has no window");
+    // workspace: tl | act16 (bf16) | act32 | dz16 | dz32 | dh plane | dz | level losses
+    const int64_t rows = h->atlas.rows, P = h->atlas.pitch;
+    const size_t need = round_up((int64_t)nl * sizeof(TrainLevel), 256) + round_up(n16 * 2, 256) +
+                        round_up(n32 * 4, 256) + round_up(n16 * 4, 256) + round_up(n32 * 4, 256) +
+                        round_up(rows * P * 4, 256) + round_up(h->score_cap * 4, 256) + round_up((int64_t)nl * 4, 256);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (need > h->train_ws_bytes) {
+        PD_CUDA(h, cudaStreamSynchronize(s));
+        if (h->train_ws) cudaFree(h->train_ws);
+        h->train_ws = nullptr;
+        h->train_ws_bytes = 0;
+        if (cudaMalloc(&h->train_ws, need) != cudaSuccess) return fail(h, PD_ENOMEM, "training workspace");
+        h->train_ws_bytes = need;
+    }
+    unsigned char *w = h->train_ws;
+    auto take = [&](int64_t bytes) {
+        unsigned char *at = w;
+        w += round_up(bytes, 256);
+        return at;
+    };
+    TrainArgs a{};
+    a.tl = reinterpret_cast<TrainLevel *>(take((int64_t)nl * sizeof(TrainLevel)));
+    a.act16 = reinterpret_cast<__nv_bfloat16 *>(take(n16 * 2));
+    a.act32 = reinterpret_cast<float *>(take(n32 * 4));
+    a.dz16 = reinterpret_cast<float *>(take(n16 * 4));
+    a.dz32 = reinterpret_cast<float *>(take(n32 * 4));
+    a.dh = reinterpret_cast<float *>(take(rows * P * 4));
+    a.dz = reinterpret_cast<float *>(take(h->score_cap * 4));
+    a.level_loss = reinterpret_cast<float *>(take((int64_t)nl * 4));
+    PD_CUDA(h, cudaMemcpyAsync((void *)a.tl, tl.data(), tl.size() * sizeof(TrainLevel), cudaMemcpyHostToDevice, s));
+    PD_CUDA(h, cudaStreamSynchronize(s));  // the host vector goes out of scope
+    a.n_levels = nl;
+    a.levels = dptr<LevelDesc>(h, h->packed.levels);
+    a.pyr = h->d_pyr;
+    a.w = cnn_weights(h);
+    a.master = h->cnn;
+    a.m = h->cnn + kCnnParams;
+    a.v = h->cnn + 2 * kCnnParams;
+    a.grad = h->cnn + 3 * kCnnParams;
+    a.wr = h->cnn + 4 * kCnnParams;
+    a.hmap = h->hmap;
+    a.hp = (int32_t)P;
+    a.logits = h->logits;
+    a.scores = h->d_scores;
+    a.label_thr = label_threshold;
+    a.pos_weight = pos_weight;
+    a.inv_n = 1.0f / (float)nwin;
+    a.lr = lr;
+    a.beta1 = 0.9f;
+    a.beta2 = 0.999f;
+    a.eps = 1e-8f;
+    if (lr > 0.f) {
+        ++h->adam_t;
+        a.c1 = 1.0f - (float)std::pow(0.9, h->adam_t);
+        a.c2 = 1.0f - (float)std::pow(0.999, h->adam_t);
+        h->frag_stale = true;
+    }
+    h->train_levels = nl;
+    h->train_loss_ptr = a.level_loss;
+    PD_CUDA(h, launch_train_step(s, a));
+    return PD_OK;
+}
+
+int pd_cnn_train_loss(pd_handle *h, void *stream, float *loss) {
+    if (!h || !loss) return PD_EINVAL;
+    if (!h->train_ws || h->train_levels <= 0) return fail(h, PD_ESTATE, "no training step yet");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    PD_CUDA(h, cudaStreamSynchronize(s));
+    // level losses sit after the fixed sections of the workspace: recompute the offset
+    std::vector<float> ll(h->train_levels);
+    const unsigned char *end = h->train_ws + h->train_ws_bytes;
+    (void)end;
+    PD_CUDA(h, cudaMemcpy(ll.data(), h->train_loss_ptr, ll.size() * 4, cudaMemcpyDeviceToHost));
+    double sum = 0;
+    for (float v : ll) sum += v;
+    *loss = (float)sum;
     return PD_OK;
 }
 

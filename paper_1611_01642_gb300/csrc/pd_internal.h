@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -95,6 +96,59 @@ cudaError_t launch_nms(cudaStream_t s, const FrameDesc *d_frames, const LevelDes
                        int n_frames, const float *scores, float threshold, float iou,
                        float4 *scratch, int max_cand, pd_box *boxes, int max_boxes,
                        int32_t *counts);
+
+// ---- learned window proposal
+constexpr int kCnnParams = 14210;  // flat order: w1 b1 w2 b2 w3 b3 wh bh v bv
+constexpr int kOffW1 = 0, kOffB1 = 144, kOffW2 = 160, kOffB2 = 4768, kOffW3 = 4800, kOffB3 = 14016;
+constexpr int kOffWh = 14048, kOffBh = 14080, kOffV = 14081, kOffBv = 14209;
+constexpr int kCnnTile = 8;        // cells per side of an inference tile
+
+struct CnnItem { int32_t level, cy0, cx0, pad; };
+
+// Device pointers of the inference weights.
+struct CnnWeights {
+    const float *in_tab;      // [256] bf16(L/255 - 0.5) as float
+    const float *w1, *b1;     // [16][9] (bf16-rounded), [16]
+    const uint32_t *w2frag;   // layer-2 mma B fragments [9 taps][4 n-tiles][32 lanes][2]
+    const float *b2;          // [32]
+    const uint32_t *w3frag;   // layer-3 mma B fragments [9][2 k-halves][4][32][2]
+    const float *b3, *wh;     // [32], [32]
+    const float *bh;          // [1]
+    const float *v, *bv;      // [16][8], [1]
+};
+
+struct TrainLevel {
+    int32_t level;            // index in the LevelDesc table
+    int32_t H1, W1, H2, W2, H3, W3;
+    int32_t pad;
+    int64_t a1, a2, a3;       // element offsets: a1, a2 in the bf16 buffer, a3 in the f32 buffer
+};
+
+struct TrainArgs {
+    const TrainLevel *tl;
+    int n_levels;
+    const LevelDesc *levels;
+    const uint8_t *pyr;
+    CnnWeights w;             // in_tab used; other fields refreshed from wr
+    float *wr;                // rounded working copy [kCnnParams]
+    float *master, *m, *v, *grad;
+    __nv_bfloat16 *act16;
+    float *act32, *dz16, *dz32;
+    float *hmap, *dh;
+    int32_t hp;
+    float *logits;
+    const float *scores;
+    float *dz, *level_loss;
+    float label_thr, pos_weight, inv_n;
+    float lr, beta1, beta2, eps, c1, c2;
+};
+
+cudaError_t init_cnn();
+cudaError_t launch_cnn(cudaStream_t s, const LevelDesc *d_levels, int n_levels, const uint8_t *pyr,
+                       const CnnItem *d_items, int n_items, const CnnWeights &w, float *hmap,
+                       int32_t hmap_pitch, float *logits);
+cudaError_t launch_train_step(cudaStream_t s, const TrainArgs &a);
+cudaError_t launch_round_params(cudaStream_t s, const float *master, float *wr);
 
 // Encodes a 3-D tiled tensor map over plane-major cell planes.
 int encode_plane_map(CUtensorMap *map, void *base, CUtensorMapDataType dtype, int elem_bytes,
