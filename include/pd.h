@@ -74,6 +74,8 @@ typedef struct pd_params {
     int32_t max_width;       /* largest frame width  (arena sizing) */
     int32_t max_height;      /* largest frame height (arena sizing) */
     int32_t flags;           /* PD_FLAG_* bits, 0 by default */
+    int32_t use_proposal;    /* 1: sparse path gated by the learned proposal (needs pd_cnn_set_params) */
+    float keep_logit_threshold; /* a window is kept iff its keep-logit > this */
 } pd_params;
 
 /* One detection: a window in frame coordinates. */
@@ -281,6 +283,20 @@ int pd_cnn_train_step(pd_handle *h, void *stream, float pos_weight, float label_
 
 /* Loss of the last training step (synchronises the stream). */
 int pd_cnn_train_loss(pd_handle *h, void *stream, float *loss);
+
+/* Sparse path on (enable = 1) or off. When on, pd_detect also runs the
+ * proposal network on every level after the pyramid; a window tile of the
+ * score kernel is computed iff it holds a window whose keep-logit exceeds
+ * keep_logit_threshold (all its windows are then scored exactly), and the
+ * cell tiles are computed iff such a tile needs them; the windows of the
+ * other tiles get score -inf. With the threshold at -inf every tile is kept
+ * and the scores equal the plain path's bit for bit. Needs parameters
+ * (pd_cnn_set_params) to enable. Affects the next pd_detect. */
+int pd_set_proposal(pd_handle *h, int enable, float keep_logit_threshold);
+
+/* Device pointer to the window keep-logits of the last pd_detect with the
+ * proposal on (same layout and offsets as pd_scores; *total = 0 when off). */
+int pd_logits(const pd_handle *h, const float **d_logits, int64_t *total);
 
 /* Allocation-free NMS. The paper has no counterpart: this exists for
  * callers that must not allocate device memory at run time -- a real-time

@@ -36,7 +36,7 @@ EXPORTED = ["pd_params_default", "pd_pyramid", "pd_create", "pd_destroy", "pd_la
             "pd_detect", "pd_detect_host", "pd_sync", "pd_frame_candidates", "pd_frame_levels", "pd_scores", "pd_boxes",
             "pd_last_launch_count", "pd_stage_times", "pd_set_tile_costs", "pd_get_tile_costs", "pd_resize_levels", "pd_cell_features", "pd_window_scores",
             "pd_nms_maps", "pd_nms_noalloc", "pd_cnn_set_params", "pd_cnn_get_params", "pd_cnn_forward",
-            "pd_cnn_train_step", "pd_cnn_train_loss"]
+            "pd_cnn_train_step", "pd_cnn_train_loss", "pd_set_proposal", "pd_logits"]
 
 
 class pd_params(ctypes.Structure):
@@ -45,7 +45,8 @@ class pd_params(ctypes.Structure):
                 ("nms_iou", ctypes.c_float), ("max_boxes_per_frame", ctypes.c_int32),
                 ("max_candidates_per_frame", ctypes.c_int32), ("max_frames", ctypes.c_int32),
                 ("max_width", ctypes.c_int32), ("max_height", ctypes.c_int32),
-                ("flags", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("use_proposal", ctypes.c_int32),
+                ("keep_logit_threshold", ctypes.c_float)]
 
 
 class pd_box(ctypes.Structure):
@@ -114,6 +115,8 @@ def load(path: str | None = None):
         "pd_cnn_forward": ([P, P, P, i, i, i, P, i, P], i),
         "pd_cnn_train_step": ([P, P, f, f, f], i),
         "pd_cnn_train_loss": ([P, P, P], i),
+        "pd_set_proposal": ([P, i, f], i),
+        "pd_logits": ([P, P, P], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -352,6 +355,17 @@ def pd_cnn_train_loss(h, stream=None) -> float:
     return float(v.value)
 
 
+def pd_set_proposal(h, enable: bool, keep_logit_threshold: float) -> None:
+    _check(load().pd_set_proposal(h, 1 if enable else 0, float(keep_logit_threshold)), h)
+
+
+def pd_logits(h):
+    p = ctypes.c_void_p()
+    total = ctypes.c_int64()
+    _check(load().pd_logits(h, ctypes.byref(p), ctypes.byref(total)), h)
+    return p.value or 0, total.value
+
+
 # ----------------------------------------------------------------------------- convenience
 class Detector:
     """Owns a pd_handle: ``Detector(w, b, max_frames=..., max_width=..., ...)``."""
@@ -374,6 +388,10 @@ class Detector:
     def detect(self, frames, stream=None):
         pd_detect(self.h, frames, stream)
 
+    def set_proposal(self, enable: bool, keep_logit_threshold: float = 0.0):
+        """Sparse path on/off (needs proposal parameters set with pd_cnn_set_params)."""
+        pd_set_proposal(self.h, enable, keep_logit_threshold)
+
     def detect_host(self, frames, stream=None):
         pd_detect_host(self.h, frames, stream)
 
@@ -386,10 +404,16 @@ class Detector:
     def boxes(self, frame: int) -> np.ndarray:
         return pd_boxes(self.h, frame, self.params.max_boxes_per_frame)
 
+    def logit_maps(self, frame: int):
+        """Keep-logit maps of the last detect with the proposal on (views, like score_maps)."""
+        return self._maps(frame, *pd_logits(self.h))
+
     def score_maps(self, frame: int):
         """List of float32 CUDA tensors (views into the handle's score buffer)."""
+        return self._maps(frame, *pd_scores(self.h))
+
+    def _maps(self, frame: int, ptr: int, total: int):
         import torch
-        ptr, total = pd_scores(self.h)
         if total == 0:
             return [torch.zeros((lv["rows"], lv["cols"]), dtype=torch.float32, device="cuda")
                     for lv in self.levels(frame)]

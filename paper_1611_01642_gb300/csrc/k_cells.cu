@@ -99,9 +99,11 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
                                                     const uint8_t *__restrict__ pyr,
                                                     CellAtlas atlas,
                                                     const CellItem *__restrict__ items,
-                                                    const uint8_t *__restrict__ lbp_map) {
+                                                    const uint8_t *__restrict__ lbp_map,
+                                                    const uint32_t *__restrict__ c_flag) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CellSmem &S = *reinterpret_cast<CellSmem *>(smem_raw);
+    if (c_flag && !c_flag[blockIdx.x]) return;  // sparse path: no kept window needs these cells
     const CellItem it = items[blockIdx.x];
     const LevelDesc L = levels[it.level];
     const int tid = threadIdx.x;
@@ -278,10 +280,10 @@ cudaError_t init_cells() {
 
 cudaError_t launch_cells(cudaStream_t s, const LevelDesc *d_levels, const uint8_t *pyr,
                          CellAtlas atlas, const CellItem *d_items, int n_items,
-                         const uint8_t *d_lbp_map) {
+                         const uint8_t *d_lbp_map, const uint32_t *c_flag) {
     if (n_items <= 0) return cudaSuccess;
     const int smem = (int)sizeof(CellSmem);
-    k_cells<<<n_items, kThreads, smem, s>>>(d_levels, pyr, atlas, d_items, d_lbp_map);
+    k_cells<<<n_items, kThreads, smem, s>>>(d_levels, pyr, atlas, d_items, d_lbp_map, c_flag);
     return cudaGetLastError();
 }
 

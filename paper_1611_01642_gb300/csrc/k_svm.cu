@@ -346,12 +346,25 @@ __device__ void svm_tile(const SvmItem &it, const LevelDesc &L, const CUtensorMa
 __global__ void __launch_bounds__(kThreads, 1)
     k_svm(const __grid_constant__ SvmMaps maps, const LevelDesc *__restrict__ levels,
           const float *__restrict__ wt, float bias, float clip, float *__restrict__ scores,
-          const SvmItem *__restrict__ items, unsigned *__restrict__ err) {
+          const SvmItem *__restrict__ items, unsigned *__restrict__ err,
+          const uint32_t *__restrict__ s_flag) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     const SvmItem it = items[blockIdx.x];
     const LevelDesc L = levels[it.level];
+    if (s_flag && !s_flag[blockIdx.x]) {
+        // sparse path: no kept window in this tile; its windows are not scored
+        const SvmShapeInfo sh = it.shape == 0 ? SvmShapeInfo{S0::TW, S0::TH, 0, 0, 0}
+                               : it.shape == 1 ? SvmShapeInfo{S1::TW, S1::TH, 0, 0, 0}
+                               : it.shape == 2 ? SvmShapeInfo{S2::TW, S2::TH, 0, 0, 0}
+                                               : SvmShapeInfo{S3::TW, S3::TH, 0, 0, 0};
+        for (int i = threadIdx.x; i < sh.tw * sh.th; i += kThreads) {
+            const int wy = it.wy0 + i / sh.tw, wx = it.wx0 + i % sh.tw;
+            if (wy < L.rows && wx < L.cols) scores[L.score_off + (int64_t)wy * L.cols + wx] = -INFINITY;
+        }
+        return;
+    }
     switch (it.shape) {
         case 0: svm_tile<S0, 4>(it, L, &maps.hog[0], &maps.lbp[0], wt, bias, clip, scores, err, smem); break;
         case 1: svm_tile<S1, 4>(it, L, &maps.hog[1], &maps.lbp[1], wt, bias, clip, scores, err, smem); break;
@@ -381,14 +394,15 @@ cudaError_t init_svm() {
 
 cudaError_t launch_svm(cudaStream_t s, const CUtensorMap *hog_maps, const CUtensorMap *lbp_maps,
                        const LevelDesc *d_levels, const float *d_w, float bias, float clip,
-                       float *scores, const SvmItem *d_items, int n_items, unsigned *d_err) {
+                       float *scores, const SvmItem *d_items, int n_items, unsigned *d_err,
+                       const uint32_t *s_flag) {
     if (n_items <= 0) return cudaSuccess;
     SvmMaps m;
     for (int i = 0; i < kSvmShapes; ++i) {
         m.hog[i] = hog_maps[i];
         m.lbp[i] = lbp_maps[i];
     }
-    k_svm<<<n_items, kThreads, kSmemMax, s>>>(m, d_levels, d_w, bias, clip, scores, d_items, d_err);
+    k_svm<<<n_items, kThreads, kSmemMax, s>>>(m, d_levels, d_w, bias, clip, scores, d_items, d_err, s_flag);
     return cudaGetLastError();
 }
 

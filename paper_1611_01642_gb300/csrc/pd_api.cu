@@ -215,6 +215,12 @@ struct pd_handle {
     float *hmap = nullptr;          // one f32 plane over the cell atlas
     float *logits = nullptr;        // window logits, score-map layout
     bool cnn_loaded = false, frag_stale = false;
+    bool proposal = false;          // sparse path on
+    bool ran_proposal = false;      // the last pd_detect ran the sparse path
+    float tau = 0.f;                // keep-logit threshold
+    uint32_t *s_flag = nullptr;     // per K4 item: holds a kept window
+    uint32_t *c_flag = nullptr;     // per K2+K3 item: needed by a kept tile
+    int64_t flag_cap = 0;
     int adam_t = 0;
     // training workspace (allocated on first use, grown with the batch)
     unsigned char *train_ws = nullptr;
@@ -306,6 +312,8 @@ void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int
         for (int y = 0; y < Hk; ++y) p.tabs.push_back(q11_entry(y, H, Hk));
     }
     const int li = (int)p.levels.size();
+    L.citem0 = (int32_t)p.c_items.size();
+    L.ctx = (L.Wc + kCellTW - 1) / kCellTW;
     for (int cy = 0; cy < L.Hc; cy += kCellTH)
         for (int cx = 0; cx < L.Wc; cx += kCellTW) p.c_items.push_back({li, cx, cy, 0});
     if (L.rows > 0) {
@@ -322,7 +330,7 @@ void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int
 
 // Plans one frame with the pyramid rule; returns PD_OK or an error.
 int plan_frame(Plan &p, const pd_params &prm, const uint8_t *ptr, int W, int H, int pitch,
-               const float *tile_cost = kDefaultTileCost) {
+               const float *tile_cost = kDefaultTileCost, bool proposal = false) {
     int32_t Wk[PD_MAX_LEVELS], Hk[PD_MAX_LEVELS];
     int n = level_sizes(W, H, prm.pyr_factor, PD_MAX_LEVELS, Wk, Hk);
     if (n < 0) return n;
@@ -343,6 +351,13 @@ int plan_frame(Plan &p, const pd_params &prm, const uint8_t *ptr, int W, int H, 
         plan_level(p, f, k, W, H, Wk[k], Hk[k], p.pyr_bytes, lp, first_shared >= 0 ? &share : nullptr,
                    tile_cost);
         p.pyr_bytes += (int64_t)lp * Hk[k];
+        if (proposal) {
+            const LevelDesc &L = p.levels.back();
+            const int li = (int)p.levels.size() - 1;
+            if (L.rows > 0)
+                for (int cy = 0; cy < L.Hc; cy += kCnnTile)
+                    for (int cx = 0; cx < L.Wc; cx += kCnnTile) p.cnn_items.push_back({li, cy, cx, 0});
+        }
     }
     if (n > 0)
         for (int y = 0; y < H; y += kResizeTH)
@@ -353,6 +368,7 @@ int plan_frame(Plan &p, const pd_params &prm, const uint8_t *ptr, int W, int H, 
 
 bool params_ok(const pd_params *p) {
     return p && p->struct_size == sizeof(pd_params) && p->pyr_factor > 1.0f && p->l2hys_clip > 0.f &&
+           !std::isnan(p->keep_logit_threshold) &&
            p->nms_iou >= 0.f && p->max_boxes_per_frame > 0 && p->max_boxes_per_frame <= 16384 &&
            p->max_candidates_per_frame > 0 &&
            p->max_candidates_per_frame <= 16384 && p->max_frames > 0 && p->max_width > 0 &&
@@ -434,6 +450,47 @@ void invalidate_cache(pd_handle *h) {
 template <class T>
 const T *dptr(pd_handle *h, int64_t off) {
     return reinterpret_cast<const T *>(h->d_desc + off);
+}
+
+}  // namespace
+
+namespace {
+
+CnnWeights cnn_weights(const pd_handle *h) {
+    const float *wr = h->cnn + 4 * kCnnParams;
+    CnnWeights w;
+    w.in_tab = h->in_tab;
+    w.w1 = wr + kOffW1;
+    w.b1 = wr + kOffB1;
+    w.w2frag = h->w2frag;
+    w.b2 = wr + kOffB2;
+    w.w3frag = h->w3frag;
+    w.b3 = wr + kOffB3;
+    w.wh = wr + kOffWh;
+    w.bh = wr + kOffBh;
+    w.v = wr + kOffV;
+    w.bv = wr + kOffBv;
+    return w;
+}
+
+// Inference fragments from the master weights (after set_params or training).
+// Waits for the device first: training steps may still be writing the
+// master weights on a stream that the copy below does not order after.
+int refresh_fragments(pd_handle *h) {
+    PD_CUDA(h, cudaDeviceSynchronize());
+    std::vector<float> p(kCnnParams);
+    PD_CUDA(h, cudaMemcpy(p.data(), h->cnn, kCnnParams * 4, cudaMemcpyDeviceToHost));
+    std::vector<uint32_t> f2(2304), f3(4608);
+    for (int tap = 0; tap < 9; ++tap)
+        for (int nt = 0; nt < 4; ++nt) pack_frag(p.data() + kOffW2, 16, 0, tap, nt, &f2[(tap * 4 + nt) * 64]);
+    for (int tap = 0; tap < 9; ++tap)
+        for (int kh = 0; kh < 2; ++kh)
+            for (int nt = 0; nt < 4; ++nt)
+                pack_frag(p.data() + kOffW3, 32, 16 * kh, tap, nt, &f3[((tap * 2 + kh) * 4 + nt) * 64]);
+    PD_CUDA(h, cudaMemcpy(h->w2frag, f2.data(), f2.size() * 4, cudaMemcpyHostToDevice));
+    PD_CUDA(h, cudaMemcpy(h->w3frag, f3.data(), f3.size() * 4, cudaMemcpyHostToDevice));
+    h->frag_stale = false;
+    return PD_OK;
 }
 
 }  // namespace
@@ -526,7 +583,12 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
             s_bound += most;
         }
         const int64_t F = params->max_frames;
-        h->desc_cap = round_up(F * (int64_t)sizeof(FrameDesc), 16) +
+        int64_t cnn_bound = 0;
+        for (const LevelDesc &L : one.levels)
+            cnn_bound += (int64_t)((L.Hc + kCnnTile - 1) / kCnnTile) * ((L.Wc + kCnnTile - 1) / kCnnTile);
+        h->flag_cap = F * std::max<int64_t>(s_bound, (int64_t)one.c_items.size()) + 64;
+        h->desc_cap = round_up(F * cnn_bound * (int64_t)sizeof(CnnItem), 16) +
+                      round_up(F * (int64_t)sizeof(FrameDesc), 16) +
                       round_up(F * (int64_t)one.levels.size() * (int64_t)sizeof(LevelDesc), 16) +
                       round_up(F * (int64_t)one.r_items.size() * (int64_t)sizeof(ResizeItem), 16) +
                       round_up(F * (int64_t)one.c_items.size() * (int64_t)sizeof(CellItem), 16) +
@@ -563,6 +625,7 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
         {(int64_t)5 * kCnnParams * 4 + 1024 + 2304 * 4 + 4608 * 4, 0},             // 11 CNN parameters
         {(int64_t)rows * P * 4, 0},                                                 // 12 head values
         {h->score_cap * 4, 0},                                                      // 13 window logits
+        {2 * h->flag_cap * 4, 0},                                                   // 14 tile flags
     };
     int64_t total = 0;
     for (auto &pt : parts) {
@@ -590,6 +653,10 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
     h->w3frag = h->w2frag + 2304;
     h->hmap = reinterpret_cast<float *>(h->arena + parts[12].off);
     h->logits = reinterpret_cast<float *>(h->arena + parts[13].off);
+    h->s_flag = reinterpret_cast<uint32_t *>(h->arena + parts[14].off);
+    h->c_flag = h->s_flag + h->flag_cap;
+    h->proposal = params->use_proposal != 0;
+    h->tau = params->keep_logit_threshold;
 
     if (cudaMallocHost(&h->h_desc, h->desc_cap) != cudaSuccess) return bail(PD_ENOMEM);
     // Results land in mapped pinned host memory: NMS writes the kept boxes and
@@ -657,16 +724,23 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     h->stream = s;
+    if (h->proposal && !h->cnn_loaded) return fail(h, PD_ESTATE, "proposal on but no parameters loaded");
+    if (h->proposal && h->frag_stale) {
+        int rr = refresh_fragments(h);
+        if (rr != PD_OK) return rr;
+    }
     Plan &p = h->plan;
     const bool reuse = h->cache_valid && sig == h->sig;
     if (!reuse) {
         invalidate_cache(h);
         p.clear();
         for (int f = 0; f < n_frames; ++f) {
-            int r = plan_frame(p, h->p, d_frames[f], widths[f], heights[f], pitches[f], h->tile_cost);
+            int r = plan_frame(p, h->p, d_frames[f], widths[f], heights[f], pitches[f], h->tile_cost,
+                               h->proposal);
             if (r != PD_OK) return fail(h, r, "frame %d: planning failed", f);
         }
-        if (p.atlas_rows > h->atlas.rows || p.pyr_bytes > h->pyr_cap || p.score_floats > h->score_cap)
+        if (p.atlas_rows > h->atlas.rows || p.pyr_bytes > h->pyr_cap || p.score_floats > h->score_cap ||
+            (int64_t)p.s_items.size() > h->flag_cap || (int64_t)p.c_items.size() > h->flag_cap)
             return fail(h, PD_EINVAL, "batch exceeds the arena");
         // full descriptor upload, once per batch shape
         int r = upload_plan(h, s, p, h->packed);
@@ -697,12 +771,23 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
         if (timed) PD_CUDA(h, record(h->stage_ev[0], q));
         PD_CUDA(h, launch_resize(q, df, dl, dptr<int32_t>(h, o.tabs), h->d_pyr, dptr<ResizeItem>(h, o.r_items),
                                  (int)p.r_items.size()));
+        const uint32_t *cf = nullptr, *sf = nullptr;
+        if (h->proposal) {
+            // learned proposal: keep-logits of every window, then the tiles to score
+            PD_CUDA(h, launch_cnn(q, dl, (int)p.levels.size(), h->d_pyr, dptr<CnnItem>(h, o.cnn_items),
+                                  (int)p.cnn_items.size(), cnn_weights(h), h->hmap, h->atlas.pitch, h->logits));
+            PD_CUDA(h, cudaMemsetAsync(h->c_flag, 0, p.c_items.size() * 4 + 4, q));
+            PD_CUDA(h, launch_proposal_flags(q, dl, dptr<SvmItem>(h, o.s_items), (int)p.s_items.size(), h->logits,
+                                             h->tau, h->s_flag, h->c_flag));
+            cf = h->c_flag;
+            sf = h->s_flag;
+        }
         if (timed) PD_CUDA(h, record(h->stage_ev[1], q));
         PD_CUDA(h, launch_cells(q, dl, h->d_pyr, h->atlas, dptr<CellItem>(h, o.c_items), (int)p.c_items.size(),
-                                h->d_lbp_map));
+                                h->d_lbp_map, cf));
         if (timed) PD_CUDA(h, record(h->stage_ev[2], q));
         PD_CUDA(h, launch_svm(q, h->hog_map, h->lbp_map, dl, h->d_w, h->bias, h->p.l2hys_clip, h->d_scores,
-                              dptr<SvmItem>(h, o.s_items), (int)p.s_items.size(), h->d_err));
+                              dptr<SvmItem>(h, o.s_items), (int)p.s_items.size(), h->d_err, sf));
         if (timed) PD_CUDA(h, record(h->stage_ev[3], q));
         PD_CUDA(h, launch_nms(q, df, dl, n_frames, h->d_scores, h->p.threshold, h->p.nms_iou,
                               h->d_nms_scratch, h->p.max_candidates_per_frame, h->m_boxes,
@@ -738,8 +823,12 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
     }
     PD_CUDA(h, cudaEventRecord(h->graph_done, s));
     h->last_launches = (p.r_items.empty() ? 0 : 1) + (p.c_items.empty() ? 0 : 1) +
-                       (p.s_items.empty() ? 0 : 1) + (n_frames > 0 ? 1 : 0);
+                       (p.s_items.empty() ? 0 : 1) + (n_frames > 0 ? 1 : 0) +
+                       (h->proposal ? (p.cnn_items.empty() ? 0 : 1) + (p.levels.empty() ? 0 : 1) +
+                                          (p.s_items.empty() ? 0 : 1)
+                                    : 0);
     h->detected = true;
+    h->ran_proposal = h->proposal;
     return PD_OK;
 }
 
@@ -818,43 +907,6 @@ int pd_get_tile_costs(const pd_handle *h, float *cost) {
 }
 
 // ----------------------------------------------------------------------------- learned proposal
-namespace {
-
-CnnWeights cnn_weights(const pd_handle *h) {
-    const float *wr = h->cnn + 4 * kCnnParams;
-    CnnWeights w;
-    w.in_tab = h->in_tab;
-    w.w1 = wr + kOffW1;
-    w.b1 = wr + kOffB1;
-    w.w2frag = h->w2frag;
-    w.b2 = wr + kOffB2;
-    w.w3frag = h->w3frag;
-    w.b3 = wr + kOffB3;
-    w.wh = wr + kOffWh;
-    w.bh = wr + kOffBh;
-    w.v = wr + kOffV;
-    w.bv = wr + kOffBv;
-    return w;
-}
-
-// Inference fragments from the master weights (after set_params or training).
-int refresh_fragments(pd_handle *h) {
-    std::vector<float> p(kCnnParams);
-    PD_CUDA(h, cudaMemcpy(p.data(), h->cnn, kCnnParams * 4, cudaMemcpyDeviceToHost));
-    std::vector<uint32_t> f2(2304), f3(4608);
-    for (int tap = 0; tap < 9; ++tap)
-        for (int nt = 0; nt < 4; ++nt) pack_frag(p.data() + kOffW2, 16, 0, tap, nt, &f2[(tap * 4 + nt) * 64]);
-    for (int tap = 0; tap < 9; ++tap)
-        for (int kh = 0; kh < 2; ++kh)
-            for (int nt = 0; nt < 4; ++nt)
-                pack_frag(p.data() + kOffW3, 32, 16 * kh, tap, nt, &f3[((tap * 2 + kh) * 4 + nt) * 64]);
-    PD_CUDA(h, cudaMemcpy(h->w2frag, f2.data(), f2.size() * 4, cudaMemcpyHostToDevice));
-    PD_CUDA(h, cudaMemcpy(h->w3frag, f3.data(), f3.size() * 4, cudaMemcpyHostToDevice));
-    h->frag_stale = false;
-    return PD_OK;
-}
-
-}  // namespace
 
 int pd_cnn_set_params(pd_handle *h, const float *params, int n) {
     if (!h || !params || n != kCnnParams) return h ? fail(h, PD_EINVAL, "expected %d parameters", kCnnParams) : PD_EINVAL;
@@ -910,6 +962,7 @@ int pd_cnn_forward(pd_handle *h, void *stream, const uint8_t *d_level, int Wk, i
 int pd_cnn_train_step(pd_handle *h, void *stream, float pos_weight, float label_threshold, float lr) {
     if (!h) return PD_EINVAL;
     if (!h->detected || !h->cache_valid) return fail(h, PD_ESTATE, "pd_cnn_train_step needs a pd_detect batch");
+    if (h->ran_proposal) return fail(h, PD_ESTATE, "labels need a pd_detect batch with the proposal off");
     if (!h->cnn_loaded) return fail(h, PD_ESTATE, "no proposal parameters (pd_cnn_set_params)");
     if (!(pos_weight > 0.f) || !(lr >= 0.f)) return fail(h, PD_EINVAL, "bad pos_weight / lr");
     const Plan &p = h->plan;
@@ -998,14 +1051,29 @@ int pd_cnn_train_loss(pd_handle *h, void *stream, float *loss) {
     if (!h->train_ws || h->train_levels <= 0) return fail(h, PD_ESTATE, "no training step yet");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     PD_CUDA(h, cudaStreamSynchronize(s));
-    // level losses sit after the fixed sections of the workspace: recompute the offset
+    // one partial loss per level (already weighted by its share of the windows)
     std::vector<float> ll(h->train_levels);
-    const unsigned char *end = h->train_ws + h->train_ws_bytes;
-    (void)end;
     PD_CUDA(h, cudaMemcpy(ll.data(), h->train_loss_ptr, ll.size() * 4, cudaMemcpyDeviceToHost));
     double sum = 0;
     for (float v : ll) sum += v;
     *loss = (float)sum;
+    return PD_OK;
+}
+
+int pd_set_proposal(pd_handle *h, int enable, float keep_logit_threshold) {
+    if (!h) return PD_EINVAL;
+    if (enable && !h->cnn_loaded) return fail(h, PD_ESTATE, "no proposal parameters (pd_cnn_set_params)");
+    if (std::isnan(keep_logit_threshold)) return fail(h, PD_EINVAL, "threshold is NaN");
+    h->proposal = enable != 0;
+    h->tau = keep_logit_threshold;
+    invalidate_cache(h);
+    return PD_OK;
+}
+
+int pd_logits(const pd_handle *h, const float **d_logits, int64_t *total) {
+    if (!h || !d_logits || !total) return PD_EINVAL;
+    *d_logits = h->logits;
+    *total = h->detected && h->ran_proposal ? h->plan.score_floats : 0;
     return PD_OK;
 }
 

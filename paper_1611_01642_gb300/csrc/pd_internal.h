@@ -45,6 +45,8 @@ struct LevelDesc {
     int32_t rows, cols; // score map size (0 when no window fits)
     int32_t xtab_off;   // Q11 source-column table of this level (Wk entries)
     int32_t ytab_off;   // Q11 source-row table of this level (Hk entries)
+    int32_t citem0;     // index of this level's first K2+K3 item
+    int32_t ctx;        // K2+K3 tiles per row of cells
 };
 
 // Work items (one CTA each).
@@ -88,10 +90,14 @@ cudaError_t launch_resize(cudaStream_t s, const FrameDesc *d_frames, const Level
                           const int32_t *d_tabs, uint8_t *pyr, const ResizeItem *d_items,
                           int n_items);
 cudaError_t launch_cells(cudaStream_t s, const LevelDesc *d_levels, const uint8_t *pyr,
-                         CellAtlas atlas, const CellItem *d_items, int n_items, const uint8_t *d_lbp_map);
+                         CellAtlas atlas, const CellItem *d_items, int n_items, const uint8_t *d_lbp_map,
+                         const uint32_t *c_flag = nullptr);
+cudaError_t launch_proposal_flags(cudaStream_t s, const LevelDesc *d_levels, const SvmItem *d_items, int n_items,
+                                  const float *logits, float tau, uint32_t *s_flag, uint32_t *c_flag);
 cudaError_t launch_svm(cudaStream_t s, const CUtensorMap *hog_maps, const CUtensorMap *lbp_maps,
                        const LevelDesc *d_levels, const float *d_w, float bias, float clip,
-                       float *scores, const SvmItem *d_items, int n_items, unsigned *d_err);
+                       float *scores, const SvmItem *d_items, int n_items, unsigned *d_err,
+                       const uint32_t *s_flag = nullptr);
 cudaError_t launch_nms(cudaStream_t s, const FrameDesc *d_frames, const LevelDesc *d_levels,
                        int n_frames, const float *scores, float threshold, float iou,
                        float4 *scratch, int max_cand, pd_box *boxes, int max_boxes,

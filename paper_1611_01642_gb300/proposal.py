@@ -1,0 +1,241 @@
+"""Training, calibration and checkpoints of the learned window proposal.
+
+The proposal network (a small CNN, defined in the header of the library) is
+not part of the paper: it predicts, for every sliding window of every pyramid
+level, whether the window's SVM score (the linear classifier of Sec. 3 over
+the HOG+LBP block features) exceeds the detection threshold, so that the
+sparse path computes cells and scores only near such windows.
+
+Labels are the detector's own scores: a window is positive iff its score on
+the plain path is above ``label_threshold``. Every training step runs on the
+GPU (pd_cnn_train_step: forward, mean binary cross-entropy with a positive
+weight, backward, Adam, all in the library's kernels); this module only
+orders the batches and keeps the bookkeeping.
+
+Checkpoint format: one ``.npz`` with ``params`` (float32[14210], the flat
+order w1 b1 w2 b2 w3 b3 wh bh v bv) and ``meta`` (a JSON string: training
+recipe, keep threshold, measured recall and keep fraction).
+"""
+from __future__ import annotations
+
+import json
+import time
+from dataclasses import asdict, dataclass, field
+
+import numpy as np
+
+from . import (CNN_PARAMS, Detector, PD_OK, pd_cnn_get_params, pd_cnn_set_params, pd_cnn_train_loss,
+               pd_cnn_train_step)
+
+
+@dataclass
+class TrainConfig:
+    lr: float = 1e-3                 # Adam step size
+    label_threshold: float = 0.0     # positive iff plain score > this
+    pos_weight: float = 0.0          # 0: neg/pos of the first batch
+    steps_per_batch: int = 4         # Adam steps on each detected batch
+    init_seed: int = 0               # He initialisation seed
+    extra: dict = field(default_factory=dict)
+
+
+def init_params(seed: int) -> np.ndarray:
+    """He-style initial parameters (flat float32), drawn from PCG64(SeedSequence([23, seed]))."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([23, seed])))
+    parts = [rng.standard_normal(16 * 9) * np.sqrt(2.0 / 9), np.zeros(16),
+             rng.standard_normal(32 * 16 * 9) * np.sqrt(2.0 / (16 * 9)), np.zeros(32),
+             rng.standard_normal(32 * 32 * 9) * np.sqrt(2.0 / (32 * 9)), np.zeros(32),
+             rng.standard_normal(32) * np.sqrt(1.0 / 32), np.zeros(1),
+             rng.standard_normal(128) * np.sqrt(1.0 / 128), np.zeros(1)]
+    p = np.concatenate(parts).astype(np.float32)
+    assert p.size == CNN_PARAMS
+    return p
+
+
+def _to_device(frames):
+    import torch
+    return [f if isinstance(f, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(f)).cuda()
+            for f in frames]
+
+
+def _flat_scores(det: Detector, n_frames: int, logits: bool = False) -> np.ndarray:
+    maps = []
+    for f in range(n_frames):
+        src = det.logit_maps(f) if logits else det.score_maps(f)
+        maps += [m.reshape(-1) for m in src]
+    import torch
+    return torch.cat(maps).cpu().numpy() if maps else np.zeros(0, np.float32)
+
+
+def train(det: Detector, batches, cfg: TrainConfig, params: np.ndarray | None = None, log=print):
+    """Trains the proposal on ``batches`` (an iterable of frame lists) and returns the flat parameters.
+
+    Each batch is detected once on the plain path (labels), then ``steps_per_batch`` Adam steps run on
+    all windows of all its levels. ``det`` must have been created with room for the largest batch.
+    """
+    det.set_proposal(False)
+    pd_cnn_set_params(det.h, init_params(cfg.init_seed) if params is None else params)
+    pos_weight = cfg.pos_weight
+    history = []
+    t0 = time.time()
+    for b, frames in enumerate(batches):
+        det.detect(_to_device(frames))
+        if det.sync() != PD_OK:
+            raise RuntimeError("detect failed while labelling")
+        if pos_weight <= 0:
+            s = _flat_scores(det, len(frames))
+            pos = int((s > cfg.label_threshold).sum())
+            pos_weight = float(max(s.size - pos, 1) / max(pos, 1))
+            log(f"pos_weight = neg/pos = {pos_weight:.2f} ({pos} of {s.size} windows positive)")
+        for _ in range(cfg.steps_per_batch):
+            pd_cnn_train_step(det.h, pos_weight, cfg.label_threshold, cfg.lr)
+        loss = pd_cnn_train_loss(det.h)
+        history.append(loss)
+        if b % 10 == 0:
+            log(f"batch {b:4d}  loss {loss:.4f}  {time.time() - t0:.1f}s")
+    cfg.pos_weight = pos_weight
+    params, _ = pd_cnn_get_params(det.h)
+    return params, history
+
+
+def window_stats(det: Detector, batches, threshold: float = 0.0):
+    """(scores, logits) of all windows of ``batches``: plain-path scores and the proposal's keep-logits."""
+    S, Z = [], []
+    for frames in batches:
+        dev = _to_device(frames)
+        det.set_proposal(False)
+        det.detect(dev)
+        if det.sync() != PD_OK:
+            raise RuntimeError("detect failed")
+        S.append(_flat_scores(det, len(frames)))
+        det.set_proposal(True, float("-inf"))
+        det.detect(dev)
+        if det.sync() != PD_OK:
+            raise RuntimeError("detect failed")
+        Z.append(_flat_scores(det, len(frames), logits=True))
+    det.set_proposal(False)
+    return np.concatenate(S), np.concatenate(Z)
+
+
+def calibrate(scores: np.ndarray, logits: np.ndarray, recall: float = 0.99, threshold: float = 0.0) -> float:
+    """Largest keep threshold tau with |{z > tau} & {s > threshold}| >= recall * |{s > threshold}|."""
+    z = np.sort(logits[scores > threshold].astype(np.float64))
+    if z.size == 0:
+        return float("-inf")
+    m = int(np.floor((1.0 - recall) * z.size))     # windows that may be dropped
+    m = min(m, z.size - 1)
+    return float(np.nextafter(np.float32(z[m]), np.float32(-np.inf)))
+
+
+def sparse_metrics(det: Detector, batches, tau: float, threshold: float = 0.0):
+    """Recall and keep fraction of the sparse path against the plain path, window by window.
+
+    recall = |scored on the sparse path and score > threshold| / |score > threshold on the plain path|;
+    keep = fraction of windows the sparse path scored (tile-level decision); window_keep = fraction
+    of windows whose own keep-logit is above tau.
+    """
+    pos = hit = kept = total = zkept = 0
+    for frames in batches:
+        dev = _to_device(frames)
+        det.set_proposal(False)
+        det.detect(dev)
+        if det.sync() != PD_OK:
+            raise RuntimeError("detect failed")
+        s = _flat_scores(det, len(frames))
+        det.set_proposal(True, tau)
+        det.detect(dev)
+        if det.sync() != PD_OK:
+            raise RuntimeError("detect failed")
+        sp = _flat_scores(det, len(frames))
+        zkept += int((_flat_scores(det, len(frames), logits=True) > tau).sum())
+        scored = ~np.isneginf(sp)
+        if not np.array_equal(sp[scored], s[scored]):
+            raise AssertionError("sparse scores differ from the plain path on scored windows")
+        p = s > threshold
+        pos += int(p.sum())
+        hit += int((p & scored).sum())
+        kept += int(scored.sum())
+        total += s.size
+    det.set_proposal(False)
+    return dict(recall=hit / max(pos, 1), keep_fraction=kept / max(total, 1),
+                window_keep_fraction=zkept / max(total, 1), positives=pos, windows=total)
+
+
+def save_checkpoint(path: str, params: np.ndarray, meta: dict) -> None:
+    np.savez(path, params=np.asarray(params, np.float32), meta=np.array(json.dumps(meta, sort_keys=True)))
+
+
+def load_checkpoint(path: str):
+    d = np.load(path, allow_pickle=False)
+    params = np.asarray(d["params"], np.float32)
+    if params.size != CNN_PARAMS:
+        raise ValueError(f"{path}: {params.size} parameters, expected {CNN_PARAMS}")
+    return params, json.loads(str(d["meta"]))
+
+
+def _scene_batches(width, height, key, first, count, batch):
+    """Synthetic frames (seeded by SeedSequence([key, i])) in batches, generated lazily."""
+    import synth
+    for i0 in range(first, first + count, batch):
+        yield [synth.make_scene(width, height, key, i, n_sil=("poisson", 10.0), heights=(48, "0.8H"))
+               for i in range(i0, min(i0 + batch, first + count))]
+
+
+def main(argv=None):
+    import argparse
+    ap = argparse.ArgumentParser(description="Train and calibrate the window proposal on synthetic scenes.")
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
+    ap.add_argument("--factor", type=float, default=1.05)
+    ap.add_argument("--train-frames", type=int, default=256)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=2)
+    ap.add_argument("--steps-per-batch", type=int, default=4)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--calib-frames", type=int, default=32)
+    ap.add_argument("--val-frames", type=int, default=32)
+    ap.add_argument("--recall", type=float, default=0.99)
+    ap.add_argument("--svm", default=None, help="npz with w, b (default: the seed-0 template)")
+    ap.add_argument("--out", required=True)
+    a = ap.parse_args(argv)
+    import os
+    import torch  # noqa: F401  (CUDA context for the frames)
+    from . import build as bld
+    bld.build()
+    svm = a.svm or os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                "tests", "golden", "svm_template_seed0.npz")
+    d = np.load(svm)
+    w, b = d["w"], float(d["b"])
+    det = Detector(w, b, max_frames=a.batch, max_width=a.width, max_height=a.height,
+                   pyr_factor=float(np.float32(a.factor)))
+    try:
+        # training frames: a fixed pool, visited once per epoch in a seeded order
+        pool = [f for batch in _scene_batches(a.width, a.height, 100, 0, a.train_frames, a.batch) for f in batch]
+        order_rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([102])))
+
+        def epochs():
+            for _ in range(a.epochs):
+                idx = order_rng.permutation(len(pool))
+                for i0 in range(0, len(idx), a.batch):
+                    yield [pool[i] for i in idx[i0:i0 + a.batch]]
+        cfg = TrainConfig(lr=a.lr, steps_per_batch=a.steps_per_batch)
+        t0 = time.time()
+        params, hist = train(det, epochs(), cfg)
+        train_s = time.time() - t0
+        pd_cnn_set_params(det.h, params)
+        calib = list(_scene_batches(a.width, a.height, 101, 0, a.calib_frames, a.batch))
+        s, z = window_stats(det, calib)
+        tau = calibrate(s, z, a.recall)
+        val = list(_scene_batches(a.width, a.height, 101, a.calib_frames, a.val_frames, a.batch))
+        m = sparse_metrics(det, val, tau)
+        meta = dict(recipe=vars(a), train=asdict(cfg), train_seconds=train_s, final_loss=hist[-1],
+                    first_loss=hist[0], keep_logit_threshold=tau,
+                    calib_window_recall=float(np.mean(z[s > 0] > tau)) if (s > 0).any() else 1.0,
+                    validation=m)
+        save_checkpoint(a.out, params, meta)
+        print(json.dumps(meta, sort_keys=True))
+    finally:
+        det.close()
+
+
+if __name__ == "__main__":
+    main()

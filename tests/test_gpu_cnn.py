@@ -147,3 +147,103 @@ def test_cnn_training_is_deterministic_and_descends(template):
     assert np.array_equal(runs[0][0], runs[1][0])
     assert runs[0][1] == runs[1][1]
     assert runs[0][1][-1] < 0.8 * runs[0][1][0]
+
+
+def _box_rows(a):
+    return [tuple(r) for r in a.tolist()]
+
+
+def test_sparse_threshold_minus_inf_equals_plain(template):
+    """With every window kept, the sparse path returns the plain path's scores and boxes bit for bit."""
+    from paper_1611_01642_gb300 import build as bld
+    bld.build()
+    w, b = template
+    frames = [synth.make_scene(1242, 375, 1, 40), synth.make_scene(640, 480, 2, 41)]
+    d = pd.Detector(w, b, max_frames=2, max_width=1242, max_height=480)
+    try:
+        pd.pd_cnn_set_params(d.h, _params(5))
+        dev = [torch.from_numpy(f).cuda() for f in frames]
+        d.detect(dev)
+        assert d.sync() == pd.PD_OK
+        plain = [[m.clone() for m in d.score_maps(f)] for f in range(2)]
+        plain_boxes = [d.boxes(f) for f in range(2)]
+        d.set_proposal(True, float("-inf"))
+        d.detect(dev)
+        assert d.sync() == pd.PD_OK
+        for f in range(2):
+            for a, m in zip(plain[f], d.score_maps(f)):
+                assert torch.equal(a, m)
+            assert _box_rows(plain_boxes[f]) == _box_rows(d.boxes(f))
+            assert len(d.logit_maps(f)) == len(plain[f])
+    finally:
+        d.close()
+
+
+@pytest.mark.parametrize("quantile", [0.9, 0.999, 1.0])
+def test_sparse_path_skips_only_unkept_tiles(template, quantile):
+    """Windows with keep-logit above the threshold are scored exactly; skipped ones are -inf and
+    none of them has a logit above the threshold; the boxes are the oracle NMS of the sparse maps;
+    the logits are those of the proposal network run level by level."""
+    from paper_1611_01642_gb300 import build as bld
+    bld.build()
+    w, b = template
+    img = synth.make_scene(1242, 375, 1, 42)
+    d = pd.Detector(w, b, max_frames=1, max_width=1242, max_height=375)
+    try:
+        pd.pd_cnn_set_params(d.h, _params(6))
+        dev = [torch.from_numpy(img).cuda()]
+        d.detect(dev)
+        assert d.sync() == pd.PD_OK
+        plain = [m.clone().cpu().numpy() for m in d.score_maps(0)]
+        d.set_proposal(True, 0.0)
+        d.detect(dev)
+        assert d.sync() == pd.PD_OK
+        logits = np.concatenate([m.cpu().numpy().ravel() for m in d.logit_maps(0)])
+        tau = float(np.quantile(logits, quantile))
+        d.set_proposal(True, tau)
+        d.detect(dev)
+        assert d.sync() == pd.PD_OK
+        sparse = [m.cpu().numpy() for m in d.score_maps(0)]
+        lg = [m.cpu().numpy() for m in d.logit_maps(0)]
+        levels = d.levels(0)
+        got_boxes = d.boxes(0)
+        n_skipped = 0
+        for lv, p_, s_, z in zip(levels, plain, sparse, lg):
+            kept = z > tau
+            assert np.array_equal(s_[kept], p_[kept])
+            skipped = np.isneginf(s_)
+            assert not (skipped & kept).any()
+            assert np.array_equal(s_[~skipped], p_[~skipped])
+            n_skipped += int(skipped.sum())
+        n_windows = sum(z.size for z in lg)
+        if quantile == 1.0:   # no window above the largest logit: every tile skipped
+            assert n_skipped == n_windows
+        print(f"quantile {quantile}: {n_skipped} of {n_windows} windows skipped")
+        # the proposal logits equal a standalone forward of each level
+        for lv, z in zip(levels, lg):
+            Wk, Hk = lv["width"], lv["height"]
+            if z.size == 0:
+                continue
+            L = oracle.resize(img, Wk, Hk)
+            Hc, Wc = Hk // 8, Wk // 8
+            hp = ((Wc + 15) // 16) * 16
+            hm = torch.zeros((Hc * hp,), device="cuda")
+            out = torch.zeros((z.size,), device="cuda")
+            pd.pd_cnn_forward(d.h, torch.from_numpy(L).cuda(), hm, hp, out)
+            torch.cuda.synchronize()
+            assert np.array_equal(out.cpu().numpy().reshape(z.shape), z)
+        ref_boxes, _ = oracle.nms(sparse, [(lv["width"], lv["height"]) for lv in levels], 1242, 375,
+                                  max_boxes=d.params.max_boxes_per_frame)
+        assert _box_rows(ref_boxes) == _box_rows(got_boxes)
+    finally:
+        d.close()
+
+
+def test_sparse_path_needs_parameters(template):
+    w, b = template
+    d = pd.Detector(w, b, max_frames=1, max_width=256, max_height=256)
+    try:
+        with pytest.raises(pd.PDError):
+            d.set_proposal(True, 0.0)
+    finally:
+        d.close()
