@@ -50,6 +50,8 @@ def parse_args(argv=None):
     ap.add_argument("--frames-per-step", type=int, default=64)
     ap.add_argument("--cpu-sample-frames", type=int, default=12,
                     help="frames the CPU oracle times for cpu_baseline (bounded sample)")
+    ap.add_argument("--proposal-steps", type=int, default=10,
+                    help="timed steps of the 16x1920x1080 plain-vs-sparse comparison (0: skip)")
     return ap.parse_args(argv)
 
 
@@ -217,6 +219,78 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+PROPOSAL_CKPT = os.path.join(ROOT, "paper_1611_01642_gb300", "weights", "proposal_1920x1080.npz")
+
+
+def run_proposal(args, pd, torch, flush):
+    """Plain vs sparse (learned proposal) path on 16 synthetic 1920x1080 frames (scene recipe 4).
+
+    Both paths run the same frames with the same timing rules as the main line (L2 flushed before
+    every step, CUDA events on the detector's stream). Recall and keep fraction are counted window
+    by window over every level of the batch: recall = |scored on the sparse path and plain score > 0|
+    / |plain score > 0|.
+    """
+    import synth
+    from paper_1611_01642_gb300 import proposal as prop
+    params, meta = prop.load_checkpoint(PROPOSAL_CKPT)
+    tau = float(meta["keep_logit_threshold"])
+    imgs = synth.make_frames(4)
+    frames = [torch.from_numpy(im).cuda() for im in imgs]
+    w, b = load_template()
+    det = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=len(frames), max_width=1920, max_height=1080,
+                      flags=pd.PD_FLAG_STAGE_TIMING)
+    pd.pd_cnn_set_params(det.h, params)
+    stream = torch.cuda.current_stream()
+
+    def timed(sparse: bool):
+        det.set_proposal(sparse, tau)
+        for _ in range(3):
+            flush.fill_(1)
+            det.detect(frames)
+            det.sync()
+        tot, st = 0.0, np.zeros(5)
+        for i in range(args.proposal_steps):
+            flush.fill_(i & 255)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            det.detect(frames)
+            e1.record(stream)
+            if det.sync() != pd.PD_OK:
+                raise RuntimeError(pd.pd_last_error(det.h))
+            tot += e0.elapsed_time(e1)
+            st += np.array(pd.pd_stage_times(det.h))
+        n = args.proposal_steps
+        return tot / n, st / n
+
+    ms_plain, st_plain = timed(False)
+    plain_scores = torch.cat([m.reshape(-1) for f in range(len(frames)) for m in det.score_maps(f)]).clone()
+    ms_sparse, st_sparse = timed(True)
+    sparse_scores = torch.cat([m.reshape(-1) for f in range(len(frames)) for m in det.score_maps(f)])
+    logits = torch.cat([m.reshape(-1) for f in range(len(frames)) for m in det.logit_maps(f)])
+    scored = ~torch.isneginf(sparse_scores)
+    pos = plain_scores > 0
+    exact = bool(torch.equal(sparse_scores[scored], plain_scores[scored]))
+    det.close()
+    names = ["pyramid", "cells", "norm_svm", "nms", "proposal"]
+    return {
+        "workload": "16 x 1920x1080 u8 frames (scene recipe 4: Poisson(10) silhouettes, 48 px..0.8H), "
+                    "pyramid factor 1.05 (44 levels)",
+        "checkpoint": os.path.relpath(PROPOSAL_CKPT, ROOT), "keep_logit_threshold": tau,
+        "plain_frames_per_s": len(frames) / (ms_plain / 1e3),
+        "sparse_frames_per_s": len(frames) / (ms_sparse / 1e3),
+        "speedup": ms_plain / ms_sparse,
+        "recall": float((pos & scored).sum().item() / max(pos.sum().item(), 1)),
+        "keep_fraction": float(scored.float().mean().item()),
+        "window_keep_fraction": float((logits > tau).float().mean().item()),
+        "proposal_share": float(st_sparse[4] / ms_sparse),
+        "scored_windows_equal_plain": exact,
+        "stage_ms_plain": dict(zip(names, map(float, st_plain))),
+        "stage_ms_sparse": dict(zip(names, map(float, st_sparse))),
+        "steps": args.proposal_steps,
+    }
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -254,7 +328,7 @@ def run_gpu(args):
     sampler.start()
     barrier(world)
     torch.cuda.synchronize()
-    total_ms, stage_ms = 0.0, np.zeros(4)
+    total_ms, stage_ms = 0.0, np.zeros(5)
     launches = 0
     for i in range(args.steps):
         flush.fill_(i & 255)
@@ -304,6 +378,10 @@ def run_gpu(args):
                 "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                               f"(max SM clock, {peak_kind})"}
 
+    proposal = None
+    if rank == 0 and args.proposal_steps > 0 and os.path.exists(PROPOSAL_CKPT):
+        proposal = run_proposal(args, pd, torch, flush)
+
     cpu = None
     if rank == 0 and world == 1 and args.cpu_sample_frames > 0:
         n = min(args.cpu_sample_frames, B)
@@ -327,6 +405,7 @@ def run_gpu(args):
         "clocks": clocks,
         "stage_ms_per_step": {"pyramid": stage_step[0], "cells": stage_step[1], "norm_svm": stage_step[2],
                               "nms": stage_step[3]},
+        "proposal": proposal,
         "px_per_ns": B * WIDTH * HEIGHT / (ms_step * 1e6),
     }
     if rank == 0:

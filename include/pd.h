@@ -175,11 +175,13 @@ int pd_last_launch_count(const pd_handle *h);
 int pd_set_tile_costs(pd_handle *h, const float *cost);
 int pd_get_tile_costs(const pd_handle *h, float *cost);
 
-/* Device time in milliseconds of each kernel of the last pd_detect, from CUDA
- * events recorded on its stream around each launch: ms[0] pyramid (K1),
- * ms[1] cell histograms (K2/K3), ms[2] block norm + window scores (K4),
- * ms[3] NMS (K5). Needs PD_FLAG_STAGE_TIMING at pd_create and a pd_sync
- * after the detect (else PD_ESTATE). */
+/* Device time in milliseconds of each stage of the last pd_detect, from CUDA
+ * events recorded on its stream around each launch (ms has 5 entries):
+ * ms[0] pyramid (K1), ms[1] cell histograms (K2/K3), ms[2] block norm +
+ * window scores (K4), ms[3] NMS (K5), ms[4] the proposal network and the
+ * tile flags of the sparse path (about 0 with the proposal off). Needs
+ * PD_FLAG_STAGE_TIMING at pd_create and a pd_sync after the detect (else
+ * PD_ESTATE). */
 int pd_stage_times(const pd_handle *h, float *ms);
 
 /* Same as pd_detect with frames in HOST memory (h_frames: host array of host

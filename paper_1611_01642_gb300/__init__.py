@@ -256,8 +256,8 @@ def pd_last_launch_count(h) -> int:
 
 
 def pd_stage_times(h):
-    """[K1, K2/K3, K4, K5] device milliseconds of the last detect (needs PD_FLAG_STAGE_TIMING)."""
-    ms = np.zeros(4, np.float32)
+    """[K1, K2/K3, K4, K5, proposal] device milliseconds of the last detect (needs PD_FLAG_STAGE_TIMING)."""
+    ms = np.zeros(5, np.float32)
     _check(load().pd_stage_times(h, ms.ctypes.data_as(ctypes.c_void_p)), h)
     return [float(v) for v in ms]
 

@@ -9,18 +9,24 @@
 //   h  = wh . a3 + bh (1x1 head),   z[wy][wx] = bv + sum V[r][s] h[wy+r][wx+s].
 // bf16 inputs, weights and stored activations; fp32 accumulation.
 //
-// k_cnn_fwd: one CTA (8 warps) per 8x8 tile of cells. It stages the 71x71
-// input pixels, computes the 35x35x16 layer-1 activations on CUDA cores, the
-// 17x17x32 layer-2 activations and the 8x8x32 layer-3 activations as implicit
-// GEMMs on the tensor cores (mma.sync m16n8k16 bf16 -> fp32; the A operand is
-// gathered from shared memory laid out position-major with padded strides so
-// that the stride-2 gathers are bank-conflict free), and writes h.
+// k_cnn_fwd: persistent CTAs (8 warps, two per SM), each walking 8x8-cell
+// tiles. The 72x80 input bytes of the next tile are fetched with cp.async
+// while the current tile is computed. Per tile: the pixels become bf16 x
+// (zero outside the level: the padding of layer 1); layer 1 runs on the
+// tensor cores as a GEMM over 4x4 pixel patches (a stride-2 3x3 window at
+// (2r-1, 2c-1) is the top-left 3x3 of the 4x4 patch there; the 7 extra taps
+// carry zero weights), giving 35x35x16 activations; layer 2 (17x17x32,
+// K = 9 taps x 16) and layer 3 (8x8x32, K = 9 x 32) are implicit GEMMs on
+// the tensor cores (mma.sync m16n8k16 bf16 -> fp32) whose A operand is
+// gathered from shared memory laid out position-major with padded strides
+// so that the stride-2 gathers are bank-conflict free; the 1x1 head gives h.
 // Zero padding of every convolution is the zero activation outside each
 // layer's grid.
-// k_cnn_pool: one thread per window, z from 128 taps of h.
 #include "pd_internal.h"
 
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 namespace pd {
 namespace {
@@ -29,28 +35,44 @@ constexpr int kThreads = 256;
 constexpr int T3 = 8;            // layer-3 tile (cells)
 constexpr int R2 = 2 * T3 + 1;   // 17 layer-2 positions per side
 constexpr int R1 = 2 * R2 + 1;   // 35 layer-1 positions per side
-constexpr int R0 = 2 * R1 + 1;   // 71 pixels per side
+constexpr int XR = 2 * R1 + 2;   // 72 pixel rows/columns under the 4x4 patches
+constexpr int kRawW = 80;        // staged bytes per row: pixels x0-1 .. x0+78, ten 8-byte chunks
+constexpr int kChunks = kRawW / 8;
+constexpr int XBW = 44;          // bf16 pixel row stride in words (72 used, padded for banks)
 constexpr int S1W = 10;          // layer-1 position stride in 32-bit words (16 ch + 4 pad bf16)
 constexpr int S2W = 18;          // layer-2 position stride in words (32 ch + 4 pad bf16)
+constexpr int M1 = R1 * R1;      // 1225 layer-1 positions
+constexpr int M1T = (M1 + 15) / 16;  // 77 m-tiles
 constexpr int M2 = R2 * R2;      // 289 layer-2 positions
 constexpr int M2T = (M2 + 15) / 16;  // 19 m-tiles
+constexpr int kW3Frag = 9 * 2 * 4 * 32;  // uint2 layer-3 B fragments
 
 struct CnnSmem {
-    float x[R0][R0 + 1];
-    uint32_t a1[R1 * R1 * S1W];
-    uint32_t a2[M2 * S2W];
-    float w1[16][9];
+    uint8_t raw[2][XR][kRawW];   // input bytes, double buffered
+    uint32_t a1[M1 * S1W];
+    union {
+        uint32_t xb[XR * XBW];   // bf16 pixel pairs (dead once layer 1 is done)
+        uint32_t a2[M2 * S2W];
+    } u;
+    uint2 w3[kW3Frag];
+    uint16_t tab[256];
     float b1[16];
     float b2[32];
     float b3[32];
     float wh[32];
     float hpart[2][64];
-    float tab[256];
 };
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// relu of both values, rounded to bf16 and packed (lo in the low half)
+__device__ __forceinline__ uint32_t relu_pack_bf16(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
 }
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
@@ -62,71 +84,72 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-__global__ void __launch_bounds__(kThreads) k_cnn_fwd(const LevelDesc *__restrict__ levels,
-                                                      const uint8_t *__restrict__ pyr,
-                                                      const CnnItem *__restrict__ items,
-                                                      const CnnWeights wts, float *__restrict__ hmap,
-                                                      int32_t hmap_pitch) {
+// 8-byte asynchronous copy global -> shared; bytes past n are zero-filled.
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, int n) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Stages the bytes of pixel rows y0 .. y0+71 and columns x0-1 .. x0+78 of an
+// item (x0 = 8 cx0 - 7, so every chunk starts on an 8-byte boundary of the
+// level row; level rows are 16-byte aligned). Chunks outside the level read
+// nothing (zero fill); the conversion below zeroes those pixels anyway.
+__device__ __forceinline__ void stage_input(uint8_t (*raw)[kRawW], const CnnItem *__restrict__ items,
+                                            const LevelDesc *__restrict__ levels, const uint8_t *__restrict__ pyr,
+                                            int item, int tid) {
+    const CnnItem it = items[item];
+    const LevelDesc L = levels[it.level];
+    const int y0 = 8 * it.cy0 - 7, xs = 8 * it.cx0 - 8;
+    const uint8_t *img = pyr + L.img_off;
+    for (int k = tid; k < XR * kChunks; k += kThreads) {
+        const int r = k / kChunks, q = k - r * kChunks;
+        const int y = y0 + r, x = xs + 8 * q;
+        int n = 0;
+        const uint8_t *src = img;
+        if (y >= 0 && y < L.Hk && x >= 0) {
+            n = min(max(L.Wk - x, 0), 8);
+            if (n > 0) src = img + (size_t)y * L.img_pitch + x;
+        }
+        cp_async8(&raw[r][8 * q], src, n);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__restrict__ levels,
+                                                         const uint8_t *__restrict__ pyr,
+                                                         const CnnItem *__restrict__ items, int n_items,
+                                                         const CnnWeights wts, float *__restrict__ hmap,
+                                                         int32_t hmap_pitch) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CnnSmem &S = *reinterpret_cast<CnnSmem *>(smem_raw);
-    const CnnItem it = items[blockIdx.x];
-    const LevelDesc L = levels[it.level];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, t = lane & 3;
-    const int Hk = L.Hk, Wk = L.Wk;
-    const int H1 = (Hk + 1) / 2, W1 = (Wk + 1) / 2;
-    const int H2 = (H1 + 1) / 2, W2 = (W1 + 1) / 2;
-    const int y3 = it.cy0, x3 = it.cx0;                  // tile origin (cells)
-    const int y2 = 2 * y3 - 1, x2 = 2 * x3 - 1;          // layer-2 region origin
-    const int y1 = 2 * y2 - 1, x1 = 2 * x2 - 1;          // layer-1 region origin
-    const int y0 = 2 * y1 - 1, x0 = 2 * x1 - 1;          // pixel region origin
-    const uint8_t *img = pyr + L.img_off;
+    int item = blockIdx.x;
+    if (item >= n_items) return;
+    stage_input(S.raw[0], items, levels, pyr, item, tid);
+    cp_async_commit();
 
-    for (int i = tid; i < 256; i += kThreads) S.tab[i] = wts.in_tab[i];
-    for (int i = tid; i < 16 * 9; i += kThreads) (&S.w1[0][0])[i] = wts.w1[i];
+    for (int i = tid; i < 256; i += kThreads) S.tab[i] = __bfloat16_as_ushort(__float2bfloat16_rn(wts.in_tab[i]));
+    for (int i = tid; i < kW3Frag; i += kThreads) S.w3[i] = reinterpret_cast<const uint2 *>(wts.w3frag)[i];
     if (tid < 16) S.b1[tid] = wts.b1[tid];
     if (tid < 32) {
         S.b2[tid] = wts.b2[tid];
         S.b3[tid] = wts.b3[tid];
         S.wh[tid] = wts.wh[tid];
     }
-    __syncthreads();
-    // ---- input pixels (zero outside the level: the padding of layer 1)
-    for (int i = tid; i < R0 * R0; i += kThreads) {
-        const int r = i / R0, c = i - r * R0;
-        const int y = y0 + r, x = x0 + c;
-        float v = 0.f;
-        if (y >= 0 && y < Hk && x >= 0 && x < Wk) v = S.tab[img[(size_t)y * L.img_pitch + x]];
-        S.x[r][c] = v;
-    }
-    __syncthreads();
-    // ---- layer 1 on CUDA cores: 35x35 positions x 16 channels
-    for (int p = tid; p < R1 * R1; p += kThreads) {
-        const int r = p / R1, c = p - r * R1;
-        const int yy = y1 + r, xx = x1 + c;
-        uint32_t *dst = &S.a1[p * S1W];
-        if (yy < 0 || yy >= H1 || xx < 0 || xx >= W1) {
+    // layer-1 B fragments: B[k][n] = w1[n][ky][kx], k = 4 ky + kx, zero for ky = 3 or kx = 3
+    uint32_t bw1[2][2];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) dst[k] = 0u;
-            continue;
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int hk = 0; hk < 2; ++hk) {
+            const int o = nt * 8 + g, ky = (t >> 1) + 2 * hk, kx = 2 * (t & 1);
+            const float lo = (ky < 3 && kx < 3) ? wts.w1[o * 9 + ky * 3 + kx] : 0.f;
+            const float hi = (ky < 3 && kx + 1 < 3) ? wts.w1[o * 9 + ky * 3 + kx + 1] : 0.f;
+            bw1[nt][hk] = pack_bf16(lo, hi);
         }
-        float in[9];
-#pragma unroll
-        for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 3; ++dx) in[dy * 3 + dx] = S.x[2 * r + dy][2 * c + dx];
-#pragma unroll
-        for (int o = 0; o < 16; o += 2) {
-            float s0 = S.b1[o], s1 = S.b1[o + 1];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                s0 = fmaf(S.w1[o][k], in[k], s0);
-                s1 = fmaf(S.w1[o + 1][k], in[k], s1);
-            }
-            dst[o >> 1] = pack_bf16(fmaxf(s0, 0.f), fmaxf(s1, 0.f));
-        }
-    }
-    // layer-2 weights as mma B fragments (9 taps x 4 n-tiles x 2 regs)
+    // layer-2 B fragments (9 taps x 4 n-tiles x 2 regs), kept in registers
     uint32_t bw2[9][4][2];
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap)
@@ -136,100 +159,164 @@ __global__ void __launch_bounds__(kThreads) k_cnn_fwd(const LevelDesc *__restric
             bw2[tap][nt][0] = v.x;
             bw2[tap][nt][1] = v.y;
         }
-    __syncthreads();
-    // ---- layer 2 on tensor cores: 289 positions x 32 channels, K = 9 x 16
-    for (int mt = warp; mt < M2T; mt += kThreads / 32) {
-        const int p0 = mt * 16 + g, p1 = p0 + 8;
-        const int q0 = min(p0, M2 - 1), q1 = min(p1, M2 - 1);  // padding rows reuse a valid row
-        const int r0 = q0 / R2, c0 = q0 - r0 * R2, r1 = q1 / R2, c1 = q1 - r1 * R2;
-        float acc[4][4];
+    const float bh = wts.bh[0];
+
+    for (int iter = 0; item < n_items; ++iter, item += gridDim.x) {
+        const int cur = iter & 1;
+        const int next = item + gridDim.x;
+        if (next < n_items) stage_input(S.raw[cur ^ 1], items, levels, pyr, next, tid);
+        cp_async_commit();
+        cp_async_wait_prev();  // this thread's copies of the current tile have landed
+        __syncthreads();       // everyone's have; the previous tile is finished
+
+        const CnnItem it = items[item];
+        const LevelDesc L = levels[it.level];
+        const int Hk = L.Hk, Wk = L.Wk;
+        const int H1 = (Hk + 1) / 2, W1 = (Wk + 1) / 2;
+        const int H2 = (H1 + 1) / 2, W2 = (W1 + 1) / 2;
+        const int y3 = it.cy0, x3 = it.cx0;                  // tile origin (cells)
+        const int y2 = 2 * y3 - 1, x2 = 2 * x3 - 1;          // layer-2 region origin
+        const int y1 = 2 * y2 - 1, x1 = 2 * x2 - 1;          // layer-1 region origin
+        const int y0 = 2 * y1 - 1, x0 = 2 * x1 - 1;          // pixel region origin
+        const bool interior1 = y1 >= 0 && x1 >= 0 && y1 + R1 <= H1 && x1 + R1 <= W1;
+        const bool interior2 = y2 >= 0 && x2 >= 0 && y2 + R2 <= H2 && x2 + R2 <= W2;
+
+        // ---- pixels -> bf16 x; xb[r][c] = x(y0 + r, x0 + c) = raw[r][c + 1]
+        for (int k = tid; k < XR * (XR / 4); k += kThreads) {
+            const int r = k / (XR / 4), j = k - r * (XR / 4);
+            const uint32_t *rw = reinterpret_cast<const uint32_t *>(S.raw[cur][r]);
+            const uint32_t v = __byte_perm(rw[j], rw[j + 1], 0x4321);
+            const int y = y0 + r, xc = x0 + 4 * j;
+            const bool rin = y >= 0 && y < Hk;
+            uint32_t e[4];
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
-#pragma unroll
-        for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-                const uint32_t *s0 = &S.a1[((2 * r0 + dy) * R1 + 2 * c0 + dx) * S1W];
-                const uint32_t *s1 = &S.a1[((2 * r1 + dy) * R1 + 2 * c1 + dx) * S1W];
-                const uint32_t a0 = s0[t], a1 = s1[t], a2 = s0[4 + t], a3 = s1[4 + t];
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt)
-                    mma_bf16(acc[nt], a0, a1, a2, a3, bw2[dy * 3 + dx][nt][0], bw2[dy * 3 + dx][nt][1]);
+            for (int b = 0; b < 4; ++b) {
+                const int x = xc + b;
+                e[b] = (rin && x >= 0 && x < Wk) ? S.tab[(v >> (8 * b)) & 255u] : 0u;
             }
-        // epilogue: bias, relu, bf16, zero outside the layer-2 grid
+            *reinterpret_cast<uint2 *>(&S.u.xb[r * XBW + 2 * j]) = make_uint2(e[0] | (e[1] << 16), e[2] | (e[3] << 16));
+        }
+        __syncthreads();
+        // ---- layer 1 on tensor cores: 1225 positions x 16 channels, K = 16 (4x4 patch)
+        for (int mt = warp; mt < M1T; mt += kThreads / 32) {
+            const int p0 = mt * 16 + g, p1 = p0 + 8;
+            const int q0 = min(p0, M1 - 1), q1 = min(p1, M1 - 1);  // padding rows reuse a valid row
+            const int r0 = q0 / R1, c0 = q0 - r0 * R1, r1 = q1 / R1, c1 = q1 - r1 * R1;
+            const uint32_t *x0w = &S.u.xb[(2 * r0 + (t >> 1)) * XBW + c0 + (t & 1)];
+            const uint32_t *x1w = &S.u.xb[(2 * r1 + (t >> 1)) * XBW + c1 + (t & 1)];
+            const uint32_t a0 = x0w[0], a1 = x1w[0], a2 = x0w[2 * XBW], a3 = x1w[2 * XBW];
+            float acc[2][4];
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int p = half ? p1 : p0;
-            if (p >= M2) continue;
-            const int r = p / R2, c = p - r * R2;
-            const bool inside = (y2 + r) >= 0 && (y2 + r) < H2 && (x2 + c) >= 0 && (x2 + c) < W2;
+            for (int nt = 0; nt < 2; ++nt) {
+                acc[nt][0] = acc[nt][2] = S.b1[nt * 8 + 2 * t];
+                acc[nt][1] = acc[nt][3] = S.b1[nt * 8 + 2 * t + 1];
+                mma_bf16(acc[nt], a0, a1, a2, a3, bw1[nt][0], bw1[nt][1]);
+            }
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int p = half ? p1 : p0;
+                if (p >= M1) continue;
+                const int r = half ? r1 : r0, c = half ? c1 : c0;
+                const bool inside =
+                    interior1 || ((y1 + r) >= 0 && (y1 + r) < H1 && (x1 + c) >= 0 && (x1 + c) < W1);
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt)
+                    S.a1[p * S1W + nt * 4 + t] =
+                        inside ? relu_pack_bf16(acc[nt][2 * half], acc[nt][2 * half + 1]) : 0u;
+            }
+        }
+        __syncthreads();
+        // ---- layer 2 on tensor cores: 289 positions x 32 channels, K = 9 x 16
+        for (int mt = warp; mt < M2T; mt += kThreads / 32) {
+            const int p0 = mt * 16 + g, p1 = p0 + 8;
+            const int q0 = min(p0, M2 - 1), q1 = min(p1, M2 - 1);
+            const int r0 = q0 / R2, c0 = q0 - r0 * R2, r1 = q1 / R2, c1 = q1 - r1 * R2;
+            float acc[4][4];
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt) {
-                const int co = nt * 8 + 2 * t;
-                float v0 = acc[nt][2 * half] + S.b2[co], v1 = acc[nt][2 * half + 1] + S.b2[co + 1];
-                v0 = inside ? fmaxf(v0, 0.f) : 0.f;
-                v1 = inside ? fmaxf(v1, 0.f) : 0.f;
-                S.a2[p * S2W + (co >> 1)] = pack_bf16(v0, v1);
+                acc[nt][0] = acc[nt][2] = S.b2[nt * 8 + 2 * t];
+                acc[nt][1] = acc[nt][3] = S.b2[nt * 8 + 2 * t + 1];
+            }
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) {
+                    const uint32_t *s0 = &S.a1[((2 * r0 + dy) * R1 + 2 * c0 + dx) * S1W];
+                    const uint32_t *s1 = &S.a1[((2 * r1 + dy) * R1 + 2 * c1 + dx) * S1W];
+                    const uint32_t a0 = s0[t], a1 = s1[t], a2 = s0[4 + t], a3 = s1[4 + t];
+#pragma unroll
+                    for (int nt = 0; nt < 4; ++nt)
+                        mma_bf16(acc[nt], a0, a1, a2, a3, bw2[dy * 3 + dx][nt][0], bw2[dy * 3 + dx][nt][1]);
+                }
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int p = half ? p1 : p0;
+                if (p >= M2) continue;
+                const int r = half ? r1 : r0, c = half ? c1 : c0;
+                const bool inside =
+                    interior2 || ((y2 + r) >= 0 && (y2 + r) < H2 && (x2 + c) >= 0 && (x2 + c) < W2);
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+                    S.u.a2[p * S2W + nt * 4 + t] =
+                        inside ? relu_pack_bf16(acc[nt][2 * half], acc[nt][2 * half + 1]) : 0u;
             }
         }
-    }
-    __syncthreads();
-    // ---- layer 3 on tensor cores: 64 positions x 32 channels, K = 9 x 32;
-    // warp w: m-tile w & 3, n-tiles 2*(w >> 2) .. +1
-    {
-        const int mt = warp & 3, nh = warp >> 2;
-        const int p0 = mt * 16 + g, p1 = p0 + 8;
-        const int r0 = p0 >> 3, c0 = p0 & 7, r1 = p1 >> 3, c1 = p1 & 7;
-        float acc[2][4];
+        __syncthreads();
+        // ---- layer 3 on tensor cores: 64 positions x 32 channels, K = 9 x 32;
+        // warp w: m-tile w & 3, n-tiles 2*(w >> 2) .. +1
+        {
+            const int mt = warp & 3, nh = warp >> 2;
+            const int p0 = mt * 16 + g, p1 = p0 + 8;
+            const int r0 = p0 >> 3, c0 = p0 & 7, r1 = p1 >> 3, c1 = p1 & 7;
+            float acc[2][4];
 #pragma unroll
-        for (int j = 0; j < 2; ++j)
+            for (int j = 0; j < 2; ++j)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
-        const uint2 *w3 = reinterpret_cast<const uint2 *>(wts.w3frag);
+                for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
 #pragma unroll
-        for (int dy = 0; dy < 3; ++dy)
+            for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-                const uint32_t *s0 = &S.a2[((2 * r0 + dy) * R2 + 2 * c0 + dx) * S2W];
-                const uint32_t *s1 = &S.a2[((2 * r1 + dy) * R2 + 2 * c1 + dx) * S2W];
+                for (int dx = 0; dx < 3; ++dx) {
+                    const uint32_t *s0 = &S.u.a2[((2 * r0 + dy) * R2 + 2 * c0 + dx) * S2W];
+                    const uint32_t *s1 = &S.u.a2[((2 * r1 + dy) * R2 + 2 * c1 + dx) * S2W];
 #pragma unroll
-                for (int kh = 0; kh < 2; ++kh) {
-                    const uint32_t a0 = s0[kh * 8 + t], a1 = s1[kh * 8 + t];
-                    const uint32_t a2 = s0[kh * 8 + 4 + t], a3 = s1[kh * 8 + 4 + t];
+                    for (int kh = 0; kh < 2; ++kh) {
+                        const uint32_t a0 = s0[kh * 8 + t], a1 = s1[kh * 8 + t];
+                        const uint32_t a2 = s0[kh * 8 + 4 + t], a3 = s1[kh * 8 + 4 + t];
 #pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const uint2 b = __ldg(&w3[(((dy * 3 + dx) * 2 + kh) * 4 + 2 * nh + j) * 32 + lane]);
-                        mma_bf16(acc[j], a0, a1, a2, a3, b.x, b.y);
+                        for (int j = 0; j < 2; ++j) {
+                            const uint2 b = S.w3[(((dy * 3 + dx) * 2 + kh) * 4 + 2 * nh + j) * 32 + lane];
+                            mma_bf16(acc[j], a0, a1, a2, a3, b.x, b.y);
+                        }
                     }
                 }
-            }
-        // bias, relu, head partial over this lane's 4 channels, reduce over t
-        float h0 = 0.f, h1 = 0.f;
+            // bias, relu, head partial over this lane's 4 channels, reduce over t
+            float h0 = 0.f, h1 = 0.f;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int co = (2 * nh + j) * 8 + 2 * t;
-            h0 = fmaf(fmaxf(acc[j][0] + S.b3[co], 0.f), S.wh[co], h0);
-            h0 = fmaf(fmaxf(acc[j][1] + S.b3[co + 1], 0.f), S.wh[co + 1], h0);
-            h1 = fmaf(fmaxf(acc[j][2] + S.b3[co], 0.f), S.wh[co], h1);
-            h1 = fmaf(fmaxf(acc[j][3] + S.b3[co + 1], 0.f), S.wh[co + 1], h1);
+            for (int j = 0; j < 2; ++j) {
+                const int co = (2 * nh + j) * 8 + 2 * t;
+                h0 = fmaf(fmaxf(acc[j][0] + S.b3[co], 0.f), S.wh[co], h0);
+                h0 = fmaf(fmaxf(acc[j][1] + S.b3[co + 1], 0.f), S.wh[co + 1], h0);
+                h1 = fmaf(fmaxf(acc[j][2] + S.b3[co], 0.f), S.wh[co], h1);
+                h1 = fmaf(fmaxf(acc[j][3] + S.b3[co + 1], 0.f), S.wh[co + 1], h1);
+            }
+            h0 += __shfl_xor_sync(0xffffffffu, h0, 1);
+            h0 += __shfl_xor_sync(0xffffffffu, h0, 2);
+            h1 += __shfl_xor_sync(0xffffffffu, h1, 1);
+            h1 += __shfl_xor_sync(0xffffffffu, h1, 2);
+            if (t == 0) {
+                S.hpart[nh][p0] = h0;
+                S.hpart[nh][p1] = h1;
+            }
         }
-        h0 += __shfl_xor_sync(0xffffffffu, h0, 1);
-        h0 += __shfl_xor_sync(0xffffffffu, h0, 2);
-        h1 += __shfl_xor_sync(0xffffffffu, h1, 1);
-        h1 += __shfl_xor_sync(0xffffffffu, h1, 2);
-        if (t == 0) {
-            S.hpart[nh][p0] = h0;
-            S.hpart[nh][p1] = h1;
+        __syncthreads();
+        if (tid < 64) {
+            const int cy = y3 + (tid >> 3), cx = x3 + (tid & 7);
+            if (cy < L.Hc && cx < L.Wc)
+                hmap[(int64_t)(L.cell_row + cy) * hmap_pitch + cx] = bh + S.hpart[0][tid] + S.hpart[1][tid];
         }
     }
-    __syncthreads();
-    if (tid < 64) {
-        const int cy = y3 + (tid >> 3), cx = x3 + (tid & 7);
-        if (cy < L.Hc && cx < L.Wc)
-            hmap[(int64_t)(L.cell_row + cy) * hmap_pitch + cx] = wts.bh[0] + S.hpart[0][tid] + S.hpart[1][tid];
-    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // One thread per window: z = bv + sum_{r<16, s<8} V[r][s] h[wy+r][wx+s].
@@ -256,9 +343,18 @@ __global__ void __launch_bounds__(256) k_cnn_pool(const LevelDesc *__restrict__ 
     (void)n_levels;
 }
 
+int g_cnn_grid = 0;  // persistent CTAs: two per SM
+
 }  // namespace
 
 cudaError_t init_cnn() {
+    if (g_cnn_grid == 0) {
+        int dev = 0, sms = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        g_cnn_grid = 2 * sms;
+    }
     return cudaFuncSetAttribute(k_cnn_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CnnSmem));
 }
 
@@ -266,7 +362,8 @@ cudaError_t launch_cnn(cudaStream_t s, const LevelDesc *d_levels, int n_levels, 
                        const CnnItem *d_items, int n_items, const CnnWeights &w, float *hmap,
                        int32_t hmap_pitch, float *logits) {
     if (n_items > 0) {
-        k_cnn_fwd<<<n_items, kThreads, sizeof(CnnSmem), s>>>(d_levels, pyr, d_items, w, hmap, hmap_pitch);
+        const int grid = std::min(n_items, g_cnn_grid > 0 ? g_cnn_grid : n_items);
+        k_cnn_fwd<<<grid, kThreads, sizeof(CnnSmem), s>>>(d_levels, pyr, d_items, n_items, w, hmap, hmap_pitch);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

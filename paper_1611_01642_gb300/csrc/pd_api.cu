@@ -204,7 +204,7 @@ struct pd_handle {
     int32_t *m_counts = nullptr;
     unsigned *h_err = nullptr;
     cudaEvent_t desc_done = nullptr;
-    cudaEvent_t stage_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t stage_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool timed = false;
     // learned proposal: parameters (fp32 master + Adam state + rounded copy),
     // inference fragments, per-cell head values, window logits
@@ -771,6 +771,7 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
         if (timed) PD_CUDA(h, record(h->stage_ev[0], q));
         PD_CUDA(h, launch_resize(q, df, dl, dptr<int32_t>(h, o.tabs), h->d_pyr, dptr<ResizeItem>(h, o.r_items),
                                  (int)p.r_items.size()));
+        if (timed) PD_CUDA(h, record(h->stage_ev[5], q));
         const uint32_t *cf = nullptr, *sf = nullptr;
         if (h->proposal) {
             // learned proposal: keep-logits of every window, then the tiles to score
@@ -942,6 +943,15 @@ int pd_cnn_forward(pd_handle *h, void *stream, const uint8_t *d_level, int Wk, i
         int r = refresh_fragments(h);
         if (r != PD_OK) return r;
     }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // the kernel fetches 8-byte chunks of level rows: other layouts go through the pyramid buffer
+    if (((uintptr_t)d_level | (uintptr_t)pitch) & 7u) {
+        const int lp = (int)round_up(Wk, 16);
+        if ((int64_t)lp * Hk > h->pyr_cap) return fail(h, PD_EINVAL, "pd_cnn_forward: level larger than the arena");
+        PD_CUDA(h, cudaMemcpy2DAsync(h->d_pyr, lp, d_level, pitch, Wk, Hk, cudaMemcpyDeviceToDevice, s));
+        d_level = h->d_pyr;
+        pitch = lp;
+    }
     Plan p;
     plan_level(p, 0, 0, Wk, Hk, Wk, Hk, 0, pitch);
     p.c_items.clear();
@@ -949,7 +959,6 @@ int pd_cnn_forward(pd_handle *h, void *stream, const uint8_t *d_level, int Wk, i
     p.tabs.clear();
     for (int cy = 0; cy < Hc; cy += kCnnTile)
         for (int cx = 0; cx < Wc; cx += kCnnTile) p.cnn_items.push_back({0, cy, cx, 0});
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Packed o;
     int r = upload_plan(h, s, p, o);
     if (r != PD_OK) return r;
@@ -1080,8 +1089,10 @@ int pd_logits(const pd_handle *h, const float **d_logits, int64_t *total) {
 int pd_stage_times(const pd_handle *h, float *ms) {
     if (!h || !ms) return PD_EINVAL;
     if (!h->timed || !h->synced) return PD_ESTATE;
-    for (int i = 0; i < 4; ++i)
-        if (cudaEventElapsedTime(&ms[i], h->stage_ev[i], h->stage_ev[i + 1]) != cudaSuccess) return PD_ECUDA;
+    // events: 0 pyramid 5 proposal 1 cells 2 scores 3 nms 4
+    static const int from[5] = {0, 1, 2, 3, 5}, to[5] = {5, 2, 3, 4, 1};
+    for (int i = 0; i < 5; ++i)
+        if (cudaEventElapsedTime(&ms[i], h->stage_ev[from[i]], h->stage_ev[to[i]]) != cudaSuccess) return PD_ECUDA;
     return PD_OK;
 }
 
