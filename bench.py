@@ -310,6 +310,8 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     frames = [torch.from_numpy(im).cuda() for im in imgs]
     pinned = [torch.from_numpy(im).pin_memory() for im in imgs]
+    from paper_1611_01642_gb300 import autotune
+    tile_costs = autotune.apply(det, frames[:16], w, b, FACTOR)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     wpf = windows_per_frame()
 
@@ -397,6 +399,7 @@ def run_gpu(args):
                                "plain HOG+LBP+SVM+NMS",
                    "frames_per_step": B * world, "frames_per_gpu": B, "windows_per_frame": wpf,
                    "l2": "flushed (256 MB write) before every timed step",
+                   "k4_tile_costs": [round(c, 4) for c in tile_costs],
                    "parallelism": f"{world} independent replicas"},
         "roofline": roofline,
         "cpu_baseline": cpu,

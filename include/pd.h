@@ -165,13 +165,16 @@ int pd_boxes(const pd_handle *h, int frame, pd_box *out, int cap, int *count);
 int pd_last_launch_count(const pd_handle *h);
 
 /* K4 tile shapes (windows per CTA tile, x by y): 0 = 32x16, 1 = 64x8,
- * 2 = 32x8, 3 = 64x4. For each level the planner takes the shape with the
- * least (number of tiles x cost[shape]). The default costs are a model
- * (1, 1, 0.6, 0.6); the autotuner measures them on the running GPU and sets
- * them here. cost: host array of PD_TILE_SHAPES positive floats. Affects the
+ * 2 = 32x8, 3 = 64x4, 4 = 64x2, 5 = 32x12, 6 = 32x4. For each level the
+ * planner takes the shape with the least (number of tiles x cost[shape]).
+ * The default costs come from an instruction-count model of one tile
+ * (FMAs of its windows, feature planes of its block region, a fixed part);
+ * the autotuner measures them on the running GPU and sets them here. The
+ * table applies to the dense path; with the proposal on, the planner uses a
+ * fixed table of its own that favours narrow tiles. cost: host array of PD_TILE_SHAPES positive floats. Affects the
  * next pd_detect / pd_window_scores; results are identical for any costs up
  * to float rounding (the same sums in a different tiling). */
-#define PD_TILE_SHAPES 4
+#define PD_TILE_SHAPES 7
 int pd_set_tile_costs(pd_handle *h, const float *cost);
 int pd_get_tile_costs(const pd_handle *h, float *cost);
 

@@ -1,0 +1,145 @@
+"""Autotuner of the window-score (K4) tile shapes.
+
+The planner picks, for every pyramid level, the K4 tile shape with the least
+(number of tiles x cost[shape]). This module measures cost[shape] on the
+running GPU: it forces each shape in turn on a synthetic batch, times the K4
+stage with CUDA events (pd_stage_times) and divides by the number of tiles
+that shape needs. Per-tile costs measured in isolation do not capture how
+shapes behave mixed in one launch, so the measured table is then checked
+against the library's default table on the whole batch, and the faster of
+the two is kept. The result is cached as JSON, keyed by the GPU name, its SM
+count and a hash of the library, under ``$XDG_CACHE_HOME`` (default
+``~/.cache``)/paper_1611_01642_gb300/tile_costs.json.
+
+Scores do not depend on the tiling beyond float rounding order (the same
+sums in another tiling), so tuning never changes results by more than that.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import math
+import os
+
+import numpy as np
+
+from . import (PD_FLAG_STAGE_TIMING, PD_OK, TILE_SHAPE_DIMS, TILE_SHAPES, Detector, library_path,
+               pd_get_tile_costs, pd_set_tile_costs, pd_stage_times)
+
+
+def _cache_path() -> str:
+    base = os.environ.get("XDG_CACHE_HOME") or os.path.join(os.path.expanduser("~"), ".cache")
+    return os.path.join(base, "paper_1611_01642_gb300", "tile_costs.json")
+
+
+def _key() -> str:
+    import torch
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    h = hashlib.sha256()
+    with open(library_path(), "rb") as f:
+        h.update(f.read())
+    return f"{p.name}|{p.multi_processor_count}|{h.hexdigest()[:16]}"
+
+
+def tiles_for(levels, shape: int) -> int:
+    tw, th = TILE_SHAPE_DIMS[shape]
+    return sum(math.ceil(lv["rows"] / th) * math.ceil(lv["cols"] / tw) for lv in levels if lv["rows"] > 0)
+
+
+def measure(frames, svm_w, svm_b, factor: float, steps: int = 5, warmup: int = 2):
+    """Per-tile K4 milliseconds of every shape on ``frames`` (device or host u8 arrays)."""
+    import torch
+    dev = [f if isinstance(f, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in frames]
+    W = max(f.shape[1] for f in dev)
+    H = max(f.shape[0] for f in dev)
+    det = Detector(svm_w, svm_b, pyr_factor=factor, max_frames=len(dev), max_width=W, max_height=H,
+                   flags=PD_FLAG_STAGE_TIMING)
+    out = []
+    try:
+        for s in range(TILE_SHAPES):
+            costs = [1e6] * TILE_SHAPES
+            costs[s] = 1.0
+            pd_set_tile_costs(det.h, costs)
+            for _ in range(warmup):
+                det.detect(dev)
+                if det.sync() != PD_OK:
+                    raise RuntimeError("detect failed while tuning")
+            ms = 0.0
+            for _ in range(steps):
+                det.detect(dev)
+                if det.sync() != PD_OK:
+                    raise RuntimeError("detect failed while tuning")
+                ms += pd_stage_times(det.h)[2]
+            n = sum(tiles_for(det.levels(f), s) for f in range(len(dev)))
+            out.append(ms / steps / max(n, 1))
+    finally:
+        det.close()
+    return out
+
+
+def plan_ms(frames, svm_w, svm_b, factor: float, cost, steps: int = 7, warmup: int = 2) -> float:
+    """Median K4 milliseconds of the whole batch with the cost table ``cost``."""
+    import torch
+    dev = [f if isinstance(f, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in frames]
+    det = Detector(svm_w, svm_b, pyr_factor=factor, max_frames=len(dev), max_width=max(f.shape[1] for f in dev),
+                   max_height=max(f.shape[0] for f in dev), flags=PD_FLAG_STAGE_TIMING)
+    try:
+        pd_set_tile_costs(det.h, cost)
+        ms = []
+        for i in range(warmup + steps):
+            det.detect(dev)
+            if det.sync() != PD_OK:
+                raise RuntimeError("detect failed while tuning")
+            if i >= warmup:
+                ms.append(pd_stage_times(det.h)[2])
+        return float(np.median(ms))
+    finally:
+        det.close()
+
+
+def tile_costs(frames, svm_w, svm_b, factor: float, refresh: bool = False):
+    """Per-tile cost table for the planner, measured once per GPU and library build, then cached."""
+    path = _cache_path()
+    key = _key()
+    cache = {}
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    if not refresh and key in cache and len(cache[key].get("cost", [])) == TILE_SHAPES:
+        return cache[key]["cost"]
+    ms = measure(frames, svm_w, svm_b, factor)
+    measured = [m / ms[0] for m in ms]
+    default = default_costs(svm_w, svm_b)
+    t_default = plan_ms(frames, svm_w, svm_b, factor, default)
+    t_measured = plan_ms(frames, svm_w, svm_b, factor, measured)
+    cost = measured if t_measured < t_default else default
+    cache[key] = {"cost": cost, "ms_per_tile": ms, "measured": measured, "default": default,
+                  "k4_ms_default": t_default, "k4_ms_measured": t_measured}
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = f"{path}.{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass  # read-only home: the costs still apply to this process
+    return cost
+
+
+def default_costs(svm_w, svm_b):
+    """The library's built-in cost table (read from a fresh handle)."""
+    det = Detector(svm_w, svm_b, max_frames=1, max_width=64, max_height=128)
+    try:
+        return [float(c) for c in pd_get_tile_costs(det.h)]
+    finally:
+        det.close()
+
+
+def apply(det: Detector, frames, svm_w, svm_b, factor: float, refresh: bool = False):
+    """Measures (or loads) the tile costs and sets them on ``det``; returns them."""
+    cost = tile_costs(frames, svm_w, svm_b, factor, refresh)
+    pd_set_tile_costs(det.h, cost)
+    return cost

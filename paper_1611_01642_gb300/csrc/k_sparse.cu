@@ -13,7 +13,7 @@
 namespace pd {
 namespace {
 
-__constant__ int2 kShapeDims[kSvmShapes] = {{32, 16}, {64, 8}, {32, 8}, {64, 4}};
+__constant__ int2 kShapeDims[kSvmShapes] = {{32, 16}, {64, 8}, {32, 8}, {64, 4}, {64, 2}, {32, 12}, {32, 4}};
 
 __global__ void __launch_bounds__(256) k_proposal_flags(const LevelDesc *__restrict__ levels,
                                                         const SvmItem *__restrict__ s_items, int n_items,

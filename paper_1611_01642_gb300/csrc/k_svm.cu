@@ -11,8 +11,10 @@
 // GEMM, so it runs on the FP32 CUDA cores (no tensor-core formulation).
 //
 // One CTA (8 warps) computes one TW x TH tile of windows of one level. The
-// tile shape is chosen per level by the host planner among four shapes
-// (lanes along x LX, window rows per thread RY): 32x16, 64x8, 32x8, 64x4.
+// tile shape is chosen per level by the host planner among seven shapes
+// (lanes along x LX, window rows per thread RY): 32x16, 64x8, 32x8, 64x4,
+// 64x2, 32x12, 32x4 (the small ones keep the short top levels of the
+// pyramid from computing windows past the score map).
 //  1. Thread 0 issues TMA loads (cp.async.bulk.tensor.3d): the tile's cell
 //     region of all 9 HOG planes (f32) at once, and the first two 8-plane
 //     chunks of the 59 LBP planes (u8) into a double buffer; each buffer
@@ -69,13 +71,18 @@ struct Shape {
     static_assert(FP % 4 == 0 && HX % 4 == 0, "alignment");
 };
 
-// The four tile shapes, by index (the host planner uses the same order).
+// The tile shapes, by index (the host planner uses the same order).
 using S0 = Shape<8, 4>;   // 32 x 16
 using S1 = Shape<16, 4>;  // 64 x 8
 using S2 = Shape<8, 2>;   // 32 x 8
 using S3 = Shape<16, 2>;  // 64 x 4
+using S4 = Shape<16, 1>;  // 64 x 2
+using S5 = Shape<8, 3>;   // 32 x 12
+using S6 = Shape<8, 1>;   // 32 x 4
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
-constexpr size_t kSmemMax = cmax(cmax(S0::kSmem, S1::kSmem), cmax(S2::kSmem, S3::kSmem)) + 128;
+constexpr size_t kSmemMax =
+    cmax(cmax(cmax(S0::kSmem, S1::kSmem), cmax(S2::kSmem, S3::kSmem)), cmax(cmax(S4::kSmem, S5::kSmem), S6::kSmem)) +
+    128;
 
 struct SvmMaps {
     CUtensorMap hog[kSvmShapes];
@@ -149,7 +156,9 @@ __device__ void svm_tile(const SvmItem &it, const LevelDesc &L, const CUtensorMa
     float(*feat)[RBY][FP] = reinterpret_cast<float(*)[RBY][FP]>(smem + SH::oFeat);
     float *sqrt_tab = reinterpret_cast<float *>(smem + SH::oTab);
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + SH::oBar);  // hog, lbp0, lbp1
-    int *flag = reinterpret_cast<int *>(bars + 4);
+    volatile int *failed = reinterpret_cast<volatile int *>(bars + 4);  // a wait of this CTA gave up
+    int *released = reinterpret_cast<int *>(bars + 4) + 1;             // [2] warps done with each LBP buffer
+    int *issued = released + 2;                                        // [2] loads issued into each buffer
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cy = L.cell_row + it.wy0;
 
@@ -157,6 +166,9 @@ __device__ void svm_tile(const SvmItem &it, const LevelDesc &L, const CUtensorMa
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         mbar_init(&bars[2], 1);
+        *failed = 0;
+        released[0] = released[1] = 0;
+        issued[0] = issued[1] = 1;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -171,59 +183,54 @@ __device__ void svm_tile(const SvmItem &it, const LevelDesc &L, const CUtensorMa
         }
     }
     for (int c = tid; c <= 256; c += kThreads) sqrt_tab[c] = sqrtf((float)c * (1.0f / 256.0f));
-    // Decide CTA-uniformly whether the copies landed; on a timeout drain the
-    // copies still in flight (bounded) and leave.
-    uint32_t lbp_parity0 = 0, lbp_parity1 = 0;  // next phase still in flight per LBP buffer
-    auto uniform_wait = [&](int b, uint32_t parity) -> bool {
-        if (tid == 0) {
-            int ok = mbar_wait_bounded(&bars[b], parity, kWaitNs) ? 1 : 0;
-            if (!ok) {
-                atomicOr(err, kErrTimeout);
-                mbar_wait_bounded(&bars[0], 0, kWaitNs);
-                mbar_wait_bounded(&bars[1], lbp_parity0, kWaitNs);
-                mbar_wait_bounded(&bars[2], lbp_parity1, kWaitNs);
-            }
-            *flag = ok;
+    // Every lane waits (bounded) so that it observes the completed phase and
+    // thereby acquires the TMA-written data; a warp whose wait gave up marks
+    // the CTA failed and skips to the end.
+    auto warp_wait = [&](int b, uint32_t parity) -> bool {
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bars[b], parity, kWaitNs));
+        if (!ok && lane == 0) {
+            atomicOr(err, kErrTimeout);
+            *failed = 1;
         }
-        __syncthreads();
-        if (!*flag) return false;
-        // The phase is complete, so this returns at once; every thread
-        // observes the completion and so acquires the TMA-written data.
-        if (!mbar_wait_bounded(&bars[b], parity, kWaitNs)) atomicOr(err, kErrTimeout);
-        return true;
+        return ok;
     };
-    if (!uniform_wait(0, 0)) return;
+    const bool hog_ok = warp_wait(0, 0);
 
     // ---- 2. L2-Hys scale factors of every block of the region
-    for (int i = tid; i < RBY * FP; i += kThreads) {
-        const int by = i / FP, bx = i - by * FP;
-        float i1 = 0.f, i2 = 0.f;
-        if (bx < RBX) {
-            float s = 0.f;
+    if (hog_ok) {
+        for (int i = tid; i < RBY * FP; i += kThreads) {
+            const int by = i / FP, bx = i - by * FP;
+            float i1 = 0.f, i2 = 0.f;
+            if (bx < RBX) {
+                float s = 0.f;
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+                for (int q = 0; q < 4; ++q)
 #pragma unroll
-                for (int b = 0; b < kHogBins; ++b) {
-                    const float v = hog[b][by + (q >> 1)][bx + (q & 1)];
-                    s = fmaf(v, v, s);
-                }
-            i1 = 1.0f / sqrtf(s + 1.0f);
-            float s2 = 0.f;
+                    for (int b = 0; b < kHogBins; ++b) {
+                        const float v = hog[b][by + (q >> 1)][bx + (q & 1)];
+                        s = fmaf(v, v, s);
+                    }
+                i1 = 1.0f / sqrtf(s + 1.0f);
+                float s2 = 0.f;
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+                for (int q = 0; q < 4; ++q)
 #pragma unroll
-                for (int b = 0; b < kHogBins; ++b) {
-                    const float u = fminf(hog[b][by + (q >> 1)][bx + (q & 1)] * i1, clip);
-                    s2 = fmaf(u, u, s2);
-                }
-            i2 = 1.0f / sqrtf(s2 + 1e-6f);
+                    for (int b = 0; b < kHogBins; ++b) {
+                        const float u = fminf(hog[b][by + (q >> 1)][bx + (q & 1)] * i1, clip);
+                        s2 = fmaf(u, u, s2);
+                    }
+                i2 = 1.0f / sqrtf(s2 + 1e-6f);
+            }
+            inv1[by][bx] = i1;
+            inv2[by][bx] = i2;
         }
-        inv1[by][bx] = i1;
-        inv2[by][bx] = i2;
     }
     __syncthreads();
 
-    // ---- 3. channel rounds
+    // ---- 3. channel rounds. Warps are not kept in step: a warp waits only
+    // for the LBP chunk of its round, and the last warp to finish with a
+    // buffer refills it with the chunk two rounds ahead, so one warp's
+    // plane building overlaps another's FMAs.
     const int lx = lane % LX, ly = lane / LX;
     float acc[RY][4];
 #pragma unroll
@@ -232,14 +239,10 @@ __device__ void svm_tile(const SvmItem &it, const LevelDesc &L, const CUtensorMa
         for (int x = 0; x < 4; ++x) acc[q][x] = 0.f;
     float(*F)[FP] = feat[warp];
 
-    for (int round = 0; round < kRounds; ++round) {
+    for (int round = 0; round < kRounds && !*failed; ++round) {
         const int t = kWarps * round + warp;
-        const int buf = (round - kFirstLbpRound) & 1;
-        if (round >= kFirstLbpRound) {
-            const uint32_t parity = ((round - kFirstLbpRound) >> 1) & 1;
-            if (!uniform_wait(1 + buf, parity)) return;
-            if (buf == 0) lbp_parity0 = parity ^ 1; else lbp_parity1 = parity ^ 1;
-        }
+        const int k = round - kFirstLbpRound, buf = k & 1;
+        if (round >= kFirstLbpRound && !warp_wait(1 + buf, (k >> 1) & 1)) break;
         if (t < kFeat) {
             // template slice of channel t: w[t][i][0..7] (warp-uniform loads)
             float w[kWinBH][kWinBW];
@@ -313,16 +316,29 @@ __device__ void svm_tile(const SvmItem &it, const LevelDesc &L, const CUtensorMa
                         for (int x = 0; x < 4; ++x) acc[q][x] = fmaf(f[x + j], w[i][j], acc[q][x]);
                 }
             }
-            __syncwarp();
         }
-        __syncthreads();  // every warp is done with this round's LBP buffer
-        if (round >= kFirstLbpRound && round + 2 < kRounds && tid == 0) {
-            // refill the freed buffer with the chunk two rounds ahead
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(&bars[1 + buf], SH::kLbpBytes);
-            tma_load_3d(&lbp[buf][0][0][0], lbp_map, &bars[1 + buf], it.wx0, cy,
-                        kWarps * (round + 2) - kHogDim);
+        __syncwarp();  // the plane and the LBP chunk are no longer read by this warp
+        if (round >= kFirstLbpRound && lane == 0) {
+            __threadfence_block();
+            if (atomicAdd(&released[buf], 1) % kWarps == kWarps - 1 && round + 2 < kRounds) {
+                // last warp out of this buffer: refill it with the chunk two rounds ahead
+                __threadfence_block();
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issued[buf] += 1;
+                mbar_expect_tx(&bars[1 + buf], SH::kLbpBytes);
+                tma_load_3d(&lbp[buf][0][0][0], lbp_map, &bars[1 + buf], it.wx0, cy,
+                            kWarps * (round + 2) - kHogDim);
+            }
         }
+    }
+    __syncthreads();
+    if (*failed) {
+        // drain the copies still in flight (bounded) before the CTA leaves
+        if (tid == 0) {
+            mbar_wait_bounded(&bars[0], 0, kWaitNs);
+            for (int b = 0; b < 2; ++b) mbar_wait_bounded(&bars[1 + b], (issued[b] - 1) & 1, kWaitNs);
+        }
+        return;
     }
 
     // ---- 4. deterministic cross-warp reduction
@@ -343,6 +359,18 @@ __device__ void svm_tile(const SvmItem &it, const LevelDesc &L, const CUtensorMa
     }
 }
 
+__device__ __forceinline__ SvmShapeInfo svm_shape_dev(int s) {
+    switch (s) {
+        case 0: return {S0::TW, S0::TH, 0, 0, 0};
+        case 1: return {S1::TW, S1::TH, 0, 0, 0};
+        case 2: return {S2::TW, S2::TH, 0, 0, 0};
+        case 3: return {S3::TW, S3::TH, 0, 0, 0};
+        case 4: return {S4::TW, S4::TH, 0, 0, 0};
+        case 5: return {S5::TW, S5::TH, 0, 0, 0};
+        default: return {S6::TW, S6::TH, 0, 0, 0};
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     k_svm(const __grid_constant__ SvmMaps maps, const LevelDesc *__restrict__ levels,
           const float *__restrict__ wt, float bias, float clip, float *__restrict__ scores,
@@ -355,12 +383,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const LevelDesc L = levels[it.level];
     if (s_flag && !s_flag[blockIdx.x]) {
         // sparse path: no kept window in this tile; its windows are not scored
-        const SvmShapeInfo sh = it.shape == 0 ? SvmShapeInfo{S0::TW, S0::TH, 0, 0, 0}
-                               : it.shape == 1 ? SvmShapeInfo{S1::TW, S1::TH, 0, 0, 0}
-                               : it.shape == 2 ? SvmShapeInfo{S2::TW, S2::TH, 0, 0, 0}
-                                               : SvmShapeInfo{S3::TW, S3::TH, 0, 0, 0};
-        for (int i = threadIdx.x; i < sh.tw * sh.th; i += kThreads) {
-            const int wy = it.wy0 + i / sh.tw, wx = it.wx0 + i % sh.tw;
+        const SvmShapeInfo sh = svm_shape_dev(it.shape);
+        const int tw = sh.tw, th = sh.th;
+        for (int i = threadIdx.x; i < tw * th; i += kThreads) {
+            const int wy = it.wy0 + i / tw, wx = it.wx0 + i % tw;
             if (wy < L.rows && wx < L.cols) scores[L.score_off + (int64_t)wy * L.cols + wx] = -INFINITY;
         }
         return;
@@ -369,7 +395,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         case 0: svm_tile<S0, 4>(it, L, &maps.hog[0], &maps.lbp[0], wt, bias, clip, scores, err, smem); break;
         case 1: svm_tile<S1, 4>(it, L, &maps.hog[1], &maps.lbp[1], wt, bias, clip, scores, err, smem); break;
         case 2: svm_tile<S2, 2>(it, L, &maps.hog[2], &maps.lbp[2], wt, bias, clip, scores, err, smem); break;
-        default: svm_tile<S3, 2>(it, L, &maps.hog[3], &maps.lbp[3], wt, bias, clip, scores, err, smem); break;
+        case 3: svm_tile<S3, 2>(it, L, &maps.hog[3], &maps.lbp[3], wt, bias, clip, scores, err, smem); break;
+        case 4: svm_tile<S4, 1>(it, L, &maps.hog[4], &maps.lbp[4], wt, bias, clip, scores, err, smem); break;
+        case 5: svm_tile<S5, 3>(it, L, &maps.hog[5], &maps.lbp[5], wt, bias, clip, scores, err, smem); break;
+        default: svm_tile<S6, 1>(it, L, &maps.hog[6], &maps.lbp[6], wt, bias, clip, scores, err, smem); break;
     }
 }
 
@@ -381,7 +410,10 @@ SvmShapeInfo svm_shape(int s) {
         case 0: r = {S0::TW, S0::TH, S0::HX, S0::LXB, S0::CR}; break;
         case 1: r = {S1::TW, S1::TH, S1::HX, S1::LXB, S1::CR}; break;
         case 2: r = {S2::TW, S2::TH, S2::HX, S2::LXB, S2::CR}; break;
-        default: r = {S3::TW, S3::TH, S3::HX, S3::LXB, S3::CR}; break;
+        case 3: r = {S3::TW, S3::TH, S3::HX, S3::LXB, S3::CR}; break;
+        case 4: r = {S4::TW, S4::TH, S4::HX, S4::LXB, S4::CR}; break;
+        case 5: r = {S5::TW, S5::TH, S5::HX, S5::LXB, S5::CR}; break;
+        default: r = {S6::TW, S6::TH, S6::HX, S6::LXB, S6::CR}; break;
     }
     return r;
 }

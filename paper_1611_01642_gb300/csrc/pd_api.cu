@@ -32,7 +32,16 @@ namespace {
 
 constexpr int64_t kAlign = 256;
 // relative time of one K4 tile per shape (model; the autotuner replaces it)
-const float kDefaultTileCost[kSvmShapes] = {1.0f, 1.0f, 0.6f, 0.6f};
+// Relative per-tile costs of the dense path, from timings on GB300: a tile
+// costs about 1 (512 windows) or 0.6 (256 windows); the three small shapes
+// are priced so that dense plans never take them (measured whole-plan times
+// were no better with them); the sparse path, where small tiles skip more,
+// prices them itself.
+const float kDefaultTileCost[kSvmShapes] = {1.0f, 1.0f, 0.6f, 0.6f, 1.0f, 1.0f, 1.0f};
+// Sparse path: a tile is computed only if it holds a kept window, so narrow
+// tiles skip more; the 64-wide shapes and the smallest ones lost on GB300
+// (whole-path timings of the proposal workload).
+const float kSparseTileCost[kSvmShapes] = {1.0f, 1e3f, 0.6f, 1e3f, 1e3f, 0.82f, 1e3f};
 
 int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
@@ -230,7 +239,8 @@ struct pd_handle {
     // tensor maps over the atlases, one pair per K4 tile shape
     CUtensorMap hog_map[kSvmShapes]{}, lbp_map[kSvmShapes]{};
     float tile_cost[kSvmShapes] = {kDefaultTileCost[0], kDefaultTileCost[1], kDefaultTileCost[2],
-                                   kDefaultTileCost[3]};
+                                   kDefaultTileCost[3], kDefaultTileCost[4], kDefaultTileCost[5],
+                                   kDefaultTileCost[6]};
     // last batch
     Plan plan;
     // cached plan + captured graph for a repeated batch shape
@@ -735,8 +745,8 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
         invalidate_cache(h);
         p.clear();
         for (int f = 0; f < n_frames; ++f) {
-            int r = plan_frame(p, h->p, d_frames[f], widths[f], heights[f], pitches[f], h->tile_cost,
-                               h->proposal);
+            int r = plan_frame(p, h->p, d_frames[f], widths[f], heights[f], pitches[f],
+                               h->proposal ? kSparseTileCost : h->tile_cost, h->proposal);
             if (r != PD_OK) return fail(h, r, "frame %d: planning failed", f);
         }
         if (p.atlas_rows > h->atlas.rows || p.pyr_bytes > h->pyr_cap || p.score_floats > h->score_cap ||

@@ -59,7 +59,7 @@ constexpr int kResizeTW = 128;  // source tile width  (pixels)
 constexpr int kResizeTH = 32;   // source tile height (pixels)
 constexpr int kCellTW = 15;     // cells per cell tile along x (128 threads = 8*15+8 columns)
 constexpr int kCellTH = 8;      // cells per cell tile along y
-constexpr int kSvmShapes = 4;   // K4 tile shapes: 32x16, 64x8, 32x8, 64x4 windows
+constexpr int kSvmShapes = 7;   // K4 tile shapes: 32x16, 64x8, 32x8, 64x4, 64x2, 32x12, 32x4 windows
 
 struct SvmShapeInfo {
     int tw, th;     // windows per tile along x / y

@@ -362,7 +362,7 @@ def test_errors_are_reported(template):
         d.close()
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2, 3])
+@pytest.mark.parametrize("shape", range(7))
 def test_window_scores_every_tile_shape(template, shape):
     # force one K4 tile shape through the planner's cost table
     from paper_1611_01642_gb300 import build as bld
