@@ -52,6 +52,8 @@ def parse_args(argv=None):
                     help="frames the CPU oracle times for cpu_baseline (bounded sample)")
     ap.add_argument("--proposal-steps", type=int, default=10,
                     help="timed steps of the 16x1920x1080 plain-vs-sparse comparison (0: skip)")
+    ap.add_argument("--proposal-frames", type=int, default=16,
+                    help="frames of the proposal comparison (16 is the workload; fewer for profiler captures)")
     return ap.parse_args(argv)
 
 
@@ -234,7 +236,7 @@ def run_proposal(args, pd, torch, flush):
     from paper_1611_01642_gb300 import proposal as prop
     params, meta = prop.load_checkpoint(PROPOSAL_CKPT)
     tau = float(meta["keep_logit_threshold"])
-    imgs = synth.make_frames(4)
+    imgs = synth.make_frames(4, limit=args.proposal_frames)
     frames = [torch.from_numpy(im).cuda() for im in imgs]
     w, b = load_template()
     det = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=len(frames), max_width=1920, max_height=1080,
@@ -274,8 +276,8 @@ def run_proposal(args, pd, torch, flush):
     det.close()
     names = ["pyramid", "cells", "norm_svm", "nms", "proposal"]
     return {
-        "workload": "16 x 1920x1080 u8 frames (scene recipe 4: Poisson(10) silhouettes, 48 px..0.8H), "
-                    "pyramid factor 1.05 (44 levels)",
+        "workload": f"{len(imgs)} x 1920x1080 u8 frames (scene recipe 4: Poisson(10) silhouettes, "
+                    "48 px..0.8H), pyramid factor 1.05 (44 levels)",
         "checkpoint": os.path.relpath(PROPOSAL_CKPT, ROOT), "keep_logit_threshold": tau,
         "plain_frames_per_s": len(frames) / (ms_plain / 1e3),
         "sparse_frames_per_s": len(frames) / (ms_sparse / 1e3),

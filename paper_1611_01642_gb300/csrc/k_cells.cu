@@ -31,7 +31,7 @@
 //    cell grid). The vertical part is accumulated per column in the thread's
 //    own shared-memory slots (no atomics, fixed row order); the horizontal
 //    part is a fixed-order weighted sum over the 16 columns that reach each
-//    cell. The result is therefore deterministic.
+//    cell, one thread per (cell, bin). The result is therefore deterministic.
 //
 // The walk proceeds in bands of 8 rows: band k covers pixel rows
 // [8(cy0+k)-4, 8(cy0+k)+4), which vote only into cell rows cy0+k-1 and
@@ -59,8 +59,8 @@ constexpr int kLbpWords = (kLbpBins + 1) / 2;  // two 16-bit counters per word
 struct CellSmem {
     int4 yv[kPixRows];                      // per pixel row: ring slot / weight of its two cell votes
     float R[kRing][kHogBins][kRPitch];      // vertical HOG partial sums per column
-    float SA[kCols / 8][kHogBins];          // per 8-column group: votes to its left cell
-    float SB[kCols / 8][kHogBins];          // per 8-column group: votes to its own cell
+    float WA[kCols];                        // per column: weight of its vote to the left cell of its group
+    float WB[kCols];                        // per column: weight of its vote to its group's own cell
     uint32_t cnt[kRing][kTW][kLbpWords];    // LBP counts of the open cell rows
     uint8_t map[256];                       // LBP code -> uniform bin
     uint8_t pix[kPixRows][kPixCols];        // [8cy0-5, 8cy0+69) x [8cx0-5, 8cx0+125), clamped
@@ -165,6 +165,8 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
         wA = (c0 == left ? w0 : 0.f) + (c1 == left ? w1 : 0.f);
         wB = (c0 == own ? w0 : 0.f) + (c1 == own ? w1 : 0.f);
     }
+    S.WA[tid] = wA;
+    S.WB[tid] = wB;
     const int n_rows = min(kTH, Hc - it.cy0);  // cell rows of this tile inside the level
 
     for (int band = 0; band <= n_rows; ++band) {
@@ -226,45 +228,53 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
             }
         }
         __syncthreads();
-        // ---- cell row cyl = band - 1 is final: horizontal HOG reduction, stores
+        // ---- cell row cyl = band - 1 is final: horizontal HOG sums, stores
         const int cyl = band - 1;
         if (cyl >= 0) {
             const int cy = it.cy0 + cyl;
-            float(*R)[kRPitch] = S.R[cyl & 1];
-            // 8-lane segmented sums of the column votes (fixed shuffle tree)
-#pragma unroll
-            for (int b = 0; b < kHogBins; ++b) {
-                const float v = R[b][tid];
-                float a = wA * v, c = wB * v;
-#pragma unroll
-                for (int o = 1; o < 8; o <<= 1) {
-                    a += __shfl_xor_sync(0xffffffffu, a, o);
-                    c += __shfl_xor_sync(0xffffffffu, c, o);
-                }
-                if ((tid & 7) == 0) {
-                    S.SA[tid >> 3][b] = a;
-                    S.SB[tid >> 3][b] = c;
-                }
-            }
-            __syncthreads();
-            for (int i = tid; i < kTW * kHogBins; i += kThreads) {
-                const int cxo = i % kTW, b = i / kTW;
+            const int64_t row = (int64_t)(L.cell_row + cy) * atlas.pitch;
+            const float(*R)[kRPitch] = S.R[cyl & 1];
+            // HOG: one thread per (bin, cell): own group with WB, next group with WA
+            for (int o = tid; o < kHogBins * kTW; o += kThreads) {
+                const int b = o / kTW, cxo = o - b * kTW;
                 const int cx = it.cx0 + cxo;
                 if (cx >= Wc) continue;
-                const float acc = S.SB[cxo][b] + S.SA[cxo + 1][b];
-                atlas.hog[(int64_t)b * atlas.hog_plane + (int64_t)(L.cell_row + cy) * atlas.pitch + cx] = acc;
+                const float4 *r4 = reinterpret_cast<const float4 *>(&R[b][8 * cxo]);
+                const float4 *wb4 = reinterpret_cast<const float4 *>(&S.WB[8 * cxo]);
+                const float4 *wa4 = reinterpret_cast<const float4 *>(&S.WA[8 * cxo + 8]);
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const float4 v = r4[k], w = wb4[k];
+                    acc = fmaf(w.x, v.x, acc);
+                    acc = fmaf(w.y, v.y, acc);
+                    acc = fmaf(w.z, v.z, acc);
+                    acc = fmaf(w.w, v.w, acc);
+                }
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const float4 v = r4[2 + k], w = wa4[k];
+                    acc = fmaf(w.x, v.x, acc);
+                    acc = fmaf(w.y, v.y, acc);
+                    acc = fmaf(w.z, v.z, acc);
+                    acc = fmaf(w.w, v.w, acc);
+                }
+                atlas.hog[(int64_t)b * atlas.hog_plane + row + cx] = acc;
             }
-            for (int i = tid; i < kLbpBins * kTW; i += kThreads) {
-                const int cxo = i % kTW, bin = i / kTW;
+            // LBP: one thread per counter word (two bins) of a cell
+            for (int o = tid; o < kLbpWords * kTW; o += kThreads) {
+                const int wd = o / kTW, cxo = o - wd * kTW;
                 const int cx = it.cx0 + cxo;
                 if (cx >= Wc) continue;
-                const uint32_t v = S.cnt[cyl & 1][cxo][bin >> 1];
-                atlas.lbp[(int64_t)bin * atlas.lbp_plane + (int64_t)(L.cell_row + cy) * atlas.pitch + cx] =
-                    (uint8_t)((v >> ((bin & 1) << 4)) & 0xffffu);
+                const uint32_t v = S.cnt[cyl & 1][cxo][wd];
+                atlas.lbp[(int64_t)(2 * wd) * atlas.lbp_plane + row + cx] = (uint8_t)(v & 0xffffu);
+                if (2 * wd + 1 < kLbpBins)
+                    atlas.lbp[(int64_t)(2 * wd + 1) * atlas.lbp_plane + row + cx] = (uint8_t)(v >> 16);
             }
             __syncthreads();
             // recycle the slots of cell row cyl for cell row cyl + 2
-            for (int i = tid; i < kHogBins * kRPitch; i += kThreads) (&R[0][0])[i] = 0.f;
+            float4 *R4 = reinterpret_cast<float4 *>(&S.R[cyl & 1][0][0]);
+            for (int i = tid; i < kHogBins * kRPitch / 4; i += kThreads) R4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int i = tid; i < kTW * kLbpWords; i += kThreads) (&S.cnt[cyl & 1][0][0])[i] = 0u;
             __syncthreads();
         }
