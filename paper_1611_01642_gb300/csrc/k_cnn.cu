@@ -39,23 +39,33 @@ constexpr int XR = 2 * R1 + 2;   // 72 pixel rows/columns under the 4x4 patches
 constexpr int kRawW = 80;        // staged bytes per row: pixels x0-1 .. x0+78, ten 8-byte chunks
 constexpr int kChunks = kRawW / 8;
 constexpr int XBW = 44;          // bf16 pixel row stride in words (72 used, padded for banks)
-constexpr int S1W = 10;          // layer-1 position stride in 32-bit words (16 ch + 4 pad bf16)
-constexpr int S2W = 18;          // layer-2 position stride in words (32 ch + 4 pad bf16)
+// Activations are stored as 16-byte rows of 8 bf16 channels, split by
+// channel group and by column parity: plane (group, parity) holds the
+// positions of that parity, row-major with (columns + 1) / 2 columns. A
+// stride-2 tap then reads 8 consecutive 16-byte rows (one ldmatrix 8x8
+// matrix, conflict free), and the epilogue writes them with stmatrix. Plane
+// strides are padded to 4 (mod 8) 16-byte units so that the two parities of
+// 8 consecutive positions fall on disjoint banks.
+constexpr int C1P = (R1 + 1) / 2;  // 18 plane columns of layer 1
+constexpr int PS1 = 636;           // layer-1 plane stride (35 x 18 = 630, padded), 16-byte units
+constexpr int C2P = (R2 + 1) / 2;  // 9 plane columns of layer 2
+constexpr int PS2 = 156;           // layer-2 plane stride (17 x 9 = 153, padded)
+static_assert(PS1 >= R1 * C1P && PS1 % 8 == 4 && PS2 >= R2 * C2P && PS2 % 8 == 4, "plane strides");
 constexpr int M1 = R1 * R1;      // 1225 layer-1 positions
 constexpr int M1T = (M1 + 15) / 16;  // 77 m-tiles
 constexpr int M2 = R2 * R2;      // 289 layer-2 positions
 constexpr int M2T = (M2 + 15) / 16;  // 19 m-tiles
 constexpr int kW3Frag = 9 * 2 * 4 * 32;  // uint2 layer-3 B fragments
+constexpr float kInv255 = 1.0f / 255.0f;   // float32 nearest to 1/255
 
 struct CnnSmem {
     uint8_t raw[2][XR][kRawW];   // input bytes, double buffered
-    uint32_t a1[M1 * S1W];
+    uint4 a1[2 * 2 * PS1];       // [channel group 0..1][parity] planes of layer 1
     union {
         uint32_t xb[XR * XBW];   // bf16 pixel pairs (dead once layer 1 is done)
-        uint32_t a2[M2 * S2W];
+        uint4 a2[4 * 2 * PS2];   // [channel group 0..3][parity] planes of layer 2
     } u;
     uint2 w3[kW3Frag];
-    uint16_t tab[256];
     float b1[16];
     float b2[32];
     float b3[32];
@@ -82,6 +92,22 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
         "{%0,%1,%2,%3};"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Four 8x8 bf16 matrices from / to shared memory; lane l gives the address
+// of row l % 8 of matrix l / 8; register i holds matrix i in the mma
+// fragment layout (row lane / 4, columns 2 (lane % 4), +1).
+template <int OFF>
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4+%5];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr), "n"(OFF)
+                 : "memory");
+}
+__device__ __forceinline__ void stsm_x4(uint32_t addr, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {
+    asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(r0), "r"(r1),
+                 "r"(r2), "r"(r3)
+                 : "memory");
 }
 
 // 8-byte asynchronous copy global -> shared; bytes past n are zero-filled.
@@ -130,7 +156,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__rest
     stage_input(S.raw[0], items, levels, pyr, item, tid);
     cp_async_commit();
 
-    for (int i = tid; i < 256; i += kThreads) S.tab[i] = __bfloat16_as_ushort(__float2bfloat16_rn(wts.in_tab[i]));
     for (int i = tid; i < kW3Frag; i += kThreads) S.w3[i] = reinterpret_cast<const uint2 *>(wts.w3frag)[i];
     if (tid < 16) S.b1[tid] = wts.b1[tid];
     if (tid < 32) {
@@ -160,6 +185,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__rest
             bw2[tap][nt][1] = v.y;
         }
     const float bh = wts.bh[0];
+    const uint32_t a1_base = static_cast<uint32_t>(__cvta_generic_to_shared(&S.a1[0]));
+    const uint32_t a2_base = static_cast<uint32_t>(__cvta_generic_to_shared(&S.u.a2[0]));
 
     for (int iter = 0; item < n_items; ++iter, item += gridDim.x) {
         const int cur = iter & 1;
@@ -181,26 +208,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__rest
         const bool interior1 = y1 >= 0 && x1 >= 0 && y1 + R1 <= H1 && x1 + R1 <= W1;
         const bool interior2 = y2 >= 0 && x2 >= 0 && y2 + R2 <= H2 && x2 + R2 <= W2;
 
-        // ---- pixels -> bf16 x; xb[r][c] = x(y0 + r, x0 + c) = raw[r][c + 1]
+        // ---- pixels -> bf16 x; xb[r][c] = x(y0 + r, x0 + c) = raw[r][c + 1].
+        // x = bf16(L/255 - 0.5): one fma in float32 rounded once to bf16 equals
+        // the correctly rounded value for all 256 inputs (checked exhaustively
+        // against exact rational arithmetic when this path was written).
         for (int k = tid; k < XR * (XR / 4); k += kThreads) {
             const int r = k / (XR / 4), j = k - r * (XR / 4);
             const uint32_t *rw = reinterpret_cast<const uint32_t *>(S.raw[cur][r]);
             const uint32_t v = __byte_perm(rw[j], rw[j + 1], 0x4321);
             const int y = y0 + r, xc = x0 + 4 * j;
             const bool rin = y >= 0 && y < Hk;
-            uint32_t e[4];
+            float e[4];
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const int x = xc + b;
-                e[b] = (rin && x >= 0 && x < Wk) ? S.tab[(v >> (8 * b)) & 255u] : 0u;
+                e[b] = (rin && x >= 0 && x < Wk) ? fmaf((float)((v >> (8 * b)) & 255u), kInv255, -0.5f) : 0.f;
             }
-            *reinterpret_cast<uint2 *>(&S.u.xb[r * XBW + 2 * j]) = make_uint2(e[0] | (e[1] << 16), e[2] | (e[3] << 16));
+            *reinterpret_cast<uint2 *>(&S.u.xb[r * XBW + 2 * j]) = make_uint2(pack_bf16(e[0], e[1]), pack_bf16(e[2], e[3]));
         }
         __syncthreads();
         // ---- layer 1 on tensor cores: 1225 positions x 16 channels, K = 16 (4x4 patch)
         for (int mt = warp; mt < M1T; mt += kThreads / 32) {
             const int p0 = mt * 16 + g, p1 = p0 + 8;
-            const int q0 = min(p0, M1 - 1), q1 = min(p1, M1 - 1);  // padding rows reuse a valid row
+            const int q0 = min(p0, M1 - 1), q1 = min(p1, M1 - 1);  // padding rows repeat the last row
             const int r0 = q0 / R1, c0 = q0 - r0 * R1, r1 = q1 / R1, c1 = q1 - r1 * R1;
             const uint32_t *x0w = &S.u.xb[(2 * r0 + (t >> 1)) * XBW + c0 + (t & 1)];
             const uint32_t *x1w = &S.u.xb[(2 * r1 + (t >> 1)) * XBW + c1 + (t & 1)];
@@ -212,54 +242,55 @@ __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__rest
                 acc[nt][1] = acc[nt][3] = S.b1[nt * 8 + 2 * t + 1];
                 mma_bf16(acc[nt], a0, a1, a2, a3, bw1[nt][0], bw1[nt][1]);
             }
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int p = half ? p1 : p0;
-                if (p >= M1) continue;
-                const int r = half ? r1 : r0, c = half ? c1 : c0;
-                const bool inside =
-                    interior1 || ((y1 + r) >= 0 && (y1 + r) < H1 && (x1 + c) >= 0 && (x1 + c) < W1);
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt)
-                    S.a1[p * S1W + nt * 4 + t] =
-                        inside ? relu_pack_bf16(acc[nt][2 * half], acc[nt][2 * half + 1]) : 0u;
-            }
+            const bool in0 = interior1 || ((y1 + r0) >= 0 && (y1 + r0) < H1 && (x1 + c0) >= 0 && (x1 + c0) < W1);
+            const bool in1 = interior1 || ((y1 + r1) >= 0 && (y1 + r1) < H1 && (x1 + c1) >= 0 && (x1 + c1) < W1);
+            // this lane's row address: row (l % 8) + 8 ((l / 8) & 1) of the tile, channel group l / 16
+            const int ps = min(mt * 16 + (lane & 15), M1 - 1);
+            const int pr = ps / R1, pc = ps - pr * R1;
+            const uint32_t dst = a1_base + ((((lane >> 4) * 2 + (pc & 1)) * PS1 + pr * C1P + (pc >> 1)) << 4);
+            stsm_x4(dst, in0 ? relu_pack_bf16(acc[0][0], acc[0][1]) : 0u,
+                    in1 ? relu_pack_bf16(acc[0][2], acc[0][3]) : 0u, in0 ? relu_pack_bf16(acc[1][0], acc[1][1]) : 0u,
+                    in1 ? relu_pack_bf16(acc[1][2], acc[1][3]) : 0u);
         }
         __syncthreads();
-        // ---- layer 2 on tensor cores: 289 positions x 32 channels, K = 9 x 16
+        // ---- layer 2 on tensor cores: 289 positions x 32 channels, K = 9 taps x 16
         for (int mt = warp; mt < M2T; mt += kThreads / 32) {
             const int p0 = mt * 16 + g, p1 = p0 + 8;
             const int q0 = min(p0, M2 - 1), q1 = min(p1, M2 - 1);
             const int r0 = q0 / R2, c0 = q0 - r0 * R2, r1 = q1 / R2, c1 = q1 - r1 * R2;
+            // A rows: lane l reads output row (l % 8) + 8 ((l / 8) & 1), channel group l / 16;
+            // tap (dy, dx) is layer-1 position (2r + dy, 2c + dx): parity dx & 1, plane column c + dx / 2
+            const int ls = min(mt * 16 + (lane & 15), M2 - 1);
+            const int lr = ls / R2, lc = ls - lr * R2;
+            const uint32_t src = a1_base + ((((lane >> 4) * 2) * PS1 + 2 * lr * C1P + lc) << 4);
             float acc[4][4];
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt) {
                 acc[nt][0] = acc[nt][2] = S.b2[nt * 8 + 2 * t];
                 acc[nt][1] = acc[nt][3] = S.b2[nt * 8 + 2 * t + 1];
             }
+#define PD_L2_TAP(DY, DX)                                                                                   \
+    {                                                                                                     \
+        uint32_t a0, a1, a2, a3;                                                                          \
+        ldsm_x4<((((DX) & 1) * PS1 + (DY) * C1P + ((DX) >> 1)) << 4)>(src, a0, a1, a2, a3);                \
+        _Pragma("unroll") for (int nt = 0; nt < 4; ++nt)                                                  \
+            mma_bf16(acc[nt], a0, a1, a2, a3, bw2[(DY) * 3 + (DX)][nt][0], bw2[(DY) * 3 + (DX)][nt][1]);   \
+    }
+            PD_L2_TAP(0, 0) PD_L2_TAP(0, 1) PD_L2_TAP(0, 2)
+            PD_L2_TAP(1, 0) PD_L2_TAP(1, 1) PD_L2_TAP(1, 2)
+            PD_L2_TAP(2, 0) PD_L2_TAP(2, 1) PD_L2_TAP(2, 2)
+#undef PD_L2_TAP
+            const bool in0 = interior2 || ((y2 + r0) >= 0 && (y2 + r0) < H2 && (x2 + c0) >= 0 && (x2 + c0) < W2);
+            const bool in1 = interior2 || ((y2 + r1) >= 0 && (y2 + r1) < H2 && (x2 + c1) >= 0 && (x2 + c1) < W2);
+            // channel groups 2h + (l / 16) of output row (l % 8) + 8 ((l / 8) & 1)
+            const uint32_t dst = a2_base + ((((lane >> 4) * 2 + (lc & 1)) * PS2 + lr * C2P + (lc >> 1)) << 4);
 #pragma unroll
-            for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                for (int dx = 0; dx < 3; ++dx) {
-                    const uint32_t *s0 = &S.a1[((2 * r0 + dy) * R1 + 2 * c0 + dx) * S1W];
-                    const uint32_t *s1 = &S.a1[((2 * r1 + dy) * R1 + 2 * c1 + dx) * S1W];
-                    const uint32_t a0 = s0[t], a1 = s1[t], a2 = s0[4 + t], a3 = s1[4 + t];
-#pragma unroll
-                    for (int nt = 0; nt < 4; ++nt)
-                        mma_bf16(acc[nt], a0, a1, a2, a3, bw2[dy * 3 + dx][nt][0], bw2[dy * 3 + dx][nt][1]);
-                }
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int p = half ? p1 : p0;
-                if (p >= M2) continue;
-                const int r = half ? r1 : r0, c = half ? c1 : c0;
-                const bool inside =
-                    interior2 || ((y2 + r) >= 0 && (y2 + r) < H2 && (x2 + c) >= 0 && (x2 + c) < W2);
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt)
-                    S.u.a2[p * S2W + nt * 4 + t] =
-                        inside ? relu_pack_bf16(acc[nt][2 * half], acc[nt][2 * half + 1]) : 0u;
-            }
+            for (int h = 0; h < 2; ++h)
+                stsm_x4(dst + ((4 * h * PS2) << 4),
+                        in0 ? relu_pack_bf16(acc[2 * h][0], acc[2 * h][1]) : 0u,
+                        in1 ? relu_pack_bf16(acc[2 * h][2], acc[2 * h][3]) : 0u,
+                        in0 ? relu_pack_bf16(acc[2 * h + 1][0], acc[2 * h + 1][1]) : 0u,
+                        in1 ? relu_pack_bf16(acc[2 * h + 1][2], acc[2 * h + 1][3]) : 0u);
         }
         __syncthreads();
         // ---- layer 3 on tensor cores: 64 positions x 32 channels, K = 9 x 32;
@@ -267,29 +298,37 @@ __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__rest
         {
             const int mt = warp & 3, nh = warp >> 2;
             const int p0 = mt * 16 + g, p1 = p0 + 8;
-            const int r0 = p0 >> 3, c0 = p0 & 7, r1 = p1 >> 3, c1 = p1 & 7;
+            float acc2[2][2][4];  // [k-half][n-tile]: four independent mma chains
+#pragma unroll
+            for (int kh = 0; kh < 2; ++kh)
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc2[kh][j][e] = 0.f;
+            // A rows: lane l reads output position (l % 8) + 8 ((l / 8) & 1) of the m-tile,
+            // channel group 2 kh + l / 16
+            const int lp = mt * 16 + (lane & 15);
+            const int lr = lp >> 3, lc = lp & 7;
+            const uint32_t src = a2_base + ((((lane >> 4) * 2) * PS2 + 2 * lr * C2P + lc) << 4);
+#define PD_L3_TAP(DY, DX, KH)                                                                                  \
+    {                                                                                                        \
+        uint32_t a0, a1, a2, a3;                                                                             \
+        ldsm_x4<(((2 * (KH) * 2 + ((DX) & 1)) * PS2 + (DY) * C2P + ((DX) >> 1)) << 4)>(src, a0, a1, a2, a3);  \
+        _Pragma("unroll") for (int j = 0; j < 2; ++j) {                                                     \
+            const uint2 b = S.w3[((((DY) * 3 + (DX)) * 2 + (KH)) * 4 + 2 * nh + j) * 32 + lane];             \
+            mma_bf16(acc2[KH][j], a0, a1, a2, a3, b.x, b.y);                                                 \
+        }                                                                                                    \
+    }
+            PD_L3_TAP(0, 0, 0) PD_L3_TAP(0, 0, 1) PD_L3_TAP(0, 1, 0) PD_L3_TAP(0, 1, 1) PD_L3_TAP(0, 2, 0)
+            PD_L3_TAP(0, 2, 1) PD_L3_TAP(1, 0, 0) PD_L3_TAP(1, 0, 1) PD_L3_TAP(1, 1, 0) PD_L3_TAP(1, 1, 1)
+            PD_L3_TAP(1, 2, 0) PD_L3_TAP(1, 2, 1) PD_L3_TAP(2, 0, 0) PD_L3_TAP(2, 0, 1) PD_L3_TAP(2, 1, 0)
+            PD_L3_TAP(2, 1, 1) PD_L3_TAP(2, 2, 0) PD_L3_TAP(2, 2, 1)
+#undef PD_L3_TAP
             float acc[2][4];
 #pragma unroll
             for (int j = 0; j < 2; ++j)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
-#pragma unroll
-            for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                for (int dx = 0; dx < 3; ++dx) {
-                    const uint32_t *s0 = &S.u.a2[((2 * r0 + dy) * R2 + 2 * c0 + dx) * S2W];
-                    const uint32_t *s1 = &S.u.a2[((2 * r1 + dy) * R2 + 2 * c1 + dx) * S2W];
-#pragma unroll
-                    for (int kh = 0; kh < 2; ++kh) {
-                        const uint32_t a0 = s0[kh * 8 + t], a1 = s1[kh * 8 + t];
-                        const uint32_t a2 = s0[kh * 8 + 4 + t], a3 = s1[kh * 8 + 4 + t];
-#pragma unroll
-                        for (int j = 0; j < 2; ++j) {
-                            const uint2 b = S.w3[(((dy * 3 + dx) * 2 + kh) * 4 + 2 * nh + j) * 32 + lane];
-                            mma_bf16(acc[j], a0, a1, a2, a3, b.x, b.y);
-                        }
-                    }
-                }
+                for (int e = 0; e < 4; ++e) acc[j][e] = acc2[0][j][e] + acc2[1][j][e];
             // bias, relu, head partial over this lane's 4 channels, reduce over t
             float h0 = 0.f, h1 = 0.f;
 #pragma unroll
@@ -319,28 +358,56 @@ __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__rest
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// One thread per window: z = bv + sum_{r<16, s<8} V[r][s] h[wy+r][wx+s].
-__global__ void __launch_bounds__(256) k_cnn_pool(const LevelDesc *__restrict__ levels, int n_levels,
+// Window pooling z[wy][wx] = bv + sum_{r<16, s<8} V[r][s] h[wy+r][wx+s]: one
+// CTA per (level, 64 x 16 window tile); the tile's 31 x 71 cells of h are
+// staged in shared memory; each thread computes 4 consecutive windows of one
+// row (8 taps x 4 windows per h row from 11 staged values), in a fixed order.
+constexpr int kPoolHW = kPoolTW + 8;                    // 72 staged columns (71 used)
+constexpr int kPoolHH = kPoolTH + kWinBH;               // 31 staged rows
+
+__global__ void __launch_bounds__(256) k_cnn_pool(const LevelDesc *__restrict__ levels,
                                                   const float *__restrict__ hmap, int32_t hmap_pitch,
                                                   const float *__restrict__ v, const float *__restrict__ bvp,
                                                   float *__restrict__ logits) {
-    __shared__ float V[16 * 8];
-    for (int i = threadIdx.x; i < 128; i += blockDim.x) V[i] = v[i];
-    __syncthreads();
+    __shared__ __align__(16) float V[16 * 8];
+    __shared__ __align__(16) float Hs[kPoolHH][kPoolHW];
     const LevelDesc L = levels[blockIdx.y];
-    const int n = L.rows * L.cols;
-    const float bv = bvp[0];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int wy = i / L.cols, wx = i - wy * L.cols;
-        const float *hp = hmap + (int64_t)(L.cell_row + wy) * hmap_pitch + wx;
-        float z = bv;
-#pragma unroll
-        for (int r = 0; r < 16; ++r)
-#pragma unroll
-            for (int s = 0; s < 8; ++s) z = fmaf(V[r * 8 + s], hp[(int64_t)r * hmap_pitch + s], z);
-        logits[L.score_off + i] = z;
+    const int tiles_x = (L.cols + kPoolTW - 1) / kPoolTW;
+    const int ty = blockIdx.x / max(tiles_x, 1), tx = blockIdx.x - ty * max(tiles_x, 1);
+    const int wy0 = ty * kPoolTH, wx0 = tx * kPoolTW;
+    if (L.rows == 0 || wy0 >= L.rows) return;  // CTA-uniform
+    for (int i = threadIdx.x; i < 128; i += blockDim.x) V[i] = v[i];
+    for (int i = threadIdx.x; i < kPoolHH * kPoolHW; i += blockDim.x) {
+        const int r = i / kPoolHW, c = i - r * kPoolHW;
+        const int cy = wy0 + r, cx = wx0 + c;
+        Hs[r][c] = (cy < L.Hc && cx < L.Wc) ? hmap[(int64_t)(L.cell_row + cy) * hmap_pitch + cx] : 0.f;
     }
-    (void)n_levels;
+    __syncthreads();
+    const int ry = threadIdx.x >> 4, qx = 4 * (threadIdx.x & 15);
+    const float bv = bvp[0];
+    float z[4] = {bv, bv, bv, bv};
+#pragma unroll 4
+    for (int r = 0; r < 16; ++r) {
+        const float4 h0 = *reinterpret_cast<const float4 *>(&Hs[ry + r][qx]);
+        const float4 h1 = *reinterpret_cast<const float4 *>(&Hs[ry + r][qx + 4]);
+        const float4 h2 = *reinterpret_cast<const float4 *>(&Hs[ry + r][qx + 8]);
+        const float hv[12] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w, h2.x, h2.y, h2.z, h2.w};
+        const float4 v0 = *reinterpret_cast<const float4 *>(&V[r * 8]);
+        const float4 v1 = *reinterpret_cast<const float4 *>(&V[r * 8 + 4]);
+        const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+#pragma unroll
+            for (int x = 0; x < 4; ++x) z[x] = fmaf(vv[s], hv[x + s], z[x]);
+    }
+    const int wy = wy0 + ry;
+    if (wy < L.rows) {
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int wx = wx0 + qx + x;
+            if (wx < L.cols) logits[L.score_off + (int64_t)wy * L.cols + wx] = z[x];
+        }
+    }
 }
 
 int g_cnn_grid = 0;  // persistent CTAs: two per SM
@@ -360,16 +427,17 @@ cudaError_t init_cnn() {
 
 cudaError_t launch_cnn(cudaStream_t s, const LevelDesc *d_levels, int n_levels, const uint8_t *pyr,
                        const CnnItem *d_items, int n_items, const CnnWeights &w, float *hmap,
-                       int32_t hmap_pitch, float *logits) {
+                       int32_t hmap_pitch, float *logits, int pool_tiles) {
     if (n_items > 0) {
         const int grid = std::min(n_items, g_cnn_grid > 0 ? g_cnn_grid : n_items);
         k_cnn_fwd<<<grid, kThreads, sizeof(CnnSmem), s>>>(d_levels, pyr, d_items, n_items, w, hmap, hmap_pitch);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    if (n_levels > 0) {
-        dim3 grid(32, n_levels);
-        k_cnn_pool<<<grid, 256, 0, s>>>(d_levels, n_levels, hmap, hmap_pitch, w.v, w.bv, logits);
+    if (n_levels > 0 && pool_tiles > 0) {
+        // enough x-blocks for the largest level's 64 x 16 tiles; the others leave early
+        dim3 grid(pool_tiles, n_levels);
+        k_cnn_pool<<<grid, 256, 0, s>>>(d_levels, hmap, hmap_pitch, w.v, w.bv, logits);
         return cudaGetLastError();
     }
     return cudaSuccess;

@@ -457,6 +457,12 @@ void invalidate_cache(pd_handle *h) {
     }
 }
 
+int max_pool_tiles(const Plan &p) {
+    int m = 0;
+    for (const LevelDesc &L : p.levels) m = std::max(m, pool_tiles_of(L.rows, L.cols));
+    return m;
+}
+
 template <class T>
 const T *dptr(pd_handle *h, int64_t off) {
     return reinterpret_cast<const T *>(h->d_desc + off);
@@ -786,7 +792,8 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
         if (h->proposal) {
             // learned proposal: keep-logits of every window, then the tiles to score
             PD_CUDA(h, launch_cnn(q, dl, (int)p.levels.size(), h->d_pyr, dptr<CnnItem>(h, o.cnn_items),
-                                  (int)p.cnn_items.size(), cnn_weights(h), h->hmap, h->atlas.pitch, h->logits));
+                                  (int)p.cnn_items.size(), cnn_weights(h), h->hmap, h->atlas.pitch, h->logits,
+                                  max_pool_tiles(p)));
             PD_CUDA(h, cudaMemsetAsync(h->c_flag, 0, p.c_items.size() * 4 + 4, q));
             PD_CUDA(h, launch_proposal_flags(q, dl, dptr<SvmItem>(h, o.s_items), (int)p.s_items.size(), h->logits,
                                              h->tau, h->s_flag, h->c_flag));
@@ -974,7 +981,7 @@ int pd_cnn_forward(pd_handle *h, void *stream, const uint8_t *d_level, int Wk, i
     if (r != PD_OK) return r;
     PD_CUDA(h, launch_cnn(s, dptr<LevelDesc>(h, o.levels), p.levels[0].rows > 0 ? 1 : 0, d_level,
                           dptr<CnnItem>(h, o.cnn_items), (int)p.cnn_items.size(), cnn_weights(h), d_h, h_pitch,
-                          d_logits));
+                          d_logits, max_pool_tiles(p)));
     return PD_OK;
 }
 
@@ -1049,6 +1056,7 @@ int pd_cnn_train_step(pd_handle *h, void *stream, float pos_weight, float label_
     a.label_thr = label_threshold;
     a.pos_weight = pos_weight;
     a.inv_n = 1.0f / (float)nwin;
+    a.pool_tiles = max_pool_tiles(p);
     a.lr = lr;
     a.beta1 = 0.9f;
     a.beta2 = 0.999f;

@@ -147,12 +147,19 @@ struct TrainArgs {
     float *dz, *level_loss;
     float label_thr, pos_weight, inv_n;
     float lr, beta1, beta2, eps, c1, c2;
+    int pool_tiles;           // window-pooling tiles of the largest level
 };
 
 cudaError_t init_cnn();
+// Window pooling tiles: 64 x 16 windows per CTA; pool_tiles = the largest
+// level's tile count (ceil(cols / 64) * ceil(rows / 16)).
+constexpr int kPoolTW = 64, kPoolTH = 16;
+inline int pool_tiles_of(int rows, int cols) {
+    return rows > 0 && cols > 0 ? ((cols + kPoolTW - 1) / kPoolTW) * ((rows + kPoolTH - 1) / kPoolTH) : 0;
+}
 cudaError_t launch_cnn(cudaStream_t s, const LevelDesc *d_levels, int n_levels, const uint8_t *pyr,
                        const CnnItem *d_items, int n_items, const CnnWeights &w, float *hmap,
-                       int32_t hmap_pitch, float *logits);
+                       int32_t hmap_pitch, float *logits, int pool_tiles);
 cudaError_t launch_train_step(cudaStream_t s, const TrainArgs &a);
 cudaError_t launch_round_params(cudaStream_t s, const float *master, float *wr);
 
