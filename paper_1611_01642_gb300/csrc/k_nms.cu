@@ -11,9 +11,12 @@
 //     into shared memory (over the no longer needed key array, whose keys
 //     move to a per-frame global scratch array) or, for very many
 //     candidates, into that global scratch;
-//  4. walks the candidates in order: one not yet suppressed is kept, all
-//     threads then suppress the later candidates whose IoU with it exceeds
-//     the threshold, and the first survivor after it is the next one kept.
+//  4. walks the candidates in order in batches of the next 32 not yet
+//     suppressed: warp 0 resolves a batch in order (pairwise suppression
+//     bits, then kept iff no kept earlier member suppresses it), and all
+//     threads then suppress the later candidates against the batch's kept
+//     members. This takes the same decisions as the one-at-a-time greedy
+//     walk (candidates between batch members are already suppressed).
 // The IoU test first evaluates the IoU in float. For boxes of this detector
 // (width >= 64, height >= 128, coordinates < 8192) the float value is within
 // 7e-5 of the exact one: each coordinate sum or difference is off by at most
@@ -216,41 +219,89 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
         ksrc = keys;
     }
     __syncthreads();
-    // Greedy walk. `next` (the first candidate after i that survived the
-    // pass) is found during the pass (per-thread min, warp min, one atomicMin
-    // per warp), so no thread rescans the flags; three slots rotate so that a
-    // pass needs one barrier (the slot reset two passes ahead never races with
-    // a read or an update). Kept indices are recorded on chip and the output
-    // boxes are written after the walk, so each pass only touches shared
-    // memory.
-    __shared__ int next_slot[3];
+    // Greedy walk in batches. Warp 0 takes the next (up to) 32 candidates not
+    // yet suppressed, in order, computes their pairwise suppression bits and
+    // resolves them in order exactly as the one-at-a-time walk would (a member
+    // is kept iff no kept member before it suppresses it: the candidates
+    // between members are already suppressed); then every thread suppresses
+    // the later candidates against the batch's kept members. Same decisions
+    // as the sequential definition, with ~32x fewer block-wide barriers.
+    __shared__ int batch[32], kbatch[32];
+    __shared__ int n_batch, n_keep, kept_total, scan_pos;
     int *kept_idx = reinterpret_cast<int *>(supp + ((cap + 15) & ~15));
-    if (tid == 0) next_slot[0] = next_slot[1] = next_slot[2] = n;
-    __syncthreads();
-    int kept = 0, i = n > 0 ? 0 : n, pass = 0;
-    while (i < n && kept < max_boxes) {
-        if (tid == 0) kept_idx[kept] = i;
-        ++kept;
-        if (kept == max_boxes) break;
-        const float4 bi = bx[i];
-        const int slot = pass % 3;
-        int first = n;  // first survivor seen by this thread
-#pragma unroll 4
-        for (int j = i + 1 + tid; j < n; j += kThreads) {
-            if (supp[j]) continue;
-            if (suppresses(bi, bx[j], iou_thr)) supp[j] = 1;
-            else first = min(first, j);
-        }
-        first = __reduce_min_sync(0xffffffffu, first);
-        if ((tid & 31) == 0 && first < n) atomicMin(&next_slot[slot], first);
-        __syncthreads();  // the one barrier of a pass
-        i = next_slot[slot];
-        // slot (pass+2)%3 was last read in the previous pass, before this
-        // barrier, and is next written in pass+2, after the next barrier
-        if (tid == 0) next_slot[(pass + 2) % 3] = n;
-        ++pass;
+    const int warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        kept_total = 0;
+        scan_pos = 0;
     }
     __syncthreads();
+    while (true) {
+        if (warp == 0) {
+            int pos = scan_pos, cnt = 0;
+            while (cnt < 32 && pos < n) {
+                const int j = pos + lane;
+                const bool alive = j < n && !supp[j];
+                const unsigned m = __ballot_sync(0xffffffffu, alive);
+                const int avail = __popc(m), take = min(avail, 32 - cnt);
+                const int rank = __popc(m & ((1u << lane) - 1u));
+                if (alive && rank < take) batch[cnt + rank] = j;
+                cnt += take;
+                if (take < avail) {  // stop right after the last member taken
+                    const unsigned last = __ballot_sync(0xffffffffu, alive && rank == take - 1);
+                    pos += __ffs(last);
+                    break;
+                }
+                pos += 32;
+            }
+            if (lane == 0) {
+                n_batch = cnt;
+                scan_pos = min(pos, n);
+            }
+        }
+        __syncthreads();
+        const int nb = n_batch;
+        if (nb == 0) break;
+        if (warp == 0) {
+            const int me = lane < nb ? batch[lane] : 0;
+            const float4 bme = bx[me];
+            unsigned row = 0;  // members after this lane's that it suppresses
+            for (int b = lane + 1; b < nb; ++b)
+                if (suppresses(bme, bx[batch[b]], iou_thr)) row |= 1u << b;
+            unsigned alive = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u), keep = 0;
+            const int kt = kept_total;
+            for (int a = 0; a < nb; ++a) {
+                const unsigned ra = __shfl_sync(0xffffffffu, row, a);
+                if ((alive >> a) & 1u) {
+                    if (kt + __popc(keep) >= max_boxes) break;
+                    keep |= 1u << a;
+                    alive &= ~ra;
+                }
+            }
+            if (lane < nb && ((keep >> lane) & 1u)) {
+                const int r = __popc(keep & ((1u << lane) - 1u));
+                kept_idx[kt + r] = me;
+                kbatch[r] = me;
+            }
+            if (lane == 0) {
+                n_keep = __popc(keep);
+                kept_total = kt + __popc(keep);
+            }
+        }
+        __syncthreads();
+        if (kept_total >= max_boxes) break;
+        const int nk = n_keep;
+        for (int j = scan_pos + tid; j < n; j += kThreads) {
+            if (supp[j]) continue;
+            const float4 bj = bx[j];
+            for (int k = 0; k < nk; ++k)
+                if (suppresses(bx[kbatch[k]], bj, iou_thr)) {
+                    supp[j] = 1;
+                    break;
+                }
+        }
+        __syncthreads();
+    }
+    const int kept = kept_total;
     pd_box *out = boxes + (size_t)f * max_boxes;
     for (int k = tid; k < kept; k += kThreads) {
         const int c = kept_idx[k];

@@ -126,6 +126,32 @@ def calibrate(scores: np.ndarray, logits: np.ndarray, recall: float = 0.99, thre
     return float(np.nextafter(np.float32(z[m]), np.float32(-np.inf)))
 
 
+def calibrate_sparse(det: Detector, batches, recall: float = 0.99, threshold: float = 0.0, lo: float | None = None,
+                     iters: int = 12):
+    """Largest keep threshold whose sparse path (tile-level keeping) still scores >= recall of the positives.
+
+    A tile is scored if any of its windows is kept, so the sparse path's recall at a given tau is at
+    least the window-level recall; this searches tau directly on the path's own recall (bisection
+    between the window-level threshold ``lo`` and the largest keep-logit of the batches).
+    """
+    batches = list(batches)
+    if lo is None:
+        s, z = window_stats(det, batches, threshold)
+        lo = calibrate(s, z, recall, threshold)
+        hi = float(z.max()) if z.size else lo
+    else:
+        hi = lo + 16.0
+    if sparse_metrics(det, batches, hi, threshold)["recall"] >= recall:
+        return hi
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        if sparse_metrics(det, batches, mid, threshold)["recall"] >= recall:
+            lo = mid
+        else:
+            hi = mid
+    return lo
+
+
 def sparse_metrics(det: Detector, batches, tau: float, threshold: float = 0.0):
     """Recall and keep fraction of the sparse path against the plain path, window by window.
 
@@ -180,6 +206,32 @@ def _scene_batches(width, height, key, first, count, batch):
                for i in range(i0, min(i0 + batch, first + count))]
 
 
+def recalibrate(path: str, out: str, calib_frames: int = 16, val_frames: int = 16, recall: float = 0.99,
+                width: int = 1920, height: int = 1080, factor: float = 1.05, batch: int = 8):
+    """Re-derives the keep threshold of a checkpoint on the sparse path's own recall; writes ``out``."""
+    import os
+    params, meta = load_checkpoint(path)
+    svm = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden",
+                       "svm_template_seed0.npz")
+    d = np.load(svm)
+    det = Detector(d["w"], float(d["b"]), max_frames=batch, max_width=width, max_height=height,
+                   pyr_factor=float(np.float32(factor)))
+    try:
+        pd_cnn_set_params(det.h, params)
+        calib = list(_scene_batches(width, height, 101, 0, calib_frames, batch))
+        s, z = window_stats(det, calib)
+        tau_window = calibrate(s, z, recall)
+        tau = calibrate_sparse(det, calib, recall)
+        val = list(_scene_batches(width, height, 101, calib_frames, val_frames, batch))
+        meta = dict(meta, keep_logit_threshold=tau, window_level_threshold=tau_window,
+                    calibration=dict(kind="path", frames=calib_frames, recall=recall),
+                    validation=sparse_metrics(det, val, tau))
+        save_checkpoint(out, params, meta)
+        return meta
+    finally:
+        det.close()
+
+
 def main(argv=None):
     import argparse
     ap = argparse.ArgumentParser(description="Train and calibrate the window proposal on synthetic scenes.")
@@ -194,6 +246,8 @@ def main(argv=None):
     ap.add_argument("--calib-frames", type=int, default=32)
     ap.add_argument("--val-frames", type=int, default=32)
     ap.add_argument("--recall", type=float, default=0.99)
+    ap.add_argument("--calibrate", choices=["window", "path"], default="path",
+                    help="keep threshold from window-level recall, or from the sparse path's own recall")
     ap.add_argument("--svm", default=None, help="npz with w, b (default: the seed-0 template)")
     ap.add_argument("--out", required=True)
     a = ap.parse_args(argv)
@@ -224,11 +278,12 @@ def main(argv=None):
         pd_cnn_set_params(det.h, params)
         calib = list(_scene_batches(a.width, a.height, 101, 0, a.calib_frames, a.batch))
         s, z = window_stats(det, calib)
-        tau = calibrate(s, z, a.recall)
+        tau_window = calibrate(s, z, a.recall)
+        tau = calibrate_sparse(det, calib, a.recall) if a.calibrate == "path" else tau_window
         val = list(_scene_batches(a.width, a.height, 101, a.calib_frames, a.val_frames, a.batch))
         m = sparse_metrics(det, val, tau)
         meta = dict(recipe=vars(a), train=asdict(cfg), train_seconds=train_s, final_loss=hist[-1],
-                    first_loss=hist[0], keep_logit_threshold=tau,
+                    first_loss=hist[0], keep_logit_threshold=tau, window_level_threshold=tau_window,
                     calib_window_recall=float(np.mean(z[s > 0] > tau)) if (s > 0).any() else 1.0,
                     validation=m)
         save_checkpoint(a.out, params, meta)
