@@ -52,6 +52,8 @@ def parse_args(argv=None):
                     help="frames the CPU oracle times for cpu_baseline (bounded sample)")
     ap.add_argument("--proposal-steps", type=int, default=10,
                     help="timed steps of the 16x1920x1080 plain-vs-sparse comparison (0: skip)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default K4 tile costs (profiler captures of a fixed plan)")
     ap.add_argument("--proposal-frames", type=int, default=16,
                     help="frames of the proposal comparison (16 is the workload; fewer for profiler captures)")
     return ap.parse_args(argv)
@@ -313,7 +315,8 @@ def run_gpu(args):
     frames = [torch.from_numpy(im).cuda() for im in imgs]
     pinned = [torch.from_numpy(im).pin_memory() for im in imgs]
     from paper_1611_01642_gb300 import autotune
-    tile_costs = autotune.apply(det, frames[:16], w, b, FACTOR)
+    tile_costs = (pd.pd_get_tile_costs(det.h) if args.no_autotune
+                  else autotune.apply(det, frames[:16], w, b, FACTOR))
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     wpf = windows_per_frame()
 
