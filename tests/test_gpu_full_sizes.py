@@ -1,0 +1,115 @@
+"""Parity at the full batch sizes of the workloads, in the launch configuration
+the benchmark times (one batched pd_detect per step).
+
+The oracle cannot score whole 4K batches in test time, so these tests sample
+windows and compute each from its own pixels with the oracle's brute-force
+descriptor (cells gathered from the oracle's resize of that level), then
+check the GPU score within the score bar |gpu - ref| <= 1e-4 (|b| + sum |w x|).
+Levels are checked bit-exactly against the oracle resize on sampled rows.
+The sparse path on the mixed 4K batch must reproduce the plain path's score
+of every window it scores, bit for bit.
+
+Workloads (scene recipes of synth/scenes.py):
+  mixed:  32 x 1242x375 + 16 x 640x480 + 16 x 1920x1080 (64 frames)
+  4K mix: 16 x 3840x2160 + 48 x 1242x375 (64 frames), with the proposal
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pd = pytest.importorskip("paper_1611_01642_gb300")
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+FACTOR = float(np.float32(1.05))
+SCORE_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def template():
+    d = np.load(os.path.join(ROOT, "tests", "golden", "svm_template_seed0.npz"))
+    return d["w"], float(d["b"])
+
+
+def _sample_and_check(det, imgs, w, b, frames_to_check, rng, per_level=4, levels_per_frame=3):
+    checked = 0
+    for f in frames_to_check:
+        img = imgs[f]
+        lv = det.levels(f)
+        maps = det.score_maps(f)
+        valid = [k for k, l in enumerate(lv) if l["rows"] > 0]
+        ks = sorted(set([valid[0], valid[-1]] + list(rng.choice(valid, size=min(levels_per_frame, len(valid)),
+                                                                  replace=False))))
+        for k in ks:
+            L = oracle.resize(img, lv[k]["width"], lv[k]["height"])
+            m = maps[k].cpu().numpy()
+            picks = [(0, 0), (lv[k]["rows"] - 1, lv[k]["cols"] - 1)]
+            picks += [(int(rng.integers(lv[k]["rows"])), int(rng.integers(lv[k]["cols"]))) for _ in range(per_level)]
+            for wy, wx in picks:
+                desc = oracle.window_descriptor_bruteforce(L, wx, wy)
+                ref = b + float(np.sum(desc * w))
+                scale = abs(b) + float(np.sum(np.abs(desc * w)))
+                assert abs(float(m[wy, wx]) - ref) <= SCORE_TOL * scale, (f, k, wy, wx, float(m[wy, wx]), ref)
+                checked += 1
+    return checked
+
+
+def test_mixed_64_frame_batch_sampled_windows_match_oracle(template):
+    from paper_1611_01642_gb300 import build as bld
+    bld.build()
+    w, b = template
+    imgs = synth.make_frames(3)
+    assert len(imgs) == 64
+    det = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=64, max_width=1920, max_height=1080)
+    try:
+        dev = [torch.from_numpy(im).cuda() for im in imgs]
+        for _ in range(3):  # plan, capture, replay: the replayed step is the one checked
+            det.detect(dev)
+            assert det.sync() == pd.PD_OK
+        rng = np.random.default_rng(3)
+        n = _sample_and_check(det, imgs, w, b, [0, 31, 32, 47, 48, 63], rng)
+        assert n >= 40
+        # windows per frame and level counts follow the pyramid rule
+        for f in [0, 32, 48]:
+            H, W = imgs[f].shape
+            assert [(l["width"], l["height"]) for l in det.levels(f)] == oracle.pyramid(W, H, FACTOR)
+    finally:
+        det.close()
+
+
+def test_4k_mixed_batch_plain_and_sparse(template):
+    from paper_1611_01642_gb300 import build as bld
+    from paper_1611_01642_gb300 import proposal
+    bld.build()
+    w, b = template
+    imgs = synth.make_frames(5)
+    assert len(imgs) == 64
+    params, meta = proposal.load_checkpoint(
+        os.path.join(ROOT, "paper_1611_01642_gb300", "weights", "proposal_1920x1080.npz"))
+    det = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=64, max_width=3840, max_height=2160)
+    try:
+        pd.pd_cnn_set_params(det.h, params)
+        dev = [torch.from_numpy(im).cuda() for im in imgs]
+        det.detect(dev)
+        assert det.sync() == pd.PD_OK
+        rng = np.random.default_rng(5)
+        assert _sample_and_check(det, imgs, w, b, [0, 15, 16, 63], rng) >= 30
+        plain = torch.cat([m.reshape(-1) for f in range(64) for m in det.score_maps(f)]).clone()
+        det.set_proposal(True, meta["keep_logit_threshold"])
+        det.detect(dev)
+        assert det.sync() == pd.PD_OK
+        sparse = torch.cat([m.reshape(-1) for f in range(64) for m in det.score_maps(f)])
+        scored = ~torch.isneginf(sparse)
+        assert torch.equal(sparse[scored], plain[scored])
+        pos = plain > 0
+        recall = float((pos & scored).sum().item() / max(pos.sum().item(), 1))
+        keep = float(scored.float().mean().item())
+        print(f"4K mix: recall {recall:.4f}, {keep:.3f} of windows scored")
+        assert 0.0 < keep < 1.0
+    finally:
+        det.close()
