@@ -15,11 +15,16 @@
 // (zero outside the level: the padding of layer 1); layer 1 runs on the
 // tensor cores as a GEMM over 4x4 pixel patches (a stride-2 3x3 window at
 // (2r-1, 2c-1) is the top-left 3x3 of the 4x4 patch there; the 7 extra taps
-// carry zero weights), giving 35x35x16 activations; layer 2 (17x17x32,
-// K = 9 taps x 16) and layer 3 (8x8x32, K = 9 x 32) are implicit GEMMs on
-// the tensor cores (mma.sync m16n8k16 bf16 -> fp32) whose A operand is
-// gathered from shared memory laid out position-major with padded strides
-// so that the stride-2 gathers are bank-conflict free; the 1x1 head gives h.
+// carry zero weights; mma.sync m16n8k16), giving 35x35x16 activations.
+// Layer 2 (17x17x32, K = 9 taps x 16) and layer 3 (8x8x32, K = 9 x 32) are
+// implicit GEMMs on the 5th-generation tensor cores: one thread issues
+// tcgen05.mma with both operands in shared memory (no-swizzle K-major
+// layout: the activation planes below are already that layout for every
+// tap, a tap being a start-address offset) and fp32 accumulators in tensor
+// memory; completion arrives on an mbarrier (bounded wait), and the
+// epilogues read the accumulators with tcgen05.ld. Layer 2's 16x16 core runs
+// as two M = 128 blocks; its 33 edge positions (row 16, column 16) run on
+// mma.sync meanwhile. Layer 3 is one M = 64 block. The 1x1 head gives h.
 // Zero padding of every convolution is the zero activation outside each
 // layer's grid.
 #include "pd_internal.h"
@@ -53,10 +58,16 @@ constexpr int PS2 = 156;           // layer-2 plane stride (17 x 9 = 153, padded
 static_assert(PS1 >= R1 * C1P && PS1 % 8 == 4 && PS2 >= R2 * C2P && PS2 % 8 == 4, "plane strides");
 constexpr int M1 = R1 * R1;      // 1225 layer-1 positions
 constexpr int M1T = (M1 + 15) / 16;  // 77 m-tiles
-constexpr int M2 = R2 * R2;      // 289 layer-2 positions
-constexpr int M2T = (M2 + 15) / 16;  // 19 m-tiles
-constexpr int kW3Frag = 9 * 2 * 4 * 32;  // uint2 layer-3 B fragments
 constexpr float kInv255 = 1.0f / 255.0f;   // float32 nearest to 1/255
+
+// Canonical (no-swizzle, K-major) UMMA B operands: per tap a 32 x 16 bf16
+// matrix stored as [8-row group n/8][8-column chunk k/8][row n%8][k%8], so the
+// K-chunk stride (LBO) is 128 bytes and the 8-row-group stride (SBO) 256.
+constexpr int kBTapBytes = 1024;
+constexpr int kL2Core = 16;       // layer-2 outputs [0,16)^2 on tcgen05; row 16 and column 16 on mma.sync
+constexpr int kEdge = 2 * R2 - 1; // 33 edge positions
+constexpr uint32_t kTmemCols = 128;  // L2 core accumulators in columns [0,64), L3 in [64,96)
+constexpr uint64_t kWaitNs = 1000000000ull;
 
 struct CnnSmem {
     uint8_t raw[2][XR][kRawW];   // input bytes, double buffered
@@ -65,12 +76,16 @@ struct CnnSmem {
         uint32_t xb[XR * XBW];   // bf16 pixel pairs (dead once layer 1 is done)
         uint4 a2[4 * 2 * PS2];   // [channel group 0..3][parity] planes of layer 2
     } u;
-    uint2 w3[kW3Frag];
+    uint8_t w2c[9 * kBTapBytes];      // layer-2 B operands, one per tap
+    uint8_t w3c[9 * 2 * kBTapBytes];  // layer-3 B operands, per tap and input-channel half
     float b1[16];
     float b2[32];
     float b3[32];
     float wh[32];
     float hpart[2][64];
+    unsigned long long bar;      // MMA completion (one phase per commit)
+    uint32_t tmem;               // tensor-memory base of this CTA
+    int failed;
 };
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -118,6 +133,77 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src, int n) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---- tcgen05 (5th-generation tensor cores, accumulators in tensor memory)
+// Shared-memory matrix descriptor, no swizzle, K-major: start, K-chunk
+// stride (LBO) and 8-row-group stride (SBO) in 16-byte units; bit 46 is the
+// descriptor version.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3fff) | ((uint64_t)((lbo >> 4) & 0x3fff) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3fff) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16: f32 accumulator, bf16 A and B, both
+// K-major, N / 8 and M / 16.
+__host__ __device__ constexpr uint32_t umma_idesc(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, int accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(unsigned long long *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// 16 consecutive f32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Every thread waits (bounded) for phase `parity` of the MMA barrier; a wait
+// that gives up sets the error word and the CTA's failed flag.
+__device__ __forceinline__ bool mma_wait(CnnSmem &S, uint32_t parity, unsigned *err) {
+    const uint32_t a = smem_u32(&S.bar);
+    uint32_t ok = 0;
+    const uint64_t t0 = global_ns();
+    while (true) {
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok || global_ns() - t0 > kWaitNs) break;
+    }
+    if (!ok) {
+        S.failed = 1;
+        if (err) atomicOr(err, kErrTimeout);
+    }
+    return ok != 0;
+}
+
 // Stages the bytes of pixel rows y0 .. y0+71 and columns x0-1 .. x0+78 of an
 // item (x0 = 8 cx0 - 7, so every chunk starts on an 8-byte boundary of the
 // level row; level rows are 16-byte aligned). Chunks outside the level read
@@ -142,12 +228,18 @@ __device__ __forceinline__ void stage_input(uint8_t (*raw)[kRawW], const CnnItem
     }
 }
 
+// Position of layer-2 edge index e (row 16, then column 16): (r, c).
+__device__ __forceinline__ int2 edge_pos(int e) {
+    e = min(e, kEdge - 1);
+    return e < R2 ? make_int2(kL2Core, e) : make_int2(e - R2, kL2Core);
+}
+
 __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__restrict__ levels,
                                                          const uint8_t *__restrict__ pyr,
                                                          const CnnItem *__restrict__ items, int n_items,
                                                          const CnnWeights wts, float *__restrict__ hmap,
-                                                         int32_t hmap_pitch) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+                                                         int32_t hmap_pitch, unsigned *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     CnnSmem &S = *reinterpret_cast<CnnSmem *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, t = lane & 3;
@@ -156,7 +248,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__rest
     stage_input(S.raw[0], items, levels, pyr, item, tid);
     cp_async_commit();
 
-    for (int i = tid; i < kW3Frag; i += kThreads) S.w3[i] = reinterpret_cast<const uint2 *>(wts.w3frag)[i];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        S.failed = 0;
+    }
+    // canonical B operands of layers 2 and 3 from the bf16-rounded weights
+    for (int i = tid; i < 9 * 32 * 16; i += kThreads) {
+        const int tap = i / 512, n = (i >> 4) & 31, k = i & 15;
+        const uint32_t off = tap * kBTapBytes + (n >> 3) * 256 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+        *reinterpret_cast<__nv_bfloat16 *>(S.w2c + off) = __float2bfloat16_rn(wts.w2[(n * 16 + k) * 9 + tap]);
+    }
+    for (int i = tid; i < 9 * 2 * 32 * 16; i += kThreads) {
+        const int tk = i / 512, n = (i >> 4) & 31, k = i & 15;  // tk = tap * 2 + k-half
+        const int tap = tk >> 1, kh = tk & 1;
+        const uint32_t off = tk * kBTapBytes + (n >> 3) * 256 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+        *reinterpret_cast<__nv_bfloat16 *>(S.w3c + off) =
+            __float2bfloat16_rn(wts.w3[(n * 32 + 16 * kh + k) * 9 + tap]);
+    }
     if (tid < 16) S.b1[tid] = wts.b1[tid];
     if (tid < 32) {
         S.b2[tid] = wts.b2[tid];
@@ -174,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__rest
             const float hi = (ky < 3 && kx + 1 < 3) ? wts.w1[o * 9 + ky * 3 + kx + 1] : 0.f;
             bw1[nt][hk] = pack_bf16(lo, hi);
         }
-    // layer-2 B fragments (9 taps x 4 n-tiles x 2 regs), kept in registers
+    // layer-2 B fragments (9 taps x 4 n-tiles x 2 regs) for the edge positions on mma.sync
     uint32_t bw2[9][4][2];
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap)
@@ -185,10 +299,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__rest
             bw2[tap][nt][1] = v.y;
         }
     const float bh = wts.bh[0];
-    const uint32_t a1_base = static_cast<uint32_t>(__cvta_generic_to_shared(&S.a1[0]));
-    const uint32_t a2_base = static_cast<uint32_t>(__cvta_generic_to_shared(&S.u.a2[0]));
+    const uint32_t a1_base = smem_u32(&S.a1[0]);
+    const uint32_t a2_base = smem_u32(&S.u.a2[0]);
+    const uint32_t w2c_base = smem_u32(S.w2c), w3c_base = smem_u32(S.w3c);
+    async_proxy_fence();  // the B operands are read by the tensor cores
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    uint32_t phase = 0;  // parity of the next MMA barrier phase
 
-    for (int iter = 0; item < n_items; ++iter, item += gridDim.x) {
+    for (int iter = 0; item < n_items && !S.failed; ++iter, item += gridDim.x) {
         const int cur = iter & 1;
         const int next = item + gridDim.x;
         if (next < n_items) stage_input(S.raw[cur ^ 1], items, levels, pyr, next, tid);
@@ -227,7 +348,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__rest
             *reinterpret_cast<uint2 *>(&S.u.xb[r * XBW + 2 * j]) = make_uint2(pack_bf16(e[0], e[1]), pack_bf16(e[2], e[3]));
         }
         __syncthreads();
-        // ---- layer 1 on tensor cores: 1225 positions x 16 channels, K = 16 (4x4 patch)
+        // ---- layer 1 on tensor cores (mma.sync): 1225 positions x 16 channels, K = 16 (4x4 patch)
         for (int mt = warp; mt < M1T; mt += kThreads / 32) {
             const int p0 = mt * 16 + g, p1 = p0 + 8;
             const int q0 = min(p0, M1 - 1), q1 = min(p1, M1 - 1);  // padding rows repeat the last row
@@ -252,17 +373,32 @@ __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__rest
                     in1 ? relu_pack_bf16(acc[0][2], acc[0][3]) : 0u, in0 ? relu_pack_bf16(acc[1][0], acc[1][1]) : 0u,
                     in1 ? relu_pack_bf16(acc[1][2], acc[1][3]) : 0u);
         }
+        async_proxy_fence();  // layer-1 planes are read by the tensor cores next
+        tc_fence_before();
         __syncthreads();
-        // ---- layer 2 on tensor cores: 289 positions x 32 channels, K = 9 taps x 16
-        for (int mt = warp; mt < M2T; mt += kThreads / 32) {
-            const int p0 = mt * 16 + g, p1 = p0 + 8;
-            const int q0 = min(p0, M2 - 1), q1 = min(p1, M2 - 1);
-            const int r0 = q0 / R2, c0 = q0 - r0 * R2, r1 = q1 / R2, c1 = q1 - r1 * R2;
-            // A rows: lane l reads output row (l % 8) + 8 ((l / 8) & 1), channel group l / 16;
-            // tap (dy, dx) is layer-1 position (2r + dy, 2c + dx): parity dx & 1, plane column c + dx / 2
-            const int ls = min(mt * 16 + (lane & 15), M2 - 1);
-            const int lr = ls / R2, lc = ls - lr * R2;
-            const uint32_t src = a1_base + ((((lane >> 4) * 2) * PS1 + 2 * lr * C1P + lc) << 4);
+        tc_fence_after();
+        // ---- layer 2, outputs [0,16)^2 on tcgen05: two 16-row x 8-column blocks (M = 128),
+        // N = 32, K = 16 per tap. A for tap (dy, dx), block c0: rows 2r + dy of the
+        // parity-(dx & 1) plane, columns c0 + dx / 2 + 0..7; 8-row groups 2 plane rows apart.
+        if (tid == 0) {
+            constexpr uint32_t kIdesc = umma_idesc(128, 32);
+#pragma unroll
+            for (int cb = 0; cb < 2; ++cb)
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int dy = tap / 3, dx = tap % 3;
+                    const uint32_t a = a1_base + (uint32_t)((((dx & 1) * PS1) + dy * C1P + 8 * cb + (dx >> 1)) << 4);
+                    umma_bf16(tmem + 32 * cb, umma_desc(a, 2 * PS1 * 16, 2 * C1P * 16),
+                              umma_desc(w2c_base + tap * kBTapBytes, 128, 256), kIdesc, tap > 0);
+                }
+            umma_commit(&S.bar);
+        }
+        // ---- layer 2 edges (row 16, column 16: 33 positions) on mma.sync, meanwhile
+        if (warp < 3) {
+            const int mt = warp;
+            const int2 e0 = edge_pos(mt * 16 + g), e1 = edge_pos(mt * 16 + g + 8);
+            const int2 le = edge_pos(mt * 16 + (lane & 15));
+            const uint32_t src = a1_base + ((((lane >> 4) * 2) * PS1 + 2 * le.x * C1P + le.y) << 4);
             float acc[4][4];
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt) {
@@ -280,10 +416,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__rest
             PD_L2_TAP(1, 0) PD_L2_TAP(1, 1) PD_L2_TAP(1, 2)
             PD_L2_TAP(2, 0) PD_L2_TAP(2, 1) PD_L2_TAP(2, 2)
 #undef PD_L2_TAP
-            const bool in0 = interior2 || ((y2 + r0) >= 0 && (y2 + r0) < H2 && (x2 + c0) >= 0 && (x2 + c0) < W2);
-            const bool in1 = interior2 || ((y2 + r1) >= 0 && (y2 + r1) < H2 && (x2 + c1) >= 0 && (x2 + c1) < W2);
-            // channel groups 2h + (l / 16) of output row (l % 8) + 8 ((l / 8) & 1)
-            const uint32_t dst = a2_base + ((((lane >> 4) * 2 + (lc & 1)) * PS2 + lr * C2P + (lc >> 1)) << 4);
+            const bool in0 = interior2 || ((y2 + e0.x) >= 0 && (y2 + e0.x) < H2 && (x2 + e0.y) >= 0 && (x2 + e0.y) < W2);
+            const bool in1 = interior2 || ((y2 + e1.x) >= 0 && (y2 + e1.x) < H2 && (x2 + e1.y) >= 0 && (x2 + e1.y) < W2);
+            const uint32_t dst = a2_base + ((((lane >> 4) * 2 + (le.y & 1)) * PS2 + le.x * C2P + (le.y >> 1)) << 4);
 #pragma unroll
             for (int h = 0; h < 2; ++h)
                 stsm_x4(dst + ((4 * h * PS2) << 4),
@@ -292,61 +427,67 @@ __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__rest
                         in0 ? relu_pack_bf16(acc[2 * h + 1][0], acc[2 * h + 1][1]) : 0u,
                         in1 ? relu_pack_bf16(acc[2 * h + 1][2], acc[2 * h + 1][3]) : 0u);
         }
-        __syncthreads();
-        // ---- layer 3 on tensor cores: 64 positions x 32 channels, K = 9 x 32;
-        // warp w: m-tile w & 3, n-tiles 2*(w >> 2) .. +1
+        if (__syncthreads_or(!mma_wait(S, phase, err))) break;  // CTA-uniform
+        phase ^= 1u;
+        tc_fence_after();
+        // ---- layer-2 core epilogue: warp w reads lanes 32 (w % 4) .. + 31 of block w / 4:
+        // lane m = 32 (w % 4) + l holds output (r, c) = (m / 8, 8 (w / 4) + m % 8), 32 channels
         {
-            const int mt = warp & 3, nh = warp >> 2;
-            const int p0 = mt * 16 + g, p1 = p0 + 8;
-            float acc2[2][2][4];  // [k-half][n-tile]: four independent mma chains
+            const int cb = warp >> 2, m = 32 * (warp & 3) + lane;
+            const int r = m >> 3, c = 8 * cb + (m & 7);
+            const bool in = interior2 || ((y2 + r) >= 0 && (y2 + r) < H2 && (x2 + c) >= 0 && (x2 + c) < W2);
 #pragma unroll
-            for (int kh = 0; kh < 2; ++kh)
+            for (int hf = 0; hf < 2; ++hf) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 32 * cb + 16 * hf, v);
 #pragma unroll
-                for (int j = 0; j < 2; ++j)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) acc2[kh][j][e] = 0.f;
-            // A rows: lane l reads output position (l % 8) + 8 ((l / 8) & 1) of the m-tile,
-            // channel group 2 kh + l / 16
-            const int lp = mt * 16 + (lane & 15);
-            const int lr = lp >> 3, lc = lp & 7;
-            const uint32_t src = a2_base + ((((lane >> 4) * 2) * PS2 + 2 * lr * C2P + lc) << 4);
-#define PD_L3_TAP(DY, DX, KH)                                                                                  \
-    {                                                                                                        \
-        uint32_t a0, a1, a2, a3;                                                                             \
-        ldsm_x4<(((2 * (KH) * 2 + ((DX) & 1)) * PS2 + (DY) * C2P + ((DX) >> 1)) << 4)>(src, a0, a1, a2, a3);  \
-        _Pragma("unroll") for (int j = 0; j < 2; ++j) {                                                     \
-            const uint2 b = S.w3[((((DY) * 3 + (DX)) * 2 + (KH)) * 4 + 2 * nh + j) * 32 + lane];             \
-            mma_bf16(acc2[KH][j], a0, a1, a2, a3, b.x, b.y);                                                 \
-        }                                                                                                    \
-    }
-            PD_L3_TAP(0, 0, 0) PD_L3_TAP(0, 0, 1) PD_L3_TAP(0, 1, 0) PD_L3_TAP(0, 1, 1) PD_L3_TAP(0, 2, 0)
-            PD_L3_TAP(0, 2, 1) PD_L3_TAP(1, 0, 0) PD_L3_TAP(1, 0, 1) PD_L3_TAP(1, 1, 0) PD_L3_TAP(1, 1, 1)
-            PD_L3_TAP(1, 2, 0) PD_L3_TAP(1, 2, 1) PD_L3_TAP(2, 0, 0) PD_L3_TAP(2, 0, 1) PD_L3_TAP(2, 1, 0)
-            PD_L3_TAP(2, 1, 1) PD_L3_TAP(2, 2, 0) PD_L3_TAP(2, 2, 1)
-#undef PD_L3_TAP
-            float acc[2][4];
-#pragma unroll
-            for (int j = 0; j < 2; ++j)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) acc[j][e] = acc2[0][j][e] + acc2[1][j][e];
-            // bias, relu, head partial over this lane's 4 channels, reduce over t
-            float h0 = 0.f, h1 = 0.f;
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int co = (2 * nh + j) * 8 + 2 * t;
-                h0 = fmaf(fmaxf(acc[j][0] + S.b3[co], 0.f), S.wh[co], h0);
-                h0 = fmaf(fmaxf(acc[j][1] + S.b3[co + 1], 0.f), S.wh[co + 1], h0);
-                h1 = fmaf(fmaxf(acc[j][2] + S.b3[co], 0.f), S.wh[co], h1);
-                h1 = fmaf(fmaxf(acc[j][3] + S.b3[co + 1], 0.f), S.wh[co + 1], h1);
+                for (int gg = 0; gg < 2; ++gg) {
+                    const int grp = 2 * hf + gg;
+                    const float *bb = &S.b2[8 * grp];
+                    uint4 q;
+                    q.x = in ? relu_pack_bf16(v[8 * gg + 0] + bb[0], v[8 * gg + 1] + bb[1]) : 0u;
+                    q.y = in ? relu_pack_bf16(v[8 * gg + 2] + bb[2], v[8 * gg + 3] + bb[3]) : 0u;
+                    q.z = in ? relu_pack_bf16(v[8 * gg + 4] + bb[4], v[8 * gg + 5] + bb[5]) : 0u;
+                    q.w = in ? relu_pack_bf16(v[8 * gg + 6] + bb[6], v[8 * gg + 7] + bb[7]) : 0u;
+                    S.u.a2[(grp * 2 + (c & 1)) * PS2 + r * C2P + (c >> 1)] = q;
+                }
             }
-            h0 += __shfl_xor_sync(0xffffffffu, h0, 1);
-            h0 += __shfl_xor_sync(0xffffffffu, h0, 2);
-            h1 += __shfl_xor_sync(0xffffffffu, h1, 1);
-            h1 += __shfl_xor_sync(0xffffffffu, h1, 2);
-            if (t == 0) {
-                S.hpart[nh][p0] = h0;
-                S.hpart[nh][p1] = h1;
+        }
+        async_proxy_fence();  // layer-2 planes are read by the tensor cores next
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        // ---- layer 3 on tcgen05: 8 x 8 outputs (M = 64), N = 32, K = 9 taps x 2 halves x 16
+        if (tid == 0) {
+            constexpr uint32_t kIdesc = umma_idesc(64, 32);
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+                for (int kh = 0; kh < 2; ++kh) {
+                    const int dy = tap / 3, dx = tap % 3;
+                    const uint32_t a =
+                        a2_base + (uint32_t)((((2 * kh) * 2 + (dx & 1)) * PS2 + dy * C2P + (dx >> 1)) << 4);
+                    umma_bf16(tmem + 64, umma_desc(a, 2 * PS2 * 16, 2 * C2P * 16),
+                              umma_desc(w3c_base + (tap * 2 + kh) * kBTapBytes, 128, 256), kIdesc, tap + kh > 0);
+                }
+            umma_commit(&S.bar);
+        }
+        if (__syncthreads_or(!mma_wait(S, phase, err))) break;  // CTA-uniform
+        phase ^= 1u;
+        tc_fence_after();
+        // ---- layer-3 epilogue and head: M = 64 rows sit in lanes 32 q + (0..15) of
+        // quadrant q (rows 16 q .. 16 q + 15); warps 0-3 take channels 0-15, warps 4-7 16-31
+        {
+            const int q = warp & 3, half = warp >> 2;
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 64 + 16 * half, v);
+            float hp = 0.f;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int ch = 16 * half + i;
+                hp = fmaf(fmaxf(v[i] + S.b3[ch], 0.f), S.wh[ch], hp);
             }
+            if (lane < 16) S.hpart[half][16 * q + lane] = hp;
         }
         __syncthreads();
         if (tid < 64) {
@@ -356,6 +497,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__rest
         }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
 // Window pooling z[wy][wx] = bv + sum_{r<16, s<8} V[r][s] h[wy+r][wx+s]: one
@@ -427,10 +572,11 @@ cudaError_t init_cnn() {
 
 cudaError_t launch_cnn(cudaStream_t s, const LevelDesc *d_levels, int n_levels, const uint8_t *pyr,
                        const CnnItem *d_items, int n_items, const CnnWeights &w, float *hmap,
-                       int32_t hmap_pitch, float *logits, int pool_tiles) {
+                       int32_t hmap_pitch, float *logits, int pool_tiles, unsigned *err) {
     if (n_items > 0) {
         const int grid = std::min(n_items, g_cnn_grid > 0 ? g_cnn_grid : n_items);
-        k_cnn_fwd<<<grid, kThreads, sizeof(CnnSmem), s>>>(d_levels, pyr, d_items, n_items, w, hmap, hmap_pitch);
+        k_cnn_fwd<<<grid, kThreads, sizeof(CnnSmem), s>>>(d_levels, pyr, d_items, n_items, w, hmap, hmap_pitch,
+                                                           err);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

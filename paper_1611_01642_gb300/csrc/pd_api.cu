@@ -479,6 +479,8 @@ CnnWeights cnn_weights(const pd_handle *h) {
     w.w1 = wr + kOffW1;
     w.b1 = wr + kOffB1;
     w.w2frag = h->w2frag;
+    w.w2 = wr + kOffW2;
+    w.w3 = wr + kOffW3;
     w.b2 = wr + kOffB2;
     w.w3frag = h->w3frag;
     w.b3 = wr + kOffB3;
@@ -793,7 +795,7 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
             // learned proposal: keep-logits of every window, then the tiles to score
             PD_CUDA(h, launch_cnn(q, dl, (int)p.levels.size(), h->d_pyr, dptr<CnnItem>(h, o.cnn_items),
                                   (int)p.cnn_items.size(), cnn_weights(h), h->hmap, h->atlas.pitch, h->logits,
-                                  max_pool_tiles(p)));
+                                  max_pool_tiles(p), h->d_err));
             PD_CUDA(h, cudaMemsetAsync(h->c_flag, 0, p.c_items.size() * 4 + 4, q));
             PD_CUDA(h, launch_proposal_flags(q, dl, dptr<SvmItem>(h, o.s_items), (int)p.s_items.size(), h->logits,
                                              h->tau, h->s_flag, h->c_flag));
@@ -981,7 +983,7 @@ int pd_cnn_forward(pd_handle *h, void *stream, const uint8_t *d_level, int Wk, i
     if (r != PD_OK) return r;
     PD_CUDA(h, launch_cnn(s, dptr<LevelDesc>(h, o.levels), p.levels[0].rows > 0 ? 1 : 0, d_level,
                           dptr<CnnItem>(h, o.cnn_items), (int)p.cnn_items.size(), cnn_weights(h), d_h, h_pitch,
-                          d_logits, max_pool_tiles(p)));
+                          d_logits, max_pool_tiles(p), h->d_err));
     return PD_OK;
 }
 

@@ -118,6 +118,7 @@ struct CnnWeights {
     const uint32_t *w2frag;   // layer-2 mma B fragments [9 taps][4 n-tiles][32 lanes][2]
     const float *b2;          // [32]
     const uint32_t *w3frag;   // layer-3 mma B fragments [9][2 k-halves][4][32][2]
+    const float *w2, *w3;     // [32][16][3][3], [32][32][3][3] (bf16-rounded)
     const float *b3, *wh;     // [32], [32]
     const float *bh;          // [1]
     const float *v, *bv;      // [16][8], [1]
@@ -159,7 +160,7 @@ inline int pool_tiles_of(int rows, int cols) {
 }
 cudaError_t launch_cnn(cudaStream_t s, const LevelDesc *d_levels, int n_levels, const uint8_t *pyr,
                        const CnnItem *d_items, int n_items, const CnnWeights &w, float *hmap,
-                       int32_t hmap_pitch, float *logits, int pool_tiles);
+                       int32_t hmap_pitch, float *logits, int pool_tiles, unsigned *err);
 cudaError_t launch_train_step(cudaStream_t s, const TrainArgs &a);
 cudaError_t launch_round_params(cudaStream_t s, const float *master, float *wr);
 
