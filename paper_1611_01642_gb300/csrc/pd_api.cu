@@ -276,23 +276,70 @@ int fail(pd_handle *h, int code, const char *fmt, ...) {
         if (e_ != cudaSuccess) return fail((h), PD_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
-// Adds one level to the plan (tables, descriptor, work items).
-// K4 tile shape of a rows x cols score map: the shape with the least
-// tiles x cost (cost = relative time of one tile of that shape).
-int pick_shape(int rows, int cols, const float *cost) {
-    int best = 0;
-    double best_c = 1e300;
+// K4 tiling of a rows x cols score map: bands of rows, each band one tile
+// height, each band a sequence of tiles of that height whose widths may
+// differ; chosen by dynamic programming to minimise the summed per-tile
+// cost (cost[s] = relative time of one tile of shape s). The last band and
+// the last tile of a band may reach past the map (their extra windows are
+// computed and not stored).
+void plan_windows(std::vector<SvmItem> &out, int li, int rows, int cols, const float *cost) {
+    if (rows <= 0 || cols <= 0) return;
+    int heights[kSvmShapes], nh = 0;
     for (int s = 0; s < kSvmShapes; ++s) {
-        const SvmShapeInfo sh = svm_shape(s);
-        const double c = (double)((rows + sh.th - 1) / sh.th) * ((cols + sh.tw - 1) / sh.tw) * cost[s];
-        if (c < best_c) {
-            best_c = c;
-            best = s;
+        const int th = svm_shape(s).th;
+        bool seen = false;
+        for (int i = 0; i < nh; ++i) seen |= heights[i] == th;
+        if (!seen) heights[nh++] = th;
+    }
+    // per height: cheapest left-to-right covering of the columns
+    std::vector<double> band_cost(nh);
+    std::vector<std::vector<int>> band_shapes(nh);
+    std::vector<double> best(cols + 1);
+    std::vector<int> pick(cols + 1);
+    for (int hi = 0; hi < nh; ++hi) {
+        best[cols] = 0.0;
+        for (int x = cols - 1; x >= 0; --x) {
+            best[x] = 1e300;
+            pick[x] = -1;
+            for (int s = 0; s < kSvmShapes; ++s) {
+                const SvmShapeInfo sh = svm_shape(s);
+                if (sh.th != heights[hi]) continue;
+                const double c = (double)cost[s] + best[std::min(cols, x + sh.tw)];
+                if (c < best[x] - 1e-12) {
+                    best[x] = c;
+                    pick[x] = s;
+                }
+            }
+        }
+        band_cost[hi] = best[0];
+        for (int x = 0; x < cols; x += svm_shape(pick[x]).tw) band_shapes[hi].push_back(pick[x]);
+    }
+    // rows: cheapest top-to-bottom sequence of bands
+    std::vector<double> rbest(rows + 1);
+    std::vector<int> rpick(rows + 1);
+    rbest[rows] = 0.0;
+    for (int y = rows - 1; y >= 0; --y) {
+        rbest[y] = 1e300;
+        rpick[y] = -1;
+        for (int hi = 0; hi < nh; ++hi) {
+            const double c = band_cost[hi] + rbest[std::min(rows, y + heights[hi])];
+            if (c < rbest[y] - 1e-12) {
+                rbest[y] = c;
+                rpick[y] = hi;
+            }
         }
     }
-    return best;
+    for (int y = 0; y < rows; y += heights[rpick[y]]) {
+        const int hi = rpick[y];
+        int x = 0;
+        for (int s : band_shapes[hi]) {
+            out.push_back({li, x, y, s});
+            x += svm_shape(s).tw;
+        }
+    }
 }
 
+// Adds one level to the plan (tables, descriptor, work items).
 void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int64_t img_off,
                 int32_t img_pitch, const LevelDesc *share = nullptr,
                 const float *tile_cost = kDefaultTileCost) {
@@ -326,12 +373,7 @@ void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int
     L.ctx = (L.Wc + kCellTW - 1) / kCellTW;
     for (int cy = 0; cy < L.Hc; cy += kCellTH)
         for (int cx = 0; cx < L.Wc; cx += kCellTW) p.c_items.push_back({li, cx, cy, 0});
-    if (L.rows > 0) {
-        const int shape = pick_shape(L.rows, L.cols, tile_cost);
-        const SvmShapeInfo sh = svm_shape(shape);
-        for (int wy = 0; wy < L.rows; wy += sh.th)
-            for (int wx = 0; wx < L.cols; wx += sh.tw) p.s_items.push_back({li, wx, wy, shape});
-    }
+    plan_windows(p.s_items, li, L.rows, L.cols, tile_cost);
     p.atlas_rows += L.Hc;
     p.score_floats += (int64_t)L.rows * L.cols;
     p.max_wc = std::max(p.max_wc, L.Wc);
@@ -593,11 +635,14 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
         int64_t s_bound = 0;
         for (const LevelDesc &L : one.levels) {
             int64_t most = 0;
+            // any band / width mix has at most (rows / smallest height + 1) bands of at
+            // most (cols / smallest width + 1) tiles
+            int min_th = 1 << 30, min_tw = 1 << 30;
             for (int sh = 0; sh < kSvmShapes; ++sh) {
-                const SvmShapeInfo si = svm_shape(sh);
-                most = std::max<int64_t>(most, (int64_t)((L.rows + si.th - 1) / si.th) *
-                                                   ((L.cols + si.tw - 1) / si.tw));
+                min_th = std::min(min_th, svm_shape(sh).th);
+                min_tw = std::min(min_tw, svm_shape(sh).tw);
             }
+            if (L.rows > 0) most = (int64_t)(L.rows / min_th + 1) * (L.cols / min_tw + 1);
             s_bound += most;
         }
         const int64_t F = params->max_frames;
