@@ -19,6 +19,7 @@ recipe, keep threshold, measured recall and keep fraction).
 from __future__ import annotations
 
 import json
+import math
 import time
 from dataclasses import asdict, dataclass, field
 
@@ -35,6 +36,7 @@ class TrainConfig:
     pos_weight: float = 0.0          # 0: neg/pos of the first batch
     steps_per_batch: int = 4         # Adam steps on each detected batch
     init_seed: int = 0               # He initialisation seed
+    total_batches: int = 0           # > 0: cosine decay of lr to 0 over this many batches
     extra: dict = field(default_factory=dict)
 
 
@@ -86,8 +88,11 @@ def train(det: Detector, batches, cfg: TrainConfig, params: np.ndarray | None = 
             pos = int((s > cfg.label_threshold).sum())
             pos_weight = float(max(s.size - pos, 1) / max(pos, 1))
             log(f"pos_weight = neg/pos = {pos_weight:.2f} ({pos} of {s.size} windows positive)")
+        lr = cfg.lr
+        if cfg.total_batches > 0:
+            lr = 0.5 * cfg.lr * (1.0 + math.cos(math.pi * min(b, cfg.total_batches) / cfg.total_batches))
         for _ in range(cfg.steps_per_batch):
-            pd_cnn_train_step(det.h, pos_weight, cfg.label_threshold, cfg.lr)
+            pd_cnn_train_step(det.h, pos_weight, cfg.label_threshold, lr)
         loss = pd_cnn_train_loss(det.h)
         history.append(loss)
         if b % 10 == 0:
@@ -243,6 +248,7 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=2)
     ap.add_argument("--steps-per-batch", type=int, default=4)
     ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--cosine", type=int, default=1, help="cosine decay of the step size over the run")
     ap.add_argument("--calib-frames", type=int, default=32)
     ap.add_argument("--val-frames", type=int, default=32)
     ap.add_argument("--recall", type=float, default=0.99)
@@ -271,7 +277,8 @@ def main(argv=None):
                 idx = order_rng.permutation(len(pool))
                 for i0 in range(0, len(idx), a.batch):
                     yield [pool[i] for i in idx[i0:i0 + a.batch]]
-        cfg = TrainConfig(lr=a.lr, steps_per_batch=a.steps_per_batch)
+        cfg = TrainConfig(lr=a.lr, steps_per_batch=a.steps_per_batch,
+                          total_batches=a.epochs * ((a.train_frames + a.batch - 1) // a.batch) if a.cosine else 0)
         t0 = time.time()
         params, hist = train(det, epochs(), cfg)
         train_s = time.time() - t0
