@@ -41,8 +41,9 @@ constexpr int T3 = 8;            // layer-3 tile (cells)
 constexpr int R2 = 2 * T3 + 1;   // 17 layer-2 positions per side
 constexpr int R1 = 2 * R2 + 1;   // 35 layer-1 positions per side
 constexpr int XR = 2 * R1 + 2;   // 72 pixel rows/columns under the 4x4 patches
-constexpr int kRawW = 80;        // staged bytes per row: pixels x0-1 .. x0+78, ten 8-byte chunks
-constexpr int kChunks = kRawW / 8;
+constexpr int kRawW = kCnnBoxW;  // staged bytes per row: pixels x0-9 .. x0+86 (TMA box)
+static_assert(XR == kCnnBoxH, "input box height");
+static_assert((XR * kRawW) % 128 == 0, "second raw buffer stays 128-byte aligned");
 constexpr int XBW = 44;          // bf16 pixel row stride in words (72 used, padded for banks)
 // Activations are stored as 16-byte rows of 8 bf16 channels, split by
 // channel group and by column parity: plane (group, parity) holds the
@@ -70,7 +71,7 @@ constexpr uint32_t kTmemCols = 128;  // L2 core accumulators in columns [0,64), 
 constexpr uint64_t kWaitNs = 1000000000ull;
 
 struct CnnSmem {
-    uint8_t raw[2][XR][kRawW];   // input bytes, double buffered
+    uint8_t raw[2][XR][kRawW];   // input bytes, double buffered (TMA destinations: 128-byte aligned)
     uint4 a1[2 * 2 * PS1];       // [channel group 0..1][parity] planes of layer 1
     union {
         uint32_t xb[XR * XBW];   // bf16 pixel pairs (dead once layer 1 is done)
@@ -84,6 +85,7 @@ struct CnnSmem {
     float wh[32];
     float hpart[2][64];
     unsigned long long bar;      // MMA completion (one phase per commit)
+    unsigned long long inbar[2]; // input tile arrival, one per raw buffer
     uint32_t tmem;               // tensor-memory base of this CTA
     int failed;
 };
@@ -124,14 +126,6 @@ __device__ __forceinline__ void stsm_x4(uint32_t addr, uint32_t r0, uint32_t r1,
                  "r"(r2), "r"(r3)
                  : "memory");
 }
-
-// 8-byte asynchronous copy global -> shared; bytes past n are zero-filled.
-__device__ __forceinline__ void cp_async8(void *dst, const void *src, int n) {
-    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -204,28 +198,36 @@ __device__ __forceinline__ bool mma_wait(CnnSmem &S, uint32_t parity, unsigned *
     return ok != 0;
 }
 
-// Stages the bytes of pixel rows y0 .. y0+71 and columns x0-1 .. x0+78 of an
-// item (x0 = 8 cx0 - 7, so every chunk starts on an 8-byte boundary of the
-// level row; level rows are 16-byte aligned). Chunks outside the level read
-// nothing (zero fill); the conversion below zeroes those pixels anyway.
-__device__ __forceinline__ void stage_input(uint8_t (*raw)[kRawW], const CnnItem *__restrict__ items,
-                                            const LevelDesc *__restrict__ levels, const uint8_t *__restrict__ pyr,
-                                            int item, int tid) {
-    const CnnItem it = items[item];
-    const LevelDesc L = levels[it.level];
-    const int y0 = 8 * it.cy0 - 7, xs = 8 * it.cx0 - 8;
-    const uint8_t *img = pyr + L.img_off;
-    for (int k = tid; k < XR * kChunks; k += kThreads) {
-        const int r = k / kChunks, q = k - r * kChunks;
-        const int y = y0 + r, x = xs + 8 * q;
-        int n = 0;
-        const uint8_t *src = img;
-        if (y >= 0 && y < L.Hk && x >= 0) {
-            n = min(max(L.Wk - x, 0), 8);
-            if (n > 0) src = img + (size_t)y * L.img_pitch + x;
-        }
-        cp_async8(&raw[r][8 * q], src, n);
+// Issues the TMA load of an item's input box into a raw buffer: bytes
+// [8 cx0 - 16, 8 cx0 + 80) of rows [8 cy0 - 7, 8 cy0 + 65) of its level (the
+// x coordinate is a multiple of 16 bytes; outside the level the box reads
+// zeros, and the conversion zeroes those pixels anyway).
+__device__ __forceinline__ void load_input(uint8_t (*raw)[kRawW], unsigned long long *bar,
+                                           const CUtensorMap *__restrict__ maps, const CnnItem &it) {
+    const uint32_t b = smem_u32(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"((uint32_t)(kRawW * XR))
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(&raw[0][0])),
+        "l"(reinterpret_cast<uint64_t>(maps + it.level)), "r"(8 * it.cx0 - 16), "r"(8 * it.cy0 - 7), "r"(b)
+        : "memory");
+}
+
+// Bounded wait (every thread) for phase `parity` of a barrier.
+__device__ __forceinline__ bool bar_wait(unsigned long long *bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    uint32_t ok = 0;
+    const uint64_t t0 = global_ns();
+    while (true) {
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok || global_ns() - t0 > kWaitNs) break;
     }
+    return ok != 0;
 }
 
 // Position of layer-2 edge index e (row 16, then column 16): (r, c).
@@ -235,7 +237,7 @@ __device__ __forceinline__ int2 edge_pos(int e) {
 }
 
 __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__restrict__ levels,
-                                                         const uint8_t *__restrict__ pyr,
+                                                         const CUtensorMap *__restrict__ lvl_maps,
                                                          const CnnItem *__restrict__ items, int n_items,
                                                          const CnnWeights wts, float *__restrict__ hmap,
                                                          int32_t hmap_pitch, unsigned *__restrict__ err) {
@@ -245,8 +247,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__rest
     const int g = lane >> 2, t = lane & 3;
     int item = blockIdx.x;
     if (item >= n_items) return;
-    stage_input(S.raw[0], items, levels, pyr, item, tid);
-    cp_async_commit();
+    if (smem_u32(S.raw) & 127u) {  // TMA destinations need 128-byte alignment: never expected
+        if (tid == 0 && err) atomicOr(err, kErrTimeout);
+        return;
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.inbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.inbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        load_input(S.raw[0], &S.inbar[0], lvl_maps, items[item]);
+    }
+    // thread 0: loads issued and not yet consumed (bit b: raw buffer b) and their phase parities
+    uint32_t pend = tid == 0 ? 1u : 0u, ppar = 0u;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
@@ -312,10 +324,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__rest
     for (int iter = 0; item < n_items && !S.failed; ++iter, item += gridDim.x) {
         const int cur = iter & 1;
         const int next = item + gridDim.x;
-        if (next < n_items) stage_input(S.raw[cur ^ 1], items, levels, pyr, next, tid);
-        cp_async_commit();
-        cp_async_wait_prev();  // this thread's copies of the current tile have landed
-        __syncthreads();       // everyone's have; the previous tile is finished
+        if (tid == 0 && next < n_items) {
+            async_proxy_fence();  // the buffer's previous bytes were read by the generic proxy
+            load_input(S.raw[cur ^ 1], &S.inbar[cur ^ 1], lvl_maps, items[next]);
+            pend |= 1u << (cur ^ 1);
+            ppar = (ppar & ~(1u << (cur ^ 1))) | ((((uint32_t)(iter + 1) >> 1) & 1u) << (cur ^ 1));
+        }
+        // this tile's input: phase iter / 2 of its buffer's barrier (CTA-uniform decision)
+        const bool in_ok = bar_wait(&S.inbar[cur], (uint32_t)(iter >> 1) & 1u);
+        if (tid == 0 && in_ok) pend &= ~(1u << cur);
+        if (__syncthreads_or(!in_ok)) {
+            if (tid == 0) {
+                S.failed = 1;
+                if (err) atomicOr(err, kErrTimeout);
+            }
+            break;
+        }
 
         const CnnItem it = items[item];
         const LevelDesc L = levels[it.level];
@@ -329,14 +353,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__rest
         const bool interior1 = y1 >= 0 && x1 >= 0 && y1 + R1 <= H1 && x1 + R1 <= W1;
         const bool interior2 = y2 >= 0 && x2 >= 0 && y2 + R2 <= H2 && x2 + R2 <= W2;
 
-        // ---- pixels -> bf16 x; xb[r][c] = x(y0 + r, x0 + c) = raw[r][c + 1].
+        // ---- pixels -> bf16 x; xb[r][c] = x(y0 + r, x0 + c) = raw[r][c + 9].
         // x = bf16(L/255 - 0.5): one fma in float32 rounded once to bf16 equals
         // the correctly rounded value for all 256 inputs (checked exhaustively
         // against exact rational arithmetic when this path was written).
         for (int k = tid; k < XR * (XR / 4); k += kThreads) {
             const int r = k / (XR / 4), j = k - r * (XR / 4);
             const uint32_t *rw = reinterpret_cast<const uint32_t *>(S.raw[cur][r]);
-            const uint32_t v = __byte_perm(rw[j], rw[j + 1], 0x4321);
+            const uint32_t v = __byte_perm(rw[j + 2], rw[j + 3], 0x4321);  // bytes 4j + 9 .. 4j + 12
             const int y = y0 + r, xc = x0 + 4 * j;
             const bool rin = y >= 0 && y < Hk;
             float e[4];
@@ -496,7 +520,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__rest
                 hmap[(int64_t)(L.cell_row + cy) * hmap_pitch + cx] = bh + S.hpart[0][tid] + S.hpart[1][tid];
         }
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    // drain loads still in flight (bounded) before the CTA leaves
+    if (tid == 0)
+        for (int b = 0; b < 2; ++b)
+            if ((pend >> b) & 1u) bar_wait(&S.inbar[b], (ppar >> b) & 1u);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -570,13 +597,13 @@ cudaError_t init_cnn() {
     return cudaFuncSetAttribute(k_cnn_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CnnSmem));
 }
 
-cudaError_t launch_cnn(cudaStream_t s, const LevelDesc *d_levels, int n_levels, const uint8_t *pyr,
+cudaError_t launch_cnn(cudaStream_t s, const LevelDesc *d_levels, int n_levels, const CUtensorMap *lvl_maps,
                        const CnnItem *d_items, int n_items, const CnnWeights &w, float *hmap,
                        int32_t hmap_pitch, float *logits, int pool_tiles, unsigned *err) {
     if (n_items > 0) {
         const int grid = std::min(n_items, g_cnn_grid > 0 ? g_cnn_grid : n_items);
-        k_cnn_fwd<<<grid, kThreads, sizeof(CnnSmem), s>>>(d_levels, pyr, d_items, n_items, w, hmap, hmap_pitch,
-                                                           err);
+        k_cnn_fwd<<<grid, kThreads, sizeof(CnnSmem), s>>>(d_levels, lvl_maps, d_items, n_items, w, hmap,
+                                                           hmap_pitch, err);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -356,7 +356,7 @@ cudaError_t launch_train_step(cudaStream_t s, const TrainArgs &a) {
     CnnWeights pw = a.w;
     pw.v = a.wr + kOffV;
     pw.bv = a.wr + kOffBv;
-    e = launch_cnn(s, a.levels, nl, nullptr, nullptr, 0, pw, a.hmap, a.hp, a.logits, a.pool_tiles, nullptr);
+    e = launch_cnn(s, a.levels, nl, nullptr, nullptr, 0, pw, a.hmap, a.hp, a.logits, a.pool_tiles, nullptr);  // pooling only
     if (e != cudaSuccess) return e;
     // loss and backward
     t_loss<<<nl, 256, 0, s>>>(a.tl, a.levels, a.logits, a.scores, a.label_thr, a.pos_weight, a.inv_n, a.dz,

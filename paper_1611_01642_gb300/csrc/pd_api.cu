@@ -76,7 +76,7 @@ struct Plan {
 
 // Byte offsets of the plan's sections inside the packed descriptor block.
 struct Packed {
-    int64_t frames, levels, r_items, c_items, s_items, cnn_items, tabs, total;
+    int64_t frames, levels, r_items, c_items, s_items, cnn_items, tabs, tmaps, total;
 };
 
 Packed pack_layout(const Plan &p) {
@@ -94,6 +94,8 @@ Packed pack_layout(const Plan &p) {
     o.s_items = take((int64_t)p.s_items.size() * sizeof(SvmItem));
     o.cnn_items = take((int64_t)p.cnn_items.size() * sizeof(CnnItem));
     o.tabs = take((int64_t)p.tabs.size() * sizeof(int32_t));
+    off = round_up(off, 64);  // tensor maps: 64-byte aligned
+    o.tmaps = take(p.cnn_items.empty() ? 0 : (int64_t)p.levels.size() * sizeof(CUtensorMap));
     o.total = off;
     return o;
 }
@@ -176,6 +178,21 @@ int encode_plane_map(CUtensorMap *map, void *base, CUtensorMapDataType dtype, in
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(map, dtype, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? PD_OK : PD_ECUDA;
+}
+
+// 2D map over one pyramid level (u8 [Hk][pitch]) for the proposal network's
+// input tiles.
+int encode_level_map(CUtensorMap *map, const uint8_t *base, int Wk, int Hk, int pitch) {
+    auto fn = get_encode();
+    if (!fn) return PD_ECUDA;
+    cuuint64_t dims[2] = {(cuuint64_t)Wk, (cuuint64_t)Hk};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch};
+    cuuint32_t box[2] = {(cuuint32_t)kCnnBoxW, (cuuint32_t)kCnnBoxH};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? PD_OK : PD_ECUDA;
 }
@@ -428,7 +445,7 @@ bool params_ok(const pd_params *p) {
 }
 
 // Packs the plan into the pinned staging buffer and sends it to the device.
-int upload_plan(pd_handle *h, cudaStream_t s, const Plan &p, Packed &o) {
+int upload_plan(pd_handle *h, cudaStream_t s, const Plan &p, Packed &o, const uint8_t *pyr_base = nullptr) {
     o = pack_layout(p);
     if (o.total > h->desc_cap) return fail(h, PD_EINVAL, "plan descriptors exceed the arena");
     PD_CUDA(h, cudaEventSynchronize(h->desc_done));  // previous copy has left the staging buffer
@@ -442,6 +459,14 @@ int upload_plan(pd_handle *h, cudaStream_t s, const Plan &p, Packed &o) {
     put(o.s_items, p.s_items.data(), p.s_items.size() * sizeof(SvmItem));
     put(o.cnn_items, p.cnn_items.data(), p.cnn_items.size() * sizeof(CnnItem));
     put(o.tabs, p.tabs.data(), p.tabs.size() * sizeof(int32_t));
+    if (!p.cnn_items.empty()) {
+        CUtensorMap *maps = reinterpret_cast<CUtensorMap *>(h->h_desc + o.tmaps);
+        for (size_t k = 0; k < p.levels.size(); ++k) {
+            const LevelDesc &L = p.levels[k];
+            if (encode_level_map(&maps[k], pyr_base + L.img_off, L.Wk, L.Hk, L.img_pitch) != PD_OK)
+                return fail(h, PD_ECUDA, "level tensor map");
+        }
+    }
     if (o.total) PD_CUDA(h, cudaMemcpyAsync(h->d_desc, h->h_desc, o.total, cudaMemcpyHostToDevice, s));
     PD_CUDA(h, cudaEventRecord(h->desc_done, s));
     return PD_OK;
@@ -650,7 +675,8 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
         for (const LevelDesc &L : one.levels)
             cnn_bound += (int64_t)((L.Hc + kCnnTile - 1) / kCnnTile) * ((L.Wc + kCnnTile - 1) / kCnnTile);
         h->flag_cap = F * std::max<int64_t>(s_bound, (int64_t)one.c_items.size()) + 64;
-        h->desc_cap = round_up(F * cnn_bound * (int64_t)sizeof(CnnItem), 16) +
+        h->desc_cap = round_up(F * (int64_t)one.levels.size() * (int64_t)sizeof(CUtensorMap), 64) + 128 +
+                      round_up(F * cnn_bound * (int64_t)sizeof(CnnItem), 16) +
                       round_up(F * (int64_t)sizeof(FrameDesc), 16) +
                       round_up(F * (int64_t)one.levels.size() * (int64_t)sizeof(LevelDesc), 16) +
                       round_up(F * (int64_t)one.r_items.size() * (int64_t)sizeof(ResizeItem), 16) +
@@ -806,7 +832,7 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
             (int64_t)p.s_items.size() > h->flag_cap || (int64_t)p.c_items.size() > h->flag_cap)
             return fail(h, PD_EINVAL, "batch exceeds the arena");
         // full descriptor upload, once per batch shape
-        int r = upload_plan(h, s, p, h->packed);
+        int r = upload_plan(h, s, p, h->packed, h->d_pyr);
         if (r != PD_OK) return r;
         h->sig = sig;
         h->cache_valid = true;
@@ -838,7 +864,8 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
         const uint32_t *cf = nullptr, *sf = nullptr;
         if (h->proposal) {
             // learned proposal: keep-logits of every window, then the tiles to score
-            PD_CUDA(h, launch_cnn(q, dl, (int)p.levels.size(), h->d_pyr, dptr<CnnItem>(h, o.cnn_items),
+            PD_CUDA(h, launch_cnn(q, dl, (int)p.levels.size(), dptr<CUtensorMap>(h, o.tmaps),
+                                  dptr<CnnItem>(h, o.cnn_items),
                                   (int)p.cnn_items.size(), cnn_weights(h), h->hmap, h->atlas.pitch, h->logits,
                                   max_pool_tiles(p), h->d_err));
             PD_CUDA(h, cudaMemsetAsync(h->c_flag, 0, p.c_items.size() * 4 + 4, q));
@@ -1008,8 +1035,8 @@ int pd_cnn_forward(pd_handle *h, void *stream, const uint8_t *d_level, int Wk, i
         if (r != PD_OK) return r;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    // the kernel fetches 8-byte chunks of level rows: other layouts go through the pyramid buffer
-    if (((uintptr_t)d_level | (uintptr_t)pitch) & 7u) {
+    // the kernel's TMA needs 16-byte aligned rows: other layouts go through the pyramid buffer
+    if (((uintptr_t)d_level | (uintptr_t)pitch) & 15u) {
         const int lp = (int)round_up(Wk, 16);
         if ((int64_t)lp * Hk > h->pyr_cap) return fail(h, PD_EINVAL, "pd_cnn_forward: level larger than the arena");
         PD_CUDA(h, cudaMemcpy2DAsync(h->d_pyr, lp, d_level, pitch, Wk, Hk, cudaMemcpyDeviceToDevice, s));
@@ -1024,10 +1051,10 @@ int pd_cnn_forward(pd_handle *h, void *stream, const uint8_t *d_level, int Wk, i
     for (int cy = 0; cy < Hc; cy += kCnnTile)
         for (int cx = 0; cx < Wc; cx += kCnnTile) p.cnn_items.push_back({0, cy, cx, 0});
     Packed o;
-    int r = upload_plan(h, s, p, o);
+    int r = upload_plan(h, s, p, o, d_level);
     if (r != PD_OK) return r;
-    PD_CUDA(h, launch_cnn(s, dptr<LevelDesc>(h, o.levels), p.levels[0].rows > 0 ? 1 : 0, d_level,
-                          dptr<CnnItem>(h, o.cnn_items), (int)p.cnn_items.size(), cnn_weights(h), d_h, h_pitch,
+    PD_CUDA(h, launch_cnn(s, dptr<LevelDesc>(h, o.levels), p.levels[0].rows > 0 ? 1 : 0,
+                          dptr<CUtensorMap>(h, o.tmaps), dptr<CnnItem>(h, o.cnn_items), (int)p.cnn_items.size(), cnn_weights(h), d_h, h_pitch,
                           d_logits, max_pool_tiles(p), h->d_err));
     return PD_OK;
 }

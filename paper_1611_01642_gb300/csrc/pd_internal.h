@@ -158,7 +158,11 @@ constexpr int kPoolTW = 64, kPoolTH = 16;
 inline int pool_tiles_of(int rows, int cols) {
     return rows > 0 && cols > 0 ? ((cols + kPoolTW - 1) / kPoolTW) * ((rows + kPoolTH - 1) / kPoolTH) : 0;
 }
-cudaError_t launch_cnn(cudaStream_t s, const LevelDesc *d_levels, int n_levels, const uint8_t *pyr,
+// Input tile of one proposal-network item: bytes [8 cx0 - 16, 8 cx0 + 80) of
+// level rows [8 cy0 - 7, 8 cy0 + 65), fetched by TMA through one 2D tensor
+// map per level (u8, box 96 x 72, zero fill outside the level).
+constexpr int kCnnBoxW = 96, kCnnBoxH = 72;
+cudaError_t launch_cnn(cudaStream_t s, const LevelDesc *d_levels, int n_levels, const CUtensorMap *lvl_maps,
                        const CnnItem *d_items, int n_items, const CnnWeights &w, float *hmap,
                        int32_t hmap_pitch, float *logits, int pool_tiles, unsigned *err);
 cudaError_t launch_train_step(cudaStream_t s, const TrainArgs &a);
