@@ -23,16 +23,6 @@ constexpr int kTileH = kResizeTH;       // 32
 constexpr int kSmemW = kTileW + 4;      // 129 used, padded
 constexpr int kSmemH = kTileH + 1;      // 33
 
-// First output coordinate whose source index is >= s (table is non-decreasing).
-__device__ __forceinline__ int lower_bound_src(const int32_t *tab, int n, int s) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if ((tab[mid] >> 11) < s) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
 __global__ void __launch_bounds__(kThreads) k_resize(const FrameDesc *__restrict__ frames,
                                                      const LevelDesc *__restrict__ levels,
                                                      const int32_t *__restrict__ tabs,
@@ -54,15 +44,16 @@ __global__ void __launch_bounds__(kThreads) k_resize(const FrameDesc *__restrict
         int y = min(it.y0 + r, fd.H - 1), x = min(it.x0 + c, fd.W - 1);
         tile[r][c] = fd.ptr[(size_t)y * fd.pitch + x];
     }
-    // Output ranges of every level (one thread per level).
+    // Output ranges of every level (one thread per level), from the
+    // planner's per-tile boundary tables.
     for (int k = tid; k < fd.n_levels; k += kThreads) {
         const LevelDesc L = levels[fd.first_level + k];
-        const int32_t *xt = tabs + L.xtab_off, *yt = tabs + L.ytab_off;
+        const int tx = it.x0 / kTileW, ty = it.y0 / kTileH;
         int4 r;
-        r.x = lower_bound_src(xt, L.Wk, it.x0);
-        r.y = lower_bound_src(xt, L.Wk, it.x0 + kTileW);
-        r.z = lower_bound_src(yt, L.Hk, it.y0);
-        r.w = lower_bound_src(yt, L.Hk, it.y0 + kTileH);
+        r.x = __ldg(tabs + L.xbnd_off + tx);
+        r.y = __ldg(tabs + L.xbnd_off + tx + 1);
+        r.z = __ldg(tabs + L.ybnd_off + ty);
+        r.w = __ldg(tabs + L.ybnd_off + ty + 1);
         ranges[k] = r;
     }
     __syncthreads();

@@ -379,11 +379,26 @@ void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int
     if (share) {
         L.xtab_off = share->xtab_off;
         L.ytab_off = share->ytab_off;
+        L.xbnd_off = share->xbnd_off;
+        L.ybnd_off = share->ybnd_off;
     } else {
         L.xtab_off = (int32_t)p.tabs.size();
         for (int x = 0; x < Wk; ++x) p.tabs.push_back(q11_entry(x, W, Wk));
         L.ytab_off = (int32_t)p.tabs.size();
         for (int y = 0; y < Hk; ++y) p.tabs.push_back(q11_entry(y, H, Hk));
+        // K1 output ranges of every source tile: boundaries t * tile of the
+        // (non-decreasing) source index, t = 0 .. ceil(n / tile)
+        auto bounds = [&](int32_t tab_off, int n_out, int n_src, int tile) {
+            const int32_t at = (int32_t)p.tabs.size();
+            int x = 0;
+            for (int t = 0; t <= (n_src + tile - 1) / tile; ++t) {
+                while (x < n_out && (p.tabs[tab_off + x] >> 11) < t * tile) ++x;
+                p.tabs.push_back(x);
+            }
+            return at;
+        };
+        L.xbnd_off = bounds(L.xtab_off, Wk, W, kResizeTW);
+        L.ybnd_off = bounds(L.ytab_off, Hk, H, kResizeTH);
     }
     const int li = (int)p.levels.size();
     L.citem0 = (int32_t)p.c_items.size();

@@ -47,6 +47,8 @@ struct LevelDesc {
     int32_t ytab_off;   // Q11 source-row table of this level (Hk entries)
     int32_t citem0;     // index of this level's first K2+K3 item
     int32_t ctx;        // K2+K3 tiles per row of cells
+    int32_t xbnd_off;   // per K1 source-tile column t: first output column whose source is >= 128 t
+    int32_t ybnd_off;   // per K1 source-tile row t: first output row whose source is >= 32 t
 };
 
 // Work items (one CTA each).
