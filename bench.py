@@ -54,6 +54,8 @@ def parse_args(argv=None):
                     help="timed steps of the 16x1920x1080 plain-vs-sparse comparison (0: skip)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default K4 tile costs (profiler captures of a fixed plan)")
+    ap.add_argument("--proposal-4k", type=int, default=1,
+                    help="also compare plain and sparse on the 4K mix (16 x 3840x2160 + 48 x 1242x375)")
     ap.add_argument("--proposal-frames", type=int, default=16,
                     help="frames of the proposal comparison (16 is the workload; fewer for profiler captures)")
     return ap.parse_args(argv)
@@ -226,8 +228,9 @@ def measured_peaks():
 PROPOSAL_CKPT = os.path.join(ROOT, "paper_1611_01642_gb300", "weights", "proposal_1920x1080.npz")
 
 
-def run_proposal(args, pd, torch, flush):
-    """Plain vs sparse (learned proposal) path on 16 synthetic 1920x1080 frames (scene recipe 4).
+def run_proposal(args, pd, torch, flush, recipe: int = 4):
+    """Plain vs sparse (learned proposal) path on a batch of synthetic frames: scene recipe 4
+    (16 x 1920x1080) or 5 (16 x 3840x2160 + 48 x 1242x375).
 
     Both paths run the same frames with the same timing rules as the main line (L2 flushed before
     every step, CUDA events on the detector's stream). Recall and keep fraction are counted window
@@ -238,11 +241,11 @@ def run_proposal(args, pd, torch, flush):
     from paper_1611_01642_gb300 import proposal as prop
     params, meta = prop.load_checkpoint(PROPOSAL_CKPT)
     tau = float(meta["keep_logit_threshold"])
-    imgs = synth.make_frames(4, limit=args.proposal_frames)
+    imgs = synth.make_frames(recipe, limit=args.proposal_frames if recipe == 4 else None)
     frames = [torch.from_numpy(im).cuda() for im in imgs]
     w, b = load_template()
-    det = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=len(frames), max_width=1920, max_height=1080,
-                      flags=pd.PD_FLAG_STAGE_TIMING)
+    det = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=len(frames), max_width=max(im.shape[1] for im in imgs),
+                      max_height=max(im.shape[0] for im in imgs), flags=pd.PD_FLAG_STAGE_TIMING)
     pd.pd_cnn_set_params(det.h, params)
     stream = torch.cuda.current_stream()
 
@@ -278,8 +281,10 @@ def run_proposal(args, pd, torch, flush):
     det.close()
     names = ["pyramid", "cells", "norm_svm", "nms", "proposal"]
     return {
-        "workload": f"{len(imgs)} x 1920x1080 u8 frames (scene recipe 4: Poisson(10) silhouettes, "
-                    "48 px..0.8H), pyramid factor 1.05 (44 levels)",
+        "workload": (f"{len(imgs)} x 1920x1080 u8 frames (scene recipe 4: Poisson(10) silhouettes, "
+                     "48 px..0.8H), pyramid factor 1.05 (44 levels)") if recipe == 4 else
+                    ("16 x 3840x2160 + 48 x 1242x375 u8 frames in one batch (scene recipe 5: Poisson(10) "
+                     "silhouettes, 48..600 px), pyramid factor 1.05 (58 / 23 levels)"),
         "checkpoint": os.path.relpath(PROPOSAL_CKPT, ROOT), "keep_logit_threshold": tau,
         "plain_frames_per_s": len(frames) / (ms_plain / 1e3),
         "sparse_frames_per_s": len(frames) / (ms_sparse / 1e3),
@@ -385,9 +390,11 @@ def run_gpu(args):
                 "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                               f"(max SM clock, {peak_kind})"}
 
-    proposal = None
+    proposal = proposal_4k = None
     if rank == 0 and args.proposal_steps > 0 and os.path.exists(PROPOSAL_CKPT):
         proposal = run_proposal(args, pd, torch, flush)
+        if args.proposal_4k:
+            proposal_4k = run_proposal(args, pd, torch, flush, recipe=5)
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_sample_frames > 0:
@@ -414,6 +421,7 @@ def run_gpu(args):
         "stage_ms_per_step": {"pyramid": stage_step[0], "cells": stage_step[1], "norm_svm": stage_step[2],
                               "nms": stage_step[3]},
         "proposal": proposal,
+        "proposal_4k_mix": proposal_4k,
         "px_per_ns": B * WIDTH * HEIGHT / (ms_step * 1e6),
     }
     if rank == 0:
