@@ -237,7 +237,6 @@ struct pd_handle {
     float *cnn = nullptr;           // [5][kCnnParams]: master, m, v, grad, rounded
     float *in_tab = nullptr;        // [256]
     uint32_t *w2frag = nullptr;     // [2304]
-    uint32_t *w3frag = nullptr;     // [4608]
     float *hmap = nullptr;          // one f32 plane over the cell atlas
     float *logits = nullptr;        // window logits, score-map layout
     bool cnn_loaded = false, frag_stale = false;
@@ -564,7 +563,6 @@ CnnWeights cnn_weights(const pd_handle *h) {
     w.w2 = wr + kOffW2;
     w.w3 = wr + kOffW3;
     w.b2 = wr + kOffB2;
-    w.w3frag = h->w3frag;
     w.b3 = wr + kOffB3;
     w.wh = wr + kOffWh;
     w.bh = wr + kOffBh;
@@ -580,15 +578,12 @@ int refresh_fragments(pd_handle *h) {
     PD_CUDA(h, cudaDeviceSynchronize());
     std::vector<float> p(kCnnParams);
     PD_CUDA(h, cudaMemcpy(p.data(), h->cnn, kCnnParams * 4, cudaMemcpyDeviceToHost));
-    std::vector<uint32_t> f2(2304), f3(4608);
+    // layer 2's mma.sync B fragments (its edge positions); the tcgen05 operands
+    // are built by the kernel from the rounded weights
+    std::vector<uint32_t> f2(2304);
     for (int tap = 0; tap < 9; ++tap)
         for (int nt = 0; nt < 4; ++nt) pack_frag(p.data() + kOffW2, 16, 0, tap, nt, &f2[(tap * 4 + nt) * 64]);
-    for (int tap = 0; tap < 9; ++tap)
-        for (int kh = 0; kh < 2; ++kh)
-            for (int nt = 0; nt < 4; ++nt)
-                pack_frag(p.data() + kOffW3, 32, 16 * kh, tap, nt, &f3[((tap * 2 + kh) * 4 + nt) * 64]);
     PD_CUDA(h, cudaMemcpy(h->w2frag, f2.data(), f2.size() * 4, cudaMemcpyHostToDevice));
-    PD_CUDA(h, cudaMemcpy(h->w3frag, f3.data(), f3.size() * 4, cudaMemcpyHostToDevice));
     h->frag_stale = false;
     return PD_OK;
 }
@@ -726,7 +721,7 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
         {(int64_t)params->max_frames * 2 * 4 + 16, 0},             // 8 counts + error word
         {h->frames_cap, 0},                                        // 9 host-input frames
         {(int64_t)params->max_frames * params->max_candidates_per_frame * 16, 0},  // 10 NMS scratch
-        {(int64_t)5 * kCnnParams * 4 + 1024 + 2304 * 4 + 4608 * 4, 0},             // 11 CNN parameters
+        {(int64_t)5 * kCnnParams * 4 + 1024 + 2304 * 4, 0},                        // 11 CNN parameters
         {(int64_t)rows * P * 4, 0},                                                 // 12 head values
         {h->score_cap * 4, 0},                                                      // 13 window logits
         {2 * h->flag_cap * 4, 0},                                                   // 14 tile flags
@@ -754,7 +749,6 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
     h->cnn = reinterpret_cast<float *>(h->arena + parts[11].off);
     h->in_tab = h->cnn + 5 * kCnnParams;
     h->w2frag = reinterpret_cast<uint32_t *>(h->in_tab + 256);
-    h->w3frag = h->w2frag + 2304;
     h->hmap = reinterpret_cast<float *>(h->arena + parts[12].off);
     h->logits = reinterpret_cast<float *>(h->arena + parts[13].off);
     h->s_flag = reinterpret_cast<uint32_t *>(h->arena + parts[14].off);

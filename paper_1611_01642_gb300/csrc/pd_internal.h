@@ -119,7 +119,6 @@ struct CnnWeights {
     const float *w1, *b1;     // [16][9] (bf16-rounded), [16]
     const uint32_t *w2frag;   // layer-2 mma B fragments [9 taps][4 n-tiles][32 lanes][2]
     const float *b2;          // [32]
-    const uint32_t *w3frag;   // layer-3 mma B fragments [9][2 k-halves][4][32][2]
     const float *w2, *w3;     // [32][16][3][3], [32][32][3][3] (bf16-rounded)
     const float *b3, *wh;     // [32], [32]
     const float *bh;          // [1]
