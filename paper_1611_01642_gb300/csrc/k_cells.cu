@@ -116,11 +116,11 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
     for (int i = tid; i < kRing * kTW * kLbpWords; i += kThreads) (&S.cnt[0][0][0])[i] = 0u;
     for (int i = tid; i < 256; i += kThreads) S.map[i] = lbp_map[i];
     const int px0 = 8 * it.cx0 - 5, py0 = 8 * it.cy0 - 5;
-    if (tid < kPixRows) {
+    for (int r = tid; r < kPixRows; r += kThreads) {
         // row y votes into cell rows floor(u), floor(u)+1 (u = (y-3.5)/8,
         // clamped into the grid) with weights 1-frac, frac; slot -1 = not
         // in this tile
-        const int y = py0 + tid;
+        const int y = py0 + r;
         const float uy = ((float)y - 3.5f) * 0.125f;
         const float fy = floorf(uy);
         const float w1 = uy - fy;
@@ -131,8 +131,9 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
         e.y = (c1 >= 0 && c1 < kTH) ? (c1 & 1) : -1;
         e.z = __float_as_int(1.f - w1);
         e.w = __float_as_int(w1);
-        S.yv[tid] = e;
+        S.yv[r] = e;
     }
+    static_assert(kPixCols <= 2 * kThreads, "two staged columns per thread at most");
     {
         const int c0 = tid, c1 = tid + kThreads;
         const int x0c = clampi(px0 + c0, 0, Wk - 1);
