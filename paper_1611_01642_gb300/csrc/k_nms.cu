@@ -145,19 +145,32 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
         const LevelDesc L = levels[fd.first_level + k];
         const int n = L.rows * L.cols;
         const float *sc = scores + L.score_off;
-        for (int i0 = 0; i0 < n; i0 += kThreads) {  // warp-aggregated appends
-            const int i = i0 + tid;
-            const float s = i < n ? sc[i] : 0.f;
-            const bool hit = i < n && s > threshold;
-            const unsigned m = __ballot_sync(0xffffffffu, hit);
-            int base = 0;
-            if ((tid & 31) == 0 && m) base = atomicAdd(&n_cand, __popc(m));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (hit) {
-                const int idx = base + __popc(m & ((1u << (tid & 31)) - 1u));
-                if (idx < cap) {
-                    const int wy = i / L.cols;
-                    keys[idx] = make_key(s, k, wy, i - wy * L.cols);
+        // warp-aggregated appends; kUnroll independent loads per thread are in
+        // flight before any of them is used (the scan is latency-bound otherwise)
+        constexpr int kUnroll = 8;
+        for (int i0 = 0; i0 < n; i0 += kThreads * kUnroll) {
+            float sv[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int i = i0 + u * kThreads + tid;
+                sv[u] = i < n ? __ldg(sc + i) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int i = i0 + u * kThreads + tid;
+                if (i0 + u * kThreads >= n) break;  // block-uniform
+                const float s = sv[u];
+                const bool hit = i < n && s > threshold;
+                const unsigned m = __ballot_sync(0xffffffffu, hit);
+                int base = 0;
+                if ((tid & 31) == 0 && m) base = atomicAdd(&n_cand, __popc(m));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (hit) {
+                    const int idx = base + __popc(m & ((1u << (tid & 31)) - 1u));
+                    if (idx < cap) {
+                        const int wy = i / L.cols;
+                        keys[idx] = make_key(s, k, wy, i - wy * L.cols);
+                    }
                 }
             }
         }
