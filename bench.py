@@ -363,19 +363,39 @@ def run_gpu(args):
     ms_step = total_ms / args.steps
     stage_step = stage_ms / args.steps
 
-    # end to end through the public API: host frames in, host boxes out
+    # end to end through the public API: host frames in, host boxes out. Two
+    # handles alternate so that step i's results are read on the host while
+    # step i+1 already runs (each step still copies its frames in and its
+    # boxes out inside the timed region).
+    det2 = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=B, max_width=WIDTH, max_height=HEIGHT)
+    pd.pd_set_tile_costs(det2.h, tile_costs)
+    for _ in range(2):
+        det2.detect_host(pinned)
+        det2.sync()
+    dets = [det, det2]
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     d2h = 0
-    for i in range(args.steps):
-        det.detect_host(pinned)
-        st = det.sync()
+
+    def finish(d):
+        st = d.sync()
         if st != pd.PD_OK:
             raise RuntimeError(f"pd_sync: {pd.ERROR_NAMES.get(st, st)}")
-        d2h += 8 * B + 4 + sum(32 * len(det.boxes(f)) for f in range(B))
+        return 8 * B + 4 + sum(32 * len(d.boxes(f)) for f in range(B))
+
+    pending = None
+    for i in range(args.steps):
+        d = dets[i & 1]
+        d.detect_host(pinned)
+        if pending is not None:
+            d2h += finish(pending)
+        pending = d
+    if pending is not None:
+        d2h += finish(pending)
     torch.cuda.synchronize()
     e2e_s = reduce_max(time.perf_counter() - t0, world, device="cuda")
+    det2.close()
     e2e = {"value": world * B * args.steps / e2e_s, "unit": "frames/s",
            "h2d_bytes_per_step": int(sum(im.nbytes for im in imgs)),
            "d2h_bytes_per_step": int(d2h // max(args.steps, 1))}
