@@ -244,11 +244,14 @@ def pd_scores(h):
 
 
 def pd_boxes(h, frame: int, cap: int = 4096) -> np.ndarray:
-    out = (pd_box * max(cap, 1))()
+    """Kept boxes of one frame as a BOX_DTYPE array (at most cap of them)."""
     count = ctypes.c_int(0)
-    _check(load().pd_boxes(h, frame, out, cap, ctypes.byref(count)), h)
-    k = min(count.value, cap)
-    return np.frombuffer(bytes(memoryview(out))[:k * ctypes.sizeof(pd_box)], dtype=BOX_DTYPE).copy()
+    lib = load()
+    _check(lib.pd_boxes(h, frame, None, 0, ctypes.byref(count)), h)
+    out = np.empty(min(count.value, cap), dtype=BOX_DTYPE)
+    if out.size:
+        _check(lib.pd_boxes(h, frame, out.ctypes.data_as(ctypes.c_void_p), out.size, ctypes.byref(count)), h)
+    return out
 
 
 def pd_last_launch_count(h) -> int:
