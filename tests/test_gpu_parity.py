@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
-Bars (written here, derived in the design doc):
+Bars (written here; each follows from the arithmetic of the step it checks):
   * resize, LBP codes/counts: bit-exact;
   * HOG cell histogram: |gpu - ref| <= 1e-4 * sum_bins |ref_cell| + 1e-6;
   * window score: |gpu - ref| <= 1e-4 * (|b| + sum_t |w_t x_t|), the scale of
