@@ -58,26 +58,34 @@ __global__ void __launch_bounds__(kThreads) k_resize(const FrameDesc *__restrict
     }
     __syncthreads();
 
-    const int tx = tid & (kTileW - 1), ty = tid >> 7;  // 128 columns x 2 rows
+    // two adjacent output columns per thread (they share the row lookups and
+    // the address work): 64 column pairs x 4 rows per pass
+    const int tx = tid & 63, ty = tid >> 6;
     for (int k = 0; k < fd.n_levels; ++k) {
         const int4 r = ranges[k];
-        const int x = r.x + tx;
+        const int x = r.x + 2 * tx;
         if (x >= r.y) continue;
+        const bool two = x + 1 < r.y;
         const LevelDesc L = levels[fd.first_level + k];
-        const int32_t ex = __ldg(tabs + L.xtab_off + x);
-        const int sx0 = (ex >> 11) - it.x0, ax = ex & 2047;
-        const int sx1 = min((ex >> 11) + 1, fd.W - 1) - it.x0;
+        const int32_t ex0 = __ldg(tabs + L.xtab_off + x);
+        const int32_t ex1 = two ? __ldg(tabs + L.xtab_off + x + 1) : ex0;
+        const int a0 = (ex0 >> 11) - it.x0, ax0 = ex0 & 2047;
+        const int b0 = min((ex0 >> 11) + 1, fd.W - 1) - it.x0;
+        const int a1 = (ex1 >> 11) - it.x0, ax1 = ex1 & 2047;
+        const int b1 = min((ex1 >> 11) + 1, fd.W - 1) - it.x0;
         uint8_t *out = pyr + L.img_off + x;
-        for (int y = r.z + ty; y < r.w; y += 2) {
+        for (int y = r.z + ty; y < r.w; y += 4) {
             const int32_t ey = __ldg(tabs + L.ytab_off + y);
             const int sy0 = (ey >> 11) - it.y0, ay = ey & 2047;
             const int sy1 = min((ey >> 11) + 1, fd.H - 1) - it.y0;
-            const int i00 = tile[sy0][sx0], i01 = tile[sy0][sx1];
-            const int i10 = tile[sy1][sx0], i11 = tile[sy1][sx1];
-            const int top = (2048 - ax) * i00 + ax * i01;
-            const int bot = (2048 - ax) * i10 + ax * i11;
-            const int v = ((2048 - ay) * top + ay * bot + (1 << 21)) >> 22;
-            out[(size_t)y * L.img_pitch] = (uint8_t)v;
+            const uint8_t *t0 = tile[sy0], *t1 = tile[sy1];
+            const int top0 = (2048 - ax0) * t0[a0] + ax0 * t0[b0];
+            const int bot0 = (2048 - ax0) * t1[a0] + ax0 * t1[b0];
+            const int top1 = (2048 - ax1) * t0[a1] + ax1 * t0[b1];
+            const int bot1 = (2048 - ax1) * t1[a1] + ax1 * t1[b1];
+            uint8_t *o = out + (size_t)y * L.img_pitch;
+            o[0] = (uint8_t)(((2048 - ay) * top0 + ay * bot0 + (1 << 21)) >> 22);
+            if (two) o[1] = (uint8_t)(((2048 - ay) * top1 + ay * bot1 + (1 << 21)) >> 22);
         }
     }
 }
