@@ -61,6 +61,8 @@ def _load():
             i, d, f = ctypes.c_int, ctypes.c_double, ctypes.c_float
             lib.pdo_pyramid.argtypes = [i, i, d, i, P, P]
             lib.pdo_pyramid.restype = i
+            lib.pdo_pyramid_up.argtypes = [i, i, d, i, i, P, P]
+            lib.pdo_pyramid_up.restype = i
             lib.pdo_resize.argtypes = [P, i, i, i, P, i, i, i]
             lib.pdo_lbp_code.argtypes = [P, i, i, i, i, i]
             lib.pdo_lbp_code.restype = i
@@ -83,6 +85,8 @@ def _load():
             lib.pdo_nms.restype = i
             lib.pdo_detect.argtypes = [P, i, i, i, d, P, d, d, f, d, i, i, P, P, P, P, P, P]
             lib.pdo_detect.restype = i
+            lib.pdo_detect_up.argtypes = [P, i, i, i, d, i, P, d, d, f, d, i, i, P, P, P, P, P, P]
+            lib.pdo_detect_up.restype = i
             _lib = lib
     return _lib
 
@@ -98,12 +102,13 @@ def _img(img: np.ndarray) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------- pyramid
-def pyramid(W: int, H: int, factor: float, max_levels: int = 1024):
-    """Level sizes [(Wk, Hk), ...] (Section 4.4; read of the stop rule)."""
+def pyramid(W: int, H: int, factor: float, max_levels: int = 1024, upscale: int = 0):
+    """Level sizes [(Wk, Hk), ...] (Section 4.4; read of the stop rule), the
+    `upscale` upsampled levels (most upsampled first) before the others."""
     lib = _load()
     wk = np.zeros(max_levels, np.int32)
     hk = np.zeros(max_levels, np.int32)
-    n = lib.pdo_pyramid(W, H, float(factor), max_levels, _p(wk), _p(hk))
+    n = lib.pdo_pyramid_up(W, H, float(factor), int(upscale), max_levels, _p(wk), _p(hk))
     if n < 0:
         raise ValueError("pyramid factor must be > 1")
     return [(int(wk[k]), int(hk[k])) for k in range(n)]
@@ -299,12 +304,12 @@ def boxes_to_array(arr, k: int) -> np.ndarray:
 
 
 def detect(img: np.ndarray, w: np.ndarray, bias: float, factor: float, threshold: float = 0.0,
-           iou_thr: float = 0.5, max_boxes: int = 4096, clip: float = CLIP):
+           iou_thr: float = 0.5, max_boxes: int = 4096, clip: float = CLIP, upscale: int = 0):
     """Whole plain path for one frame. Returns dict(levels, scores (list of f64 maps), boxes, n_candidates)."""
     lib = _load()
     img = _img(img)
     H, W = img.shape
-    dims = pyramid(W, H, factor)
+    dims = pyramid(W, H, factor, upscale=upscale)
     total = sum(max(hk // 8 - WIN_BH, 0) * max(wk // 8 - WIN_BW, 0) for wk, hk in dims)
     sc = np.zeros(max(total, 1), np.float64)
     wk = np.zeros(1024, np.int32)
@@ -313,9 +318,9 @@ def detect(img: np.ndarray, w: np.ndarray, bias: float, factor: float, threshold
     ncand = ctypes.c_int(0)
     out = (Box * max(max_boxes, 1))()
     w64 = np.ascontiguousarray(w, np.float64).reshape(-1)
-    k = lib.pdo_detect(_p(img), W, H, W, float(factor), _p(w64), float(bias), float(clip),
-                       float(threshold), float(iou_thr), max_boxes, 1024, ctypes.byref(nl), _p(wk),
-                       _p(hk), _p(sc), out, ctypes.byref(ncand))
+    k = lib.pdo_detect_up(_p(img), W, H, W, float(factor), int(upscale), _p(w64), float(bias), float(clip),
+                          float(threshold), float(iou_thr), max_boxes, 1024, ctypes.byref(nl), _p(wk),
+                          _p(hk), _p(sc), out, ctypes.byref(ncand))
     if k < 0:
         raise MemoryError("oracle detect")
     maps = []

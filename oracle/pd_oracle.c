@@ -50,10 +50,31 @@ static long long floor_div(long long a, long long b) /* b > 0 */
  * Wk = floor(W/s_k + 1e-9), Hk = floor(H/s_k + 1e-9), and levels are kept
  * while a 64x128 window still fits. Returns the number of levels.
  * ------------------------------------------------------------------------- */
+int pdo_pyramid_up(int W, int H, double factor, int upscale, int max_levels, int *Wk, int *Hk);
+
 int pdo_pyramid(int W, int H, double factor, int max_levels, int *Wk, int *Hk)
 {
+    return pdo_pyramid_up(W, H, factor, 0, max_levels, Wk, Hk);
+}
+
+/* With `upscale` > 0 the pyramid also holds the upsampled levels k = -upscale
+ * .. -1 (scale factor^k < 1, the same size rule), first, most upsampled
+ * first; they reach pedestrians shorter than the 128-pixel window (the
+ * 1242x375 workload's "about 40 levels" at factor 1.05 are 23 levels of the
+ * stop rule plus 17 upsampled ones). Every level must still hold a window. */
+int pdo_pyramid_up(int W, int H, double factor, int upscale, int max_levels, int *Wk, int *Hk)
+{
     int n = 0;
-    if (!(factor > 1.0)) return -1;
+    if (!(factor > 1.0) || upscale < 0) return -1;
+    for (int k = -upscale; k < 0 && n < max_levels; ++k) {
+        double s = pow(factor, (double)k);
+        int wk = (int)floor((double)W / s + 1e-9);
+        int hk = (int)floor((double)H / s + 1e-9);
+        if (wk < 64 || hk < 128) continue;
+        Wk[n] = wk;
+        Hk[n] = hk;
+        ++n;
+    }
     for (int k = 0; n < max_levels; ++k) {
         double s = pow(factor, (double)k);
         int wk = (int)floor((double)W / s + 1e-9);
@@ -493,12 +514,26 @@ int pdo_nms(const float *scores, int n_levels, const int *rows, const int *cols,
  * to back into `scores` (double) and, rounded, used for NMS. Returns the
  * number of boxes, or -1 on allocation failure.
  * ------------------------------------------------------------------------- */
+int pdo_detect_up(const uint8_t *img, int W, int H, int pitch, double factor, int upscale, const double *w,
+                  double bias, double clip, float threshold, double iou_thr, int max_boxes,
+                  int max_levels, int *n_levels_out, int *Wk, int *Hk, double *scores,
+                  pdo_box *boxes, int *n_candidates);
+
 int pdo_detect(const uint8_t *img, int W, int H, int pitch, double factor, const double *w,
                double bias, double clip, float threshold, double iou_thr, int max_boxes,
                int max_levels, int *n_levels_out, int *Wk, int *Hk, double *scores,
                pdo_box *boxes, int *n_candidates)
 {
-    int nl = pdo_pyramid(W, H, factor, max_levels, Wk, Hk);
+    return pdo_detect_up(img, W, H, pitch, factor, 0, w, bias, clip, threshold, iou_thr, max_boxes, max_levels,
+                         n_levels_out, Wk, Hk, scores, boxes, n_candidates);
+}
+
+int pdo_detect_up(const uint8_t *img, int W, int H, int pitch, double factor, int upscale, const double *w,
+                  double bias, double clip, float threshold, double iou_thr, int max_boxes,
+                  int max_levels, int *n_levels_out, int *Wk, int *Hk, double *scores,
+                  pdo_box *boxes, int *n_candidates)
+{
+    int nl = pdo_pyramid_up(W, H, factor, upscale, max_levels, Wk, Hk);
     *n_levels_out = nl < 0 ? 0 : nl;
     if (nl <= 0) {
         *n_candidates = 0;

@@ -467,3 +467,55 @@ def test_block_cell_order_tl_tr_bl_br():
         v = f[by, bx, :36]
         assert np.count_nonzero(v) == 1 and v[q * 9 + 4] > 0.99, (by, bx, q)
     assert np.count_nonzero(f[:, :, :36]) == 4
+
+
+# ----------------------------------------------------------------------------- upsampled levels
+def test_upscaled_pyramid_adds_levels_before_the_frame():
+    # 1242x375 at factor 1.05: 23 levels by the stop rule, plus 17 upsampled = 40
+    f = float(np.float32(1.05))
+    plain = oracle.pyramid(1242, 375, f)
+    up = oracle.pyramid(1242, 375, f, upscale=17)
+    assert len(plain) == 23 and len(up) == 40
+    assert up[17:] == plain
+    # hand arithmetic: 1242 x 1.05 = 1304.1, 375 x 1.05 = 393.75; x 1.1025: 1369.3, 413.4
+    assert up[16] == (1304, 393) and up[15] == (1369, 413)
+    widths = [wk for wk, _ in up]
+    assert all(a > b for a, b in zip(widths, widths[1:]))
+
+
+def test_resize_2x_upsampling_closed_form():
+    # Wk = 2W: destination 2u reads source u-1, u with weights 1/4, 3/4 (u >= 1;
+    # column 0 clamps to source 0), destination 2u+1 reads u, u+1 with 3/4, 1/4
+    # (the last clamps to W-1); Q11 is exact for quarter weights, so the
+    # level is (sum of the 4 weighted taps in 16ths + 8) // 16.
+    rng = np.random.default_rng(11)
+    img = rng.integers(0, 256, size=(8, 8)).astype(np.uint8)
+    got = oracle.resize(img, 16, 16)
+
+    def taps(n):
+        t = []
+        for x in range(2 * n):
+            u = x // 2
+            if x % 2 == 0:
+                t.append([(0, 4)] if u == 0 else [(u - 1, 1), (u, 3)])
+            else:
+                t.append([(n - 1, 4)] if u == n - 1 else [(u, 3), (u + 1, 1)])
+        return t
+    tx, ty = taps(8), taps(8)
+    ref = np.zeros((16, 16), np.int64)
+    for y in range(16):
+        for x in range(16):
+            s = sum(wy * wx * int(img[sy, sx]) for sy, wy in ty[y] for sx, wx in tx[x])
+            ref[y, x] = (s + 8) // 16
+    assert np.array_equal(got.astype(np.int64), ref)
+
+
+def test_detect_with_upscaled_levels_scores_each_level():
+    w, b = synth.random_svm(3)
+    f = float(np.float32(1.2))
+    img = synth.make_scene(160, 200, 1, 5)
+    ref = oracle.detect(img, w, b, f, upscale=2)
+    assert ref["levels"] == oracle.pyramid(160, 200, f, upscale=2)
+    assert ref["levels"][0][0] > 160 and len(ref["levels"]) == len(oracle.pyramid(160, 200, f)) + 2
+    for (wk, hk), m in zip(ref["levels"], ref["scores"]):
+        assert np.allclose(m, oracle.level_scores(oracle.resize(img, wk, hk), w, b), rtol=0, atol=1e-9)
