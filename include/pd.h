@@ -76,6 +76,8 @@ typedef struct pd_params {
     int32_t flags;           /* PD_FLAG_* bits, 0 by default */
     int32_t use_proposal;    /* 1: sparse path gated by the learned proposal (needs pd_cnn_set_params) */
     float keep_logit_threshold; /* a window is kept iff its keep-logit > this */
+    int32_t upscale_levels;  /* 0..64 upsampled levels (scale pyr_factor^-j, j = upscale..1) placed
+                                before the frame's level 0; 0 by default (the stop rule alone) */
 } pd_params;
 
 /* One detection: a window in frame coordinates. */
@@ -104,6 +106,13 @@ int pd_params_default(pd_params *p);
  * while a 64x128 window fits). Host only. Wk/Hk: host arrays of max_levels
  * entries. Returns the number of levels (>= 0) or PD_EINVAL. */
 int pd_pyramid(int W, int H, float factor, int max_levels, int32_t *Wk, int32_t *Hk);
+
+/* Same with `upscale_levels` upsampled levels first (most upsampled first):
+ * level j of those is floor(W f^(upscale-j) + 1e-9) x floor(H f^(upscale-j)
+ * + 1e-9), each kept if a 64x128 window fits (Section 4.4 pyramid; the
+ * upsampled levels reach pedestrians shorter than the window). Returns the
+ * number of levels or PD_EINVAL. */
+int pd_pyramid_ex(int W, int H, float factor, int upscale_levels, int max_levels, int32_t *Wk, int32_t *Hk);
 
 /* Creates a detector. svm_w: host float[15][7][95] template in window order
  * (block row i, block column j, feature t: 36 HOG values = 4 cells x 9 bins
@@ -206,8 +215,9 @@ int pd_detect_host(pd_handle *h, void *stream, int n_frames, const uint8_t *cons
 
 /* K1, Section 4.4 pyramid: writes levels 0..n_levels-1 of one W x H frame
  * (fixed-point bilinear, 11-bit weights, each level resampled straight from
- * the frame; the frame is read once). Level k is Wk[k] x Hk[k] (host arrays)
- * at d_levels + level_offsets[k] (host array, bytes) with pitch
+ * the frame; the frame is read once). Level k is Wk[k] x Hk[k] (host arrays;
+ * 1 .. 4W x 1 .. 4H, so upsampled levels too) at d_levels + level_offsets[k]
+ * (host array, bytes) with pitch
  * level_pitches[k] (host array, >= Wk[k]). n_levels <= PD_MAX_LEVELS.
  * Errors: PD_EINVAL, PD_ECUDA. */
 int pd_resize_levels(pd_handle *h, void *stream, const uint8_t *d_frame, int W, int H, int pitch, int n_levels,

@@ -36,7 +36,7 @@ EXPORTED = ["pd_params_default", "pd_pyramid", "pd_create", "pd_destroy", "pd_la
             "pd_detect", "pd_detect_host", "pd_sync", "pd_frame_candidates", "pd_frame_levels", "pd_scores", "pd_boxes",
             "pd_last_launch_count", "pd_stage_times", "pd_set_tile_costs", "pd_get_tile_costs", "pd_resize_levels", "pd_cell_features", "pd_window_scores",
             "pd_nms_maps", "pd_nms_noalloc", "pd_cnn_set_params", "pd_cnn_get_params", "pd_cnn_forward",
-            "pd_cnn_train_step", "pd_cnn_train_loss", "pd_set_proposal", "pd_logits"]
+            "pd_cnn_train_step", "pd_cnn_train_loss", "pd_set_proposal", "pd_logits", "pd_pyramid_ex"]
 
 
 class pd_params(ctypes.Structure):
@@ -46,7 +46,7 @@ class pd_params(ctypes.Structure):
                 ("max_candidates_per_frame", ctypes.c_int32), ("max_frames", ctypes.c_int32),
                 ("max_width", ctypes.c_int32), ("max_height", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("use_proposal", ctypes.c_int32),
-                ("keep_logit_threshold", ctypes.c_float)]
+                ("keep_logit_threshold", ctypes.c_float), ("upscale_levels", ctypes.c_int32)]
 
 
 class pd_box(ctypes.Structure):
@@ -91,6 +91,7 @@ def load(path: str | None = None):
     sig = {
         "pd_params_default": ([P], i),
         "pd_pyramid": ([i, i, f, i, P, P], i),
+        "pd_pyramid_ex": ([i, i, f, i, i, P, P], i),
         "pd_create": ([P, P, f, P], i),
         "pd_destroy": ([P], None),
         "pd_last_error": ([P], ctypes.c_char_p),
@@ -158,11 +159,11 @@ def pd_params_default(**overrides) -> pd_params:
     return p
 
 
-def pd_pyramid(W: int, H: int, factor: float, max_levels: int = MAX_LEVELS):
+def pd_pyramid(W: int, H: int, factor: float, max_levels: int = MAX_LEVELS, upscale_levels: int = 0):
     wk = np.zeros(max_levels, np.int32)
     hk = np.zeros(max_levels, np.int32)
-    n = load().pd_pyramid(W, H, float(factor), max_levels, wk.ctypes.data_as(ctypes.c_void_p),
-                          hk.ctypes.data_as(ctypes.c_void_p))
+    n = load().pd_pyramid_ex(W, H, float(factor), int(upscale_levels), max_levels,
+                             wk.ctypes.data_as(ctypes.c_void_p), hk.ctypes.data_as(ctypes.c_void_p))
     if n < 0:
         raise PDError(n, "pd_pyramid")
     return [(int(wk[k]), int(hk[k])) for k in range(n)]

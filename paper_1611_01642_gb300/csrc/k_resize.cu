@@ -1,7 +1,8 @@
 // K1 -- image pyramid (Section 4.4, pyramidal sliding window; Section 4.1 step 2).
 //
 // Every pyramid level is a fixed-point bilinear resample (11-bit weights) of
-// the frame itself, not of the previous level. One CTA owns a 128x32 source
+// the frame itself, not of the previous level (downsampled levels, and the
+// optional upsampled ones placed before them). One CTA owns a 128x32 source
 // tile of one frame: it stages the tile (+1 pixel of right/bottom halo) in
 // shared memory once and then writes, for every level of that frame, the
 // output pixels whose top-left source sample falls inside the tile. The
@@ -63,29 +64,30 @@ __global__ void __launch_bounds__(kThreads) k_resize(const FrameDesc *__restrict
     const int tx = tid & 63, ty = tid >> 6;
     for (int k = 0; k < fd.n_levels; ++k) {
         const int4 r = ranges[k];
-        const int x = r.x + 2 * tx;
-        if (x >= r.y) continue;
-        const bool two = x + 1 < r.y;
-        const LevelDesc L = levels[fd.first_level + k];
-        const int32_t ex0 = __ldg(tabs + L.xtab_off + x);
-        const int32_t ex1 = two ? __ldg(tabs + L.xtab_off + x + 1) : ex0;
-        const int a0 = (ex0 >> 11) - it.x0, ax0 = ex0 & 2047;
-        const int b0 = min((ex0 >> 11) + 1, fd.W - 1) - it.x0;
-        const int a1 = (ex1 >> 11) - it.x0, ax1 = ex1 & 2047;
-        const int b1 = min((ex1 >> 11) + 1, fd.W - 1) - it.x0;
-        uint8_t *out = pyr + L.img_off + x;
-        for (int y = r.z + ty; y < r.w; y += 4) {
-            const int32_t ey = __ldg(tabs + L.ytab_off + y);
-            const int sy0 = (ey >> 11) - it.y0, ay = ey & 2047;
-            const int sy1 = min((ey >> 11) + 1, fd.H - 1) - it.y0;
-            const uint8_t *t0 = tile[sy0], *t1 = tile[sy1];
-            const int top0 = (2048 - ax0) * t0[a0] + ax0 * t0[b0];
-            const int bot0 = (2048 - ax0) * t1[a0] + ax0 * t1[b0];
-            const int top1 = (2048 - ax1) * t0[a1] + ax1 * t0[b1];
-            const int bot1 = (2048 - ax1) * t1[a1] + ax1 * t1[b1];
-            uint8_t *o = out + (size_t)y * L.img_pitch;
-            o[0] = (uint8_t)(((2048 - ay) * top0 + ay * bot0 + (1 << 21)) >> 22);
-            if (two) o[1] = (uint8_t)(((2048 - ay) * top1 + ay * bot1 + (1 << 21)) >> 22);
+        // (an upsampled level has more than 128 output columns per tile: passes of 128)
+        for (int x = r.x + 2 * tx; x < r.y; x += 128) {
+            const bool two = x + 1 < r.y;
+            const LevelDesc L = levels[fd.first_level + k];
+            const int32_t ex0 = __ldg(tabs + L.xtab_off + x);
+            const int32_t ex1 = two ? __ldg(tabs + L.xtab_off + x + 1) : ex0;
+            const int a0 = (ex0 >> 11) - it.x0, ax0 = ex0 & 2047;
+            const int b0 = min((ex0 >> 11) + 1, fd.W - 1) - it.x0;
+            const int a1 = (ex1 >> 11) - it.x0, ax1 = ex1 & 2047;
+            const int b1 = min((ex1 >> 11) + 1, fd.W - 1) - it.x0;
+            uint8_t *out = pyr + L.img_off + x;
+            for (int y = r.z + ty; y < r.w; y += 4) {
+                const int32_t ey = __ldg(tabs + L.ytab_off + y);
+                const int sy0 = (ey >> 11) - it.y0, ay = ey & 2047;
+                const int sy1 = min((ey >> 11) + 1, fd.H - 1) - it.y0;
+                const uint8_t *t0 = tile[sy0], *t1 = tile[sy1];
+                const int top0 = (2048 - ax0) * t0[a0] + ax0 * t0[b0];
+                const int bot0 = (2048 - ax0) * t1[a0] + ax0 * t1[b0];
+                const int top1 = (2048 - ax1) * t0[a1] + ax1 * t0[b1];
+                const int bot1 = (2048 - ax1) * t1[a1] + ax1 * t1[b1];
+                uint8_t *o = out + (size_t)y * L.img_pitch;
+                o[0] = (uint8_t)(((2048 - ay) * top0 + ay * bot0 + (1 << 21)) >> 22);
+                if (two) o[1] = (uint8_t)(((2048 - ay) * top1 + ay * bot1 + (1 << 21)) >> 22);
+            }
         }
     }
 }

@@ -123,9 +123,21 @@ int32_t q11_entry(int x, int n, int m) {
     return (idx << 11) | a;
 }
 
-int level_sizes(int W, int H, double factor, int max_levels, int32_t *Wk, int32_t *Hk) {
-    if (!(factor > 1.0) || W < 0 || H < 0) return PD_EINVAL;
+// Pyramid level sizes: the `upscale` upsampled levels k = -upscale .. -1
+// first (most upsampled first), then k = 0, 1, ... while a 64x128 window
+// fits; level k is floor(W / factor^k + 1e-9) x floor(H / factor^k + 1e-9).
+int level_sizes(int W, int H, double factor, int upscale, int max_levels, int32_t *Wk, int32_t *Hk) {
+    if (!(factor > 1.0) || W < 0 || H < 0 || upscale < 0) return PD_EINVAL;
     int n = 0;
+    for (int k = -upscale; k < 0 && n < max_levels; ++k) {
+        const double s = std::pow(factor, (double)k);
+        const int wk = (int)std::floor((double)W / s + 1e-9);
+        const int hk = (int)std::floor((double)H / s + 1e-9);
+        if (wk < 64 || hk < 128) continue;
+        Wk[n] = wk;
+        Hk[n] = hk;
+        ++n;
+    }
     for (int k = 0; n < max_levels; ++k) {
         const double s = std::pow(factor, (double)k);
         const int wk = (int)std::floor((double)W / s + 1e-9);
@@ -415,7 +427,7 @@ void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int
 int plan_frame(Plan &p, const pd_params &prm, const uint8_t *ptr, int W, int H, int pitch,
                const float *tile_cost = kDefaultTileCost, bool proposal = false) {
     int32_t Wk[PD_MAX_LEVELS], Hk[PD_MAX_LEVELS];
-    int n = level_sizes(W, H, prm.pyr_factor, PD_MAX_LEVELS, Wk, Hk);
+    int n = level_sizes(W, H, prm.pyr_factor, prm.upscale_levels, PD_MAX_LEVELS, Wk, Hk);
     if (n < 0) return n;
     FrameDesc fd{};
     fd.ptr = ptr;
@@ -451,7 +463,7 @@ int plan_frame(Plan &p, const pd_params &prm, const uint8_t *ptr, int W, int H, 
 
 bool params_ok(const pd_params *p) {
     return p && p->struct_size == sizeof(pd_params) && p->pyr_factor > 1.0f && p->l2hys_clip > 0.f &&
-           !std::isnan(p->keep_logit_threshold) &&
+           !std::isnan(p->keep_logit_threshold) && p->upscale_levels >= 0 && p->upscale_levels <= 64 &&
            p->nms_iou >= 0.f && p->max_boxes_per_frame > 0 && p->max_boxes_per_frame <= 16384 &&
            p->max_candidates_per_frame > 0 &&
            p->max_candidates_per_frame <= 16384 && p->max_frames > 0 && p->max_width > 0 &&
@@ -611,7 +623,12 @@ int pd_params_default(pd_params *p) {
 
 int pd_pyramid(int W, int H, float factor, int max_levels, int32_t *Wk, int32_t *Hk) {
     if (!Wk || !Hk || max_levels < 0) return PD_EINVAL;
-    return level_sizes(W, H, factor, max_levels, Wk, Hk);
+    return level_sizes(W, H, factor, 0, max_levels, Wk, Hk);
+}
+
+int pd_pyramid_ex(int W, int H, float factor, int upscale_levels, int max_levels, int32_t *Wk, int32_t *Hk) {
+    if (!Wk || !Hk || max_levels < 0) return PD_EINVAL;
+    return level_sizes(W, H, factor, upscale_levels, max_levels, Wk, Hk);
 }
 
 const char *pd_last_error(const pd_handle *h) { return h ? h->err.c_str() : "null handle"; }
@@ -1252,7 +1269,7 @@ int pd_resize_levels(pd_handle *h, void *stream, const uint8_t *d_frame, int W, 
     fd.first_level = 0;
     fd.n_levels = n_levels;
     for (int k = 0; k < n_levels; ++k) {
-        if (Wk[k] < 1 || Hk[k] < 1 || Wk[k] > W || Hk[k] > H || level_pitches[k] < Wk[k])
+        if (Wk[k] < 1 || Hk[k] < 1 || Wk[k] > 4 * W || Hk[k] > 4 * H || level_pitches[k] < Wk[k])
             return fail(h, PD_EINVAL, "pd_resize_levels: level %d size %dx%d", k, Wk[k], Hk[k]);
         plan_level(p, 0, k, W, H, Wk[k], Hk[k], level_offsets[k], level_pitches[k]);
     }

@@ -35,7 +35,7 @@ def test_header_declarations_are_all_exported(lib):
 
 def test_params_default(lib):
     p = pd.pd_params_default()
-    assert p.struct_size == 52
+    assert p.struct_size == 56
     assert abs(p.pyr_factor - 1.05) < 1e-6 and abs(p.l2hys_clip - 0.2) < 1e-7
     assert p.threshold == 0.0 and p.nms_iou == 0.5 and p.max_candidates_per_frame == 16384
 
@@ -46,6 +46,8 @@ def test_pyramid_matches_oracle_rule(lib):
                       (640, 480, 1.05), (64, 128, 1.1), (63, 500, 1.1)]:
         f32 = float(np.float32(f))
         assert pd.pd_pyramid(W, H, f32) == oracle.pyramid(W, H, f32)
+        for up in [1, 17]:
+            assert pd.pd_pyramid(W, H, f32, upscale_levels=up) == oracle.pyramid(W, H, f32, upscale=up)
 
 
 def test_pyramid_rejects_bad_factor(lib):

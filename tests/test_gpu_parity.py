@@ -83,7 +83,9 @@ def test_resize_arbitrary_ratios_and_pitched_frame(det):
     pitched = np.zeros((200, 333), np.uint8)
     pitched[:, :300] = img
     frame = torch.from_numpy(pitched).cuda()[:, :300]
-    levels = [(300, 200), (150, 100), (299, 199), (17, 3), (1, 1), (100, 200), (300, 7)]
+    # downsampled, odd, degenerate and upsampled (up to 3x) levels
+    levels = [(300, 200), (150, 100), (299, 199), (17, 3), (1, 1), (100, 200), (300, 7),
+              (600, 400), (331, 213), (900, 250), (301, 600)]
     pitches = [wk + 5 for wk, _ in levels]
     offs = list(np.cumsum([0] + [p * hk for (wk, hk), p in zip(levels, pitches)])[:-1])
     out = torch.zeros(int(sum(p * hk for (wk, hk), p in zip(levels, pitches))), dtype=torch.uint8,
@@ -285,6 +287,32 @@ def test_detect_scores_match_oracle(template, cfg, W, H, factor):
         levels = [(lv["width"], lv["height"]) for lv in d.levels(0)]
         _check_boxes(d.boxes(0), [sc for _, sc in ref], [feat for feat, _ in ref], levels, w, b, W, H)
         assert pd.pd_last_launch_count(d.h) == 4
+    finally:
+        d.close()
+
+
+def test_detect_with_upscaled_levels_matches_oracle(template):
+    # the pyramid's upsampled levels (before the frame's own level 0) through the whole path
+    from paper_1611_01642_gb300 import build as bld
+    bld.build()
+    w, b = template
+    W, H, up = 320, 240, 3
+    img = synth.make_scene(W, H, 1, 3)
+    d = pd.Detector(w, b, max_frames=1, max_width=W, max_height=H, pyr_factor=F12, upscale_levels=up)
+    try:
+        d.detect([torch.from_numpy(img).cuda()])
+        assert d.sync() == pd.PD_OK
+        dims = oracle.pyramid(W, H, F12, upscale=up)
+        assert [(lv["width"], lv["height"]) for lv in d.levels(0)] == dims
+        assert dims[0][0] > W
+        ref = oracle.detect(img, w, b, F12, upscale=up)
+        feats = []
+        for k, ((wk, hk), g) in enumerate(zip(dims, d.score_maps(0))):
+            L = oracle.resize(img, wk, hk)
+            hog, lbp, feat, sc = oracle.level_all(L, w, b)
+            feats.append(feat)
+            _check_scores(g.cpu().numpy(), feat, w, b, sc, f"level {k}")
+        _check_boxes(d.boxes(0), ref["scores"], feats, dims, w, b, W, H)
     finally:
         d.close()
 
