@@ -52,12 +52,16 @@ def parse_args(argv=None):
                     help="frames the CPU oracle times for cpu_baseline (bounded sample)")
     ap.add_argument("--proposal-steps", type=int, default=10,
                     help="timed steps of the 16x1920x1080 plain-vs-sparse comparison (0: skip)")
+    ap.add_argument("--svm", default="tc", choices=["tc", "fp32"],
+                    help="window-score kernel: tensor cores (default) or the FP32 CUDA-core kernel")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="keep the library's default K4 tile costs (profiler captures of a fixed plan)")
+                    help="keep the library's default tile costs of the FP32 kernel (profiler captures)")
     ap.add_argument("--proposal-4k", type=int, default=1,
                     help="also compare plain and sparse on the 4K mix (16 x 3840x2160 + 48 x 1242x375)")
     ap.add_argument("--proposal-frames", type=int, default=16,
                     help="frames of the proposal comparison (16 is the workload; fewer for profiler captures)")
+    ap.add_argument("--upscale-steps", type=int, default=10,
+                    help="timed steps of the same batch with 17 upsampled levels (40 levels per frame; 0: skip)")
     return ap.parse_args(argv)
 
 
@@ -100,9 +104,58 @@ def make_frames(indices):
     return [synth.make_scene(WIDTH, HEIGHT, CFG_ID, i) for i in indices]
 
 
-def windows_per_frame() -> int:
+def svm_flag(args, pd) -> int:
+    return pd.PD_FLAG_SVM_FP32 if args.svm == "fp32" else 0
+
+
+def windows_per_frame(upscale: int = 0) -> int:
     from paper_1611_01642_gb300 import pd_pyramid
-    return sum(max(hk // 8 - 15, 0) * max(wk // 8 - 7, 0) for wk, hk in pd_pyramid(WIDTH, HEIGHT, FACTOR))
+    return sum(max(hk // 8 - 15, 0) * max(wk // 8 - 7, 0)
+               for wk, hk in pd_pyramid(WIDTH, HEIGHT, FACTOR, upscale_levels=upscale))
+
+
+UPSCALE_LEVELS = 17     # 1242x375 at f = 1.05: 17 upsampled + 23 downsampled = 40 levels
+# (with the upsampled levels a frame of this scene recipe has up to ~20,000 windows
+# scoring above 0: the NMS takes up to 65,536 candidates per frame)
+
+
+def run_upscaled(args, pd, torch, frames, flush, tile_costs, fp32_peak):
+    """The same batch with the 17 upsampled levels in front of the 23 (40 levels per frame), under
+    the main line's timing rules. A secondary figure: the headline line is the 23-level pyramid."""
+    w, b = load_template()
+    det = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=len(frames), max_width=WIDTH, max_height=HEIGHT,
+                      upscale_levels=UPSCALE_LEVELS, max_candidates_per_frame=65536,
+                      flags=pd.PD_FLAG_STAGE_TIMING | svm_flag(args, pd))
+    pd.pd_set_tile_costs(det.h, tile_costs)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        flush.fill_(1)
+        det.detect(frames)
+        det.sync()
+    tot, st = 0.0, np.zeros(5)
+    for i in range(args.upscale_steps):
+        flush.fill_(i & 255)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        det.detect(frames)
+        e1.record(stream)
+        if det.sync() != pd.PD_OK:
+            raise RuntimeError(pd.pd_last_error(det.h))
+        tot += e0.elapsed_time(e1)
+        st += np.array(pd.pd_stage_times(det.h))
+    n_levels = len(det.levels(0))
+    det.close()
+    ms, st = tot / args.upscale_steps, st / args.upscale_steps
+    wpf = windows_per_frame(UPSCALE_LEVELS)
+    k4 = len(frames) * wpf * FLOP_PER_WINDOW / (st[2] / 1e3) / 1e12
+    return {"workload": f"{len(frames)} x {WIDTH}x{HEIGHT} u8 frames, pyramid factor 1.05 with "
+                        f"{UPSCALE_LEVELS} upsampled levels ({n_levels} levels), plain HOG+LBP+SVM+NMS "
+                        "(NMS candidate cap 65,536 per frame)",
+            "frames_per_s": len(frames) / (ms / 1e3), "ms_per_step": ms, "levels_per_frame": n_levels,
+            "windows_per_frame": wpf, "k4_tflops": k4, "k4_frac_of_fp32_peak": k4 / fp32_peak,
+            "stage_ms_per_step": dict(zip(["pyramid", "cells", "norm_svm", "nms"], map(float, st[:4]))),
+            "steps": args.upscale_steps}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -245,7 +298,7 @@ def run_proposal(args, pd, torch, flush, recipe: int = 4):
     frames = [torch.from_numpy(im).cuda() for im in imgs]
     w, b = load_template()
     det = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=len(frames), max_width=max(im.shape[1] for im in imgs),
-                      max_height=max(im.shape[0] for im in imgs), flags=pd.PD_FLAG_STAGE_TIMING)
+                      max_height=max(im.shape[0] for im in imgs), flags=pd.PD_FLAG_STAGE_TIMING | svm_flag(args, pd))
     pd.pd_cnn_set_params(det.h, params)
     stream = torch.cuda.current_stream()
 
@@ -315,12 +368,12 @@ def run_gpu(args):
     w, b = load_template()
     imgs = make_frames(rank_frame_indices(rank, B))
     det = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=B, max_width=WIDTH, max_height=HEIGHT,
-                      flags=pd.PD_FLAG_STAGE_TIMING)
+                      flags=pd.PD_FLAG_STAGE_TIMING | svm_flag(args, pd))
     stream = torch.cuda.current_stream()
     frames = [torch.from_numpy(im).cuda() for im in imgs]
     pinned = [torch.from_numpy(im).pin_memory() for im in imgs]
     from paper_1611_01642_gb300 import autotune
-    tile_costs = (pd.pd_get_tile_costs(det.h) if args.no_autotune
+    tile_costs = (pd.pd_get_tile_costs(det.h) if args.no_autotune or args.svm != "fp32"
                   else autotune.apply(det, frames[:16], w, b, FACTOR))
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     wpf = windows_per_frame()
@@ -367,7 +420,8 @@ def run_gpu(args):
     # handles alternate so that step i's results are read on the host while
     # step i+1 already runs (each step still copies its frames in and its
     # boxes out inside the timed region).
-    det2 = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=B, max_width=WIDTH, max_height=HEIGHT)
+    det2 = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=B, max_width=WIDTH, max_height=HEIGHT,
+                       flags=svm_flag(args, pd))
     pd.pd_set_tile_costs(det2.h, tile_costs)
     for _ in range(2):
         det2.detect_host(pinned)
@@ -410,6 +464,10 @@ def run_gpu(args):
                 "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                               f"(max SM clock, {peak_kind})"}
 
+    upscaled = None
+    if rank == 0 and args.upscale_steps > 0:
+        upscaled = run_upscaled(args, pd, torch, frames, flush, tile_costs, fp32_peak)
+
     proposal = proposal_4k = None
     if rank == 0 and args.proposal_steps > 0 and os.path.exists(PROPOSAL_CKPT):
         proposal = run_proposal(args, pd, torch, flush)
@@ -440,6 +498,7 @@ def run_gpu(args):
         "clocks": clocks,
         "stage_ms_per_step": {"pyramid": stage_step[0], "cells": stage_step[1], "norm_svm": stage_step[2],
                               "nms": stage_step[3]},
+        "upscaled_40_levels": upscaled,
         "proposal": proposal,
         "proposal_4k_mix": proposal_4k,
         "px_per_ns": B * WIDTH * HEIGHT / (ms_step * 1e6),

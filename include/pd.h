@@ -57,6 +57,12 @@ extern "C" {
 
 /* pd_params.flags */
 #define PD_FLAG_STAGE_TIMING 1 /* record CUDA events around each kernel of pd_detect */
+/* K4 on the FP32 CUDA cores (tiled direct correlation) instead of the default
+ * tensor-core kernel (one bf16-split GEMM per block row, fp32 accumulation).
+ * Both stay within the score tolerance of the float64 definition; scores of
+ * one kernel do not depend on how it tiles a level, and the sparse path
+ * reproduces the dense path's scores of the same kernel bit for bit. */
+#define PD_FLAG_SVM_FP32 2
 
 typedef struct pd_handle pd_handle;
 
@@ -69,7 +75,8 @@ typedef struct pd_params {
     float threshold;         /* a window is a detection iff score > threshold (0) */
     float nms_iou;           /* NMS suppresses when IoU > nms_iou (0.5) */
     int32_t max_boxes_per_frame;      /* NMS output cap per frame (4096), <= 16384 */
-    int32_t max_candidates_per_frame; /* windows above threshold per frame, <= 16384 */
+    int32_t max_candidates_per_frame; /* windows above threshold per frame, <= 65536 (default 16384;
+                                       * above 16384 the NMS sorts in global memory, slower) */
     int32_t max_frames;      /* frames per pd_detect call (arena sizing) */
     int32_t max_width;       /* largest frame width  (arena sizing) */
     int32_t max_height;      /* largest frame height (arena sizing) */
@@ -173,7 +180,7 @@ int pd_boxes(const pd_handle *h, int frame, pd_box *out, int cap, int *count);
 /* Number of this library's kernel launches issued by the last pd_detect. */
 int pd_last_launch_count(const pd_handle *h);
 
-/* K4 tile shapes (windows per CTA tile, x by y): 0 = 32x16, 1 = 64x8,
+/* Tile shapes of the FP32 K4 (PD_FLAG_SVM_FP32; windows per CTA tile, x by y): 0 = 32x16, 1 = 64x8,
  * 2 = 32x8, 3 = 64x4, 4 = 64x2, 5 = 32x12, 6 = 32x4. For each level the
  * planner takes the shape with the least (number of tiles x cost[shape]).
  * The default costs come from an instruction-count model of one tile
@@ -237,7 +244,8 @@ int pd_cell_features(pd_handle *h, void *stream, const uint8_t *d_level, int Wk,
 /* K4, Section 4.4 (Algorithm 6) with block normalisation: the score map of
  * one level from its cell planes (layouts of pd_cell_features; LBP counts
  * must be <= 64, as a cell has 64 pixels), using the handle's template and
- * bias: d_scores float32 [cells_y-15][cells_x-7], row pitch cells_x-7. The
+ * bias and its K4 kernel (tensor cores, or FP32 with PD_FLAG_SVM_FP32):
+ * d_scores float32 [cells_y-15][cells_x-7], row pitch cells_x-7. The
  * cell planes are read through TMA: d_hog and d_lbp must be 16-byte aligned,
  * cell_pitch a multiple of 16, hog_plane a multiple of 4 and lbp_plane a
  * multiple of 16 elements. Errors: PD_EINVAL, PD_ECUDA. */
@@ -300,13 +308,15 @@ int pd_cnn_train_step(pd_handle *h, void *stream, float pos_weight, float label_
 int pd_cnn_train_loss(pd_handle *h, void *stream, float *loss);
 
 /* Sparse path on (enable = 1) or off. When on, pd_detect also runs the
- * proposal network on every level after the pyramid; a window tile of the
- * score kernel is computed iff it holds a window whose keep-logit exceeds
- * keep_logit_threshold (all its windows are then scored exactly), and the
- * cell tiles are computed iff such a tile needs them; the windows of the
- * other tiles get score -inf. With the threshold at -inf every tile is kept
- * and the scores equal the plain path's bit for bit. Needs parameters
- * (pd_cnn_set_params) to enable. Affects the next pd_detect. */
+ * proposal network on every level after the pyramid. A window is kept when
+ * its keep-logit exceeds keep_logit_threshold; the window tiles of the FP32
+ * score kernel's plan that hold a kept window mark the cell tiles under them,
+ * and only marked cell tiles are computed. The tensor-core score kernel then
+ * scores every window whose cell tiles are all marked (a superset of the kept
+ * windows: every window of a kept tile); the FP32 kernel scores the windows
+ * of kept tiles. Scored windows get exactly the plain path's score, the
+ * others -inf. With the threshold at -inf every window is scored. Needs
+ * parameters (pd_cnn_set_params) to enable. Affects the next pd_detect. */
 int pd_set_proposal(pd_handle *h, int enable, float keep_logit_threshold);
 
 /* Device pointer to the window keep-logits of the last pd_detect with the

@@ -1,4 +1,5 @@
-"""Autotuner of the window-score (K4) tile shapes.
+"""Autotuner of the tile shapes of the FP32 window-score kernel (K4 with
+PD_FLAG_SVM_FP32; the tensor-core K4 walks fixed strips and needs no table).
 
 The planner picks, for every pyramid level, the K4 tile shape with the least
 (number of tiles x cost[shape]). This module measures cost[shape] on the
@@ -23,7 +24,7 @@ import os
 
 import numpy as np
 
-from . import (PD_FLAG_STAGE_TIMING, PD_OK, TILE_SHAPE_DIMS, TILE_SHAPES, Detector, library_path,
+from . import (PD_FLAG_STAGE_TIMING, PD_FLAG_SVM_FP32, PD_OK, TILE_SHAPE_DIMS, TILE_SHAPES, Detector, library_path,
                pd_get_tile_costs, pd_set_tile_costs, pd_stage_times)
 
 
@@ -53,7 +54,7 @@ def measure(frames, svm_w, svm_b, factor: float, steps: int = 5, warmup: int = 2
     W = max(f.shape[1] for f in dev)
     H = max(f.shape[0] for f in dev)
     det = Detector(svm_w, svm_b, pyr_factor=factor, max_frames=len(dev), max_width=W, max_height=H,
-                   flags=PD_FLAG_STAGE_TIMING)
+                   flags=PD_FLAG_STAGE_TIMING | PD_FLAG_SVM_FP32)
     out = []
     try:
         for s in range(TILE_SHAPES):
@@ -82,7 +83,7 @@ def plan_ms(frames, svm_w, svm_b, factor: float, cost, steps: int = 7, warmup: i
     import torch
     dev = [f if isinstance(f, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in frames]
     det = Detector(svm_w, svm_b, pyr_factor=factor, max_frames=len(dev), max_width=max(f.shape[1] for f in dev),
-                   max_height=max(f.shape[0] for f in dev), flags=PD_FLAG_STAGE_TIMING)
+                   max_height=max(f.shape[0] for f in dev), flags=PD_FLAG_STAGE_TIMING | PD_FLAG_SVM_FP32)
     try:
         pd_set_tile_costs(det.h, cost)
         ms = []

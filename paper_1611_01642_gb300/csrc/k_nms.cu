@@ -6,6 +6,8 @@
 //     shared-memory key list (64-bit keys: the float score mapped to an
 //     order-reversing integer in the high word, level/wy/wx in the low word,
 //     so ascending keys = score descending, then level, wy, wx ascending);
+//     with a candidate cap above 16,384 the key list lives in the frame's
+//     global scratch instead (same steps, slower sort);
 //  2. bitonic-sorts the keys;
 //  3. decodes every candidate's box once (exactly rounded float division)
 //     into shared memory (over the no longer needed key array, whose keys
@@ -37,7 +39,8 @@ namespace pd {
 namespace {
 
 constexpr int kThreads = 1024;
-constexpr int kMaxCandidates = 16384;  // keys + flags + kept list fit in shared memory
+constexpr int kMaxCandidates = 16384;     // keys + flags + kept list fit in shared memory
+constexpr int kMaxCandidatesBig = 65536;  // keys in global scratch
 constexpr int kMaxBoxes = 16384;
 
 __device__ __forceinline__ unsigned long long make_key(float s, int level, int wy, int wx) {
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
                                                   float iou_thr, int cap, float4 *__restrict__ scratch,
                                                   pd_box *__restrict__ boxes, int max_boxes,
                                                   int32_t *__restrict__ counts) {
-    extern __shared__ unsigned long long keys[];  // [cap_pow2], cap bytes of flags, kept list
+    extern __shared__ unsigned long long skeys[];  // [cap_pow2] keys (small caps), cap bytes of flags, kept list
     __shared__ int n_cand;
     __shared__ int2 wkhk[PD_MAX_LEVELS];  // level sizes of this frame
     const int f = blockIdx.x, tid = threadIdx.x;
@@ -137,7 +140,10 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
     }
     int cap_pow2 = 1;
     while (cap_pow2 < cap) cap_pow2 <<= 1;
-    uint8_t *supp = reinterpret_cast<uint8_t *>(keys + cap_pow2);
+    const bool big = cap > kMaxCandidates;
+    float4 *gbx = scratch + (size_t)f * nms_scratch_float4s(cap);
+    unsigned long long *keys = big ? reinterpret_cast<unsigned long long *>(gbx + cap) : skeys;
+    uint8_t *supp = reinterpret_cast<uint8_t *>(big ? skeys : skeys + cap_pow2);
 
     if (tid == 0) n_cand = 0;
     __syncthreads();
@@ -209,10 +215,9 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
     // keys then move to the global scratch, where only kept ones are read
     // again), otherwise in the global scratch. Each greedy pass reads every
     // remaining box, so keeping them on chip shortens every pass.
-    float4 *gbx = scratch + (size_t)f * cap;
     const float4 *bx;
     const unsigned long long *ksrc;
-    if (2 * n <= cap_pow2) {
+    if (!big && 2 * n <= cap_pow2) {
         unsigned long long *gkeys = reinterpret_cast<unsigned long long *>(gbx);
         for (int i = tid; i < n; i += kThreads) gkeys[i] = keys[i];
         __syncthreads();
@@ -342,7 +347,8 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
 size_t nms_smem(int cap, int max_boxes) {
     int p = 1;
     while (p < cap) p <<= 1;
-    return (size_t)p * sizeof(unsigned long long) + (size_t)((cap + 15) & ~15) + 4 * (size_t)max_boxes;
+    const size_t keys = cap > kMaxCandidates ? 0 : (size_t)p * sizeof(unsigned long long);
+    return keys + (size_t)((cap + 15) & ~15) + 4 * (size_t)max_boxes;
 }
 
 }  // namespace
@@ -357,7 +363,7 @@ cudaError_t launch_nms(cudaStream_t s, const FrameDesc *d_frames, const LevelDes
                        float4 *scratch, int max_cand, pd_box *boxes, int max_boxes,
                        int32_t *counts) {
     if (n_frames <= 0) return cudaSuccess;
-    if (max_cand < 1 || max_cand > kMaxCandidates || max_boxes < 1 || max_boxes > kMaxBoxes)
+    if (max_cand < 1 || max_cand > kMaxCandidatesBig || max_boxes < 1 || max_boxes > kMaxBoxes)
         return cudaErrorInvalidValue;
     k_nms<<<n_frames, kThreads, nms_smem(max_cand, max_boxes), s>>>(d_frames, d_levels, scores, threshold, iou,
                                                          max_cand, scratch, boxes, max_boxes, counts);

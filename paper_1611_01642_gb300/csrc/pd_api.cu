@@ -51,6 +51,7 @@ struct Plan {
     std::vector<ResizeItem> r_items;
     std::vector<CellItem> c_items;
     std::vector<SvmItem> s_items;
+    std::vector<TcItem> t_items;
     std::vector<CnnItem> cnn_items;
     std::vector<int32_t> tabs;
     int64_t pyr_bytes = 0;
@@ -67,6 +68,7 @@ struct Plan {
         r_items.clear();
         c_items.clear();
         s_items.clear();
+        t_items.clear();
         cnn_items.clear();
         tabs.clear();
         pyr_bytes = score_floats = 0;
@@ -76,7 +78,7 @@ struct Plan {
 
 // Byte offsets of the plan's sections inside the packed descriptor block.
 struct Packed {
-    int64_t frames, levels, r_items, c_items, s_items, cnn_items, tabs, tmaps, total;
+    int64_t frames, levels, r_items, c_items, s_items, t_items, cnn_items, tabs, tmaps, total;
 };
 
 Packed pack_layout(const Plan &p) {
@@ -92,6 +94,7 @@ Packed pack_layout(const Plan &p) {
     o.r_items = take((int64_t)p.r_items.size() * sizeof(ResizeItem));
     o.c_items = take((int64_t)p.c_items.size() * sizeof(CellItem));
     o.s_items = take((int64_t)p.s_items.size() * sizeof(SvmItem));
+    o.t_items = take((int64_t)p.t_items.size() * sizeof(TcItem));
     o.cnn_items = take((int64_t)p.cnn_items.size() * sizeof(CnnItem));
     o.tabs = take((int64_t)p.tabs.size() * sizeof(int32_t));
     off = round_up(off, 64);  // tensor maps: 64-byte aligned
@@ -266,6 +269,9 @@ struct pd_handle {
     float *train_loss_ptr = nullptr;
     // tensor maps over the atlases, one pair per K4 tile shape
     CUtensorMap hog_map[kSvmShapes]{}, lbp_map[kSvmShapes]{};
+    CUtensorMap tc_hog_map{}, tc_lbp_map{};  // the same planes for the tensor-core K4
+    int *d_queue = nullptr;                  // its item counter (zeroed before each launch)
+    int sm_count = 1;
     float tile_cost[kSvmShapes] = {kDefaultTileCost[0], kDefaultTileCost[1], kDefaultTileCost[2],
                                    kDefaultTileCost[3], kDefaultTileCost[4], kDefaultTileCost[5],
                                    kDefaultTileCost[6]};
@@ -367,6 +373,24 @@ void plan_windows(std::vector<SvmItem> &out, int li, int rows, int cols, const f
     }
 }
 
+// Tensor-core K4 items of a rows x cols score map: strips of kTcStrip window
+// columns, each cut into near-equal pieces of at most kTcChunk window rows
+// (a piece also reads the 14 block rows below its last window row).
+void plan_tc(std::vector<TcItem> &out, int li, int rows, int cols) {
+    if (rows <= 0 || cols <= 0) return;
+    const int pieces = (rows + kTcChunk - 1) / kTcChunk;
+    for (int x = 0; x < cols; x += kTcStrip)
+        for (int k = 0; k < pieces; ++k)
+            out.push_back({li, x, (int)((int64_t)rows * k / pieces), (int)((int64_t)rows * (k + 1) / pieces)});
+}
+
+// Largest items first (block rows walked: window rows + 14), so that the
+// persistent CTAs' queue ends with the small ones.
+void order_tc(std::vector<TcItem> &t) {
+    std::stable_sort(t.begin(), t.end(),
+                     [](const TcItem &a, const TcItem &b) { return a.wy1 - a.wy0 > b.wy1 - b.wy0; });
+}
+
 // Adds one level to the plan (tables, descriptor, work items).
 void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int64_t img_off,
                 int32_t img_pitch, const LevelDesc *share = nullptr,
@@ -417,6 +441,7 @@ void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int
     for (int cy = 0; cy < L.Hc; cy += kCellTH)
         for (int cx = 0; cx < L.Wc; cx += kCellTW) p.c_items.push_back({li, cx, cy, 0});
     plan_windows(p.s_items, li, L.rows, L.cols, tile_cost);
+    plan_tc(p.t_items, li, L.rows, L.cols);
     p.atlas_rows += L.Hc;
     p.score_floats += (int64_t)L.rows * L.cols;
     p.max_wc = std::max(p.max_wc, L.Wc);
@@ -466,7 +491,7 @@ bool params_ok(const pd_params *p) {
            !std::isnan(p->keep_logit_threshold) && p->upscale_levels >= 0 && p->upscale_levels <= 64 &&
            p->nms_iou >= 0.f && p->max_boxes_per_frame > 0 && p->max_boxes_per_frame <= 16384 &&
            p->max_candidates_per_frame > 0 &&
-           p->max_candidates_per_frame <= 16384 && p->max_frames > 0 && p->max_width > 0 &&
+           p->max_candidates_per_frame <= 65536 && p->max_frames > 0 && p->max_width > 0 &&
            p->max_height > 0;
 }
 
@@ -483,6 +508,7 @@ int upload_plan(pd_handle *h, cudaStream_t s, const Plan &p, Packed &o, const ui
     put(o.r_items, p.r_items.data(), p.r_items.size() * sizeof(ResizeItem));
     put(o.c_items, p.c_items.data(), p.c_items.size() * sizeof(CellItem));
     put(o.s_items, p.s_items.data(), p.s_items.size() * sizeof(SvmItem));
+    put(o.t_items, p.t_items.data(), p.t_items.size() * sizeof(TcItem));
     put(o.cnn_items, p.cnn_items.data(), p.cnn_items.size() * sizeof(CnnItem));
     put(o.tabs, p.tabs.data(), p.tabs.size() * sizeof(int32_t));
     if (!p.cnn_items.empty()) {
@@ -511,6 +537,18 @@ int encode_svm_maps(CUtensorMap *hog_maps, CUtensorMap *lbp_maps, const float *h
                              svm_lbp_chunk()) != PD_OK)
             return PD_ECUDA;
     }
+    return PD_OK;
+}
+
+// The tensor-core K4's maps: one cell row of a 112-cell strip of the 9 HOG
+// planes, and of a 128-cell strip of the 59 LBP planes.
+int encode_tc_maps(CUtensorMap *hog_map, CUtensorMap *lbp_map, const float *hog, const uint8_t *lbp, int64_t pitch,
+                   int64_t rows, int64_t hog_plane, int64_t lbp_plane) {
+    if (encode_plane_map(hog_map, const_cast<float *>(hog), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, pitch, rows,
+                         kHogBins, hog_plane, 112, 1, kHogBins) != PD_OK ||
+        encode_plane_map(lbp_map, const_cast<uint8_t *>(lbp), CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, pitch, rows,
+                         kLbpBins, lbp_plane, 128, 1, kLbpBins) != PD_OK)
+        return PD_ECUDA;
     return PD_OK;
 }
 
@@ -664,7 +702,8 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
         return code;
     };
     if (cudaGetDevice(&h->device) != cudaSuccess) return bail(PD_ECUDA);
-    if (init_cells() != cudaSuccess || init_svm() != cudaSuccess || init_nms() != cudaSuccess ||
+    if (init_cells() != cudaSuccess || init_svm() != cudaSuccess || init_svm_tc() != cudaSuccess ||
+        init_nms() != cudaSuccess ||
         init_cnn() != cudaSuccess)
         return bail(PD_ECUDA);
 
@@ -709,6 +748,7 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
                       round_up(F * (int64_t)one.r_items.size() * (int64_t)sizeof(ResizeItem), 16) +
                       round_up(F * (int64_t)one.c_items.size() * (int64_t)sizeof(CellItem), 16) +
                       round_up(F * s_bound * (int64_t)sizeof(SvmItem), 16) +
+                      round_up(F * (int64_t)one.t_items.size() * (int64_t)sizeof(TcItem), 16) +
                       round_up(F * (int64_t)one.tabs.size() * 4, 16) + 4096;
         h->desc_cap = round_up(h->desc_cap, kAlign);
     }
@@ -737,7 +777,8 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
         {(int64_t)params->max_frames * params->max_boxes_per_frame * (int64_t)sizeof(pd_box), 0},  // 7
         {(int64_t)params->max_frames * 2 * 4 + 16, 0},             // 8 counts + error word
         {h->frames_cap, 0},                                        // 9 host-input frames
-        {(int64_t)params->max_frames * params->max_candidates_per_frame * 16, 0},  // 10 NMS scratch
+        {(int64_t)params->max_frames * (int64_t)nms_scratch_float4s(params->max_candidates_per_frame) * 16,
+         0},                                                                        // 10 NMS scratch
         {(int64_t)5 * kCnnParams * 4 + 1024 + 2304 * 4, 0},                        // 11 CNN parameters
         {(int64_t)rows * P * 4, 0},                                                 // 12 head values
         {h->score_cap * 4, 0},                                                      // 13 window logits
@@ -761,6 +802,7 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
     h->d_boxes = reinterpret_cast<pd_box *>(h->arena + parts[7].off);
     h->d_counts = reinterpret_cast<int32_t *>(h->arena + parts[8].off);
     h->d_err = reinterpret_cast<unsigned *>(h->d_counts + 2 * params->max_frames);
+    h->d_queue = reinterpret_cast<int *>(h->d_err + 1);
     h->d_frames = h->arena + parts[9].off;
     h->d_nms_scratch = reinterpret_cast<float4 *>(h->arena + parts[10].off);
     h->cnn = reinterpret_cast<float *>(h->arena + parts[11].off);
@@ -811,7 +853,11 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
         cudaMemcpy(h->d_lbp_map, map, 256, cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(PD_ECUDA);
     if (encode_svm_maps(h->hog_map, h->lbp_map, h->atlas.hog, h->atlas.lbp, P, rows, h->atlas.hog_plane,
-                        h->atlas.lbp_plane) != PD_OK)
+                        h->atlas.lbp_plane) != PD_OK ||
+        encode_tc_maps(&h->tc_hog_map, &h->tc_lbp_map, h->atlas.hog, h->atlas.lbp, P, rows, h->atlas.hog_plane,
+                       h->atlas.lbp_plane) != PD_OK)
+        return bail(PD_ECUDA);
+    if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
         return bail(PD_ECUDA);
     *out = h;
     return PD_OK;
@@ -854,6 +900,7 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
                                h->proposal ? kSparseTileCost : h->tile_cost, h->proposal);
             if (r != PD_OK) return fail(h, r, "frame %d: planning failed", f);
         }
+        order_tc(p.t_items);
         if (p.atlas_rows > h->atlas.rows || p.pyr_bytes > h->pyr_cap || p.score_floats > h->score_cap ||
             (int64_t)p.s_items.size() > h->flag_cap || (int64_t)p.c_items.size() > h->flag_cap)
             return fail(h, PD_EINVAL, "batch exceeds the arena");
@@ -904,8 +951,15 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
         PD_CUDA(h, launch_cells(q, dl, h->d_pyr, h->atlas, dptr<CellItem>(h, o.c_items), (int)p.c_items.size(),
                                 h->d_lbp_map, cf));
         if (timed) PD_CUDA(h, record(h->stage_ev[2], q));
-        PD_CUDA(h, launch_svm(q, h->hog_map, h->lbp_map, dl, h->d_w, h->bias, h->p.l2hys_clip, h->d_scores,
-                              dptr<SvmItem>(h, o.s_items), (int)p.s_items.size(), h->d_err, sf));
+        if (h->p.flags & PD_FLAG_SVM_FP32) {
+            PD_CUDA(h, launch_svm(q, h->hog_map, h->lbp_map, dl, h->d_w, h->bias, h->p.l2hys_clip, h->d_scores,
+                                  dptr<SvmItem>(h, o.s_items), (int)p.s_items.size(), h->d_err, sf));
+        } else {
+            PD_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), q));
+            PD_CUDA(h, launch_svm_tc(q, h->tc_hog_map, h->tc_lbp_map, dl, dptr<TcItem>(h, o.t_items),
+                                     (int)p.t_items.size(), h->d_queue, h->sm_count, h->d_w, h->bias,
+                                     h->p.l2hys_clip, h->d_scores, cf, h->d_err));
+        }
         if (timed) PD_CUDA(h, record(h->stage_ev[3], q));
         PD_CUDA(h, launch_nms(q, df, dl, n_frames, h->d_scores, h->p.threshold, h->p.nms_iou,
                               h->d_nms_scratch, h->p.max_candidates_per_frame, h->m_boxes,
@@ -1073,6 +1127,7 @@ int pd_cnn_forward(pd_handle *h, void *stream, const uint8_t *d_level, int Wk, i
     plan_level(p, 0, 0, Wk, Hk, Wk, Hk, 0, pitch);
     p.c_items.clear();
     p.s_items.clear();
+    p.t_items.clear();
     p.tabs.clear();
     for (int cy = 0; cy < Hc; cy += kCnnTile)
         for (int cx = 0; cx < Wc; cx += kCnnTile) p.cnn_items.push_back({0, cy, cx, 0});
@@ -1278,6 +1333,7 @@ int pd_resize_levels(pd_handle *h, void *stream, const uint8_t *d_frame, int W, 
     p.frames.push_back(fd);
     p.c_items.clear();
     p.s_items.clear();
+    p.t_items.clear();
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Packed o;
     int r = upload_plan(h, s, p, o);
@@ -1299,6 +1355,7 @@ int pd_cell_features(pd_handle *h, void *stream, const uint8_t *d_level, int Wk,
     Plan p;
     plan_level(p, 0, 0, Wk, Hk, Wk, Hk, 0, pitch);
     p.s_items.clear();
+    p.t_items.clear();
     p.tabs.clear();
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Packed o;
@@ -1332,17 +1389,31 @@ int pd_window_scores(pd_handle *h, void *stream, const float *d_hog, int64_t hog
     p.c_items.clear();
     p.tabs.clear();
     if (p.s_items.empty()) return PD_OK;
-    CUtensorMap hm[kSvmShapes], lm[kSvmShapes];
+    const bool fp32 = (h->p.flags & PD_FLAG_SVM_FP32) != 0;
+    if (fp32)
+        p.t_items.clear();
+    else
+        p.s_items.clear();
+    order_tc(p.t_items);
+    CUtensorMap hm[kSvmShapes], lm[kSvmShapes], th, tl;
     const int64_t rows = std::max(cells_y, 1);
-    if (encode_svm_maps(hm, lm, d_hog, d_lbp, cell_pitch, rows, hog_plane, lbp_plane) != PD_OK)
+    if (encode_svm_maps(hm, lm, d_hog, d_lbp, cell_pitch, rows, hog_plane, lbp_plane) != PD_OK ||
+        encode_tc_maps(&th, &tl, d_hog, d_lbp, cell_pitch, rows, hog_plane, lbp_plane) != PD_OK)
         return fail(h, PD_ECUDA, "pd_window_scores: tensor map encoding failed");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Packed o;
     int r = upload_plan(h, s, p, o);
     if (r != PD_OK) return r;
     PD_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), s));
-    PD_CUDA(h, launch_svm(s, hm, lm, dptr<LevelDesc>(h, o.levels), h->d_w, h->bias, h->p.l2hys_clip,
-                          d_scores, dptr<SvmItem>(h, o.s_items), (int)p.s_items.size(), h->d_err));
+    if (fp32) {
+        PD_CUDA(h, launch_svm(s, hm, lm, dptr<LevelDesc>(h, o.levels), h->d_w, h->bias, h->p.l2hys_clip,
+                              d_scores, dptr<SvmItem>(h, o.s_items), (int)p.s_items.size(), h->d_err));
+    } else {
+        PD_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), s));
+        PD_CUDA(h, launch_svm_tc(s, th, tl, dptr<LevelDesc>(h, o.levels), dptr<TcItem>(h, o.t_items),
+                                 (int)p.t_items.size(), h->d_queue, h->sm_count, h->d_w, h->bias,
+                                 h->p.l2hys_clip, d_scores, nullptr, h->d_err));
+    }
     return PD_OK;
 }
 

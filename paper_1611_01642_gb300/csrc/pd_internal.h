@@ -55,6 +55,7 @@ struct LevelDesc {
 struct ResizeItem { int32_t frame, x0, y0, pad; };   // source tile of a frame
 struct CellItem { int32_t level, cx0, cy0, pad; };   // cell tile of a level
 struct SvmItem { int32_t level, wx0, wy0, shape; };  // window tile of a level, tile shape index
+struct TcItem { int32_t level, wx0, wy0, wy1; };     // tensor-core K4: window columns [wx0, wx0 + 104), rows [wy0, wy1)
 
 // Tiles.
 constexpr int kResizeTW = 128;  // source tile width  (pixels)
@@ -62,6 +63,8 @@ constexpr int kResizeTH = 32;   // source tile height (pixels)
 constexpr int kCellTW = 15;     // cells per cell tile along x (128 threads = 8*15+8 columns)
 constexpr int kCellTH = 8;      // cells per cell tile along y
 constexpr int kSvmShapes = 7;   // K4 tile shapes: 32x16, 64x8, 32x8, 64x4, 64x2, 32x12, 32x4 windows
+constexpr int kTcStrip = 104;   // tensor-core K4: window columns per item
+constexpr int kTcChunk = 64;    // tensor-core K4: window rows per item at most
 
 struct SvmShapeInfo {
     int tw, th;     // windows per tile along x / y
@@ -100,6 +103,24 @@ cudaError_t launch_svm(cudaStream_t s, const CUtensorMap *hog_maps, const CUtens
                        const LevelDesc *d_levels, const float *d_w, float bias, float clip,
                        float *scores, const SvmItem *d_items, int n_items, unsigned *d_err,
                        const uint32_t *s_flag = nullptr);
+// Tensor-core K4: persistent CTAs (grid at most one per SM) over an item
+// queue (*d_queue must be 0 at launch); c_flag non-null selects the sparse
+// path. hog_map / lbp_map: 3-D maps over the cell planes with boxes of
+// 112 x 1 x 9 (f32) and 128 x 1 x 59 (u8).
+cudaError_t init_svm_tc();
+int svm_tc_smem_bytes();
+cudaError_t launch_svm_tc(cudaStream_t s, const CUtensorMap &hog_map, const CUtensorMap &lbp_map,
+                          const LevelDesc *d_levels, const TcItem *d_items, int n_items, int *d_queue, int grid,
+                          const float *d_w, float bias, float clip, float *scores, const uint32_t *c_flag,
+                          unsigned *d_err);
+// Per-frame NMS scratch (float4 units) for a candidate cap: the decoded
+// boxes, plus the sort keys when the cap is above 16,384 (shared memory
+// holds them below).
+__host__ __device__ inline size_t nms_scratch_float4s(int cap) {
+    size_t p = 1;
+    while (p < (size_t)cap) p <<= 1;
+    return cap > 16384 ? (size_t)cap + p / 2 : (size_t)cap;
+}
 cudaError_t launch_nms(cudaStream_t s, const FrameDesc *d_frames, const LevelDesc *d_levels,
                        int n_frames, const float *scores, float threshold, float iou,
                        float4 *scratch, int max_cand, pd_box *boxes, int max_boxes,

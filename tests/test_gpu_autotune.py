@@ -1,4 +1,4 @@
-"""GPU tests of the K4 tile-shape autotuner and of shape independence.
+"""GPU tests of the FP32 K4's tile-shape autotuner and of shape independence.
 
 Every K4 tile shape accumulates a window's 15 x 7 x 95 products in the same
 order (block rows, then columns, per channel; channels split over the 8
@@ -39,7 +39,8 @@ def test_scores_identical_for_every_tiling(template):
     w, b = template
     frames = [synth.make_scene(1242, 375, 2, 7), synth.make_scene(640, 480, 3, 8)]
     dev = [torch.from_numpy(f).cuda() for f in frames]
-    d = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=2, max_width=1242, max_height=480)
+    d = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=2, max_width=1242, max_height=480,
+                    flags=pd.PD_FLAG_SVM_FP32)
     try:
         ref = _scores(d, dev)
         for s in range(pd.TILE_SHAPES):

@@ -153,13 +153,15 @@ def _box_rows(a):
     return [tuple(r) for r in a.tolist()]
 
 
-def test_sparse_threshold_minus_inf_equals_plain(template):
-    """With every window kept, the sparse path returns the plain path's scores and boxes bit for bit."""
+@pytest.mark.parametrize("flags", [0, pd.PD_FLAG_SVM_FP32])
+def test_sparse_threshold_minus_inf_equals_plain(template, flags):
+    """With every window kept, the sparse path returns the plain path's scores and boxes bit for bit
+    (tensor-core and FP32 window-score kernels)."""
     from paper_1611_01642_gb300 import build as bld
     bld.build()
     w, b = template
     frames = [synth.make_scene(1242, 375, 1, 40), synth.make_scene(640, 480, 2, 41)]
-    d = pd.Detector(w, b, max_frames=2, max_width=1242, max_height=480)
+    d = pd.Detector(w, b, max_frames=2, max_width=1242, max_height=480, flags=flags)
     try:
         pd.pd_cnn_set_params(d.h, _params(5))
         dev = [torch.from_numpy(f).cuda() for f in frames]
@@ -179,16 +181,18 @@ def test_sparse_threshold_minus_inf_equals_plain(template):
         d.close()
 
 
+@pytest.mark.parametrize("flags", [0, pd.PD_FLAG_SVM_FP32])
 @pytest.mark.parametrize("quantile", [0.9, 0.999, 1.0])
-def test_sparse_path_skips_only_unkept_tiles(template, quantile):
+def test_sparse_path_skips_only_unkept_tiles(template, quantile, flags):
     """Windows with keep-logit above the threshold are scored exactly; skipped ones are -inf and
     none of them has a logit above the threshold; the boxes are the oracle NMS of the sparse maps;
-    the logits are those of the proposal network run level by level."""
+    the logits are those of the proposal network run level by level (tensor-core and FP32
+    window-score kernels)."""
     from paper_1611_01642_gb300 import build as bld
     bld.build()
     w, b = template
     img = synth.make_scene(1242, 375, 1, 42)
-    d = pd.Detector(w, b, max_frames=1, max_width=1242, max_height=375)
+    d = pd.Detector(w, b, max_frames=1, max_width=1242, max_height=375, flags=flags)
     try:
         pd.pd_cnn_set_params(d.h, _params(6))
         dev = [torch.from_numpy(img).cuda()]

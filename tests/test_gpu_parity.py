@@ -153,7 +153,8 @@ def _scores_gpu_from_cells(det, hog, lbp):
     return out.cpu().numpy()[:rows * cols].reshape(rows, cols)
 
 
-@pytest.mark.parametrize("W,H", [(64, 128), (72, 136), (300, 260), (520, 410), (1242, 375)])
+@pytest.mark.parametrize("W,H", [(64, 128), (72, 136), (300, 260), (520, 410), (1242, 375), (900, 700),
+                                 (300, 900), (896, 128)])
 def test_window_scores_from_oracle_cells(det, template, W, H):
     w, b = template
     L = synth.random_image(W, H, 101 + W, smooth=True)
@@ -198,6 +199,33 @@ def test_nms_exact_on_identical_maps(det, seed):
     kept, ncand = counts.cpu().numpy().tolist()
     ref, rcand = oracle.nms(maps, levels, W, H, threshold=0.0, iou_thr=0.5, max_boxes=4096)
     assert ncand == rcand and kept == len(ref)
+    got = np.frombuffer(boxes.cpu().numpy().tobytes(), dtype=pd.BOX_DTYPE)[:kept]
+    for name in ["level", "wx", "wy", "x", "y", "w", "h", "score"]:
+        assert np.array_equal(got[name], ref[name]), name
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_nms_exact_with_more_candidates_than_shared_memory_holds(template, seed):
+    # caps above 16,384 candidates keep the sort keys in global memory
+    W, H = 1242, 375
+    levels = oracle.pyramid(W, H, F105)
+    dims = [(hk // 8 - 15, wk // 8 - 7) for wk, hk in levels]
+    maps = synth.random_score_maps(dims, 10 + seed, n_distinct=64 if seed else 4096, pos_frac=0.8)
+    flat = np.concatenate([m.ravel() for m in maps]).astype(np.float32)
+    w, b = template
+    d = pd.Detector(w, b, max_frames=1, max_width=W, max_height=H, max_candidates_per_frame=40000,
+                    max_boxes_per_frame=4096)
+    try:
+        boxes = torch.zeros((4096, 8), dtype=torch.int32, device="cuda")
+        counts = torch.zeros(2, dtype=torch.int32, device="cuda")
+        pd.pd_nms_maps(d.h, torch.from_numpy(flat).cuda(), [q[0] for q in dims], [q[1] for q in dims],
+                       levels, W, H, boxes, 4096, counts)
+        torch.cuda.synchronize()
+    finally:
+        d.close()
+    kept, ncand = counts.cpu().numpy().tolist()
+    ref, rcand = oracle.nms(maps, levels, W, H, threshold=0.0, iou_thr=0.5, max_boxes=4096)
+    assert rcand > 16384 and ncand == rcand and kept == len(ref)
     got = np.frombuffer(boxes.cpu().numpy().tobytes(), dtype=pd.BOX_DTYPE)[:kept]
     for name in ["level", "wx", "wy", "x", "y", "w", "h", "score"]:
         assert np.array_equal(got[name], ref[name]), name
@@ -392,11 +420,11 @@ def test_errors_are_reported(template):
 
 @pytest.mark.parametrize("shape", range(7))
 def test_window_scores_every_tile_shape(template, shape):
-    # force one K4 tile shape through the planner's cost table
+    # force one tile shape of the FP32 K4 through the planner's cost table
     from paper_1611_01642_gb300 import build as bld
     bld.build()
     w, b = template
-    d = pd.Detector(w, b, max_frames=1, max_width=700, max_height=600)
+    d = pd.Detector(w, b, max_frames=1, max_width=700, max_height=600, flags=pd.PD_FLAG_SVM_FP32)
     try:
         costs = [1e6] * pd.TILE_SHAPES
         costs[shape] = 1.0
