@@ -16,35 +16,37 @@
 // summing xh.wh + xl.wh + xh.wl (K = 3 x 96; the dropped xl.wl and the
 // rounding of the low parts are below 2^-16 of |x w| per term).
 //
-// One persistent CTA per SM (8 warps) takes items from a queue: an item is a
-// strip of up to 104 window columns and up to 64 window rows of one level.
-// It walks the strip's block rows top to bottom:
-//  * TMA (cp.async.bulk.tensor.3d) brings cell rows into a ring of four
-//    slots: the 9 HOG planes (f32) and the 59 LBP count planes (u8) of the
-//    strip's 112 + 16 cells; the LBP counts of a staged row are replaced in
-//    place by the sums of horizontally adjacent cells.
-//  * Producers: threads 0-127 build the HOG part of one A row each (36 cell
-//    values, L2-Hys, bf16 split), threads 128-255 the LBP part (2 x 2 count
-//    sum, L1-sqrt and its bf16 split from a 512-entry table). A row m holds
-//    block wx0 + 26 (m / 32) + m % 32: every warp of 32 rows covers 26
-//    windows and the 6 blocks to their right, so the j terms stay inside a
-//    warp and move with shuffles.
-//  * Thread 0 issues the 18 MMAs of the row (K-major, no-swizzle canonical
-//    layouts in shared memory; D in one of two 128-column TMEM buffers) and
-//    commits them to an mbarrier. The A operand is double buffered: the
-//    producers build row r + 1 while row r's MMAs run.
-//  * Epilogue of row r - 1 (all warps; warp w reads TMEM lanes 32 (w % 4)
-//    and half w / 4 of the 105 columns): lane l sums P[l + j][(i, j)] over j
-//    with shuffles and adds it to the running score of window row r - 1 - i.
-//    Warps of half 0 carry i = 0..7, half 1 i = 8..14; a window row's partial
-//    sum passes from half 0 to half 1 through shared memory, so every score
-//    is b plus its terms in the fixed order (i, j) = (0,0), (0,1), ...: the
-//    result does not depend on how the level is cut into items.
+// One persistent CTA per SM takes items from a queue: an item is a strip of
+// up to 104 window columns and up to 64 window rows of one level, walked one
+// block row at a time by a warp-specialised pipeline (mbarriers between the
+// roles, bounded waits):
+//  * 8 producer warps: first all of them replace a staged row's LBP counts
+//    by sums of horizontally adjacent cells (in place); then warps 0-3 give
+//    A row m (block wx0 + 26 (m / 32) + m % 32) the 36 values of its 2x2 HOG
+//    cells (L2-Hys, bf16 split) and LBP bins 0..19, warps 4-7 LBP bins
+//    20..58 (the 2 x 2 count sums, L1-sqrt and its bf16 split from a
+//    512-entry table). Every group of 32 rows covers 26 windows and the 6
+//    blocks to their right, so the j terms of a window stay inside one warp
+//    of the epilogue;
+//  * one thread (lane 0 of the first epilogue warp, between its epilogue
+//    rows) issues the TMA (cp.async.bulk.tensor.3d) of cell rows into a ring
+//    of four slots (the 9 HOG planes, f32, and the 59 LBP count planes, u8,
+//    of the strip's 112 + 16 cells) and the 18 MMAs of every block row
+//    (K-major no-swizzle canonical operands in shared memory, D in one of
+//    two 128-column TMEM buffers), committed to the A-free and D-full
+//    barriers;
+//  * 4 epilogue warps (warp e reads TMEM lanes 32 e .. 32 e + 31): lane l adds
+//    P[l + j][(i, j)] (a shuffle by j) to the running score of window row
+//    r - i, for all 105 positions, in the fixed order (i, j) = (0,0), (0,1),
+//    ..., so every score is b plus its terms in one order whatever the item
+//    cut; window row r - 14 is complete and stored.
+// The A operand and the accumulators are double buffered, so the producers
+// build row r + 1 and the epilogue reads row r - 1 while row r's MMAs run.
 // Sparse path: a window is scored when every cell tile under it was
 // computed; block rows that no such window needs are skipped, other windows
-// get -inf. Waits are bounded (1 s): a wait that gives up sets the error
-// word and the CTA drains its copies and MMAs, frees its tensor memory and
-// leaves.
+// get -inf. A wait that gives up (1 s) sets the error word and a CTA flag
+// that ends every role's waits; the CTA then drains its copies and MMAs,
+// frees its tensor memory and leaves.
 #include "pd_internal.h"
 
 #include <cuda_bf16.h>
@@ -52,7 +54,9 @@
 namespace pd {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kWarps = 12;            // 4 HOG, 4 LBP, 4 epilogue (one thread of which also issues)
+constexpr int kProducers = 8;         // producer warps
+constexpr int kThreads = 32 * kWarps;
 constexpr int kM = 128;               // A rows = TMEM lanes
 constexpr int kN = 112;               // 105 template positions, padded
 constexpr int kWinPerWarp = 26;
@@ -63,6 +67,7 @@ constexpr int kLbpX = 128;            // LBP cells per staged row (box width, fr
 constexpr int kSlots = 4;
 constexpr uint32_t kTmemCols = 256;   // two accumulator buffers of 128 columns
 constexpr uint64_t kWaitNs = 1000000000ull;
+constexpr int kProducerBarrier = 1;   // named barrier of the producer warps
 static_assert(4 * kWinPerWarp == kTcStrip, "strip width");
 static_assert(kWinPerWarp + kWinBW - 1 <= 32, "window blocks inside a warp");
 
@@ -79,15 +84,18 @@ struct TcSmem {
     uint8_t b[14 * kSBO];             // B operand: template high | low parts
     Slot slot[kSlots];                // staged cell rows
     uint32_t tab[512];                // sum of 4 cell counts -> bf16 high | low << 16 of sqrt(S / 256)
-    float handoff[2][kM];             // window-row partial sums from half 0 to half 1
     uint32_t win_ok[kTcChunk][4];     // sparse: window of the strip is scored
     uint8_t row_ok[kTcChunk];         // sparse: window row holds a scored window
     uint8_t tflag[16][16];            // sparse: cell-tile flags of the item's region
-    unsigned long long cbar[kSlots];  // cell row arrival
-    unsigned long long mbar[2];       // MMA completion per accumulator buffer
-    unsigned long long wbar;          // unused spare barrier slot
+    unsigned long long cfull[kSlots];   // cell row arrived (TMA transaction count)
+    unsigned long long cempty[kSlots];  // cell row no longer read (8 producer warps)
+    unsigned long long afull[2];        // A operand written (8 producer warps)
+    unsigned long long aempty[2];       // A operand read by the MMAs (commit)
+    unsigned long long dfull[2];        // accumulators written (commit)
+    unsigned long long dempty[2];       // accumulators read (4 epilogue warps)
     uint32_t tmem;
     int item;
+    volatile int failed;
 };
 static_assert(offsetof(TcSmem, slot) % 128 == 0 && offsetof(TcSmem, b) % 1024 == 0, "alignment");
 
@@ -99,19 +107,38 @@ __device__ __forceinline__ uint64_t global_ns() {
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
     return t;
 }
-__device__ __forceinline__ bool bar_wait(unsigned long long *bar, uint32_t parity) {
-    const uint32_t a = smem_u32(bar);
-    uint32_t ok = 0;
-    const uint64_t t0 = global_ns();
-    while (true) {
-        asm volatile(
-            "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-            : "=r"(ok)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (ok || global_ns() - t0 > kWaitNs) break;
-    }
+__device__ __forceinline__ bool try_wait(unsigned long long *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
     return ok != 0;
+}
+// Bounded wait for phase `parity`; gives up after 1 s (and marks the CTA
+// failed) or as soon as another role has marked it failed.
+__device__ __forceinline__ bool bar_wait(TcSmem &S, unsigned long long *bar, uint32_t parity, unsigned *err) {
+    if (try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!S.failed) {
+        if (try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitNs) {
+            S.failed = 1;
+            atomicOr(err, kErrTimeout);
+            break;
+        }
+    }
+    return false;
+}
+// Drain wait (after a failure): bounded, ignores the failed flag.
+__device__ __forceinline__ void drain_wait(unsigned long long *bar, uint32_t parity) {
+    const uint64_t t0 = global_ns();
+    while (!try_wait(bar, parity) && global_ns() - t0 < kWaitNs) {
+    }
+}
+__device__ __forceinline__ void arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void tma_3d(void *dst, const CUtensorMap *map, unsigned long long *bar, int x, int y,
                                        int z) {
@@ -143,11 +170,6 @@ __device__ __forceinline__ void umma_commit(unsigned long long *bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-#define PD_LD_X8(taddr, v, o)                                                                              \
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"                 \
-                 : "=f"(v[o + 0]), "=f"(v[o + 1]), "=f"(v[o + 2]), "=f"(v[o + 3]), "=f"(v[o + 4]),         \
-                   "=f"(v[o + 5]), "=f"(v[o + 6]), "=f"(v[o + 7])                                           \
-                 : "r"(taddr))
 #define PD_LD_X16(taddr, v, o)                                                                             \
     asm volatile(                                                                                          \
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "  \
@@ -173,10 +195,10 @@ __device__ __forceinline__ void st_v2(uint32_t addr, uint32_t a, uint32_t b) {
     asm volatile("st.shared.v2.b32 [%0], {%1,%2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
 }
 
-// HOG part of A row m (features 0..35): cells (r, c), (r, c+1), (r+1, c),
-// (r+1, c+1) of slots s0 (row r) and s1 (row r + 1), L2-Hys.
-__device__ __forceinline__ void build_hog(const Slot &s0, const Slot &s1, int c, bool valid, float clip,
-                                          uint32_t row) {
+// HOG part of A row m (K 0..35): the 36 values of its cells (r, c),
+// (r, c+1), (r+1, c), (r+1, c+1) (slots s0 = row r, s1 = row r + 1), in the
+// template's order (cells TL, TR, BL, BR, 9 bins each), L2-Hys, bf16 split.
+__device__ __forceinline__ void build_hog(const Slot &s0, const Slot &s1, int c, float clip, uint32_t row) {
     float v[36];
 #pragma unroll
     for (int b = 0; b < kHogBins; ++b) {
@@ -185,69 +207,99 @@ __device__ __forceinline__ void build_hog(const Slot &s0, const Slot &s1, int c,
         v[18 + b] = s1.hog[b][c];
         v[27 + b] = s1.hog[b][c + 1];
     }
-    float ss = 0.f;
+    // sums of squares in four interleaved partial sums (independent chains)
+    float q[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int t = 0; t < 36; ++t) ss = fmaf(v[t], v[t], ss);
-    const float i1 = 1.0f / sqrtf(ss + 1.0f);
-    float s2 = 0.f;
+    for (int t = 0; t < 36; ++t) q[t & 3] = fmaf(v[t], v[t], q[t & 3]);
+    const float i1 = rsqrtf((q[0] + q[1]) + (q[2] + q[3]) + 1.0f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = 0.f;
 #pragma unroll
     for (int t = 0; t < 36; ++t) {
         v[t] = fminf(v[t] * i1, clip);
-        s2 = fmaf(v[t], v[t], s2);
+        q[t & 3] = fmaf(v[t], v[t], q[t & 3]);
     }
-    const float i2 = 1.0f / sqrtf(s2 + 1e-6f);
-    uint32_t hi[18], lo[18];
+    const float i2 = rsqrtf((q[0] + q[1]) + (q[2] + q[3]) + 1e-6f);
+    // 16-byte chunks of 8 features (the fifth holds 4 HOG values), stored as
+    // they are split
 #pragma unroll
-    for (int p = 0; p < 18; ++p) {
-        const float a = valid ? v[2 * p] * i2 : 0.f, b = valid ? v[2 * p + 1] * i2 : 0.f;
-        split2(a, b, hi[p], lo[p]);
-    }
+    for (int ch = 0; ch < 5; ++ch) {
+        uint32_t hi[4], lo[4];
 #pragma unroll
-    for (int ch = 0; ch < 4; ++ch) {
-        st_v4(row + ch * 128, hi[4 * ch], hi[4 * ch + 1], hi[4 * ch + 2], hi[4 * ch + 3]);
-        st_v4(row + (12 + ch) * 128, lo[4 * ch], lo[4 * ch + 1], lo[4 * ch + 2], lo[4 * ch + 3]);
+        for (int p = 0; p < 4; ++p) {
+            const int t = 8 * ch + 2 * p;
+            if (t < 36) split2(v[t] * i2, v[t + 1] * i2, hi[p], lo[p]);
+        }
+        if (ch < 4) {
+            st_v4(row + ch * 128, hi[0], hi[1], hi[2], hi[3]);
+            st_v4(row + (12 + ch) * 128, lo[0], lo[1], lo[2], lo[3]);
+        } else {
+            st_v2(row + 4 * 128, hi[0], hi[1]);
+            st_v2(row + 16 * 128, lo[0], lo[1]);
+        }
     }
-    st_v2(row + 4 * 128, hi[16], hi[17]);
-    st_v2(row + 16 * 128, lo[16], lo[17]);
 }
 
-// LBP part of A row m (features 36..95): the staged rows hold sums of
-// horizontally adjacent cells, so cells (r, c..c+1) + (r+1, c..c+1) are two
-// loads; the table gives the bf16 split of sqrt(S / 256).
-__device__ __forceinline__ void build_lbp(const Slot &s0, const Slot &s1, const uint32_t *tab, int c, bool valid,
+// LBP part of A row m (features 36..95), K chunks [CH0, CH1): the staged rows
+// hold sums of horizontally adjacent cells, so cells (r, c..c+1) +
+// (r+1, c..c+1) are two loads; the table gives the bf16 split of
+// sqrt(S / 256). Chunk 4 holds bins 0..3 in its upper half, chunks 5..11 bins
+// 4..58 and the zero feature 95; each chunk is stored as soon as it is packed.
+template <int CH0, int CH1>
+__device__ __forceinline__ void build_lbp(const Slot &s0, const Slot &s1, const uint32_t *tab, int c,
                                           uint32_t row) {
-    uint32_t e[60];
 #pragma unroll
-    for (int t = 0; t < kLbpBins; ++t) e[t] = valid ? tab[(uint32_t)s0.lbp[t][c] + (uint32_t)s1.lbp[t][c]] : 0u;
-    e[59] = 0u;
-    uint32_t hi[30], lo[30];
+    for (int ch = CH0; ch < CH1; ++ch) {
+        const int t0 = ch == 4 ? 0 : 8 * ch - 36;
+        const int np = ch == 4 ? 2 : 4;
+        uint32_t hi[4], lo[4];
 #pragma unroll
-    for (int p = 0; p < 30; ++p) {
-        hi[p] = __byte_perm(e[2 * p], e[2 * p + 1], 0x5410);
-        lo[p] = __byte_perm(e[2 * p], e[2 * p + 1], 0x7632);
-    }
-    st_v2(row + 4 * 128 + 8, hi[0], hi[1]);
-    st_v2(row + 16 * 128 + 8, lo[0], lo[1]);
-#pragma unroll
-    for (int ch = 5; ch < 12; ++ch) {
-        const int p = 2 + 4 * (ch - 5);
-        st_v4(row + ch * 128, hi[p], hi[p + 1], hi[p + 2], hi[p + 3]);
-        st_v4(row + (12 + ch) * 128, lo[p], lo[p + 1], lo[p + 2], lo[p + 3]);
+        for (int p = 0; p < np; ++p) {
+            const int t = t0 + 2 * p;
+            const uint32_t e0 = tab[(uint32_t)s0.lbp[t][c] + (uint32_t)s1.lbp[t][c]];
+            const uint32_t e1 = t + 1 < kLbpBins ? tab[(uint32_t)s0.lbp[t + 1][c] + (uint32_t)s1.lbp[t + 1][c]] : 0u;
+            hi[p] = __byte_perm(e0, e1, 0x5410);
+            lo[p] = __byte_perm(e0, e1, 0x7632);
+        }
+        if (ch == 4) {
+            st_v2(row + 4 * 128 + 8, hi[0], hi[1]);
+            st_v2(row + 16 * 128 + 8, lo[0], lo[1]);
+        } else {
+            st_v4(row + ch * 128, hi[0], hi[1], hi[2], hi[3]);
+            st_v4(row + (12 + ch) * 128, lo[0], lo[1], lo[2], lo[3]);
+        }
     }
 }
 
-// In place: LBP count c[t][x] -> c[t][x] + c[t][x + 1] (x < 127) of a
-// staged row. One warp per plane row; counts are at most 64, and the 7-bit
-// mask keeps bytes that hold no valid count from carrying into a neighbour.
-__device__ __forceinline__ void pair_sums(Slot &s, int tid) {
-    for (int w = tid; w < kLbpBins * 32; w += kThreads) {
-        uint32_t *row = reinterpret_cast<uint32_t *>(s.lbp[w >> 5]);
-        const int k = w & 31;
-        const uint32_t x = row[k] & 0x7f7f7f7fu;
-        const uint32_t y = k < 31 ? row[k + 1] & 0x7f7f7f7fu : 0u;
-        __syncwarp();
-        row[k] = x + __funnelshift_r(x, y, 8);
+// In place, by the 256 producer threads: LBP count c[t][x] -> c[t][x] +
+// c[t][x + 1] (x < 127) of a staged row. A warp takes whole plane rows (word
+// k of the row per lane), all its loads first; counts are at most 64, and
+// the 7-bit mask keeps bytes that hold no valid count from carrying into a
+// neighbour.
+constexpr int kPairIters = (kLbpBins * 32 + 255) / 256;  // 8
+__device__ __forceinline__ void pair_sums(Slot &s, int pt) {
+    uint32_t x[kPairIters], y[kPairIters];
+    const int k = pt & 31;
+#pragma unroll
+    for (int n = 0; n < kPairIters; ++n) {
+        const int w = pt + 256 * n;
+        if (w < kLbpBins * 32) {
+            const uint32_t *row = reinterpret_cast<const uint32_t *>(s.lbp[w >> 5]);
+            x[n] = row[k] & 0x7f7f7f7fu;
+            y[n] = k < 31 ? row[k + 1] & 0x7f7f7f7fu : 0u;
+        }
     }
+    __syncwarp();
+#pragma unroll
+    for (int n = 0; n < kPairIters; ++n) {
+        const int w = pt + 256 * n;
+        if (w < kLbpBins * 32) reinterpret_cast<uint32_t *>(s.lbp[w >> 5])[k] = x[n] + __funnelshift_r(x[n], y[n], 8);
+    }
+}
+
+// named barrier of the producer warps
+__device__ __forceinline__ void producer_barrier() {
+    asm volatile("bar.sync %0, %1;" ::"n"(kProducerBarrier), "n"(32 * kProducers) : "memory");
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -263,10 +315,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         return;
     }
     if (tid == 0) {
-        for (int s = 0; s < kSlots; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.cbar[s])));
-        for (int s = 0; s < 2; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar[s])));
+        auto init = [](unsigned long long *bar, uint32_t count) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+        };
+        for (int s = 0; s < kSlots; ++s) {
+            init(&S.cfull[s], 1);
+            init(&S.cempty[s], kProducers);
+        }
+        for (int s = 0; s < 2; ++s) {
+            init(&S.afull[s], kProducers);
+            init(&S.aempty[s], 1);
+            init(&S.dfull[s], 1);
+            init(&S.dempty[s], 4);
+        }
+        S.failed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -296,35 +358,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         S.tab[s] = e;
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B -> tensor cores
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = S.tmem;
     const uint32_t a_base = smem_u32(S.a[0]), b_base = smem_u32(S.b);
 
-    // CTA-uniform pipeline state
-    uint32_t nrow = 0;      // block rows processed (A buffer, D buffer and MMA barrier phase)
-    uint32_t ncell = 0;     // cell rows loaded (slot and its barrier phase)
-    uint32_t issued = 0;    // thread 0: cell rows whose load was issued
-    int fail = 0;           // warp-uniform: a wait of this warp gave up
-    // bounded wait, decided for the whole warp (shuffles and tcgen05.ld below
-    // need every lane)
-    auto uwait = [&](unsigned long long *bar, uint32_t parity) -> bool {
-        const bool ok = __all_sync(0xffffffffu, !fail && bar_wait(bar, parity));
-        if (!ok) fail = 1;
-        return ok;
-    };
-
-    const int q = warp & 3, half = warp >> 2;
-    float acc[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+    // pipeline counters, advanced identically by every role
+    uint32_t nrow = 0;      // block rows (A buffer, D buffer, their barrier phases)
+    uint32_t ncell = 0;     // cell rows loaded (slot and its barrier phases)
+    uint32_t issued = 0, committed = 0;  // control thread: loads issued, MMA rows committed
 
     for (;;) {
         if (tid == 0) S.item = atomicAdd(queue, 1);
         __syncthreads();
         const int item = S.item;
-        if (item >= n_items) break;
+        if (item >= n_items || S.failed) break;
         const TcItem it = items[item];
         const LevelDesc L = levels[it.level];
         const int wend = min(it.wx0 + kTcStrip, L.cols);
@@ -332,7 +382,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool sparse = c_flag != nullptr;
         const int xl = it.wx0 & ~15;   // LBP box origin (16-byte boundary)
 
-        // ---- sparse: which windows of the item are scored
+        // ---- sparse: which windows of the item are scored (all threads)
         if (sparse) {
             const int ty0 = it.wy0 / kCellTH, ty1 = (it.wy1 - 1 + kWinBH) / kCellTH;
             const int tx0 = it.wx0 / kCellTW, tx1 = (wend - 1 + kWinBW) / kCellTW;
@@ -342,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 S.tflag[ty - ty0][tx - tx0] = c_flag[L.citem0 + ty * L.ctx + tx] != 0u;
             }
             __syncthreads();
-            for (int row = warp; row < nrows; row += kThreads / 32) {
+            for (int row = warp; row < nrows; row += kWarps) {
                 const int wy = it.wy0 + row;
                 const int a0 = wy / kCellTH - ty0, a1 = (wy + kWinBH) / kCellTH - ty0;
                 uint32_t any = 0u;
@@ -360,14 +410,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     any |= bits;
                 }
                 if (lane == 0) S.row_ok[row] = any != 0u;
-                if (!any)  // no scored window in this row: it is never reached below
+                if (!any)  // no scored window in this row: it is never stored below
                     for (int wx = it.wx0 + lane; wx < wend; wx += 32)
                         scores[L.score_off + (int64_t)wy * L.cols + wx] = -INFINITY;
             }
             __syncthreads();
         }
 
-        // ---- runs of block rows: [ra, rb]
+        // ---- runs of block rows [ra, rb]; every role walks the same runs
         int r_next = it.wy0;
         const int r_last = it.wy1 - 1 + kWinBH - 1;
         while (r_next <= r_last) {
@@ -385,140 +435,161 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (S.row_ok[w2 - it.wy0]) rb = w2 + kWinBH - 1;
             }
             const int n_cell = rb - ra + 2;  // cell rows ra .. rb + 1
+            const int n_blk = rb - ra + 1;
             auto slot_of = [&](int u) -> Slot & { return S.slot[(ncell + u) % kSlots]; };
-            auto issue = [&](int u) {  // thread 0: load cell row ra + u
-                const uint32_t idx = ncell + u;
-                Slot &s = S.slot[idx % kSlots];
-                unsigned long long *bar = &S.cbar[idx % kSlots];
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                             "r"((uint32_t)(sizeof(float) * kHogBins * kHogX + kLbpBins * kLbpX))
-                             : "memory");
-                tma_3d(&s.hog[0][0], &hog_map, bar, it.wx0, L.cell_row + ra + u, 0);
-                tma_3d(&s.lbp[0][0], &lbp_map, bar, xl, L.cell_row + ra + u, 0);
-                ++issued;
+            // bounded wait by every lane of a warp, decided for the whole warp
+            auto warp_wait = [&](unsigned long long *bar, uint32_t parity) {
+                return __all_sync(0xffffffffu, bar_wait(S, bar, parity, err));
             };
-            auto wait_cell = [&](int u) -> bool {
+            auto cell_wait = [&](int u) {  // cell row ra + u has arrived
                 const uint32_t idx = ncell + u;
-                return uwait(&S.cbar[idx % kSlots], (idx / kSlots) & 1u);
+                return warp_wait(&S.cfull[idx % kSlots], (idx / kSlots) & 1u);
             };
-            if (tid == 0)
-                for (int u = 0; u < min(kSlots, n_cell); ++u) issue(u);
-            // the first two rows: arrival and pair sums
-            for (int u = 0; u < 2; ++u)
-                if (wait_cell(u)) pair_sums(slot_of(u), tid);
-            if (__syncthreads_or(fail)) goto abort;
 
-            for (int r = ra; r <= rb + 1; ++r) {
-                const int u = r - ra;
-                if (r <= rb) {
-                    // pair sums of cell row r + 2 (first used by block row r + 1)
-                    if (u + 2 < n_cell && wait_cell(u + 2)) pair_sums(slot_of(u + 2), tid);
-                    // block features of row r -> A[nrow & 1]
-                    if (!fail) {
-                        const int m = tid & (kM - 1);
-                        const int c = kWinPerWarp * (m >> 5) + (m & 31);
-                        const bool valid = it.wx0 + c < L.Wc - 1;
-                        const uint32_t row = a_base + (nrow & 1) * (16 * kSBO) + (m >> 3) * kSBO + (m & 7) * 16;
-                        if (tid < kM)
-                            build_hog(slot_of(u), slot_of(u + 1), c, valid, clip, row);
-                        else
-                            build_lbp(slot_of(u), slot_of(u + 1), S.tab, c + it.wx0 - xl, valid, row);
-                    }
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // A -> tensor cores
-                }
-                if (__syncthreads_or(fail)) goto abort;
-                if (r <= rb && tid == 0) {
-                    tc_fence_after();
-                    const uint32_t d = tmem + (nrow & 1) * 128;
-                    const uint32_t a0 = a_base + (nrow & 1) * (16 * kSBO);
-#pragma unroll
-                    for (int s = 0; s < 6; ++s) umma(d, umma_desc(a0 + 256 * s), umma_desc(b_base + 256 * s), s > 0);
-#pragma unroll
-                    for (int s = 0; s < 6; ++s)
-                        umma(d, umma_desc(a0 + 12 * 128 + 256 * s), umma_desc(b_base + 256 * s), 1);
-#pragma unroll
-                    for (int s = 0; s < 6; ++s)
-                        umma(d, umma_desc(a0 + 256 * s), umma_desc(b_base + 12 * 128 + 256 * s), 1);
-                    umma_commit(&S.mbar[nrow & 1]);
-                    // cell row r is no longer read: its slot takes row r + 4
-                    if (u + kSlots < n_cell) issue(u + kSlots);
-                }
-                // ---- epilogue of block row r - 1
-                if (r > ra) {
-                    const uint32_t k = nrow - 1;  // its index
-                    const int rr = r - 1;
-                    if (uwait(&S.mbar[k & 1], (k >> 1) & 1u)) {
-                        tc_fence_after();
-                        const uint32_t t0 = tmem + ((uint32_t)(32 * q) << 16) + (k & 1) * 128;
-                        if (half == 0) {
-                            float v[56];
-                            PD_LD_X16(t0, v, 0);
-                            PD_LD_X16(t0 + 16, v, 16);
-                            PD_LD_X16(t0 + 32, v, 32);
-                            PD_LD_X8(t0 + 48, v, 48);
-                            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                            acc[0] = bias;
-#pragma unroll
-                            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                                for (int j = 0; j < kWinBW; ++j) {
-                                    const float x = v[kWinBW * i + j];
-                                    acc[i] += j ? __shfl_down_sync(0xffffffffu, x, j) : x;
-                                }
-                            S.handoff[(rr - 7) & 1][32 * q + lane] = acc[7];
-#pragma unroll
-                            for (int i = 7; i > 0; --i) acc[i] = acc[i - 1];
+            if (warp < kProducers) {
+                // ---- producers: warps 0-3 HOG and LBP bins 0..19, warps 4-7
+                // LBP bins 20..58, for rows 32 (w % 4) + lane
+                const bool is_lbp = warp >= 4;
+                const int m = 32 * (warp & 3) + lane;
+                const int c = kWinPerWarp * (m >> 5) + (m & 31);
+                const int cl = c + it.wx0 - xl;
+                // (a row whose block lies past the level's last block holds whatever
+                // the staged cells give: its products only reach windows past the
+                // score map, which are never stored)
+                bool ok = cell_wait(0);
+                if (ok) pair_sums(slot_of(0), tid);
+                for (int u = 0; u < n_blk; ++u) {
+                    const uint32_t k = nrow + u;
+                    ok = ok && cell_wait(u) && cell_wait(u + 1);
+                    if (ok) pair_sums(slot_of(u + 1), tid);
+                    producer_barrier();  // every producer warp, also after a failed wait
+                    if (ok && k >= 2) ok = warp_wait(&S.aempty[k & 1], ((k >> 1) - 1) & 1u);
+                    if (ok) {
+                        const uint32_t row = a_base + (k & 1) * (16 * kSBO) + (m >> 3) * kSBO + (m & 7) * 16;
+                        const Slot &s0 = slot_of(u), &s1 = slot_of(u + 1);
+                        if (!is_lbp) {
+                            build_hog(s0, s1, c, clip, row);
+                            build_lbp<4, 7>(s0, s1, S.tab, cl, row);
                         } else {
-                            float v[56];
-                            PD_LD_X8(t0 + 56, v, 0);
-                            PD_LD_X16(t0 + 64, v, 8);
-                            PD_LD_X16(t0 + 80, v, 24);
-                            PD_LD_X16(t0 + 96, v, 40);
-                            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                            acc[0] = S.handoff[(rr - 8) & 1][32 * q + lane];
-#pragma unroll
-                            for (int i = 0; i < 7; ++i)
-#pragma unroll
-                                for (int j = 0; j < kWinBW; ++j) {
-                                    const float x = v[kWinBW * i + j];
-                                    acc[i] += j ? __shfl_down_sync(0xffffffffu, x, j) : x;
-                                }
-                            const int wy = rr - (kWinBH - 1);
-                            const int wl = kWinPerWarp * q + lane;
-                            const int wx = it.wx0 + wl;
-                            if (wy >= it.wy0 && lane < kWinPerWarp && wx < wend) {
-                                const bool ok = !sparse || ((S.win_ok[wy - it.wy0][wl >> 5] >> (wl & 31)) & 1u);
-                                scores[L.score_off + (int64_t)wy * L.cols + wx] = ok ? acc[6] : -INFINITY;
-                            }
-#pragma unroll
-                            for (int i = 6; i > 0; --i) acc[i] = acc[i - 1];
+                            build_lbp<7, 12>(s0, s1, S.tab, cl, row);
                         }
-                        tc_fence_before();
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // A -> tensor cores
+                    }
+                    __syncwarp();
+                    if (ok && lane == 0) {
+                        arrive(&S.afull[k & 1]);
+                        arrive(&S.cempty[(ncell + u) % kSlots]);
+                        if (u == n_blk - 1) arrive(&S.cempty[(ncell + u + 1) % kSlots]);
                     }
                 }
-                if (r <= rb) ++nrow;
+            } else {
+                // ---- epilogue warps 8-11 (TMEM lanes 32 q .. 32 q + 31); lane 0 of
+                // warp 8 also issues the cell loads and the MMAs of each row
+                // before the epilogue of the row above it
+                const int q = warp & 3;
+                const bool ctrl = warp == kProducers && lane == 0;
+                const int wl = kWinPerWarp * q + lane;
+                const int wx = it.wx0 + wl;
+                bool ok = true, cok = true;  // epilogue / control progress
+                float acc[kWinBH];           // running scores of window rows r - i (a run starts afresh)
+#pragma unroll
+                for (int i = 0; i < kWinBH; ++i) acc[i] = 0.f;
+                auto issue = [&](int u) {  // control: load cell row ra + u into its slot once free
+                    const uint32_t idx = ncell + u;
+                    if (idx >= kSlots)
+                        cok = cok && bar_wait(S, &S.cempty[idx % kSlots], (idx / kSlots - 1) & 1u, err);
+                    if (!cok) return;
+                    Slot &sl = S.slot[idx % kSlots];
+                    unsigned long long *bar = &S.cfull[idx % kSlots];
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                                 "r"((uint32_t)(sizeof(float) * kHogBins * kHogX + kLbpBins * kLbpX))
+                                 : "memory");
+                    tma_3d(&sl.hog[0][0], &hog_map, bar, it.wx0, L.cell_row + ra + u, 0);
+                    tma_3d(&sl.lbp[0][0], &lbp_map, bar, xl, L.cell_row + ra + u, 0);
+                    issued = idx + 1;
+                };
+                if (ctrl)
+                    for (int u = 0; u < min(kSlots, n_cell); ++u) issue(u);
+                for (int u = 0; u <= n_blk; ++u) {
+                    if (ctrl && u < n_blk && cok) {
+                        const uint32_t k = nrow + u;
+                        cok = bar_wait(S, &S.afull[k & 1], (k >> 1) & 1u, err);
+                        if (cok && k >= 2) cok = bar_wait(S, &S.dempty[k & 1], ((k >> 1) - 1) & 1u, err);
+                        if (cok) {
+                            tc_fence_after();
+                            const uint32_t d = tmem + (k & 1) * 128;
+                            const uint32_t a0 = a_base + (k & 1) * (16 * kSBO);
+#pragma unroll
+                            for (int s = 0; s < 6; ++s)
+                                umma(d, umma_desc(a0 + 256 * s), umma_desc(b_base + 256 * s), s > 0);
+#pragma unroll
+                            for (int s = 0; s < 6; ++s)
+                                umma(d, umma_desc(a0 + 12 * 128 + 256 * s), umma_desc(b_base + 256 * s), 1);
+#pragma unroll
+                            for (int s = 0; s < 6; ++s)
+                                umma(d, umma_desc(a0 + 256 * s), umma_desc(b_base + 12 * 128 + 256 * s), 1);
+                            umma_commit(&S.aempty[k & 1]);
+                            umma_commit(&S.dfull[k & 1]);
+                            committed = k + 1;
+                            // cell row ra + u is released after this block row: its slot takes ra + u + 4
+                            if (u + kSlots < n_cell) issue(u + kSlots);
+                        }
+                    }
+                    __syncwarp();
+                    if (u == 0) continue;
+                    // epilogue of block row ra + u - 1
+                    const uint32_t k = nrow + u - 1;
+                    const int r = ra + u - 1;
+                    ok = ok && warp_wait(&S.dfull[k & 1], (k >> 1) & 1u);
+                    if (!ok) continue;
+                    tc_fence_after();
+                    const uint32_t t0 = tmem + ((uint32_t)(32 * q) << 16) + (k & 1) * 128;
+                    // 105 columns in seven groups of 16
+                    acc[0] = bias;
+#pragma unroll
+                    for (int g = 0; g < 7; ++g) {
+                        float v[16];
+                        PD_LD_X16(t0 + 16 * g, v, 0);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        if (g == 6) {
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) arrive(&S.dempty[k & 1]);  // the accumulators may be overwritten
+                        }
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const int n = 16 * g + e;  // (i, j) = (n / 7, n % 7)
+                            if (n < kWinBH * kWinBW) {
+                                const int i = n / kWinBW, j = n % kWinBW;
+                                acc[i] += j ? __shfl_down_sync(0xffffffffu, v[e], j) : v[e];
+                            }
+                        }
+                    }
+                    const int wy = r - (kWinBH - 1);
+                    if (wy >= it.wy0 && lane < kWinPerWarp && wx < wend) {
+                        const bool keep = !sparse || ((S.win_ok[wy - it.wy0][wl >> 5] >> (wl & 31)) & 1u);
+                        scores[L.score_off + (int64_t)wy * L.cols + wx] = keep ? acc[kWinBH - 1] : -INFINITY;
+                    }
+#pragma unroll
+                    for (int i = kWinBH - 1; i > 0; --i) acc[i] = acc[i - 1];
+                }
             }
+            nrow += n_blk;
             ncell += n_cell;
-            if (__syncthreads_or(fail)) goto abort;
             r_next = rb + 1;
         }
+        __syncthreads();  // the item is done by every role (nothing in flight unless a wait failed)
+        if (S.failed) break;
     }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
-    return;
 
-abort:
-    // a wait gave up: drain this CTA's copies and MMAs (bounded), free the
-    // tensor memory and leave
-    if (tid == 0) {
-        atomicOr(err, kErrTimeout);
-        // the last load of each slot (earlier ones completed before their slot was reused)
-        for (uint32_t idx = max(ncell, issued > kSlots ? issued - kSlots : 0u); idx < issued; ++idx)
-            bar_wait(&S.cbar[idx % kSlots], (idx / kSlots) & 1u);
-        if (nrow > 0) bar_wait(&S.mbar[(nrow - 1) & 1], ((nrow - 1) >> 1) & 1u);
+    __syncthreads();
+    if (S.failed && warp == kProducers && lane == 0) {
+        // drain this CTA's copies and MMAs (bounded) before the tensor memory
+        // is freed: the last load of every slot, the last commit
+        for (uint32_t idx = issued > kSlots ? issued - kSlots : 0u; idx < issued; ++idx)
+            drain_wait(&S.cfull[idx % kSlots], (idx / kSlots) & 1u);
+        if (committed > 0) drain_wait(&S.dfull[(committed - 1) & 1], ((committed - 1) >> 1) & 1u);
     }
     tc_fence_before();
     __syncthreads();
@@ -526,7 +597,6 @@ abort:
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-#undef PD_LD_X8
 #undef PD_LD_X16
 
 }  // namespace
