@@ -21,27 +21,29 @@
 // block row at a time by a warp-specialised pipeline (mbarriers between the
 // roles, bounded waits):
 //  * 8 producer warps: first all of them replace a staged row's LBP counts
-//    by sums of horizontally adjacent cells (in place); then warps 0-3 give
-//    A row m (block wx0 + 26 (m / 32) + m % 32) the 36 values of its 2x2 HOG
-//    cells (L2-Hys, bf16 split) and LBP bins 0..19, warps 4-7 LBP bins
-//    20..58 (the 2 x 2 count sums, L1-sqrt and its bf16 split from a
-//    512-entry table). Every group of 32 rows covers 26 windows and the 6
-//    blocks to their right, so the j terms of a window stay inside one warp
-//    of the epilogue;
+//    by sums of horizontally adjacent cells (in place); then they write the
+//    A operand straight into tensor memory (tcgen05.st: row m = lane m, two
+//    bf16 per column), row m holding block wx0 + 26 (m / 32) + m % 32: warps
+//    0-3 the 36 values of its 2x2 HOG cells (L2-Hys, bf16 split) and LBP
+//    bins 0..19, warps 4-7 LBP bins 20..58 (the 2 x 2 count sums, L1-sqrt
+//    and its bf16 split from a 512-entry table). Every group of 32 rows
+//    covers 26 windows and the 6 blocks to their right, so the j terms of a
+//    window stay inside one warp of the epilogue;
 //  * one thread (lane 0 of the first epilogue warp, between its epilogue
 //    rows) issues the TMA (cp.async.bulk.tensor.3d) of cell rows into a ring
 //    of four slots (the 9 HOG planes, f32, and the 59 LBP count planes, u8,
-//    of the strip's 112 + 16 cells) and the 18 MMAs of every block row
-//    (K-major no-swizzle canonical operands in shared memory, D in one of
-//    two 128-column TMEM buffers), committed to the A-free and D-full
-//    barriers;
+//    of the strip's 112 + 16 cells) and the 18 MMAs of every block row (A in
+//    tensor memory, the template's B operand K-major no-swizzle canonical in
+//    shared memory, D in one of two 128-column TMEM buffers), committed to
+//    the A-free and D-full barriers;
 //  * 4 epilogue warps (warp e reads TMEM lanes 32 e .. 32 e + 31): lane l adds
 //    P[l + j][(i, j)] (a shuffle by j) to the running score of window row
 //    r - i, for all 105 positions, in the fixed order (i, j) = (0,0), (0,1),
 //    ..., so every score is b plus its terms in one order whatever the item
 //    cut; window row r - 14 is complete and stored.
-// The A operand and the accumulators are double buffered, so the producers
-// build row r + 1 and the epilogue reads row r - 1 while row r's MMAs run.
+// The A operand (two 96-column TMEM stages) and the accumulators are double
+// buffered, so the producers build row r + 1 and the epilogue reads row
+// r - 1 while row r's MMAs run.
 // Sparse path: a window is scored when every cell tile under it was
 // computed; block rows that no such window needs are skipped, other windows
 // get -inf. A wait that gives up (1 s) sets the error word and a CTA flag
@@ -65,7 +67,8 @@ constexpr int kSBO = kChunks * 128;   // bytes per 8-row group
 constexpr int kHogX = 112;            // HOG cells per staged row (TMA box width)
 constexpr int kLbpX = 128;            // LBP cells per staged row (box width, from a 16-cell boundary)
 constexpr int kSlots = 4;
-constexpr uint32_t kTmemCols = 256;   // two accumulator buffers of 128 columns
+constexpr uint32_t kTmemCols = 512;   // two accumulator buffers of 128 columns, two A stages of 96
+constexpr uint32_t kTmemA = 256;      // first A stage column (bf16 pairs: high parts 0..47, low 48..95)
 constexpr uint64_t kWaitNs = 1000000000ull;
 constexpr int kProducerBarrier = 1;   // named barrier of the producer warps
 static_assert(4 * kWinPerWarp == kTcStrip, "strip width");
@@ -80,7 +83,6 @@ struct Slot {
 static_assert(sizeof(Slot) % 128 == 0 && offsetof(Slot, lbp) % 128 == 0, "TMA destinations");
 
 struct TcSmem {
-    uint8_t a[2][16 * kSBO];          // A operands, double buffered
     uint8_t b[14 * kSBO];             // B operand: template high | low parts
     Slot slot[kSlots];                // staged cell rows
     uint32_t tab[512];                // sum of 4 cell counts -> bf16 high | low << 16 of sqrt(S / 256)
@@ -97,7 +99,7 @@ struct TcSmem {
     int item;
     volatile int failed;
 };
-static_assert(offsetof(TcSmem, slot) % 128 == 0 && offsetof(TcSmem, b) % 1024 == 0, "alignment");
+static_assert(offsetof(TcSmem, slot) % 128 == 0 && offsetof(TcSmem, b) == 0, "alignment");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -156,11 +158,12 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {  // K chunk stri
 }
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
                             ((uint32_t)(kM >> 4) << 24);  // f32 D, bf16 A and B, K-major, N, M
-__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, int acc) {
+// A from tensor memory (lane m = row m, K packed two bf16 per column)
+__device__ __forceinline__ void umma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, int acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+        "r"(a_tmem), "l"(b), "r"(kIdesc), "r"(acc)
         : "memory");
 }
 __device__ __forceinline__ void umma_commit(unsigned long long *bar) {
@@ -188,17 +191,49 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
     hi = h;
     lo = l;
 }
-__device__ __forceinline__ void st_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-    asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+// this thread's TMEM lane: 4, 8 or 16 consecutive 32-bit columns from taddr
+__device__ __forceinline__ void tst4(uint32_t t, const uint32_t *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(t), "r"(v[0]), "r"(v[1]),
+                 "r"(v[2]), "r"(v[3])
+                 : "memory");
 }
-__device__ __forceinline__ void st_v2(uint32_t addr, uint32_t a, uint32_t b) {
-    asm volatile("st.shared.v2.b32 [%0], {%1,%2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
+__device__ __forceinline__ void tst8(uint32_t t, const uint32_t *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(t), "r"(v[0]),
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tst16(uint32_t t, const uint32_t *v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(t),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
 }
 
-// HOG part of A row m (K 0..35): the 36 values of its cells (r, c),
-// (r, c+1), (r+1, c), (r+1, c+1) (slots s0 = row r, s1 = row r + 1), in the
-// template's order (cells TL, TR, BL, BR, 9 bins each), L2-Hys, bf16 split.
-__device__ __forceinline__ void build_hog(const Slot &s0, const Slot &s1, int c, float clip, uint32_t row) {
+// LBP features of A row m for bins [T0, T0 + 2 NP) (bin 59 is the zero pad):
+// the staged rows hold sums of horizontally adjacent cells, so cells
+// (r, c..c+1) + (r+1, c..c+1) are two loads; the table gives the bf16 split
+// of sqrt(S / 256), packed two bins per word.
+template <int T0, int NP>
+__device__ __forceinline__ void lbp_pairs(const Slot &s0, const Slot &s1, const uint32_t *tab, int c, uint32_t *hi,
+                                          uint32_t *lo) {
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int t = T0 + 2 * p;
+        const uint32_t e0 = tab[(uint32_t)s0.lbp[t][c] + (uint32_t)s1.lbp[t][c]];
+        const uint32_t e1 = t + 1 < kLbpBins ? tab[(uint32_t)s0.lbp[t + 1][c] + (uint32_t)s1.lbp[t + 1][c]] : 0u;
+        hi[p] = __byte_perm(e0, e1, 0x5410);
+        lo[p] = __byte_perm(e0, e1, 0x7632);
+    }
+}
+
+// Features 0..55 of A row m into its TMEM lane (columns a + f / 2 for the high
+// parts, a + 48 + f / 2 for the low parts): the 36 HOG values of its cells
+// (r, c), (r, c+1), (r+1, c), (r+1, c+1) (slots s0 = row r, s1 = row r + 1) in
+// the template's order (cells TL, TR, BL, BR, 9 bins each), L2-Hys, bf16
+// split; then LBP bins 0..19 (LBP column cl).
+__device__ __forceinline__ void build_hog(const Slot &s0, const Slot &s1, const uint32_t *tab, int c, int cl,
+                                          float clip, uint32_t a) {
     float v[36];
 #pragma unroll
     for (int b = 0; b < kHogBins; ++b) {
@@ -220,55 +255,30 @@ __device__ __forceinline__ void build_hog(const Slot &s0, const Slot &s1, int c,
         q[t & 3] = fmaf(v[t], v[t], q[t & 3]);
     }
     const float i2 = rsqrtf((q[0] + q[1]) + (q[2] + q[3]) + 1e-6f);
-    // 16-byte chunks of 8 features (the fifth holds 4 HOG values), stored as
-    // they are split
+    uint32_t hi[16], lo[16];
 #pragma unroll
-    for (int ch = 0; ch < 5; ++ch) {
-        uint32_t hi[4], lo[4];
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int t = 8 * ch + 2 * p;
-            if (t < 36) split2(v[t] * i2, v[t + 1] * i2, hi[p], lo[p]);
-        }
-        if (ch < 4) {
-            st_v4(row + ch * 128, hi[0], hi[1], hi[2], hi[3]);
-            st_v4(row + (12 + ch) * 128, lo[0], lo[1], lo[2], lo[3]);
-        } else {
-            st_v2(row + 4 * 128, hi[0], hi[1]);
-            st_v2(row + 16 * 128, lo[0], lo[1]);
-        }
-    }
+    for (int p = 0; p < 16; ++p) split2(v[2 * p] * i2, v[2 * p + 1] * i2, hi[p], lo[p]);
+    tst16(a, hi);        // features 0..31
+    tst16(a + 48, lo);
+    // features 32..55: HOG 32..35, LBP bins 0..19
+    split2(v[32] * i2, v[33] * i2, hi[0], lo[0]);
+    split2(v[34] * i2, v[35] * i2, hi[1], lo[1]);
+    lbp_pairs<0, 10>(s0, s1, tab, cl, hi + 2, lo + 2);
+    tst8(a + 16, hi);
+    tst4(a + 24, hi + 8);
+    tst8(a + 64, lo);
+    tst4(a + 72, lo + 8);
 }
 
-// LBP part of A row m (features 36..95), K chunks [CH0, CH1): the staged rows
-// hold sums of horizontally adjacent cells, so cells (r, c..c+1) +
-// (r+1, c..c+1) are two loads; the table gives the bf16 split of
-// sqrt(S / 256). Chunk 4 holds bins 0..3 in its upper half, chunks 5..11 bins
-// 4..58 and the zero feature 95; each chunk is stored as soon as it is packed.
-template <int CH0, int CH1>
-__device__ __forceinline__ void build_lbp(const Slot &s0, const Slot &s1, const uint32_t *tab, int c,
-                                          uint32_t row) {
-#pragma unroll
-    for (int ch = CH0; ch < CH1; ++ch) {
-        const int t0 = ch == 4 ? 0 : 8 * ch - 36;
-        const int np = ch == 4 ? 2 : 4;
-        uint32_t hi[4], lo[4];
-#pragma unroll
-        for (int p = 0; p < np; ++p) {
-            const int t = t0 + 2 * p;
-            const uint32_t e0 = tab[(uint32_t)s0.lbp[t][c] + (uint32_t)s1.lbp[t][c]];
-            const uint32_t e1 = t + 1 < kLbpBins ? tab[(uint32_t)s0.lbp[t + 1][c] + (uint32_t)s1.lbp[t + 1][c]] : 0u;
-            hi[p] = __byte_perm(e0, e1, 0x5410);
-            lo[p] = __byte_perm(e0, e1, 0x7632);
-        }
-        if (ch == 4) {
-            st_v2(row + 4 * 128 + 8, hi[0], hi[1]);
-            st_v2(row + 16 * 128 + 8, lo[0], lo[1]);
-        } else {
-            st_v4(row + ch * 128, hi[0], hi[1], hi[2], hi[3]);
-            st_v4(row + (12 + ch) * 128, lo[0], lo[1], lo[2], lo[3]);
-        }
-    }
+// Features 56..95 of A row m (LBP bins 20..58 and the zero pad): columns
+// a + 28 .. a + 47 and a + 76 .. a + 95.
+__device__ __forceinline__ void build_lbp(const Slot &s0, const Slot &s1, const uint32_t *tab, int cl, uint32_t a) {
+    uint32_t hi[20], lo[20];
+    lbp_pairs<20, 20>(s0, s1, tab, cl, hi, lo);
+    tst4(a + 28, hi);
+    tst16(a + 32, hi + 4);
+    tst4(a + 76, lo);
+    tst16(a + 80, lo + 4);
 }
 
 // In place, by the 256 producer threads: LBP count c[t][x] -> c[t][x] +
@@ -363,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = S.tmem;
-    const uint32_t a_base = smem_u32(S.a[0]), b_base = smem_u32(S.b);
+    const uint32_t b_base = smem_u32(S.b);
 
     // pipeline counters, advanced identically by every role
     uint32_t nrow = 0;      // block rows (A buffer, D buffer, their barrier phases)
@@ -465,15 +475,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                     producer_barrier();  // every producer warp, also after a failed wait
                     if (ok && k >= 2) ok = warp_wait(&S.aempty[k & 1], ((k >> 1) - 1) & 1u);
                     if (ok) {
-                        const uint32_t row = a_base + (k & 1) * (16 * kSBO) + (m >> 3) * kSBO + (m & 7) * 16;
+                        tc_fence_after();
+                        // this warp's TMEM lanes 32 (w % 4) .., A stage k % 2
+                        const uint32_t a = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + kTmemA + (k & 1) * 96;
                         const Slot &s0 = slot_of(u), &s1 = slot_of(u + 1);
-                        if (!is_lbp) {
-                            build_hog(s0, s1, c, clip, row);
-                            build_lbp<4, 7>(s0, s1, S.tab, cl, row);
-                        } else {
-                            build_lbp<7, 12>(s0, s1, S.tab, cl, row);
-                        }
-                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // A -> tensor cores
+                        if (!is_lbp)
+                            build_hog(s0, s1, S.tab, c, cl, clip, a);
+                        else
+                            build_lbp(s0, s1, S.tab, cl, a);
+                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                        tc_fence_before();
                     }
                     __syncwarp();
                     if (ok && lane == 0) {
@@ -519,16 +530,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (cok) {
                             tc_fence_after();
                             const uint32_t d = tmem + (k & 1) * 128;
-                            const uint32_t a0 = a_base + (k & 1) * (16 * kSBO);
+                            const uint32_t a0 = tmem + kTmemA + (k & 1) * 96;  // 8 columns per K step
 #pragma unroll
                             for (int s = 0; s < 6; ++s)
-                                umma(d, umma_desc(a0 + 256 * s), umma_desc(b_base + 256 * s), s > 0);
+                                umma_ts(d, a0 + 8 * s, umma_desc(b_base + 256 * s), s > 0);
 #pragma unroll
                             for (int s = 0; s < 6; ++s)
-                                umma(d, umma_desc(a0 + 12 * 128 + 256 * s), umma_desc(b_base + 256 * s), 1);
+                                umma_ts(d, a0 + 48 + 8 * s, umma_desc(b_base + 256 * s), 1);
 #pragma unroll
                             for (int s = 0; s < 6; ++s)
-                                umma(d, umma_desc(a0 + 256 * s), umma_desc(b_base + 12 * 128 + 256 * s), 1);
+                                umma_ts(d, a0 + 8 * s, umma_desc(b_base + 12 * 128 + 256 * s), 1);
                             umma_commit(&S.aempty[k & 1]);
                             umma_commit(&S.dfull[k & 1]);
                             committed = k + 1;
