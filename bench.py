@@ -36,6 +36,13 @@ WIDTH, HEIGHT = 1242, 375
 FACTOR = float(np.float32(1.05))
 CFG_ID = 2                      # scene recipe of the 1242x375 workload
 FLOP_PER_WINDOW = 2 * 15 * 7 * 95   # 9,975 FMA
+# Algorithmic operations per pixel of a level's cell grid (HOG + LBP cells, Algorithms 1, 4, 5):
+# LBP 18 (8 compares, 8 code shifts/ors, bin lookup, count), HOG 37 (gradient 2, magnitude 4,
+# orientation 1 atan2 + 2, orientation interpolation 4, spatial weights 4, 8 weighted votes 16,
+# vote weights 4).
+OPS_PER_CELL_PIXEL = 55
+# Tensor-core K4 MMA per block row of a strip: M 128 x N 112 x K 288 (bf16 high/low split)
+TC_FLOP_PER_UNIT = 2 * 128 * 112 * 288
 PAPER_FPS_1242x375 = 20.0       # Tegra X1, HOGLBP-SVM (context: another machine)
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "frames/s (1242x375, HOG+LBP+SVM+NMS)"
@@ -106,6 +113,25 @@ def make_frames(indices):
 
 def svm_flag(args, pd) -> int:
     return pd.PD_FLAG_SVM_FP32 if args.svm == "fp32" else 0
+
+
+def cells_per_frame() -> int:
+    from paper_1611_01642_gb300 import pd_pyramid
+    return sum((wk // 8) * (hk // 8) for wk, hk in pd_pyramid(WIDTH, HEIGHT, FACTOR))
+
+
+def tc_units_per_frame() -> int:
+    """Block rows the tensor-core K4 walks per frame: strips of 104 window columns, each cut into
+    pieces of at most 64 window rows, each piece also walking the 14 block rows below it."""
+    from paper_1611_01642_gb300 import pd_pyramid
+    n = 0
+    for wk, hk in pd_pyramid(WIDTH, HEIGHT, FACTOR):
+        rows, cols = hk // 8 - 15, wk // 8 - 7
+        if rows <= 0 or cols <= 0:
+            continue
+        pieces = -(-rows // 64)
+        n += -(-cols // 104) * (rows + 14 * pieces)
+    return n
 
 
 def windows_per_frame(upscale: int = 0) -> int:
@@ -250,10 +276,11 @@ def _file_hash(path: str) -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per K4 launch from the committed ncu summary, if the kernel is unchanged."""
-    path = os.path.join(ROOT, "profiles", "k_svm_1242x375_b64.txt")
-    src = os.path.join(ROOT, "paper_1611_01642_gb300", "csrc", "k_svm.cu")
+def recorded_traffic(profile: str, source: str):
+    """DRAM bytes per launch (scaled to the bench's 64-frame batch) from a committed ncu summary,
+    if the kernel's source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", profile)
+    src = os.path.join(ROOT, "paper_1611_01642_gb300", "csrc", source)
     if not os.path.exists(path):
         return None
     rec = {}
@@ -456,13 +483,41 @@ def run_gpu(args):
 
     peaks, peak_kind = measured_peaks()
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
-    fp32_peak = sm_count * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12  # TFLOP/s
-    achieved = B * wpf * FLOP_PER_WINDOW / (stage_step[2] / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": recorded_traffic(),
-                "kernel": "k_svm (block L2-Hys norm + window correlation, FP32 FMA)",
-                "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
-                              f"(max SM clock, {peak_kind})"}
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s (FMA = 2)
+    lane_peak = sm_count * 128 * sm_mhz * 1e6 / 1e12       # T lane-ops/s
+    # cells (K2 + K3): ALU bound; one op = one lane slot
+    cells_ops = B * cells_per_frame() * 64 * OPS_PER_CELL_PIXEL
+    cells_ach = cells_ops / (stage_step[1] / 1e3) / 1e12
+    roof_cells = {"bound": "alu", "achieved": cells_ach, "peak": lane_peak, "unit": "Tops/s",
+                  "frac": cells_ach / lane_peak,
+                  "traffic": recorded_traffic("k_cells_1242x375_b64.txt", "k_cells.cu"),
+                  "kernel": "k_cells (uniform LBP + soft-binned HOG cell histograms)",
+                  "peak_basis": f"{sm_count} SMs x 128 lanes x {sm_mhz} MHz, one op per lane slot "
+                                f"({OPS_PER_CELL_PIXEL} algorithmic ops per cell-grid pixel; max SM clock, "
+                                f"{peak_kind})"}
+    # window scores (K4)
+    k4_s = stage_step[2] / 1e3
+    if args.svm == "fp32":
+        k4_ach = B * wpf * FLOP_PER_WINDOW / k4_s / 1e12
+        roof_k4 = {"bound": "alu", "achieved": k4_ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                   "frac": k4_ach / fp32_peak, "traffic": None,
+                   "kernel": "k_svm (block L2-Hys norm + window correlation, FP32 FMA)",
+                   "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {sm_mhz} MHz ({peak_kind})"}
+    else:
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        k4_ach = B * wpf * FLOP_PER_WINDOW / k4_s / 1e12
+        executed = B * tc_units_per_frame() * TC_FLOP_PER_UNIT / k4_s / 1e12
+        roof_k4 = {"bound": "tensor", "achieved": k4_ach, "peak": bf16, "unit": "TFLOP/s",
+                   "frac": k4_ach / bf16, "executed_tflops": executed, "executed_frac": executed / bf16,
+                   "traffic": recorded_traffic("k_svm_tc_1242x375_b64.txt", "k_svm_tc.cu"),
+                   "kernel": "k_svm_tc (block norms + window scores as bf16-split tcgen05 GEMMs)",
+                   "peak_basis": f"bf16 dense, cuBLAS burst ({peak_kind}); achieved counts the "
+                                 f"definition's 19,950 flop per window, executed the MMAs issued "
+                                 f"(3 bf16 terms, padding, strip halo)"}
+    stage_names = ["k_resize", "k_cells", "k_svm_tc" if args.svm != "fp32" else "k_svm", "k_nms"]
+    dominant = stage_names[int(np.argmax(stage_step[:4]))]
+    roofline = roof_cells if dominant == "k_cells" else roof_k4 if dominant.startswith("k_svm") else roof_cells
 
     upscaled = None
     if rank == 0 and args.upscale_steps > 0:
@@ -492,6 +547,7 @@ def run_gpu(args):
                    "k4_tile_costs": [round(c, 4) for c in tile_costs],
                    "parallelism": f"{world} independent replicas"},
         "roofline": roofline,
+        "roofline_k4": roof_k4,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
