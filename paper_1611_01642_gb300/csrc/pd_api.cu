@@ -943,7 +943,7 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
                                   max_pool_tiles(p), h->d_err));
             PD_CUDA(h, cudaMemsetAsync(h->c_flag, 0, p.c_items.size() * 4 + 4, q));
             PD_CUDA(h, launch_proposal_flags(q, dl, dptr<SvmItem>(h, o.s_items), (int)p.s_items.size(), h->logits,
-                                             h->tau, h->s_flag, h->c_flag));
+                                             h->tau, h->s_flag, h->c_flag, !(h->p.flags & PD_FLAG_SVM_FP32)));
             cf = h->c_flag;
             sf = h->s_flag;
         }

@@ -98,7 +98,8 @@ cudaError_t launch_cells(cudaStream_t s, const LevelDesc *d_levels, const uint8_
                          CellAtlas atlas, const CellItem *d_items, int n_items, const uint8_t *d_lbp_map,
                          const uint32_t *c_flag = nullptr);
 cudaError_t launch_proposal_flags(cudaStream_t s, const LevelDesc *d_levels, const SvmItem *d_items, int n_items,
-                                  const float *logits, float tau, uint32_t *s_flag, uint32_t *c_flag);
+                                  const float *logits, float tau, uint32_t *s_flag, uint32_t *c_flag,
+                                  bool per_window);
 cudaError_t launch_svm(cudaStream_t s, const CUtensorMap *hog_maps, const CUtensorMap *lbp_maps,
                        const LevelDesc *d_levels, const float *d_w, float bias, float clip,
                        float *scores, const SvmItem *d_items, int n_items, unsigned *d_err,
