@@ -171,58 +171,63 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
     const int n_rows = min(kTH, Hc - it.cy0);  // cell rows of this tile inside the level
 
     for (int band = 0; band <= n_rows; ++band) {
+        // band rows yb .. yb+7 (the staged region holds yb-1 .. yb+8, clamped to
+        // the level); rows outside the cell grid [0, gridH) are skipped
         const int yb = 8 * (it.cy0 + band) - 4;
-        const int y_begin = max(yb, 0);
-        const int y_end = min(yb + 8, gridH);
-        if (active && y_begin < y_end) {
+        if (active) {
             auto row = [&](int yy, int &l, int &m, int &r) {
                 const uint8_t *p = &S.pix[yy - py0][sc];
                 l = p[-1];
                 m = p[0];
                 r = p[1];
             };
-            int al, am, ar, bl, bm, br, cl, cm, cr;
-            row(y_begin - 1, al, am, ar);
-            row(y_begin, bl, bm, br);
-            for (int y = y_begin; y < y_end; ++y) {
+            int al, am, ar, bl, bm, br;
+            row(yb - 1, al, am, ar);
+            row(yb, bl, bm, br);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int y = yb + k;
+                int cl, cm, cr;
                 row(y + 1, cl, cm, cr);
-                // ---- HOG vote
-                const int gx = br - bl;
-                const int gy = cm - am;
-                const float m2 = (float)(gx * gx + gy * gy);
-                const float mag = m2 > 0.f ? m2 * rsqrtf(m2) : 0.f;
-                const float bpos = orientation_bins(gx, gy) - 0.5f;  // in [-0.5, 8.5]
-                const float bf = floorf(bpos);
-                const float o1 = bpos - bf, o0 = 1.f - o1;
-                int b0 = (int)bf;
-                int b1 = b0 + 1;
-                b0 = b0 < 0 ? b0 + kHogBins : b0;
-                b1 = b1 >= kHogBins ? b1 - kHogBins : b1;
-                b0 = clampi(b0, 0, kHogBins - 1);  // guards; no-ops for bpos in [-0.5, 8.5]
-                b1 = clampi(b1, 0, kHogBins - 1);
-                const int4 yv = S.yv[y - py0];
-                const float mo0 = mag * o0, mo1 = mag * o1;
-                if (yv.x >= 0) {
-                    const float w = __int_as_float(yv.z);
-                    float *R0 = &S.R[yv.x][0][rc];
-                    R0[b0 * kRPitch] += mo0 * w;
-                    R0[b1 * kRPitch] += mo1 * w;
-                }
-                if (yv.y >= 0) {
-                    const float w = __int_as_float(yv.w);
-                    float *R1 = &S.R[yv.y][0][rc];
-                    R1[b0 * kRPitch] += mo0 * w;
-                    R1[b1 * kRPitch] += mo1 * w;
-                }
-                // ---- LBP code and count (core pixels only)
-                const int cyl = (y >> 3) - it.cy0;
-                if (core_x && cyl >= 0 && cyl < kTH) {
-                    const int c = bm;
-                    const int code = (al >= c) | ((am >= c) << 1) | ((ar >= c) << 2) |
-                                     ((br >= c) << 3) | ((cr >= c) << 4) | ((cm >= c) << 5) |
-                                     ((cl >= c) << 6) | ((bl >= c) << 7);
-                    const int bin = S.map[code];
-                    atomicAdd(&S.cnt[cyl & 1][cxl][bin >> 1], 1u << ((bin & 1) << 4));
+                if (y >= 0 && y < gridH) {
+                    // ---- HOG vote
+                    const int gx = br - bl;
+                    const int gy = cm - am;
+                    const float m2 = (float)(gx * gx + gy * gy);
+                    const float mag = m2 > 0.f ? m2 * rsqrtf(m2) : 0.f;
+                    // bpos in [-0.5, 8.5): floor in [-1, 8], so b0 = -1 wraps to 8
+                    // and b1 = 9 to 0
+                    const float bpos = orientation_bins(gx, gy) - 0.5f;
+                    const float bf = floorf(bpos);
+                    const float o1 = bpos - bf, o0 = 1.f - o1;
+                    const int bi = (int)bf;
+                    const int b0 = bi < 0 ? kHogBins - 1 : bi;
+                    const int b1 = bi + 1 >= kHogBins ? 0 : bi + 1;
+                    const int4 yv = S.yv[y - py0];
+                    const float mo0 = mag * o0, mo1 = mag * o1;
+                    if (yv.x >= 0) {
+                        const float w = __int_as_float(yv.z);
+                        float *R0 = &S.R[yv.x][0][rc];
+                        R0[b0 * kRPitch] += mo0 * w;
+                        R0[b1 * kRPitch] += mo1 * w;
+                    }
+                    if (yv.y >= 0) {
+                        const float w = __int_as_float(yv.w);
+                        float *R1 = &S.R[yv.y][0][rc];
+                        R1[b0 * kRPitch] += mo0 * w;
+                        R1[b1 * kRPitch] += mo1 * w;
+                    }
+                    // ---- LBP code and count (core pixels only; the cell row is
+                    // band - 1 for k < 4, band for k >= 4)
+                    const int cyl = band - 1 + (k >= 4 ? 1 : 0);
+                    if (core_x && cyl >= 0 && cyl < kTH) {
+                        const int c = bm;
+                        const int code = (al >= c) | ((am >= c) << 1) | ((ar >= c) << 2) |
+                                         ((br >= c) << 3) | ((cr >= c) << 4) | ((cm >= c) << 5) |
+                                         ((cl >= c) << 6) | ((bl >= c) << 7);
+                        const int bin = S.map[code];
+                        atomicAdd(&S.cnt[cyl & 1][cxl][bin >> 1], 1u << ((bin & 1) << 4));
+                    }
                 }
                 al = bl; am = bm; ar = br;
                 bl = cl; bm = cm; br = cr;
