@@ -67,6 +67,8 @@ def parse_args(argv=None):
                     help="also compare plain and sparse on the 4K mix (16 x 3840x2160 + 48 x 1242x375)")
     ap.add_argument("--proposal-frames", type=int, default=16,
                     help="frames of the proposal comparison (16 is the workload; fewer for profiler captures)")
+    ap.add_argument("--other-k4-steps", type=int, default=10,
+                    help="timed steps of the same batch with the other window-score kernel (0: skip)")
     ap.add_argument("--upscale-steps", type=int, default=10,
                     help="timed steps of the same batch with 17 upsampled levels (40 levels per frame; 0: skip)")
     return ap.parse_args(argv)
@@ -153,13 +155,30 @@ def run_upscaled(args, pd, torch, frames, flush, tile_costs, fp32_peak):
                       upscale_levels=UPSCALE_LEVELS, max_candidates_per_frame=65536,
                       flags=pd.PD_FLAG_STAGE_TIMING | svm_flag(args, pd))
     pd.pd_set_tile_costs(det.h, tile_costs)
+    ms, st = time_detector(det, frames, flush, args.upscale_steps, pd, torch)
+    n_levels = len(det.levels(0))
+    det.close()
+    wpf = windows_per_frame(UPSCALE_LEVELS)
+    k4 = len(frames) * wpf * FLOP_PER_WINDOW / (st[2] / 1e3) / 1e12
+    return {"workload": f"{len(frames)} x {WIDTH}x{HEIGHT} u8 frames, pyramid factor 1.05 with "
+                        f"{UPSCALE_LEVELS} upsampled levels ({n_levels} levels), plain HOG+LBP+SVM+NMS "
+                        "(NMS candidate cap 65,536 per frame)",
+            "frames_per_s": len(frames) / (ms / 1e3), "ms_per_step": ms, "levels_per_frame": n_levels,
+            "windows_per_frame": wpf, "k4_algorithmic_tflops": k4,
+            "stage_ms_per_step": dict(zip(["pyramid", "cells", "norm_svm", "nms"], map(float, st[:4]))),
+            "steps": args.upscale_steps}
+
+
+def time_detector(det, frames, flush, steps, pd, torch, warmup: int = 3):
+    """Mean step time (CUDA events on the current stream, L2 flushed before every step) and mean
+    per-stage times of `steps` detects of `frames` after `warmup` untimed ones."""
     stream = torch.cuda.current_stream()
-    for _ in range(3):
+    for _ in range(warmup):
         flush.fill_(1)
         det.detect(frames)
         det.sync()
     tot, st = 0.0, np.zeros(5)
-    for i in range(args.upscale_steps):
+    for i in range(steps):
         flush.fill_(i & 255)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -170,18 +189,59 @@ def run_upscaled(args, pd, torch, frames, flush, tile_costs, fp32_peak):
             raise RuntimeError(pd.pd_last_error(det.h))
         tot += e0.elapsed_time(e1)
         st += np.array(pd.pd_stage_times(det.h))
-    n_levels = len(det.levels(0))
-    det.close()
-    ms, st = tot / args.upscale_steps, st / args.upscale_steps
-    wpf = windows_per_frame(UPSCALE_LEVELS)
-    k4 = len(frames) * wpf * FLOP_PER_WINDOW / (st[2] / 1e3) / 1e12
-    return {"workload": f"{len(frames)} x {WIDTH}x{HEIGHT} u8 frames, pyramid factor 1.05 with "
-                        f"{UPSCALE_LEVELS} upsampled levels ({n_levels} levels), plain HOG+LBP+SVM+NMS "
-                        "(NMS candidate cap 65,536 per frame)",
-            "frames_per_s": len(frames) / (ms / 1e3), "ms_per_step": ms, "levels_per_frame": n_levels,
-            "windows_per_frame": wpf, "k4_tflops": k4, "k4_frac_of_fp32_peak": k4 / fp32_peak,
-            "stage_ms_per_step": dict(zip(["pyramid", "cells", "norm_svm", "nms"], map(float, st[:4]))),
-            "steps": args.upscale_steps}
+    return tot / steps, st / steps
+
+
+def run_other_k4(args, pd, torch, frames, flush, w, b, fp32_peak, bf16_peak):
+    """The same batch with the other window-score kernel (FP32 CUDA cores when the main line runs
+    the tensor cores, and the reverse), so that one bench line carries both."""
+    from paper_1611_01642_gb300 import autotune
+    other = "fp32" if args.svm != "fp32" else "tc"
+    flags = pd.PD_FLAG_STAGE_TIMING | (pd.PD_FLAG_SVM_FP32 if other == "fp32" else 0)
+    det = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=len(frames), max_width=WIDTH, max_height=HEIGHT,
+                      flags=flags)
+    try:
+        costs = (autotune.apply(det, frames[:16], w, b, FACTOR)
+                 if other == "fp32" and not args.no_autotune else pd.pd_get_tile_costs(det.h))
+        ms, st = time_detector(det, frames, flush, args.other_k4_steps, pd, torch)
+    finally:
+        det.close()
+    k4 = len(frames) * windows_per_frame() * FLOP_PER_WINDOW / (st[2] / 1e3) / 1e12
+    peak = fp32_peak if other == "fp32" else bf16_peak
+    return {"kernel": "k_svm (FP32 CUDA cores, PD_FLAG_SVM_FP32)" if other == "fp32"
+                      else "k_svm_tc (tensor cores)",
+            "frames_per_s": len(frames) / (ms / 1e3), "ms_per_step": ms, "k4_ms": float(st[2]),
+            "k4_algorithmic_tflops": k4, "k4_frac_of_peak": k4 / peak,
+            "peak": peak, "tile_costs": [round(c, 4) for c in costs] if other == "fp32" else None,
+            "steps": args.other_k4_steps}
+
+
+def hbm_per_kernel(stage_ms, svm: str):
+    """Achieved HBM GB/s of each kernel of the step: the DRAM bytes of one launch recorded by ncu
+    (committed summary, scaled to the 64-frame batch; only for kernels whose source is unchanged
+    since the capture) over the kernel's CUDA-event time in this run."""
+    path = os.path.join(ROOT, "profiles", "dram_per_kernel_1242x375_b64.txt")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("@"):
+                k, v = line[1:].split("=", 1)
+                name, src, nbytes = v.split()
+                rec[k.strip()] = (name, src, float(nbytes))
+    peak = float(measured_peaks()[0].get("hbm_gbs", 6800.0))
+    out = {}
+    for kernel, t in zip(["k_resize", "k_cells", "k_svm_tc" if svm != "fp32" else "k_svm", "k_nms"], stage_ms):
+        if kernel not in rec:
+            continue
+        name, src_hash, nbytes = rec[kernel]
+        if _file_hash(os.path.join(ROOT, "paper_1611_01642_gb300", "csrc", name)) != src_hash:
+            out[kernel] = None
+            continue
+        gbs = nbytes / (t / 1e3) / 1e9
+        out[kernel] = {"dram_bytes": nbytes, "achieved_gbs": gbs, "frac_of_peak": gbs / peak}
+    return out
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -517,7 +577,16 @@ def run_gpu(args):
                                  f"(3 bf16 terms, padding, strip halo)"}
     stage_names = ["k_resize", "k_cells", "k_svm_tc" if args.svm != "fp32" else "k_svm", "k_nms"]
     dominant = stage_names[int(np.argmax(stage_step[:4]))]
+    hbm = hbm_per_kernel(stage_step[:4], args.svm)
+    for name, roof in (("k_cells", roof_cells), (stage_names[2], roof_k4)):
+        if roof["traffic"] is None and hbm and hbm.get(name):
+            roof["traffic"] = hbm[name]["dram_bytes"]
     roofline = roof_cells if dominant == "k_cells" else roof_k4 if dominant.startswith("k_svm") else roof_cells
+
+    other_k4 = None
+    if rank == 0 and args.other_k4_steps > 0:
+        other_k4 = run_other_k4(args, pd, torch, frames, flush, w, b, fp32_peak,
+                                float(peaks.get("bf16_tflops", 1900.0)))
 
     upscaled = None
     if rank == 0 and args.upscale_steps > 0:
@@ -548,6 +617,8 @@ def run_gpu(args):
                    "parallelism": f"{world} independent replicas"},
         "roofline": roofline,
         "roofline_k4": roof_k4,
+        "hbm_per_kernel": hbm,
+        "other_k4": other_k4,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
