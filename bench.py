@@ -67,6 +67,8 @@ def parse_args(argv=None):
                     help="also compare plain and sparse on the 4K mix (16 x 3840x2160 + 48 x 1242x375)")
     ap.add_argument("--proposal-frames", type=int, default=16,
                     help="frames of the proposal comparison (16 is the workload; fewer for profiler captures)")
+    ap.add_argument("--pipeline-steps", type=int, default=10,
+                    help="timed steps of the HOG-SVM and LBP-SVM pipelines on the same batch (0: skip)")
     ap.add_argument("--other-k4-steps", type=int, default=10,
                     help="timed steps of the same batch with the other window-score kernel (0: skip)")
     ap.add_argument("--upscale-steps", type=int, default=10,
@@ -214,6 +216,23 @@ def run_other_k4(args, pd, torch, frames, flush, w, b, fp32_peak, bf16_peak):
             "k4_algorithmic_tflops": k4, "k4_frac_of_peak": k4 / peak,
             "peak": peak, "tile_costs": [round(c, 4) for c in costs] if other == "fp32" else None,
             "steps": args.other_k4_steps}
+
+
+def run_pipelines(args, pd, torch, frames, flush, w, b):
+    """The paper's other two pipelines (Section 4.1) on the same batch: HOG-SVM and LBP-SVM (only
+    that feature's cells computed; windows scored with that feature's weights)."""
+    out = {}
+    for name, flag in (("hog_svm", pd.PD_FLAG_HOG_ONLY), ("lbp_svm", pd.PD_FLAG_LBP_ONLY)):
+        det = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=len(frames), max_width=WIDTH, max_height=HEIGHT,
+                          flags=pd.PD_FLAG_STAGE_TIMING | flag | svm_flag(args, pd))
+        try:
+            ms, st = time_detector(det, frames, flush, args.pipeline_steps, pd, torch)
+        finally:
+            det.close()
+        out[name] = {"frames_per_s": len(frames) / (ms / 1e3), "ms_per_step": ms,
+                     "stage_ms_per_step": dict(zip(["pyramid", "cells", "norm_svm", "nms"], map(float, st[:4])))}
+    out["steps"] = args.pipeline_steps
+    return out
 
 
 def hbm_per_kernel(stage_ms, svm: str):
@@ -588,6 +607,10 @@ def run_gpu(args):
         other_k4 = run_other_k4(args, pd, torch, frames, flush, w, b, fp32_peak,
                                 float(peaks.get("bf16_tflops", 1900.0)))
 
+    pipelines = None
+    if rank == 0 and args.pipeline_steps > 0:
+        pipelines = run_pipelines(args, pd, torch, frames, flush, w, b)
+
     upscaled = None
     if rank == 0 and args.upscale_steps > 0:
         upscaled = run_upscaled(args, pd, torch, frames, flush, tile_costs, fp32_peak)
@@ -619,6 +642,7 @@ def run_gpu(args):
         "roofline_k4": roof_k4,
         "hbm_per_kernel": hbm,
         "other_k4": other_k4,
+        "pipelines": pipelines,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,

@@ -63,6 +63,13 @@ extern "C" {
  * one kernel do not depend on how it tiles a level, and the sparse path
  * reproduces the dense path's scores of the same kernel bit for bit. */
 #define PD_FLAG_SVM_FP32 2
+/* The HOG-SVM and LBP-SVM pipelines of Section 4.1 (default: HOGLBP-SVM):
+ * only that feature's cell histograms are computed, and windows are scored
+ * with the template's weights of that feature (the others are taken as 0),
+ * so a score is b + sum over the 15 x 7 blocks of the 36 HOG (or 59 LBP)
+ * block features times their weights. At most one of the two. */
+#define PD_FLAG_HOG_ONLY 4
+#define PD_FLAG_LBP_ONLY 8
 
 typedef struct pd_handle pd_handle;
 

@@ -40,7 +40,9 @@
 // and LBP counts therefore live in rings of 2 cell rows, which keeps the CTA
 // at ~23 KB of shared memory (many CTAs per SM).
 // Outputs go to plane-major cell atlases: hog[b][row][cx] (f32),
-// lbp[bin][row][cx] (u8, counts <= 64).
+// lbp[bin][row][cx] (u8, counts <= 64). `feat` selects the features computed
+// (HOG, LBP or both: the HOG-SVM and LBP-SVM pipelines of Section 4.1 skip
+// the other one).
 #include "pd_internal.h"
 
 namespace pd {
@@ -95,12 +97,14 @@ __device__ __forceinline__ float orientation_bins(int gx, int gy) {
     return gx < 0 ? 9.0f - phi : phi;          // mirror into (90, 180)
 }
 
+template <int FEAT>
 __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict__ levels,
                                                     const uint8_t *__restrict__ pyr,
                                                     CellAtlas atlas,
                                                     const CellItem *__restrict__ items,
                                                     const uint8_t *__restrict__ lbp_map,
                                                     const uint32_t *__restrict__ c_flag) {
+    constexpr int feat = FEAT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CellSmem &S = *reinterpret_cast<CellSmem *>(smem_raw);
     if (c_flag && !c_flag[blockIdx.x]) return;  // sparse path: no kept window needs these cells
@@ -189,7 +193,7 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
                 const int y = yb + k;
                 int cl, cm, cr;
                 row(y + 1, cl, cm, cr);
-                if (y >= 0 && y < gridH) {
+                if (y >= 0 && y < gridH && (feat & kFeatHog)) {
                     // ---- HOG vote
                     const int gx = br - bl;
                     const int gy = cm - am;
@@ -217,6 +221,8 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
                         R1[b0 * kRPitch] += mo0 * w;
                         R1[b1 * kRPitch] += mo1 * w;
                     }
+                }
+                if (y >= 0 && y < gridH && (feat & kFeatLbp)) {
                     // ---- LBP code and count (core pixels only; the cell row is
                     // band - 1 for k < 4, band for k >= 4)
                     const int cyl = band - 1 + (k >= 4 ? 1 : 0);
@@ -241,7 +247,7 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
             const int64_t row = (int64_t)(L.cell_row + cy) * atlas.pitch;
             const float(*R)[kRPitch] = S.R[cyl & 1];
             // HOG: one thread per (bin, cell): own group with WB, next group with WA
-            for (int o = tid; o < kHogBins * kTW; o += kThreads) {
+            for (int o = tid; o < ((feat & kFeatHog) ? kHogBins * kTW : 0); o += kThreads) {
                 const int b = o / kTW, cxo = o - b * kTW;
                 const int cx = it.cx0 + cxo;
                 if (cx >= Wc) continue;
@@ -268,7 +274,7 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
                 atlas.hog[(int64_t)b * atlas.hog_plane + row + cx] = acc;
             }
             // LBP: one thread per counter word (two bins) of a cell
-            for (int o = tid; o < kLbpWords * kTW; o += kThreads) {
+            for (int o = tid; o < ((feat & kFeatLbp) ? kLbpWords * kTW : 0); o += kThreads) {
                 const int wd = o / kTW, cxo = o - wd * kTW;
                 const int cx = it.cx0 + cxo;
                 if (cx >= Wc) continue;
@@ -290,16 +296,22 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
 }  // namespace
 
 cudaError_t init_cells() {
-    return cudaFuncSetAttribute(k_cells, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(CellSmem));
+    for (auto fn : {k_cells<kFeatHog | kFeatLbp>, k_cells<kFeatHog>, k_cells<kFeatLbp>}) {
+        const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)sizeof(CellSmem));
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_cells(cudaStream_t s, const LevelDesc *d_levels, const uint8_t *pyr,
                          CellAtlas atlas, const CellItem *d_items, int n_items,
-                         const uint8_t *d_lbp_map, const uint32_t *c_flag) {
+                         const uint8_t *d_lbp_map, const uint32_t *c_flag, int feat) {
     if (n_items <= 0) return cudaSuccess;
     const int smem = (int)sizeof(CellSmem);
-    k_cells<<<n_items, kThreads, smem, s>>>(d_levels, pyr, atlas, d_items, d_lbp_map, c_flag);
+    auto fn = feat == kFeatHog ? k_cells<kFeatHog> : feat == kFeatLbp ? k_cells<kFeatLbp>
+                                                                        : k_cells<kFeatHog | kFeatLbp>;
+    fn<<<n_items, kThreads, smem, s>>>(d_levels, pyr, atlas, d_items, d_lbp_map, c_flag);
     return cudaGetLastError();
 }
 

@@ -45,6 +45,13 @@ const float kSparseTileCost[kSvmShapes] = {1.0f, 1e3f, 0.6f, 1e3f, 1e3f, 0.82f, 
 
 int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
+// Cell features a pipeline uses (Section 4.1: HOG-SVM, LBP-SVM or HOGLBP-SVM).
+int features_of(int32_t flags) {
+    if (flags & PD_FLAG_HOG_ONLY) return kFeatHog;
+    if (flags & PD_FLAG_LBP_ONLY) return kFeatLbp;
+    return kFeatHog | kFeatLbp;
+}
+
 struct Plan {
     std::vector<FrameDesc> frames;
     std::vector<LevelDesc> levels;
@@ -492,7 +499,8 @@ bool params_ok(const pd_params *p) {
            p->nms_iou >= 0.f && p->max_boxes_per_frame > 0 && p->max_boxes_per_frame <= 16384 &&
            p->max_candidates_per_frame > 0 &&
            p->max_candidates_per_frame <= 65536 && p->max_frames > 0 && p->max_width > 0 &&
-           p->max_height > 0;
+           p->max_height > 0 &&
+           (p->flags & (PD_FLAG_HOG_ONLY | PD_FLAG_LBP_ONLY)) != (PD_FLAG_HOG_ONLY | PD_FLAG_LBP_ONLY);
 }
 
 // Packs the plan into the pinned staging buffer and sends it to the device.
@@ -838,12 +846,17 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
         cudaEventRecord(h->graph_done, 0) != cudaSuccess)
         return bail(PD_ECUDA);
 
-    // template -> [t][i][8] (j padded), lbp map
+    // template -> [t][i][8] (j padded), lbp map; a HOG-only or LBP-only
+    // pipeline scores with the other features' weights at zero (its cells
+    // are not computed)
     std::vector<float> wt((size_t)kFeat * kWinBH * kWPad, 0.f);
+    const int feat = features_of(params->flags);
     for (int i = 0; i < kWinBH; ++i)
         for (int j = 0; j < kWinBW; ++j)
-            for (int t = 0; t < kFeat; ++t)
-                wt[((size_t)t * kWinBH + i) * kWPad + j] = svm_w[((size_t)i * kWinBW + j) * kFeat + t];
+            for (int t = 0; t < kFeat; ++t) {
+                const bool used = t < kHogDim ? (feat & kFeatHog) != 0 : (feat & kFeatLbp) != 0;
+                wt[((size_t)t * kWinBH + i) * kWPad + j] = used ? svm_w[((size_t)i * kWinBW + j) * kFeat + t] : 0.f;
+            }
     float tab[256];
     for (int v = 0; v < 256; ++v) tab[v] = bf16_round_host((double)v / 255.0 - 0.5);
     if (cudaMemcpy(h->in_tab, tab, sizeof tab, cudaMemcpyHostToDevice) != cudaSuccess) return bail(PD_ECUDA);
@@ -949,7 +962,7 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
         }
         if (timed) PD_CUDA(h, record(h->stage_ev[1], q));
         PD_CUDA(h, launch_cells(q, dl, h->d_pyr, h->atlas, dptr<CellItem>(h, o.c_items), (int)p.c_items.size(),
-                                h->d_lbp_map, cf));
+                                h->d_lbp_map, cf, features_of(h->p.flags)));
         if (timed) PD_CUDA(h, record(h->stage_ev[2], q));
         if (h->p.flags & PD_FLAG_SVM_FP32) {
             PD_CUDA(h, launch_svm(q, h->hog_map, h->lbp_map, dl, h->d_w, h->bias, h->p.l2hys_clip, h->d_scores,

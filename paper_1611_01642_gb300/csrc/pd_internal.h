@@ -94,9 +94,11 @@ cudaError_t init_nms();
 cudaError_t launch_resize(cudaStream_t s, const FrameDesc *d_frames, const LevelDesc *d_levels,
                           const int32_t *d_tabs, uint8_t *pyr, const ResizeItem *d_items,
                           int n_items);
+// feat: kFeatHog | kFeatLbp (the features the pipeline uses)
+constexpr int kFeatHog = 1, kFeatLbp = 2;
 cudaError_t launch_cells(cudaStream_t s, const LevelDesc *d_levels, const uint8_t *pyr,
                          CellAtlas atlas, const CellItem *d_items, int n_items, const uint8_t *d_lbp_map,
-                         const uint32_t *c_flag = nullptr);
+                         const uint32_t *c_flag = nullptr, int feat = kFeatHog | kFeatLbp);
 cudaError_t launch_proposal_flags(cudaStream_t s, const LevelDesc *d_levels, const SvmItem *d_items, int n_items,
                                   const float *logits, float tau, uint32_t *s_flag, uint32_t *c_flag,
                                   bool per_window);

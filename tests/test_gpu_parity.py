@@ -345,6 +345,41 @@ def test_detect_with_upscaled_levels_matches_oracle(template):
         d.close()
 
 
+@pytest.mark.parametrize("kernel", [0, pd.PD_FLAG_SVM_FP32])
+@pytest.mark.parametrize("pipeline", ["hog", "lbp"])
+def test_hog_only_and_lbp_only_pipelines_match_oracle(template, pipeline, kernel):
+    # HOG-SVM / LBP-SVM (Section 4.1): only that feature's cells are computed and the
+    # other features' weights count as zero, so the oracle is the full definition with
+    # those weights zeroed
+    from paper_1611_01642_gb300 import build as bld
+    bld.build()
+    w, b = template
+    W, H = 640, 480
+    img = synth.make_scene(W, H, 3, 61)
+    flag = pd.PD_FLAG_HOG_ONLY if pipeline == "hog" else pd.PD_FLAG_LBP_ONLY
+    wm = w.copy()
+    if pipeline == "hog":
+        wm[:, :, 36:] = 0.0
+    else:
+        wm[:, :, :36] = 0.0
+    d = pd.Detector(w, b, max_frames=1, max_width=W, max_height=H, pyr_factor=F12, flags=flag | kernel)
+    try:
+        d.detect([torch.from_numpy(img).cuda()])
+        assert d.sync() == pd.PD_OK
+        dims = [(lv["width"], lv["height"]) for lv in d.levels(0)]
+        assert dims == oracle.pyramid(W, H, F12)
+        ref = oracle.detect(img, wm, b, F12)
+        feats = []
+        for k, ((wk, hk), g) in enumerate(zip(dims, d.score_maps(0))):
+            L = oracle.resize(img, wk, hk)
+            _, _, feat, sc = oracle.level_all(L, wm, b)
+            feats.append(feat)
+            _check_scores(g.cpu().numpy(), feat, wm, b, sc, f"{pipeline} level {k}")
+        _check_boxes(d.boxes(0), ref["scores"], feats, dims, wm, b, W, H)
+    finally:
+        d.close()
+
+
 def test_batched_equals_single_frames(template):
     from paper_1611_01642_gb300 import build as bld
     bld.build()
