@@ -515,12 +515,52 @@ def run_gpu(args):
         stage_ms += np.array(pd.pd_stage_times(det.h))
         launches += pd.pd_last_launch_count(det.h)
     torch.cuda.synchronize()
+    serial_ms = reduce_max(total_ms, world, device="cuda")
+    stage_step = stage_ms / args.steps
+
+    # Pipelined: two handles alternate on two streams, so that step i+1's first
+    # kernels run on the SMs that step i's last ones (NMS: one CTA per frame)
+    # leave idle. K steps in all, timed from one event before the first to the
+    # later of the two streams' events after the last; a handle is reused only
+    # after its previous step has been synced (its arena holds the results).
+    det_b = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=B, max_width=WIDTH, max_height=HEIGHT,
+                        flags=pd.PD_FLAG_STAGE_TIMING | svm_flag(args, pd))
+    pd.pd_set_tile_costs(det_b.h, tile_costs)
+    streams = [stream, torch.cuda.Stream()]
+    pipe = [det, det_b]
+    for _ in range(max(args.warmup, 0)):
+        for d, s_ in zip(pipe, streams):
+            d.detect(frames, stream=s_)
+        for d in pipe:
+            d.sync()
+    barrier(world)
+    torch.cuda.synchronize()
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_start.record(streams[0])
+    streams[1].wait_event(e_start)
+    launches = 0
+    for i in range(args.steps):
+        d, s_ = pipe[i & 1], streams[i & 1]
+        if i >= 2 and d.sync() != pd.PD_OK:
+            raise RuntimeError(f"pd_sync: {pd.pd_last_error(d.h)}")
+        with torch.cuda.stream(s_):
+            flush.fill_(i & 255)
+        d.detect(frames, stream=s_)
+        launches += pd.pd_last_launch_count(d.h)
+    e_end = [torch.cuda.Event(enable_timing=True) for _ in streams]
+    for e, s_ in zip(e_end, streams):
+        e.record(s_)
+    for d in pipe:
+        if d.sync() != pd.PD_OK:
+            raise RuntimeError(f"pd_sync: {pd.pd_last_error(d.h)}")
+    torch.cuda.synchronize()
     barrier(world)
     clocks = sampler.stop()
-    total_ms = reduce_max(total_ms, world, device="cuda")
+    pipe_ms = max(e_start.elapsed_time(e) for e in e_end)
+    total_ms = reduce_max(pipe_ms, world, device="cuda")
+    det_b.close()
     value = world * B * args.steps / (total_ms / 1e3)
     ms_step = total_ms / args.steps
-    stage_step = stage_ms / args.steps
 
     # end to end through the public API: host frames in, host boxes out. Two
     # handles alternate so that step i's results are read on the host while
@@ -530,7 +570,7 @@ def run_gpu(args):
                        flags=svm_flag(args, pd))
     pd.pd_set_tile_costs(det2.h, tile_costs)
     for _ in range(2):
-        det2.detect_host(pinned)
+        det2.detect_host(pinned, stream=streams[1])
         det2.sync()
     dets = [det, det2]
     barrier(world)
@@ -547,7 +587,7 @@ def run_gpu(args):
     pending = None
     for i in range(args.steps):
         d = dets[i & 1]
-        d.detect_host(pinned)
+        d.detect_host(pinned, stream=streams[i & 1])
         if pending is not None:
             d2h += finish(pending)
         pending = d
@@ -634,6 +674,8 @@ def run_gpu(args):
         "vs_baseline": value / PAPER_FPS_1242x375, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{WIDTH}x{HEIGHT} u8 frames, pyramid factor 1.05 (23 levels), "
                                "plain HOG+LBP+SVM+NMS",
+                   "timing": "K steps on two detector handles alternating on two streams (step i+1 may "
+                             "overlap step i); serial: the same K steps on one handle, each timed alone",
                    "frames_per_step": B * world, "frames_per_gpu": B, "windows_per_frame": wpf,
                    "l2": "flushed (256 MB write) before every timed step",
                    "k4_tile_costs": [round(c, 4) for c in tile_costs],
@@ -647,6 +689,7 @@ def run_gpu(args):
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
+        "serial": {"value": world * B * args.steps / (serial_ms / 1e3), "ms_per_step": serial_ms / args.steps},
         "stage_ms_per_step": {"pyramid": stage_step[0], "cells": stage_step[1], "norm_svm": stage_step[2],
                               "nms": stage_step[3]},
         "upscaled_40_levels": upscaled,
