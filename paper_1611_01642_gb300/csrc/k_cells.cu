@@ -56,6 +56,7 @@ constexpr int kPixCols = kCols + 2;   // + gradient / LBP halo
 constexpr int kPixRows = 8 * kTH + 10;
 constexpr int kRing = 2;              // open cell rows
 constexpr int kRPitch = kCols;                 // bin stride: a multiple of 32 banks
+static_assert(kCols == kThreads, "one pixel column (and its vote slots) per thread");
 constexpr int kLbpWords = (kLbpBins + 1) / 2;  // two 16-bit counters per word
 
 struct CellSmem {
@@ -83,18 +84,16 @@ __device__ __forceinline__ float atan_bins01(float z) {
     return p * z * 2.8647889756541160f;  // 9/pi
 }
 
-// Unsigned orientation of (gx, gy) in bin units: theta_degrees / 20, in [0, 9).
+// Unsigned orientation of (gx, gy) in bin units: theta_degrees / 20, in
+// [0, 9] (9 only for theta = 180 degrees, the same orientation as 0: both
+// give the same two votes below).
 __device__ __forceinline__ float orientation_bins(int gx, int gy) {
-    if (gy < 0 || (gy == 0 && gx < 0)) {
-        gx = -gx;
-        gy = -gy;
-    }
-    const float ax = (float)abs(gx), ay = (float)gy;  // ay >= 0
-    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const int ax = abs(gx), ay = abs(gy);
+    const float mx = (float)max(ax, ay), mn = (float)min(ax, ay);
     const float z = mx > 0.f ? __fdividef(mn, mx) : 0.f;
-    float phi = atan_bins01(z);                // angle to the nearer axis
+    float phi = atan_bins01(z);                // angle of (|gx|, |gy|) to the nearer axis
     if (ay > ax) phi = 4.5f - phi;             // 90 degrees - phi
-    return gx < 0 ? 9.0f - phi : phi;          // mirror into (90, 180)
+    return (gx ^ gy) < 0 ? 9.0f - phi : phi;   // opposite signs: mirror into (90, 180)
 }
 
 template <int FEAT>
@@ -199,8 +198,8 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
                     const int gy = cm - am;
                     const float m2 = (float)(gx * gx + gy * gy);
                     const float mag = m2 > 0.f ? m2 * rsqrtf(m2) : 0.f;
-                    // bpos in [-0.5, 8.5): floor in [-1, 8], so b0 = -1 wraps to 8
-                    // and b1 = 9 to 0
+                    // bpos in [-0.5, 8.5]: floor in [-1, 8], so b0 = -1 wraps to 8
+                    // and b1 = 9 to 0 (bpos -0.5 and 8.5 give the same votes)
                     const float bpos = orientation_bins(gx, gy) - 0.5f;
                     const float bf = floorf(bpos);
                     const float o1 = bpos - bf, o0 = 1.f - o1;
@@ -277,18 +276,18 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
             for (int o = tid; o < ((feat & kFeatLbp) ? kLbpWords * kTW : 0); o += kThreads) {
                 const int wd = o / kTW, cxo = o - wd * kTW;
                 const int cx = it.cx0 + cxo;
-                if (cx >= Wc) continue;
                 const uint32_t v = S.cnt[cyl & 1][cxo][wd];
+                S.cnt[cyl & 1][cxo][wd] = 0u;  // recycled for cell row cyl + 2
+                if (cx >= Wc) continue;
                 atlas.lbp[(int64_t)(2 * wd) * atlas.lbp_plane + row + cx] = (uint8_t)(v & 0xffffu);
                 if (2 * wd + 1 < kLbpBins)
                     atlas.lbp[(int64_t)(2 * wd + 1) * atlas.lbp_plane + row + cx] = (uint8_t)(v >> 16);
             }
             __syncthreads();
-            // recycle the slots of cell row cyl for cell row cyl + 2
-            float4 *R4 = reinterpret_cast<float4 *>(&S.R[cyl & 1][0][0]);
-            for (int i = tid; i < kHogBins * kRPitch / 4; i += kThreads) R4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int i = tid; i < kTW * kLbpWords; i += kThreads) (&S.cnt[cyl & 1][0][0])[i] = 0u;
-            __syncthreads();
+            // recycle the HOG slots of cell row cyl for cell row cyl + 2: only
+            // this thread votes into its column, so it clears it itself
+#pragma unroll
+            for (int b = 0; b < kHogBins; ++b) S.R[cyl & 1][b][tid] = 0.f;
         }
     }
 }
