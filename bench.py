@@ -67,6 +67,8 @@ def parse_args(argv=None):
                     help="also compare plain and sparse on the 4K mix (16 x 3840x2160 + 48 x 1242x375)")
     ap.add_argument("--proposal-frames", type=int, default=16,
                     help="frames of the proposal comparison (16 is the workload; fewer for profiler captures)")
+    ap.add_argument("--scheme-reps", type=int, default=5,
+                    help="timed calls per kernel scheme and size in the px/ns sweep (0: skip the sweep)")
     ap.add_argument("--pipeline-steps", type=int, default=10,
                     help="timed steps of the HOG-SVM and LBP-SVM pipelines on the same batch (0: skip)")
     ap.add_argument("--other-k4-steps", type=int, default=10,
@@ -233,6 +235,61 @@ def run_pipelines(args, pd, torch, frames, flush, w, b):
                      "stage_ms_per_step": dict(zip(["pyramid", "cells", "norm_svm", "nms"], map(float, st[:4])))}
     out["steps"] = args.pipeline_steps
     return out
+
+
+SCHEME_SIZES = [(320, 240), (640, 480), (1280, 720), (1920, 1080), (3840, 2160)]
+
+
+def run_schemes(args, pd, torch, w, b):
+    """px/ns of the paper's kernel schemes and of the fused kernels on single levels of growing size
+    (Section 5.3's per-algorithm comparison): cells (LBP / HOG) from a level image, window scores
+    from cell planes. Each figure: the median of `--scheme-reps` calls timed with CUDA events."""
+    import synth
+    stream = torch.cuda.current_stream()
+    det = pd.Detector(w, b, max_frames=1, max_width=SCHEME_SIZES[-1][0], max_height=SCHEME_SIZES[-1][1],
+                      flags=svm_flag(args, pd))
+
+    def timed(fn):
+        fn()
+        ms = []
+        for _ in range(args.scheme_reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms))
+
+    names = ["lbp_naive", "lbp_scalable", "hog_global", "hog_local", "hog_shared", "cells_fused",
+             "svm_naive", "svm_warp", "svm_fused"]
+    out = {n: [] for n in names}
+    try:
+        for W, H in SCHEME_SIZES:
+            L = torch.from_numpy(synth.random_image(W, H, W + H, smooth=True)).cuda()
+            Hc, Wc = H // 8, W // 8
+            cp = max(16, -(-Wc // 16) * 16)
+            plane = Hc * cp
+            hog = torch.zeros((9 * plane,), dtype=torch.float32, device="cuda")
+            lbp = torch.zeros((59 * plane,), dtype=torch.uint8, device="cuda")
+            scores = torch.zeros((max((Hc - 15) * (Wc - 7), 1),), dtype=torch.float32, device="cuda")
+            px = W * H
+            for n, sch in (("lbp_naive", pd.PD_SCHEME_LBP_NAIVE), ("lbp_scalable", pd.PD_SCHEME_LBP_SCALABLE)):
+                out[n].append(px / (timed(lambda: pd.pd_scheme_cells(det.h, sch, L, None, 0, lbp, plane, cp)) * 1e6))
+            for n, sch in (("hog_global", pd.PD_SCHEME_HOG_GLOBAL), ("hog_local", pd.PD_SCHEME_HOG_LOCAL),
+                           ("hog_shared", pd.PD_SCHEME_HOG_SHARED)):
+                out[n].append(px / (timed(lambda: pd.pd_scheme_cells(det.h, sch, L, hog, plane, None, 0, cp)) * 1e6))
+            out["cells_fused"].append(
+                px / (timed(lambda: pd.pd_cell_features(det.h, L, hog, plane, lbp, plane, cp)) * 1e6))
+            for n, sch in (("svm_naive", pd.PD_SCHEME_SVM_NAIVE), ("svm_warp", pd.PD_SCHEME_SVM_WARP)):
+                out[n].append(px / (timed(lambda: pd.pd_scheme_window_scores(
+                    det.h, sch, hog, plane, lbp, plane, cp, Wc, Hc, scores)) * 1e6))
+            out["svm_fused"].append(px / (timed(lambda: pd.pd_window_scores(
+                det.h, hog, plane, lbp, plane, cp, Wc, Hc, scores)) * 1e6))
+    finally:
+        det.close()
+    return {"unit": "px/ns", "sizes": [f"{W}x{H}" for W, H in SCHEME_SIZES], "reps": args.scheme_reps,
+            "note": "cells_fused computes LBP and HOG together; svm_fused is the K4 the line runs", **out}
 
 
 def hbm_per_kernel(stage_ms, svm: str):
@@ -647,6 +704,10 @@ def run_gpu(args):
         other_k4 = run_other_k4(args, pd, torch, frames, flush, w, b, fp32_peak,
                                 float(peaks.get("bf16_tflops", 1900.0)))
 
+    schemes = None
+    if rank == 0 and args.scheme_reps > 0:
+        schemes = run_schemes(args, pd, torch, w, b)
+
     pipelines = None
     if rank == 0 and args.pipeline_steps > 0:
         pipelines = run_pipelines(args, pd, torch, frames, flush, w, b)
@@ -685,6 +746,7 @@ def run_gpu(args):
         "hbm_per_kernel": hbm,
         "other_k4": other_k4,
         "pipelines": pipelines,
+        "schemes": schemes,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,

@@ -353,6 +353,43 @@ int pd_nms_noalloc(void *stream, const float *d_scores, int n_levels, const int3
                    const int32_t *cols, const int32_t *Wk, const int32_t *Hk, int W, int H, float threshold,
                    float nms_iou, int max_candidates, pd_box *d_boxes, int max_boxes, int32_t *d_counts);
 
+/* ---------------------------------------------------------------------------
+ * The paper's own kernel schemes (Section 4.2-4.4 and its per-algorithm
+ * results, Section 5.3), re-expressed on this GPU for comparison with the
+ * fused kernels above. They compute the same cell histograms and window
+ * scores (same readings, same parity bars), with the paper's work
+ * decompositions:
+ *   PD_SCHEME_LBP_NAIVE     LBP code stencil (one thread per pixel), then one
+ *                           thread per cell histogram (Map pattern);
+ *   PD_SCHEME_LBP_SCALABLE  LBP code stencil, then one thread per pixel adding
+ *                           to its cell histogram with atomics (Scatter);
+ *   PD_SCHEME_HOG_GLOBAL / _LOCAL / _SHARED
+ *                           gradient stencil (magnitude and orientation per
+ *                           pixel), then one thread per cell histogram
+ *                           (large-grain) accumulating its votes in global
+ *                           memory, in a local array, or in shared memory;
+ *   PD_SCHEME_SVM_NAIVE     block features materialised (one thread per
+ *                           block), then one thread per window dot product;
+ *   PD_SCHEME_SVM_WARP      the same features, one warp per window (lanes
+ *                           split the products, shuffle reduction).
+ * pd_scheme_cells writes the LBP planes (LBP schemes) or the HOG planes (HOG
+ * schemes) in the layout of pd_cell_features; pd_scheme_window_scores takes
+ * and returns what pd_window_scores does. Both allocate a scratch buffer on
+ * first use (cudaMalloc; grown when a larger level comes, freed by
+ * pd_destroy). Errors: PD_EINVAL (bad argument or scheme), PD_ENOMEM, PD_ECUDA. */
+#define PD_SCHEME_LBP_NAIVE 1
+#define PD_SCHEME_LBP_SCALABLE 2
+#define PD_SCHEME_HOG_GLOBAL 3
+#define PD_SCHEME_HOG_LOCAL 4
+#define PD_SCHEME_HOG_SHARED 5
+#define PD_SCHEME_SVM_NAIVE 6
+#define PD_SCHEME_SVM_WARP 7
+int pd_scheme_cells(pd_handle *h, void *stream, int scheme, const uint8_t *d_level, int Wk, int Hk, int pitch,
+                    float *d_hog, int64_t hog_plane, uint8_t *d_lbp, int64_t lbp_plane, int cell_pitch);
+int pd_scheme_window_scores(pd_handle *h, void *stream, int scheme, const float *d_hog, int64_t hog_plane,
+                            const uint8_t *d_lbp, int64_t lbp_plane, int cell_pitch, int cells_x, int cells_y,
+                            float *d_scores);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,7 +39,8 @@ EXPORTED = ["pd_params_default", "pd_pyramid", "pd_create", "pd_destroy", "pd_la
             "pd_detect", "pd_detect_host", "pd_sync", "pd_frame_candidates", "pd_frame_levels", "pd_scores", "pd_boxes",
             "pd_last_launch_count", "pd_stage_times", "pd_set_tile_costs", "pd_get_tile_costs", "pd_resize_levels", "pd_cell_features", "pd_window_scores",
             "pd_nms_maps", "pd_nms_noalloc", "pd_cnn_set_params", "pd_cnn_get_params", "pd_cnn_forward",
-            "pd_cnn_train_step", "pd_cnn_train_loss", "pd_set_proposal", "pd_logits", "pd_pyramid_ex"]
+            "pd_cnn_train_step", "pd_cnn_train_loss", "pd_set_proposal", "pd_logits", "pd_pyramid_ex",
+            "pd_scheme_cells", "pd_scheme_window_scores"]
 
 
 class pd_params(ctypes.Structure):
@@ -112,6 +113,8 @@ def load(path: str | None = None):
         "pd_resize_levels": ([P, P, P, i, i, i, i, P, P, P, P, P], i),
         "pd_cell_features": ([P, P, P, i, i, i, P, i64, P, i64, i], i),
         "pd_window_scores": ([P, P, P, i64, P, i64, i, i, i, P], i),
+        "pd_scheme_cells": ([P, P, i, P, i, i, i, P, i64, P, i64, i], i),
+        "pd_scheme_window_scores": ([P, P, i, P, i64, P, i64, i, i, i, P], i),
         "pd_nms_maps": ([P, P, P, i, P, P, P, P, i, i, P, i, P], i),
         "pd_nms_noalloc": ([P, P, i, P, P, P, P, i, i, f, f, i, P, i, P], i),
         "pd_cnn_set_params": ([P, P, i], i),
@@ -303,6 +306,25 @@ def pd_window_scores(h, hog, hog_plane: int, lbp, lbp_plane: int, cell_pitch: in
                      cells_y: int, scores, stream=None) -> None:
     _check(load().pd_window_scores(h, _stream(stream), _ptr(hog), hog_plane, _ptr(lbp), lbp_plane,
                                    cell_pitch, cells_x, cells_y, _ptr(scores)), h)
+
+
+# The paper's kernel schemes (comparison with the fused kernels; see include/pd.h).
+PD_SCHEME_LBP_NAIVE, PD_SCHEME_LBP_SCALABLE = 1, 2
+PD_SCHEME_HOG_GLOBAL, PD_SCHEME_HOG_LOCAL, PD_SCHEME_HOG_SHARED = 3, 4, 5
+PD_SCHEME_SVM_NAIVE, PD_SCHEME_SVM_WARP = 6, 7
+
+
+def pd_scheme_cells(h, scheme: int, level, hog, hog_plane: int, lbp, lbp_plane: int, cell_pitch: int,
+                    stream=None) -> None:
+    _check(load().pd_scheme_cells(h, _stream(stream), scheme, _ptr(level), level.shape[1], level.shape[0],
+                                  level.stride(0), _ptr(hog) if hog is not None else None, hog_plane,
+                                  _ptr(lbp) if lbp is not None else None, lbp_plane, cell_pitch), h)
+
+
+def pd_scheme_window_scores(h, scheme: int, hog, hog_plane: int, lbp, lbp_plane: int, cell_pitch: int,
+                            cells_x: int, cells_y: int, scores, stream=None) -> None:
+    _check(load().pd_scheme_window_scores(h, _stream(stream), scheme, _ptr(hog), hog_plane, _ptr(lbp), lbp_plane,
+                                          cell_pitch, cells_x, cells_y, _ptr(scores)), h)
 
 
 def pd_nms_maps(h, scores, rows, cols, level_dims, W: int, H: int, boxes, max_boxes: int, counts,

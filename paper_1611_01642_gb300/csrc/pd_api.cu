@@ -271,6 +271,8 @@ struct pd_handle {
     int adam_t = 0;
     // training workspace (allocated on first use, grown with the batch)
     unsigned char *train_ws = nullptr;
+    unsigned char *scheme_ws = nullptr;  // scratch of the paper's kernel schemes (grown on demand)
+    size_t scheme_ws_bytes = 0;
     size_t train_ws_bytes = 0;
     int train_levels = 0;
     float *train_loss_ptr = nullptr;
@@ -691,6 +693,7 @@ void pd_destroy(pd_handle *h) {
     if (h->desc_done) cudaEventDestroy(h->desc_done);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->train_ws) cudaFree(h->train_ws);
+    if (h->scheme_ws) cudaFree(h->scheme_ws);
     if (h->graph_done) cudaEventDestroy(h->graph_done);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (auto &e : h->stage_ev)
@@ -1467,6 +1470,55 @@ int pd_nms_maps(pd_handle *h, void *stream, const float *d_scores, int n_levels,
     PD_CUDA(h, launch_nms(s, dptr<FrameDesc>(h, o.frames), dptr<LevelDesc>(h, o.levels), 1, d_scores,
                           h->p.threshold, h->p.nms_iou, h->d_nms_scratch, h->p.max_candidates_per_frame,
                           d_boxes, max_boxes, d_counts));
+    return PD_OK;
+}
+
+namespace {
+// Scratch of the kernel-scheme entries, grown on demand (the stream is
+// synchronised first: earlier work on it may still use the old buffer).
+int scheme_scratch(pd_handle *h, cudaStream_t s, size_t need) {
+    if (need <= h->scheme_ws_bytes) return PD_OK;
+    PD_CUDA(h, cudaStreamSynchronize(s));
+    if (h->scheme_ws) cudaFree(h->scheme_ws);
+    h->scheme_ws = nullptr;
+    h->scheme_ws_bytes = 0;
+    if (cudaMalloc(&h->scheme_ws, need) != cudaSuccess) return fail(h, PD_ENOMEM, "scheme scratch");
+    h->scheme_ws_bytes = need;
+    return PD_OK;
+}
+}  // namespace
+
+int pd_scheme_cells(pd_handle *h, void *stream, int scheme, const uint8_t *d_level, int Wk, int Hk, int pitch,
+                    float *d_hog, int64_t hog_plane, uint8_t *d_lbp, int64_t lbp_plane, int cell_pitch) {
+    if (!h) return PD_EINVAL;
+    const int Wc = Wk / 8, Hc = Hk / 8;
+    const bool lbp_s = scheme == PD_SCHEME_LBP_NAIVE || scheme == PD_SCHEME_LBP_SCALABLE;
+    const bool hog_s = scheme == PD_SCHEME_HOG_GLOBAL || scheme == PD_SCHEME_HOG_LOCAL || scheme == PD_SCHEME_HOG_SHARED;
+    if (!(lbp_s || hog_s) || !d_level || Wk < 1 || Hk < 1 || pitch < Wk || cell_pitch < Wc ||
+        (lbp_s && (!d_lbp || lbp_plane < (int64_t)Hc * cell_pitch)) ||
+        (hog_s && (!d_hog || hog_plane < (int64_t)Hc * cell_pitch)))
+        return fail(h, PD_EINVAL, "pd_scheme_cells: bad argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int r = scheme_scratch(h, s, scheme_cells_scratch(Wk, Hk));
+    if (r != PD_OK) return r;
+    PD_CUDA(h, launch_scheme_cells(s, scheme, d_level, Wk, Hk, pitch, d_hog, hog_plane, d_lbp, lbp_plane,
+                                   cell_pitch, h->d_lbp_map, h->scheme_ws));
+    return PD_OK;
+}
+
+int pd_scheme_window_scores(pd_handle *h, void *stream, int scheme, const float *d_hog, int64_t hog_plane,
+                            const uint8_t *d_lbp, int64_t lbp_plane, int cell_pitch, int cells_x, int cells_y,
+                            float *d_scores) {
+    if (!h) return PD_EINVAL;
+    if ((scheme != PD_SCHEME_SVM_NAIVE && scheme != PD_SCHEME_SVM_WARP) || !d_hog || !d_lbp || !d_scores ||
+        cells_x < 0 || cells_y < 0 || cell_pitch < cells_x || hog_plane < (int64_t)cells_y * cell_pitch ||
+        lbp_plane < (int64_t)cells_y * cell_pitch)
+        return fail(h, PD_EINVAL, "pd_scheme_window_scores: bad argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int r = scheme_scratch(h, s, scheme_scores_scratch(cells_x, cells_y));
+    if (r != PD_OK) return r;
+    PD_CUDA(h, launch_scheme_scores(s, scheme, d_hog, hog_plane, d_lbp, lbp_plane, cell_pitch, cells_x, cells_y,
+                                    h->d_w, h->bias, h->p.l2hys_clip, d_scores, h->scheme_ws));
     return PD_OK;
 }
 

@@ -129,6 +129,16 @@ cudaError_t launch_nms(cudaStream_t s, const FrameDesc *d_frames, const LevelDes
                        float4 *scratch, int max_cand, pd_box *boxes, int max_boxes,
                        int32_t *counts);
 
+// ---- the paper's kernel schemes (comparison with the fused kernels)
+size_t scheme_cells_scratch(int Wk, int Hk);
+cudaError_t launch_scheme_cells(cudaStream_t s, int scheme, const uint8_t *img, int Wk, int Hk, int pitch, float *hog,
+                                int64_t hog_plane, uint8_t *lbp, int64_t lbp_plane, int cell_pitch,
+                                const uint8_t *bin_of, unsigned char *scratch);
+size_t scheme_scores_scratch(int cells_x, int cells_y);
+cudaError_t launch_scheme_scores(cudaStream_t s, int scheme, const float *hog, int64_t hog_plane,
+                                 const uint8_t *lbp, int64_t lbp_plane, int cell_pitch, int cells_x, int cells_y,
+                                 const float *wt, float bias, float clip, float *scores, unsigned char *scratch);
+
 // ---- learned window proposal
 constexpr int kCnnParams = 14210;  // flat order: w1 b1 w2 b2 w3 b3 wh bh v bv
 constexpr int kOffW1 = 0, kOffB1 = 144, kOffW2 = 160, kOffB2 = 4768, kOffW3 = 4800, kOffB3 = 14016;
