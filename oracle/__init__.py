@@ -27,6 +27,7 @@ _lock = threading.Lock()
 _lib = None
 
 HOG_BINS = 9
+HOG_DIM = 36
 LBP_BINS = 59
 FEAT = 95
 WIN_BW = 7
@@ -73,10 +74,14 @@ def _load():
             lib.pdo_orientation_vote.argtypes = [d, P, P, P, P]
             lib.pdo_spatial_vote.argtypes = [i, i, P, P, P, P]
             lib.pdo_hog_cells.argtypes = [P, i, i, i, P]
+            lib.pdo_block_spatial_vote.argtypes = [i, P, P, P, P]
+            lib.pdo_hog_blocks.argtypes = [P, i, i, i, P]
+            lib.pdo_block_features_pb.argtypes = [P, P, i, i, d, P]
             lib.pdo_l2hys.argtypes = [P, i, d]
             lib.pdo_block_features.argtypes = [P, P, i, i, d, P]
             lib.pdo_scores.argtypes = [P, i, i, P, d, P]
             lib.pdo_level_scores.argtypes = [P, i, i, i, P, d, d, P, P, P, P]
+            lib.pdo_level_scores_ex.argtypes = [P, i, i, i, P, d, d, i, P, P, P, P]
             lib.pdo_window_descriptor_bruteforce.argtypes = [P, i, i, i, i, i, d, P]
             lib.pdo_window_box.argtypes = [i, i, i, i, i, i, P, P, P, P]
             lib.pdo_iou.argtypes = [P, P]
@@ -87,6 +92,8 @@ def _load():
             lib.pdo_detect.restype = i
             lib.pdo_detect_up.argtypes = [P, i, i, i, d, i, P, d, d, f, d, i, i, P, P, P, P, P, P]
             lib.pdo_detect_up.restype = i
+            lib.pdo_detect_ex.argtypes = [P, i, i, i, d, i, i, P, d, d, f, d, i, i, P, P, P, P, P, P]
+            lib.pdo_detect_ex.restype = i
             _lib = lib
     return _lib
 
@@ -199,6 +206,26 @@ def hog_cells(L: np.ndarray) -> np.ndarray:
     return out
 
 
+def block_spatial_vote(l: int):
+    """(c0, c1, w0, w1) of local coordinate l inside a 16-pixel block (cells -1 and 2 are outside it)."""
+    lib = _load()
+    c = np.zeros(2, np.int32)
+    w = np.zeros(2, np.float64)
+    lib.pdo_block_spatial_vote(l, _p(c[0:1]), _p(c[1:2]), _p(w[0:1]), _p(w[1:2]))
+    return int(c[0]), int(c[1]), float(w[0]), float(w[1])
+
+
+def hog_blocks(L: np.ndarray) -> np.ndarray:
+    """f64[Hb][Wb][36] per-block HOG histograms (Algorithm 5, each block from its own pixels)."""
+    lib = _load()
+    L = _img(L)
+    Hb, Wb = L.shape[0] // 8 - 1, L.shape[1] // 8 - 1
+    out = np.zeros((max(Hb, 0), max(Wb, 0), HOG_DIM), np.float64)
+    if Hb > 0 and Wb > 0:
+        lib.pdo_hog_blocks(_p(L), L.shape[1], L.shape[0], L.shape[1], _p(out))
+    return out
+
+
 def l2hys(v: np.ndarray, clip: float = CLIP) -> np.ndarray:
     lib = _load()
     v = np.ascontiguousarray(v, dtype=np.float64).copy()
@@ -218,6 +245,18 @@ def block_features(hog: np.ndarray, lbp: np.ndarray, clip: float = CLIP) -> np.n
     return out
 
 
+def block_features_pb(hogb: np.ndarray, lbp: np.ndarray, clip: float = CLIP) -> np.ndarray:
+    """f64[Hb][Wb][95] from per-block HOG histograms (hog_blocks) and LBP cell counts."""
+    lib = _load()
+    hogb = np.ascontiguousarray(hogb, dtype=np.float64)
+    lbp = np.ascontiguousarray(lbp, dtype=np.uint8)
+    Hc, Wc = lbp.shape[:2]
+    assert hogb.shape == (Hc - 1, Wc - 1, HOG_DIM)
+    out = np.zeros((Hc - 1, Wc - 1, FEAT), np.float64)
+    lib.pdo_block_features_pb(_p(hogb), _p(lbp), Hc, Wc, float(clip), _p(out))
+    return out
+
+
 def scores(feat: np.ndarray, w: np.ndarray, bias: float) -> np.ndarray:
     """f64[Hb-14][Wb-6] window scores (Algorithm 6)."""
     lib = _load()
@@ -232,11 +271,16 @@ def scores(feat: np.ndarray, w: np.ndarray, bias: float) -> np.ndarray:
     return out
 
 
-def level_all(L: np.ndarray, w: np.ndarray, bias: float, clip: float = CLIP):
-    """(hog cells, lbp cells, block features, scores) of one level image."""
-    hog = hog_cells(L)
+def level_all(L: np.ndarray, w: np.ndarray, bias: float, clip: float = CLIP, per_block: bool = False):
+    """(hog cells, lbp cells, block features, scores) of one level image; with
+    per_block the first item is the per-block HOG histograms (hog_blocks)."""
     lbp = lbp_cells(L)
-    feat = block_features(hog, lbp, clip)
+    if per_block:
+        hog = hog_blocks(L)
+        feat = block_features_pb(hog, lbp, clip)
+    else:
+        hog = hog_cells(L)
+        feat = block_features(hog, lbp, clip)
     return hog, lbp, feat, scores(feat, w, bias)
 
 
@@ -304,7 +348,8 @@ def boxes_to_array(arr, k: int) -> np.ndarray:
 
 
 def detect(img: np.ndarray, w: np.ndarray, bias: float, factor: float, threshold: float = 0.0,
-           iou_thr: float = 0.5, max_boxes: int = 4096, clip: float = CLIP, upscale: int = 0):
+           iou_thr: float = 0.5, max_boxes: int = 4096, clip: float = CLIP, upscale: int = 0,
+           per_block: bool = False):
     """Whole plain path for one frame. Returns dict(levels, scores (list of f64 maps), boxes, n_candidates)."""
     lib = _load()
     img = _img(img)
@@ -318,7 +363,8 @@ def detect(img: np.ndarray, w: np.ndarray, bias: float, factor: float, threshold
     ncand = ctypes.c_int(0)
     out = (Box * max(max_boxes, 1))()
     w64 = np.ascontiguousarray(w, np.float64).reshape(-1)
-    k = lib.pdo_detect_up(_p(img), W, H, W, float(factor), int(upscale), _p(w64), float(bias), float(clip),
+    k = lib.pdo_detect_ex(_p(img), W, H, W, float(factor), int(upscale), int(per_block), _p(w64), float(bias),
+                          float(clip),
                           float(threshold), float(iou_thr), max_boxes, 1024, ctypes.byref(nl), _p(wk),
                           _p(hk), _p(sc), out, ctypes.byref(ncand))
     if k < 0:

@@ -16,6 +16,7 @@
  *   image / level      u8  [H][pitch]
  *   LBP cell counts    u8  [Hc][Wc][59]
  *   HOG cell histogram f64 [Hc][Wc][9]
+ *   HOG block histogram f64 [Hb][Wb][36]  (per-block reading, cells TL TR BL BR)
  *   block feature      f64 [Hb][Wb][95]   (36 HOG values then 59 LBP values)
  *   SVM template       f64 [15][7][95]
  *   score map          f64 [Hc-15][Wc-7]
@@ -270,6 +271,60 @@ void pdo_hog_cells(const uint8_t *L, int Wk, int Hk, int pitch, double *cells)
         }
 }
 
+/* Spatial vote inside one 16x16 block along one axis (per-block reading of
+ * Algorithm 5): the block's two cell centres sit at local coordinates 3.5 and
+ * 11.5; local coordinate l (0..15) votes into cells floor(u) and floor(u)+1,
+ * u = (l - 3.5)/8, with weights 1-frac and frac. Cells -1 and 2 lie outside
+ * the block and their votes are dropped by the caller, so a pixel lands in
+ * one or two cells per axis. */
+void pdo_block_spatial_vote(int l, int *c0, int *c1, double *w0, double *w1)
+{
+    double u = ((double)l - 3.5) / 8.0;
+    double f = floor(u);
+    *c0 = (int)f;
+    *c1 = (int)f + 1;
+    *w1 = u - f;
+    *w0 = 1.0 - *w1;
+}
+
+/* HOG block histograms, per-block reading (Section 4.3, Algorithm 5): one
+ * histogram of 4 cells x 9 bins per 16x16 block (stride 8, Hb = Hc-1 by
+ * Wb = Wc-1), filled by the block's own 256 pixels only. Each pixel
+ * (Algorithm 4 gradient) adds magnitude x orientation weight x spatial
+ * weights to the cells of the block its vote reaches, i.e. to 2, 4 or 8 bins
+ * depending on where it sits in the block (Section 4.3). Votes towards cells
+ * outside the block are not kept, so neighbouring blocks do not share cell
+ * histograms. Output f64 [Hb][Wb][36], cell q = 2 a + b (a row, b column of
+ * the cell in the block) at q*9. */
+void pdo_hog_blocks(const uint8_t *L, int Wk, int Hk, int pitch, double *blocks)
+{
+    int Hb = Hk / 8 - 1, Wb = Wk / 8 - 1;
+    if (Hb <= 0 || Wb <= 0) return;
+    for (int by = 0; by < Hb; ++by)
+        for (int bx = 0; bx < Wb; ++bx) {
+            double *f = blocks + ((size_t)by * Wb + bx) * PDO_HOG_DIM;
+            for (int t = 0; t < PDO_HOG_DIM; ++t) f[t] = 0.0;
+            for (int i = 0; i < 16; ++i)
+                for (int j = 0; j < 16; ++j) {
+                    double mag, th;
+                    pdo_gradient(L, Wk, Hk, pitch, 8 * bx + j, 8 * by + i, &mag, &th);
+                    int ob[2], cy[2], cx[2];
+                    double ow[2], wy[2], wx[2];
+                    pdo_orientation_vote(th, &ob[0], &ob[1], &ow[0], &ow[1]);
+                    pdo_block_spatial_vote(i, &cy[0], &cy[1], &wy[0], &wy[1]);
+                    pdo_block_spatial_vote(j, &cx[0], &cx[1], &wx[0], &wx[1]);
+                    for (int a = 0; a < 2; ++a) {
+                        if (cy[a] < 0 || cy[a] > 1) continue;
+                        for (int b = 0; b < 2; ++b) {
+                            if (cx[b] < 0 || cx[b] > 1) continue;
+                            for (int o = 0; o < 2; ++o)
+                                f[(2 * cy[a] + cx[b]) * PDO_HOG_BINS + ob[o]] += mag * ow[o] * wx[b] * wy[a];
+                        }
+                    }
+                }
+        }
+}
+
 /* ---------------------------------------------------------------------------
  * Block features (Section 4.2, Algorithm 3; Section 4.3). A block is 2x2
  * cells (16x16 pixels) at a stride of one cell (50% overlap), Hb = Hc-1,
@@ -321,6 +376,33 @@ void pdo_block_features(const double *hog, const uint8_t *lbp, int Hc, int Wc,
         }
 }
 
+/* Block features with the per-block HOG histograms: the block's own 36 HOG
+ * values (pdo_hog_blocks) L2-Hys normalised, then the LBP part as in
+ * pdo_block_features. */
+void pdo_block_features_pb(const double *hogb, const uint8_t *lbp, int Hc, int Wc,
+                           double clip, double *feat)
+{
+    int Hb = Hc - 1, Wb = Wc - 1;
+    for (int by = 0; by < Hb; ++by)
+        for (int bx = 0; bx < Wb; ++bx) {
+            double *f = feat + ((size_t)by * Wb + bx) * PDO_FEAT;
+            const double *hb = hogb + ((size_t)by * Wb + bx) * PDO_HOG_DIM;
+            for (int t = 0; t < PDO_HOG_DIM; ++t) f[t] = hb[t];
+            pdo_l2hys(f, PDO_HOG_DIM, clip);
+            double h[PDO_LBP_BINS], tot = 0.0;
+            for (int t = 0; t < PDO_LBP_BINS; ++t) {
+                h[t] = 0.0;
+                for (int q = 0; q < 4; ++q) {
+                    int cy = by + q / 2, cx = bx + q % 2;
+                    h[t] += (double)lbp[((size_t)cy * Wc + cx) * PDO_LBP_BINS + t];
+                }
+                tot += h[t];
+            }
+            for (int t = 0; t < PDO_LBP_BINS; ++t)
+                f[PDO_HOG_DIM + t] = tot > 0.0 ? sqrt(h[t] / tot) : 0.0;
+        }
+}
+
 /* ---------------------------------------------------------------------------
  * Sliding-window linear SVM (Section 4.4, Algorithm 6): the window whose
  * top-left block is (wx, wy) covers 15x7 blocks; its descriptor is those
@@ -346,16 +428,30 @@ void pdo_scores(const double *feat, int Hb, int Wb, const double *w, double bias
 }
 
 /* Whole level: cells, block features and scores of one pyramid level image.
- * hog/lbp/feat are caller scratch of the sizes given in the file header. */
+ * hog/lbp/feat are caller scratch of the sizes given in the file header;
+ * with per_block the HOG part comes from pdo_hog_blocks and hog must hold
+ * Hb*Wb*36 values. */
+void pdo_level_scores_ex(const uint8_t *L, int Wk, int Hk, int pitch, const double *w,
+                         double bias, double clip, int per_block, double *hog, uint8_t *lbp,
+                         double *feat, double *scores)
+{
+    int Wc = Wk / 8, Hc = Hk / 8;
+    pdo_lbp_cells(L, Wk, Hk, pitch, lbp);
+    if (per_block) {
+        pdo_hog_blocks(L, Wk, Hk, pitch, hog);
+        pdo_block_features_pb(hog, lbp, Hc, Wc, clip, feat);
+    } else {
+        pdo_hog_cells(L, Wk, Hk, pitch, hog);
+        pdo_block_features(hog, lbp, Hc, Wc, clip, feat);
+    }
+    pdo_scores(feat, Hc - 1, Wc - 1, w, bias, scores);
+}
+
 void pdo_level_scores(const uint8_t *L, int Wk, int Hk, int pitch, const double *w,
                       double bias, double clip, double *hog, uint8_t *lbp, double *feat,
                       double *scores)
 {
-    int Wc = Wk / 8, Hc = Hk / 8;
-    pdo_hog_cells(L, Wk, Hk, pitch, hog);
-    pdo_lbp_cells(L, Wk, Hk, pitch, lbp);
-    pdo_block_features(hog, lbp, Hc, Wc, clip, feat);
-    pdo_scores(feat, Hc - 1, Wc - 1, w, bias, scores);
+    pdo_level_scores_ex(L, Wk, Hk, pitch, w, bias, clip, 0, hog, lbp, feat, scores);
 }
 
 /* ---------------------------------------------------------------------------
@@ -512,10 +608,11 @@ int pdo_nms(const float *scores, int n_levels, const int *rows, const int *cols,
  * The whole plain path for one frame (Section 4.1 steps 2-5): pyramid,
  * per-level features and scores, NMS. Scores of all levels are written back
  * to back into `scores` (double) and, rounded, used for NMS. Returns the
- * number of boxes, or -1 on allocation failure.
+ * number of boxes, or -1 on allocation failure. per_block selects the
+ * per-block HOG histograms (pdo_hog_blocks) instead of the shared cells.
  * ------------------------------------------------------------------------- */
-int pdo_detect_up(const uint8_t *img, int W, int H, int pitch, double factor, int upscale, const double *w,
-                  double bias, double clip, float threshold, double iou_thr, int max_boxes,
+int pdo_detect_ex(const uint8_t *img, int W, int H, int pitch, double factor, int upscale, int per_block,
+                  const double *w, double bias, double clip, float threshold, double iou_thr, int max_boxes,
                   int max_levels, int *n_levels_out, int *Wk, int *Hk, double *scores,
                   pdo_box *boxes, int *n_candidates);
 
@@ -524,11 +621,21 @@ int pdo_detect(const uint8_t *img, int W, int H, int pitch, double factor, const
                int max_levels, int *n_levels_out, int *Wk, int *Hk, double *scores,
                pdo_box *boxes, int *n_candidates)
 {
-    return pdo_detect_up(img, W, H, pitch, factor, 0, w, bias, clip, threshold, iou_thr, max_boxes, max_levels,
+    return pdo_detect_ex(img, W, H, pitch, factor, 0, 0, w, bias, clip, threshold, iou_thr, max_boxes, max_levels,
                          n_levels_out, Wk, Hk, scores, boxes, n_candidates);
 }
 
 int pdo_detect_up(const uint8_t *img, int W, int H, int pitch, double factor, int upscale, const double *w,
+                  double bias, double clip, float threshold, double iou_thr, int max_boxes,
+                  int max_levels, int *n_levels_out, int *Wk, int *Hk, double *scores,
+                  pdo_box *boxes, int *n_candidates)
+{
+    return pdo_detect_ex(img, W, H, pitch, factor, upscale, 0, w, bias, clip, threshold, iou_thr, max_boxes,
+                         max_levels, n_levels_out, Wk, Hk, scores, boxes, n_candidates);
+}
+
+int pdo_detect_ex(const uint8_t *img, int W, int H, int pitch, double factor, int upscale, int per_block,
+                  const double *w,
                   double bias, double clip, float threshold, double iou_thr, int max_boxes,
                   int max_levels, int *n_levels_out, int *Wk, int *Hk, double *scores,
                   pdo_box *boxes, int *n_candidates)
@@ -549,7 +656,7 @@ int pdo_detect_up(const uint8_t *img, int W, int H, int pitch, double factor, in
     }
     size_t maxcells = maxpx / 64 + 1;
     uint8_t *L = (uint8_t *)malloc(maxpx);
-    double *hog = (double *)malloc(maxcells * PDO_HOG_BINS * sizeof(double));
+    double *hog = (double *)malloc(maxcells * PDO_HOG_DIM * sizeof(double));
     uint8_t *lbp = (uint8_t *)malloc(maxcells * PDO_LBP_BINS);
     double *feat = (double *)malloc(maxcells * PDO_FEAT * sizeof(double));
     float *fs = (float *)malloc((total ? total : 1) * sizeof(float));
@@ -560,7 +667,7 @@ int pdo_detect_up(const uint8_t *img, int W, int H, int pitch, double factor, in
     size_t off = 0;
     for (int k = 0; k < nl; ++k) {
         pdo_resize(img, W, H, pitch, L, Wk[k], Hk[k], Wk[k]);
-        pdo_level_scores(L, Wk[k], Hk[k], Wk[k], w, bias, clip, hog, lbp, feat, scores + off);
+        pdo_level_scores_ex(L, Wk[k], Hk[k], Wk[k], w, bias, clip, per_block, hog, lbp, feat, scores + off);
         for (size_t i = 0; i < (size_t)rows[k] * cols[k]; ++i) fs[off + i] = (float)scores[off + i];
         off += (size_t)rows[k] * cols[k];
     }

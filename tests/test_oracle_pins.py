@@ -519,3 +519,167 @@ def test_detect_with_upscaled_levels_scores_each_level():
     assert ref["levels"][0][0] > 160 and len(ref["levels"]) == len(oracle.pyramid(160, 200, f)) + 2
     for (wk, hk), m in zip(ref["levels"], ref["scores"]):
         assert np.allclose(m, oracle.level_scores(oracle.resize(img, wk, hk), w, b), rtol=0, atol=1e-9)
+
+
+# ----------------------------------------------------------------------------- HOG blocks (per-block reading)
+def _tent_kept(l):
+    """Weight of local coordinate l (0..15) kept inside a 16-pixel block, summed over its cells."""
+    return min(1.0, (4.5 + l) / 8.0, (19.5 - l) / 8.0)
+
+
+def test_block_spatial_vote_values_and_mirror():
+    cases = {0: {0: 9 / 16}, 3: {0: 15 / 16}, 4: {0: 15 / 16, 1: 1 / 16}, 7: {0: 9 / 16, 1: 7 / 16},
+             11: {0: 1 / 16, 1: 15 / 16}, 12: {1: 15 / 16}, 15: {1: 9 / 16}}
+    for l, want in cases.items():
+        c0, c1, w0, w1 = oracle.block_spatial_vote(l)
+        got = {c: w for c, w in ((c0, w0), (c1, w1)) if 0 <= c <= 1 and w != 0.0}
+        assert got == want, (l, got)
+    for l in range(16):
+        a = oracle.block_spatial_vote(l)
+        b = oracle.block_spatial_vote(15 - l)
+        ka = {c: w for c, w in ((a[0], a[2]), (a[1], a[3])) if 0 <= c <= 1}
+        kb = {1 - c: w for c, w in ((b[0], b[2]), (b[1], b[3])) if 0 <= c <= 1}
+        assert ka == kb and abs(sum(ka.values()) - _tent_kept(l)) < 1e-15, l
+
+
+def test_hog_blocks_single_impulse_closed_form():
+    # One bright pixel at (11, 11) of a black 32x32 image (the 4 gradient
+    # pixels of the HOG cell pin above). Blocks (0,0), (0,1), (1,0), (1,1)
+    # hold them; inside a block the cell centres are at local 3.5 and 11.5 and
+    # votes leaving the block are dropped: local 2 -> cell 0 13/16; 3 -> cell 0
+    # 15/16; 4 -> cells 0/1 15/16, 1/16; 10 -> 3/16, 13/16; 11 -> 1/16, 15/16;
+    # 12 -> cell 1 15/16.
+    img = np.zeros((32, 32), np.uint8)
+    img[11, 11] = 100
+    hb = oracle.hog_blocks(img)
+    assert hb.shape == (3, 3, 36)
+    w = {2: {0: 13 / 16}, 3: {0: 15 / 16}, 4: {0: 15 / 16, 1: 1 / 16},
+         10: {0: 3 / 16, 1: 13 / 16}, 11: {0: 1 / 16, 1: 15 / 16}, 12: {1: 15 / 16}}
+    ref = np.zeros((3, 3, 36))
+    for (px, py, bins) in [(10, 11, {8: 50, 0: 50}), (12, 11, {8: 50, 0: 50}),
+                           (11, 10, {4: 100}), (11, 12, {4: 100})]:
+        for by in range(3):
+            for bx in range(3):
+                ly, lx = py - 8 * by, px - 8 * bx
+                if not (0 <= ly < 16 and 0 <= lx < 16):
+                    continue
+                for a, wa in w[ly].items():
+                    for b, wb in w[lx].items():
+                        for o, m in bins.items():
+                            ref[by, bx, (2 * a + b) * 9 + o] += m * wa * wb
+    assert np.allclose(hb, ref, rtol=0, atol=1e-12)
+    # a pixel lands in 2, 4 or 8 bins: in block (1, 1) the four gradient
+    # pixels sit at local (2, 3), (4, 3), (3, 2), (3, 4) and fill bins 0, 4, 8
+    # of cell 0, bins 0, 8 of cell 1 and bin 4 of cell 2 only
+    assert np.count_nonzero(hb[1, 1]) == 6
+
+
+def test_hog_blocks_ramp_closed_form():
+    # I = 3x + 10 (64 x 48): interior gx = 6, gx = 3 on the two border columns,
+    # gy = 0, theta = 0 -> bins 8 and 0 with 1/2 each. A cell of a block keeps
+    # sum_l of its tent over the 16 block pixels = 7 per axis, so interior
+    # blocks hold 0.5 * 6 * 7 * 7 = 147 in bins 0 and 8 of every cell (the
+    # shared cell grid gives 0.5 * 6 * 8 * 8 = 192). Block column 0 loses
+    # 3 * 9/16 on pixel column 0 of its left cells.
+    x = np.arange(64)
+    img = np.tile((3 * x + 10).astype(np.uint8), (48, 1))
+    hb = oracle.hog_blocks(img).reshape(5, 7, 4, 9)
+    ref = np.zeros((5, 7, 4, 9))
+    ref[:, :, :, 0] = ref[:, :, :, 8] = 147.0
+    left = 0.5 * 7 * (42 - 3 * 9 / 16)
+    ref[:, 0, 0, [0, 8]] = ref[:, 0, 2, [0, 8]] = left
+    ref[:, 6, 1, [0, 8]] = ref[:, 6, 3, [0, 8]] = left
+    assert np.allclose(hb, ref, rtol=0, atol=1e-9)
+    hc = oracle.hog_cells(img)
+    assert np.allclose(hc[1:-1, 1:-1, 0], 192.0, rtol=0, atol=1e-9)
+    # the same ramp along y: theta = 90 -> bin 4 only, 6 * 49 = 294
+    hv = oracle.hog_blocks(img.T.copy()).reshape(7, 5, 4, 9)
+    assert np.allclose(hv[1:-1, :, :, 4], 294.0, rtol=0, atol=1e-9)
+    assert np.allclose(np.delete(hv, 4, axis=3), 0.0, rtol=0, atol=1e-12)
+
+
+def test_hog_blocks_total_mass_closed_form():
+    # summed over its 36 values a block holds sum_p |g(p)| T(lx) T(ly), T the
+    # kept tent weight (9/16 .. 1 .. 9/16), with |g| from clamped central
+    # differences computed here with numpy
+    img = synth.random_image(56, 43, 21, smooth=False)
+    hb = oracle.hog_blocks(img)
+    Lp = np.pad(img.astype(np.float64), 1, mode="edge")
+    gx = Lp[1:-1, 2:] - Lp[1:-1, :-2]
+    gy = Lp[2:, 1:-1] - Lp[:-2, 1:-1]
+    mag = np.hypot(gx, gy)
+    T = np.array([_tent_kept(l) for l in range(16)])
+    Hb, Wb = hb.shape[:2]
+    for by in range(Hb):
+        for bx in range(Wb):
+            want = float(T @ mag[8 * by:8 * by + 16, 8 * bx:8 * bx + 16] @ T)
+            assert abs(hb[by, bx].sum() - want) <= 1e-11 * max(want, 1.0), (by, bx)
+    assert np.all(hb >= 0)
+
+
+def test_hog_blocks_equal_cells_when_gradients_stay_in_the_block_centre():
+    # A 6x6 random patch at rows/cols 8b+5 .. 8b+10 of a constant image: every
+    # nonzero gradient lies in the central 8x8 of block b, where each vote
+    # reaches the block's own 4 cells with the shared grid's weights, so the
+    # block equals the 4 shared cells exactly (and the cells hold nothing
+    # else).
+    rng = np.random.default_rng(5)
+    img = np.full((40, 48), 77, np.uint8)
+    by, bx = 2, 3
+    img[8 * by + 5:8 * by + 11, 8 * bx + 5:8 * bx + 11] = rng.integers(0, 256, (6, 6))
+    hb = oracle.hog_blocks(img)
+    hc = oracle.hog_cells(img)
+    cells = np.concatenate([hc[by, bx], hc[by, bx + 1], hc[by + 1, bx], hc[by + 1, bx + 1]])
+    assert cells.sum() > 0
+    assert np.array_equal(hb[by, bx], cells)
+
+
+def test_hog_blocks_are_local_and_cells_are_not():
+    # a block reads only its 16x16 pixels and their 1-pixel gradient halo
+    # (Section 4.3: block histograms cannot be assembled from shared cells)
+    img = synth.random_image(64, 56, 22, smooth=False)
+    by, bx = 2, 3
+    other = img.copy()
+    mask = np.ones_like(img, bool)
+    mask[8 * by - 1:8 * by + 17, 8 * bx - 1:8 * bx + 17] = False
+    other[mask] = 255 - other[mask]
+    other[8 * by - 1:8 * by + 17, 8 * bx - 1] = img[8 * by - 1:8 * by + 17, 8 * bx - 1]  # halo kept
+    a, b = oracle.hog_blocks(img), oracle.hog_blocks(other)
+    assert np.array_equal(a[by, bx], b[by, bx])
+    assert not np.array_equal(a[by, bx - 1], b[by, bx - 1])
+    ca, cb = oracle.hog_cells(img), oracle.hog_cells(other)
+    assert not np.array_equal(ca[by:by + 2, bx:bx + 2], cb[by:by + 2, bx:bx + 2])
+
+
+def test_hog_blocks_mirror_symmetry():
+    # left-right: block bx -> Wb-1-bx, cell column b -> 1-b, bin o -> 8-o;
+    # up-down: block by -> Hb-1-by, cell row a -> 1-a, bin o -> 8-o
+    img = synth.random_image(48, 40, 23, smooth=False)
+    h = oracle.hog_blocks(img).reshape(4, 5, 2, 2, 9)
+    hl = oracle.hog_blocks(img[:, ::-1].copy()).reshape(4, 5, 2, 2, 9)
+    hu = oracle.hog_blocks(img[::-1, :].copy()).reshape(4, 5, 2, 2, 9)
+    assert np.allclose(hl, h[:, ::-1, :, ::-1, ::-1], rtol=0, atol=1e-9)
+    assert np.allclose(hu, h[::-1, :, ::-1, :, ::-1], rtol=0, atol=1e-9)
+
+
+def test_block_features_pb_parts():
+    img = synth.random_image(80, 72, 24, smooth=True)
+    hb = oracle.hog_blocks(img)
+    lbp = oracle.lbp_cells(img)
+    f = oracle.block_features_pb(hb, lbp)
+    g = oracle.block_features(oracle.hog_cells(img), lbp)
+    assert np.array_equal(f[..., 36:], g[..., 36:])
+    for by, bx in [(0, 0), (3, 5), (7, 8)]:
+        assert np.allclose(f[by, bx, :36], oracle.l2hys(hb[by, bx]), rtol=0, atol=0)
+    assert not np.allclose(f[..., :36], g[..., :36], atol=1e-3)
+
+
+def test_detect_per_block_matches_stagewise_composition():
+    w = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                             "svm_template_seed0.npz"))
+    img = synth.make_scene(160, 300, 2, 25)
+    F = float(np.float32(1.2))
+    ref = oracle.detect(img, w["w"], float(w["b"]), F, per_block=True)
+    for (wk, hk), sc in zip(ref["levels"], ref["scores"]):
+        L = oracle.resize(img, wk, hk)
+        assert np.array_equal(sc, oracle.level_all(L, w["w"], float(w["b"]), per_block=True)[3])
