@@ -70,6 +70,16 @@ extern "C" {
  * block features times their weights. At most one of the two. */
 #define PD_FLAG_HOG_ONLY 4
 #define PD_FLAG_LBP_ONLY 8
+/* Per-block HOG (Section 4.3, Algorithm 5 read per block): each 16x16 block's
+ * 4 cell histograms are filled by the block's own 256 pixels only. A pixel
+ * votes bilinearly towards the two nearest of the block's cell centres (local
+ * 3.5 and 11.5) on each axis, and votes towards a cell outside the block are
+ * dropped, so it lands in 2, 4 or 8 bins. Neighbouring blocks then do not
+ * share cell histograms. The default instead bins every pixel on one shared
+ * cell grid, with clamped borders. The cell planes then hold 36 HOG planes
+ * (see pd_cell_features). Tensor-core K4 only: not with PD_FLAG_SVM_FP32 or
+ * PD_FLAG_LBP_ONLY (PD_EINVAL). */
+#define PD_FLAG_HOG_PER_BLOCK 16
 
 typedef struct pd_handle pd_handle;
 
@@ -244,12 +254,19 @@ int pd_resize_levels(pd_handle *h, void *stream, const uint8_t *d_frame, int W, 
  * (cell_pitch >= floor(Wk/8), a multiple of 16):
  *   d_hog  float32 [9][cells_y][cell_pitch]   (plane stride hog_plane elems)
  *   d_lbp  uint8   [59][cells_y][cell_pitch]  (plane stride lbp_plane elems)
- * hog_plane / lbp_plane >= cells_y * cell_pitch. Errors: PD_EINVAL, PD_ECUDA. */
+ * hog_plane / lbp_plane >= cells_y * cell_pitch. With PD_FLAG_HOG_PER_BLOCK
+ * d_hog holds 36 planes: plane 9 q + bin of cell (cy, cx) is its histogram
+ * restricted to the block in which it sits at place q (0 top-left, 1
+ * top-right, 2 bottom-left, 3 bottom-right), so block (by, bx) is planes
+ * 0-8 of cell (by, bx), 9-17 of (by, bx+1), 18-26 of (by+1, bx) and 27-35 of
+ * (by+1, bx+1) (values at places no block uses are unspecified).
+ * Errors: PD_EINVAL, PD_ECUDA. */
 int pd_cell_features(pd_handle *h, void *stream, const uint8_t *d_level, int Wk, int Hk, int pitch, float *d_hog,
                      int64_t hog_plane, uint8_t *d_lbp, int64_t lbp_plane, int cell_pitch);
 
 /* K4, Section 4.4 (Algorithm 6) with block normalisation: the score map of
- * one level from its cell planes (layouts of pd_cell_features; LBP counts
+ * one level from its cell planes (layouts of pd_cell_features, 36 HOG planes
+ * with PD_FLAG_HOG_PER_BLOCK; LBP counts
  * must be <= 64, as a cell has 64 pixels), using the handle's template and
  * bias and its K4 kernel (tensor cores, or FP32 with PD_FLAG_SVM_FP32):
  * d_scores float32 [cells_y-15][cells_x-7], row pitch cells_x-7. The

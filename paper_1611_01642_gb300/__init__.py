@@ -32,6 +32,7 @@ PD_FLAG_STAGE_TIMING = 1
 PD_FLAG_SVM_FP32 = 2
 PD_FLAG_HOG_ONLY = 4
 PD_FLAG_LBP_ONLY = 8
+PD_FLAG_HOG_PER_BLOCK = 16
 TILE_SHAPES = 7
 TILE_SHAPE_DIMS = [(32, 16), (64, 8), (32, 8), (64, 4), (64, 2), (32, 12), (32, 4)]  # windows per K4 tile (x, y)
 

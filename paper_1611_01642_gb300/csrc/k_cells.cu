@@ -43,6 +43,21 @@
 // lbp[bin][row][cx] (u8, counts <= 64). `feat` selects the features computed
 // (HOG, LBP or both: the HOG-SVM and LBP-SVM pipelines of Section 4.1 skip
 // the other one).
+//
+// Per-block HOG (kFeatHogBlock, Algorithm 5 read per 16x16 block): a block's
+// 4 cell histograms take only the block's own pixels, with the votes of the
+// shared grid left unclamped (a vote towards a cell outside the block is
+// dropped). Cell (cy, cx) sits at one of 4 places q = 2a + b of the blocks
+// that contain it (a = 0: it is the block's top cell, so the block spans
+// pixel rows [8cy, 8cy + 16); a = 1: rows [8cy - 8, 8cy + 8); b likewise on
+// x), and the kernel writes its 4 restricted histograms Q_q to planes
+// 9q + bin. Block (by, bx) is then [Q_0(by, bx), Q_1(by, bx+1),
+// Q_2(by+1, bx), Q_3(by+1, bx+1)]. Of the pixel rows that vote into cell row
+// t, those in [8t, 8t + 12) belong to a = 0 and those in [8t - 4, 8t + 8) to
+// a = 1: a band row votes into both a's of one of its two cell rows and one
+// a of the other (3 vertical slots per pixel instead of 2). On x, the 4
+// column sums of a cell's two groups are split in halves: b = 0 drops the
+// first half of its own group, b = 1 the second half of the next one.
 #include "pd_internal.h"
 
 namespace pd {
@@ -59,9 +74,10 @@ constexpr int kRPitch = kCols;                 // bin stride: a multiple of 32 b
 static_assert(kCols == kThreads, "one pixel column (and its vote slots) per thread");
 constexpr int kLbpWords = (kLbpBins + 1) / 2;  // two 16-bit counters per word
 
+template <int NA>
 struct CellSmem {
     int4 yv[kPixRows];                      // per pixel row: ring slot / weight of its two cell votes
-    float R[kRing][kHogBins][kRPitch];      // vertical HOG partial sums per column
+    float R[kRing][NA][kHogBins][kRPitch];  // vertical HOG partial sums per column (NA = 2: per a)
     float WA[kCols];                        // per column: weight of its vote to the left cell of its group
     float WB[kCols];                        // per column: weight of its vote to its group's own cell
     uint32_t cnt[kRing][kTW][kLbpWords];    // LBP counts of the open cell rows
@@ -104,8 +120,10 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
                                                     const uint8_t *__restrict__ lbp_map,
                                                     const uint32_t *__restrict__ c_flag) {
     constexpr int feat = FEAT;
+    constexpr bool pb = (FEAT & kFeatHogBlock) != 0;  // per-block HOG
+    constexpr int NA = pb ? 2 : 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    CellSmem &S = *reinterpret_cast<CellSmem *>(smem_raw);
+    CellSmem<NA> &S = *reinterpret_cast<CellSmem<NA> *>(smem_raw);
     if (c_flag && !c_flag[blockIdx.x]) return;  // sparse path: no kept window needs these cells
     const CellItem it = items[blockIdx.x];
     const LevelDesc L = levels[it.level];
@@ -115,20 +133,21 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
     const int Wk = L.Wk, Hk = L.Hk, Wc = L.Wc, Hc = L.Hc;
     const int gridW = 8 * Wc, gridH = 8 * Hc;
 
-    for (int i = tid; i < kRing * kHogBins * kRPitch; i += kThreads) (&S.R[0][0][0])[i] = 0.f;
+    for (int i = tid; i < kRing * NA * kHogBins * kRPitch; i += kThreads) (&S.R[0][0][0][0])[i] = 0.f;
     for (int i = tid; i < kRing * kTW * kLbpWords; i += kThreads) (&S.cnt[0][0][0])[i] = 0u;
     for (int i = tid; i < 256; i += kThreads) S.map[i] = lbp_map[i];
     const int px0 = 8 * it.cx0 - 5, py0 = 8 * it.cy0 - 5;
     for (int r = tid; r < kPixRows; r += kThreads) {
         // row y votes into cell rows floor(u), floor(u)+1 (u = (y-3.5)/8,
-        // clamped into the grid) with weights 1-frac, frac; slot -1 = not
-        // in this tile
+        // clamped into the grid; per-block: unclamped, rows outside the grid
+        // dropped) with weights 1-frac, frac; slot -1 = not in this tile
         const int y = py0 + r;
         const float uy = ((float)y - 3.5f) * 0.125f;
         const float fy = floorf(uy);
         const float w1 = uy - fy;
-        const int c0 = clampi((int)fy, 0, Hc - 1) - it.cy0;
-        const int c1 = clampi((int)fy + 1, 0, Hc - 1) - it.cy0;
+        const int f0 = (int)fy;
+        const int c0 = (pb ? (f0 >= 0 && f0 < Hc ? f0 : -(1 << 20)) : clampi(f0, 0, Hc - 1)) - it.cy0;
+        const int c1 = (pb ? (f0 + 1 < Hc ? f0 + 1 : -(1 << 20)) : clampi(f0 + 1, 0, Hc - 1)) - it.cy0;
         int4 e;
         e.x = (c0 >= 0 && c0 < kTH) ? (c0 & 1) : -1;
         e.y = (c1 >= 0 && c1 < kTH) ? (c1 & 1) : -1;
@@ -157,14 +176,15 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
     const int cxl = (x >> 3) - it.cx0;
     const int rc = tid;
     // Horizontal vote of this column: pixel column x reaches cells
-    // cx0+g-1 and cx0+g (g = tid/8) with weights wA, wB (clamped into the grid;
-    // zero outside it).
+    // cx0+g-1 and cx0+g (g = tid/8) with weights wA, wB (clamped into the grid,
+    // unclamped for per-block HOG; zero outside it).
     float wA = 0.f, wB = 0.f;
     if (active) {
         const float ux = ((float)x - 3.5f) * 0.125f;
         const float fx = floorf(ux);
         const float w1 = ux - fx, w0 = 1.f - w1;
-        const int c0 = clampi((int)fx, 0, Wc - 1), c1 = clampi((int)fx + 1, 0, Wc - 1);
+        const int c0 = pb ? (int)fx : clampi((int)fx, 0, Wc - 1);
+        const int c1 = pb ? (int)fx + 1 : clampi((int)fx + 1, 0, Wc - 1);
         const int left = it.cx0 + (tid >> 3) - 1, own = left + 1;
         wA = (c0 == left ? w0 : 0.f) + (c1 == left ? w1 : 0.f);
         wB = (c0 == own ? w0 : 0.f) + (c1 == own ? w1 : 0.f);
@@ -208,17 +228,47 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
                     const int b1 = bi + 1 >= kHogBins ? 0 : bi + 1;
                     const int4 yv = S.yv[y - py0];
                     const float mo0 = mag * o0, mo1 = mag * o1;
-                    if (yv.x >= 0) {
-                        const float w = __int_as_float(yv.z);
-                        float *R0 = &S.R[yv.x][0][rc];
-                        R0[b0 * kRPitch] += mo0 * w;
-                        R0[b1 * kRPitch] += mo1 * w;
-                    }
-                    if (yv.y >= 0) {
-                        const float w = __int_as_float(yv.w);
-                        float *R1 = &S.R[yv.y][0][rc];
-                        R1[b0 * kRPitch] += mo0 * w;
-                        R1[b1 * kRPitch] += mo1 * w;
+                    if constexpr (!pb) {
+                        if (yv.x >= 0) {
+                            const float w = __int_as_float(yv.z);
+                            float *R0 = &S.R[yv.x][0][0][rc];
+                            R0[b0 * kRPitch] += mo0 * w;
+                            R0[b1 * kRPitch] += mo1 * w;
+                        }
+                        if (yv.y >= 0) {
+                            const float w = __int_as_float(yv.w);
+                            float *R1 = &S.R[yv.y][0][0][rc];
+                            R1[b0 * kRPitch] += mo0 * w;
+                            R1[b1 * kRPitch] += mo1 * w;
+                        }
+                    } else {
+                        // a band row above the band's centre (k < 4) lies in both a's
+                        // of the upper cell row and in a = 1 of the lower one; below
+                        // it (k >= 4), in a = 0 of the upper and both of the lower
+                        if (yv.x >= 0) {
+                            const float w = __int_as_float(yv.z);
+                            const float v0 = mo0 * w, v1 = mo1 * w;
+                            float *R0 = &S.R[yv.x][0][0][rc];
+                            R0[b0 * kRPitch] += v0;
+                            R0[b1 * kRPitch] += v1;
+                            if (k < 4) {
+                                R0 += kHogBins * kRPitch;
+                                R0[b0 * kRPitch] += v0;
+                                R0[b1 * kRPitch] += v1;
+                            }
+                        }
+                        if (yv.y >= 0) {
+                            const float w = __int_as_float(yv.w);
+                            const float v0 = mo0 * w, v1 = mo1 * w;
+                            float *R1 = &S.R[yv.y][NA - 1][0][rc];
+                            R1[b0 * kRPitch] += v0;
+                            R1[b1 * kRPitch] += v1;
+                            if (k >= 4) {
+                                R1 -= kHogBins * kRPitch;
+                                R1[b0 * kRPitch] += v0;
+                                R1[b1 * kRPitch] += v1;
+                            }
+                        }
                     }
                 }
                 if (y >= 0 && y < gridH && (feat & kFeatLbp)) {
@@ -244,9 +294,34 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
         if (cyl >= 0) {
             const int cy = it.cy0 + cyl;
             const int64_t row = (int64_t)(L.cell_row + cy) * atlas.pitch;
-            const float(*R)[kRPitch] = S.R[cyl & 1];
+            const float(*R)[kRPitch] = S.R[cyl & 1][0];
             // HOG: one thread per (bin, cell): own group with WB, next group with WA
-            for (int o = tid; o < ((feat & kFeatHog) ? kHogBins * kTW : 0); o += kThreads) {
+            if (pb) {
+                // per-block: halves of both groups for each a; b = 0 drops the
+                // first half of the own group, b = 1 the second half of the next
+                for (int o = tid; o < 2 * kHogBins * kTW; o += kThreads) {
+                    const int a = o / (kHogBins * kTW), ob = o - a * (kHogBins * kTW);
+                    const int bin = ob / kTW, cxo = ob - bin * kTW;
+                    const int cx = it.cx0 + cxo;
+                    if (cx >= Wc) continue;
+                    const float *Ra = &S.R[cyl & 1][a][bin][8 * cxo];
+                    float h[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float4 v = reinterpret_cast<const float4 *>(Ra)[k];
+                        const float4 w = reinterpret_cast<const float4 *>(k < 2 ? &S.WB[8 * cxo] : &S.WA[8 * cxo + 8])[k & 1];
+                        float acc = w.x * v.x;
+                        acc = fmaf(w.y, v.y, acc);
+                        acc = fmaf(w.z, v.z, acc);
+                        acc = fmaf(w.w, v.w, acc);
+                        h[k] = acc;
+                    }
+                    const int64_t at = row + cx;
+                    atlas.hog[(int64_t)((2 * a) * kHogBins + bin) * atlas.hog_plane + at] = (h[1] + h[2]) + h[3];
+                    atlas.hog[(int64_t)((2 * a + 1) * kHogBins + bin) * atlas.hog_plane + at] = (h[0] + h[1]) + h[2];
+                }
+            }
+            for (int o = tid; o < ((feat & kFeatHog) && !pb ? kHogBins * kTW : 0); o += kThreads) {
                 const int b = o / kTW, cxo = o - b * kTW;
                 const int cx = it.cx0 + cxo;
                 if (cx >= Wc) continue;
@@ -287,17 +362,38 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
             // recycle the HOG slots of cell row cyl for cell row cyl + 2: only
             // this thread votes into its column, so it clears it itself
 #pragma unroll
-            for (int b = 0; b < kHogBins; ++b) S.R[cyl & 1][b][tid] = 0.f;
+            for (int a = 0; a < NA; ++a)
+#pragma unroll
+                for (int b = 0; b < kHogBins; ++b) S.R[cyl & 1][a][b][tid] = 0.f;
         }
     }
 }
 
 }  // namespace
 
+namespace {
+using CellFn = void (*)(const LevelDesc *, const uint8_t *, CellAtlas, const CellItem *, const uint8_t *,
+                        const uint32_t *);
+constexpr int kBlk = kFeatHogBlock;
+const CellFn kCellFns[5] = {k_cells<kFeatHog | kFeatLbp>, k_cells<kFeatHog>, k_cells<kFeatLbp>,
+                            k_cells<kFeatHog | kFeatLbp | kBlk>, k_cells<kFeatHog | kBlk>};
+const int kCellSmem[5] = {(int)sizeof(CellSmem<1>), (int)sizeof(CellSmem<1>), (int)sizeof(CellSmem<1>),
+                          (int)sizeof(CellSmem<2>), (int)sizeof(CellSmem<2>)};
+int cell_fn_index(int feat) {
+    switch (feat) {
+        case kFeatHog: return 1;
+        case kFeatLbp: return 2;
+        case kFeatHog | kFeatLbp | kBlk: return 3;
+        case kFeatHog | kBlk: return 4;
+        default: return 0;
+    }
+}
+}  // namespace
+
 cudaError_t init_cells() {
-    for (auto fn : {k_cells<kFeatHog | kFeatLbp>, k_cells<kFeatHog>, k_cells<kFeatLbp>}) {
-        const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)sizeof(CellSmem));
+    for (int i = 0; i < 5; ++i) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(kCellFns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, kCellSmem[i]);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -307,10 +403,8 @@ cudaError_t launch_cells(cudaStream_t s, const LevelDesc *d_levels, const uint8_
                          CellAtlas atlas, const CellItem *d_items, int n_items,
                          const uint8_t *d_lbp_map, const uint32_t *c_flag, int feat) {
     if (n_items <= 0) return cudaSuccess;
-    const int smem = (int)sizeof(CellSmem);
-    auto fn = feat == kFeatHog ? k_cells<kFeatHog> : feat == kFeatLbp ? k_cells<kFeatLbp>
-                                                                        : k_cells<kFeatHog | kFeatLbp>;
-    fn<<<n_items, kThreads, smem, s>>>(d_levels, pyr, atlas, d_items, d_lbp_map, c_flag);
+    const int k = cell_fn_index(feat);
+    kCellFns[k]<<<n_items, kThreads, kCellSmem[k], s>>>(d_levels, pyr, atlas, d_items, d_lbp_map, c_flag);
     return cudaGetLastError();
 }
 

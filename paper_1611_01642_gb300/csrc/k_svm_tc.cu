@@ -44,6 +44,10 @@
 // The A operand (two 96-column TMEM stages) and the accumulators are double
 // buffered, so the producers build row r + 1 and the epilogue reads row
 // r - 1 while row r's MMAs run.
+// Per-block HOG (Algorithm 5 read per block): each staged cell row holds 36
+// HOG planes, the cell's 4 block-restricted histograms (plane 9 q + bin, q =
+// its place in the block); a block takes q = 0, 1 from row r and q = 2, 3
+// from row r + 1, and nothing else changes.
 // Sparse path: a window is scored when every cell tile under it was
 // computed; block rows that no such window needs are skipped, other windows
 // get -inf. A wait that gives up (1 s) sets the error word and a CTA flag
@@ -74,17 +78,20 @@ constexpr int kProducerBarrier = 1;   // named barrier of the producer warps
 static_assert(4 * kWinPerWarp == kTcStrip, "strip width");
 static_assert(kWinPerWarp + kWinBW - 1 <= 32, "window blocks inside a warp");
 
-struct Slot {
-    float hog[kHogBins][kHogX];       // 4032 B
-    uint8_t pad0[64];
-    uint8_t lbp[kLbpBins][kLbpX];     // 7552 B
+template <int HP>  // HOG planes per cell row: 9, or 36 for per-block HOG
+struct SlotT {
+    static constexpr int kPlanes = HP;
+    float hog[HP][kHogX];                       // 4032 B (16128 B per-block)
+    alignas(128) uint8_t lbp[kLbpBins][kLbpX];  // 7552 B
     uint8_t pad1[128];
 };
-static_assert(sizeof(Slot) % 128 == 0 && offsetof(Slot, lbp) % 128 == 0, "TMA destinations");
+static_assert(sizeof(SlotT<9>) == 11776 && offsetof(SlotT<9>, lbp) == 4096, "slot layout");
+static_assert(sizeof(SlotT<36>) % 128 == 0 && offsetof(SlotT<36>, lbp) % 128 == 0, "TMA destinations");
 
-struct TcSmem {
+template <int HP>
+struct TcSmemT {
     uint8_t b[14 * kSBO];             // B operand: template high | low parts
-    Slot slot[kSlots];                // staged cell rows
+    SlotT<HP> slot[kSlots];           // staged cell rows
     uint32_t tab[512];                // sum of 4 cell counts -> bf16 high | low << 16 of sqrt(S / 256)
     uint32_t win_ok[kTcChunk][4];     // sparse: window of the strip is scored
     uint8_t row_ok[kTcChunk];         // sparse: window row holds a scored window
@@ -99,7 +106,7 @@ struct TcSmem {
     int item;
     volatile int failed;
 };
-static_assert(offsetof(TcSmem, slot) % 128 == 0 && offsetof(TcSmem, b) == 0, "alignment");
+static_assert(offsetof(TcSmemT<9>, slot) % 128 == 0 && offsetof(TcSmemT<36>, slot) % 128 == 0, "alignment");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -120,7 +127,8 @@ __device__ __forceinline__ bool try_wait(unsigned long long *bar, uint32_t parit
 }
 // Bounded wait for phase `parity`; gives up after 1 s (and marks the CTA
 // failed) or as soon as another role has marked it failed.
-__device__ __forceinline__ bool bar_wait(TcSmem &S, unsigned long long *bar, uint32_t parity, unsigned *err) {
+template <class SM>
+__device__ __forceinline__ bool bar_wait(SM &S, unsigned long long *bar, uint32_t parity, unsigned *err) {
     if (try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (!S.failed) {
@@ -214,7 +222,7 @@ __device__ __forceinline__ void tst16(uint32_t t, const uint32_t *v) {
 // the staged rows hold sums of horizontally adjacent cells, so cells
 // (r, c..c+1) + (r+1, c..c+1) are two loads; the table gives the bf16 split
 // of sqrt(S / 256), packed two bins per word.
-template <int T0, int NP>
+template <int T0, int NP, class Slot>
 __device__ __forceinline__ void lbp_pairs(const Slot &s0, const Slot &s1, const uint32_t *tab, int c, uint32_t *hi,
                                           uint32_t *lo) {
 #pragma unroll
@@ -232,15 +240,17 @@ __device__ __forceinline__ void lbp_pairs(const Slot &s0, const Slot &s1, const 
 // (r, c), (r, c+1), (r+1, c), (r+1, c+1) (slots s0 = row r, s1 = row r + 1) in
 // the template's order (cells TL, TR, BL, BR, 9 bins each), L2-Hys, bf16
 // split; then LBP bins 0..19 (LBP column cl).
+template <class Slot>
 __device__ __forceinline__ void build_hog(const Slot &s0, const Slot &s1, const uint32_t *tab, int c, int cl,
                                           float clip, uint32_t a) {
+    constexpr int pq = Slot::kPlanes == 36 ? kHogBins : 0;  // per-block: plane set of the cell's place
     float v[36];
 #pragma unroll
     for (int b = 0; b < kHogBins; ++b) {
         v[b] = s0.hog[b][c];
-        v[9 + b] = s0.hog[b][c + 1];
-        v[18 + b] = s1.hog[b][c];
-        v[27 + b] = s1.hog[b][c + 1];
+        v[9 + b] = s0.hog[pq + b][c + 1];
+        v[18 + b] = s1.hog[2 * pq + b][c];
+        v[27 + b] = s1.hog[3 * pq + b][c + 1];
     }
     // sums of squares in four interleaved partial sums (independent chains)
     float q[4] = {0.f, 0.f, 0.f, 0.f};
@@ -272,6 +282,7 @@ __device__ __forceinline__ void build_hog(const Slot &s0, const Slot &s1, const 
 
 // Features 56..95 of A row m (LBP bins 20..58 and the zero pad): columns
 // a + 28 .. a + 47 and a + 76 .. a + 95.
+template <class Slot>
 __device__ __forceinline__ void build_lbp(const Slot &s0, const Slot &s1, const uint32_t *tab, int cl, uint32_t a) {
     uint32_t hi[20], lo[20];
     lbp_pairs<20, 20>(s0, s1, tab, cl, hi, lo);
@@ -287,6 +298,7 @@ __device__ __forceinline__ void build_lbp(const Slot &s0, const Slot &s1, const 
 // the 7-bit mask keeps bytes that hold no valid count from carrying into a
 // neighbour.
 constexpr int kPairIters = (kLbpBins * 32 + 255) / 256;  // 8
+template <class Slot>
 __device__ __forceinline__ void pair_sums(Slot &s, int pt) {
     uint32_t x[kPairIters], y[kPairIters];
     const int k = pt & 31;
@@ -312,11 +324,14 @@ __device__ __forceinline__ void producer_barrier() {
     asm volatile("bar.sync %0, %1;" ::"n"(kProducerBarrier), "n"(32 * kProducers) : "memory");
 }
 
+template <int HP>
 __global__ void __launch_bounds__(kThreads, 1)
     k_svm_tc(const __grid_constant__ CUtensorMap hog_map, const __grid_constant__ CUtensorMap lbp_map,
              const LevelDesc *__restrict__ levels, const TcItem *__restrict__ items, int n_items,
              int *__restrict__ queue, const float *__restrict__ wt, float bias, float clip,
              float *__restrict__ scores, const uint32_t *__restrict__ c_flag, unsigned *__restrict__ err) {
+    using Slot = SlotT<HP>;
+    using TcSmem = TcSmemT<HP>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem &S = *reinterpret_cast<TcSmem *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -514,7 +529,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     unsigned long long *bar = &S.cfull[idx % kSlots];
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                                 "r"((uint32_t)(sizeof(float) * kHogBins * kHogX + kLbpBins * kLbpX))
+                                 "r"((uint32_t)(sizeof(float) * HP * kHogX + kLbpBins * kLbpX))
                                  : "memory");
                     tma_3d(&sl.hog[0][0], &hog_map, bar, it.wx0, L.cell_row + ra + u, 0);
                     tma_3d(&sl.lbp[0][0], &lbp_map, bar, xl, L.cell_row + ra + u, 0);
@@ -613,19 +628,29 @@ __global__ void __launch_bounds__(kThreads, 1)
 }  // namespace
 
 cudaError_t init_svm_tc() {
-    return cudaFuncSetAttribute(k_svm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
+    cudaError_t e = cudaFuncSetAttribute(k_svm_tc<kHogBins>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(TcSmemT<kHogBins>));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_svm_tc<4 * kHogBins>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(TcSmemT<4 * kHogBins>));
 }
 
-int svm_tc_smem_bytes() { return (int)sizeof(TcSmem); }
+int svm_tc_smem_bytes(int hog_planes) {
+    return hog_planes == 4 * kHogBins ? (int)sizeof(TcSmemT<4 * kHogBins>) : (int)sizeof(TcSmemT<kHogBins>);
+}
 
 cudaError_t launch_svm_tc(cudaStream_t s, const CUtensorMap &hog_map, const CUtensorMap &lbp_map,
                           const LevelDesc *d_levels, const TcItem *d_items, int n_items, int *d_queue, int grid,
                           const float *d_w, float bias, float clip, float *scores, const uint32_t *c_flag,
-                          unsigned *d_err) {
+                          unsigned *d_err, int hog_planes) {
     if (n_items <= 0) return cudaSuccess;
     grid = grid < n_items ? grid : n_items;
-    k_svm_tc<<<grid, kThreads, sizeof(TcSmem), s>>>(hog_map, lbp_map, d_levels, d_items, n_items, d_queue, d_w,
-                                                    bias, clip, scores, c_flag, d_err);
+    if (hog_planes == 4 * kHogBins)
+        k_svm_tc<4 * kHogBins><<<grid, kThreads, sizeof(TcSmemT<4 * kHogBins>), s>>>(
+            hog_map, lbp_map, d_levels, d_items, n_items, d_queue, d_w, bias, clip, scores, c_flag, d_err);
+    else
+        k_svm_tc<kHogBins><<<grid, kThreads, sizeof(TcSmemT<kHogBins>), s>>>(
+            hog_map, lbp_map, d_levels, d_items, n_items, d_queue, d_w, bias, clip, scores, c_flag, d_err);
     return cudaGetLastError();
 }
 

@@ -46,11 +46,16 @@ const float kSparseTileCost[kSvmShapes] = {1.0f, 1e3f, 0.6f, 1e3f, 1e3f, 0.82f, 
 int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
 // Cell features a pipeline uses (Section 4.1: HOG-SVM, LBP-SVM or HOGLBP-SVM).
+// Per-block HOG (Algorithm 5 read per block) adds kFeatHogBlock.
 int features_of(int32_t flags) {
-    if (flags & PD_FLAG_HOG_ONLY) return kFeatHog;
+    const int blk = (flags & PD_FLAG_HOG_PER_BLOCK) ? kFeatHogBlock : 0;
+    if (flags & PD_FLAG_HOG_ONLY) return kFeatHog | blk;
     if (flags & PD_FLAG_LBP_ONLY) return kFeatLbp;
-    return kFeatHog | kFeatLbp;
+    return kFeatHog | kFeatLbp | blk;
 }
+
+// HOG planes of the cell atlas: 9 bins, or 4 places x 9 bins per cell.
+int hog_planes_of(int32_t flags) { return (flags & PD_FLAG_HOG_PER_BLOCK) ? 4 * kHogBins : kHogBins; }
 
 struct Plan {
     std::vector<FrameDesc> frames;
@@ -502,7 +507,8 @@ bool params_ok(const pd_params *p) {
            p->max_candidates_per_frame > 0 &&
            p->max_candidates_per_frame <= 65536 && p->max_frames > 0 && p->max_width > 0 &&
            p->max_height > 0 &&
-           (p->flags & (PD_FLAG_HOG_ONLY | PD_FLAG_LBP_ONLY)) != (PD_FLAG_HOG_ONLY | PD_FLAG_LBP_ONLY);
+           (p->flags & (PD_FLAG_HOG_ONLY | PD_FLAG_LBP_ONLY)) != (PD_FLAG_HOG_ONLY | PD_FLAG_LBP_ONLY) &&
+           !((p->flags & PD_FLAG_HOG_PER_BLOCK) && (p->flags & (PD_FLAG_SVM_FP32 | PD_FLAG_LBP_ONLY)));
 }
 
 // Packs the plan into the pinned staging buffer and sends it to the device.
@@ -550,12 +556,12 @@ int encode_svm_maps(CUtensorMap *hog_maps, CUtensorMap *lbp_maps, const float *h
     return PD_OK;
 }
 
-// The tensor-core K4's maps: one cell row of a 112-cell strip of the 9 HOG
-// planes, and of a 128-cell strip of the 59 LBP planes.
+// The tensor-core K4's maps: one cell row of a 112-cell strip of the 9 (or,
+// per-block HOG, 36) HOG planes, and of a 128-cell strip of the 59 LBP planes.
 int encode_tc_maps(CUtensorMap *hog_map, CUtensorMap *lbp_map, const float *hog, const uint8_t *lbp, int64_t pitch,
-                   int64_t rows, int64_t hog_plane, int64_t lbp_plane) {
+                   int64_t rows, int64_t hog_plane, int64_t lbp_plane, int hog_planes = kHogBins) {
     if (encode_plane_map(hog_map, const_cast<float *>(hog), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, pitch, rows,
-                         kHogBins, hog_plane, 112, 1, kHogBins) != PD_OK ||
+                         hog_planes, hog_plane, 112, 1, hog_planes) != PD_OK ||
         encode_plane_map(lbp_map, const_cast<uint8_t *>(lbp), CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, pitch, rows,
                          kLbpBins, lbp_plane, 128, 1, kLbpBins) != PD_OK)
         return PD_ECUDA;
@@ -782,7 +788,7 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
         {256, 0},                                                  // 1 lbp map
         {h->desc_cap, 0},                                          // 2 descriptors
         {h->pyr_cap, 0},                                           // 3 pyramid
-        {(int64_t)kHogBins * h->atlas.hog_plane * 4, 0},           // 4 hog atlas
+        {(int64_t)hog_planes_of(params->flags) * h->atlas.hog_plane * 4, 0},  // 4 hog atlas
         {(int64_t)kLbpBins * h->atlas.lbp_plane, 0},               // 5 lbp atlas
         {h->score_cap * 4, 0},                                     // 6 scores
         {(int64_t)params->max_frames * params->max_boxes_per_frame * (int64_t)sizeof(pd_box), 0},  // 7
@@ -871,7 +877,7 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
     if (encode_svm_maps(h->hog_map, h->lbp_map, h->atlas.hog, h->atlas.lbp, P, rows, h->atlas.hog_plane,
                         h->atlas.lbp_plane) != PD_OK ||
         encode_tc_maps(&h->tc_hog_map, &h->tc_lbp_map, h->atlas.hog, h->atlas.lbp, P, rows, h->atlas.hog_plane,
-                       h->atlas.lbp_plane) != PD_OK)
+                       h->atlas.lbp_plane, hog_planes_of(params->flags)) != PD_OK)
         return bail(PD_ECUDA);
     if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
         return bail(PD_ECUDA);
@@ -974,7 +980,7 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
             PD_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), q));
             PD_CUDA(h, launch_svm_tc(q, h->tc_hog_map, h->tc_lbp_map, dl, dptr<TcItem>(h, o.t_items),
                                      (int)p.t_items.size(), h->d_queue, h->sm_count, h->d_w, h->bias,
-                                     h->p.l2hys_clip, h->d_scores, cf, h->d_err));
+                                     h->p.l2hys_clip, h->d_scores, cf, h->d_err, hog_planes_of(h->p.flags)));
         }
         if (timed) PD_CUDA(h, record(h->stage_ev[3], q));
         PD_CUDA(h, launch_nms(q, df, dl, n_frames, h->d_scores, h->p.threshold, h->p.nms_iou,
@@ -1385,7 +1391,8 @@ int pd_cell_features(pd_handle *h, void *stream, const uint8_t *d_level, int Wk,
     a.pitch = cell_pitch;
     a.rows = Hc;
     PD_CUDA(h, launch_cells(s, dptr<LevelDesc>(h, o.levels), d_level, a, dptr<CellItem>(h, o.c_items),
-                            (int)p.c_items.size(), h->d_lbp_map));
+                            (int)p.c_items.size(), h->d_lbp_map, nullptr,
+                            kFeatHog | kFeatLbp | (features_of(h->p.flags) & kFeatHogBlock)));
     return PD_OK;
 }
 
@@ -1414,7 +1421,8 @@ int pd_window_scores(pd_handle *h, void *stream, const float *d_hog, int64_t hog
     CUtensorMap hm[kSvmShapes], lm[kSvmShapes], th, tl;
     const int64_t rows = std::max(cells_y, 1);
     if (encode_svm_maps(hm, lm, d_hog, d_lbp, cell_pitch, rows, hog_plane, lbp_plane) != PD_OK ||
-        encode_tc_maps(&th, &tl, d_hog, d_lbp, cell_pitch, rows, hog_plane, lbp_plane) != PD_OK)
+        encode_tc_maps(&th, &tl, d_hog, d_lbp, cell_pitch, rows, hog_plane, lbp_plane,
+                       hog_planes_of(h->p.flags)) != PD_OK)
         return fail(h, PD_ECUDA, "pd_window_scores: tensor map encoding failed");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Packed o;
@@ -1428,7 +1436,7 @@ int pd_window_scores(pd_handle *h, void *stream, const float *d_hog, int64_t hog
         PD_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), s));
         PD_CUDA(h, launch_svm_tc(s, th, tl, dptr<LevelDesc>(h, o.levels), dptr<TcItem>(h, o.t_items),
                                  (int)p.t_items.size(), h->d_queue, h->sm_count, h->d_w, h->bias,
-                                 h->p.l2hys_clip, d_scores, nullptr, h->d_err));
+                                 h->p.l2hys_clip, d_scores, nullptr, h->d_err, hog_planes_of(h->p.flags)));
     }
     return PD_OK;
 }

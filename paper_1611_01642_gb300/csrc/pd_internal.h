@@ -77,7 +77,7 @@ int svm_lbp_chunk();  // LBP planes per TMA box
 
 // Cell atlas: plane-major [plane][atlas_rows][pitch]; pitch in elements.
 struct CellAtlas {
-    float *hog;        // 9 planes
+    float *hog;        // 9 planes (36 for per-block HOG)
     uint8_t *lbp;      // 59 planes
     int64_t hog_plane; // elements per HOG plane
     int64_t lbp_plane; // elements per LBP plane
@@ -94,8 +94,10 @@ cudaError_t init_nms();
 cudaError_t launch_resize(cudaStream_t s, const FrameDesc *d_frames, const LevelDesc *d_levels,
                           const int32_t *d_tabs, uint8_t *pyr, const ResizeItem *d_items,
                           int n_items);
-// feat: kFeatHog | kFeatLbp (the features the pipeline uses)
-constexpr int kFeatHog = 1, kFeatLbp = 2;
+// feat: kFeatHog | kFeatLbp (the features the pipeline uses), plus
+// kFeatHogBlock for per-block HOG (36 planes: the 4 block-restricted
+// histograms of every cell, plane 9 q + bin)
+constexpr int kFeatHog = 1, kFeatLbp = 2, kFeatHogBlock = 4;
 cudaError_t launch_cells(cudaStream_t s, const LevelDesc *d_levels, const uint8_t *pyr,
                          CellAtlas atlas, const CellItem *d_items, int n_items, const uint8_t *d_lbp_map,
                          const uint32_t *c_flag = nullptr, int feat = kFeatHog | kFeatLbp);
@@ -109,13 +111,13 @@ cudaError_t launch_svm(cudaStream_t s, const CUtensorMap *hog_maps, const CUtens
 // Tensor-core K4: persistent CTAs (grid at most one per SM) over an item
 // queue (*d_queue must be 0 at launch); c_flag non-null selects the sparse
 // path. hog_map / lbp_map: 3-D maps over the cell planes with boxes of
-// 112 x 1 x 9 (f32) and 128 x 1 x 59 (u8).
+// 112 x 1 x hog_planes (f32; 9, or 36 for per-block HOG) and 128 x 1 x 59 (u8).
 cudaError_t init_svm_tc();
-int svm_tc_smem_bytes();
+int svm_tc_smem_bytes(int hog_planes = kHogBins);
 cudaError_t launch_svm_tc(cudaStream_t s, const CUtensorMap &hog_map, const CUtensorMap &lbp_map,
                           const LevelDesc *d_levels, const TcItem *d_items, int n_items, int *d_queue, int grid,
                           const float *d_w, float bias, float clip, float *scores, const uint32_t *c_flag,
-                          unsigned *d_err);
+                          unsigned *d_err, int hog_planes = kHogBins);
 // Per-frame NMS scratch (float4 units) for a candidate cap: the decoded
 // boxes, plus the sort keys when the cap is above 16,384 (shared memory
 // holds them below).

@@ -62,7 +62,9 @@ def test_create_rejects_bad_params_without_gpu(lib):
         pd.pd_create(p, np.zeros((15, 7, 95), np.float32), 0.0)
     assert e.value.code == pd.PD_EINVAL
     for bad in [dict(max_candidates_per_frame=65537), dict(upscale_levels=65),
-                dict(flags=pd.PD_FLAG_HOG_ONLY | pd.PD_FLAG_LBP_ONLY)]:
+                dict(flags=pd.PD_FLAG_HOG_ONLY | pd.PD_FLAG_LBP_ONLY),
+                dict(flags=pd.PD_FLAG_HOG_PER_BLOCK | pd.PD_FLAG_SVM_FP32),
+                dict(flags=pd.PD_FLAG_HOG_PER_BLOCK | pd.PD_FLAG_LBP_ONLY)]:
         p = pd.pd_params_default(**bad)
         with pytest.raises(pd.PDError) as e:
             pd.pd_create(p, np.zeros((15, 7, 95), np.float32), 0.0)
