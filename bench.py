@@ -222,9 +222,11 @@ def run_other_k4(args, pd, torch, frames, flush, w, b, fp32_peak, bf16_peak):
 
 def run_pipelines(args, pd, torch, frames, flush, w, b):
     """The paper's other two pipelines (Section 4.1) on the same batch: HOG-SVM and LBP-SVM (only
-    that feature's cells computed; windows scored with that feature's weights)."""
+    that feature's cells computed; windows scored with that feature's weights); and HOGLBP-SVM with
+    per-block HOG (Algorithm 5 read per 16x16 block: 36 HOG planes per cell, tensor-core K4)."""
     out = {}
-    for name, flag in (("hog_svm", pd.PD_FLAG_HOG_ONLY), ("lbp_svm", pd.PD_FLAG_LBP_ONLY)):
+    per_block = [("hoglbp_svm_per_block_hog", pd.PD_FLAG_HOG_PER_BLOCK)] if svm_flag(args, pd) == 0 else []
+    for name, flag in [("hog_svm", pd.PD_FLAG_HOG_ONLY), ("lbp_svm", pd.PD_FLAG_LBP_ONLY)] + per_block:
         det = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=len(frames), max_width=WIDTH, max_height=HEIGHT,
                           flags=pd.PD_FLAG_STAGE_TIMING | flag | svm_flag(args, pd))
         try:
@@ -262,8 +264,11 @@ def run_schemes(args, pd, torch, w, b):
         return float(np.median(ms))
 
     names = ["lbp_naive", "lbp_scalable", "hog_global", "hog_local", "hog_shared", "cells_fused",
-             "svm_naive", "svm_warp", "svm_fused"]
+             "svm_naive", "svm_warp", "svm_fused", "hog_block_global", "hog_block_local", "hog_block_shared",
+             "cells_fused_per_block", "svm_fused_per_block"]
     out = {n: [] for n in names}
+    det_pb = pd.Detector(w, b, max_frames=1, max_width=SCHEME_SIZES[-1][0], max_height=SCHEME_SIZES[-1][1],
+                         flags=pd.PD_FLAG_HOG_PER_BLOCK)
     try:
         for W, H in SCHEME_SIZES:
             L = torch.from_numpy(synth.random_image(W, H, W + H, smooth=True)).cuda()
@@ -286,10 +291,22 @@ def run_schemes(args, pd, torch, w, b):
                     det.h, sch, hog, plane, lbp, plane, cp, Wc, Hc, scores)) * 1e6))
             out["svm_fused"].append(px / (timed(lambda: pd.pd_window_scores(
                 det.h, hog, plane, lbp, plane, cp, Wc, Hc, scores)) * 1e6))
+            # per-block HOG (Algorithm 5 read per block): thread-per-block schemes, fused kernels
+            hog36 = torch.zeros((36 * plane,), dtype=torch.float32, device="cuda")
+            for n, sch in (("hog_block_global", pd.PD_SCHEME_HOG_GLOBAL), ("hog_block_local", pd.PD_SCHEME_HOG_LOCAL),
+                           ("hog_block_shared", pd.PD_SCHEME_HOG_SHARED)):
+                out[n].append(px / (timed(lambda: pd.pd_scheme_cells(det_pb.h, sch, L, hog36, plane, None, 0, cp))
+                                    * 1e6))
+            out["cells_fused_per_block"].append(
+                px / (timed(lambda: pd.pd_cell_features(det_pb.h, L, hog36, plane, lbp, plane, cp)) * 1e6))
+            out["svm_fused_per_block"].append(px / (timed(lambda: pd.pd_window_scores(
+                det_pb.h, hog36, plane, lbp, plane, cp, Wc, Hc, scores)) * 1e6))
     finally:
         det.close()
+        det_pb.close()
     return {"unit": "px/ns", "sizes": [f"{W}x{H}" for W, H in SCHEME_SIZES], "reps": args.scheme_reps,
-            "note": "cells_fused computes LBP and HOG together; svm_fused is the K4 the line runs", **out}
+            "note": "cells_fused computes LBP and HOG together; svm_fused is the K4 the line runs; "
+                    "*_per_block: per-block HOG (36 HOG planes per cell; tensor-core K4)", **out}
 
 
 def hbm_per_kernel(stage_ms, svm: str):

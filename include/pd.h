@@ -391,9 +391,12 @@ int pd_nms_noalloc(void *stream, const float *d_scores, int n_levels, const int3
  *                           split the products, shuffle reduction).
  * pd_scheme_cells writes the LBP planes (LBP schemes) or the HOG planes (HOG
  * schemes) in the layout of pd_cell_features; pd_scheme_window_scores takes
- * and returns what pd_window_scores does. Both allocate a scratch buffer on
- * first use (cudaMalloc; grown when a larger level comes, freed by
- * pd_destroy). Errors: PD_EINVAL (bad argument or scheme), PD_ENOMEM, PD_ECUDA. */
+ * and returns what pd_window_scores does. With PD_FLAG_HOG_PER_BLOCK the HOG
+ * schemes are Algorithm 5 as laid out in Section 4.3: one thread per 16x16
+ * block (Global / Local / Shared: where its 36-bin histogram lives), writing
+ * the 36-plane per-block layout, which the SVM schemes then read. Both
+ * allocate a scratch buffer on first use (cudaMalloc; grown when a larger
+ * level comes, freed by pd_destroy). Errors: PD_EINVAL (bad argument or scheme), PD_ENOMEM, PD_ECUDA. */
 #define PD_SCHEME_LBP_NAIVE 1
 #define PD_SCHEME_LBP_SCALABLE 2
 #define PD_SCHEME_HOG_GLOBAL 3

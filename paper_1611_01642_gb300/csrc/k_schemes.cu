@@ -4,7 +4,10 @@
 // kernels (clamped borders, uniform-LBP bins, one global cell grid with
 // bilinear votes, L2-Hys and L1-sqrt blocks), so that their results can be
 // checked against the same oracle and their speed compared with the fused
-// kernels. They are separate stages with materialised intermediates, as in
+// kernels. With per-block HOG the HOG schemes are Algorithm 5 as the paper
+// lays it out: one thread per 16x16 block walks its 256 pixels into a 36-bin
+// histogram (global, local or shared memory), written to the 36-plane
+// per-block layout that the fused cells kernel also produces. They are separate stages with materialised intermediates, as in
 // the paper: an LBP bin image, gradient magnitude / orientation images and a
 // block-feature array.
 #include "pd_internal.h"
@@ -142,10 +145,76 @@ __global__ void k_hog_cells(const float *__restrict__ mag, const float *__restri
         for (int b = 0; b < kHogBins; ++b) out[(int64_t)b * hog_plane] = sh[b][threadIdx.x];
 }
 
+// Per-block HOG histograms (Algorithm 5), one thread per block: its 16 x 16
+// pixels vote bilinearly towards the block's cell centres (local 3.5 and
+// 11.5), votes leaving the block dropped; the histogram lives in global
+// memory (MODE 0: the block's own 36 output values), a local array (1) or
+// shared memory (2). Output: place q of the block is plane 9 q + bin of cell
+// (by + q / 2, bx + q % 2).
+template <int MODE>
+__global__ void k_hog_blocks(const float *__restrict__ mag, const float *__restrict__ pos, int gw, int Wb, int Hb,
+                             float *__restrict__ hog, int64_t hog_plane, int cell_pitch) {
+    __shared__ float sh[MODE == 2 ? kHogDim : 1][kT];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Wb * Hb) return;
+    const int by = i / Wb, bx = i - by * Wb;
+    auto at = [&](int t) {  // output value t = 9 q + bin of this block
+        const int q = t / kHogBins;
+        return hog + (int64_t)t * hog_plane + (int64_t)(by + (q >> 1)) * cell_pitch + bx + (q & 1);
+    };
+    float loc[MODE == 1 ? kHogDim : 1];
+    for (int t = 0; t < kHogDim; ++t) {
+        if (MODE == 0) *at(t) = 0.f;
+        if (MODE == 1) loc[t] = 0.f;
+        if (MODE == 2) sh[t][threadIdx.x] = 0.f;
+    }
+    auto add = [&](int t, float v) {
+        if (MODE == 0) *at(t) += v;
+        if (MODE == 1) loc[t] += v;
+        if (MODE == 2) sh[t][threadIdx.x] += v;
+    };
+    for (int iy = 0; iy < 16; ++iy) {
+        const float uy = ((float)iy - 3.5f) * 0.125f;
+        const float fy = floorf(uy);
+        const float vy = uy - fy;
+        const int a0 = (int)fy;  // -1, 0 or 1; a0 + 1 in 0..2
+        for (int ix = 0; ix < 16; ++ix) {
+            const float ux = ((float)ix - 3.5f) * 0.125f;
+            const float fx = floorf(ux);
+            const float vx = ux - fx;
+            const int c0 = (int)fx;
+            const size_t p = (size_t)(8 * by + iy) * gw + 8 * bx + ix;
+            const float bp = pos[p], m = mag[p];
+            const float bf = floorf(bp);
+            const float o1 = bp - bf;
+            const int bi = (int)bf;
+            const int b0 = bi < 0 ? kHogBins - 1 : bi, b1 = bi + 1 >= kHogBins ? 0 : bi + 1;
+            for (int da = 0; da < 2; ++da) {
+                const int a = a0 + da;
+                if (a < 0 || a > 1) continue;
+                const float wa = da ? vy : 1.f - vy;
+                for (int db = 0; db < 2; ++db) {
+                    const int b = c0 + db;
+                    if (b < 0 || b > 1) continue;
+                    const float w = m * wa * (db ? vx : 1.f - vx);
+                    add((2 * a + b) * kHogBins + b0, w * (1.f - o1));
+                    add((2 * a + b) * kHogBins + b1, w * o1);
+                }
+            }
+        }
+    }
+    if (MODE == 1)
+        for (int t = 0; t < kHogDim; ++t) *at(t) = loc[t];
+    if (MODE == 2)
+        for (int t = 0; t < kHogDim; ++t) *at(t) = sh[t][threadIdx.x];
+}
+
 // Block features, one thread per block: the 2 x 2 cells' 36 HOG values with
 // L2-Hys, then the summed LBP counts with L1-sqrt (a block holds 256 pixels).
+// qs = 9 reads the per-block layout (cell of place q from planes 9 q ..).
 __global__ void k_blocks(const float *__restrict__ hog, int64_t hog_plane, const uint8_t *__restrict__ lbp,
-                         int64_t lbp_plane, int cell_pitch, int Wb, int Hb, float clip, float *__restrict__ feat) {
+                         int64_t lbp_plane, int cell_pitch, int Wb, int Hb, float clip, int qs,
+                         float *__restrict__ feat) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= Wb * Hb) return;
     const int by = i / Wb, bx = i - by * Wb;
@@ -153,7 +222,8 @@ __global__ void k_blocks(const float *__restrict__ hog, int64_t hog_plane, const
     float s = 0.f;
     for (int q = 0; q < 4; ++q)
         for (int b = 0; b < kHogBins; ++b) {
-            const float v = hog[(int64_t)b * hog_plane + (int64_t)(by + (q >> 1)) * cell_pitch + bx + (q & 1)];
+            const float v =
+                hog[(int64_t)(qs * q + b) * hog_plane + (int64_t)(by + (q >> 1)) * cell_pitch + bx + (q & 1)];
             f[9 * q + b] = v;
             s += v * v;
         }
@@ -215,7 +285,7 @@ size_t scheme_cells_scratch(int Wk, int Hk) {
 
 cudaError_t launch_scheme_cells(cudaStream_t s, int scheme, const uint8_t *img, int Wk, int Hk, int pitch, float *hog,
                                 int64_t hog_plane, uint8_t *lbp, int64_t lbp_plane, int cell_pitch,
-                                const uint8_t *bin_of, unsigned char *scratch) {
+                                const uint8_t *bin_of, unsigned char *scratch, bool per_block) {
     const int Wc = Wk / 8, Hc = Hk / 8, gw = 8 * Wc, gh = 8 * Hc;
     if (Wc == 0 || Hc == 0) return cudaSuccess;
     uint8_t *codes = scratch;
@@ -236,7 +306,16 @@ cudaError_t launch_scheme_cells(cudaStream_t s, int scheme, const uint8_t *img, 
         }
     } else {
         k_gradient<<<pix, kT, 0, s>>>(img, Wk, Hk, pitch, gw, gh, mag, pos);
-        if (scheme == PD_SCHEME_HOG_GLOBAL)
+        const int Wb = Wc - 1, Hb = Hc - 1, blk = (Wb * Hb + kT - 1) / kT;
+        if (per_block) {
+            if (Wb <= 0 || Hb <= 0) return cudaGetLastError();
+            if (scheme == PD_SCHEME_HOG_GLOBAL)
+                k_hog_blocks<0><<<blk, kT, 0, s>>>(mag, pos, gw, Wb, Hb, hog, hog_plane, cell_pitch);
+            else if (scheme == PD_SCHEME_HOG_LOCAL)
+                k_hog_blocks<1><<<blk, kT, 0, s>>>(mag, pos, gw, Wb, Hb, hog, hog_plane, cell_pitch);
+            else
+                k_hog_blocks<2><<<blk, kT, 0, s>>>(mag, pos, gw, Wb, Hb, hog, hog_plane, cell_pitch);
+        } else if (scheme == PD_SCHEME_HOG_GLOBAL)
             k_hog_cells<0><<<cells_blocks, kT, 0, s>>>(mag, pos, gw, gh, Wc, Hc, hog, hog_plane, cell_pitch);
         else if (scheme == PD_SCHEME_HOG_LOCAL)
             k_hog_cells<1><<<cells_blocks, kT, 0, s>>>(mag, pos, gw, gh, Wc, Hc, hog, hog_plane, cell_pitch);
@@ -252,11 +331,13 @@ size_t scheme_scores_scratch(int cells_x, int cells_y) {
 
 cudaError_t launch_scheme_scores(cudaStream_t s, int scheme, const float *hog, int64_t hog_plane,
                                  const uint8_t *lbp, int64_t lbp_plane, int cell_pitch, int cells_x, int cells_y,
-                                 const float *wt, float bias, float clip, float *scores, unsigned char *scratch) {
+                                 const float *wt, float bias, float clip, float *scores, unsigned char *scratch,
+                                 bool per_block) {
     const int Wb = cells_x - 1, Hb = cells_y - 1, rows = cells_y - kWinBH, cols = cells_x - kWinBW;
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     float *feat = reinterpret_cast<float *>(scratch);
-    k_blocks<<<(Wb * Hb + kT - 1) / kT, kT, 0, s>>>(hog, hog_plane, lbp, lbp_plane, cell_pitch, Wb, Hb, clip, feat);
+    k_blocks<<<(Wb * Hb + kT - 1) / kT, kT, 0, s>>>(hog, hog_plane, lbp, lbp_plane, cell_pitch, Wb, Hb, clip,
+                                                    per_block ? kHogBins : 0, feat);
     if (scheme == PD_SCHEME_SVM_NAIVE)
         k_svm_naive<<<(rows * cols + kT - 1) / kT, kT, 0, s>>>(feat, Wb, wt, bias, rows, cols, scores);
     else

@@ -1510,7 +1510,8 @@ int pd_scheme_cells(pd_handle *h, void *stream, int scheme, const uint8_t *d_lev
     int r = scheme_scratch(h, s, scheme_cells_scratch(Wk, Hk));
     if (r != PD_OK) return r;
     PD_CUDA(h, launch_scheme_cells(s, scheme, d_level, Wk, Hk, pitch, d_hog, hog_plane, d_lbp, lbp_plane,
-                                   cell_pitch, h->d_lbp_map, h->scheme_ws));
+                                   cell_pitch, h->d_lbp_map, h->scheme_ws,
+                                   (h->p.flags & PD_FLAG_HOG_PER_BLOCK) != 0));
     return PD_OK;
 }
 
@@ -1526,7 +1527,8 @@ int pd_scheme_window_scores(pd_handle *h, void *stream, int scheme, const float 
     int r = scheme_scratch(h, s, scheme_scores_scratch(cells_x, cells_y));
     if (r != PD_OK) return r;
     PD_CUDA(h, launch_scheme_scores(s, scheme, d_hog, hog_plane, d_lbp, lbp_plane, cell_pitch, cells_x, cells_y,
-                                    h->d_w, h->bias, h->p.l2hys_clip, d_scores, h->scheme_ws));
+                                    h->d_w, h->bias, h->p.l2hys_clip, d_scores, h->scheme_ws,
+                                    (h->p.flags & PD_FLAG_HOG_PER_BLOCK) != 0));
     return PD_OK;
 }
 

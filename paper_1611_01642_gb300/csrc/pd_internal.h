@@ -135,11 +135,12 @@ cudaError_t launch_nms(cudaStream_t s, const FrameDesc *d_frames, const LevelDes
 size_t scheme_cells_scratch(int Wk, int Hk);
 cudaError_t launch_scheme_cells(cudaStream_t s, int scheme, const uint8_t *img, int Wk, int Hk, int pitch, float *hog,
                                 int64_t hog_plane, uint8_t *lbp, int64_t lbp_plane, int cell_pitch,
-                                const uint8_t *bin_of, unsigned char *scratch);
+                                const uint8_t *bin_of, unsigned char *scratch, bool per_block);
 size_t scheme_scores_scratch(int cells_x, int cells_y);
 cudaError_t launch_scheme_scores(cudaStream_t s, int scheme, const float *hog, int64_t hog_plane,
                                  const uint8_t *lbp, int64_t lbp_plane, int cell_pitch, int cells_x, int cells_y,
-                                 const float *wt, float bias, float clip, float *scores, unsigned char *scratch);
+                                 const float *wt, float bias, float clip, float *scores, unsigned char *scratch,
+                                 bool per_block);
 
 // ---- learned window proposal
 constexpr int kCnnParams = 14210;  // flat order: w1 b1 w2 b2 w3 b3 wh bh v bv

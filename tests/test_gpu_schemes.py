@@ -103,3 +103,64 @@ def test_scheme_arguments_are_checked(det):
     assert e.value.code == pd.PD_EINVAL
     with pytest.raises(pd.PDError):  # an LBP scheme without LBP planes
         pd.pd_scheme_cells(h.h, pd.PD_SCHEME_LBP_NAIVE, L, None, 0, None, 32, 16)
+
+
+@pytest.fixture(scope="module")
+def det_pb():
+    from paper_1611_01642_gb300 import build as bld
+    bld.build()
+    d = np.load(os.path.join(ROOT, "tests", "golden", "svm_template_seed0.npz"))
+    h = pd.Detector(d["w"], float(d["b"]), max_frames=1, max_width=64, max_height=128,
+                    flags=pd.PD_FLAG_HOG_PER_BLOCK)
+    yield h, d["w"], float(d["b"])
+    h.close()
+
+
+@pytest.mark.parametrize("scheme", [pd.PD_SCHEME_HOG_GLOBAL, pd.PD_SCHEME_HOG_LOCAL, pd.PD_SCHEME_HOG_SHARED])
+@pytest.mark.parametrize("W,H", [(16, 16), (23, 17), (130, 200), (640, 480)])
+def test_hog_block_schemes_within_tolerance(det_pb, scheme, W, H):
+    # Algorithm 5 as the paper lays it out: one thread per block histogram
+    h, _, _ = det_pb
+    L = synth.random_image(W, H, 13 * W + H, smooth=W > 100)
+    Hc, Wc = H // 8, W // 8
+    cp, plane = _planes(Hc, Wc)
+    hog = torch.full((36 * plane,), float("nan"), dtype=torch.float32, device="cuda")
+    pd.pd_scheme_cells(h.h, scheme, torch.from_numpy(L).cuda(), hog, plane, None, 0, cp)
+    torch.cuda.synchronize()
+    q = hog.cpu().numpy().reshape(4, 9, max(Hc, 1), cp)[:, :, :Hc, :Wc]
+    got = np.concatenate([q[0, :, :-1, :-1], q[1, :, :-1, 1:], q[2, :, 1:, :-1], q[3, :, 1:, 1:]],
+                         axis=0).transpose(1, 2, 0)
+    ref = oracle.hog_blocks(L)
+    tol = HOG_TOL * ref.sum(axis=2, keepdims=True) + 1e-6
+    assert np.all(np.abs(got - ref) <= tol), float(np.max(np.abs(got - ref) - tol))
+
+
+@pytest.mark.parametrize("scheme", [pd.PD_SCHEME_SVM_NAIVE, pd.PD_SCHEME_SVM_WARP])
+def test_svm_schemes_on_per_block_planes(det_pb, scheme):
+    h, w, b = det_pb
+    W, H = 300, 260
+    L = synth.random_image(W, H, 17, smooth=True)
+    hb = oracle.hog_blocks(L).astype(np.float32)
+    lbp = oracle.lbp_cells(L)
+    feat = oracle.block_features_pb(hb.astype(np.float64), lbp)
+    ref = oracle.scores(feat, w, b)
+    Hc, Wc = lbp.shape[:2]
+    cp, plane = _planes(Hc, Wc)
+    q = np.zeros((4, 9, Hc, cp), np.float32)
+    t = hb.transpose(2, 0, 1).reshape(4, 9, Hc - 1, Wc - 1)
+    q[0, :, :-1, :Wc - 1] = t[0]
+    q[1, :, :-1, 1:Wc] = t[1]
+    q[2, :, 1:, :Wc - 1] = t[2]
+    q[3, :, 1:, 1:Wc] = t[3]
+    lp = np.zeros((59, Hc, cp), np.uint8)
+    lp[:, :, :Wc] = lbp.transpose(2, 0, 1)
+    rows, cols = ref.shape
+    out = torch.full((rows * cols,), float("nan"), dtype=torch.float32, device="cuda")
+    pd.pd_scheme_window_scores(h.h, scheme, torch.from_numpy(q.ravel()).cuda(), plane,
+                               torch.from_numpy(lp.ravel()).cuda(), plane, cp, Wc, Hc, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().reshape(rows, cols).astype(np.float64)
+    wabs = np.abs(w.astype(np.float64))
+    scale = np.abs(b) + np.array([[np.sum(np.abs(feat[y:y + 15, x:x + 7]) * wabs) for x in range(cols)]
+                                  for y in range(rows)])
+    assert np.all(np.abs(got - ref) <= SCORE_TOL * scale), float(np.max(np.abs(got - ref) / scale))
