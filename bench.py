@@ -75,7 +75,12 @@ def parse_args(argv=None):
                     help="timed steps of the same batch with the other window-score kernel (0: skip)")
     ap.add_argument("--upscale-steps", type=int, default=10,
                     help="timed steps of the same batch with 17 upsampled levels (40 levels per frame; 0: skip)")
-    return ap.parse_args(argv)
+    ap.add_argument("--hog-per-block", action="store_true",
+                    help="main step with per-block HOG (Algorithm 5 read per 16x16 block; tensor-core K4 only)")
+    args = ap.parse_args(argv)
+    if args.hog_per_block and args.svm == "fp32":
+        ap.error("--hog-per-block needs the tensor-core K4 (--svm tc)")
+    return args
 
 
 def dist_env():
@@ -119,6 +124,11 @@ def make_frames(indices):
 
 def svm_flag(args, pd) -> int:
     return pd.PD_FLAG_SVM_FP32 if args.svm == "fp32" else 0
+
+
+def main_flags(args, pd) -> int:
+    """Flags of the main step's detectors: the K4 kernel, and per-block HOG if asked for."""
+    return svm_flag(args, pd) | (pd.PD_FLAG_HOG_PER_BLOCK if args.hog_per_block else 0)
 
 
 def cells_per_frame() -> int:
@@ -548,7 +558,7 @@ def run_gpu(args):
     w, b = load_template()
     imgs = make_frames(rank_frame_indices(rank, B))
     det = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=B, max_width=WIDTH, max_height=HEIGHT,
-                      flags=pd.PD_FLAG_STAGE_TIMING | svm_flag(args, pd))
+                      flags=pd.PD_FLAG_STAGE_TIMING | main_flags(args, pd))
     stream = torch.cuda.current_stream()
     frames = [torch.from_numpy(im).cuda() for im in imgs]
     pinned = [torch.from_numpy(im).pin_memory() for im in imgs]
@@ -598,7 +608,7 @@ def run_gpu(args):
     # later of the two streams' events after the last; a handle is reused only
     # after its previous step has been synced (its arena holds the results).
     det_b = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=B, max_width=WIDTH, max_height=HEIGHT,
-                        flags=pd.PD_FLAG_STAGE_TIMING | svm_flag(args, pd))
+                        flags=pd.PD_FLAG_STAGE_TIMING | main_flags(args, pd))
     pd.pd_set_tile_costs(det_b.h, tile_costs)
     streams = [stream, torch.cuda.Stream()]
     pipe = [det, det_b]
@@ -641,7 +651,7 @@ def run_gpu(args):
     # step i+1 already runs (each step still copies its frames in and its
     # boxes out inside the timed region).
     det2 = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=B, max_width=WIDTH, max_height=HEIGHT,
-                       flags=svm_flag(args, pd))
+                       flags=main_flags(args, pd))
     pd.pd_set_tile_costs(det2.h, tile_costs)
     for _ in range(2):
         det2.detect_host(pinned, stream=streams[1])
@@ -684,7 +694,8 @@ def run_gpu(args):
     cells_ach = cells_ops / (stage_step[1] / 1e3) / 1e12
     roof_cells = {"bound": "alu", "achieved": cells_ach, "peak": lane_peak, "unit": "Tops/s",
                   "frac": cells_ach / lane_peak,
-                  "traffic": recorded_traffic("k_cells_1242x375_b64.txt", "k_cells.cu"),
+                  "traffic": None if args.hog_per_block else recorded_traffic("k_cells_1242x375_b64.txt",
+                                                                              "k_cells.cu"),
                   "kernel": "k_cells (uniform LBP + soft-binned HOG cell histograms)",
                   "peak_basis": f"{sm_count} SMs x 128 lanes x {sm_mhz} MHz, one op per lane slot "
                                 f"({OPS_PER_CELL_PIXEL} algorithmic ops per cell-grid pixel; max SM clock, "
@@ -703,14 +714,16 @@ def run_gpu(args):
         executed = B * tc_units_per_frame() * TC_FLOP_PER_UNIT / k4_s / 1e12
         roof_k4 = {"bound": "tensor", "achieved": k4_ach, "peak": bf16, "unit": "TFLOP/s",
                    "frac": k4_ach / bf16, "executed_tflops": executed, "executed_frac": executed / bf16,
-                   "traffic": recorded_traffic("k_svm_tc_1242x375_b64.txt", "k_svm_tc.cu"),
+                   "traffic": None if args.hog_per_block else recorded_traffic("k_svm_tc_1242x375_b64.txt",
+                                                                               "k_svm_tc.cu"),
                    "kernel": "k_svm_tc (block norms + window scores as bf16-split tcgen05 GEMMs)",
                    "peak_basis": f"bf16 dense, cuBLAS burst ({peak_kind}); achieved counts the "
                                  f"definition's 19,950 flop per window, executed the MMAs issued "
                                  f"(3 bf16 terms, padding, strip halo)"}
     stage_names = ["k_resize", "k_cells", "k_svm_tc" if args.svm != "fp32" else "k_svm", "k_nms"]
     dominant = stage_names[int(np.argmax(stage_step[:4]))]
-    hbm = hbm_per_kernel(stage_step[:4], args.svm)
+    # (the recorded DRAM bytes are those of the default shared-cell kernels)
+    hbm = None if args.hog_per_block else hbm_per_kernel(stage_step[:4], args.svm)
     for name, roof in (("k_cells", roof_cells), (stage_names[2], roof_k4)):
         if roof["traffic"] is None and hbm and hbm.get(name):
             roof["traffic"] = hbm[name]["dram_bytes"]
@@ -751,7 +764,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": value / PAPER_FPS_1242x375, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{WIDTH}x{HEIGHT} u8 frames, pyramid factor 1.05 (23 levels), "
-                               "plain HOG+LBP+SVM+NMS",
+                               "plain HOG+LBP+SVM+NMS" + (", per-block HOG" if args.hog_per_block else ""),
                    "timing": "K steps on two detector handles alternating on two streams (step i+1 may "
                              "overlap step i); serial: the same K steps on one handle, each timed alone",
                    "frames_per_step": B * world, "frames_per_gpu": B, "windows_per_frame": wpf,
