@@ -439,9 +439,9 @@ def _file_hash(path: str) -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def recorded_traffic(profile: str, source: str):
-    """DRAM bytes per launch (scaled to the bench's 64-frame batch) from a committed ncu summary,
-    if the kernel's source is unchanged since the capture."""
+def recorded_traffic(profile: str, source: str, key: str = "dram_bytes_per_launch"):
+    """DRAM bytes per launch (scaled to the bench's 64-frame batch), or another recorded figure
+    (`key`), from a committed ncu summary, if the kernel's source is unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", profile)
     src = os.path.join(ROOT, "paper_1611_01642_gb300", "csrc", source)
     if not os.path.exists(path):
@@ -455,7 +455,7 @@ def recorded_traffic(profile: str, source: str):
     if rec.get("source_sha256_16") != _file_hash(src):
         return None
     try:
-        return float(rec["dram_bytes_per_launch"])
+        return float(rec[key])
     except (KeyError, ValueError):
         return None
 
@@ -699,7 +699,11 @@ def run_gpu(args):
                   "kernel": "k_cells (uniform LBP + soft-binned HOG cell histograms)",
                   "peak_basis": f"{sm_count} SMs x 128 lanes x {sm_mhz} MHz, one op per lane slot "
                                 f"({OPS_PER_CELL_PIXEL} algorithmic ops per cell-grid pixel; max SM clock, "
-                                f"{peak_kind})"}
+                                f"{peak_kind})",
+                  # ncu, same source: fraction of cycles the schedulers issued (the kernel runs ~3.6
+                  # instructions per algorithmic op: addressing, shared-memory traffic, control)
+                  "issue_active_frac": None if args.hog_per_block else recorded_traffic(
+                      "k_cells_1242x375_b64.txt", "k_cells.cu", "issue_active_frac")}
     # window scores (K4)
     k4_s = stage_step[2] / 1e3
     if args.svm == "fp32":
@@ -716,6 +720,8 @@ def run_gpu(args):
                    "frac": k4_ach / bf16, "executed_tflops": executed, "executed_frac": executed / bf16,
                    "traffic": None if args.hog_per_block else recorded_traffic("k_svm_tc_1242x375_b64.txt",
                                                                                "k_svm_tc.cu"),
+                   "tensor_active_frac": None if args.hog_per_block else recorded_traffic(
+                       "k_svm_tc_1242x375_b64.txt", "k_svm_tc.cu", "tensor_active_frac"),
                    "kernel": "k_svm_tc (block norms + window scores as bf16-split tcgen05 GEMMs)",
                    "peak_basis": f"bf16 dense, cuBLAS burst ({peak_kind}); achieved counts the "
                                  f"definition's 19,950 flop per window, executed the MMAs issued "

@@ -153,10 +153,10 @@ def _box_rows(a):
     return [tuple(r) for r in a.tolist()]
 
 
-@pytest.mark.parametrize("flags", [0, pd.PD_FLAG_SVM_FP32])
+@pytest.mark.parametrize("flags", [0, pd.PD_FLAG_SVM_FP32, pd.PD_FLAG_HOG_PER_BLOCK])
 def test_sparse_threshold_minus_inf_equals_plain(template, flags):
     """With every window kept, the sparse path returns the plain path's scores and boxes bit for bit
-    (tensor-core and FP32 window-score kernels)."""
+    (tensor-core and FP32 window-score kernels, and per-block HOG)."""
     from paper_1611_01642_gb300 import build as bld
     bld.build()
     w, b = template
@@ -181,13 +181,13 @@ def test_sparse_threshold_minus_inf_equals_plain(template, flags):
         d.close()
 
 
-@pytest.mark.parametrize("flags", [0, pd.PD_FLAG_SVM_FP32])
+@pytest.mark.parametrize("flags", [0, pd.PD_FLAG_SVM_FP32, pd.PD_FLAG_HOG_PER_BLOCK])
 @pytest.mark.parametrize("quantile", [0.9, 0.999, 1.0])
 def test_sparse_path_skips_only_unkept_tiles(template, quantile, flags):
     """Windows with keep-logit above the threshold are scored exactly; skipped ones are -inf and
     none of them has a logit above the threshold; the boxes are the oracle NMS of the sparse maps;
     the logits are those of the proposal network run level by level (tensor-core and FP32
-    window-score kernels)."""
+    window-score kernels, and per-block HOG)."""
     from paper_1611_01642_gb300 import build as bld
     bld.build()
     w, b = template

@@ -113,3 +113,41 @@ def test_4k_mixed_batch_plain_and_sparse(template):
         assert 0.0 < keep < 1.0
     finally:
         det.close()
+
+
+def test_bench_batch_per_block_hog_sampled_windows_match_oracle(template):
+    """The benchmark's batch (64 x 1242x375, factor 1.05, 23 levels) with per-block HOG, replayed
+    from the captured graph: sampled windows of sampled levels against the oracle's per-block
+    features (Algorithm 5 read per block) within the score bar."""
+    from paper_1611_01642_gb300 import build as bld
+    bld.build()
+    w, b = template
+    imgs = [synth.make_scene(1242, 375, 2, 900 + i) for i in range(64)]
+    det = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=64, max_width=1242, max_height=375,
+                      flags=pd.PD_FLAG_HOG_PER_BLOCK)
+    try:
+        dev = [torch.from_numpy(im).cuda() for im in imgs]
+        for _ in range(3):
+            det.detect(dev)
+            assert det.sync() == pd.PD_OK
+        rng = np.random.default_rng(11)
+        checked = 0
+        for f in [0, 17, 63]:
+            lv = det.levels(f)
+            maps = det.score_maps(f)
+            valid = [k for k, l in enumerate(lv) if l["rows"] > 0]
+            for k in sorted(set([valid[0], valid[-1], int(rng.choice(valid))])):
+                L = oracle.resize(imgs[f], lv[k]["width"], lv[k]["height"])
+                feat = oracle.block_features_pb(oracle.hog_blocks(L), oracle.lbp_cells(L))
+                m = maps[k].cpu().numpy()
+                picks = [(0, 0), (lv[k]["rows"] - 1, lv[k]["cols"] - 1)]
+                picks += [(int(rng.integers(lv[k]["rows"])), int(rng.integers(lv[k]["cols"]))) for _ in range(4)]
+                for wy, wx in picks:
+                    x = feat[wy:wy + 15, wx:wx + 7]
+                    ref = b + float(np.sum(x * w))
+                    scale = abs(b) + float(np.sum(np.abs(x * w)))
+                    assert abs(float(m[wy, wx]) - ref) <= SCORE_TOL * scale, (f, k, wy, wx)
+                    checked += 1
+        assert checked >= 40
+    finally:
+        det.close()
