@@ -11,18 +11,19 @@
 //
 // Per pixel:
 //  * LBP (Algorithm 1): 8 comparisons with the clockwise neighbours (a
-//    neighbour >= centre gives 1), uniform-pattern bin via a 256-entry table,
-//    and a shared-memory integer count of its own cell (Algorithm 2; integer
-//    atomics on two 16-bit counters per word, so the counts are exact and
-//    order independent).
+//    neighbour >= centre gives 1), and a shared-memory integer count of its
+//    own cell (Algorithm 2; integer atomics on two 16-bit counters per word,
+//    so the counts are exact and order independent); a 256-entry table maps
+//    the code straight to its uniform bin's counter word and increment.
 //  * HOG (Algorithm 4): central differences with clamped borders, magnitude
 //    sqrt(gx^2 + gy^2), unsigned orientation in [0, 180). The orientation is
 //    evaluated directly in bin units: the gradient is folded into the upper
 //    half plane, reduced to an octant so that z = min/max in [0, 1], and
 //    atan(z) comes from an odd polynomial z*P(z^2) of degree 13 whose
 //    coefficients were fitted for this kernel (weighted least squares on
-//    Chebyshev nodes of [0, 1]); its float32 evaluation is within 3.4e-7 rad
-//    (2e-5 degrees, 1e-6 of a bin) of the true arctangent, and the vote is
+//    Chebyshev nodes of [0, 1]) and then scaled to bin units; its float32
+//    evaluation is within 1e-6 of a bin (2e-5 degrees) of the true
+//    arctangent, and the vote is
 //    continuous in the angle, so the histogram error stays far below the
 //    1e-4 parity bar.
 //    The vote is linear between the two nearest of 9 orientation bins and
@@ -81,23 +82,24 @@ struct CellSmem {
     float WA[kCols];                        // per column: weight of its vote to the left cell of its group
     float WB[kCols];                        // per column: weight of its vote to its group's own cell
     uint32_t cnt[kRing][kTW][kLbpWords];    // LBP counts of the open cell rows
-    uint8_t map[256];                       // LBP code -> uniform bin
+    uint2 map[256];                         // LBP code -> (counter word byte offset, increment)
     uint8_t pix[kPixRows][kPixCols];        // [8cy0-5, 8cy0+69) x [8cx0-5, 8cx0+125), clamped
 };
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
-// atan(z) * 9/pi (radians -> 20-degree bins) for z in [0, 1].
+// atan(z) * 9/pi (radians -> 20-degree bins) for z in [0, 1]: the fitted
+// polynomial's coefficients scaled by 9/pi and rounded to float.
 __device__ __forceinline__ float atan_bins01(float z) {
     const float s = z * z;
-    float p = 0.0068117850460112095f;
-    p = fmaf(p, s, -0.03360419720411301f);
-    p = fmaf(p, s, 0.07962365448474884f);
-    p = fmaf(p, s, -0.1323334127664566f);
-    p = fmaf(p, s, 0.19807815551757812f);
-    p = fmaf(p, s, -0.3331736922264099f);
-    p = fmaf(p, s, 0.9999961256980896f);
-    return p * z * 2.8647889756541160f;  // 9/pi
+    float p = 0.019514326006174088f;
+    p = fmaf(p, s, -0.09626893699169159f);
+    p = fmaf(p, s, 0.22810496389865875f);
+    p = fmaf(p, s, -0.3791072964668274f);
+    p = fmaf(p, s, 0.5674521327018738f);
+    p = fmaf(p, s, -0.9544723033905029f);
+    p = fmaf(p, s, 2.8647778034210205f);
+    return p * z;
 }
 
 // Unsigned orientation of (gx, gy) in bin units: theta_degrees / 20, in
@@ -106,7 +108,9 @@ __device__ __forceinline__ float atan_bins01(float z) {
 __device__ __forceinline__ float orientation_bins(int gx, int gy) {
     const int ax = abs(gx), ay = abs(gy);
     const float mx = (float)max(ax, ay), mn = (float)min(ax, ay);
-    const float z = mx > 0.f ? __fdividef(mn, mx) : 0.f;
+    // mx is 0 or >= 1, so adding 1e-30 changes nothing but the 0 / 0 case
+    // (which becomes 0 without a branch)
+    const float z = __fdividef(mn, mx + 1e-30f);
     float phi = atan_bins01(z);                // angle of (|gx|, |gy|) to the nearer axis
     if (ay > ax) phi = 4.5f - phi;             // 90 degrees - phi
     return (gx ^ gy) < 0 ? 9.0f - phi : phi;   // opposite signs: mirror into (90, 180)
@@ -135,7 +139,11 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
 
     for (int i = tid; i < kRing * NA * kHogBins * kRPitch; i += kThreads) (&S.R[0][0][0][0])[i] = 0.f;
     for (int i = tid; i < kRing * kTW * kLbpWords; i += kThreads) (&S.cnt[0][0][0])[i] = 0u;
-    for (int i = tid; i < 256; i += kThreads) S.map[i] = lbp_map[i];
+    for (int i = tid; i < 256; i += kThreads) {
+        // uniform bin -> its 16-bit counter: word (byte offset) and increment
+        const int bn = lbp_map[i];
+        S.map[i] = make_uint2((uint32_t)(bn >> 1) * 4u, 1u << ((bn & 1) << 4));
+    }
     const int px0 = 8 * it.cx0 - 5, py0 = 8 * it.cy0 - 5;
     for (int r = tid; r < kPixRows; r += kThreads) {
         // row y votes into cell rows floor(u), floor(u)+1 (u = (y-3.5)/8,
@@ -217,7 +225,8 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
                     const int gx = br - bl;
                     const int gy = cm - am;
                     const float m2 = (float)(gx * gx + gy * gy);
-                    const float mag = m2 > 0.f ? m2 * rsqrtf(m2) : 0.f;
+                    // m2 is 0 or >= 1: the 1e-30 only turns 0 * inf into 0
+                    const float mag = m2 * rsqrtf(m2 + 1e-30f);
                     // bpos in [-0.5, 8.5]: floor in [-1, 8], so b0 = -1 wraps to 8
                     // and b1 = 9 to 0 (bpos -0.5 and 8.5 give the same votes)
                     const float bpos = orientation_bins(gx, gy) - 0.5f;
@@ -280,8 +289,8 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
                         const int code = (al >= c) | ((am >= c) << 1) | ((ar >= c) << 2) |
                                          ((br >= c) << 3) | ((cr >= c) << 4) | ((cm >= c) << 5) |
                                          ((cl >= c) << 6) | ((bl >= c) << 7);
-                        const int bin = S.map[code];
-                        atomicAdd(&S.cnt[cyl & 1][cxl][bin >> 1], 1u << ((bin & 1) << 4));
+                        const uint2 e = S.map[code];
+                        atomicAdd(reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(&S.cnt[cyl & 1][cxl][0]) + e.x), e.y);
                     }
                 }
                 al = bl; am = bm; ar = br;
