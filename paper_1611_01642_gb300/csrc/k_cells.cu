@@ -5,7 +5,7 @@
 // first stages the 130 x 74 pixel region it reads (the tile, the 4 pixels on
 // each side whose HOG votes still reach it, and the 1-pixel gradient halo,
 // with the level's clamp-to-edge border baked in) in shared memory with one
-// burst of coalesced loads. Thread t then owns pixel column
+// burst of coalesced 16-byte loads. Thread t then owns pixel column
 // x = 8*cx0 - 4 + t and walks down the rows [8*cy0 - 4, 8*cy0 + 68) with its
 // 3x3 neighbourhood in registers.
 //
@@ -68,7 +68,7 @@ constexpr int kThreads = 128;
 constexpr int kTW = kCellTW;          // 15 cells
 constexpr int kTH = kCellTH;          // 8 cells
 constexpr int kCols = 8 * kTW + 8;    // 128 columns (one per thread)
-constexpr int kPixCols = kCols + 2;   // + gradient / LBP halo
+constexpr int kPixCols = kCols + 16;  // + gradient / LBP halo, from a 16-byte boundary
 constexpr int kPixRows = 8 * kTH + 10;
 constexpr int kRing = 2;              // open cell rows
 constexpr int kRPitch = kCols;                 // bin stride: a multiple of 32 banks
@@ -83,7 +83,7 @@ struct CellSmem {
     float WB[kCols];                        // per column: weight of its vote to its group's own cell
     uint32_t cnt[kRing][kTW][kLbpWords];    // LBP counts of the open cell rows
     uint2 map[256];                         // LBP code -> (counter word byte offset, increment)
-    uint8_t pix[kPixRows][kPixCols];        // [8cy0-5, 8cy0+69) x [8cx0-5, 8cx0+125), clamped
+    uint8_t pix[kPixRows][kPixCols];        // rows [8cy0-5, 8cy0+69) x columns from xs, clamped
 };
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
@@ -163,23 +163,42 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
         e.w = __float_as_int(w1);
         S.yv[r] = e;
     }
-    static_assert(kPixCols <= 2 * kThreads, "two staged columns per thread at most");
+    static_assert(kPixCols % 16 == 0 && kPixCols >= kCols + 13, "16-byte chunks covering the halo");
+    // Staging: rows [py0, py0 + kPixRows) and the 144 columns from
+    // xs = 8 cx0 - 8 rounded down to a multiple of 16 (they hold the 130
+    // columns [px0, px0 + 130) the tile reads), in 16-byte chunks: one
+    // 16-byte load each where the chunk lies inside the level row (and the
+    // level is 16-byte aligned), else byte loads clamped to the level.
+    const int xs = (px0 - 3) & ~15;
     {
-        const int c0 = tid, c1 = tid + kThreads;
-        const int x0c = clampi(px0 + c0, 0, Wk - 1);
-        const int x1c = clampi(px0 + c1, 0, Wk - 1);
-#pragma unroll 8
-        for (int r = 0; r < kPixRows; ++r) {
-            const uint8_t *p = img + (size_t)clampi(py0 + r, 0, Hk - 1) * pitch;
-            S.pix[r][c0] = p[x0c];
-            if (c1 < kPixCols) S.pix[r][c1] = p[x1c];
+        constexpr int kChunks = kPixCols / 16;
+        const bool al = ((reinterpret_cast<uintptr_t>(img) | (uintptr_t)pitch) & 15u) == 0;
+        for (int i = tid; i < kPixRows * kChunks; i += kThreads) {
+            const int r = i / kChunks, q = i - r * kChunks;
+            const int x0 = xs + 16 * q;
+            const uint8_t *row = img + (size_t)clampi(py0 + r, 0, Hk - 1) * pitch;
+            uint4 v;
+            if (al && x0 >= 0 && x0 + 16 <= Wk) {
+                v = *reinterpret_cast<const uint4 *>(row + x0);
+            } else {
+                uint32_t wv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    uint32_t wd = 0;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) wd |= (uint32_t)row[clampi(x0 + 4 * k + j, 0, Wk - 1)] << (8 * j);
+                    wv[k] = wd;
+                }
+                v = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            }
+            reinterpret_cast<uint4 *>(S.pix[r])[q] = v;
         }
     }
     __syncthreads();
 
     const int x = 8 * it.cx0 - 4 + tid;
     const bool active = x >= 0 && x < gridW;
-    const int sc = x - px0;  // shared-memory column of x
+    const int sc = x - xs;  // shared-memory column of x
     const bool core_x = (x >= 8 * it.cx0) && (x < 8 * it.cx0 + 8 * kTW);
     const int cxl = (x >> 3) - it.cx0;
     const int rc = tid;
@@ -236,7 +255,7 @@ __global__ void __launch_bounds__(kThreads) k_cells(const LevelDesc *__restrict_
                     const int b0 = bi < 0 ? kHogBins - 1 : bi;
                     const int b1 = bi + 1 >= kHogBins ? 0 : bi + 1;
                     const int4 yv = S.yv[y - py0];
-                    const float mo0 = mag * o0, mo1 = mag * o1;
+                    const float mo1 = mag * o1, mo0 = mag - mo1;
                     if constexpr (!pb) {
                         if (yv.x >= 0) {
                             const float w = __int_as_float(yv.z);
