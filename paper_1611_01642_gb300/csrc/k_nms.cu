@@ -8,7 +8,10 @@
 //     so ascending keys = score descending, then level, wy, wx ascending);
 //     with a candidate cap above 16,384 the key list lives in the frame's
 //     global scratch instead (same steps, slower sort);
-//  2. bitonic-sorts the keys;
+//  2. sorts the keys: a bitonic sort in shared memory, or, for caps above
+//     16,384, bitonic sorts of 8,192-key chunks in shared memory followed by
+//     merge passes over the global key list (each thread merges its slice
+//     of outputs after locating it by binary search on the two runs);
 //  3. decodes every candidate's box once (exactly rounded float division)
 //     into shared memory (over the no longer needed key array, whose keys
 //     move to a per-frame global scratch array) or, for very many
@@ -123,6 +126,81 @@ __device__ __forceinline__ bool suppresses(const float4 &a, const float4 &b, flo
     return iou4(a, b) > (double)thr;
 }
 
+constexpr int kSortChunk = 8192;  // keys per shared-memory chunk of the large-cap sort (64 KB)
+
+// Ascending bitonic sort of m (a power of two) keys in shared memory.
+__device__ __forceinline__ void bitonic_smem(unsigned long long *k, int m, int tid) {
+    for (int len = 2; len <= m; len <<= 1) {
+        for (int j = len >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < m; i += kThreads) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long a = k[i], b = k[ixj];
+                    if ((a > b) == ((i & len) == 0)) {
+                        k[i] = b;
+                        k[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Large caps: keys[0, np) (np a power of two >= n, padded with ~0) sorted
+// ascending: chunks of up to kSortChunk keys sorted in shared memory `sm`,
+// then merge passes doubling the run length, ping-ponging through `tmp`
+// (np keys); the result ends in keys.
+__device__ void sort_large(unsigned long long *keys, unsigned long long *tmp, int np,
+                           unsigned long long *sm, int tid) {
+    const int C = np < kSortChunk ? np : kSortChunk;
+    for (int c0 = 0; c0 < np; c0 += C) {
+        for (int i = tid; i < C; i += kThreads) sm[i] = keys[c0 + i];
+        __syncthreads();
+        bitonic_smem(sm, C, tid);
+        for (int i = tid; i < C; i += kThreads) keys[c0 + i] = sm[i];
+        __syncthreads();
+    }
+    unsigned long long *src = keys, *dst = tmp;
+    const int per = np / kThreads;  // outputs per thread (np >= 2 C here, so per divides every pair)
+    for (int w = C; w < np; w <<= 1) {
+        const int o0 = tid * per;
+        const int base = o0 & ~(2 * w - 1), d = o0 - base;
+        const unsigned long long *A = src + base, *B = src + base + w;
+        // i = keys taken from A among the pair's first d outputs (A first on ties)
+        int lo = d > w ? d - w : 0, hi = d < w ? d : w;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (A[mid] <= B[d - 1 - mid])
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        int i = lo, j = d - lo;
+        unsigned long long a = i < w ? A[i] : ~0ull, b = j < w ? B[j] : ~0ull;
+        for (int k = 0; k < per; ++k) {
+            const bool take_a = j >= w || (i < w && a <= b);
+            if (take_a) {
+                dst[o0 + k] = a;
+                ++i;
+                a = i < w ? A[i] : ~0ull;
+            } else {
+                dst[o0 + k] = b;
+                ++j;
+                b = j < w ? B[j] : ~0ull;
+            }
+        }
+        __syncthreads();
+        unsigned long long *t = src;
+        src = dst;
+        dst = t;
+    }
+    if (src != keys) {
+        for (int i = tid; i < np; i += kThreads) keys[i] = src[i];
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ frames,
                                                   const LevelDesc *__restrict__ levels,
                                                   const float *__restrict__ scores, float threshold,
@@ -193,24 +271,15 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
     int np = 1;
     while (np < n) np <<= 1;
     for (int i = n + tid; i < np; i += kThreads) keys[i] = ~0ull;
+    __syncthreads();
+    if (big) {
+        // the boxes region (cap float4s) is free until the decode below
+        sort_large(keys, reinterpret_cast<unsigned long long *>(gbx), np, skeys, tid);
+    } else {
+        bitonic_smem(keys, np, tid);
+    }
     for (int i = tid; i < n; i += kThreads) supp[i] = 0;
     __syncthreads();
-    for (int k = 2; k <= np; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < np; i += kThreads) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const unsigned long long a = keys[i], b = keys[ixj];
-                    const bool up = (i & k) == 0;
-                    if ((a > b) == up) {
-                        keys[i] = b;
-                        keys[ixj] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
     // Decoded boxes: in shared memory when they fit in the key region (the
     // keys then move to the global scratch, where only kept ones are read
     // again), otherwise in the global scratch. Each greedy pass reads every
@@ -348,7 +417,10 @@ size_t nms_smem(int cap, int max_boxes) {
     int p = 1;
     while (p < cap) p <<= 1;
     const size_t keys = cap > kMaxCandidates ? 0 : (size_t)p * sizeof(unsigned long long);
-    return keys + (size_t)((cap + 15) & ~15) + 4 * (size_t)max_boxes;
+    const size_t walk = keys + (size_t)((cap + 15) & ~15) + 4 * (size_t)max_boxes;
+    // large caps: the sort's key chunks use the same shared memory first
+    const size_t chunk = cap > kMaxCandidates ? (size_t)kSortChunk * sizeof(unsigned long long) : 0;
+    return walk > chunk ? walk : chunk;
 }
 
 }  // namespace
