@@ -25,8 +25,9 @@
 //    A operand straight into tensor memory (tcgen05.st: row m = lane m, two
 //    bf16 per column), row m holding block wx0 + 26 (m / 32) + m % 32: warps
 //    0-3 the 36 values of its 2x2 HOG cells (L2-Hys, bf16 split) and LBP
-//    bins 0..19, warps 4-7 LBP bins 20..58 (the 2 x 2 count sums, L1-sqrt
-//    and its bf16 split from a 512-entry table). Every group of 32 rows
+//    bins 0..9, warps 4-7 LBP bins 10..58 (the 2 x 2 count sums, L1-sqrt
+//    and its bf16 split from a 512-entry table; the split balances the two
+//    groups' work per row). Every group of 32 rows
 //    covers 26 windows and the 6 blocks to their right, so the j terms of a
 //    window stay inside one warp of the epilogue;
 //  * one thread (lane 0 of the first epilogue warp, between its epilogue
@@ -75,6 +76,7 @@ constexpr uint32_t kTmemCols = 512;   // two accumulator buffers of 128 columns,
 constexpr uint32_t kTmemA = 256;      // first A stage column (bf16 pairs: high parts 0..47, low 48..95)
 constexpr uint64_t kWaitNs = 1000000000ull;
 constexpr int kProducerBarrier = 1;   // named barrier of the producer warps
+constexpr int kHogLbpPairs = 5;       // LBP bin pairs built by the HOG warps (the LBP warps take the rest)
 static_assert(4 * kWinPerWarp == kTcStrip, "strip width");
 static_assert(kWinPerWarp + kWinBW - 1 <= 32, "window blocks inside a warp");
 
@@ -200,6 +202,12 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
     lo = l;
 }
 // this thread's TMEM lane: 4, 8 or 16 consecutive 32-bit columns from taddr
+__device__ __forceinline__ void tst1(uint32_t t, const uint32_t *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(t), "r"(v[0]) : "memory");
+}
+__device__ __forceinline__ void tst2(uint32_t t, const uint32_t *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};" ::"r"(t), "r"(v[0]), "r"(v[1]) : "memory");
+}
 __device__ __forceinline__ void tst4(uint32_t t, const uint32_t *v) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(t), "r"(v[0]), "r"(v[1]),
                  "r"(v[2]), "r"(v[3])
@@ -235,11 +243,11 @@ __device__ __forceinline__ void lbp_pairs(const Slot &s0, const Slot &s1, const 
     }
 }
 
-// Features 0..55 of A row m into its TMEM lane (columns a + f / 2 for the high
+// Features 0..45 of A row m into its TMEM lane (columns a + f / 2 for the high
 // parts, a + 48 + f / 2 for the low parts): the 36 HOG values of its cells
 // (r, c), (r, c+1), (r+1, c), (r+1, c+1) (slots s0 = row r, s1 = row r + 1) in
 // the template's order (cells TL, TR, BL, BR, 9 bins each), L2-Hys, bf16
-// split; then LBP bins 0..19 (LBP column cl).
+// split; then LBP bins 0..9 (LBP column cl).
 template <class Slot>
 __device__ __forceinline__ void build_hog(const Slot &s0, const Slot &s1, const uint32_t *tab, int c, int cl,
                                           float clip, uint32_t a) {
@@ -270,26 +278,31 @@ __device__ __forceinline__ void build_hog(const Slot &s0, const Slot &s1, const 
     for (int p = 0; p < 16; ++p) split2(v[2 * p] * i2, v[2 * p + 1] * i2, hi[p], lo[p]);
     tst16(a, hi);        // features 0..31
     tst16(a + 48, lo);
-    // features 32..55: HOG 32..35, LBP bins 0..19
+    // features 32..35 (HOG) and the first kHogLbpPairs LBP bin pairs
     split2(v[32] * i2, v[33] * i2, hi[0], lo[0]);
     split2(v[34] * i2, v[35] * i2, hi[1], lo[1]);
-    lbp_pairs<0, 10>(s0, s1, tab, cl, hi + 2, lo + 2);
-    tst8(a + 16, hi);
-    tst4(a + 24, hi + 8);
-    tst8(a + 64, lo);
-    tst4(a + 72, lo + 8);
+    static_assert(kHogLbpPairs == 5, "TMEM column split");
+    lbp_pairs<0, kHogLbpPairs>(s0, s1, tab, cl, hi + 2, lo + 2);  // columns 16..22
+    tst4(a + 16, hi);
+    tst2(a + 20, hi + 4);
+    tst1(a + 22, hi + 6);
+    tst4(a + 64, lo);
+    tst2(a + 68, lo + 4);
+    tst1(a + 70, lo + 6);
 }
 
-// Features 56..95 of A row m (LBP bins 20..58 and the zero pad): columns
-// a + 28 .. a + 47 and a + 76 .. a + 95.
+// Features 46..95 of A row m (LBP bins 10..58 and the zero pad): columns
+// a + 23 .. a + 47 and a + 71 .. a + 95.
 template <class Slot>
 __device__ __forceinline__ void build_lbp(const Slot &s0, const Slot &s1, const uint32_t *tab, int cl, uint32_t a) {
-    uint32_t hi[20], lo[20];
-    lbp_pairs<20, 20>(s0, s1, tab, cl, hi, lo);
-    tst4(a + 28, hi);
-    tst16(a + 32, hi + 4);
-    tst4(a + 76, lo);
-    tst16(a + 80, lo + 4);
+    uint32_t hi[25], lo[25];
+    lbp_pairs<2 * kHogLbpPairs, 30 - kHogLbpPairs>(s0, s1, tab, cl, hi, lo);  // bins 10..59: columns 23..47
+    tst1(a + 23, hi);
+    tst8(a + 24, hi + 1);
+    tst16(a + 32, hi + 9);
+    tst1(a + 71, lo);
+    tst8(a + 72, lo + 1);
+    tst16(a + 80, lo + 9);
 }
 
 // In place, by the 256 producer threads: LBP count c[t][x] -> c[t][x] +
@@ -472,8 +485,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             };
 
             if (warp < kProducers) {
-                // ---- producers: warps 0-3 HOG and LBP bins 0..19, warps 4-7
-                // LBP bins 20..58, for rows 32 (w % 4) + lane
+                // ---- producers: warps 0-3 HOG and LBP bins 0..9, warps 4-7
+                // LBP bins 10..58, for rows 32 (w % 4) + lane
                 const bool is_lbp = warp >= 4;
                 const int m = 32 * (warp & 3) + lane;
                 const int c = kWinPerWarp * (m >> 5) + (m & 31);
