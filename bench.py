@@ -696,7 +696,8 @@ def run_gpu(args):
                   "frac": cells_ach / lane_peak,
                   "traffic": None if args.hog_per_block else recorded_traffic("k_cells_1242x375_b64.txt",
                                                                               "k_cells.cu"),
-                  "kernel": "k_cells (uniform LBP + soft-binned HOG cell histograms)",
+                  "kernel": "k_cells (uniform LBP + soft-binned HOG cell histograms)" + (
+                      "; per-block HOG variant, ops still counted as for shared cells" if args.hog_per_block else ""),
                   "peak_basis": f"{sm_count} SMs x 128 lanes x {sm_mhz} MHz, one op per lane slot "
                                 f"({OPS_PER_CELL_PIXEL} algorithmic ops per cell-grid pixel; max SM clock, "
                                 f"{peak_kind})",
