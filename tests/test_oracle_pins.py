@@ -683,3 +683,25 @@ def test_detect_per_block_matches_stagewise_composition():
     for (wk, hk), sc in zip(ref["levels"], ref["scores"]):
         L = oracle.resize(img, wk, hk)
         assert np.array_equal(sc, oracle.level_all(L, w["w"], float(w["b"]), per_block=True)[3])
+
+
+def test_hog_blocks_brute_force_tent_form_on_a_tiny_image():
+    # the same histograms from a different form of the definition: each cell
+    # of a block weighs a pixel by the tent max(0, 1 - |l - centre| / 8) on each
+    # axis (centres at local 3.5 and 11.5), summed over the block's 256 pixels
+    # only; orientation from the oracle's own pinned vote
+    img = synth.random_image(32, 24, 26, smooth=False)
+    hb = oracle.hog_blocks(img)
+    Hb, Wb = hb.shape[:2]
+    tent = lambda d: max(0.0, 1.0 - abs(d) / 8.0)
+    for by in range(Hb):
+        for bx in range(Wb):
+            ref = np.zeros(36)
+            for i in range(16):
+                for j in range(16):
+                    m, th = oracle.gradient(img, 8 * bx + j, 8 * by + i)
+                    for (o, wo) in oracle.orientation_vote(th):
+                        for a in range(2):
+                            for b in range(2):
+                                ref[(2 * a + b) * 9 + o] += m * wo * tent(i - (3.5 + 8 * a)) * tent(j - (3.5 + 8 * b))
+            assert np.allclose(hb[by, bx], ref, rtol=0, atol=1e-9 * max(1.0, ref.sum())), (by, bx)
