@@ -398,7 +398,13 @@ def pd_logits(h):
 
 # ----------------------------------------------------------------------------- convenience
 class Detector:
-    """Owns a pd_handle: ``Detector(w, b, max_frames=..., max_width=..., ...)``."""
+    """Owns a pd_handle: ``Detector(w, b, max_frames=..., max_width=..., ...)``.
+
+    Keyword arguments are pd_params fields (pyr_factor, upscale_levels, threshold,
+    nms_iou, max_boxes_per_frame, max_candidates_per_frame, flags, ...). flags
+    selects the pipeline (PD_FLAG_HOG_ONLY, PD_FLAG_LBP_ONLY), per-block HOG
+    (PD_FLAG_HOG_PER_BLOCK), the FP32 window-score kernel (PD_FLAG_SVM_FP32)
+    and per-stage timing (PD_FLAG_STAGE_TIMING)."""
 
     def __init__(self, svm_w, svm_b, **params):
         self.params = pd_params_default(**params)
