@@ -405,6 +405,74 @@ void order_tc(std::vector<TcItem> &t) {
                      [](const TcItem &a, const TcItem &b) { return a.wy1 - a.wy0 > b.wy1 - b.wy0; });
 }
 
+// K1 tables of one level (Section 4.4 resample, reading Q).
+//   ytab: per output row its Q11 entry (source row << 11 | weight);
+//   ybnd: per source-tile row t, the first output row whose source row is >= 32 t;
+//   xtab: per group of G output columns (G = 4; G = 1 when a group of 4
+//         would reach more than kResizeBW - 2 source columns past the left
+//         edge of the tile that owns it), an int4 of the packed column
+//         weights (2048 - a) | a << 16 (lanes past G are 0);
+//   xq:   per group one word: byte i = index of column i's source quad in the
+//         owner tile's shared-memory quad row (resize_quad_index of its source
+//         column relative to the tile). Columns past the level's width repeat
+//         its last column;
+//   xbnd: per source-tile column t, the first group whose first column's
+//         source index is >= 128 t (the owner of a group is that tile).
+void k1_tables(Plan &p, LevelDesc &L, int W, int H, int Wk, int Hk) {
+    std::vector<int32_t> ex(Wk);
+    for (int x = 0; x < Wk; ++x) ex[x] = q11_entry(x, W, Wk);
+    auto src = [&](int x) { return ex[std::min(x, Wk - 1)] >> 11; };
+    auto span_of = [&](int G) {
+        int span = 0;
+        for (int g = 0; g * G < Wk; ++g) {
+            const int owner = src(g * G) / kResizeTW;
+            for (int i = 0; i < G; ++i) span = std::max(span, src(g * G + i) - owner * kResizeTW + 2);
+        }
+        return span;
+    };
+    int G = 4, span = span_of(4);
+    if (span > kResizeBW) {
+        G = 1;
+        span = span_of(1);
+    }
+    L.rgroup = G;
+    L.rspan = span;
+    const int groups = (Wk + G - 1) / G;
+    while (p.tabs.size() % 4) p.tabs.push_back(0);
+    L.xtab_off = (int32_t)p.tabs.size();
+    for (int g = 0; g < groups; ++g)
+        for (int i = 0; i < 4; ++i) {
+            const int a = ex[std::min(g * G + i, Wk - 1)] & 2047;
+            p.tabs.push_back(i < G ? (int32_t)((uint32_t)(2048 - a) | ((uint32_t)a << 16)) : 0);
+        }
+    L.xq_off = (int32_t)p.tabs.size();
+    for (int g = 0; g < groups; ++g) {
+        const int owner = src(g * G) / kResizeTW;
+        uint32_t w = 0;
+        for (int i = 0; i < G; ++i)
+            w |= (uint32_t)resize_quad_index(src(g * G + i) - owner * kResizeTW) << (8 * i);
+        p.tabs.push_back((int32_t)w);
+    }
+    L.ytab_off = (int32_t)p.tabs.size();
+    for (int y = 0; y < Hk; ++y) p.tabs.push_back(q11_entry(y, H, Hk));
+    L.xbnd_off = (int32_t)p.tabs.size();
+    {
+        int g = 0;
+        for (int t = 0; t <= (W + kResizeTW - 1) / kResizeTW; ++t) {
+            while (g < groups && src(g * G) < t * kResizeTW) ++g;
+            p.tabs.push_back(g);
+        }
+    }
+    L.ybnd_off = (int32_t)p.tabs.size();
+    {
+        int y = 0;
+        for (int t = 0; t <= (H + kResizeTH - 1) / kResizeTH; ++t) {
+            while (y < Hk && (p.tabs[L.ytab_off + y] >> 11) < t * kResizeTH) ++y;
+            p.tabs.push_back(y);
+        }
+    }
+}
+
 // Adds one level to the plan (tables, descriptor, work items).
 void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int64_t img_off,
                 int32_t img_pitch, const LevelDesc *share = nullptr,
@@ -430,24 +498,11 @@ void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int
         L.ytab_off = share->ytab_off;
         L.xbnd_off = share->xbnd_off;
         L.ybnd_off = share->ybnd_off;
+        L.rgroup = share->rgroup;
+        L.rspan = share->rspan;
+        L.xq_off = share->xq_off;
     } else {
-        L.xtab_off = (int32_t)p.tabs.size();
-        for (int x = 0; x < Wk; ++x) p.tabs.push_back(q11_entry(x, W, Wk));
-        L.ytab_off = (int32_t)p.tabs.size();
-        for (int y = 0; y < Hk; ++y) p.tabs.push_back(q11_entry(y, H, Hk));
-        // K1 output ranges of every source tile: boundaries t * tile of the
-        // (non-decreasing) source index, t = 0 .. ceil(n / tile)
-        auto bounds = [&](int32_t tab_off, int n_out, int n_src, int tile) {
-            const int32_t at = (int32_t)p.tabs.size();
-            int x = 0;
-            for (int t = 0; t <= (n_src + tile - 1) / tile; ++t) {
-                while (x < n_out && (p.tabs[tab_off + x] >> 11) < t * tile) ++x;
-                p.tabs.push_back(x);
-            }
-            return at;
-        };
-        L.xbnd_off = bounds(L.xtab_off, Wk, W, kResizeTW);
-        L.ybnd_off = bounds(L.ytab_off, Hk, H, kResizeTH);
+        k1_tables(p, L, W, H, Wk, Hk);
     }
     const int li = (int)p.levels.size();
     L.citem0 = (int32_t)p.c_items.size();
@@ -460,6 +515,13 @@ void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int
     p.score_floats += (int64_t)L.rows * L.cols;
     p.max_wc = std::max(p.max_wc, L.Wc);
     p.levels.push_back(L);
+}
+
+// Source bytes K1 stages per tile row of a frame: what its levels need.
+int32_t staged_bytes(const Plan &p, const FrameDesc &fd) {
+    int32_t bw = 2;
+    for (int k = 0; k < fd.n_levels; ++k) bw = std::max(bw, p.levels[fd.first_level + k].rspan);
+    return bw;
 }
 
 // Plans one frame with the pyramid rule; returns PD_OK or an error.
@@ -493,6 +555,7 @@ int plan_frame(Plan &p, const pd_params &prm, const uint8_t *ptr, int W, int H, 
                     for (int cx = 0; cx < L.Wc; cx += kCnnTile) p.cnn_items.push_back({li, cy, cx, 0});
         }
     }
+    fd.rbw = staged_bytes(p, fd);
     if (n > 0)
         for (int y = 0; y < H; y += kResizeTH)
             for (int x = 0; x < W; x += kResizeTW) p.r_items.push_back({f, x, y, 0});
@@ -719,7 +782,8 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
         return code;
     };
     if (cudaGetDevice(&h->device) != cudaSuccess) return bail(PD_ECUDA);
-    if (init_cells() != cudaSuccess || init_svm() != cudaSuccess || init_svm_tc() != cudaSuccess ||
+    if (init_resize() != cudaSuccess || init_cells() != cudaSuccess || init_svm() != cudaSuccess ||
+        init_svm_tc() != cudaSuccess ||
         init_nms() != cudaSuccess ||
         init_cnn() != cudaSuccess)
         return bail(PD_ECUDA);
@@ -1350,6 +1414,7 @@ int pd_resize_levels(pd_handle *h, void *stream, const uint8_t *d_frame, int W, 
             return fail(h, PD_EINVAL, "pd_resize_levels: level %d size %dx%d", k, Wk[k], Hk[k]);
         plan_level(p, 0, k, W, H, Wk[k], Hk[k], level_offsets[k], level_pitches[k]);
     }
+    fd.rbw = staged_bytes(p, fd);
     for (int y = 0; y < H; y += kResizeTH)
         for (int x = 0; x < W; x += kResizeTW) p.r_items.push_back({0, x, y, 0});
     p.frames.push_back(fd);

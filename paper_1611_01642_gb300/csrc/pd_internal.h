@@ -28,7 +28,7 @@ struct FrameDesc {
     const uint8_t *ptr;
     int32_t W, H, pitch;
     int32_t first_level, n_levels;  // range in the LevelDesc table
-    int32_t pad;
+    int32_t rbw;                    // K1: source bytes staged per tile row (max of the levels' rspan)
 };
 
 // One (frame, level).
@@ -43,12 +43,17 @@ struct LevelDesc {
     int32_t img_pitch;  // bytes
     int32_t cell_row;   // first row of this level in the cell atlas
     int32_t rows, cols; // score map size (0 when no window fits)
-    int32_t xtab_off;   // Q11 source-column table of this level (Wk entries)
-    int32_t ytab_off;   // Q11 source-row table of this level (Hk entries)
+    int32_t xtab_off;   // K1 column weights: per group of rgroup output columns an int4 of packed
+                        // weights (2048 - a) | a << 16 (16-byte aligned; unused lanes 0)
+    int32_t ytab_off;   // Q11 source-row table of this level (Hk entries: row << 11 | weight)
     int32_t citem0;     // index of this level's first K2+K3 item
     int32_t ctx;        // K2+K3 tiles per row of cells
-    int32_t xbnd_off;   // per K1 source-tile column t: first output column whose source is >= 128 t
+    int32_t xbnd_off;   // per K1 source-tile column t: first column group whose first source is >= 128 t
     int32_t ybnd_off;   // per K1 source-tile row t: first output row whose source is >= 32 t
+    int32_t rgroup;     // K1 output columns per group: 4, or 1 when a group of 4 reaches past the halo
+    int32_t rspan;      // K1 source bytes a tile row needs for this level (<= kResizeBW)
+    int32_t xq_off;     // K1 column quads: per group one word, byte i = quad index of column i
+    int32_t pad;
 };
 
 // Work items (one CTA each).
@@ -60,6 +65,9 @@ struct TcItem { int32_t level, wx0, wy0, wy1; };     // tensor-core K4: window c
 // Tiles.
 constexpr int kResizeTW = 128;  // source tile width  (pixels)
 constexpr int kResizeTH = 32;   // source tile height (pixels)
+constexpr int kResizeBW = 160;  // source bytes staged per tile row at most (tile + right halo)
+// K1 shared-memory quad word of source column d of a tile row (skewed by d / 32)
+__host__ __device__ inline int resize_quad_index(int d) { return d + (d >> 5); }
 constexpr int kCellTW = 15;     // cells per cell tile along x (128 threads = 8*15+8 columns)
 constexpr int kCellTH = 8;      // cells per cell tile along y
 constexpr int kSvmShapes = 7;   // K4 tile shapes: 32x16, 64x8, 32x8, 64x4, 64x2, 32x12, 32x4 windows
@@ -89,6 +97,7 @@ struct CellAtlas {
 cudaError_t init_cells();
 cudaError_t init_svm();
 cudaError_t init_nms();
+cudaError_t init_resize();
 
 // Kernel launchers (host functions defined next to their kernels).
 cudaError_t launch_resize(cudaStream_t s, const FrameDesc *d_frames, const LevelDesc *d_levels,
