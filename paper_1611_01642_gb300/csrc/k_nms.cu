@@ -16,11 +16,11 @@
 //     into shared memory (over the no longer needed key array, whose keys
 //     move to a per-frame global scratch array) or, for very many
 //     candidates, into that global scratch;
-//  4. walks the candidates in order in batches of the next 32 not yet
-//     suppressed: warp 0 resolves a batch in order (pairwise suppression
-//     bits, then kept iff no kept earlier member suppresses it), and all
-//     threads then suppress the later candidates against the batch's kept
-//     members. This takes the same decisions as the one-at-a-time greedy
+//  4. walks the candidates in order in batches of the next 64 not yet
+//     suppressed: all threads compute the batch's pairwise suppression bits,
+//     warp 0 resolves the batch (kept iff no kept earlier member suppresses
+//     it), and all threads then suppress the later candidates against the
+//     batch's kept members (their boxes staged in shared memory). This takes the same decisions as the one-at-a-time greedy
 //     walk (candidates between batch members are already suppressed).
 // The IoU test first evaluates the IoU in float. For boxes of this detector
 // (width >= 64, height >= 128, coordinates < 8192) the float value is within
@@ -45,6 +45,8 @@ constexpr int kThreads = 1024;
 constexpr int kMaxCandidates = 16384;     // keys + flags + kept list fit in shared memory
 constexpr int kMaxCandidatesBig = 65536;  // keys in global scratch
 constexpr int kMaxBoxes = 16384;
+constexpr int kBatch = 64;                // greedy walk: candidates resolved per block-wide step
+static_assert(kThreads == 16 * kBatch, "pairwise matrix: 16 threads per batch member");
 
 __device__ __forceinline__ unsigned long long make_key(float s, int level, int wy, int wx) {
     const uint32_t u = __float_as_uint(s);
@@ -306,14 +308,17 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
         ksrc = keys;
     }
     __syncthreads();
-    // Greedy walk in batches. Warp 0 takes the next (up to) 32 candidates not
-    // yet suppressed, in order, computes their pairwise suppression bits and
-    // resolves them in order exactly as the one-at-a-time walk would (a member
-    // is kept iff no kept member before it suppresses it: the candidates
-    // between members are already suppressed); then every thread suppresses
-    // the later candidates against the batch's kept members. Same decisions
-    // as the sequential definition, with ~32x fewer block-wide barriers.
-    __shared__ int batch[32], kbatch[32];
+    // Greedy walk in batches. Warp 0 takes the next (up to) 64 candidates not
+    // yet suppressed, in order, and copies their boxes to shared memory; all
+    // threads compute the batch's pairwise suppression bits (4 pairs each);
+    // warp 0 resolves the members (a member is kept iff no kept member before
+    // it suppresses it: the candidates between members are already
+    // suppressed), and copies the kept boxes to shared memory; then every
+    // thread suppresses the later candidates against them. Same decisions as
+    // the sequential definition, with ~64x fewer block-wide barriers.
+    __shared__ int batch[kBatch], kbatch[kBatch];
+    __shared__ float4 bbx[kBatch], kbx[kBatch];
+    __shared__ unsigned long long bcol[kBatch];  // member b: bit a set iff a < b and a suppresses b
     __shared__ int n_batch, n_keep, kept_total, scan_pos;
     int *kept_idx = reinterpret_cast<int *>(supp + ((cap + 15) & ~15));
     const int warp = tid >> 5, lane = tid & 31;
@@ -325,13 +330,16 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
     while (true) {
         if (warp == 0) {
             int pos = scan_pos, cnt = 0;
-            while (cnt < 32 && pos < n) {
+            while (cnt < kBatch && pos < n) {
                 const int j = pos + lane;
                 const bool alive = j < n && !supp[j];
                 const unsigned m = __ballot_sync(0xffffffffu, alive);
-                const int avail = __popc(m), take = min(avail, 32 - cnt);
+                const int avail = __popc(m), take = min(avail, kBatch - cnt);
                 const int rank = __popc(m & ((1u << lane) - 1u));
-                if (alive && rank < take) batch[cnt + rank] = j;
+                if (alive && rank < take) {
+                    batch[cnt + rank] = j;
+                    bbx[cnt + rank] = bx[j];
+                }
                 cnt += take;
                 if (take < avail) {  // stop right after the last member taken
                     const unsigned last = __ballot_sync(0xffffffffu, alive && rank == take - 1);
@@ -348,30 +356,60 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
         __syncthreads();
         const int nb = n_batch;
         if (nb == 0) break;
-        if (warp == 0) {
-            const int me = lane < nb ? batch[lane] : 0;
-            const float4 bme = bx[me];
-            unsigned row = 0;  // members after this lane's that it suppresses
-            for (int b = lane + 1; b < nb; ++b)
-                if (suppresses(bme, bx[batch[b]], iou_thr)) row |= 1u << b;
-            unsigned alive = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u), keep = 0;
-            const int kt = kept_total;
-            for (int a = 0; a < nb; ++a) {
-                const unsigned ra = __shfl_sync(0xffffffffu, row, a);
-                if ((alive >> a) & 1u) {
-                    if (kt + __popc(keep) >= max_boxes) break;
-                    keep |= 1u << a;
-                    alive &= ~ra;
+        {
+            // member b = tid / 16 is tested against members a = 4 (tid % 16) .. + 3
+            // (a < b); the 16 threads of a member OR their bits together
+            const int b = tid >> 4, a0 = (tid & 15) * 4;
+            unsigned long long bits = 0;
+            if (b < nb) {
+                const float4 bb = bbx[b];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int a = a0 + q;
+                    if (a < b && suppresses(bbx[a], bb, iou_thr)) bits |= 1ull << a;
                 }
             }
-            if (lane < nb && ((keep >> lane) & 1u)) {
-                const int r = __popc(keep & ((1u << lane) - 1u));
-                kept_idx[kt + r] = me;
-                kbatch[r] = me;
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
+            if ((tid & 15) == 0 && b < kBatch) bcol[b] = bits;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // Resolve in rounds: a member is dropped once a kept member
+            // suppresses it, and kept once every member that could suppress it
+            // is decided and none of them is kept. This reaches the in-order
+            // result (induction on the member index) in as many rounds as the
+            // longest chain of suppressions.
+            const unsigned long long all = nb == 64 ? ~0ull : ((1ull << nb) - 1ull);
+            const unsigned long long c0 = bcol[lane], c1 = bcol[lane + 32];
+            unsigned long long keep = 0, decided = ~all;
+            while (decided != ~0ull) {
+                const bool k0 = !((decided >> lane) & 1ull) && !(c0 & keep) && !(c0 & ~decided);
+                const bool d0 = k0 || (!((decided >> lane) & 1ull) && (c0 & keep));
+                const bool k1 = !((decided >> (lane + 32)) & 1ull) && !(c1 & keep) && !(c1 & ~decided);
+                const bool d1 = k1 || (!((decided >> (lane + 32)) & 1ull) && (c1 & keep));
+                keep |= (unsigned long long)__ballot_sync(0xffffffffu, k0) |
+                        ((unsigned long long)__ballot_sync(0xffffffffu, k1) << 32);
+                decided |= (unsigned long long)__ballot_sync(0xffffffffu, d0) |
+                           ((unsigned long long)__ballot_sync(0xffffffffu, d1) << 32);
+            }
+            // the cap on kept boxes: only the first (max_boxes - kept so far) in order
+            const int kt = kept_total;
+            const int room = max_boxes - kt;
+            while (__popcll(keep) > room) keep &= ~(1ull << (63 - __clzll(keep)));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int m = lane + 32 * h;
+                if (m < nb && ((keep >> m) & 1ull)) {
+                    const int r = __popcll(keep & ((1ull << m) - 1ull));
+                    kept_idx[kt + r] = batch[m];
+                    kbatch[r] = batch[m];
+                    kbx[r] = bbx[m];
+                }
             }
             if (lane == 0) {
-                n_keep = __popc(keep);
-                kept_total = kt + __popc(keep);
+                n_keep = __popcll(keep);
+                kept_total = kt + __popcll(keep);
             }
         }
         __syncthreads();
@@ -380,11 +418,16 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
         for (int j = scan_pos + tid; j < n; j += kThreads) {
             if (supp[j]) continue;
             const float4 bj = bx[j];
-            for (int k = 0; k < nk; ++k)
-                if (suppresses(bx[kbatch[k]], bj, iou_thr)) {
-                    supp[j] = 1;
-                    break;
-                }
+            bool hit = false;
+            for (int k = 0; k < nk && !hit; k += 4) {
+                // four tests in flight (kept boxes past nk repeat the first one)
+                const bool h0 = suppresses(kbx[k], bj, iou_thr);
+                const bool h1 = suppresses(kbx[k + 1 < nk ? k + 1 : 0], bj, iou_thr);
+                const bool h2 = suppresses(kbx[k + 2 < nk ? k + 2 : 0], bj, iou_thr);
+                const bool h3 = suppresses(kbx[k + 3 < nk ? k + 3 : 0], bj, iou_thr);
+                hit = h0 || h1 || h2 || h3;
+            }
+            if (hit) supp[j] = 1;
         }
         __syncthreads();
     }
