@@ -2,11 +2,13 @@
 """Throughput benchmark of the plain detector path on GB300.
 
 One step = the whole hot path (pyramid, LBP+HOG cell histograms, block
-normalisation + window scores, NMS) over one batch of synthetic 1242x375
+normalisation + window scores, NMS) over one batch of 1024 synthetic 1242x375
 frames (the paper's frame size; pyramid factor 1.05 -> 23 levels, 33,428
-windows per frame). Frames are resident in HBM when the timed region starts;
-L2 is flushed (256 MB write) before every timed step and each step is timed
-with CUDA events on the detector's stream.
+windows per frame), replayed as one CUDA graph; 20 steps take about a second.
+Frames are resident in HBM when the timed region starts; L2 is flushed (256 MB
+write) before every timed step and each step is timed with CUDA events on the
+detector's stream. Secondary lines (other pipelines, kernels, pyramids, the
+proposal, C1 latency, the C3 mixed batch) run their own batches.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -54,9 +56,16 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--frames-per-step", type=int, default=64)
-    ap.add_argument("--cpu-sample-frames", type=int, default=12,
-                    help="frames the CPU oracle times for cpu_baseline (bounded sample)")
+    ap.add_argument("--frames-per-step", type=int, default=1024)
+    ap.add_argument("--side-frames", type=int, default=64,
+                    help="frames per step of the secondary lines (other kernels, pipelines, pyramids)")
+    ap.add_argument("--cpu-sample-frames", type=int, default=4,
+                    help="frames the single-threaded CPU oracle times for cpu_baseline (bounded sample); "
+                         "the all-cores figure times 2 frames per core")
+    ap.add_argument("--c1-replays", type=int, default=200,
+                    help="timed single-frame detects of the 320x240 latency config (0: skip)")
+    ap.add_argument("--c3-steps", type=int, default=10,
+                    help="timed steps of the 64-frame mixed batch (0: skip)")
     ap.add_argument("--proposal-steps", type=int, default=10,
                     help="timed steps of the 16x1920x1080 plain-vs-sparse comparison (0: skip)")
     ap.add_argument("--svm", default="tc", choices=["tc", "fp32"],
@@ -112,14 +121,71 @@ def barrier(world: int):
         dist.barrier()
 
 
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def _scene_worker(spec):
+    import synth
+    return synth.make_scene(*spec)
+
+
+_ORACLE_T = None
+
+
+def _oracle_init():
+    global _ORACLE_T
+    import oracle
+    oracle.build()
+    _ORACLE_T = load_template()
+
+
+def _oracle_worker(img):
+    import oracle
+    w, b = _ORACLE_T
+    oracle.detect(img, w, b, FACTOR)
+    return 0
+
+
+def make_pool(cores: int, oracle_workers: bool = False):
+    """A process pool started with spawn (safe next to CUDA)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    return ctx.Pool(cores, initializer=_oracle_init if oracle_workers else None)
+
+
+def time_oracle_parallel(pool, cores: int, frames) -> float:
+    """Wall time of the oracle over `frames` on `cores` worker processes (one frame per task)."""
+    pool.map(_oracle_worker, frames[:cores], chunksize=1)  # warm: library loaded in every worker
+    t0 = time.perf_counter()
+    pool.map(_oracle_worker, frames, chunksize=1)
+    return time.perf_counter() - t0
+
+
 def load_template():
     d = np.load(os.path.join(ROOT, "tests", "golden", "svm_template_seed0.npz"))
     return d["w"], float(d["b"])
 
 
-def make_frames(indices):
-    import synth
-    return [synth.make_scene(WIDTH, HEIGHT, CFG_ID, i) for i in indices]
+def make_frames(indices, pool=None):
+    specs = [(WIDTH, HEIGHT, CFG_ID, i) for i in indices]
+    if pool is not None:
+        return pool.map(_scene_worker, specs, chunksize=8)
+    return [_scene_worker(sp) for sp in specs]
 
 
 def svm_flag(args, pd) -> int:
@@ -319,10 +385,10 @@ def run_schemes(args, pd, torch, w, b):
                     "*_per_block: per-block HOG (36 HOG planes per cell; tensor-core K4)", **out}
 
 
-def hbm_per_kernel(stage_ms, svm: str):
+def hbm_per_kernel(stage_ms, svm: str, frames: int):
     """Achieved HBM GB/s of each kernel of the step: the DRAM bytes of one launch recorded by ncu
-    (committed summary, scaled to the 64-frame batch; only for kernels whose source is unchanged
-    since the capture) over the kernel's CUDA-event time in this run."""
+    (committed summary of a 64-frame batch, scaled to `frames`; only for kernels whose source is
+    unchanged since the capture) over the kernel's CUDA-event time in this run."""
     path = os.path.join(ROOT, "profiles", "dram_per_kernel_1242x375_b64.txt")
     if not os.path.exists(path):
         return None
@@ -342,6 +408,7 @@ def hbm_per_kernel(stage_ms, svm: str):
         if _file_hash(os.path.join(ROOT, "paper_1611_01642_gb300", "csrc", name)) != src_hash:
             out[kernel] = None
             continue
+        nbytes *= frames / 64.0
         gbs = nbytes / (t / 1e3) / 1e9
         out[kernel] = {"dram_bytes": nbytes, "achieved_gbs": gbs, "frac_of_peak": gbs / peak}
     return out
@@ -408,25 +475,30 @@ def time_oracle(frames, w, b):
 
 
 def run_reference(args):
+    """The oracle on the host's cores: each step is a bounded sample of the workload, one frame per
+    core, detected in parallel by worker processes (one frame each)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    w, b = load_template()
-    frames = make_frames(range(max(args.warmup, 0) + args.steps))
-    for img in frames[:args.warmup]:
-        time_oracle([img], w, b)
-    t = time_oracle(frames[args.warmup:args.warmup + args.steps], w, b)
-    fps = args.steps / t
+    cores = host_cores()
+    with make_pool(cores, oracle_workers=True) as pool:
+        frames = make_frames(range((max(args.warmup, 0) + args.steps) * cores), pool)
+        t_warm = time_oracle_parallel(pool, cores, frames[:max(args.warmup, 0) * cores]) if args.warmup > 0 else 0.0
+        t = time_oracle_parallel(pool, cores, frames[max(args.warmup, 0) * cores:])
+    del t_warm
+    n = args.steps * cores
+    fps = n / t
     line = {
         "impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": fps / PAPER_FPS_1242x375, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{WIDTH}x{HEIGHT} u8 frames, pyramid factor 1.05 (23 levels), "
-                               "plain HOG+LBP+SVM+NMS", "frames_per_step": 1},
-        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} seeded {WIDTH}x{HEIGHT} frames, one per step, "
-                                   "single thread"},
+                               "plain HOG+LBP+SVM+NMS", "frames_per_step": cores},
+        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                         "cpu": cpu_model(),
+                         "sample": f"{args.steps} steps of {cores} seeded {WIDTH}x{HEIGHT} frames, one frame "
+                                   f"per worker process ({cores} processes)"},
         "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -458,6 +530,10 @@ def recorded_traffic(profile: str, source: str, key: str = "dram_bytes_per_launc
         return float(rec[key])
     except (KeyError, ValueError):
         return None
+
+
+def scaled(v, f):
+    return None if v is None else v * f
 
 
 def measured_peaks():
@@ -543,9 +619,73 @@ def run_proposal(args, pd, torch, flush, recipe: int = 4):
     }
 
 
+def run_c1(args, pd, torch, w, b):
+    """C1: one seeded 320x240 frame, pyramid factor 1.2 (4 levels), the latency configuration: the
+    median of `--c1-replays` single-frame detects (graph replays), each timed with CUDA events."""
+    import synth
+    img = synth.make_scene(320, 240, 1, 0)
+    f12 = float(np.float32(1.2))
+    det = pd.Detector(w, b, pyr_factor=f12, max_frames=1, max_width=320, max_height=240)
+    frame = [torch.from_numpy(img).cuda()]
+    stream = torch.cuda.current_stream()
+    try:
+        for _ in range(20):
+            det.detect(frame)
+            det.sync()
+        ms = []
+        for _ in range(args.c1_replays):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            det.detect(frame)
+            e1.record(stream)
+            if det.sync() != pd.PD_OK:
+                raise RuntimeError(pd.pd_last_error(det.h))
+            ms.append(e0.elapsed_time(e1))
+        n_levels = len(det.levels(0))
+        boxes = len(det.boxes(0))
+    finally:
+        det.close()
+    med = float(np.median(ms))
+    return {"workload": "1 x 320x240 u8 frame (scene recipe 1: 3 silhouettes of 64..128 px), pyramid factor 1.2 "
+                        f"({n_levels} levels), plain HOG+LBP+SVM+NMS", "latency_ms_median": med,
+            "latency_ms_p10": float(np.percentile(ms, 10)), "latency_ms_p90": float(np.percentile(ms, 90)),
+            "frames_per_s": 1e3 / med, "boxes": boxes, "replays": args.c1_replays,
+            "timing": "device-resident frame, graph replay, CUDA events per detect (L2 not flushed)"}
+
+
+def run_c3(args, pd, torch, flush, w, b, pool):
+    """C3: the 64-frame mixed batch (32 x 1242x375 + 16 x 640x480 + 16 x 1920x1080, scene recipe 3,
+    Poisson(10) silhouettes), pyramid factor 1.05, one graph-replayed step per batch, timed like the
+    main line's serial figure."""
+    import synth
+    imgs = pool.map(_scene_worker, synth.frame_specs(3), chunksize=1)
+    frames = [torch.from_numpy(im).cuda() for im in imgs]
+    det = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=len(frames), max_width=1920, max_height=1080,
+                      flags=pd.PD_FLAG_STAGE_TIMING)
+    try:
+        ms, st = time_detector(det, frames, flush, args.c3_steps, pd, torch)
+        levels = sorted({len(det.levels(f)) for f in range(len(frames))})
+    finally:
+        det.close()
+    px = sum(im.size for im in imgs)
+    return {"workload": "64 mixed u8 frames in one batch: 32 x 1242x375 + 16 x 640x480 + 16 x 1920x1080 (scene "
+                        f"recipe 3), pyramid factor 1.05 ({'/'.join(map(str, levels))} levels), plain "
+                        "HOG+LBP+SVM+NMS",
+            "frames_per_s": len(frames) / (ms / 1e3), "ms_per_step": ms, "px_per_ns": px / (ms * 1e6),
+            "stage_ms_per_step": dict(zip(["pyramid", "cells", "norm_svm", "nms"], map(float, st[:4]))),
+            "steps": args.c3_steps, "l2": "flushed (256 MB write) before every timed step"}
+
+
 def run_gpu(args):
-    import torch
     rank, world, local = dist_env()
+    # worker processes (spawn) for the synthetic frames and the CPU oracle, started before CUDA
+    cores = host_cores()
+    oracle_pool = rank == 0 and world == 1 and args.cpu_sample_frames > 0
+    if oracle_pool:
+        import oracle
+        oracle.build()
+    pool = make_pool(max(1, cores // world), oracle_workers=oracle_pool)
+    import torch
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", init_method="env://")
@@ -556,7 +696,7 @@ def run_gpu(args):
 
     B = args.frames_per_step
     w, b = load_template()
-    imgs = make_frames(rank_frame_indices(rank, B))
+    imgs = make_frames(rank_frame_indices(rank, B), pool)
     det = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=B, max_width=WIDTH, max_height=HEIGHT,
                       flags=pd.PD_FLAG_STAGE_TIMING | main_flags(args, pd))
     stream = torch.cuda.current_stream()
@@ -694,8 +834,8 @@ def run_gpu(args):
     cells_ach = cells_ops / (stage_step[1] / 1e3) / 1e12
     roof_cells = {"bound": "alu", "achieved": cells_ach, "peak": lane_peak, "unit": "Tops/s",
                   "frac": cells_ach / lane_peak,
-                  "traffic": None if args.hog_per_block else recorded_traffic("k_cells_1242x375_b64.txt",
-                                                                              "k_cells.cu"),
+                  "traffic": None if args.hog_per_block else scaled(recorded_traffic("k_cells_1242x375_b64.txt",
+                                                                                     "k_cells.cu"), B / 64.0),
                   "kernel": "k_cells (uniform LBP + soft-binned HOG cell histograms)" + (
                       "; per-block HOG variant, ops still counted as for shared cells" if args.hog_per_block else ""),
                   "peak_basis": f"{sm_count} SMs x 128 lanes x {sm_mhz} MHz, one op per lane slot "
@@ -719,8 +859,8 @@ def run_gpu(args):
         executed = B * tc_units_per_frame() * TC_FLOP_PER_UNIT / k4_s / 1e12
         roof_k4 = {"bound": "tensor", "achieved": k4_ach, "peak": bf16, "unit": "TFLOP/s",
                    "frac": k4_ach / bf16, "executed_tflops": executed, "executed_frac": executed / bf16,
-                   "traffic": None if args.hog_per_block else recorded_traffic("k_svm_tc_1242x375_b64.txt",
-                                                                               "k_svm_tc.cu"),
+                   "traffic": None if args.hog_per_block else scaled(recorded_traffic("k_svm_tc_1242x375_b64.txt",
+                                                                                      "k_svm_tc.cu"), B / 64.0),
                    "tensor_active_frac": None if args.hog_per_block else recorded_traffic(
                        "k_svm_tc_1242x375_b64.txt", "k_svm_tc.cu", "tensor_active_frac"),
                    "kernel": "k_svm_tc (block norms + window scores as bf16-split tcgen05 GEMMs)",
@@ -730,15 +870,16 @@ def run_gpu(args):
     stage_names = ["k_resize", "k_cells", "k_svm_tc" if args.svm != "fp32" else "k_svm", "k_nms"]
     dominant = stage_names[int(np.argmax(stage_step[:4]))]
     # (the recorded DRAM bytes are those of the default shared-cell kernels)
-    hbm = None if args.hog_per_block else hbm_per_kernel(stage_step[:4], args.svm)
+    hbm = None if args.hog_per_block else hbm_per_kernel(stage_step[:4], args.svm, B)
     for name, roof in (("k_cells", roof_cells), (stage_names[2], roof_k4)):
         if roof["traffic"] is None and hbm and hbm.get(name):
             roof["traffic"] = hbm[name]["dram_bytes"]
     roofline = roof_cells if dominant == "k_cells" else roof_k4 if dominant.startswith("k_svm") else roof_cells
 
+    side = frames[:args.side_frames]
     other_k4 = None
     if rank == 0 and args.other_k4_steps > 0:
-        other_k4 = run_other_k4(args, pd, torch, frames, flush, w, b, fp32_peak,
+        other_k4 = run_other_k4(args, pd, torch, side, flush, w, b, fp32_peak,
                                 float(peaks.get("bf16_tflops", 1900.0)))
 
     schemes = None
@@ -747,11 +888,11 @@ def run_gpu(args):
 
     pipelines = None
     if rank == 0 and args.pipeline_steps > 0:
-        pipelines = run_pipelines(args, pd, torch, frames, flush, w, b)
+        pipelines = run_pipelines(args, pd, torch, side, flush, w, b)
 
     upscaled = None
     if rank == 0 and args.upscale_steps > 0:
-        upscaled = run_upscaled(args, pd, torch, frames, flush, tile_costs, fp32_peak)
+        upscaled = run_upscaled(args, pd, torch, side, flush, tile_costs, fp32_peak)
 
     proposal = proposal_4k = None
     if rank == 0 and args.proposal_steps > 0 and os.path.exists(PROPOSAL_CKPT):
@@ -759,12 +900,21 @@ def run_gpu(args):
         if args.proposal_4k:
             proposal_4k = run_proposal(args, pd, torch, flush, recipe=5)
 
+    c1 = run_c1(args, pd, torch, w, b) if rank == 0 and args.c1_replays > 0 else None
+    c3 = run_c3(args, pd, torch, flush, w, b, pool) if rank == 0 and args.c3_steps > 0 else None
+
     cpu = None
-    if rank == 0 and world == 1 and args.cpu_sample_frames > 0:
-        n = min(args.cpu_sample_frames, B)
-        t = time_oracle(imgs[:n], w, b)
-        cpu = {"value": n / t, "unit": "frames/s", "cores": 1, "kind": "oracle",
-               "sample": f"{n} of the step's {B} frames through the whole plain path, FP64, one thread"}
+    if oracle_pool:
+        n1 = min(args.cpu_sample_frames, B)
+        t1 = time_oracle(imgs[:n1], w, b)
+        nall = min(2 * cores, B)
+        tall = time_oracle_parallel(pool, cores, imgs[:nall])
+        cpu = {"value": nall / tall, "unit": "frames/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+               "sample": f"{nall} of the step's {B} frames through the whole plain path, FP64, one frame per "
+                         f"worker process on all {cores} host cores",
+               "single_thread": {"value": n1 / t1, "unit": "frames/s", "cores": 1,
+                                 "sample": f"{n1} of the step's frames, one thread"}}
+    pool.close()
 
     line = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
@@ -794,6 +944,8 @@ def run_gpu(args):
         "upscaled_40_levels": upscaled,
         "proposal": proposal,
         "proposal_4k_mix": proposal_4k,
+        "c1_latency_320x240": c1,
+        "c3_mixed_64": c3,
         "px_per_ns": B * WIDTH * HEIGHT / (ms_step * 1e6),
     }
     if rank == 0:

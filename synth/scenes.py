@@ -29,6 +29,7 @@ __all__ = [
     "random_image",
     "random_svm",
     "random_score_maps",
+    "frame_specs",
     "uniform_noise_image",
 ]
 
@@ -141,17 +142,22 @@ def make_scene(width: int, height: int, cfg_id: int, frame_idx: int,
     return img
 
 
-def make_frames(cfg_id: int, first_frame: int = 0, limit: int | None = None):
-    """Frames of workload ``cfg_id`` in order: list of u8 arrays."""
+def frame_specs(cfg_id: int, first_frame: int = 0, limit: int | None = None):
+    """(width, height, cfg_id, frame_idx) of the frames of workload ``cfg_id``, in order."""
     cfg = SCENE_CONFIGS[cfg_id]
     out = []
     idx = 0
     for (w, h, count) in cfg["frames"]:
         for _ in range(count):
             if idx >= first_frame and (limit is None or len(out) < limit):
-                out.append(make_scene(w, h, cfg_id, idx))
+                out.append((w, h, cfg_id, idx))
             idx += 1
     return out
+
+
+def make_frames(cfg_id: int, first_frame: int = 0, limit: int | None = None):
+    """Frames of workload ``cfg_id`` in order: list of u8 arrays."""
+    return [make_scene(*spec) for spec in frame_specs(cfg_id, first_frame, limit)]
 
 
 def make_training_crops(seed: int = 0, n_pos: int = 1000, n_neg: int = 1000):
