@@ -360,9 +360,10 @@ int pd_logits(const pd_handle *h, const float **d_logits, int64_t *total);
  * limits a call to max_candidates <= 16384 and n_levels <= PD_MAX_LEVELS
  * (larger values, or max_boxes > 16384, return PD_EINVAL). The caller passes inputs and outputs as
  * for pd_nms_maps: d_scores, d_boxes (cap max_boxes) and d_counts (kept,
- * candidates; a candidate overflow writes 0 and -candidates). The first call
- * on a device looks up the array's device address and sets the kernel's
- * shared-memory limit, so make that first call outside any stream capture.
+ * candidates; a candidate overflow writes 0 and -candidates). Every call
+ * looks up the array's device address on the current device and sets the
+ * kernel's shared-memory limit (host calls that allocate nothing); make the
+ * first call on a device outside any stream capture.
  * All calls share the one array and it keeps the last call's contents, so
  * calls that overlap on the GPU (two streams, two threads) race: serialise
  * them. Errors: PD_EINVAL, PD_ECUDA. Asynchronous on `stream`. */

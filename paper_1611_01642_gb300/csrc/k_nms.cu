@@ -34,8 +34,6 @@
 // evaluation of the definition. Decisions are therefore the same as those of
 // a plain double-precision implementation, and the slow double path runs
 // only for the rare pairs in the band.
-#include <mutex>
-
 #include "pd_internal.h"
 
 namespace pd {
@@ -316,7 +314,7 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
     // suppressed), and copies the kept boxes to shared memory; then every
     // thread suppresses the later candidates against them. Same decisions as
     // the sequential definition, with ~64x fewer block-wide barriers.
-    __shared__ int batch[kBatch], kbatch[kBatch];
+    __shared__ int batch[kBatch];
     __shared__ float4 bbx[kBatch], kbx[kBatch];
     __shared__ unsigned long long bcol[kBatch];  // member b: bit a set iff a < b and a suppresses b
     __shared__ int n_batch, n_keep, kept_total, scan_pos;
@@ -403,7 +401,6 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
                 if (m < nb && ((keep >> m) & 1ull)) {
                     const int r = __popcll(keep & ((1ull << m) - 1ull));
                     kept_idx[kt + r] = batch[m];
-                    kbatch[r] = batch[m];
                     kbx[r] = bbx[m];
                 }
             }
@@ -539,10 +536,6 @@ __global__ void k_nms_noalloc_setup(const __grid_constant__ NoAllocGeometry g, N
     }
 }
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-NoAllocScratch *g_noalloc_addr[kMaxDevices] = {};
-
 }  // namespace
 
 }  // namespace pd
@@ -571,22 +564,14 @@ extern "C" int pd_nms_noalloc(void *stream, const float *d_scores, int n_levels,
         g.score_off[k] = off;
         off += (int64_t)rows[k] * cols[k];
     }
-    // Once per device: the device address of the scratch array (the host-side
-    // symbol is only a stand-in) and the kernel's shared-memory opt-in.
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return PD_ECUDA;
-    if (dev < 0 || dev >= kMaxDevices) return PD_EINVAL;
-    NoAllocScratch *scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_addr[dev]) {
-            void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_nms_scratch) != cudaSuccess || !p) return PD_ECUDA;
-            if (init_nms() != cudaSuccess) return PD_ECUDA;
-            g_noalloc_addr[dev] = reinterpret_cast<NoAllocScratch *>(p);
-        }
-        scratch = g_noalloc_addr[dev];
-    }
+    // Every call: the current device's address of the scratch array (the
+    // host-side symbol is only a stand-in) and the kernel's shared-memory
+    // opt-in. Both are cheap host calls; doing them each time keeps the
+    // address right after a device reset or on a new primary context.
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_nms_scratch) != cudaSuccess || !p) return PD_ECUDA;
+    if (init_nms() != cudaSuccess) return PD_ECUDA;
+    NoAllocScratch *scratch = reinterpret_cast<NoAllocScratch *>(p);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     k_nms_noalloc_setup<<<1, 128, 0, s>>>(g, scratch);
     if (cudaGetLastError() != cudaSuccess) return PD_ECUDA;

@@ -12,6 +12,7 @@ of every window it scores, bit for bit.
 Workloads (scene recipes of synth/scenes.py):
   mixed:  32 x 1242x375 + 16 x 640x480 + 16 x 1920x1080 (64 frames)
   4K mix: 16 x 3840x2160 + 48 x 1242x375 (64 frames), with the proposal
+  40 levels: 64 x 1242x375 with 17 upsampled levels in front (NMS cap 65,536)
 """
 import os
 
@@ -149,5 +150,40 @@ def test_bench_batch_per_block_hog_sampled_windows_match_oracle(template):
                     assert abs(float(m[wy, wx]) - ref) <= SCORE_TOL * scale, (f, k, wy, wx)
                     checked += 1
         assert checked >= 40
+    finally:
+        det.close()
+
+
+def test_40_level_batch_sampled_windows_and_nms_match_oracle(template):
+    """The secondary benchmark line: 64 x 1242x375 frames with 17 upsampled levels in front of the
+    23 (40 levels, 293,397 windows per frame; reading R2), replayed from the captured graph.
+    Level sizes follow the pyramid rule, sampled windows of sampled levels (the most upsampled one
+    included) are within the score bar of the oracle's brute-force descriptor, and the NMS of two
+    frames (about 10,000-40,000 candidates each: the large-cap sort path) equals the oracle's greedy
+    NMS on the same float32 score maps."""
+    from paper_1611_01642_gb300 import build as bld
+    bld.build()
+    w, b = template
+    imgs = [synth.make_scene(1242, 375, 2, i) for i in range(64)]
+    det = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=64, max_width=1242, max_height=375,
+                      upscale_levels=17, max_candidates_per_frame=65536)
+    try:
+        dev = [torch.from_numpy(im).cuda() for im in imgs]
+        for _ in range(3):  # plan, capture, replay: the replayed step is the one checked
+            det.detect(dev)
+            assert det.sync() == pd.PD_OK
+        assert [(l["width"], l["height"]) for l in det.levels(0)] == oracle.pyramid(1242, 375, FACTOR, upscale=17)
+        assert len(det.levels(0)) == 40
+        rng = np.random.default_rng(17)
+        assert _sample_and_check(det, imgs, w, b, [0, 40, 63], rng, per_level=3, levels_per_frame=3) >= 25
+        for f in (5, 63):
+            lv = det.levels(f)
+            maps = [m.cpu().numpy() for m in det.score_maps(f)]
+            ref, ncand = oracle.nms(maps, [(l["width"], l["height"]) for l in lv], 1242, 375)
+            assert pd.pd_frame_candidates(det.h, f) == ncand and ncand > 16384 // 4
+            got = det.boxes(f)
+            assert len(got) == len(ref)
+            for name in ("x", "y", "w", "h", "score", "level", "wx", "wy"):
+                assert np.array_equal(got[name], ref[name]), (f, name)
     finally:
         det.close()
