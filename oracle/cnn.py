@@ -16,7 +16,13 @@ inputs and bfloat16 weights):
 with conv3x3_s2_p1(a)[o][i][j] = b[o] + sum_{c,dy,dx} W[o][c][dy][dx]
 a[c][2i+dy-1][2j+dx-1] (zero outside), output size ceil(n/2). The window
 (wx, wy) covers cells wx..wx+7 x wy..wy+15, the same windows as the SVM score
-map (Hc-15 x Wc-7). Training minimises the mean binary cross-entropy with
+map (Hc-15 x Wc-7).
+
+Level groups (reading of this project): with a step m the network runs on
+levels 0, m, 2m, ... of a frame, and level k pools the head map of level
+j = m floor(k/m) read at the cell holding each of its cells' centres (cell
+(cy, cx) of level k -> row min(floor((2cy+1) Hk_j / (2 Hk_k)), Hc_j - 1),
+column likewise with the widths). m = 1 is the network on every level. Training minimises the mean binary cross-entropy with
 logits and positive weight p, and steps with Adam.
 
 Functions here are written for clarity: loops over layers, numpy einsum /
@@ -145,6 +151,36 @@ def forward_q(L: np.ndarray, q: dict):
     z = window_pool(h, q["v"], q["bv"][0], rows, cols)
     cache = dict(q=q, x=x, z1=z1, a1=a1, z2=z2, a2=a2, z3=z3, a3=a3, h=h)
     return z, cache
+
+
+def head_resample(h_src: np.ndarray, src_size, dst_size) -> np.ndarray:
+    """Head map of a level (dst_size = (Wk, Hk)) read from another level of its frame (src_size):
+    destination cell (cy, cx) takes the source cell holding its centre, row
+    min(floor((2cy+1) Hk_src / (2 Hk_dst)), Hc_src - 1), column likewise."""
+    (ws, hs), (wd, hd) = src_size, dst_size
+    ys = np.minimum(((2 * np.arange(hd // 8) + 1) * hs) // (2 * hd), hs // 8 - 1)
+    xs = np.minimum(((2 * np.arange(wd // 8) + 1) * ws) // (2 * wd), ws // 8 - 1)
+    return np.asarray(h_src)[np.ix_(ys, xs)]
+
+
+def frame_logits(levels, p: dict, step: int = 1):
+    """Keep-logits of every level of one frame (list of level images, largest first) when the
+    network runs on levels 0, step, 2 step, ... and each level pools its group level's head map
+    (head_resample; the identity for the group level itself)."""
+    q = rounded(p)
+    heads, out = {}, []
+    for k, L in enumerate(levels):
+        j = step * (k // step)
+        if j not in heads:
+            heads[j] = forward_q(levels[j], q)[1]["h"]
+        Hk, Wk = L.shape
+        src = (levels[j].shape[1], levels[j].shape[0])
+        h = head_resample(heads[j], src, (Wk, Hk))
+        rows, cols = max(Hk // 8 - 15, 0), max(Wk // 8 - 7, 0)
+        if rows == 0 or cols == 0:
+            rows = cols = 0
+        out.append(window_pool(h, q["v"], q["bv"][0], rows, cols))
+    return out
 
 
 def bce_with_logits(z: np.ndarray, y: np.ndarray, pos_weight: float):

@@ -112,3 +112,53 @@ def test_training_reduces_loss_on_a_tiny_problem():
         first = loss if first is None else first
         p = opt.step(p, cnn.flatten(g))
     assert loss < 0.5 * first
+
+
+# ----------------------------------------------------------------------------- level groups
+def test_head_resample_identity_and_exact_half():
+    rng = np.random.default_rng(7)
+    h = rng.standard_normal((20, 30))
+    assert np.array_equal(cnn.head_resample(h, (240, 160), (240, 160)), h)
+    # a level exactly half the size: destination cell (cy, cx) reads source (2cy+1, 2cx+1)
+    g = cnn.head_resample(h, (240, 160), (120, 80))
+    assert g.shape == (10, 15)
+    assert np.array_equal(g, h[1::2, 1::2])
+
+
+def test_head_resample_reads_the_cell_holding_each_centre():
+    """Brute force with exact rationals: the source cell read for destination cell c contains the
+    destination cell's centre (8c + 4) mapped to source pixels, clamped to the source's cells."""
+    from fractions import Fraction
+    rng = np.random.default_rng(8)
+    for (ws, hs), (wd, hd) in [((333, 257), (301, 233)), ((1242, 375), (1127, 340)), ((640, 480), (350, 262))]:
+        h = rng.standard_normal((hs // 8, ws // 8))
+        g = cnn.head_resample(h, (ws, hs), (wd, hd))
+        assert g.shape == (hd // 8, wd // 8)
+        idx = {v: (i, j) for (i, j), v in np.ndenumerate(h)}
+        for cy in range(hd // 8):
+            for cx in range(wd // 8):
+                sy, sx = idx[g[cy, cx]]
+                py = Fraction(8 * cy + 4) * hs / hd
+                px = Fraction(8 * cx + 4) * ws / wd
+                assert sy == min(int(py // 8), hs // 8 - 1)
+                assert sx == min(int(px // 8), ws // 8 - 1)
+
+
+def test_frame_logits_step_one_is_the_per_level_network():
+    rng = np.random.default_rng(9)
+    p = cnn.init_params(3)
+    img = (rng.random((200, 300)) * 255).astype(np.uint8)
+    levels = [img, img[:180, :270].copy(), img[:150, :200].copy()]
+    z = cnn.frame_logits(levels, p, step=1)
+    for L, zk in zip(levels, z):
+        assert np.array_equal(zk, cnn.forward(L, p)[0])
+    # with step 3 the first level is unchanged and the others pool resampled heads of level 0
+    z3 = cnn.frame_logits(levels, p, step=3)
+    assert np.array_equal(z3[0], z[0])
+    h0 = cnn.forward(levels[0], p)[1]["h"]
+    q = cnn.rounded(p)
+    for k in (1, 2):
+        Hk, Wk = levels[k].shape
+        h = cnn.head_resample(h0, (300, 200), (Wk, Hk))
+        ref = cnn.window_pool(h, q["v"], q["bv"][0], Hk // 8 - 15, Wk // 8 - 7)
+        assert np.array_equal(z3[k], ref)
