@@ -102,6 +102,9 @@ typedef struct pd_params {
     float keep_logit_threshold; /* a window is kept iff its keep-logit > this */
     int32_t upscale_levels;  /* 0..64 upsampled levels (scale pyr_factor^-j, j = upscale..1) placed
                                 before the frame's level 0; 0 by default (the stop rule alone) */
+    int32_t proposal_level_step; /* 1..16: the proposal network runs on levels 0, m, 2m, ... of each
+                                    frame (m = this value) and every level's head map is taken from
+                                    the first level of its group; 1 (every level) by default */
 } pd_params;
 
 /* One detection: a window in frame coordinates. */
@@ -342,6 +345,17 @@ int pd_cnn_train_loss(pd_handle *h, void *stream, float *loss);
  * others -inf. With the threshold at -inf every window is scored. Needs
  * parameters (pd_cnn_set_params) to enable. Affects the next pd_detect. */
 int pd_set_proposal(pd_handle *h, int enable, float keep_logit_threshold);
+
+/* Level groups of the learned proposal (this library's addition; the
+ * paper has no learned stage). With m = level_step the network runs on the
+ * frame's levels 0, m, 2m, ... only; level k takes its head map from level
+ * j = m * floor(k / m) by nearest cell: cell (cy, cx) of level k reads cell
+ * (min(floor((2 cy + 1) Hk_j / (2 Hk_k)), cells_y_j - 1),
+ *  min(floor((2 cx + 1) Wk_j / (2 Wk_k)), cells_x_j - 1)) of level j, the
+ * cell holding its centre; the window pooling then runs on every level as
+ * before. m = 1 is the network on every level. 1 <= level_step <= 16, else
+ * PD_EINVAL. Affects the next pd_detect (the batch plan is rebuilt). */
+int pd_set_proposal_levels(pd_handle *h, int level_step);
 
 /* Device pointer to the window keep-logits of the last pd_detect with the
  * proposal on (same layout and offsets as pd_scores; *total = 0 when off). */

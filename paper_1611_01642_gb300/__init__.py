@@ -40,7 +40,8 @@ EXPORTED = ["pd_params_default", "pd_pyramid", "pd_create", "pd_destroy", "pd_la
             "pd_detect", "pd_detect_host", "pd_sync", "pd_frame_candidates", "pd_frame_levels", "pd_scores", "pd_boxes",
             "pd_last_launch_count", "pd_stage_times", "pd_set_tile_costs", "pd_get_tile_costs", "pd_resize_levels", "pd_cell_features", "pd_window_scores",
             "pd_nms_maps", "pd_nms_noalloc", "pd_cnn_set_params", "pd_cnn_get_params", "pd_cnn_forward",
-            "pd_cnn_train_step", "pd_cnn_train_loss", "pd_set_proposal", "pd_logits", "pd_pyramid_ex",
+            "pd_cnn_train_step", "pd_cnn_train_loss", "pd_set_proposal", "pd_set_proposal_levels",
+            "pd_logits", "pd_pyramid_ex",
             "pd_scheme_cells", "pd_scheme_window_scores"]
 
 
@@ -51,7 +52,8 @@ class pd_params(ctypes.Structure):
                 ("max_candidates_per_frame", ctypes.c_int32), ("max_frames", ctypes.c_int32),
                 ("max_width", ctypes.c_int32), ("max_height", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("use_proposal", ctypes.c_int32),
-                ("keep_logit_threshold", ctypes.c_float), ("upscale_levels", ctypes.c_int32)]
+                ("keep_logit_threshold", ctypes.c_float), ("upscale_levels", ctypes.c_int32),
+                ("proposal_level_step", ctypes.c_int32)]
 
 
 class pd_box(ctypes.Structure):
@@ -124,6 +126,7 @@ def load(path: str | None = None):
         "pd_cnn_train_step": ([P, P, f, f, f], i),
         "pd_cnn_train_loss": ([P, P, P], i),
         "pd_set_proposal": ([P, i, f], i),
+        "pd_set_proposal_levels": ([P, i], i),
         "pd_logits": ([P, P, P], i),
     }
     for name, (args, res) in sig.items():
@@ -389,6 +392,11 @@ def pd_set_proposal(h, enable: bool, keep_logit_threshold: float) -> None:
     _check(load().pd_set_proposal(h, 1 if enable else 0, float(keep_logit_threshold)), h)
 
 
+def pd_set_proposal_levels(h, level_step: int) -> None:
+    """The proposal network runs on every level_step-th level; the others read its head map."""
+    _check(load().pd_set_proposal_levels(h, int(level_step)), h)
+
+
 def pd_logits(h):
     p = ctypes.c_void_p()
     total = ctypes.c_int64()
@@ -424,8 +432,11 @@ class Detector:
     def detect(self, frames, stream=None):
         pd_detect(self.h, frames, stream)
 
-    def set_proposal(self, enable: bool, keep_logit_threshold: float = 0.0):
-        """Sparse path on/off (needs proposal parameters set with pd_cnn_set_params)."""
+    def set_proposal(self, enable: bool, keep_logit_threshold: float = 0.0, level_step: int | None = None):
+        """Sparse path on/off (needs proposal parameters set with pd_cnn_set_params); level_step:
+        the network runs on every level_step-th level of a frame (None: unchanged)."""
+        if level_step is not None:
+            pd_set_proposal_levels(self.h, level_step)
         pd_set_proposal(self.h, enable, keep_logit_threshold)
 
     def detect_host(self, frames, stream=None):

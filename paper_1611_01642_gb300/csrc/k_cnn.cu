@@ -534,6 +534,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_cnn_fwd(const LevelDesc *__rest
 // CTA per (level, 64 x 16 window tile); the tile's 31 x 71 cells of h are
 // staged in shared memory; each thread computes 4 consecutive windows of one
 // row (8 taps x 4 windows per h row from 11 staged values), in a fixed order.
+// With level groups a level's h is its group level's head map read at the
+// cell holding each cell's centre: row min(floor((2 cy + 1) Hk_j / (2 Hk)),
+// Hc_j - 1), column likewise (the identity for the group level itself).
 constexpr int kPoolHW = kPoolTW + 8;                    // 72 staged columns (71 used)
 constexpr int kPoolHH = kPoolTH + kWinBH;               // 31 staged rows
 
@@ -548,11 +551,19 @@ __global__ void __launch_bounds__(256) k_cnn_pool(const LevelDesc *__restrict__ 
     const int ty = blockIdx.x / max(tiles_x, 1), tx = blockIdx.x - ty * max(tiles_x, 1);
     const int wy0 = ty * kPoolTH, wx0 = tx * kPoolTW;
     if (L.rows == 0 || wy0 >= L.rows) return;  // CTA-uniform
+    const LevelDesc J = levels[L.hsrc];
+    const bool same = L.hsrc == (int)blockIdx.y;
     for (int i = threadIdx.x; i < 128; i += blockDim.x) V[i] = v[i];
     for (int i = threadIdx.x; i < kPoolHH * kPoolHW; i += blockDim.x) {
         const int r = i / kPoolHW, c = i - r * kPoolHW;
         const int cy = wy0 + r, cx = wx0 + c;
-        Hs[r][c] = (cy < L.Hc && cx < L.Wc) ? hmap[(int64_t)(L.cell_row + cy) * hmap_pitch + cx] : 0.f;
+        float hv = 0.f;
+        if (cy < L.Hc && cx < L.Wc) {
+            const int sy = same ? cy : min((2 * cy + 1) * J.Hk / (2 * L.Hk), J.Hc - 1);
+            const int sx = same ? cx : min((2 * cx + 1) * J.Wk / (2 * L.Wk), J.Wc - 1);
+            hv = hmap[(int64_t)(J.cell_row + sy) * hmap_pitch + sx];
+        }
+        Hs[r][c] = hv;
     }
     __syncthreads();
     const int ry = threadIdx.x >> 4, qx = 4 * (threadIdx.x & 15);

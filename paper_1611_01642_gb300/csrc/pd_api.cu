@@ -505,6 +505,7 @@ void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int
         k1_tables(p, L, W, H, Wk, Hk);
     }
     const int li = (int)p.levels.size();
+    L.hsrc = li;
     L.citem0 = (int32_t)p.c_items.size();
     L.ctx = (L.Wc + kCellTW - 1) / kCellTW;
     for (int cy = 0; cy < L.Hc; cy += kCellTH)
@@ -548,9 +549,13 @@ int plan_frame(Plan &p, const pd_params &prm, const uint8_t *ptr, int W, int H, 
                    tile_cost);
         p.pyr_bytes += (int64_t)lp * Hk[k];
         if (proposal) {
-            const LevelDesc &L = p.levels.back();
+            // level groups: the network runs on levels 0, m, 2m, ...; level k uses the head
+            // map of level m floor(k / m) (its first level, the largest)
+            LevelDesc &L = p.levels.back();
             const int li = (int)p.levels.size() - 1;
-            if (L.rows > 0)
+            const int m = prm.proposal_level_step;
+            L.hsrc = fd.first_level + m * (k / m);
+            if (L.rows > 0 && k % m == 0)
                 for (int cy = 0; cy < L.Hc; cy += kCnnTile)
                     for (int cx = 0; cx < L.Wc; cx += kCnnTile) p.cnn_items.push_back({li, cy, cx, 0});
         }
@@ -566,6 +571,7 @@ int plan_frame(Plan &p, const pd_params &prm, const uint8_t *ptr, int W, int H, 
 bool params_ok(const pd_params *p) {
     return p && p->struct_size == sizeof(pd_params) && p->pyr_factor > 1.0f && p->l2hys_clip > 0.f &&
            !std::isnan(p->keep_logit_threshold) && p->upscale_levels >= 0 && p->upscale_levels <= 64 &&
+           p->proposal_level_step >= 1 && p->proposal_level_step <= 16 &&
            p->nms_iou >= 0.f && p->max_boxes_per_frame > 0 && p->max_boxes_per_frame <= 16384 &&
            p->max_candidates_per_frame > 0 &&
            p->max_candidates_per_frame <= 65536 && p->max_frames > 0 && p->max_width > 0 &&
@@ -735,6 +741,7 @@ int pd_params_default(pd_params *p) {
     p->max_width = 1242;
     p->max_height = 375;
     p->flags = 0;
+    p->proposal_level_step = 1;
     return PD_OK;
 }
 
@@ -1334,6 +1341,14 @@ int pd_set_proposal(pd_handle *h, int enable, float keep_logit_threshold) {
     if (std::isnan(keep_logit_threshold)) return fail(h, PD_EINVAL, "threshold is NaN");
     h->proposal = enable != 0;
     h->tau = keep_logit_threshold;
+    invalidate_cache(h);
+    return PD_OK;
+}
+
+int pd_set_proposal_levels(pd_handle *h, int level_step) {
+    if (!h) return PD_EINVAL;
+    if (level_step < 1 || level_step > 16) return fail(h, PD_EINVAL, "level step %d outside [1, 16]", level_step);
+    h->p.proposal_level_step = level_step;
     invalidate_cache(h);
     return PD_OK;
 }

@@ -53,7 +53,7 @@ struct LevelDesc {
     int32_t rgroup;     // K1 output columns per group: 4, or 1 when a group of 4 reaches past the halo
     int32_t rspan;      // K1 source bytes a tile row needs for this level (<= kResizeBW)
     int32_t xq_off;     // K1 column quads: per group one word, byte i = quad index of column i
-    int32_t pad;
+    int32_t hsrc;       // proposal: index (in this table) of the level whose head map this level uses
 };
 
 // Work items (one CTA each).

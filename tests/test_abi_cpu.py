@@ -35,7 +35,7 @@ def test_header_declarations_are_all_exported(lib):
 
 def test_params_default(lib):
     p = pd.pd_params_default()
-    assert p.struct_size == 56
+    assert p.struct_size == 60 and p.proposal_level_step == 1
     assert abs(p.pyr_factor - 1.05) < 1e-6 and abs(p.l2hys_clip - 0.2) < 1e-7
     assert p.threshold == 0.0 and p.nms_iou == 0.5 and p.max_candidates_per_frame == 16384
 

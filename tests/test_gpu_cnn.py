@@ -251,3 +251,38 @@ def test_sparse_path_needs_parameters(template):
             d.set_proposal(True, 0.0)
     finally:
         d.close()
+
+
+@pytest.mark.parametrize("step", [1, 2, 3])
+def test_level_group_logits_match_oracle(template, step):
+    """Keep-logits of every level of a batch through pd_detect with the network on every step-th
+    level (level groups: each level pools its group level's head map read at the cell holding each
+    centre) against the oracle's frame_logits, within the proposal bar; two frames of different
+    sizes, so the groups of each frame are their own."""
+    from paper_1611_01642_gb300 import build as bld
+    bld.build()
+    w, b = template
+    frames = [synth.make_scene(640, 480, 2, 60), synth.make_scene(421, 300, 2, 61)]
+    d = pd.Detector(w, b, max_frames=2, max_width=640, max_height=480, proposal_level_step=step)
+    try:
+        p32 = _params(7)
+        pd.pd_cnn_set_params(d.h, p32)
+        d.set_proposal(True, float("-inf"))
+        d.detect([torch.from_numpy(f).cuda() for f in frames])
+        assert d.sync() == pd.PD_OK
+        p = ocnn.unflatten(p32.astype(np.float64))
+        for f, img in enumerate(frames):
+            lv = d.levels(f)
+            levels = [oracle.resize(img, l["width"], l["height"]) for l in lv]
+            ref = ocnn.frame_logits(levels, p, step=step)
+            got = d.logit_maps(f)
+            assert len(got) == len(ref)
+            for k, (g, r) in enumerate(zip(got, ref)):
+                if r.size:
+                    _close(g.cpu().numpy(), r, f"frame {f} level {k} step {step}")
+        # the same network on every level (step 1) differs from a grouped level's logits
+        if step > 1:
+            z1 = ocnn.frame_logits([oracle.resize(frames[0], l["width"], l["height"]) for l in d.levels(0)], p)
+            assert not np.allclose(z1[1], d.logit_maps(0)[1].cpu().numpy())
+    finally:
+        d.close()
