@@ -560,6 +560,7 @@ def run_proposal(args, pd, torch, flush, recipe: int = 4):
     from paper_1611_01642_gb300 import proposal as prop
     params, meta = prop.load_checkpoint(PROPOSAL_CKPT)
     tau = float(meta["keep_logit_threshold"])
+    step = int(meta.get("level_step", 1))
     imgs = synth.make_frames(recipe, limit=args.proposal_frames if recipe == 4 else None)
     frames = [torch.from_numpy(im).cuda() for im in imgs]
     w, b = load_template()
@@ -569,7 +570,7 @@ def run_proposal(args, pd, torch, flush, recipe: int = 4):
     stream = torch.cuda.current_stream()
 
     def timed(sparse: bool):
-        det.set_proposal(sparse, tau)
+        det.set_proposal(sparse, tau, level_step=step)
         for _ in range(3):
             flush.fill_(1)
             det.detect(frames)
@@ -605,6 +606,7 @@ def run_proposal(args, pd, torch, flush, recipe: int = 4):
                     ("16 x 3840x2160 + 48 x 1242x375 u8 frames in one batch (scene recipe 5: Poisson(10) "
                      "silhouettes, 48..600 px), pyramid factor 1.05 (58 / 23 levels)"),
         "checkpoint": os.path.relpath(PROPOSAL_CKPT, ROOT), "keep_logit_threshold": tau,
+        "level_step": step,
         "plain_frames_per_s": len(frames) / (ms_plain / 1e3),
         "sparse_frames_per_s": len(frames) / (ms_sparse / 1e3),
         "speedup": ms_plain / ms_sparse,

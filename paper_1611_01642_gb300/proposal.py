@@ -212,8 +212,10 @@ def _scene_batches(width, height, key, first, count, batch):
 
 
 def recalibrate(path: str, out: str, calib_frames: int = 16, val_frames: int = 16, recall: float = 0.99,
-                width: int = 1920, height: int = 1080, factor: float = 1.05, batch: int = 8):
-    """Re-derives the keep threshold of a checkpoint on the sparse path's own recall; writes ``out``."""
+                width: int = 1920, height: int = 1080, factor: float = 1.05, batch: int = 8,
+                level_step: int | None = None):
+    """Re-derives the keep threshold of a checkpoint on the sparse path's own recall; writes ``out``.
+    level_step: the network runs on every level_step-th level (None: the checkpoint's, else 1)."""
     import os
     params, meta = load_checkpoint(path)
     svm = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden",
@@ -223,12 +225,14 @@ def recalibrate(path: str, out: str, calib_frames: int = 16, val_frames: int = 1
                    pyr_factor=float(np.float32(factor)))
     try:
         pd_cnn_set_params(det.h, params)
+        step = int(level_step if level_step is not None else meta.get("level_step", 1))
+        det.set_proposal(False, 0.0, level_step=step)
         calib = list(_scene_batches(width, height, 101, 0, calib_frames, batch))
         s, z = window_stats(det, calib)
         tau_window = calibrate(s, z, recall)
         tau = calibrate_sparse(det, calib, recall)
         val = list(_scene_batches(width, height, 101, calib_frames, val_frames, batch))
-        meta = dict(meta, keep_logit_threshold=tau, window_level_threshold=tau_window,
+        meta = dict(meta, keep_logit_threshold=tau, window_level_threshold=tau_window, level_step=step,
                     calibration=dict(kind="path", frames=calib_frames, recall=recall),
                     validation=sparse_metrics(det, val, tau))
         save_checkpoint(out, params, meta)
