@@ -707,6 +707,10 @@ def run_gpu(args):
     from paper_1611_01642_gb300 import autotune
     tile_costs = (pd.pd_get_tile_costs(det.h) if args.no_autotune or args.svm != "fp32"
                   else autotune.apply(det, frames[:16], w, b, FACTOR))
+    # launch shapes of the default path (pyramid groups per warp task, score-kernel item rows),
+    # timed on 64 of the step's frames, cached per GPU, library build and workload
+    tuning = (pd.pd_get_tuning(det.h) if args.no_autotune else
+              autotune.apply_default(det, frames[:64], w, b, FACTOR, flags=main_flags(args, pd)))
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     wpf = windows_per_frame()
 
@@ -752,6 +756,7 @@ def run_gpu(args):
     det_b = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=B, max_width=WIDTH, max_height=HEIGHT,
                         flags=pd.PD_FLAG_STAGE_TIMING | main_flags(args, pd))
     pd.pd_set_tile_costs(det_b.h, tile_costs)
+    pd.pd_set_tuning(det_b.h, tuning["k1_groups"], tuning["tc_item_rows"])
     streams = [stream, torch.cuda.Stream()]
     pipe = [det, det_b]
     for _ in range(max(args.warmup, 0)):
@@ -795,6 +800,7 @@ def run_gpu(args):
     det2 = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=B, max_width=WIDTH, max_height=HEIGHT,
                        flags=main_flags(args, pd))
     pd.pd_set_tile_costs(det2.h, tile_costs)
+    pd.pd_set_tuning(det2.h, tuning["k1_groups"], tuning["tc_item_rows"])
     for _ in range(2):
         det2.detect_host(pinned, stream=streams[1])
         det2.sync()
@@ -929,6 +935,8 @@ def run_gpu(args):
                    "frames_per_step": B * world, "frames_per_gpu": B, "windows_per_frame": wpf,
                    "l2": "flushed (256 MB write) before every timed step",
                    "k4_tile_costs": [round(c, 4) for c in tile_costs],
+                   "launch_shapes": dict(tuning, source="autotuner (pyramid and score stage times on 64 "
+                                         "of the step's frames)" if not args.no_autotune else "library defaults"),
                    "parallelism": f"{world} independent replicas"},
         "roofline": roofline,
         "roofline_k4": roof_k4,

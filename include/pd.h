@@ -200,6 +200,24 @@ int pd_boxes(const pd_handle *h, int frame, pd_box *out, int cap, int *count);
 /* Number of this library's kernel launches issued by the last pd_detect. */
 int pd_last_launch_count(const pd_handle *h);
 
+/* Launch shapes of the default path (this library's addition), chosen by an
+ * autotuner that times them on the caller's workload:
+ *   k1_groups     column groups (of 4 output pixels) per warp task of the
+ *                 pyramid kernel: 4, 8 or 16; a warp's 32 lanes are
+ *                 k1_groups groups x 32 / k1_groups row slices (default 8);
+ *   tc_item_rows  window rows per work item of the tensor-core score kernel,
+ *                 8 .. 64: a 104-window strip is cut into near-equal pieces
+ *                 of at most this many rows, each piece also reading the 14
+ *                 block rows below its last window row (default 64).
+ * Results do not depend on them: every output is the same sum in the same
+ * order. Errors: PD_EINVAL. Affects the next pd_detect. */
+typedef struct pd_tuning {
+    int32_t k1_groups;
+    int32_t tc_item_rows;
+} pd_tuning;
+int pd_set_tuning(pd_handle *h, const pd_tuning *t);
+int pd_get_tuning(const pd_handle *h, pd_tuning *t);
+
 /* Tile shapes of the FP32 K4 (PD_FLAG_SVM_FP32; windows per CTA tile, x by y): 0 = 32x16, 1 = 64x8,
  * 2 = 32x8, 3 = 64x4, 4 = 64x2, 5 = 32x12, 6 = 32x4. For each level the
  * planner takes the shape with the least (number of tiles x cost[shape]).

@@ -41,6 +41,7 @@ EXPORTED = ["pd_params_default", "pd_pyramid", "pd_create", "pd_destroy", "pd_la
             "pd_last_launch_count", "pd_stage_times", "pd_set_tile_costs", "pd_get_tile_costs", "pd_resize_levels", "pd_cell_features", "pd_window_scores",
             "pd_nms_maps", "pd_nms_noalloc", "pd_cnn_set_params", "pd_cnn_get_params", "pd_cnn_forward",
             "pd_cnn_train_step", "pd_cnn_train_loss", "pd_set_proposal", "pd_set_proposal_levels",
+            "pd_set_tuning", "pd_get_tuning",
             "pd_logits", "pd_pyramid_ex",
             "pd_scheme_cells", "pd_scheme_window_scores"]
 
@@ -54,6 +55,10 @@ class pd_params(ctypes.Structure):
                 ("flags", ctypes.c_int32), ("use_proposal", ctypes.c_int32),
                 ("keep_logit_threshold", ctypes.c_float), ("upscale_levels", ctypes.c_int32),
                 ("proposal_level_step", ctypes.c_int32)]
+
+
+class pd_tuning(ctypes.Structure):
+    _fields_ = [("k1_groups", ctypes.c_int32), ("tc_item_rows", ctypes.c_int32)]
 
 
 class pd_box(ctypes.Structure):
@@ -127,6 +132,8 @@ def load(path: str | None = None):
         "pd_cnn_train_loss": ([P, P, P], i),
         "pd_set_proposal": ([P, i, f], i),
         "pd_set_proposal_levels": ([P, i], i),
+        "pd_set_tuning": ([P, P], i),
+        "pd_get_tuning": ([P, P], i),
         "pd_logits": ([P, P, P], i),
     }
     for name, (args, res) in sig.items():
@@ -390,6 +397,19 @@ def pd_cnn_train_loss(h, stream=None) -> float:
 
 def pd_set_proposal(h, enable: bool, keep_logit_threshold: float) -> None:
     _check(load().pd_set_proposal(h, 1 if enable else 0, float(keep_logit_threshold)), h)
+
+
+def pd_set_tuning(h, k1_groups: int, tc_item_rows: int) -> None:
+    """Launch shapes of the default path (pyramid column groups per warp task, tensor-core score
+    kernel window rows per item); results do not depend on them."""
+    t = pd_tuning(int(k1_groups), int(tc_item_rows))
+    _check(load().pd_set_tuning(h, ctypes.byref(t)), h)
+
+
+def pd_get_tuning(h) -> dict:
+    t = pd_tuning()
+    _check(load().pd_get_tuning(h, ctypes.byref(t)), h)
+    return {"k1_groups": t.k1_groups, "tc_item_rows": t.tc_item_rows}
 
 
 def pd_set_proposal_levels(h, level_step: int) -> None:

@@ -41,8 +41,6 @@ constexpr int kTH = kResizeTH;                 // 32 source rows per tile
 constexpr int kTP = 176;                       // staged byte row pitch (>= kResizeBW + 8, 16-byte multiple)
 constexpr int kQP = 193;                       // quad row pitch in words: >= resize_quad_index(kResizeBW - 2) + 1
                                                // and 1 mod 32, so quad rows sy and sy + 1 start one bank apart
-constexpr int kCG = 8;                         // column groups per warp task (lanes: 8 groups x 4 row slices)
-constexpr int kRS = 32 / kCG;                  // row slices per warp
 constexpr int kML = PD_MAX_LEVELS;
 constexpr int kStageIters = ((kTH + 1) * ((kResizeBW + 3) / 4) + kThreads - 1) / kThreads;  // staged words per thread
 static_assert(kTP >= kResizeBW + 8 && kTP % 16 == 0, "staged row pitch");
@@ -73,11 +71,14 @@ __device__ __forceinline__ uint32_t pack4(uint32_t o0, uint32_t o1, uint32_t o2,
     return __byte_perm(__byte_perm(o0, o1, 0x0073), __byte_perm(o2, o3, 0x0073), 0x5410);
 }
 
+// kCG column groups per warp task; the warp's lanes are kCG groups x kRS row slices.
+template <int kCG>
 __global__ void __launch_bounds__(kThreads, 5) k_resize(const FrameDesc *__restrict__ frames,
                                                         const LevelDesc *__restrict__ levels,
                                                         const int32_t *__restrict__ tabs,
                                                         uint8_t *__restrict__ pyr,
                                                         const ResizeItem *__restrict__ items) {
+    constexpr int kRS = 32 / kCG;
     extern __shared__ __align__(16) uint8_t smem[];
     uint8_t *tile = smem + kOffTile;
     uint32_t *quad = reinterpret_cast<uint32_t *>(smem + kOffQuad);
@@ -297,14 +298,22 @@ __global__ void __launch_bounds__(kThreads, 5) k_resize(const FrameDesc *__restr
 }  // namespace
 
 cudaError_t init_resize() {
-    return cudaFuncSetAttribute(k_resize, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(k_resize<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resize<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resize<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    return e;
 }
 
 cudaError_t launch_resize(cudaStream_t s, const FrameDesc *d_frames, const LevelDesc *d_levels,
                           const int32_t *d_tabs, uint8_t *pyr, const ResizeItem *d_items,
-                          int n_items) {
+                          int n_items, int k1_groups) {
     if (n_items <= 0) return cudaSuccess;
-    k_resize<<<n_items, kThreads, kSmemBytes, s>>>(d_frames, d_levels, d_tabs, pyr, d_items);
+    if (k1_groups == 4)
+        k_resize<4><<<n_items, kThreads, kSmemBytes, s>>>(d_frames, d_levels, d_tabs, pyr, d_items);
+    else if (k1_groups == 16)
+        k_resize<16><<<n_items, kThreads, kSmemBytes, s>>>(d_frames, d_levels, d_tabs, pyr, d_items);
+    else
+        k_resize<8><<<n_items, kThreads, kSmemBytes, s>>>(d_frames, d_levels, d_tabs, pyr, d_items);
     return cudaGetLastError();
 }
 

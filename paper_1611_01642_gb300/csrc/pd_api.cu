@@ -66,6 +66,7 @@ struct Plan {
     std::vector<TcItem> t_items;
     std::vector<CnnItem> cnn_items;
     std::vector<int32_t> tabs;
+    int tc_rows = kTcChunk;  // tensor-core K4 window rows per item (tuning; kept by clear())
     int64_t pyr_bytes = 0;
     int64_t score_floats = 0;
     int32_t atlas_rows = 0;
@@ -289,6 +290,7 @@ struct pd_handle {
     float tile_cost[kSvmShapes] = {kDefaultTileCost[0], kDefaultTileCost[1], kDefaultTileCost[2],
                                    kDefaultTileCost[3], kDefaultTileCost[4], kDefaultTileCost[5],
                                    kDefaultTileCost[6]};
+    pd_tuning tuning{8, kTcChunk};  // launch shapes of the default path (autotuner output)
     // last batch
     Plan plan;
     // cached plan + captured graph for a repeated batch shape
@@ -388,11 +390,11 @@ void plan_windows(std::vector<SvmItem> &out, int li, int rows, int cols, const f
 }
 
 // Tensor-core K4 items of a rows x cols score map: strips of kTcStrip window
-// columns, each cut into near-equal pieces of at most kTcChunk window rows
+// columns, each cut into near-equal pieces of at most `chunk` window rows
 // (a piece also reads the 14 block rows below its last window row).
-void plan_tc(std::vector<TcItem> &out, int li, int rows, int cols) {
+void plan_tc(std::vector<TcItem> &out, int li, int rows, int cols, int chunk) {
     if (rows <= 0 || cols <= 0) return;
-    const int pieces = (rows + kTcChunk - 1) / kTcChunk;
+    const int pieces = (rows + chunk - 1) / chunk;
     for (int x = 0; x < cols; x += kTcStrip)
         for (int k = 0; k < pieces; ++k)
             out.push_back({li, x, (int)((int64_t)rows * k / pieces), (int)((int64_t)rows * (k + 1) / pieces)});
@@ -511,7 +513,7 @@ void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int
     for (int cy = 0; cy < L.Hc; cy += kCellTH)
         for (int cx = 0; cx < L.Wc; cx += kCellTW) p.c_items.push_back({li, cx, cy, 0});
     plan_windows(p.s_items, li, L.rows, L.cols, tile_cost);
-    plan_tc(p.t_items, li, L.rows, L.cols);
+    plan_tc(p.t_items, li, L.rows, L.cols, p.tc_rows);
     p.atlas_rows += L.Hc;
     p.score_floats += (int64_t)L.rows * L.cols;
     p.max_wc = std::max(p.max_wc, L.Wc);
@@ -810,6 +812,7 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
     // tables (frames of different sizes do not share them).
     {
         Plan one;
+        one.tc_rows = kTcMinChunk;  // the most tensor-core K4 items any tuning can ask for
         plan_frame(one, *params, nullptr, params->max_width, params->max_height, params->max_width);
         int64_t s_bound = 0;
         for (const LevelDesc &L : one.levels) {
@@ -988,6 +991,7 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
     if (!reuse) {
         invalidate_cache(h);
         p.clear();
+        p.tc_rows = h->tuning.tc_item_rows;
         for (int f = 0; f < n_frames; ++f) {
             int r = plan_frame(p, h->p, d_frames[f], widths[f], heights[f], pitches[f],
                                h->proposal ? kSparseTileCost : h->tile_cost, h->proposal);
@@ -1025,7 +1029,7 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
         PD_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), q));
         if (timed) PD_CUDA(h, record(h->stage_ev[0], q));
         PD_CUDA(h, launch_resize(q, df, dl, dptr<int32_t>(h, o.tabs), h->d_pyr, dptr<ResizeItem>(h, o.r_items),
-                                 (int)p.r_items.size()));
+                                 (int)p.r_items.size(), h->tuning.k1_groups));
         if (timed) PD_CUDA(h, record(h->stage_ev[5], q));
         const uint32_t *cf = nullptr, *sf = nullptr;
         if (h->proposal) {
@@ -1345,6 +1349,22 @@ int pd_set_proposal(pd_handle *h, int enable, float keep_logit_threshold) {
     return PD_OK;
 }
 
+int pd_set_tuning(pd_handle *h, const pd_tuning *t) {
+    if (!h || !t) return PD_EINVAL;
+    if ((t->k1_groups != 4 && t->k1_groups != 8 && t->k1_groups != 16) || t->tc_item_rows < kTcMinChunk ||
+        t->tc_item_rows > kTcChunk)
+        return fail(h, PD_EINVAL, "tuning: k1_groups %d, tc_item_rows %d", t->k1_groups, t->tc_item_rows);
+    h->tuning = *t;
+    invalidate_cache(h);
+    return PD_OK;
+}
+
+int pd_get_tuning(const pd_handle *h, pd_tuning *t) {
+    if (!h || !t) return PD_EINVAL;
+    *t = h->tuning;
+    return PD_OK;
+}
+
 int pd_set_proposal_levels(pd_handle *h, int level_step) {
     if (!h) return PD_EINVAL;
     if (level_step < 1 || level_step > 16) return fail(h, PD_EINVAL, "level step %d outside [1, 16]", level_step);
@@ -1442,7 +1462,7 @@ int pd_resize_levels(pd_handle *h, void *stream, const uint8_t *d_frame, int W, 
     if (r != PD_OK) return r;
     PD_CUDA(h, launch_resize(s, dptr<FrameDesc>(h, o.frames), dptr<LevelDesc>(h, o.levels),
                              dptr<int32_t>(h, o.tabs), d_levels, dptr<ResizeItem>(h, o.r_items),
-                             (int)p.r_items.size()));
+                             (int)p.r_items.size(), h->tuning.k1_groups));
     return PD_OK;
 }
 
@@ -1487,6 +1507,7 @@ int pd_window_scores(pd_handle *h, void *stream, const float *d_hog, int64_t hog
         (reinterpret_cast<uintptr_t>(d_hog) & 15) || (reinterpret_cast<uintptr_t>(d_lbp) & 15))
         return fail(h, PD_EINVAL, "pd_window_scores: bad argument");
     Plan p;
+    p.tc_rows = h->tuning.tc_item_rows;
     plan_level(p, 0, 0, 8 * cells_x, 8 * cells_y, 8 * cells_x, 8 * cells_y, 0, 8 * cells_x, nullptr,
                h->tile_cost);
     p.c_items.clear();

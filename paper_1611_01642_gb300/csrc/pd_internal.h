@@ -72,7 +72,8 @@ constexpr int kCellTW = 15;     // cells per cell tile along x (128 threads = 8*
 constexpr int kCellTH = 8;      // cells per cell tile along y
 constexpr int kSvmShapes = 7;   // K4 tile shapes: 32x16, 64x8, 32x8, 64x4, 64x2, 32x12, 32x4 windows
 constexpr int kTcStrip = 104;   // tensor-core K4: window columns per item
-constexpr int kTcChunk = 64;    // tensor-core K4: window rows per item at most
+constexpr int kTcChunk = 64;    // tensor-core K4: window rows per item at most (tunable down to kTcMinChunk)
+constexpr int kTcMinChunk = 8;
 
 struct SvmShapeInfo {
     int tw, th;     // windows per tile along x / y
@@ -100,9 +101,10 @@ cudaError_t init_nms();
 cudaError_t init_resize();
 
 // Kernel launchers (host functions defined next to their kernels).
+// k1_groups: column groups per warp task (4, 8 or 16)
 cudaError_t launch_resize(cudaStream_t s, const FrameDesc *d_frames, const LevelDesc *d_levels,
                           const int32_t *d_tabs, uint8_t *pyr, const ResizeItem *d_items,
-                          int n_items);
+                          int n_items, int k1_groups = 8);
 // feat: kFeatHog | kFeatLbp (the features the pipeline uses), plus
 // kFeatHogBlock for per-block HOG (36 planes: the 4 block-restricted
 // histograms of every cell, plane 9 q + bin)

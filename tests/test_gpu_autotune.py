@@ -77,3 +77,55 @@ def test_autotuner_measures_caches_and_applies(template, tmp_path, monkeypatch):
         assert np.allclose(pd.pd_get_tile_costs(d.h), cost)
     finally:
         d.close()
+
+
+def _boxes(d, n):
+    return [[tuple(r) for r in d.boxes(f).tolist()] for f in range(n)]
+
+
+def test_default_path_results_identical_for_every_launch_shape(template):
+    """The pyramid kernel's column groups per warp task and the tensor-core score kernel's window
+    rows per item change the work split only: levels, score maps and boxes are bit-identical."""
+    from paper_1611_01642_gb300 import build as bld
+    bld.build()
+    w, b = template
+    frames = [synth.make_scene(1242, 375, 2, 9), synth.make_scene(700, 500, 3, 10)]
+    dev = [torch.from_numpy(f).cuda() for f in frames]
+    d = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=2, max_width=1242, max_height=500)
+    try:
+        assert pd.pd_get_tuning(d.h) == {"k1_groups": 8, "tc_item_rows": 64}
+        ref, ref_b = _scores(d, dev), _boxes(d, 2)
+        for g, r in [(4, 64), (16, 64), (8, 8), (8, 16), (4, 37), (16, 48)]:
+            pd.pd_set_tuning(d.h, g, r)
+            got = _scores(d, dev)
+            for a, x in zip(ref, got):
+                assert np.array_equal(a, x), (g, r)
+            assert _boxes(d, 2) == ref_b, (g, r)
+        for bad in [(2, 64), (8, 7), (8, 65)]:
+            with pytest.raises(pd.PDError):
+                pd.pd_set_tuning(d.h, *bad)
+    finally:
+        d.close()
+
+
+def test_default_path_autotuner_picks_caches_and_applies(template, tmp_path, monkeypatch):
+    from paper_1611_01642_gb300 import autotune
+    from paper_1611_01642_gb300 import build as bld
+    bld.build()
+    monkeypatch.setenv("XDG_CACHE_HOME", str(tmp_path))
+    w, b = template
+    frames = [synth.make_scene(1242, 375, 2, i) for i in range(8)]
+    t = autotune.tune_default_path(frames, w, b, FACTOR)
+    assert t["k1_groups"] in autotune.K1_GROUPS and t["tc_item_rows"] in autotune.TC_ITEM_ROWS
+    path = tmp_path / "paper_1611_01642_gb300" / "default_path.json"
+    entry = next(iter(json.loads(path.read_text()).values()))
+    assert entry["tuning"] == t
+    assert min(entry["pyramid_ms"], key=entry["pyramid_ms"].get) == str(t["k1_groups"])
+    assert min(entry["scores_ms"], key=entry["scores_ms"].get) == str(t["tc_item_rows"])
+    monkeypatch.setattr(autotune, "_stage_ms", lambda *a, **k: pytest.fail("measured again"))
+    d = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=8, max_width=1242, max_height=375)
+    try:
+        assert autotune.apply_default(d, frames, w, b, FACTOR) == t
+        assert pd.pd_get_tuning(d.h) == t
+    finally:
+        d.close()
