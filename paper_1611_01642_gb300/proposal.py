@@ -241,6 +241,53 @@ def recalibrate(path: str, out: str, calib_frames: int = 16, val_frames: int = 1
         det.close()
 
 
+def _scene_worker(args):
+    import synth
+    width, height, key, i = args
+    return synth.make_scene(width, height, key, i, n_sil=("poisson", 10.0), heights=(48, "0.8H"))
+
+
+def _scene_pool(width, height, key, count, workers=0):
+    """Frames i < count of scenes [key, i] (as _scene_batches), generated by spawned worker processes."""
+    import multiprocessing as mp
+    import os
+    n = workers or os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(n) as pool:
+        return pool.map(_scene_worker, [(width, height, key, i) for i in range(count)], chunksize=4)
+
+
+def _curve(det: Detector, a, sizes):
+    """Keep fraction at the calibrated recall against the training-set size: one model per size, all
+    from the same initial parameters and for the same number of batches (a small set is visited more
+    times), so that only the amount of training data differs."""
+    pool = _scene_pool(a.width, a.height, 100, max(sizes), a.workers)
+    calib = list(_scene_batches(a.width, a.height, 101, 0, a.calib_frames, a.batch))
+    val = list(_scene_batches(a.width, a.height, 101, a.calib_frames, a.val_frames, a.batch))
+    for n in sizes:
+        order_rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([102, n])))
+
+        def batches():
+            done = 0
+            while done < a.curve_batches:
+                idx = order_rng.permutation(n)
+                for i0 in range(0, n, a.batch):
+                    if done == a.curve_batches:
+                        return
+                    yield [pool[i] for i in idx[i0:i0 + a.batch]]
+                    done += 1
+        cfg = TrainConfig(lr=a.lr, steps_per_batch=a.steps_per_batch, total_batches=a.curve_batches if a.cosine else 0)
+        t0 = time.time()
+        params, hist = train(det, batches(), cfg, log=lambda *x: None)
+        train_s = time.time() - t0
+        pd_cnn_set_params(det.h, params)
+        det.set_proposal(False, 0.0, level_step=a.level_step)
+        tau = calibrate_sparse(det, calib, a.recall)
+        m = sparse_metrics(det, val, tau)
+        print(json.dumps(dict(train_frames=n, batches=a.curve_batches, steps=a.curve_batches * a.steps_per_batch,
+                              level_step=a.level_step, final_loss=hist[-1], keep_logit_threshold=tau,
+                              train_seconds=train_s, **m)), flush=True)
+
+
 def main(argv=None):
     import argparse
     ap = argparse.ArgumentParser(description="Train and calibrate the window proposal on synthetic scenes.")
@@ -259,8 +306,17 @@ def main(argv=None):
     ap.add_argument("--calibrate", choices=["window", "path"], default="path",
                     help="keep threshold from window-level recall, or from the sparse path's own recall")
     ap.add_argument("--svm", default=None, help="npz with w, b (default: the seed-0 template)")
-    ap.add_argument("--out", required=True)
+    ap.add_argument("--level-step", type=int, default=1,
+                    help="the network runs on every level_step-th level when calibrating (stored in the meta)")
+    ap.add_argument("--curve", default=None,
+                    help="comma-separated training-set sizes: train one model per size (same start, "
+                         "--curve-batches batches each) and print its calibrated keep fraction; no checkpoint")
+    ap.add_argument("--curve-batches", type=int, default=192)
+    ap.add_argument("--workers", type=int, default=0, help="processes generating the scenes (0: all cores)")
+    ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
+    if a.curve is None and a.out is None:
+        ap.error("--out is required (or --curve)")
     import os
     import torch  # noqa: F401  (CUDA context for the frames)
     from . import build as bld
@@ -272,8 +328,11 @@ def main(argv=None):
     det = Detector(w, b, max_frames=a.batch, max_width=a.width, max_height=a.height,
                    pyr_factor=float(np.float32(a.factor)))
     try:
+        if a.curve is not None:
+            _curve(det, a, [int(v) for v in a.curve.split(",")])
+            return
         # training frames: a fixed pool, visited once per epoch in a seeded order
-        pool = [f for batch in _scene_batches(a.width, a.height, 100, 0, a.train_frames, a.batch) for f in batch]
+        pool = _scene_pool(a.width, a.height, 100, a.train_frames, a.workers)
         order_rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([102])))
 
         def epochs():
@@ -287,6 +346,7 @@ def main(argv=None):
         params, hist = train(det, epochs(), cfg)
         train_s = time.time() - t0
         pd_cnn_set_params(det.h, params)
+        det.set_proposal(False, 0.0, level_step=a.level_step)
         calib = list(_scene_batches(a.width, a.height, 101, 0, a.calib_frames, a.batch))
         s, z = window_stats(det, calib)
         tau_window = calibrate(s, z, a.recall)
@@ -295,6 +355,7 @@ def main(argv=None):
         m = sparse_metrics(det, val, tau)
         meta = dict(recipe=vars(a), train=asdict(cfg), train_seconds=train_s, final_loss=hist[-1],
                     first_loss=hist[0], keep_logit_threshold=tau, window_level_threshold=tau_window,
+                    level_step=a.level_step,
                     calib_window_recall=float(np.mean(z[s > 0] > tau)) if (s > 0).any() else 1.0,
                     validation=m)
         save_checkpoint(a.out, params, meta)
