@@ -128,6 +128,81 @@ __device__ __forceinline__ bool suppresses(const float4 &a, const float4 &b, flo
 
 constexpr int kSortChunk = 8192;  // keys per shared-memory chunk of the large-cap sort (64 KB)
 
+// Ascending bitonic sort of m = R * kThreads keys in shared memory k, with
+// each thread holding the R consecutive keys [tid R, tid R + R) in registers:
+// compare-exchange steps of stride j < R run in registers, R <= j < 32 R with
+// warp shuffles (the partner is lane ^ j / R, same register), and only
+// j >= 32 R through shared memory with a block barrier per step. Same network
+// (and result) as bitonic_smem, with log2(m / 32R)-many fewer barriers per
+// stage.
+template <int R>
+__device__ __forceinline__ void bitonic_hybrid(unsigned long long *k, int m, int tid) {
+    unsigned long long v[R];
+    const int base = tid * R, lane = tid & 31;
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = k[base + i];
+    for (int len = 2; len <= m; len <<= 1) {
+        int j = len >> 1;
+        if (j >= 32 * R) {
+            // large strides: through shared memory
+#pragma unroll
+            for (int i = 0; i < R; ++i) k[base + i] = v[i];
+            __syncthreads();
+            for (; j >= 32 * R; j >>= 1) {
+                for (int i = tid; i < m; i += kThreads) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const unsigned long long a = k[i], b = k[ixj];
+                        if ((a > b) == ((i & len) == 0)) {
+                            k[i] = b;
+                            k[ixj] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int i = 0; i < R; ++i) v[i] = k[base + i];
+            __syncthreads();  // every thread has read its keys before the next stage writes
+        }
+        for (; j >= R; j >>= 1) {
+            // partner: lane ^ (j / R), same register
+            const int lm = j / R;
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const int g = base + i;
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[i], lm);
+                const bool lower = (lane & lm) == 0, asc = (g & len) == 0;
+                v[i] = (lower == asc) ? (v[i] < o ? v[i] : o) : (v[i] < o ? o : v[i]);
+            }
+        }
+        // in registers: strides R/2 .. 1 (compile-time, so v stays in registers);
+        // a stage of length len has only the strides below len
+#pragma unroll
+        for (int jj = R / 2; jj > 0; jj >>= 1) {
+            if (jj >= len) continue;
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const int p = i ^ jj;
+                if (p > i) {
+                    const bool asc = ((base + i) & len) == 0;
+                    const unsigned long long a = v[i], b = v[p];
+                    const bool sw = (a > b) == asc;
+                    v[i] = sw ? b : a;
+                    v[p] = sw ? a : b;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) k[base + i] = v[i];
+    __syncthreads();
+}
+
+// Ascending sort of m (a power of two) keys in shared memory: the hybrid
+// bitonic network for 1024 <= m <= 8192, the plain one otherwise.
+__device__ __forceinline__ void bitonic_sort_smem(unsigned long long *k, int m, int tid);
+
 // Ascending bitonic sort of m (a power of two) keys in shared memory.
 __device__ __forceinline__ void bitonic_smem(unsigned long long *k, int m, int tid) {
     for (int len = 2; len <= m; len <<= 1) {
@@ -147,6 +222,16 @@ __device__ __forceinline__ void bitonic_smem(unsigned long long *k, int m, int t
     }
 }
 
+__device__ __forceinline__ void bitonic_sort_smem(unsigned long long *k, int m, int tid) {
+    switch (m) {
+        case 1024: bitonic_hybrid<1>(k, m, tid); break;
+        case 2048: bitonic_hybrid<2>(k, m, tid); break;
+        case 4096: bitonic_hybrid<4>(k, m, tid); break;
+        case 8192: bitonic_hybrid<8>(k, m, tid); break;
+        default: bitonic_smem(k, m, tid);  // (16384 keys would need 32 registers per thread for them)
+    }
+}
+
 // Large caps: keys[0, np) (np a power of two >= n, padded with ~0) sorted
 // ascending: chunks of up to kSortChunk keys sorted in shared memory `sm`,
 // then merge passes doubling the run length, ping-ponging through `tmp`
@@ -157,7 +242,7 @@ __device__ void sort_large(unsigned long long *keys, unsigned long long *tmp, in
     for (int c0 = 0; c0 < np; c0 += C) {
         for (int i = tid; i < C; i += kThreads) sm[i] = keys[c0 + i];
         __syncthreads();
-        bitonic_smem(sm, C, tid);
+        bitonic_sort_smem(sm, C, tid);
         for (int i = tid; i < C; i += kThreads) keys[c0 + i] = sm[i];
         __syncthreads();
     }
@@ -276,7 +361,7 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
         // the boxes region (cap float4s) is free until the decode below
         sort_large(keys, reinterpret_cast<unsigned long long *>(gbx), np, skeys, tid);
     } else {
-        bitonic_smem(keys, np, tid);
+        bitonic_sort_smem(keys, np, tid);
     }
     for (int i = tid; i < n; i += kThreads) supp[i] = 0;
     __syncthreads();

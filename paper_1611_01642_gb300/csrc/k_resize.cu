@@ -39,8 +39,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kTW = kResizeTW;                 // 128 source columns per tile
 constexpr int kTH = kResizeTH;                 // 32 source rows per tile
 constexpr int kTP = 176;                       // staged byte row pitch (>= kResizeBW + 8, 16-byte multiple)
-constexpr int kQP = 193;                       // quad row pitch in words: >= resize_quad_index(kResizeBW - 2) + 1
-                                               // and 1 mod 32, so quad rows sy and sy + 1 start one bank apart
+constexpr int kQP = kResizeQP;                 // quad row pitch in words
 constexpr int kML = PD_MAX_LEVELS;
 constexpr int kStageIters = ((kTH + 1) * ((kResizeBW + 3) / 4) + kThreads - 1) / kThreads;  // staged words per thread
 static_assert(kTP >= kResizeBW + 8 && kTP % 16 == 0, "staged row pitch");
@@ -252,15 +251,16 @@ __global__ void __launch_bounds__(kThreads, 5) k_resize(const FrameDesc *__restr
         const int x = G * gg;
         const int y0 = rg.z + j, re = rg.z + rg.w;
         const int nrow = y0 < re ? (re - y0 + kRS - 1) / kRS : 0;
-        const int32_t *yp = tabs + L.ytab_off + y0;
+        const int2 *yp = reinterpret_cast<const int2 *>(tabs + L.ytab_off) + y0;
         uint8_t *op = pyr + L.img_off + x + (size_t)y0 * pitch;
         const size_t ostep = (size_t)kRS * pitch;
         if (G == 4) {
             const uint32_t a0 = quad_base + 4u * (qo & 255u), a1 = quad_base + 4u * ((qo >> 8) & 255u);
             const uint32_t a2 = quad_base + 4u * ((qo >> 16) & 255u), a3 = quad_base + 4u * (qo >> 24);
-            auto px4 = [&](int32_t ey, uint32_t &o0, uint32_t &o1, uint32_t &o2, uint32_t &o3) {
-                const uint32_t ro = (uint32_t)(ey >> 11) * (uint32_t)(kQP * 4);
-                const uint32_t wb = ((uint32_t)ey & 2047u) << 2, wt = 8192u - wb;
+            // row entry: byte offset of the top source row's quad row, packed scaled row weights
+            auto px4 = [&](int2 e, uint32_t &o0, uint32_t &o1, uint32_t &o2, uint32_t &o3) {
+                const uint32_t ro = (uint32_t)e.x;
+                const uint32_t wt = (uint32_t)e.y & 0xffffu, wb = (uint32_t)e.y >> 16;
                 o0 = q11_pixel(a0 + ro, (uint32_t)wx.x, wt, wb);
                 o1 = q11_pixel(a1 + ro, (uint32_t)wx.y, wt, wb);
                 o2 = q11_pixel(a2 + ro, (uint32_t)wx.z, wt, wb);
@@ -285,10 +285,9 @@ __global__ void __launch_bounds__(kThreads, 5) k_resize(const FrameDesc *__restr
         } else {
             const uint32_t a0 = quad_base + 4u * (qo & 255u);
             for (int i = 0; i < nrow; ++i, yp += kRS, op += ostep) {
-                const int32_t ey = __ldg(yp);
-                const uint32_t ro = (uint32_t)(ey >> 11) * (uint32_t)(kQP * 4);
-                const uint32_t wb = ((uint32_t)ey & 2047u) << 2, wt = 8192u - wb;
-                *op = (uint8_t)(q11_pixel(a0 + ro, (uint32_t)wx.x, wt, wb) >> 24);
+                const int2 e = __ldg(yp);
+                *op = (uint8_t)(q11_pixel(a0 + (uint32_t)e.x, (uint32_t)wx.x, (uint32_t)e.y & 0xffffu,
+                                          (uint32_t)e.y >> 16) >> 24);
             }
         }
         }

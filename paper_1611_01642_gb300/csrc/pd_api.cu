@@ -408,7 +408,9 @@ void order_tc(std::vector<TcItem> &t) {
 }
 
 // K1 tables of one level (Section 4.4 resample, reading Q).
-//   ytab: per output row its Q11 entry (source row << 11 | weight);
+//   ytab: per output row an int2: the byte offset of its top source row's
+//         quad row (source row * 4 * kResizeQP; the kernel subtracts the
+//         tile's first row) and its scaled row weights (8192 - 4 a) | 4 a << 16;
 //   ybnd: per source-tile row t, the first output row whose source row is >= 32 t;
 //   xtab: per group of G output columns (G = 4; G = 1 when a group of 4
 //         would reach more than kResizeBW - 2 source columns past the left
@@ -455,8 +457,15 @@ void k1_tables(Plan &p, LevelDesc &L, int W, int H, int Wk, int Hk) {
             w |= (uint32_t)resize_quad_index(src(g * G + i) - owner * kResizeTW) << (8 * i);
         p.tabs.push_back((int32_t)w);
     }
+    std::vector<int32_t> ey(Hk);
+    for (int y = 0; y < Hk; ++y) ey[y] = q11_entry(y, H, Hk);
+    while (p.tabs.size() % 2) p.tabs.push_back(0);
     L.ytab_off = (int32_t)p.tabs.size();
-    for (int y = 0; y < Hk; ++y) p.tabs.push_back(q11_entry(y, H, Hk));
+    for (int y = 0; y < Hk; ++y) {
+        const uint32_t a = (uint32_t)ey[y] & 2047u;
+        p.tabs.push_back((ey[y] >> 11) * 4 * kResizeQP);
+        p.tabs.push_back((int32_t)((8192u - 4u * a) | ((4u * a) << 16)));
+    }
     L.xbnd_off = (int32_t)p.tabs.size();
     {
         int g = 0;
@@ -469,7 +478,7 @@ void k1_tables(Plan &p, LevelDesc &L, int W, int H, int Wk, int Hk) {
     {
         int y = 0;
         for (int t = 0; t <= (H + kResizeTH - 1) / kResizeTH; ++t) {
-            while (y < Hk && (p.tabs[L.ytab_off + y] >> 11) < t * kResizeTH) ++y;
+            while (y < Hk && (ey[y] >> 11) < t * kResizeTH) ++y;
             p.tabs.push_back(y);
         }
     }

@@ -45,7 +45,8 @@ struct LevelDesc {
     int32_t rows, cols; // score map size (0 when no window fits)
     int32_t xtab_off;   // K1 column weights: per group of rgroup output columns an int4 of packed
                         // weights (2048 - a) | a << 16 (16-byte aligned; unused lanes 0)
-    int32_t ytab_off;   // Q11 source-row table of this level (Hk entries: row << 11 | weight)
+    int32_t ytab_off;   // K1 row table: per output row an int2 {byte offset of its top source row's
+                        // quad row (source row * 4 * kResizeQP), (8192 - 4 a) | 4 a << 16}
     int32_t citem0;     // index of this level's first K2+K3 item
     int32_t ctx;        // K2+K3 tiles per row of cells
     int32_t xbnd_off;   // per K1 source-tile column t: first column group whose first source is >= 128 t
@@ -68,6 +69,9 @@ constexpr int kResizeTH = 32;   // source tile height (pixels)
 constexpr int kResizeBW = 160;  // source bytes staged per tile row at most (tile + right halo)
 // K1 shared-memory quad word of source column d of a tile row (skewed by d / 32)
 __host__ __device__ inline int resize_quad_index(int d) { return d + (d >> 5); }
+// K1 quad row pitch in words: > resize_quad_index(kResizeBW - 2) and 1 mod 32, so that
+// quad rows sy and sy + 1 start one bank apart
+constexpr int kResizeQP = 193;
 constexpr int kCellTW = 15;     // cells per cell tile along x (128 threads = 8*15+8 columns)
 constexpr int kCellTH = 8;      // cells per cell tile along y
 constexpr int kSvmShapes = 7;   // K4 tile shapes: 32x16, 64x8, 32x8, 64x4, 64x2, 32x12, 32x4 windows

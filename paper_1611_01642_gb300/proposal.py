@@ -25,8 +25,8 @@ from dataclasses import asdict, dataclass, field
 
 import numpy as np
 
-from . import (CNN_PARAMS, Detector, PD_OK, pd_cnn_get_params, pd_cnn_set_params, pd_cnn_train_loss,
-               pd_cnn_train_step)
+from . import (CNN_PARAMS, Detector, PD_EOVERFLOW, PD_OK, pd_cnn_get_params, pd_cnn_set_params,
+               pd_cnn_train_loss, pd_cnn_train_step)
 
 
 @dataclass
@@ -81,7 +81,9 @@ def train(det: Detector, batches, cfg: TrainConfig, params: np.ndarray | None = 
     t0 = time.time()
     for b, frames in enumerate(batches):
         det.detect(_to_device(frames))
-        if det.sync() != PD_OK:
+        # labels come from the score maps, which a frame with more NMS candidates
+        # than the cap (PD_EOVERFLOW: no boxes for it) still has in full
+        if det.sync() not in (PD_OK, PD_EOVERFLOW):
             raise RuntimeError("detect failed while labelling")
         if pos_weight <= 0:
             s = _flat_scores(det, len(frames))
@@ -109,12 +111,12 @@ def window_stats(det: Detector, batches, threshold: float = 0.0):
         dev = _to_device(frames)
         det.set_proposal(False)
         det.detect(dev)
-        if det.sync() != PD_OK:
+        if det.sync() not in (PD_OK, PD_EOVERFLOW):  # (scores only: an NMS overflow is fine)
             raise RuntimeError("detect failed")
         S.append(_flat_scores(det, len(frames)))
         det.set_proposal(True, float("-inf"))
         det.detect(dev)
-        if det.sync() != PD_OK:
+        if det.sync() not in (PD_OK, PD_EOVERFLOW):  # (scores only: an NMS overflow is fine)
             raise RuntimeError("detect failed")
         Z.append(_flat_scores(det, len(frames), logits=True))
     det.set_proposal(False)
@@ -169,12 +171,12 @@ def sparse_metrics(det: Detector, batches, tau: float, threshold: float = 0.0):
         dev = _to_device(frames)
         det.set_proposal(False)
         det.detect(dev)
-        if det.sync() != PD_OK:
+        if det.sync() not in (PD_OK, PD_EOVERFLOW):  # (scores only: an NMS overflow is fine)
             raise RuntimeError("detect failed")
         s = _flat_scores(det, len(frames))
         det.set_proposal(True, tau)
         det.detect(dev)
-        if det.sync() != PD_OK:
+        if det.sync() not in (PD_OK, PD_EOVERFLOW):  # (scores only: an NMS overflow is fine)
             raise RuntimeError("detect failed")
         sp = _flat_scores(det, len(frames))
         zkept += int((_flat_scores(det, len(frames), logits=True) > tau).sum())
