@@ -135,72 +135,117 @@ constexpr int kSortChunk = 8192;  // keys per shared-memory chunk of the large-c
 // j >= 32 R through shared memory with a block barrier per step. Same network
 // (and result) as bitonic_smem, with log2(m / 32R)-many fewer barriers per
 // stage.
+// The register and shuffle steps of one stage (stride j and below) for the
+// R keys a thread holds, whose global indices are g0 .. g0 + R - 1.
 template <int R>
-__device__ __forceinline__ void bitonic_hybrid(unsigned long long *k, int m, int tid) {
+__device__ __forceinline__ void bitonic_reg_steps(unsigned long long (&v)[R], int g0, int j, int len, int lane) {
+    for (; j >= R; j >>= 1) {
+        // partner: lane ^ (j / R), same register
+        const int lm = j / R;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[i], lm);
+            const bool lower = (lane & lm) == 0, asc = ((g0 + i) & len) == 0;
+            v[i] = (lower == asc) ? (v[i] < o ? v[i] : o) : (v[i] < o ? o : v[i]);
+        }
+    }
+    // in registers: strides R/2 .. 1 (compile-time, so v stays in registers);
+    // a stage of length len has only the strides below len
+#pragma unroll
+    for (int jj = R / 2; jj > 0; jj >>= 1) {
+        if (jj >= len) continue;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int p = i ^ jj;
+            if (p > i) {
+                const bool asc = ((g0 + i) & len) == 0;
+                const unsigned long long a = v[i], b = v[p];
+                const bool sw = (a > b) == asc;
+                v[i] = sw ? b : a;
+                v[p] = sw ? a : b;
+            }
+        }
+    }
+}
+
+// Compare-exchange steps of stride j .. jmin (>= jmin) over k[lo, lo + m) in
+// shared memory, one block barrier per step (global indices lo + i).
+__device__ __forceinline__ void bitonic_smem_steps(unsigned long long *k, int lo, int m, int j, int jmin, int len,
+                                                   int tid) {
+    for (; j >= jmin; j >>= 1) {
+        for (int i = tid; i < m; i += kThreads) {
+            const int ixj = i ^ j;
+            if (ixj > i) {
+                const unsigned long long a = k[lo + i], b = k[lo + ixj];
+                if ((a > b) == (((lo + i) & len) == 0)) {
+                    k[lo + i] = b;
+                    k[lo + ixj] = a;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Ascending bitonic sort of m = R * kThreads keys k[lo, lo + m) in shared
+// memory (as part of a larger network when lo > 0: directions follow the
+// global index), each thread holding the R consecutive keys [lo + tid R,
+// lo + tid R + R) in registers: compare-exchange steps of stride j < R run in
+// registers, R <= j < 32 R with warp shuffles (the partner is lane ^ j / R,
+// same register), and only j >= 32 R through shared memory with a block
+// barrier per step. Same network (and result) as bitonic_smem, with
+// log2(32R)-many fewer barriers per stage. Stages len = 2 .. len_max.
+template <int R>
+__device__ __forceinline__ void bitonic_hybrid(unsigned long long *k, int lo, int len_max, int tid) {
+    constexpr int m = R * kThreads;
     unsigned long long v[R];
-    const int base = tid * R, lane = tid & 31;
+    const int base = lo + tid * R, lane = tid & 31;
 #pragma unroll
     for (int i = 0; i < R; ++i) v[i] = k[base + i];
-    for (int len = 2; len <= m; len <<= 1) {
+    for (int len = 2; len <= len_max; len <<= 1) {
         int j = len >> 1;
         if (j >= 32 * R) {
             // large strides: through shared memory
 #pragma unroll
             for (int i = 0; i < R; ++i) k[base + i] = v[i];
             __syncthreads();
-            for (; j >= 32 * R; j >>= 1) {
-                for (int i = tid; i < m; i += kThreads) {
-                    const int ixj = i ^ j;
-                    if (ixj > i) {
-                        const unsigned long long a = k[i], b = k[ixj];
-                        if ((a > b) == ((i & len) == 0)) {
-                            k[i] = b;
-                            k[ixj] = a;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
+            bitonic_smem_steps(k, lo, m, j, 32 * R, len, tid);
+            j = 16 * R;
 #pragma unroll
             for (int i = 0; i < R; ++i) v[i] = k[base + i];
             __syncthreads();  // every thread has read its keys before the next stage writes
         }
-        for (; j >= R; j >>= 1) {
-            // partner: lane ^ (j / R), same register
-            const int lm = j / R;
-#pragma unroll
-            for (int i = 0; i < R; ++i) {
-                const int g = base + i;
-                const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[i], lm);
-                const bool lower = (lane & lm) == 0, asc = (g & len) == 0;
-                v[i] = (lower == asc) ? (v[i] < o ? v[i] : o) : (v[i] < o ? o : v[i]);
-            }
-        }
-        // in registers: strides R/2 .. 1 (compile-time, so v stays in registers);
-        // a stage of length len has only the strides below len
-#pragma unroll
-        for (int jj = R / 2; jj > 0; jj >>= 1) {
-            if (jj >= len) continue;
-#pragma unroll
-            for (int i = 0; i < R; ++i) {
-                const int p = i ^ jj;
-                if (p > i) {
-                    const bool asc = ((base + i) & len) == 0;
-                    const unsigned long long a = v[i], b = v[p];
-                    const bool sw = (a > b) == asc;
-                    v[i] = sw ? b : a;
-                    v[p] = sw ? a : b;
-                }
-            }
-        }
+        bitonic_reg_steps<R>(v, base, j, len, lane);
     }
 #pragma unroll
     for (int i = 0; i < R; ++i) k[base + i] = v[i];
     __syncthreads();
 }
 
+// 16,384 keys: each 8,192-key half sorted by the hybrid network (the second
+// half descending, as the bitonic network has it), then the last stage's
+// large strides in shared memory and its small ones per half in registers.
+__device__ __forceinline__ void bitonic_hybrid_16k(unsigned long long *k, int tid) {
+    constexpr int R = 8, H = R * kThreads, M = 2 * H;
+    bitonic_hybrid<R>(k, 0, H, tid);
+    bitonic_hybrid<R>(k, H, H, tid);
+    bitonic_smem_steps(k, 0, M, M / 2, 32 * R, M, tid);
+    const int lane = tid & 31;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        unsigned long long v[R];
+        const int base = h * H + tid * R;
+#pragma unroll
+        for (int i = 0; i < R; ++i) v[i] = k[base + i];
+        bitonic_reg_steps<R>(v, base, 16 * R, M, lane);
+#pragma unroll
+        for (int i = 0; i < R; ++i) k[base + i] = v[i];
+    }
+    __syncthreads();
+}
+
 // Ascending sort of m (a power of two) keys in shared memory: the hybrid
-// bitonic network for 1024 <= m <= 8192, the plain one otherwise.
+// bitonic network for 1024 <= m <= 16384, the plain one otherwise.
 __device__ __forceinline__ void bitonic_sort_smem(unsigned long long *k, int m, int tid);
 
 // Ascending bitonic sort of m (a power of two) keys in shared memory.
@@ -224,11 +269,12 @@ __device__ __forceinline__ void bitonic_smem(unsigned long long *k, int m, int t
 
 __device__ __forceinline__ void bitonic_sort_smem(unsigned long long *k, int m, int tid) {
     switch (m) {
-        case 1024: bitonic_hybrid<1>(k, m, tid); break;
-        case 2048: bitonic_hybrid<2>(k, m, tid); break;
-        case 4096: bitonic_hybrid<4>(k, m, tid); break;
-        case 8192: bitonic_hybrid<8>(k, m, tid); break;
-        default: bitonic_smem(k, m, tid);  // (16384 keys would need 32 registers per thread for them)
+        case 1024: bitonic_hybrid<1>(k, 0, m, tid); break;
+        case 2048: bitonic_hybrid<2>(k, 0, m, tid); break;
+        case 4096: bitonic_hybrid<4>(k, 0, m, tid); break;
+        case 8192: bitonic_hybrid<8>(k, 0, m, tid); break;
+        case 16384: bitonic_hybrid_16k(k, tid); break;
+        default: bitonic_smem(k, m, tid);
     }
 }
 
