@@ -44,6 +44,7 @@ constexpr int kMaxCandidates = 16384;     // keys + flags + kept list fit in sha
 constexpr int kMaxCandidatesBig = 65536;  // keys in global scratch
 constexpr int kMaxBoxes = 16384;
 constexpr int kBatch = 64;                // greedy walk: candidates resolved per block-wide step
+constexpr int kGrid = 64;                 // culling grid: kGrid x kGrid cells over the frame
 static_assert(kThreads == 16 * kBatch, "pairwise matrix: 16 threads per batch member");
 
 __device__ __forceinline__ unsigned long long make_key(float s, int level, int wy, int wx) {
@@ -437,50 +438,68 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
         ksrc = keys;
     }
     __syncthreads();
-    // Greedy walk in batches. Warp 0 takes the next (up to) 64 candidates not
-    // yet suppressed, in order, and copies their boxes to shared memory; all
-    // threads compute the batch's pairwise suppression bits (4 pairs each);
-    // warp 0 resolves the members (a member is kept iff no kept member before
-    // it suppresses it: the candidates between members are already
-    // suppressed), and copies the kept boxes to shared memory; then every
-    // thread suppresses the later candidates against them. Same decisions as
-    // the sequential definition, with ~64x fewer block-wide barriers.
+    // Greedy walk in batches. All threads find the next (up to) 64 candidates
+    // not yet suppressed, in order (1024 positions per round), and copy their
+    // boxes to shared memory; all threads compute the batch's pairwise
+    // suppression bits (4 pairs each); warp 0 resolves the members (a member
+    // is kept iff no kept member before it suppresses it: the candidates
+    // between members are already suppressed) and copies the kept boxes to
+    // shared memory; then every thread suppresses the later candidates against
+    // them. Same decisions as the sequential definition, with ~64x fewer
+    // block-wide barriers.
+    //
+    // Culling (IoU threshold >= 0.5): if IoU(A, B) > 0.5 then A's centre lies
+    // in B (were it outside B on one axis, A and B would overlap on at most
+    // half of A's extent there, so inter <= |A| / 2, and inter > (|A| + |B|)
+    // / 3 would need |B| < |A| / 2 while inter <= |B| needs |B| > |A| / 2).
+    // Each batch marks the cells of a 64 x 64 grid over the frame that its
+    // kept boxes cover (one cell of margin for rounding); a candidate whose
+    // centre's cell is unmarked cannot be suppressed by them and skips its
+    // IoU tests.
     __shared__ int batch[kBatch];
     __shared__ float4 bbx[kBatch], kbx[kBatch];
     __shared__ unsigned long long bcol[kBatch];  // member b: bit a set iff a < b and a suppresses b
     __shared__ int n_batch, n_keep, kept_total, scan_pos;
+    __shared__ int wcnt[kThreads / 32];
+    __shared__ uint32_t gmask[kGrid * kGrid / 32];  // culling grid, one bit per cell
     int *kept_idx = reinterpret_cast<int *>(supp + ((cap + 15) & ~15));
     const int warp = tid >> 5, lane = tid & 31;
+    const bool cull = iou_thr >= 0.5f;
+    const float gsx = (float)kGrid / (float)fd.W, gsy = (float)kGrid / (float)fd.H;
     if (tid == 0) {
         kept_total = 0;
         scan_pos = 0;
     }
     __syncthreads();
     while (true) {
-        if (warp == 0) {
-            int pos = scan_pos, cnt = 0;
+        // ---- the next batch: the first kBatch alive candidates at or after scan_pos
+        {
+            int cnt = 0, pos = scan_pos;
             while (cnt < kBatch && pos < n) {
-                const int j = pos + lane;
+                const int j = pos + tid;
                 const bool alive = j < n && !supp[j];
                 const unsigned m = __ballot_sync(0xffffffffu, alive);
-                const int avail = __popc(m), take = min(avail, kBatch - cnt);
-                const int rank = __popc(m & ((1u << lane) - 1u));
-                if (alive && rank < take) {
-                    batch[cnt + rank] = j;
-                    bbx[cnt + rank] = bx[j];
+                if (lane == 0) wcnt[warp] = __popc(m);
+                __syncthreads();
+                int before = 0, total = 0;
+#pragma unroll 8
+                for (int w = 0; w < kThreads / 32; ++w) {
+                    const int c = wcnt[w];
+                    before += w < warp ? c : 0;
+                    total += c;
                 }
-                cnt += take;
-                if (take < avail) {  // stop right after the last member taken
-                    const unsigned last = __ballot_sync(0xffffffffu, alive && rank == take - 1);
-                    pos += __ffs(last);
-                    break;
+                const int rank = cnt + before + __popc(m & ((1u << lane) - 1u));
+                if (alive && rank < kBatch) {
+                    batch[rank] = j;
+                    bbx[rank] = bx[j];
+                    if (rank == kBatch - 1) scan_pos = j + 1;  // stop right after the last member
                 }
-                pos += 32;
+                if (cnt + total < kBatch && tid == 0) scan_pos = min(pos + kThreads, n);
+                cnt = min(cnt + total, kBatch);
+                pos += kThreads;
+                __syncthreads();  // wcnt reused by the next round; scan_pos, batch visible
             }
-            if (lane == 0) {
-                n_batch = cnt;
-                scan_pos = min(pos, n);
-            }
+            if (tid == 0) n_batch = cnt;
         }
         __syncthreads();
         const int nb = n_batch;
@@ -543,9 +562,35 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
         __syncthreads();
         if (kept_total >= max_boxes) break;
         const int nk = n_keep;
+        if (cull) {
+            // grid cells under the kept boxes, with one cell of margin
+            for (int i = tid; i < kGrid * kGrid / 32; i += kThreads) gmask[i] = 0u;
+            __syncthreads();
+            for (int t = tid; t < nk * kGrid; t += kThreads) {
+                const int k = t / kGrid, cy = t - k * kGrid;
+                const float4 b = kbx[k];
+                const int y0 = max((int)floorf(b.y * gsy) - 1, 0), y1 = min((int)floorf((b.y + b.w) * gsy) + 1, kGrid - 1);
+                if (cy < y0 || cy > y1) continue;
+                const int x0 = max((int)floorf(b.x * gsx) - 1, 0), x1 = min((int)floorf((b.x + b.z) * gsx) + 1, kGrid - 1);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int lo = max(x0 - 32 * h, 0), hi = min(x1 - 32 * h, 31);
+                    if (lo <= hi) {
+                        const uint32_t bits = (hi - lo == 31 ? 0xffffffffu : ((1u << (hi - lo + 1)) - 1u)) << lo;
+                        atomicOr(&gmask[cy * 2 + h], bits);
+                    }
+                }
+            }
+            __syncthreads();
+        }
         for (int j = scan_pos + tid; j < n; j += kThreads) {
             if (supp[j]) continue;
             const float4 bj = bx[j];
+            if (cull) {
+                const int cx = min(max((int)floorf((bj.x + 0.5f * bj.z) * gsx), 0), kGrid - 1);
+                const int cy = min(max((int)floorf((bj.y + 0.5f * bj.w) * gsy), 0), kGrid - 1);
+                if (!((gmask[cy * 2 + (cx >> 5)] >> (cx & 31)) & 1u)) continue;  // no kept box holds its centre
+            }
             bool hit = false;
             for (int k = 0; k < nk && !hit; k += 4) {
                 // four tests in flight (kept boxes past nk repeat the first one)
