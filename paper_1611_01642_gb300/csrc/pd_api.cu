@@ -62,6 +62,7 @@ struct Plan {
     std::vector<LevelDesc> levels;
     std::vector<ResizeItem> r_items;
     std::vector<CellItem> c_items;
+    std::vector<StripItem> strips;
     std::vector<SvmItem> s_items;
     std::vector<TcItem> t_items;
     std::vector<CnnItem> cnn_items;
@@ -80,6 +81,7 @@ struct Plan {
         levels.clear();
         r_items.clear();
         c_items.clear();
+        strips.clear();
         s_items.clear();
         t_items.clear();
         cnn_items.clear();
@@ -91,7 +93,7 @@ struct Plan {
 
 // Byte offsets of the plan's sections inside the packed descriptor block.
 struct Packed {
-    int64_t frames, levels, r_items, c_items, s_items, t_items, cnn_items, tabs, tmaps, total;
+    int64_t frames, levels, r_items, c_items, strips, s_items, t_items, cnn_items, tabs, tmaps, total;
 };
 
 Packed pack_layout(const Plan &p) {
@@ -106,6 +108,7 @@ Packed pack_layout(const Plan &p) {
     o.levels = take((int64_t)p.levels.size() * sizeof(LevelDesc));
     o.r_items = take((int64_t)p.r_items.size() * sizeof(ResizeItem));
     o.c_items = take((int64_t)p.c_items.size() * sizeof(CellItem));
+    o.strips = take((int64_t)p.strips.size() * sizeof(StripItem));
     o.s_items = take((int64_t)p.s_items.size() * sizeof(SvmItem));
     o.t_items = take((int64_t)p.t_items.size() * sizeof(TcItem));
     o.cnn_items = take((int64_t)p.cnn_items.size() * sizeof(CnnItem));
@@ -400,6 +403,12 @@ void plan_tc(std::vector<TcItem> &out, int li, int rows, int cols, int chunk) {
             out.push_back({li, x, (int)((int64_t)rows * k / pieces), (int)((int64_t)rows * (k + 1) / pieces)});
 }
 
+// K2+K3 strips: tallest first, so that the grid ends with the short ones.
+void order_strips(std::vector<StripItem> &t) {
+    std::stable_sort(t.begin(), t.end(),
+                     [](const StripItem &a, const StripItem &b) { return a.cy1 - a.cy0 > b.cy1 - b.cy0; });
+}
+
 // Largest items first (block rows walked: window rows + 14), so that the
 // persistent CTAs' queue ends with the small ones.
 void order_tc(std::vector<TcItem> &t) {
@@ -521,6 +530,9 @@ void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int
     L.ctx = (L.Wc + kCellTW - 1) / kCellTW;
     for (int cy = 0; cy < L.Hc; cy += kCellTH)
         for (int cx = 0; cx < L.Wc; cx += kCellTW) p.c_items.push_back({li, cx, cy, 0});
+    for (int cx = 0; cx < L.Wc; cx += kCellTW)
+        for (int cy = 0; cy < L.Hc; cy += kCellTH * kStripTiles)
+            p.strips.push_back({li, cx, cy, std::min(cy + kCellTH * kStripTiles, L.Hc)});
     plan_windows(p.s_items, li, L.rows, L.cols, tile_cost);
     plan_tc(p.t_items, li, L.rows, L.cols, p.tc_rows);
     p.atlas_rows += L.Hc;
@@ -603,6 +615,7 @@ int upload_plan(pd_handle *h, cudaStream_t s, const Plan &p, Packed &o, const ui
     put(o.levels, p.levels.data(), p.levels.size() * sizeof(LevelDesc));
     put(o.r_items, p.r_items.data(), p.r_items.size() * sizeof(ResizeItem));
     put(o.c_items, p.c_items.data(), p.c_items.size() * sizeof(CellItem));
+    put(o.strips, p.strips.data(), p.strips.size() * sizeof(StripItem));
     put(o.s_items, p.s_items.data(), p.s_items.size() * sizeof(SvmItem));
     put(o.t_items, p.t_items.data(), p.t_items.size() * sizeof(TcItem));
     put(o.cnn_items, p.cnn_items.data(), p.cnn_items.size() * sizeof(CnnItem));
@@ -693,6 +706,18 @@ int max_pool_tiles(const Plan &p) {
 template <class T>
 const T *dptr(pd_handle *h, int64_t off) {
     return reinterpret_cast<const T *>(h->d_desc + off);
+}
+
+// K2+K3 of a plan: the warp-per-strip kernel, or for per-block HOG the
+// CTA-per-tile kernel.
+cudaError_t launch_cell_stage(pd_handle *h, cudaStream_t s, const LevelDesc *dl, const uint8_t *pyr,
+                              const CellAtlas &atlas, const Plan &p, const Packed &o, const uint32_t *c_flag,
+                              int feat) {
+    if (feat & kFeatHogBlock)
+        return launch_cells(s, dl, pyr, atlas, dptr<CellItem>(h, o.c_items), (int)p.c_items.size(), h->d_lbp_map,
+                            c_flag, feat);
+    return launch_cells_warp(s, dl, pyr, atlas, dptr<StripItem>(h, o.strips), (int)p.strips.size(), h->d_lbp_map,
+                             c_flag, feat);
 }
 
 }  // namespace
@@ -800,8 +825,8 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
         return code;
     };
     if (cudaGetDevice(&h->device) != cudaSuccess) return bail(PD_ECUDA);
-    if (init_resize() != cudaSuccess || init_cells() != cudaSuccess || init_svm() != cudaSuccess ||
-        init_svm_tc() != cudaSuccess ||
+    if (init_resize() != cudaSuccess || init_cells() != cudaSuccess || init_cells_warp() != cudaSuccess ||
+        init_svm() != cudaSuccess || init_svm_tc() != cudaSuccess ||
         init_nms() != cudaSuccess ||
         init_cnn() != cudaSuccess)
         return bail(PD_ECUDA);
@@ -847,6 +872,7 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
                       round_up(F * (int64_t)one.levels.size() * (int64_t)sizeof(LevelDesc), 16) +
                       round_up(F * (int64_t)one.r_items.size() * (int64_t)sizeof(ResizeItem), 16) +
                       round_up(F * (int64_t)one.c_items.size() * (int64_t)sizeof(CellItem), 16) +
+                      round_up(F * (int64_t)one.strips.size() * (int64_t)sizeof(StripItem), 16) +
                       round_up(F * s_bound * (int64_t)sizeof(SvmItem), 16) +
                       round_up(F * (int64_t)one.t_items.size() * (int64_t)sizeof(TcItem), 16) +
                       round_up(F * (int64_t)one.tabs.size() * 4, 16) + 4096;
@@ -1007,6 +1033,7 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
             if (r != PD_OK) return fail(h, r, "frame %d: planning failed", f);
         }
         order_tc(p.t_items);
+        order_strips(p.strips);
         if (p.atlas_rows > h->atlas.rows || p.pyr_bytes > h->pyr_cap || p.score_floats > h->score_cap ||
             (int64_t)p.s_items.size() > h->flag_cap || (int64_t)p.c_items.size() > h->flag_cap)
             return fail(h, PD_EINVAL, "batch exceeds the arena");
@@ -1054,8 +1081,7 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
             sf = h->s_flag;
         }
         if (timed) PD_CUDA(h, record(h->stage_ev[1], q));
-        PD_CUDA(h, launch_cells(q, dl, h->d_pyr, h->atlas, dptr<CellItem>(h, o.c_items), (int)p.c_items.size(),
-                                h->d_lbp_map, cf, features_of(h->p.flags)));
+        PD_CUDA(h, launch_cell_stage(h, q, dl, h->d_pyr, h->atlas, p, o, cf, features_of(h->p.flags)));
         if (timed) PD_CUDA(h, record(h->stage_ev[2], q));
         if (h->p.flags & PD_FLAG_SVM_FP32) {
             PD_CUDA(h, launch_svm(q, h->hog_map, h->lbp_map, dl, h->d_w, h->bias, h->p.l2hys_clip, h->d_scores,
@@ -1232,6 +1258,7 @@ int pd_cnn_forward(pd_handle *h, void *stream, const uint8_t *d_level, int Wk, i
     Plan p;
     plan_level(p, 0, 0, Wk, Hk, Wk, Hk, 0, pitch);
     p.c_items.clear();
+    p.strips.clear();
     p.s_items.clear();
     p.t_items.clear();
     p.tabs.clear();
@@ -1463,6 +1490,7 @@ int pd_resize_levels(pd_handle *h, void *stream, const uint8_t *d_frame, int W, 
         for (int x = 0; x < W; x += kResizeTW) p.r_items.push_back({0, x, y, 0});
     p.frames.push_back(fd);
     p.c_items.clear();
+    p.strips.clear();
     p.s_items.clear();
     p.t_items.clear();
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -1499,9 +1527,8 @@ int pd_cell_features(pd_handle *h, void *stream, const uint8_t *d_level, int Wk,
     a.lbp_plane = lbp_plane;
     a.pitch = cell_pitch;
     a.rows = Hc;
-    PD_CUDA(h, launch_cells(s, dptr<LevelDesc>(h, o.levels), d_level, a, dptr<CellItem>(h, o.c_items),
-                            (int)p.c_items.size(), h->d_lbp_map, nullptr,
-                            kFeatHog | kFeatLbp | (features_of(h->p.flags) & kFeatHogBlock)));
+    PD_CUDA(h, launch_cell_stage(h, s, dptr<LevelDesc>(h, o.levels), d_level, a, p, o, nullptr,
+                                 kFeatHog | kFeatLbp | (features_of(h->p.flags) & kFeatHogBlock)));
     return PD_OK;
 }
 
@@ -1520,6 +1547,7 @@ int pd_window_scores(pd_handle *h, void *stream, const float *d_hog, int64_t hog
     plan_level(p, 0, 0, 8 * cells_x, 8 * cells_y, 8 * cells_x, 8 * cells_y, 0, 8 * cells_x, nullptr,
                h->tile_cost);
     p.c_items.clear();
+    p.strips.clear();
     p.tabs.clear();
     if (p.s_items.empty()) return PD_OK;
     const bool fp32 = (h->p.flags & PD_FLAG_SVM_FP32) != 0;

@@ -62,6 +62,7 @@ struct ResizeItem { int32_t frame, x0, y0, pad; };   // source tile of a frame
 struct CellItem { int32_t level, cx0, cy0, pad; };   // cell tile of a level
 struct SvmItem { int32_t level, wx0, wy0, shape; };  // window tile of a level, tile shape index
 struct TcItem { int32_t level, wx0, wy0, wy1; };     // tensor-core K4: window columns [wx0, wx0 + 104), rows [wy0, wy1)
+struct StripItem { int32_t level, cx0, cy0, cy1; };  // K2+K3 warp: cells [cx0, cx0 + 15) x rows [cy0, cy1)
 
 // Tiles.
 constexpr int kResizeTW = 128;  // source tile width  (pixels)
@@ -74,6 +75,7 @@ __host__ __device__ inline int resize_quad_index(int d) { return d + (d >> 5); }
 constexpr int kResizeQP = 193;
 constexpr int kCellTW = 15;     // cells per cell tile along x (128 threads = 8*15+8 columns)
 constexpr int kCellTH = 8;      // cells per cell tile along y
+constexpr int kStripTiles = 4;  // cell tiles per K2+K3 strip (one warp each), top to bottom
 constexpr int kSvmShapes = 7;   // K4 tile shapes: 32x16, 64x8, 32x8, 64x4, 64x2, 32x12, 32x4 windows
 constexpr int kTcStrip = 104;   // tensor-core K4: window columns per item
 constexpr int kTcChunk = 64;    // tensor-core K4: window rows per item at most (tunable down to kTcMinChunk)
@@ -116,6 +118,11 @@ constexpr int kFeatHog = 1, kFeatLbp = 2, kFeatHogBlock = 4;
 cudaError_t launch_cells(cudaStream_t s, const LevelDesc *d_levels, const uint8_t *pyr,
                          CellAtlas atlas, const CellItem *d_items, int n_items, const uint8_t *d_lbp_map,
                          const uint32_t *c_flag = nullptr, int feat = kFeatHog | kFeatLbp);
+// Default K2+K3 (HOG and / or LBP without per-block HOG): one warp per strip.
+cudaError_t init_cells_warp();
+cudaError_t launch_cells_warp(cudaStream_t s, const LevelDesc *d_levels, const uint8_t *pyr, CellAtlas atlas,
+                              const StripItem *d_items, int n_items, const uint8_t *d_lbp_map,
+                              const uint32_t *c_flag, int feat);
 cudaError_t launch_proposal_flags(cudaStream_t s, const LevelDesc *d_levels, const SvmItem *d_items, int n_items,
                                   const float *logits, float tau, uint32_t *s_flag, uint32_t *c_flag,
                                   bool per_window);
