@@ -80,7 +80,7 @@ struct WarpSmem {
     uint32_t cnt[2 * kCntRing];     // LBP counters of the 2 open cell rows
 };
 struct StripSmem {
-    uint2 map[256];                 // LBP code -> (counter word byte offset, increment)
+    uint2 map[256];                 // LBP code -> (counter word index, increment)
     WarpSmem w[kWarps];
 };
 
@@ -102,9 +102,16 @@ __device__ __forceinline__ int dp2a_diff_hi(uint32_t b, int c) {
     return d;
 }
 
+// Operands here are 0 or >= 1e-30 (never subnormal), so the flush-to-zero
+// forms are exact.
 __device__ __forceinline__ float sqrt_approx(float x) {
     float y;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 
@@ -143,7 +150,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
     if (kLbp) {
         for (int i = threadIdx.x; i < 256; i += kWarps * 32) {
             const int bn = lbp_map[i];
-            S.map[i] = make_uint2((uint32_t)(bn >> 2) * 4u, 1u << ((bn & 3) * 8));
+            S.map[i] = make_uint2((uint32_t)(bn >> 2), 1u << ((bn & 3) * 8));
         }
         __syncthreads();
     }
@@ -170,10 +177,10 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
 
     // ---- lane constants
     const int sw = (lane >> 3) & 3;
-    // byte offset of slot 0 of pixel j's column, less the bias of the rounded angle's bits
+    // float index of slot 0 of pixel j's column, less the bias of the rounded angle's bits
     uint32_t vb[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) vb[j] = 4u * (uint32_t)(4 * lane + (j ^ sw)) + 512u - kMagicBits * 512u;
+    for (int j = 0; j < 4; ++j) vb[j] = (uint32_t)(4 * lane + (j ^ sw)) + 128u - kMagicBits * 128u;
     // epilogue x-weights by slot position p (column j = p ^ sw): own cell, neighbour cell
     float wo[4], wn[4];
     {
@@ -196,8 +203,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
         }
     }
     const bool core = (unsigned)(lane - 1) < 30u;  // lanes 1..30 own strip pixels (LBP)
-    char *cnt_lane = reinterpret_cast<char *>(Wm.cnt + (core ? ((lane - 1) >> 1) : 0) * kCntWords);
-    char *Rc = reinterpret_cast<char *>(Wm.R);
+    const int cnt_lane = (core ? ((lane - 1) >> 1) : 0) * kCntWords;  // word index of the lane's cell
     __syncwarp();
 
     // ---- rows
@@ -230,10 +236,10 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
     };
 
     // ---- one pixel row (rows a / b / c = y - 1, y, y + 1): HOG votes with
-    // weights wa, wb into the vote slots at byte offsets va[j] (cell row
-    // band - 1) and va[j] + dB (cell row band); LBP counts at cnt_row
+    // weights wa, wb into the vote slots at float indices va[j] (cell row
+    // band - 1) and va[j] + dB (cell row band); LBP counts at word cnt_row
     auto pixel_row = [&](const Row &ra, const Row &rb, const Row &rc, float wa, float wb, const uint32_t (&va)[4],
-                         int dB, const char *cnt_row) {
+                         int dB, int cnt_row) {
         if (kHog) {
             const uint32_t P01 = __byte_perm(rb.r, rb.l, 0x5140), P23 = __byte_perm(rb.r, rb.l, 0x7362);
             const uint32_t Q01 = __byte_perm(rc.c, ra.c, 0x5140), Q23 = __byte_perm(rc.c, ra.c, 0x7362);
@@ -247,7 +253,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
                 const float mag = sqrt_approx(fmaf(fx, fx, fy * fy));
                 const float ax = fabsf(fx), ay = fabsf(fy);
                 // mx is 0 or >= 1: the 1e-30 only turns 0 / 0 into 0
-                const float z = __fdividef(fminf(ax, ay), fmaxf(ax, ay) + 1e-30f);
+                const float z = fminf(ax, ay) * rcp_approx(fmaxf(ax, ay) + 1e-30f);
                 const float pz = atan_bins_poly(z * z);
                 // theta = phi, 4.5 - phi (steep), 9 - phi (opposite signs), 4.5 + phi (both);
                 // the vote position is theta - 0.5, rounded below through theta - 1
@@ -258,9 +264,9 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
                 const float tm1 = fmaf(pz, zs, off);
                 const float t = tm1 + kMagic;
                 const float o1 = (tm1 + 0.5f) - (t - kMagic);
-                const uint32_t oa = (uint32_t)__float_as_int(t) * 512u + va[j];
-                float *v = reinterpret_cast<float *>(Rc + (size_t)oa);
-                float *u = reinterpret_cast<float *>(Rc + (size_t)(oa + (uint32_t)dB));
+                const int oa = (int)((uint32_t)__float_as_int(t) * 128u + va[j]);
+                float *v = Wm.R + oa;
+                float *u = Wm.R + (oa + dB);
                 const float mo1 = mag * o1, mo0 = mag - mo1;
                 v[0] = fmaf(mo0, wa, v[0]);
                 v[kSCols] = fmaf(mo1, wa, v[kSCols]);
@@ -278,7 +284,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const uint2 e = S.map[(code >> (8 * j)) & 0xffu];
-                    atomicAdd(reinterpret_cast<uint32_t *>(const_cast<char *>(cnt_row) + e.x), e.y);
+                    atomicAdd(&Wm.cnt[cnt_row + (int)e.x], e.y);
                 }
             }
         }
@@ -405,12 +411,12 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
         }
         const bool pf = band + 1 <= nb && (need(band) || need(band + 1));
         const int ringA = (band + 1) & 1;
-        const int dB = (ringA ? -1 : 1) * kRingStride * 4;  // bytes from row band - 1's slots to row band's
+        const int dB = (ringA ? -1 : 1) * kRingStride;  // floats from row band - 1's slots to row band's
         uint32_t va[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) va[j] = vb[j] + (uint32_t)(ringA * kRingStride * 4);
-        const char *cnt_a = cnt_lane + ringA * kCntRing * 4;
-        const char *cnt_b = cnt_lane + (ringA ^ 1) * kCntRing * 4;
+        for (int j = 0; j < 4; ++j) va[j] = vb[j] + (uint32_t)(ringA * kRingStride);
+        const int cnt_a = cnt_lane + ringA * kCntRing;
+        const int cnt_b = cnt_lane + (ringA ^ 1) * kCntRing;
 #pragma unroll 1
         for (int i = 0; i < 4; ++i) {
             const Row c0 = mkrow(p0), c1 = mkrow(p1);
@@ -421,7 +427,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
             // band rows k = 2i, 2i + 1: weights (7.5 - k) / 8 and (k + 0.5) / 8;
             // LBP cell row band - 1 for k < 4, band for k >= 4
             const float wa0 = (7.5f - 2 * i) * 0.125f;
-            const char *cr = i < 2 ? cnt_a : cnt_b;
+            const int cr = i < 2 ? cnt_a : cnt_b;
             const int y = yb + 2 * i;
             if (y >= 0 && y < gridH) pixel_row(ra, rb, c0, wa0, 1.f - wa0, va, dB, cr);
             if (y + 1 >= 0 && y + 1 < gridH) pixel_row(rb, c0, c1, wa0 - 0.125f, 1.125f - wa0, va, dB, cr);
