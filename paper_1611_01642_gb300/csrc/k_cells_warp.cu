@@ -69,15 +69,13 @@ static_assert(kSCols == 4 * 32, "four pixel columns per lane");
 constexpr int kSlots = kHogBins + 2;             // vote slots per column (bins -1 .. 9)
 constexpr int kRingStride = kSlots * kSCols;     // floats per open cell row
 constexpr int kCntWords = (kLbpBins + 3) / 4;    // words of four 8-bit counters per cell
-constexpr int kCntCells = 16;                    // strip cells 0..14 (+ 1 unused)
-constexpr int kCntRing = kCntCells * kCntWords;  // words per open cell row
 constexpr uint32_t kHi = 0x80808080u;
 constexpr float kMagic = 12582912.0f;            // 1.5 * 2^23
 constexpr uint32_t kMagicBits = 0x4B400000u;
 
 struct WarpSmem {
     float R[2 * kRingStride];       // HOG vote slots of the 2 open cell rows
-    uint32_t cnt[2 * kCntRing];     // LBP counters of the 2 open cell rows
+    uint32_t cnt[kCntWords * 32];   // LBP counters of the open cell row: [word][lane], lane-private
 };
 struct StripSmem {
     uint2 map[256];                 // LBP code -> (counter word index, increment)
@@ -150,7 +148,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
     if (kLbp) {
         for (int i = threadIdx.x; i < 256; i += kWarps * 32) {
             const int bn = lbp_map[i];
-            S.map[i] = make_uint2((uint32_t)(bn >> 2), 1u << ((bn & 3) * 8));
+            S.map[i] = make_uint2((uint32_t)(bn >> 2) * 32u, 1u << ((bn & 3) * 8));
         }
         __syncthreads();
     }
@@ -173,7 +171,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
         for (int i = lane; i < 2 * kRingStride / 4; i += 32)
             reinterpret_cast<float4 *>(Wm.R)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (kLbp)
-        for (int i = lane; i < 2 * kCntRing; i += 32) Wm.cnt[i] = 0u;
+        for (int i = lane; i < kCntWords * 32; i += 32) Wm.cnt[i] = 0u;
 
     // ---- lane constants
     const int sw = (lane >> 3) & 3;
@@ -203,7 +201,6 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
         }
     }
     const bool core = (unsigned)(lane - 1) < 30u;  // lanes 1..30 own strip pixels (LBP)
-    const int cnt_lane = (core ? ((lane - 1) >> 1) : 0) * kCntWords;  // word index of the lane's cell
     __syncwarp();
 
     // ---- rows
@@ -237,9 +234,9 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
 
     // ---- one pixel row (rows a / b / c = y - 1, y, y + 1): HOG votes with
     // weights wa, wb into the vote slots at float indices va[j] (cell row
-    // band - 1) and va[j] + dB (cell row band); LBP counts at word cnt_row
+    // band - 1) and va[j] + dB (cell row band); LBP counts into the lane's counters
     auto pixel_row = [&](const Row &ra, const Row &rb, const Row &rc, float wa, float wb, const uint32_t (&va)[4],
-                         int dB, int cnt_row) {
+                         int dB) {
         if (kHog) {
             const uint32_t P01 = __byte_perm(rb.r, rb.l, 0x5140), P23 = __byte_perm(rb.r, rb.l, 0x7362);
             const uint32_t Q01 = __byte_perm(rc.c, ra.c, 0x5140), Q23 = __byte_perm(rc.c, ra.c, 0x7362);
@@ -284,13 +281,40 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const uint2 e = S.map[(code >> (8 * j)) & 0xffu];
-                    atomicAdd(&Wm.cnt[cnt_row + (int)e.x], e.y);
+                    atomicAdd(&Wm.cnt[(int)e.x + lane], e.y);
                 }
             }
         }
     };
 
-    // ---- cell row r = band - 1 is final: write it, recycle its slots
+    // ---- LBP of cell row r = band - 1 is final after the band's first 4 rows:
+    // a cell's counts are its two lanes' counters; write them, clear
+    auto emit_lbp = [&](int band, bool walked) {
+        __syncwarp();  // every lane's counts of row r are in
+        const int r = band - 1;
+        const int c = lane & 15, half = lane >> 4;
+        if (walked && need(r) && c < kCellTW && cx0 + c < Wc) {
+            const int64_t pl = atlas.lbp_plane;
+            // bin planes 32 half .. 32 half + 31 of cell c
+            uint8_t *dst = atlas.lbp + (int64_t)(L.cell_row + cy0 + r) * atlas.pitch + cx0 + c + 32 * half * pl;
+            const uint32_t *cw = Wm.cnt + half * 8 * 32 + 2 * c + 1;
+            const int nw = half ? kCntWords - 8 : 8;
+#pragma unroll 1
+            for (int i = 0; i < nw; ++i) {
+                const uint32_t val = cw[i * 32] + cw[i * 32 + 1];  // counts <= 32 each: no carry
+                dst[0] = (uint8_t)val;
+                dst[pl] = (uint8_t)(val >> 8);
+                dst[2 * pl] = (uint8_t)(val >> 16);
+                if (32 * half + 4 * i + 3 < kLbpBins) dst[3 * pl] = (uint8_t)(val >> 24);
+                dst += 4 * pl;
+            }
+        }
+        __syncwarp();  // read before cleared
+#pragma unroll
+        for (int wd = 0; wd < kCntWords; ++wd) Wm.cnt[wd * 32 + lane] = 0u;
+    };
+
+    // ---- HOG of cell row r = band - 1 is final: write it, recycle its slots
     auto emit = [&](int band, bool walked) {
         const int ringA = (band + 1) & 1, ringB = band & 1;
         const int r = band - 1;
@@ -359,30 +383,6 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
             for (int s = 0; s < kSlots; ++s)
                 *reinterpret_cast<float4 *>(Ra + s * kSCols) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (kLbp) {
-            __syncwarp();  // every lane's counts of row r are in
-            const int c = lane & 15, half = lane >> 4;
-            uint32_t *cw = Wm.cnt + ringA * kCntRing + c * kCntWords + half * 8;
-            if (out && c < kCellTW && cx0 + c < Wc) {
-                uint8_t *dst = atlas.lbp + rowoff + cx0 + c;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int wd = half * 8 + i;
-                    if (wd < kCntWords) {
-                        const uint32_t val = cw[i];
-#pragma unroll
-                        for (int qb = 0; qb < 4; ++qb)
-                            if (4 * wd + qb < kLbpBins)
-                                dst[(int64_t)(4 * wd + qb) * atlas.lbp_plane] = (uint8_t)(val >> (8 * qb));
-                    }
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-                if (half * 8 + i < kCntWords) cw[i] = 0u;
-            // the next band's counts go to the other row's words until this
-            // one is reused two bands later, after another __syncwarp
-        }
     };
 
     // ---- the walk: bands 0..nb. Rows arrive in pairs, the next pair loaded
@@ -395,7 +395,10 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
     for (int band = 0; band <= nb; ++band) {
         const int yb = 8 * (cy0 + band) - 4;
         if (!(need(band - 1) || need(band))) {
-            if (walked_prev) emit(band, false);  // recycle row band - 1's slots
+            if (walked_prev) {  // recycle row band - 1's slots and counters
+                emit(band, false);
+                if (kLbp) emit_lbp(band, false);
+            }
             have = false;
             walked_prev = false;
             continue;
@@ -415,8 +418,6 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
         uint32_t va[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) va[j] = vb[j] + (uint32_t)(ringA * kRingStride);
-        const int cnt_a = cnt_lane + ringA * kCntRing;
-        const int cnt_b = cnt_lane + (ringA ^ 1) * kCntRing;
 #pragma unroll 1
         for (int i = 0; i < 4; ++i) {
             const Row c0 = mkrow(p0), c1 = mkrow(p1);
@@ -427,12 +428,12 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
             // band rows k = 2i, 2i + 1: weights (7.5 - k) / 8 and (k + 0.5) / 8;
             // LBP cell row band - 1 for k < 4, band for k >= 4
             const float wa0 = (7.5f - 2 * i) * 0.125f;
-            const int cr = i < 2 ? cnt_a : cnt_b;
             const int y = yb + 2 * i;
-            if (y >= 0 && y < gridH) pixel_row(ra, rb, c0, wa0, 1.f - wa0, va, dB, cr);
-            if (y + 1 >= 0 && y + 1 < gridH) pixel_row(rb, c0, c1, wa0 - 0.125f, 1.125f - wa0, va, dB, cr);
+            if (y >= 0 && y < gridH) pixel_row(ra, rb, c0, wa0, 1.f - wa0, va, dB);
+            if (y + 1 >= 0 && y + 1 < gridH) pixel_row(rb, c0, c1, wa0 - 0.125f, 1.125f - wa0, va, dB);
             ra = c0;
             rb = c1;
+            if (kLbp && i == 1) emit_lbp(band, true);
         }
         emit(band, true);
         have = pf;
