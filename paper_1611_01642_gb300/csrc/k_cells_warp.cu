@@ -235,8 +235,9 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
     // ---- one pixel row (rows a / b / c = y - 1, y, y + 1): HOG votes with
     // weights wa, wb into the vote slots at float indices va[j] (cell row
     // band - 1) and va[j] + dB (cell row band); LBP counts into the lane's counters
+    // (a row outside the cell grid votes with weight 0 and counts nothing)
     auto pixel_row = [&](const Row &ra, const Row &rb, const Row &rc, float wa, float wb, const uint32_t (&va)[4],
-                         int dB) {
+                         int dB, bool valid) {
         if (kHog) {
             const uint32_t P01 = __byte_perm(rb.r, rb.l, 0x5140), P23 = __byte_perm(rb.r, rb.l, 0x7362);
             const uint32_t Q01 = __byte_perm(rc.c, ra.c, 0x5140), Q23 = __byte_perm(rc.c, ra.c, 0x7362);
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
                                   (ge4(ra.r, clo, cn7) >> 5) | (ge4(rb.r, clo, cn7) >> 4) |
                                   (ge4(rc.r, clo, cn7) >> 3) | (ge4(rc.c, clo, cn7) >> 2) |
                                   (ge4(rc.l, clo, cn7) >> 1) | ge4(rb.l, clo, cn7);
-            if (core) {
+            if (core && valid) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const uint2 e = S.map[(code >> (8 * j)) & 0xffu];
@@ -429,8 +430,9 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
             // LBP cell row band - 1 for k < 4, band for k >= 4
             const float wa0 = (7.5f - 2 * i) * 0.125f;
             const int y = yb + 2 * i;
-            if (y >= 0 && y < gridH) pixel_row(ra, rb, c0, wa0, 1.f - wa0, va, dB);
-            if (y + 1 >= 0 && y + 1 < gridH) pixel_row(rb, c0, c1, wa0 - 0.125f, 1.125f - wa0, va, dB);
+            const bool v0 = y >= 0 && y < gridH, v1 = y + 1 >= 0 && y + 1 < gridH;
+            pixel_row(ra, rb, c0, v0 ? wa0 : 0.f, v0 ? 1.f - wa0 : 0.f, va, dB, v0);
+            pixel_row(rb, c0, c1, v1 ? wa0 - 0.125f : 0.f, v1 ? 1.125f - wa0 : 0.f, va, dB, v1);
             ra = c0;
             rb = c1;
             if (kLbp && i == 1) emit_lbp(band, true);
