@@ -55,6 +55,7 @@
 // Sparse path: c_flag marks the 15 x 8-cell tiles to compute; a band is
 // walked when one of its two cell rows lies in a marked tile, and a cell
 // row is written when its tile is marked.
+#include <algorithm>
 #include <type_traits>
 #include <utility>
 
@@ -140,8 +141,8 @@ __device__ __forceinline__ uint32_t ge4(uint32_t n, uint32_t c_lo, uint32_t c_no
 template <int FEAT>
 __global__ void __launch_bounds__(kWarps * 32, 4)
     k_cells_warp(const LevelDesc *__restrict__ levels, const uint8_t *__restrict__ pyr, CellAtlas atlas,
-                 const StripItem *__restrict__ items, int n_items, const uint8_t *__restrict__ lbp_map,
-                 const uint32_t *__restrict__ c_flag) {
+                 const StripItem *__restrict__ items, int n_items, int *__restrict__ queue,
+                 const uint8_t *__restrict__ lbp_map, const uint32_t *__restrict__ c_flag) {
     constexpr bool kHog = (FEAT & kFeatHog) != 0, kLbp = (FEAT & kFeatLbp) != 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StripSmem &S = *reinterpret_cast<StripSmem *>(smem_raw);
@@ -153,298 +154,303 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
         __syncthreads();
     }
     const int lane = threadIdx.x & 31;
-    const int item = blockIdx.x * kWarps + (threadIdx.x >> 5);
-    if (item >= n_items) return;
     WarpSmem &Wm = S.w[threadIdx.x >> 5];
-    const StripItem it = items[item];
-    const LevelDesc L = levels[it.level];
-    const uint8_t *img = pyr + L.img_off;
-    const int pitch = L.img_pitch, Wk = L.Wk, Hk = L.Hk, Wc = L.Wc, Hc = L.Hc;
-    const int gridH = 8 * Hc;
-    const int cx0 = it.cx0, cy0 = it.cy0, nb = it.cy1 - it.cy0;
-    const int tx = cx0 / kCellTW;
-    const int x = 8 * cx0 - 4 + 4 * lane;  // first pixel column of this lane
-    const bool fast = (((reinterpret_cast<uintptr_t>(img) | (uintptr_t)pitch) & 3u) == 0) && x >= 4 &&
-                      x + 8 <= Wk;
+    // persistent warps: each takes the next strip (tallest first) until none is left
+    for (;;) {
+        int item = lane == 0 ? atomicAdd(queue, 1) : 0;
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) return;
+        const StripItem it = items[item];
+        const LevelDesc L = levels[it.level];
+        const uint8_t *img = pyr + L.img_off;
+        const int pitch = L.img_pitch, Wk = L.Wk, Hk = L.Hk, Wc = L.Wc, Hc = L.Hc;
+        const int gridH = 8 * Hc;
+        const int cx0 = it.cx0, cy0 = it.cy0, nb = it.cy1 - it.cy0;
+        const int tx = cx0 / kCellTW;
+        const int x = 8 * cx0 - 4 + 4 * lane;  // first pixel column of this lane
+        const bool fast = (((reinterpret_cast<uintptr_t>(img) | (uintptr_t)pitch) & 3u) == 0) && x >= 4 &&
+                          x + 8 <= Wk;
 
-    if (kHog)
-        for (int i = lane; i < 2 * kRingStride / 4; i += 32)
-            reinterpret_cast<float4 *>(Wm.R)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (kLbp)
-        for (int i = lane; i < kCntWords * 32; i += 32) Wm.cnt[i] = 0u;
+        if (kHog)
+            for (int i = lane; i < 2 * kRingStride / 4; i += 32)
+                reinterpret_cast<float4 *>(Wm.R)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (kLbp)
+            for (int i = lane; i < kCntWords * 32; i += 32) Wm.cnt[i] = 0u;
 
-    // ---- lane constants
-    const int sw = (lane >> 3) & 3;
-    // float index of slot 0 of pixel j's column, less the bias of the rounded angle's bits
-    uint32_t vb[4];
+        // ---- lane constants
+        const int sw = (lane >> 3) & 3;
+        // float index of slot 0 of pixel j's column, less the bias of the rounded angle's bits
+        uint32_t vb[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) vb[j] = (uint32_t)(4 * lane + (j ^ sw)) + 128u - kMagicBits * 128u;
-    // epilogue x-weights by slot position p (column j = p ^ sw): own cell, neighbour cell
-    float wo[4], wn[4];
-    {
-        const int own = cx0 + ((lane - 1) >> 1);
-        const int nbr = own + ((lane & 1) ? -1 : 1);
+        for (int j = 0; j < 4; ++j) vb[j] = (uint32_t)(4 * lane + (j ^ sw)) + 128u - kMagicBits * 128u;
+        // epilogue x-weights by slot position p (column j = p ^ sw): own cell, neighbour cell
+        float wo[4], wn[4];
+        {
+            const int own = cx0 + ((lane - 1) >> 1);
+            const int nbr = own + ((lane & 1) ? -1 : 1);
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int xc = x + (p ^ sw);
-            float a = 0.f, b = 0.f;
-            if (xc >= 0 && xc < 8 * Wc) {
-                const float ux = ((float)xc - 3.5f) * 0.125f;
-                const float fx = floorf(ux);
-                const float w1 = ux - fx, w0 = 1.f - w1;
-                const int c0 = clampi((int)fx, 0, Wc - 1), c1 = clampi((int)fx + 1, 0, Wc - 1);
-                a = (c0 == own ? w0 : 0.f) + (c1 == own ? w1 : 0.f);
-                b = (c0 == nbr ? w0 : 0.f) + (c1 == nbr ? w1 : 0.f);
-            }
-            wo[p] = a;
-            wn[p] = b;
-        }
-    }
-    const bool core = (unsigned)(lane - 1) < 30u;  // lanes 1..30 own strip pixels (LBP)
-    __syncwarp();
-
-    // ---- rows
-    auto fetch = [&](int y, uint32_t (&w)[3]) {
-        const uint8_t *row = img + (size_t)clampi(y, 0, Hk - 1) * pitch;
-        if (fast) {
-            const uint32_t *p = reinterpret_cast<const uint32_t *>(row + x);
-            w[0] = __ldg(p - 1);
-            w[1] = __ldg(p);
-            w[2] = __ldg(p + 1);
-        } else {
-            uint32_t v[6];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) v[i] = __ldg(row + clampi(x - 1 + i, 0, Wk - 1));
-            w[0] = v[0] << 24;
-            w[1] = v[1] | (v[2] << 8) | (v[3] << 16) | (v[4] << 24);
-            w[2] = v[5];
-        }
-    };
-    auto mkrow = [](const uint32_t (&w)[3]) {
-        Row r;
-        r.l = __funnelshift_r(w[0], w[1], 24);
-        r.c = w[1];
-        r.r = __funnelshift_r(w[1], w[2], 8);
-        return r;
-    };
-    auto need = [&](int r) -> bool {  // strip cell row r is computed
-        if (r < 0 || r >= nb) return false;
-        return !c_flag || c_flag[L.citem0 + ((cy0 + r) / kCellTH) * L.ctx + tx] != 0u;
-    };
-
-    // ---- one pixel row (rows a / b / c = y - 1, y, y + 1): HOG votes with
-    // weights wa, wb into the vote slots at float indices va[j] (cell row
-    // band - 1) and va[j] + dB (cell row band); LBP counts into the lane's counters
-    // (a row outside the cell grid votes with weight 0 and counts nothing)
-    auto pixel_row = [&](const Row &ra, const Row &rb, const Row &rc, float wa, float wb, const uint32_t (&va)[4],
-                         int dB, bool valid) {
-        if (kHog) {
-            const uint32_t P01 = __byte_perm(rb.r, rb.l, 0x5140), P23 = __byte_perm(rb.r, rb.l, 0x7362);
-            const uint32_t Q01 = __byte_perm(rc.c, ra.c, 0x5140), Q23 = __byte_perm(rc.c, ra.c, 0x7362);
-            const int gxb[4] = {dp2a_diff_lo(P01, (int)kMagicBits), dp2a_diff_hi(P01, (int)kMagicBits),
-                                dp2a_diff_lo(P23, (int)kMagicBits), dp2a_diff_hi(P23, (int)kMagicBits)};
-            const int gyb[4] = {dp2a_diff_lo(Q01, (int)kMagicBits), dp2a_diff_hi(Q01, (int)kMagicBits),
-                                dp2a_diff_lo(Q23, (int)kMagicBits), dp2a_diff_hi(Q23, (int)kMagicBits)};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float fx = __int_as_float(gxb[j]) - kMagic, fy = __int_as_float(gyb[j]) - kMagic;
-                const float mag = sqrt_approx(fmaf(fx, fx, fy * fy));
-                const float ax = fabsf(fx), ay = fabsf(fy);
-                // mx is 0 or >= 1: the 1e-30 only turns 0 / 0 into 0
-                const float z = fminf(ax, ay) * rcp_approx(fmaxf(ax, ay) + 1e-30f);
-                const float pz = atan_bins_poly(z * z);
-                // theta = phi, 4.5 - phi (steep), 9 - phi (opposite signs), 4.5 + phi (both);
-                // the vote position is theta - 0.5, rounded below through theta - 1
-                const bool steep = ay > ax;
-                const bool mirror = (int)(__float_as_uint(fx) ^ __float_as_uint(fy)) < 0;
-                const float zs = (steep != mirror) ? -z : z;
-                const float off = steep ? 3.5f : (mirror ? 8.0f : -1.0f);
-                const float tm1 = fmaf(pz, zs, off);
-                const float t = tm1 + kMagic;
-                const float o1 = (tm1 + 0.5f) - (t - kMagic);
-                const int oa = (int)((uint32_t)__float_as_int(t) * 128u + va[j]);
-                float *v = Wm.R + oa;
-                float *u = Wm.R + (oa + dB);
-                const float mo1 = mag * o1, mo0 = mag - mo1;
-                v[0] = fmaf(mo0, wa, v[0]);
-                v[kSCols] = fmaf(mo1, wa, v[kSCols]);
-                u[0] = fmaf(mo0, wb, u[0]);
-                u[kSCols] = fmaf(mo1, wb, u[kSCols]);
+            for (int p = 0; p < 4; ++p) {
+                const int xc = x + (p ^ sw);
+                float a = 0.f, b = 0.f;
+                if (xc >= 0 && xc < 8 * Wc) {
+                    const float ux = ((float)xc - 3.5f) * 0.125f;
+                    const float fx = floorf(ux);
+                    const float w1 = ux - fx, w0 = 1.f - w1;
+                    const int c0 = clampi((int)fx, 0, Wc - 1), c1 = clampi((int)fx + 1, 0, Wc - 1);
+                    a = (c0 == own ? w0 : 0.f) + (c1 == own ? w1 : 0.f);
+                    b = (c0 == nbr ? w0 : 0.f) + (c1 == nbr ? w1 : 0.f);
+                }
+                wo[p] = a;
+                wn[p] = b;
             }
         }
-        if (kLbp) {
-            const uint32_t clo = rb.c & ~kHi, cn7 = ~rb.c & kHi;
-            const uint32_t code = (ge4(ra.l, clo, cn7) >> 7) | (ge4(ra.c, clo, cn7) >> 6) |
-                                  (ge4(ra.r, clo, cn7) >> 5) | (ge4(rb.r, clo, cn7) >> 4) |
-                                  (ge4(rc.r, clo, cn7) >> 3) | (ge4(rc.c, clo, cn7) >> 2) |
-                                  (ge4(rc.l, clo, cn7) >> 1) | ge4(rb.l, clo, cn7);
-            if (core && valid) {
+        const bool core = (unsigned)(lane - 1) < 30u;  // lanes 1..30 own strip pixels (LBP)
+        __syncwarp();
+
+        // ---- rows
+        auto fetch = [&](int y, uint32_t (&w)[3]) {
+            const uint8_t *row = img + (size_t)clampi(y, 0, Hk - 1) * pitch;
+            if (fast) {
+                const uint32_t *p = reinterpret_cast<const uint32_t *>(row + x);
+                w[0] = __ldg(p - 1);
+                w[1] = __ldg(p);
+                w[2] = __ldg(p + 1);
+            } else {
+                uint32_t v[6];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) v[i] = __ldg(row + clampi(x - 1 + i, 0, Wk - 1));
+                w[0] = v[0] << 24;
+                w[1] = v[1] | (v[2] << 8) | (v[3] << 16) | (v[4] << 24);
+                w[2] = v[5];
+            }
+        };
+        auto mkrow = [](const uint32_t (&w)[3]) {
+            Row r;
+            r.l = __funnelshift_r(w[0], w[1], 24);
+            r.c = w[1];
+            r.r = __funnelshift_r(w[1], w[2], 8);
+            return r;
+        };
+        auto need = [&](int r) -> bool {  // strip cell row r is computed
+            if (r < 0 || r >= nb) return false;
+            return !c_flag || c_flag[L.citem0 + ((cy0 + r) / kCellTH) * L.ctx + tx] != 0u;
+        };
+
+        // ---- one pixel row (rows a / b / c = y - 1, y, y + 1): HOG votes with
+        // weights wa, wb into the vote slots at float indices va[j] (cell row
+        // band - 1) and va[j] + dB (cell row band); LBP counts into the lane's counters
+        // (a row outside the cell grid votes with weight 0 and counts nothing)
+        auto pixel_row = [&](const Row &ra, const Row &rb, const Row &rc, float wa, float wb, const uint32_t (&va)[4],
+                             int dB, bool valid) {
+            if (kHog) {
+                const uint32_t P01 = __byte_perm(rb.r, rb.l, 0x5140), P23 = __byte_perm(rb.r, rb.l, 0x7362);
+                const uint32_t Q01 = __byte_perm(rc.c, ra.c, 0x5140), Q23 = __byte_perm(rc.c, ra.c, 0x7362);
+                const int gxb[4] = {dp2a_diff_lo(P01, (int)kMagicBits), dp2a_diff_hi(P01, (int)kMagicBits),
+                                    dp2a_diff_lo(P23, (int)kMagicBits), dp2a_diff_hi(P23, (int)kMagicBits)};
+                const int gyb[4] = {dp2a_diff_lo(Q01, (int)kMagicBits), dp2a_diff_hi(Q01, (int)kMagicBits),
+                                    dp2a_diff_lo(Q23, (int)kMagicBits), dp2a_diff_hi(Q23, (int)kMagicBits)};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const uint2 e = S.map[(code >> (8 * j)) & 0xffu];
-                    atomicAdd(&Wm.cnt[(int)e.x + lane], e.y);
+                    const float fx = __int_as_float(gxb[j]) - kMagic, fy = __int_as_float(gyb[j]) - kMagic;
+                    const float mag = sqrt_approx(fmaf(fx, fx, fy * fy));
+                    const float ax = fabsf(fx), ay = fabsf(fy);
+                    // mx is 0 or >= 1: the 1e-30 only turns 0 / 0 into 0
+                    const float z = fminf(ax, ay) * rcp_approx(fmaxf(ax, ay) + 1e-30f);
+                    const float pz = atan_bins_poly(z * z);
+                    // theta = phi, 4.5 - phi (steep), 9 - phi (opposite signs), 4.5 + phi (both);
+                    // the vote position is theta - 0.5, rounded below through theta - 1
+                    const bool steep = ay > ax;
+                    const bool mirror = (int)(__float_as_uint(fx) ^ __float_as_uint(fy)) < 0;
+                    const float zs = (steep != mirror) ? -z : z;
+                    const float off = steep ? 3.5f : (mirror ? 8.0f : -1.0f);
+                    const float tm1 = fmaf(pz, zs, off);
+                    const float t = tm1 + kMagic;
+                    const float o1 = (tm1 + 0.5f) - (t - kMagic);
+                    const int oa = (int)((uint32_t)__float_as_int(t) * 128u + va[j]);
+                    float *v = Wm.R + oa;
+                    float *u = Wm.R + (oa + dB);
+                    const float mo1 = mag * o1, mo0 = mag - mo1;
+                    v[0] = fmaf(mo0, wa, v[0]);
+                    v[kSCols] = fmaf(mo1, wa, v[kSCols]);
+                    u[0] = fmaf(mo0, wb, u[0]);
+                    u[kSCols] = fmaf(mo1, wb, u[kSCols]);
                 }
             }
-        }
-    };
+            if (kLbp) {
+                const uint32_t clo = rb.c & ~kHi, cn7 = ~rb.c & kHi;
+                const uint32_t code = (ge4(ra.l, clo, cn7) >> 7) | (ge4(ra.c, clo, cn7) >> 6) |
+                                      (ge4(ra.r, clo, cn7) >> 5) | (ge4(rb.r, clo, cn7) >> 4) |
+                                      (ge4(rc.r, clo, cn7) >> 3) | (ge4(rc.c, clo, cn7) >> 2) |
+                                      (ge4(rc.l, clo, cn7) >> 1) | ge4(rb.l, clo, cn7);
+                if (core && valid) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint2 e = S.map[(code >> (8 * j)) & 0xffu];
+                        atomicAdd(&Wm.cnt[(int)e.x + lane], e.y);
+                    }
+                }
+            }
+        };
 
-    // ---- LBP of cell row r = band - 1 is final after the band's first 4 rows:
-    // a cell's counts are its two lanes' counters; write them, clear
-    auto emit_lbp = [&](int band, bool walked) {
-        __syncwarp();  // every lane's counts of row r are in
-        const int r = band - 1;
-        const int c = lane & 15, half = lane >> 4;
-        if (walked && need(r) && c < kCellTW && cx0 + c < Wc) {
-            const int64_t pl = atlas.lbp_plane;
-            // bin planes 32 half .. 32 half + 31 of cell c
-            uint8_t *dst = atlas.lbp + (int64_t)(L.cell_row + cy0 + r) * atlas.pitch + cx0 + c + 32 * half * pl;
-            const uint32_t *cw = Wm.cnt + half * 8 * 32 + 2 * c + 1;
-            const int nw = half ? kCntWords - 8 : 8;
+        // ---- LBP of cell row r = band - 1 is final after the band's first 4 rows:
+        // a cell's counts are its two lanes' counters; write them, clear
+        auto emit_lbp = [&](int band, bool walked) {
+            __syncwarp();  // every lane's counts of row r are in
+            const int r = band - 1;
+            const int c = lane & 15, half = lane >> 4;
+            if (walked && need(r) && c < kCellTW && cx0 + c < Wc) {
+                const int64_t pl = atlas.lbp_plane;
+                // bin planes 32 half .. 32 half + 31 of cell c
+                uint8_t *dst = atlas.lbp + (int64_t)(L.cell_row + cy0 + r) * atlas.pitch + cx0 + c + 32 * half * pl;
+                const uint32_t *cw = Wm.cnt + half * 8 * 32 + 2 * c + 1;
+                const int nw = half ? kCntWords - 8 : 8;
 #pragma unroll 1
-            for (int i = 0; i < nw; ++i) {
-                const uint32_t val = cw[i * 32] + cw[i * 32 + 1];  // counts <= 32 each: no carry
-                dst[0] = (uint8_t)val;
-                dst[pl] = (uint8_t)(val >> 8);
-                dst[2 * pl] = (uint8_t)(val >> 16);
-                if (32 * half + 4 * i + 3 < kLbpBins) dst[3 * pl] = (uint8_t)(val >> 24);
-                dst += 4 * pl;
-            }
-        }
-        __syncwarp();  // read before cleared
-#pragma unroll
-        for (int wd = 0; wd < kCntWords; ++wd) Wm.cnt[wd * 32 + lane] = 0u;
-    };
-
-    // ---- HOG of cell row r = band - 1 is final: write it, recycle its slots
-    auto emit = [&](int band, bool walked) {
-        const int ringA = (band + 1) & 1, ringB = band & 1;
-        const int r = band - 1;
-        const bool out = walked && need(r);
-        const int64_t rowoff = (int64_t)(L.cell_row + cy0 + r) * atlas.pitch;
-        if (kHog) {
-            float *Ra = Wm.R + ringA * kRingStride + 4 * lane;
-            if (walked && band == 0 && cy0 == 0) {
-                // top of the level: the rows above cell row 0 vote into row 0
-                float *Rb = Wm.R + ringB * kRingStride + 4 * lane;
-#pragma unroll
-                for (int s = 0; s < kSlots; ++s) {
-                    float4 a = *reinterpret_cast<float4 *>(Ra + s * kSCols);
-                    float4 &b = *reinterpret_cast<float4 *>(Rb + s * kSCols);
-                    b.x += a.x;
-                    b.y += a.y;
-                    b.z += a.z;
-                    b.w += a.w;
+                for (int i = 0; i < nw; ++i) {
+                    const uint32_t val = cw[i * 32] + cw[i * 32 + 1];  // counts <= 32 each: no carry
+                    dst[0] = (uint8_t)val;
+                    dst[pl] = (uint8_t)(val >> 8);
+                    dst[2 * pl] = (uint8_t)(val >> 16);
+                    if (32 * half + 4 * i + 3 < kLbpBins) dst[3 * pl] = (uint8_t)(val >> 24);
+                    dst += 4 * pl;
                 }
             }
-            if (out) {
-                if (band == nb && cy0 + nb == Hc) {
-                    // bottom of the level: the rows below the last cell row vote into it
-                    const float *Rb = Wm.R + ringB * kRingStride + 4 * lane;
+            __syncwarp();  // read before cleared
+#pragma unroll
+            for (int wd = 0; wd < kCntWords; ++wd) Wm.cnt[wd * 32 + lane] = 0u;
+        };
+
+        // ---- HOG of cell row r = band - 1 is final: write it, recycle its slots
+        auto emit = [&](int band, bool walked) {
+            const int ringA = (band + 1) & 1, ringB = band & 1;
+            const int r = band - 1;
+            const bool out = walked && need(r);
+            const int64_t rowoff = (int64_t)(L.cell_row + cy0 + r) * atlas.pitch;
+            if (kHog) {
+                float *Ra = Wm.R + ringA * kRingStride + 4 * lane;
+                if (walked && band == 0 && cy0 == 0) {
+                    // top of the level: the rows above cell row 0 vote into row 0
+                    float *Rb = Wm.R + ringB * kRingStride + 4 * lane;
 #pragma unroll
                     for (int s = 0; s < kSlots; ++s) {
-                        float4 &a = *reinterpret_cast<float4 *>(Ra + s * kSCols);
-                        const float4 b = *reinterpret_cast<const float4 *>(Rb + s * kSCols);
-                        a.x += b.x;
-                        a.y += b.y;
-                        a.z += b.z;
-                        a.w += b.w;
+                        float4 a = *reinterpret_cast<float4 *>(Ra + s * kSCols);
+                        float4 &b = *reinterpret_cast<float4 *>(Rb + s * kSCols);
+                        b.x += a.x;
+                        b.y += a.y;
+                        b.z += a.z;
+                        b.w += a.w;
                     }
                 }
-                const bool st = (lane & 1) && lane <= 2 * kCellTW - 1 && cx0 + ((lane - 1) >> 1) < Wc;
-                float *dst = atlas.hog + rowoff + cx0 + ((lane - 1) >> 1);
+                if (out) {
+                    if (band == nb && cy0 + nb == Hc) {
+                        // bottom of the level: the rows below the last cell row vote into it
+                        const float *Rb = Wm.R + ringB * kRingStride + 4 * lane;
 #pragma unroll
-                for (int h = 0; h < kHogBins; ++h) {
-                    // bin h is slot h + 1; bin 0 also slot 10, bin 8 also slot 0
-                    float4 v = *reinterpret_cast<const float4 *>(Ra + (h + 1) * kSCols);
-                    if (h == 0 || h == kHogBins - 1) {
-                        const float4 u = *reinterpret_cast<const float4 *>(Ra + (h == 0 ? kSlots - 1 : 0) * kSCols);
-                        v.x += u.x;
-                        v.y += u.y;
-                        v.z += u.z;
-                        v.w += u.w;
+                        for (int s = 0; s < kSlots; ++s) {
+                            float4 &a = *reinterpret_cast<float4 *>(Ra + s * kSCols);
+                            const float4 b = *reinterpret_cast<const float4 *>(Rb + s * kSCols);
+                            a.x += b.x;
+                            a.y += b.y;
+                            a.z += b.z;
+                            a.w += b.w;
+                        }
                     }
-                    float own = wo[0] * v.x;
-                    own = fmaf(wo[1], v.y, own);
-                    own = fmaf(wo[2], v.z, own);
-                    own = fmaf(wo[3], v.w, own);
-                    float nbv = wn[0] * v.x;
-                    nbv = fmaf(wn[1], v.y, nbv);
-                    nbv = fmaf(wn[2], v.z, nbv);
-                    nbv = fmaf(wn[3], v.w, nbv);
-                    // cell (t - 1) / 2 at odd lane t: own(t) + own(t + 1) + nb(t - 1) + nb(t + 2)
-                    const float o_next = __shfl_down_sync(0xffffffffu, own, 1);
-                    const float n_prev = __shfl_up_sync(0xffffffffu, nbv, 1);
-                    const float n_next2 = __shfl_down_sync(0xffffffffu, nbv, 2);
-                    const float tot = ((own + o_next) + n_prev) + n_next2;
-                    if (st) dst[(int64_t)h * atlas.hog_plane] = tot;
+                    const bool st = (lane & 1) && lane <= 2 * kCellTW - 1 && cx0 + ((lane - 1) >> 1) < Wc;
+                    float *dst = atlas.hog + rowoff + cx0 + ((lane - 1) >> 1);
+#pragma unroll
+                    for (int h = 0; h < kHogBins; ++h) {
+                        // bin h is slot h + 1; bin 0 also slot 10, bin 8 also slot 0
+                        float4 v = *reinterpret_cast<const float4 *>(Ra + (h + 1) * kSCols);
+                        if (h == 0 || h == kHogBins - 1) {
+                            const float4 u = *reinterpret_cast<const float4 *>(Ra + (h == 0 ? kSlots - 1 : 0) * kSCols);
+                            v.x += u.x;
+                            v.y += u.y;
+                            v.z += u.z;
+                            v.w += u.w;
+                        }
+                        float own = wo[0] * v.x;
+                        own = fmaf(wo[1], v.y, own);
+                        own = fmaf(wo[2], v.z, own);
+                        own = fmaf(wo[3], v.w, own);
+                        float nbv = wn[0] * v.x;
+                        nbv = fmaf(wn[1], v.y, nbv);
+                        nbv = fmaf(wn[2], v.z, nbv);
+                        nbv = fmaf(wn[3], v.w, nbv);
+                        // cell (t - 1) / 2 at odd lane t: own(t) + own(t + 1) + nb(t - 1) + nb(t + 2)
+                        const float o_next = __shfl_down_sync(0xffffffffu, own, 1);
+                        const float n_prev = __shfl_up_sync(0xffffffffu, nbv, 1);
+                        const float n_next2 = __shfl_down_sync(0xffffffffu, nbv, 2);
+                        const float tot = ((own + o_next) + n_prev) + n_next2;
+                        if (st) dst[(int64_t)h * atlas.hog_plane] = tot;
+                    }
                 }
+                // clear the slots of row r for row r + 2 (only this lane wrote them)
+#pragma unroll
+                for (int s = 0; s < kSlots; ++s)
+                    *reinterpret_cast<float4 *>(Ra + s * kSCols) = make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            // clear the slots of row r for row r + 2 (only this lane wrote them)
-#pragma unroll
-            for (int s = 0; s < kSlots; ++s)
-                *reinterpret_cast<float4 *>(Ra + s * kSCols) = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    };
+        };
 
-    // ---- the walk: bands 0..nb. Rows arrive in pairs, the next pair loaded
-    // while the current one is processed (across band boundaries too).
-    uint32_t p0[3], p1[3];
-    Row ra, rb;
-    bool have = false;   // p0, p1 and ra, rb hold this band's first rows
-    bool walked_prev = false;
+        // ---- the walk: bands 0..nb. Rows arrive in pairs, the next pair loaded
+        // while the current one is processed (across band boundaries too).
+        uint32_t p0[3], p1[3];
+        Row ra, rb;
+        bool have = false;   // p0, p1 and ra, rb hold this band's first rows
+        bool walked_prev = false;
 #pragma unroll 1
-    for (int band = 0; band <= nb; ++band) {
-        const int yb = 8 * (cy0 + band) - 4;
-        if (!(need(band - 1) || need(band))) {
-            if (walked_prev) {  // recycle row band - 1's slots and counters
-                emit(band, false);
-                if (kLbp) emit_lbp(band, false);
+        for (int band = 0; band <= nb; ++band) {
+            const int yb = 8 * (cy0 + band) - 4;
+            if (!(need(band - 1) || need(band))) {
+                if (walked_prev) {  // recycle row band - 1's slots and counters
+                    emit(band, false);
+                    if (kLbp) emit_lbp(band, false);
+                }
+                have = false;
+                walked_prev = false;
+                continue;
             }
-            have = false;
-            walked_prev = false;
-            continue;
-        }
-        if (!have) {
-            uint32_t w[3];
-            fetch(yb - 1, w);
-            ra = mkrow(w);
-            fetch(yb, w);
-            rb = mkrow(w);
-            fetch(yb + 1, p0);
-            fetch(yb + 2, p1);
-        }
-        const bool pf = band + 1 <= nb && (need(band) || need(band + 1));
-        const int ringA = (band + 1) & 1;
-        const int dB = (ringA ? -1 : 1) * kRingStride;  // floats from row band - 1's slots to row band's
-        uint32_t va[4];
+            if (!have) {
+                uint32_t w[3];
+                fetch(yb - 1, w);
+                ra = mkrow(w);
+                fetch(yb, w);
+                rb = mkrow(w);
+                fetch(yb + 1, p0);
+                fetch(yb + 2, p1);
+            }
+            const bool pf = band + 1 <= nb && (need(band) || need(band + 1));
+            const int ringA = (band + 1) & 1;
+            const int dB = (ringA ? -1 : 1) * kRingStride;  // floats from row band - 1's slots to row band's
+            uint32_t va[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) va[j] = vb[j] + (uint32_t)(ringA * kRingStride);
+            for (int j = 0; j < 4; ++j) va[j] = vb[j] + (uint32_t)(ringA * kRingStride);
 #pragma unroll 1
-        for (int i = 0; i < 4; ++i) {
-            const Row c0 = mkrow(p0), c1 = mkrow(p1);
-            if (i < 3 || pf) {
-                fetch(yb + 3 + 2 * i, p0);
-                fetch(yb + 4 + 2 * i, p1);
+            for (int i = 0; i < 4; ++i) {
+                const Row c0 = mkrow(p0), c1 = mkrow(p1);
+                if (i < 3 || pf) {
+                    fetch(yb + 3 + 2 * i, p0);
+                    fetch(yb + 4 + 2 * i, p1);
+                }
+                // band rows k = 2i, 2i + 1: weights (7.5 - k) / 8 and (k + 0.5) / 8;
+                // LBP cell row band - 1 for k < 4, band for k >= 4
+                const float wa0 = (7.5f - 2 * i) * 0.125f;
+                const int y = yb + 2 * i;
+                const bool v0 = y >= 0 && y < gridH, v1 = y + 1 >= 0 && y + 1 < gridH;
+                pixel_row(ra, rb, c0, v0 ? wa0 : 0.f, v0 ? 1.f - wa0 : 0.f, va, dB, v0);
+                pixel_row(rb, c0, c1, v1 ? wa0 - 0.125f : 0.f, v1 ? 1.125f - wa0 : 0.f, va, dB, v1);
+                ra = c0;
+                rb = c1;
+                if (kLbp && i == 1) emit_lbp(band, true);
             }
-            // band rows k = 2i, 2i + 1: weights (7.5 - k) / 8 and (k + 0.5) / 8;
-            // LBP cell row band - 1 for k < 4, band for k >= 4
-            const float wa0 = (7.5f - 2 * i) * 0.125f;
-            const int y = yb + 2 * i;
-            const bool v0 = y >= 0 && y < gridH, v1 = y + 1 >= 0 && y + 1 < gridH;
-            pixel_row(ra, rb, c0, v0 ? wa0 : 0.f, v0 ? 1.f - wa0 : 0.f, va, dB, v0);
-            pixel_row(rb, c0, c1, v1 ? wa0 - 0.125f : 0.f, v1 ? 1.125f - wa0 : 0.f, va, dB, v1);
-            ra = c0;
-            rb = c1;
-            if (kLbp && i == 1) emit_lbp(band, true);
+            emit(band, true);
+            have = pf;
+            walked_prev = true;
         }
-        emit(band, true);
-        have = pf;
-        walked_prev = true;
+        __syncwarp();  // the next strip reuses the warp's shared memory
     }
 }
 
-using StripFn = void (*)(const LevelDesc *, const uint8_t *, CellAtlas, const StripItem *, int, const uint8_t *,
-                         const uint32_t *);
+using StripFn = void (*)(const LevelDesc *, const uint8_t *, CellAtlas, const StripItem *, int, int *,
+                         const uint8_t *, const uint32_t *);
 const StripFn kStripFns[3] = {k_cells_warp<kFeatHog | kFeatLbp>, k_cells_warp<kFeatHog>,
                               k_cells_warp<kFeatLbp>};
 
@@ -466,11 +472,13 @@ cudaError_t init_cells_warp() {
 }
 
 cudaError_t launch_cells_warp(cudaStream_t s, const LevelDesc *d_levels, const uint8_t *pyr, CellAtlas atlas,
-                              const StripItem *d_items, int n_items, const uint8_t *d_lbp_map,
-                              const uint32_t *c_flag, int feat) {
+                              const StripItem *d_items, int n_items, int *d_queue, int sm_count,
+                              const uint8_t *d_lbp_map, const uint32_t *c_flag, int feat) {
     if (n_items <= 0) return cudaSuccess;
-    kStripFns[strip_fn_index(feat)]<<<(n_items + kWarps - 1) / kWarps, kWarps * 32, sizeof(StripSmem), s>>>(
-        d_levels, pyr, atlas, d_items, n_items, d_lbp_map, c_flag);
+    // resident CTAs: 4 per SM (shared memory); the warps share the strip queue
+    const int grid = std::min((n_items + kWarps - 1) / kWarps, 4 * sm_count);
+    kStripFns[strip_fn_index(feat)]<<<grid, kWarps * 32, sizeof(StripSmem), s>>>(d_levels, pyr, atlas, d_items,
+                                                                                 n_items, d_queue, d_lbp_map, c_flag);
     return cudaGetLastError();
 }
 

@@ -288,7 +288,7 @@ struct pd_handle {
     // tensor maps over the atlases, one pair per K4 tile shape
     CUtensorMap hog_map[kSvmShapes]{}, lbp_map[kSvmShapes]{};
     CUtensorMap tc_hog_map{}, tc_lbp_map{};  // the same planes for the tensor-core K4
-    int *d_queue = nullptr;                  // its item counter (zeroed before each launch)
+    int *d_queue = nullptr;                  // [2]: K4's and K2+K3's item counters (zeroed before each launch)
     int sm_count = 1;
     float tile_cost[kSvmShapes] = {kDefaultTileCost[0], kDefaultTileCost[1], kDefaultTileCost[2],
                                    kDefaultTileCost[3], kDefaultTileCost[4], kDefaultTileCost[5],
@@ -716,8 +716,11 @@ cudaError_t launch_cell_stage(pd_handle *h, cudaStream_t s, const LevelDesc *dl,
     if (feat & kFeatHogBlock)
         return launch_cells(s, dl, pyr, atlas, dptr<CellItem>(h, o.c_items), (int)p.c_items.size(), h->d_lbp_map,
                             c_flag, feat);
-    return launch_cells_warp(s, dl, pyr, atlas, dptr<StripItem>(h, o.strips), (int)p.strips.size(), h->d_lbp_map,
-                             c_flag, feat);
+    int *queue = h->d_queue + 1;  // the strip counter (K4's is d_queue[0])
+    const cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    return launch_cells_warp(s, dl, pyr, atlas, dptr<StripItem>(h, o.strips), (int)p.strips.size(), queue,
+                             h->sm_count, h->d_lbp_map, c_flag, feat);
 }
 
 }  // namespace

@@ -120,9 +120,10 @@ cudaError_t launch_cells(cudaStream_t s, const LevelDesc *d_levels, const uint8_
                          const uint32_t *c_flag = nullptr, int feat = kFeatHog | kFeatLbp);
 // Default K2+K3 (HOG and / or LBP without per-block HOG): one warp per strip.
 cudaError_t init_cells_warp();
+// Persistent warps over a strip queue (*d_queue must be 0 at launch).
 cudaError_t launch_cells_warp(cudaStream_t s, const LevelDesc *d_levels, const uint8_t *pyr, CellAtlas atlas,
-                              const StripItem *d_items, int n_items, const uint8_t *d_lbp_map,
-                              const uint32_t *c_flag, int feat);
+                              const StripItem *d_items, int n_items, int *d_queue, int sm_count,
+                              const uint8_t *d_lbp_map, const uint32_t *c_flag, int feat);
 cudaError_t launch_proposal_flags(cudaStream_t s, const LevelDesc *d_levels, const SvmItem *d_items, int n_items,
                                   const float *logits, float tau, uint32_t *s_flag, uint32_t *c_flag,
                                   bool per_window);
