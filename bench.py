@@ -842,17 +842,17 @@ def run_gpu(args):
     cells_ach = cells_ops / (stage_step[1] / 1e3) / 1e12
     roof_cells = {"bound": "alu", "achieved": cells_ach, "peak": lane_peak, "unit": "Tops/s",
                   "frac": cells_ach / lane_peak,
-                  "traffic": None if args.hog_per_block else scaled(recorded_traffic("k_cells_1242x375_b64.txt",
-                                                                                     "k_cells.cu"), B / 64.0),
-                  "kernel": "k_cells (uniform LBP + soft-binned HOG cell histograms)" + (
+                  "traffic": None if args.hog_per_block else scaled(
+                      recorded_traffic("k_cells_warp_1242x375_b32.txt", "k_cells_warp.cu"), B / 64.0),
+                  "kernel": "k_cells_warp (uniform LBP + soft-binned HOG cell histograms, a warp per strip)" + (
                       "; per-block HOG variant, ops still counted as for shared cells" if args.hog_per_block else ""),
                   "peak_basis": f"{sm_count} SMs x 128 lanes x {sm_mhz} MHz, one op per lane slot "
                                 f"({OPS_PER_CELL_PIXEL} algorithmic ops per cell-grid pixel; max SM clock, "
                                 f"{peak_kind})",
-                  # ncu, same source: fraction of cycles the schedulers issued (the kernel runs ~3.6
+                  # ncu, same source: fraction of cycles the schedulers issued (the kernel runs ~1.9
                   # instructions per algorithmic op: addressing, shared-memory traffic, control)
                   "issue_active_frac": None if args.hog_per_block else recorded_traffic(
-                      "k_cells_1242x375_b64.txt", "k_cells.cu", "issue_active_frac")}
+                      "k_cells_warp_1242x375_b32.txt", "k_cells_warp.cu", "issue_active_frac")}
     # window scores (K4)
     k4_s = stage_step[2] / 1e3
     if args.svm == "fp32":

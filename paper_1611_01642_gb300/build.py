@@ -18,7 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpd.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["k_resize.cu", "k_cells.cu", "k_cells_warp.cu", "k_svm.cu", "k_svm_tc.cu", "k_nms.cu", "k_cnn.cu", "k_cnn_train.cu", "k_sparse.cu", "k_schemes.cu", "pd_api.cu"]
+SOURCES = ["k_resize.cu", "k_cells.cu", "k_cells_warp.cu", "k_svm.cu", "k_svm_tc.cu", "k_nms.cu", "k_cnn.cu",
+           "k_cnn_train.cu", "k_sparse.cu", "k_schemes.cu", "pd_api.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-I", INCLUDE]

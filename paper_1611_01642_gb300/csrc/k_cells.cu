@@ -1,5 +1,9 @@
-// K2 + K3 -- HOG and uniform-LBP cell histograms of one pyramid level
-// (Section 4.2, Algorithms 1-2; Section 4.3, Algorithms 4-5).
+// K2 + K3 with per-block HOG -- HOG and uniform-LBP cell histograms of one
+// pyramid level (Section 4.2, Algorithms 1-2; Section 4.3, Algorithms 4-5),
+// the HOG histograms restricted to each 16x16 block (kFeatHogBlock below).
+// The shared-cell features (the default) run on the warp-per-strip kernel of
+// k_cells_warp.cu; this CTA-per-tile kernel keeps the general FEAT template
+// it was written with.
 //
 // One CTA of 128 threads owns a tile of 15 x 8 cells (120 x 64 pixels). It
 // first stages the 130 x 74 pixel region it reads (the tile, the 4 pixels on
@@ -403,25 +407,14 @@ namespace {
 using CellFn = void (*)(const LevelDesc *, const uint8_t *, CellAtlas, const CellItem *, const uint8_t *,
                         const uint32_t *);
 constexpr int kBlk = kFeatHogBlock;
-const CellFn kCellFns[5] = {k_cells<kFeatHog | kFeatLbp>, k_cells<kFeatHog>, k_cells<kFeatLbp>,
-                            k_cells<kFeatHog | kFeatLbp | kBlk>, k_cells<kFeatHog | kBlk>};
-const int kCellSmem[5] = {(int)sizeof(CellSmem<1>), (int)sizeof(CellSmem<1>), (int)sizeof(CellSmem<1>),
-                          (int)sizeof(CellSmem<2>), (int)sizeof(CellSmem<2>)};
-int cell_fn_index(int feat) {
-    switch (feat) {
-        case kFeatHog: return 1;
-        case kFeatLbp: return 2;
-        case kFeatHog | kFeatLbp | kBlk: return 3;
-        case kFeatHog | kBlk: return 4;
-        default: return 0;
-    }
-}
+// per-block HOG only (the shared-cell features run on the warp-per-strip kernel)
+const CellFn kCellFns[2] = {k_cells<kFeatHog | kFeatLbp | kBlk>, k_cells<kFeatHog | kBlk>};
+const int kCellSmem = (int)sizeof(CellSmem<2>);
 }  // namespace
 
 cudaError_t init_cells() {
-    for (int i = 0; i < 5; ++i) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(kCellFns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, kCellSmem[i]);
+    for (int i = 0; i < 2; ++i) {
+        const cudaError_t e = cudaFuncSetAttribute(kCellFns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, kCellSmem);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -430,9 +423,10 @@ cudaError_t init_cells() {
 cudaError_t launch_cells(cudaStream_t s, const LevelDesc *d_levels, const uint8_t *pyr,
                          CellAtlas atlas, const CellItem *d_items, int n_items,
                          const uint8_t *d_lbp_map, const uint32_t *c_flag, int feat) {
+    if (!(feat & kFeatHogBlock)) return cudaErrorInvalidValue;
     if (n_items <= 0) return cudaSuccess;
-    const int k = cell_fn_index(feat);
-    kCellFns[k]<<<n_items, kThreads, kCellSmem[k], s>>>(d_levels, pyr, atlas, d_items, d_lbp_map, c_flag);
+    const int k = (feat & kFeatLbp) ? 0 : 1;
+    kCellFns[k]<<<n_items, kThreads, kCellSmem, s>>>(d_levels, pyr, atlas, d_items, d_lbp_map, c_flag);
     return cudaGetLastError();
 }
 

@@ -3,7 +3,7 @@
 // strip of cells, four pixel columns per lane.
 //
 // A strip is 15 cells wide and up to kStripTiles cell tiles (8 cell rows
-// each) tall. Its warp walks the 128 pixel columns [8 cx0 - 4, 8 cx0 + 124)
+// each) tall (the planner takes shorter strips for small batches). Its warp walks the 128 pixel columns [8 cx0 - 4, 8 cx0 + 124)
 // (the strip and the 4 columns on each side whose HOG votes still reach it):
 // lane t owns columns 8 cx0 - 4 + 4t .. + 3, which lie in one cell (strip
 // cell (t - 1) / 2; lanes 0 and 31 lie in the neighbouring strips). The warp
@@ -475,8 +475,10 @@ cudaError_t launch_cells_warp(cudaStream_t s, const LevelDesc *d_levels, const u
                               const StripItem *d_items, int n_items, int *d_queue, int sm_count,
                               const uint8_t *d_lbp_map, const uint32_t *c_flag, int feat) {
     if (n_items <= 0) return cudaSuccess;
-    // resident CTAs: 4 per SM (shared memory); the warps share the strip queue
-    const int grid = std::min((n_items + kWarps - 1) / kWarps, 4 * sm_count);
+    // resident CTAs: 4 per SM (shared memory); the warps share the strip queue. A
+    // small plan gets one CTA per strip, so that its warps spread over the SMs.
+    static_assert(kWarps * 4 == kStripWarpsPerSm, "resident warps per SM");
+    const int grid = std::min(n_items, 4 * sm_count);
     kStripFns[strip_fn_index(feat)]<<<grid, kWarps * 32, sizeof(StripSmem), s>>>(d_levels, pyr, atlas, d_items,
                                                                                  n_items, d_queue, d_lbp_map, c_flag);
     return cudaGetLastError();

@@ -403,9 +403,28 @@ void plan_tc(std::vector<TcItem> &out, int li, int rows, int cols, int chunk) {
             out.push_back({li, x, (int)((int64_t)rows * k / pieces), (int)((int64_t)rows * (k + 1) / pieces)});
 }
 
-// K2+K3 strips: tallest first, so that the grid ends with the short ones.
-void order_strips(std::vector<StripItem> &t) {
-    std::stable_sort(t.begin(), t.end(),
+// K2+K3 strips of every level of a plan, tallest first (the warps take them
+// in this order, so the queue ends with the short ones). A strip is
+// kStripTiles cell tiles tall, or shorter (down to 2 cell rows) when the
+// plan would give fewer strips than the device holds warps: a warp alone on
+// an SM exposes every latency, so small batches take more, shorter strips.
+// The strip height does not change the result (every cell row sums its
+// votes in the same order).
+void plan_strips(Plan &p, int resident_warps) {
+    auto count = [&](int rows) {
+        int64_t n = 0;
+        for (const LevelDesc &L : p.levels) n += (int64_t)L.ctx * ((L.Hc + rows - 1) / rows);
+        return n;
+    };
+    int rows = kCellTH * kStripTiles;
+    while (rows > 2 && count(rows) < resident_warps) rows /= 2;
+    p.strips.clear();
+    for (int li = 0; li < (int)p.levels.size(); ++li) {
+        const LevelDesc &L = p.levels[li];
+        for (int cx = 0; cx < L.Wc; cx += kCellTW)
+            for (int cy = 0; cy < L.Hc; cy += rows) p.strips.push_back({li, cx, cy, std::min(cy + rows, L.Hc)});
+    }
+    std::stable_sort(p.strips.begin(), p.strips.end(),
                      [](const StripItem &a, const StripItem &b) { return a.cy1 - a.cy0 > b.cy1 - b.cy0; });
 }
 
@@ -530,9 +549,6 @@ void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int
     L.ctx = (L.Wc + kCellTW - 1) / kCellTW;
     for (int cy = 0; cy < L.Hc; cy += kCellTH)
         for (int cx = 0; cx < L.Wc; cx += kCellTW) p.c_items.push_back({li, cx, cy, 0});
-    for (int cx = 0; cx < L.Wc; cx += kCellTW)
-        for (int cy = 0; cy < L.Hc; cy += kCellTH * kStripTiles)
-            p.strips.push_back({li, cx, cy, std::min(cy + kCellTH * kStripTiles, L.Hc)});
     plan_windows(p.s_items, li, L.rows, L.cols, tile_cost);
     plan_tc(p.t_items, li, L.rows, L.cols, p.tc_rows);
     p.atlas_rows += L.Hc;
@@ -875,7 +891,7 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
                       round_up(F * (int64_t)one.levels.size() * (int64_t)sizeof(LevelDesc), 16) +
                       round_up(F * (int64_t)one.r_items.size() * (int64_t)sizeof(ResizeItem), 16) +
                       round_up(F * (int64_t)one.c_items.size() * (int64_t)sizeof(CellItem), 16) +
-                      round_up(F * (int64_t)one.strips.size() * (int64_t)sizeof(StripItem), 16) +
+                      round_up(4 * F * (int64_t)one.c_items.size() * (int64_t)sizeof(StripItem), 16) +  // 2-row strips
                       round_up(F * s_bound * (int64_t)sizeof(SvmItem), 16) +
                       round_up(F * (int64_t)one.t_items.size() * (int64_t)sizeof(TcItem), 16) +
                       round_up(F * (int64_t)one.tabs.size() * 4, 16) + 4096;
@@ -1036,7 +1052,7 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
             if (r != PD_OK) return fail(h, r, "frame %d: planning failed", f);
         }
         order_tc(p.t_items);
-        order_strips(p.strips);
+        plan_strips(p, h->sm_count * kStripWarpsPerSm);
         if (p.atlas_rows > h->atlas.rows || p.pyr_bytes > h->pyr_cap || p.score_floats > h->score_cap ||
             (int64_t)p.s_items.size() > h->flag_cap || (int64_t)p.c_items.size() > h->flag_cap)
             return fail(h, PD_EINVAL, "batch exceeds the arena");
@@ -1516,6 +1532,7 @@ int pd_cell_features(pd_handle *h, void *stream, const uint8_t *d_level, int Wk,
         return fail(h, PD_EINVAL, "pd_cell_features: bad argument");
     Plan p;
     plan_level(p, 0, 0, Wk, Hk, Wk, Hk, 0, pitch);
+    plan_strips(p, h->sm_count * kStripWarpsPerSm);
     p.s_items.clear();
     p.t_items.clear();
     p.tabs.clear();

@@ -73,9 +73,10 @@ __host__ __device__ inline int resize_quad_index(int d) { return d + (d >> 5); }
 // K1 quad row pitch in words: > resize_quad_index(kResizeBW - 2) and 1 mod 32, so that
 // quad rows sy and sy + 1 start one bank apart
 constexpr int kResizeQP = 193;
-constexpr int kCellTW = 15;     // cells per cell tile along x (128 threads = 8*15+8 columns)
+constexpr int kCellTW = 15;     // cells per cell tile along x (8*15+8 = 128 columns: 128 threads, or 32 lanes x 4)
 constexpr int kCellTH = 8;      // cells per cell tile along y
-constexpr int kStripTiles = 4;  // cell tiles per K2+K3 strip (one warp each), top to bottom
+constexpr int kStripTiles = 4;  // cell tiles per K2+K3 strip (one warp each), top to bottom, at most
+constexpr int kStripWarpsPerSm = 16;  // K2+K3 warps resident per SM (4 CTAs of 4)
 constexpr int kSvmShapes = 7;   // K4 tile shapes: 32x16, 64x8, 32x8, 64x4, 64x2, 32x12, 32x4 windows
 constexpr int kTcStrip = 104;   // tensor-core K4: window columns per item
 constexpr int kTcChunk = 64;    // tensor-core K4: window rows per item at most (tunable down to kTcMinChunk)
@@ -111,9 +112,10 @@ cudaError_t init_resize();
 cudaError_t launch_resize(cudaStream_t s, const FrameDesc *d_frames, const LevelDesc *d_levels,
                           const int32_t *d_tabs, uint8_t *pyr, const ResizeItem *d_items,
                           int n_items, int k1_groups = 8);
-// feat: kFeatHog | kFeatLbp (the features the pipeline uses), plus
-// kFeatHogBlock for per-block HOG (36 planes: the 4 block-restricted
-// histograms of every cell, plane 9 q + bin)
+// CTA-per-tile K2+K3 for per-block HOG: feat = kFeatHogBlock | kFeatHog
+// (| kFeatLbp); 36 HOG planes, the 4 block-restricted histograms of every
+// cell, plane 9 q + bin. Other feature sets: cudaErrorInvalidValue (they
+// run on launch_cells_warp).
 constexpr int kFeatHog = 1, kFeatLbp = 2, kFeatHogBlock = 4;
 cudaError_t launch_cells(cudaStream_t s, const LevelDesc *d_levels, const uint8_t *pyr,
                          CellAtlas atlas, const CellItem *d_items, int n_items, const uint8_t *d_lbp_map,
