@@ -9,7 +9,7 @@
 //     with a candidate cap above 16,384 the key list lives in the frame's
 //     global scratch instead (same steps, slower sort);
 //  2. sorts the keys: a bitonic sort in shared memory, or, for caps above
-//     16,384, bitonic sorts of 8,192-key chunks in shared memory followed by
+//     16,384, bitonic sorts of 16,384-key chunks in shared memory followed by
 //     merge passes over the global key list (each thread merges its slice
 //     of outputs after locating it by binary search on the two runs);
 //  3. decodes every candidate's box once (exactly rounded float division)
@@ -44,8 +44,9 @@ constexpr int kMaxCandidates = 16384;     // keys + flags + kept list fit in sha
 constexpr int kMaxCandidatesBig = 65536;  // keys in global scratch
 constexpr int kMaxBoxes = 16384;
 constexpr int kBatch = 64;                // greedy walk: candidates resolved per block-wide step
-constexpr int kGrid = 64;                 // culling grid: kGrid x kGrid cells over the frame
+constexpr int kGrid = 32;                 // culling grid: kGrid x kGrid cells over the frame
 static_assert(kThreads == 16 * kBatch, "pairwise matrix: 16 threads per batch member");
+static_assert(kThreads == kGrid * kGrid, "one culling cell per thread");
 
 __device__ __forceinline__ unsigned long long make_key(float s, int level, int wy, int wx) {
     const uint32_t u = __float_as_uint(s);
@@ -127,7 +128,7 @@ __device__ __forceinline__ bool suppresses(const float4 &a, const float4 &b, flo
     return iou4(a, b) > (double)thr;
 }
 
-constexpr int kSortChunk = 8192;  // keys per shared-memory chunk of the large-cap sort (64 KB)
+constexpr int kSortChunk = 16384;  // keys per shared-memory chunk of the large-cap sort (128 KB)
 
 // Ascending bitonic sort of m = R * kThreads keys in shared memory k, with
 // each thread holding the R consecutive keys [tid R, tid R + R) in registers:
@@ -452,16 +453,17 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
     // in B (were it outside B on one axis, A and B would overlap on at most
     // half of A's extent there, so inter <= |A| / 2, and inter > (|A| + |B|)
     // / 3 would need |B| < |A| / 2 while inter <= |B| needs |B| > |A| / 2).
-    // Each batch marks the cells of a 64 x 64 grid over the frame that its
-    // kept boxes cover (one cell of margin for rounding); a candidate whose
-    // centre's cell is unmarked cannot be suppressed by them and skips its
-    // IoU tests.
+    // Each batch records, for every cell of a 32 x 32 grid over the frame,
+    // which of its kept boxes cover the cell (one cell of margin for
+    // rounding); a candidate is tested only against the kept boxes that cover
+    // its centre's cell (no test at all when none does).
     __shared__ int batch[kBatch];
     __shared__ float4 bbx[kBatch], kbx[kBatch];
     __shared__ unsigned long long bcol[kBatch];  // member b: bit a set iff a < b and a suppresses b
     __shared__ int n_batch, n_keep, kept_total, scan_pos;
     __shared__ int wcnt[kThreads / 32];
-    __shared__ uint32_t gmask[kGrid * kGrid / 32];  // culling grid, one bit per cell
+    __shared__ unsigned long long cmask[kGrid * kGrid];  // culling grid: kept boxes covering each cell
+    __shared__ int4 krect[kBatch];                       // kept boxes' cell ranges x0, x1, y0, y1
     int *kept_idx = reinterpret_cast<int *>(supp + ((cap + 15) & ~15));
     const int warp = tid >> 5, lane = tid & 31;
     const bool cull = iou_thr >= 0.5f;
@@ -563,42 +565,52 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
         if (kept_total >= max_boxes) break;
         const int nk = n_keep;
         if (cull) {
-            // grid cells under the kept boxes, with one cell of margin
-            for (int i = tid; i < kGrid * kGrid / 32; i += kThreads) gmask[i] = 0u;
-            __syncthreads();
-            for (int t = tid; t < nk * kGrid; t += kThreads) {
-                const int k = t / kGrid, cy = t - k * kGrid;
-                const float4 b = kbx[k];
-                const int y0 = max((int)floorf(b.y * gsy) - 1, 0), y1 = min((int)floorf((b.y + b.w) * gsy) + 1, kGrid - 1);
-                if (cy < y0 || cy > y1) continue;
-                const int x0 = max((int)floorf(b.x * gsx) - 1, 0), x1 = min((int)floorf((b.x + b.z) * gsx) + 1, kGrid - 1);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int lo = max(x0 - 32 * h, 0), hi = min(x1 - 32 * h, 31);
-                    if (lo <= hi) {
-                        const uint32_t bits = (hi - lo == 31 ? 0xffffffffu : ((1u << (hi - lo + 1)) - 1u)) << lo;
-                        atomicOr(&gmask[cy * 2 + h], bits);
-                    }
-                }
+            // grid cells under each kept box, with one cell of margin; then per
+            // cell (one per thread) the set of kept boxes that cover it
+            if (tid < nk) {
+                const float4 b = kbx[tid];
+                krect[tid] = make_int4(max((int)floorf(b.x * gsx) - 1, 0),
+                                       min((int)floorf((b.x + b.z) * gsx) + 1, kGrid - 1),
+                                       max((int)floorf(b.y * gsy) - 1, 0),
+                                       min((int)floorf((b.y + b.w) * gsy) + 1, kGrid - 1));
             }
+            __syncthreads();
+            const int cx = tid & (kGrid - 1), cy = tid / kGrid;
+            unsigned long long m = 0ull;
+            for (int k = 0; k < nk; ++k) {
+                const int4 r = krect[k];
+                if (cx >= r.x && cx <= r.y && cy >= r.z && cy <= r.w) m |= 1ull << k;
+            }
+            cmask[tid] = m;
             __syncthreads();
         }
-        for (int j = scan_pos + tid; j < n; j += kThreads) {
+        int j = scan_pos + tid;
+        float4 bnext = j < n ? bx[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (; j < n; j += kThreads) {
+            // the next box is loaded while this one is tested (global for large caps)
+            const float4 bj = bnext;
+            if (j + kThreads < n) bnext = bx[j + kThreads];
             if (supp[j]) continue;
-            const float4 bj = bx[j];
+            bool hit = false;
             if (cull) {
+                // only the kept boxes that cover the centre's cell can suppress it
                 const int cx = min(max((int)floorf((bj.x + 0.5f * bj.z) * gsx), 0), kGrid - 1);
                 const int cy = min(max((int)floorf((bj.y + 0.5f * bj.w) * gsy), 0), kGrid - 1);
-                if (!((gmask[cy * 2 + (cx >> 5)] >> (cx & 31)) & 1u)) continue;  // no kept box holds its centre
-            }
-            bool hit = false;
-            for (int k = 0; k < nk && !hit; k += 4) {
-                // four tests in flight (kept boxes past nk repeat the first one)
-                const bool h0 = suppresses(kbx[k], bj, iou_thr);
-                const bool h1 = suppresses(kbx[k + 1 < nk ? k + 1 : 0], bj, iou_thr);
-                const bool h2 = suppresses(kbx[k + 2 < nk ? k + 2 : 0], bj, iou_thr);
-                const bool h3 = suppresses(kbx[k + 3 < nk ? k + 3 : 0], bj, iou_thr);
-                hit = h0 || h1 || h2 || h3;
+                unsigned long long m = cmask[cy * kGrid + cx];
+                while (m && !hit) {
+                    const int k = __ffsll((long long)m) - 1;
+                    m &= m - 1ull;
+                    hit = suppresses(kbx[k], bj, iou_thr);
+                }
+            } else {
+                for (int k = 0; k < nk && !hit; k += 4) {
+                    // four tests in flight (kept boxes past nk repeat the first one)
+                    const bool h0 = suppresses(kbx[k], bj, iou_thr);
+                    const bool h1 = suppresses(kbx[k + 1 < nk ? k + 1 : 0], bj, iou_thr);
+                    const bool h2 = suppresses(kbx[k + 2 < nk ? k + 2 : 0], bj, iou_thr);
+                    const bool h3 = suppresses(kbx[k + 3 < nk ? k + 3 : 0], bj, iou_thr);
+                    hit = h0 || h1 || h2 || h3;
+                }
             }
             if (hit) supp[j] = 1;
         }
