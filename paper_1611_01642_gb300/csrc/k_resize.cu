@@ -52,7 +52,8 @@ constexpr int kOffRng = kOffQuad + ((kTH * kQP * 4 + 15) & ~15);  // int4 per le
 constexpr int kOffCnt = kOffRng + kML * 16;             // int per level: warp tasks (-1: the copied level)
 constexpr int kOffPre = kOffCnt + kML * 4;              // int per level + 1: first task
 constexpr int kOffMisc = kOffPre + (kML + 1) * 4;       // copied level, task counter
-constexpr int kSmemBytes = kOffMisc + 16;
+constexpr int kOffLvl = (kOffMisc + 16 + 15) & ~15;     // per level: the fields the task loop reads
+constexpr int kSmemBytes = kOffLvl + kML * 32;
 static_assert(kOffQuad % 16 == 0 && kOffRng % 16 == 0, "alignment");
 
 // One output pixel: its quad (taps) at shared-memory byte address qa, packed
@@ -85,6 +86,8 @@ __global__ void __launch_bounds__(kThreads, 5) k_resize(const FrameDesc *__restr
     int *s_cnt = reinterpret_cast<int *>(smem + kOffCnt);
     int *s_pre = reinterpret_cast<int *>(smem + kOffPre);
     int *s_misc = reinterpret_cast<int *>(smem + kOffMisc);
+    // per level: {img_off lo, img_off hi, pitch, Wk}, {rgroup, xtab_off, xq_off, ytab_off}
+    int4 *s_lvl = reinterpret_cast<int4 *>(smem + kOffLvl);
 
     const ResizeItem it = items[blockIdx.x];
     const FrameDesc fd = frames[it.frame];
@@ -129,6 +132,9 @@ __global__ void __launch_bounds__(kThreads, 5) k_resize(const FrameDesc *__restr
             const int ng = ge - gs, nr = re - rs;
             const bool work = !copy && ng > 0 && nr > 0;
             s_rng[k] = make_int4(gs, ng, rs, nr);
+            s_lvl[2 * k] = make_int4((int)(uint32_t)(uint64_t)L.img_off, (int)((uint64_t)L.img_off >> 32),
+                                     L.img_pitch, L.Wk);
+            s_lvl[2 * k + 1] = make_int4(L.rgroup, L.xtab_off, L.xq_off, L.ytab_off);
             // warp tasks (-1 marks the copied level: a frame has at most one level of scale 1)
             s_cnt[k] = copy ? -1 : work ? (ng + kCG - 1) / kCG : 0;
         }
@@ -243,16 +249,17 @@ __global__ void __launch_bounds__(kThreads, 5) k_resize(const FrameDesc *__restr
         const int4 rg = s_rng[k];
         const int g = (t - s_pre[k]) * kCG + c;
         if (g < rg.y) {
-        const LevelDesc &L = levels[fd.first_level + k];
+        const int4 la = s_lvl[2 * k], lb = s_lvl[2 * k + 1];
+        const int64_t img_off = (int64_t)(((uint64_t)(uint32_t)la.y << 32) | (uint32_t)la.x);
         const int gg = rg.x + g;
-        const int4 wx = __ldg(reinterpret_cast<const int4 *>(tabs + L.xtab_off) + gg);
-        const uint32_t qo = (uint32_t)__ldg(tabs + L.xq_off + gg);
-        const int G = L.rgroup, Wk = L.Wk, pitch = L.img_pitch;
+        const int4 wx = __ldg(reinterpret_cast<const int4 *>(tabs + lb.y) + gg);
+        const uint32_t qo = (uint32_t)__ldg(tabs + lb.z + gg);
+        const int G = lb.x, Wk = la.w, pitch = la.z;
         const int x = G * gg;
         const int y0 = rg.z + j, re = rg.z + rg.w;
         const int nrow = y0 < re ? (re - y0 + kRS - 1) / kRS : 0;
-        const int2 *yp = reinterpret_cast<const int2 *>(tabs + L.ytab_off) + y0;
-        uint8_t *op = pyr + L.img_off + x + (size_t)y0 * pitch;
+        const int2 *yp = reinterpret_cast<const int2 *>(tabs + lb.w) + y0;
+        uint8_t *op = pyr + img_off + x + (size_t)y0 * pitch;
         const size_t ostep = (size_t)kRS * pitch;
         if (G == 4) {
             const uint32_t a0 = quad_base + 4u * (qo & 255u), a1 = quad_base + 4u * ((qo >> 8) & 255u);
@@ -266,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_resize(const FrameDesc *__restr
                 o2 = q11_pixel(a2 + ro, (uint32_t)wx.z, wt, wb);
                 o3 = q11_pixel(a3 + ro, (uint32_t)wx.w, wt, wb);
             };
-            if (x + 4 <= Wk && ((reinterpret_cast<uintptr_t>(pyr + L.img_off) | (uintptr_t)pitch) & 3) == 0) {
+            if (x + 4 <= Wk && ((reinterpret_cast<uintptr_t>(pyr + img_off) | (uintptr_t)pitch) & 3) == 0) {
 #pragma unroll 2
                 for (int i = 0; i < nrow; ++i, yp += kRS, op += ostep) {
                     uint32_t o0, o1, o2, o3;
