@@ -34,6 +34,8 @@
 // evaluation of the definition. Decisions are therefore the same as those of
 // a plain double-precision implementation, and the slow double path runs
 // only for the rare pairs in the band.
+#include <cooperative_groups.h>
+
 #include "pd_internal.h"
 
 namespace pd {
@@ -343,19 +345,32 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
     extern __shared__ unsigned long long skeys[];  // [cap_pow2] keys (small caps), cap bytes of flags, kept list
     __shared__ int n_cand;
     __shared__ int2 wkhk[PD_MAX_LEVELS];  // level sizes of this frame
-    const int f = blockIdx.x, tid = threadIdx.x;
+    __shared__ int s_ok, s_done, s_bx_smem;  // leader's state: candidates fit; walk over; boxes on chip
+    // A frame is one cluster of C CTAs (C = 1 without a cluster launch). Rank
+    // 0, the leader, collects, sorts, decodes, picks and resolves the batches
+    // exactly as a lone CTA would; every rank takes a 1/C share of each
+    // suppression pass, reading the leader's flags and boxes through
+    // distributed shared memory. All ranks pass the same cluster barriers:
+    // whether the walk goes on is read from the leader after a barrier.
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+    const bool leader = rank == 0;
+    const int f = blockIdx.x / C, tid = threadIdx.x;
     const FrameDesc fd = frames[f];
-    for (int k = tid; k < fd.n_levels; k += kThreads) {
-        const LevelDesc L = levels[fd.first_level + k];
-        wkhk[k] = make_int2(L.Wk, L.Hk);
-    }
     int cap_pow2 = 1;
     while (cap_pow2 < cap) cap_pow2 <<= 1;
     const bool big = cap > kMaxCandidates;
     float4 *gbx = scratch + (size_t)f * nms_scratch_float4s(cap);
     unsigned long long *keys = big ? reinterpret_cast<unsigned long long *>(gbx + cap) : skeys;
     uint8_t *supp = reinterpret_cast<uint8_t *>(big ? skeys : skeys + cap_pow2);
-
+    const float4 *bx = gbx;
+    const unsigned long long *ksrc = keys;
+    if (leader) {
+    for (int k = tid; k < fd.n_levels; k += kThreads) {
+        const LevelDesc L = levels[fd.first_level + k];
+        wkhk[k] = make_int2(L.Wk, L.Hk);
+    }
     if (tid == 0) n_cand = 0;
     __syncthreads();
     for (int k = 0; k < fd.n_levels; ++k) {
@@ -398,9 +413,9 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
         if (tid == 0) {
             counts[2 * f] = 0;
             counts[2 * f + 1] = -n;
+            s_ok = 0;
         }
-        return;
-    }
+    } else {
     int np = 1;
     while (np < n) np <<= 1;
     for (int i = n + tid; i < np; i += kThreads) keys[i] = ~0ull;
@@ -417,8 +432,6 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
     // keys then move to the global scratch, where only kept ones are read
     // again), otherwise in the global scratch. Each greedy pass reads every
     // remaining box, so keeping them on chip shortens every pass.
-    const float4 *bx;
-    const unsigned long long *ksrc;
     if (!big && 2 * n <= cap_pow2) {
         unsigned long long *gkeys = reinterpret_cast<unsigned long long *>(gbx);
         for (int i = tid; i < n; i += kThreads) gkeys[i] = keys[i];
@@ -438,7 +451,22 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
         bx = gbx;
         ksrc = keys;
     }
-    __syncthreads();
+    if (tid == 0) {
+        s_ok = 1;
+        s_bx_smem = bx != gbx;
+    }
+    }
+    }
+    cluster.sync();  // the leader's candidates, flags and boxes are in place
+    if (!(leader ? s_ok : *cluster.map_shared_rank(&s_ok, 0))) {
+        cluster.sync();  // nobody leaves while another rank reads its shared memory
+        return;
+    }
+    const int n = leader ? n_cand : *cluster.map_shared_rank(&n_cand, 0);
+    // the flags and the boxes of the walk: the leader's own, or read remotely
+    uint8_t *fl = leader ? supp : cluster.map_shared_rank(supp, 0);
+    if (!leader && *cluster.map_shared_rank(&s_bx_smem, 0))
+        bx = cluster.map_shared_rank(reinterpret_cast<float4 *>(keys), 0);
     // Greedy walk in batches. All threads find the next (up to) 64 candidates
     // not yet suppressed, in order (1024 positions per round), and copy their
     // boxes to shared memory; all threads compute the batch's pairwise
@@ -468,102 +496,117 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
     const int warp = tid >> 5, lane = tid & 31;
     const bool cull = iou_thr >= 0.5f;
     const float gsx = (float)kGrid / (float)fd.W, gsy = (float)kGrid / (float)fd.H;
-    if (tid == 0) {
+    if (tid == 0 && leader) {
         kept_total = 0;
         scan_pos = 0;
     }
     __syncthreads();
     while (true) {
-        // ---- the next batch: the first kBatch alive candidates at or after scan_pos
-        {
-            int cnt = 0, pos = scan_pos;
-            while (cnt < kBatch && pos < n) {
-                const int j = pos + tid;
-                const bool alive = j < n && !supp[j];
-                const unsigned m = __ballot_sync(0xffffffffu, alive);
-                if (lane == 0) wcnt[warp] = __popc(m);
-                __syncthreads();
-                int before = 0, total = 0;
+        if (leader) {
+            // ---- the next batch: the first kBatch alive candidates at or after scan_pos
+            {
+                int cnt = 0, pos = scan_pos;
+                while (cnt < kBatch && pos < n) {
+                    const int j = pos + tid;
+                    const bool alive = j < n && !fl[j];
+                    const unsigned m = __ballot_sync(0xffffffffu, alive);
+                    if (lane == 0) wcnt[warp] = __popc(m);
+                    __syncthreads();
+                    int before = 0, total = 0;
 #pragma unroll 8
-                for (int w = 0; w < kThreads / 32; ++w) {
-                    const int c = wcnt[w];
-                    before += w < warp ? c : 0;
-                    total += c;
+                    for (int w = 0; w < kThreads / 32; ++w) {
+                        const int c = wcnt[w];
+                        before += w < warp ? c : 0;
+                        total += c;
+                    }
+                    const int slot = cnt + before + __popc(m & ((1u << lane) - 1u));
+                    if (alive && slot < kBatch) {
+                        batch[slot] = j;
+                        bbx[slot] = bx[j];
+                        if (slot == kBatch - 1) scan_pos = j + 1;  // stop right after the last member
+                    }
+                    if (cnt + total < kBatch && tid == 0) scan_pos = min(pos + kThreads, n);
+                    cnt = min(cnt + total, kBatch);
+                    pos += kThreads;
+                    __syncthreads();  // wcnt reused by the next round; scan_pos, batch visible
                 }
-                const int rank = cnt + before + __popc(m & ((1u << lane) - 1u));
-                if (alive && rank < kBatch) {
-                    batch[rank] = j;
-                    bbx[rank] = bx[j];
-                    if (rank == kBatch - 1) scan_pos = j + 1;  // stop right after the last member
-                }
-                if (cnt + total < kBatch && tid == 0) scan_pos = min(pos + kThreads, n);
-                cnt = min(cnt + total, kBatch);
-                pos += kThreads;
-                __syncthreads();  // wcnt reused by the next round; scan_pos, batch visible
+                if (tid == 0) n_batch = cnt;
             }
-            if (tid == 0) n_batch = cnt;
-        }
-        __syncthreads();
-        const int nb = n_batch;
-        if (nb == 0) break;
-        {
-            // member b = tid / 16 is tested against members a = 4 (tid % 16) .. + 3
-            // (a < b); the 16 threads of a member OR their bits together
-            const int b = tid >> 4, a0 = (tid & 15) * 4;
-            unsigned long long bits = 0;
-            if (b < nb) {
-                const float4 bb = bbx[b];
+            __syncthreads();
+            const int nb = n_batch;
+            if (nb > 0) {
+                {
+                    // member b = tid / 16 is tested against members a = 4 (tid % 16) .. + 3
+                    // (a < b); the 16 threads of a member OR their bits together
+                    const int b = tid >> 4, a0 = (tid & 15) * 4;
+                    unsigned long long bits = 0;
+                    if (b < nb) {
+                        const float4 bb = bbx[b];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int a = a0 + q;
-                    if (a < b && suppresses(bbx[a], bb, iou_thr)) bits |= 1ull << a;
+                        for (int q = 0; q < 4; ++q) {
+                            const int a = a0 + q;
+                            if (a < b && suppresses(bbx[a], bb, iou_thr)) bits |= 1ull << a;
+                        }
+                    }
+#pragma unroll
+                    for (int o = 8; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
+                    if ((tid & 15) == 0 && b < kBatch) bcol[b] = bits;
+                }
+                __syncthreads();
+                if (warp == 0) {
+                    // Resolve in rounds: a member is dropped once a kept member
+                    // suppresses it, and kept once every member that could suppress it
+                    // is decided and none of them is kept. This reaches the in-order
+                    // result (induction on the member index) in as many rounds as the
+                    // longest chain of suppressions.
+                    const unsigned long long all = nb == 64 ? ~0ull : ((1ull << nb) - 1ull);
+                    const unsigned long long c0 = bcol[lane], c1 = bcol[lane + 32];
+                    unsigned long long keep = 0, decided = ~all;
+                    while (decided != ~0ull) {
+                        const bool k0 = !((decided >> lane) & 1ull) && !(c0 & keep) && !(c0 & ~decided);
+                        const bool d0 = k0 || (!((decided >> lane) & 1ull) && (c0 & keep));
+                        const bool k1 = !((decided >> (lane + 32)) & 1ull) && !(c1 & keep) && !(c1 & ~decided);
+                        const bool d1 = k1 || (!((decided >> (lane + 32)) & 1ull) && (c1 & keep));
+                        keep |= (unsigned long long)__ballot_sync(0xffffffffu, k0) |
+                                ((unsigned long long)__ballot_sync(0xffffffffu, k1) << 32);
+                        decided |= (unsigned long long)__ballot_sync(0xffffffffu, d0) |
+                                   ((unsigned long long)__ballot_sync(0xffffffffu, d1) << 32);
+                    }
+                    // the cap on kept boxes: only the first (max_boxes - kept so far) in order
+                    const int kt = kept_total;
+                    const int room = max_boxes - kt;
+                    while (__popcll(keep) > room) keep &= ~(1ull << (63 - __clzll(keep)));
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int m = lane + 32 * h;
+                        if (m < nb && ((keep >> m) & 1ull)) {
+                            const int r = __popcll(keep & ((1ull << m) - 1ull));
+                            kept_idx[kt + r] = batch[m];
+                            kbx[r] = bbx[m];
+                        }
+                    }
+                    if (lane == 0) {
+                        n_keep = __popcll(keep);
+                        kept_total = kt + __popcll(keep);
+                    }
                 }
             }
-#pragma unroll
-            for (int o = 8; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
-            if ((tid & 15) == 0 && b < kBatch) bcol[b] = bits;
+            __syncthreads();
+            if (tid == 0) s_done = nb == 0 || kept_total >= max_boxes;
         }
-        __syncthreads();
-        if (warp == 0) {
-            // Resolve in rounds: a member is dropped once a kept member
-            // suppresses it, and kept once every member that could suppress it
-            // is decided and none of them is kept. This reaches the in-order
-            // result (induction on the member index) in as many rounds as the
-            // longest chain of suppressions.
-            const unsigned long long all = nb == 64 ? ~0ull : ((1ull << nb) - 1ull);
-            const unsigned long long c0 = bcol[lane], c1 = bcol[lane + 32];
-            unsigned long long keep = 0, decided = ~all;
-            while (decided != ~0ull) {
-                const bool k0 = !((decided >> lane) & 1ull) && !(c0 & keep) && !(c0 & ~decided);
-                const bool d0 = k0 || (!((decided >> lane) & 1ull) && (c0 & keep));
-                const bool k1 = !((decided >> (lane + 32)) & 1ull) && !(c1 & keep) && !(c1 & ~decided);
-                const bool d1 = k1 || (!((decided >> (lane + 32)) & 1ull) && (c1 & keep));
-                keep |= (unsigned long long)__ballot_sync(0xffffffffu, k0) |
-                        ((unsigned long long)__ballot_sync(0xffffffffu, k1) << 32);
-                decided |= (unsigned long long)__ballot_sync(0xffffffffu, d0) |
-                           ((unsigned long long)__ballot_sync(0xffffffffu, d1) << 32);
-            }
-            // the cap on kept boxes: only the first (max_boxes - kept so far) in order
-            const int kt = kept_total;
-            const int room = max_boxes - kt;
-            while (__popcll(keep) > room) keep &= ~(1ull << (63 - __clzll(keep)));
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int m = lane + 32 * h;
-                if (m < nb && ((keep >> m) & 1ull)) {
-                    const int r = __popcll(keep & ((1ull << m) - 1ull));
-                    kept_idx[kt + r] = batch[m];
-                    kbx[r] = bbx[m];
-                }
-            }
-            if (lane == 0) {
-                n_keep = __popcll(keep);
-                kept_total = kt + __popcll(keep);
-            }
+        cluster.sync();  // the batch is resolved (or the walk is over)
+        if (leader ? s_done : *cluster.map_shared_rank(&s_done, 0)) break;
+        int nk, sp;
+        if (leader) {
+            nk = n_keep;
+            sp = scan_pos;
+        } else {  // the kept boxes of the batch and the scan start, from the leader
+            nk = *cluster.map_shared_rank(&n_keep, 0);
+            sp = *cluster.map_shared_rank(&scan_pos, 0);
+            const float4 *lk = cluster.map_shared_rank(kbx, 0);
+            for (int k = tid; k < nk; k += kThreads) kbx[k] = lk[k];
+            __syncthreads();
         }
-        __syncthreads();
-        if (kept_total >= max_boxes) break;
-        const int nk = n_keep;
         if (cull) {
             // grid cells under each kept box, with one cell of margin; then per
             // cell (one per thread) the set of kept boxes that cover it
@@ -584,13 +627,13 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
             cmask[tid] = m;
             __syncthreads();
         }
-        int j = scan_pos + tid;
+        int j = sp + rank * kThreads + tid;  // this rank's share: every C-th run of kThreads
         float4 bnext = j < n ? bx[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-        for (; j < n; j += kThreads) {
+        for (; j < n; j += C * kThreads) {
             // the next box is loaded while this one is tested (global for large caps)
             const float4 bj = bnext;
-            if (j + kThreads < n) bnext = bx[j + kThreads];
-            if (supp[j]) continue;
+            if (j + C * kThreads < n) bnext = bx[j + C * kThreads];
+            if (fl[j]) continue;
             bool hit = false;
             if (cull) {
                 // only the kept boxes that cover the centre's cell can suppress it
@@ -612,10 +655,12 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
                     hit = h0 || h1 || h2 || h3;
                 }
             }
-            if (hit) supp[j] = 1;
+            if (hit) fl[j] = 1;
         }
-        __syncthreads();
+        cluster.sync();  // every rank's share of the pass is done
     }
+    cluster.sync();  // nobody leaves while another rank reads its shared memory
+    if (!leader) return;
     const int kept = kept_total;
     pd_box *out = boxes + (size_t)f * max_boxes;
     for (int k = tid; k < kept; k += kThreads) {
@@ -653,21 +698,73 @@ size_t nms_smem(int cap, int max_boxes) {
 
 }  // namespace
 
+namespace {
+int g_nms_max_cluster = 1;  // largest cluster of k_nms CTAs the device can hold (1, 2, 4 or 8)
+}  // namespace
+
 cudaError_t init_nms() {
-    return cudaFuncSetAttribute(k_nms, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)nms_smem(kMaxCandidates, kMaxBoxes));
+    const int smem = (int)nms_smem(kMaxCandidates, kMaxBoxes);
+    const cudaError_t e = cudaFuncSetAttribute(k_nms, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    g_nms_max_cluster = 1;
+    for (int c = 8; c >= 2; c >>= 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(c);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = (size_t)smem;
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = c;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_nms, &cfg) == cudaSuccess && n > 0) {
+            g_nms_max_cluster = c;
+            break;
+        }
+        (void)cudaGetLastError();  // a refused size is not an error: try a smaller one
+    }
+    return cudaSuccess;
+}
+
+int nms_cluster_for(int n_frames, int sm_count) {
+    // the CTAs of a frame share its suppression passes; only while every CTA
+    // still gets an SM of its own (one 1024-thread CTA per SM)
+    int c = 1;
+    while (2 * c <= g_nms_max_cluster && (int64_t)n_frames * 2 * c <= sm_count) c *= 2;
+    return c;
 }
 
 cudaError_t launch_nms(cudaStream_t s, const FrameDesc *d_frames, const LevelDesc *d_levels,
                        int n_frames, const float *scores, float threshold, float iou,
                        float4 *scratch, int max_cand, pd_box *boxes, int max_boxes,
-                       int32_t *counts) {
+                       int32_t *counts, int cluster) {
     if (n_frames <= 0) return cudaSuccess;
-    if (max_cand < 1 || max_cand > kMaxCandidatesBig || max_boxes < 1 || max_boxes > kMaxBoxes)
+    if (max_cand < 1 || max_cand > kMaxCandidatesBig || max_boxes < 1 || max_boxes > kMaxBoxes ||
+        cluster < 1 || cluster > 8 || (cluster & (cluster - 1)))
         return cudaErrorInvalidValue;
-    k_nms<<<n_frames, kThreads, nms_smem(max_cand, max_boxes), s>>>(d_frames, d_levels, scores, threshold, iou,
-                                                         max_cand, scratch, boxes, max_boxes, counts);
-    return cudaGetLastError();
+    const size_t smem = nms_smem(max_cand, max_boxes);
+    if (cluster == 1) {
+        k_nms<<<n_frames, kThreads, smem, s>>>(d_frames, d_levels, scores, threshold, iou, max_cand, scratch,
+                                               boxes, max_boxes, counts);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_frames * cluster);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = cluster;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_nms, d_frames, d_levels, scores, threshold, iou, max_cand, scratch, boxes,
+                              max_boxes, counts);
 }
 
 // ---------------------------------------------------------------------------

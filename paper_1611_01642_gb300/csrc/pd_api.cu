@@ -1114,7 +1114,7 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
         if (timed) PD_CUDA(h, record(h->stage_ev[3], q));
         PD_CUDA(h, launch_nms(q, df, dl, n_frames, h->d_scores, h->p.threshold, h->p.nms_iou,
                               h->d_nms_scratch, h->p.max_candidates_per_frame, h->m_boxes,
-                              h->p.max_boxes_per_frame, h->m_counts));
+                              h->p.max_boxes_per_frame, h->m_counts, nms_cluster_for(n_frames, h->sm_count)));
         if (timed) PD_CUDA(h, record(h->stage_ev[4], q));
         return PD_OK;
     };
@@ -1635,7 +1635,7 @@ int pd_nms_maps(pd_handle *h, void *stream, const float *d_scores, int n_levels,
     if (r != PD_OK) return r;
     PD_CUDA(h, launch_nms(s, dptr<FrameDesc>(h, o.frames), dptr<LevelDesc>(h, o.levels), 1, d_scores,
                           h->p.threshold, h->p.nms_iou, h->d_nms_scratch, h->p.max_candidates_per_frame,
-                          d_boxes, max_boxes, d_counts));
+                          d_boxes, max_boxes, d_counts, nms_cluster_for(1, h->sm_count)));
     return PD_OK;
 }
 

@@ -151,10 +151,13 @@ __host__ __device__ inline size_t nms_scratch_float4s(int cap) {
     while (p < (size_t)cap) p <<= 1;
     return cap > 16384 ? (size_t)cap + p / 2 : (size_t)cap;
 }
+// cluster: CTAs per frame (1, 2, 4 or 8; a thread-block cluster that shares
+// the frame's suppression passes); nms_cluster_for picks it for a batch.
 cudaError_t launch_nms(cudaStream_t s, const FrameDesc *d_frames, const LevelDesc *d_levels,
                        int n_frames, const float *scores, float threshold, float iou,
                        float4 *scratch, int max_cand, pd_box *boxes, int max_boxes,
-                       int32_t *counts);
+                       int32_t *counts, int cluster = 1);
+int nms_cluster_for(int n_frames, int sm_count);
 
 // ---- the paper's kernel schemes (comparison with the fused kernels)
 size_t scheme_cells_scratch(int Wk, int Hk);
