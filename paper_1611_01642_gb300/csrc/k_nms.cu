@@ -283,23 +283,29 @@ __device__ __forceinline__ void bitonic_sort_smem(unsigned long long *k, int m, 
 }
 
 // Large caps: keys[0, np) (np a power of two >= n, padded with ~0) sorted
-// ascending: chunks of up to kSortChunk keys sorted in shared memory `sm`,
-// then merge passes doubling the run length, ping-ponging through `tmp`
-// (np keys); the result ends in keys.
-__device__ void sort_large(unsigned long long *keys, unsigned long long *tmp, int np,
-                           unsigned long long *sm, int tid) {
+// ascending by the nr CTAs of a frame's cluster (rank = this CTA): chunks of
+// up to kSortChunk keys sorted in each CTA's shared memory `sm` (chunk c by
+// rank c mod nr), then merge passes doubling the run length, ping-ponging
+// through `tmp` (np keys), each of the nr * kThreads threads merging its
+// slice of the output; the result ends in keys. csync is the cluster-wide
+// barrier (the keys are in global memory).
+template <class Sync>
+__device__ void sort_large(unsigned long long *keys, unsigned long long *tmp, int np, unsigned long long *sm,
+                           int tid, int rank, int nr, Sync &&csync) {
     const int C = np < kSortChunk ? np : kSortChunk;
-    for (int c0 = 0; c0 < np; c0 += C) {
+    for (int c0 = rank * C; c0 < np; c0 += nr * C) {
         for (int i = tid; i < C; i += kThreads) sm[i] = keys[c0 + i];
         __syncthreads();
         bitonic_sort_smem(sm, C, tid);
         for (int i = tid; i < C; i += kThreads) keys[c0 + i] = sm[i];
         __syncthreads();
     }
+    csync();
     unsigned long long *src = keys, *dst = tmp;
-    const int per = np / kThreads;  // outputs per thread (np >= 2 C here, so per divides every pair)
+    const int g = rank * kThreads + tid;
+    const int per = np / (nr * kThreads);  // outputs per thread (np >= 2 C here, so per divides every pair)
     for (int w = C; w < np; w <<= 1) {
-        const int o0 = tid * per;
+        const int o0 = g * per;
         const int base = o0 & ~(2 * w - 1), d = o0 - base;
         const unsigned long long *A = src + base, *B = src + base + w;
         // i = keys taken from A among the pair's first d outputs (A first on ties)
@@ -325,14 +331,14 @@ __device__ void sort_large(unsigned long long *keys, unsigned long long *tmp, in
                 b = j < w ? B[j] : ~0ull;
             }
         }
-        __syncthreads();
+        csync();
         unsigned long long *t = src;
         src = dst;
         dst = t;
     }
     if (src != keys) {
-        for (int i = tid; i < np; i += kThreads) keys[i] = src[i];
-        __syncthreads();
+        for (int i = g; i < np; i += nr * kThreads) keys[i] = src[i];
+        csync();
     }
 }
 
@@ -345,13 +351,15 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
     extern __shared__ unsigned long long skeys[];  // [cap_pow2] keys (small caps), cap bytes of flags, kept list
     __shared__ int n_cand;
     __shared__ int2 wkhk[PD_MAX_LEVELS];  // level sizes of this frame
-    __shared__ int s_ok, s_done, s_bx_smem;  // leader's state: candidates fit; walk over; boxes on chip
-    // A frame is one cluster of C CTAs (C = 1 without a cluster launch). Rank
-    // 0, the leader, collects, sorts, decodes, picks and resolves the batches
-    // exactly as a lone CTA would; every rank takes a 1/C share of each
-    // suppression pass, reading the leader's flags and boxes through
-    // distributed shared memory. All ranks pass the same cluster barriers:
-    // whether the walk goes on is read from the leader after a barrier.
+    __shared__ int s_done, s_bx_smem;  // leader's state: walk over; boxes on chip
+    // A frame is one cluster of C CTAs (C = 1 without a cluster launch). Every
+    // rank collects a share of the frame's candidates into the leader's list;
+    // with large caps (keys in global memory) every rank also sorts and
+    // decodes a share. Rank 0, the leader, sorts small lists and picks and
+    // resolves the batches exactly as a lone CTA would; every rank takes a
+    // 1/C share of each suppression pass, reading the leader's flags and
+    // boxes through distributed shared memory. All ranks pass the same
+    // cluster barriers: what comes next is read from the leader after one.
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     const int C = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
@@ -366,103 +374,109 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
     uint8_t *supp = reinterpret_cast<uint8_t *>(big ? skeys : skeys + cap_pow2);
     const float4 *bx = gbx;
     const unsigned long long *ksrc = keys;
-    if (leader) {
     for (int k = tid; k < fd.n_levels; k += kThreads) {
         const LevelDesc L = levels[fd.first_level + k];
         wkhk[k] = make_int2(L.Wk, L.Hk);
     }
-    if (tid == 0) n_cand = 0;
-    __syncthreads();
-    for (int k = 0; k < fd.n_levels; ++k) {
-        const LevelDesc L = levels[fd.first_level + k];
-        const int n = L.rows * L.cols;
-        const float *sc = scores + L.score_off;
-        // warp-aggregated appends; kUnroll independent loads per thread are in
-        // flight before any of them is used (the scan is latency-bound otherwise)
-        constexpr int kUnroll = 8;
-        for (int i0 = 0; i0 < n; i0 += kThreads * kUnroll) {
-            float sv[kUnroll];
+    if (tid == 0 && leader) n_cand = 0;
+    cluster.sync();  // the leader's counter is zero
+    {
+        // every rank scans its share of the windows (every C-th run of
+        // kThreads * kUnroll of a level) and appends to the leader's list
+        int *cnt = leader ? &n_cand : cluster.map_shared_rank(&n_cand, 0);
+        unsigned long long *kw = big ? keys : leader ? skeys : cluster.map_shared_rank(skeys, 0);
+        for (int k = 0; k < fd.n_levels; ++k) {
+            const LevelDesc L = levels[fd.first_level + k];
+            const int n = L.rows * L.cols;
+            const float *sc = scores + L.score_off;
+            // warp-aggregated appends; kUnroll independent loads per thread are in
+            // flight before any of them is used (the scan is latency-bound otherwise)
+            constexpr int kUnroll = 8;
+            for (int i0 = rank * kThreads * kUnroll; i0 < n; i0 += C * kThreads * kUnroll) {
+                float sv[kUnroll];
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const int i = i0 + u * kThreads + tid;
-                sv[u] = i < n ? __ldg(sc + i) : 0.f;
-            }
+                for (int u = 0; u < kUnroll; ++u) {
+                    const int i = i0 + u * kThreads + tid;
+                    sv[u] = i < n ? __ldg(sc + i) : 0.f;
+                }
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const int i = i0 + u * kThreads + tid;
-                if (i0 + u * kThreads >= n) break;  // block-uniform
-                const float s = sv[u];
-                const bool hit = i < n && s > threshold;
-                const unsigned m = __ballot_sync(0xffffffffu, hit);
-                int base = 0;
-                if ((tid & 31) == 0 && m) base = atomicAdd(&n_cand, __popc(m));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (hit) {
-                    const int idx = base + __popc(m & ((1u << (tid & 31)) - 1u));
-                    if (idx < cap) {
-                        const int wy = i / L.cols;
-                        keys[idx] = make_key(s, k, wy, i - wy * L.cols);
+                for (int u = 0; u < kUnroll; ++u) {
+                    const int i = i0 + u * kThreads + tid;
+                    if (i0 + u * kThreads >= n) break;  // block-uniform
+                    const float s = sv[u];
+                    const bool hit = i < n && s > threshold;
+                    const unsigned m = __ballot_sync(0xffffffffu, hit);
+                    int base = 0;
+                    if ((tid & 31) == 0 && m) base = atomicAdd(cnt, __popc(m));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (hit) {
+                        const int idx = base + __popc(m & ((1u << (tid & 31)) - 1u));
+                        if (idx < cap) {
+                            const int wy = i / L.cols;
+                            kw[idx] = make_key(s, k, wy, i - wy * L.cols);
+                        }
                     }
                 }
             }
         }
     }
-    __syncthreads();
-    const int n = n_cand;
+    cluster.sync();  // every rank's candidates are in
+    const int n = leader ? n_cand : *cluster.map_shared_rank(&n_cand, 0);
     if (n > cap) {
-        if (tid == 0) {
+        if (leader && tid == 0) {
             counts[2 * f] = 0;
             counts[2 * f + 1] = -n;
-            s_ok = 0;
         }
-    } else {
-    int np = 1;
-    while (np < n) np <<= 1;
-    for (int i = n + tid; i < np; i += kThreads) keys[i] = ~0ull;
-    __syncthreads();
-    if (big) {
-        // the boxes region (cap float4s) is free until the decode below
-        sort_large(keys, reinterpret_cast<unsigned long long *>(gbx), np, skeys, tid);
-    } else {
-        bitonic_sort_smem(keys, np, tid);
-    }
-    for (int i = tid; i < n; i += kThreads) supp[i] = 0;
-    __syncthreads();
-    // Decoded boxes: in shared memory when they fit in the key region (the
-    // keys then move to the global scratch, where only kept ones are read
-    // again), otherwise in the global scratch. Each greedy pass reads every
-    // remaining box, so keeping them on chip shortens every pass.
-    if (!big && 2 * n <= cap_pow2) {
-        unsigned long long *gkeys = reinterpret_cast<unsigned long long *>(gbx);
-        for (int i = tid; i < n; i += kThreads) gkeys[i] = keys[i];
-        __syncthreads();
-        float4 *sbx = reinterpret_cast<float4 *>(keys);
-        for (int i = tid; i < n; i += kThreads) {  // each thread re-reads only its own writes
-            const pd_box b = decode(gkeys[i], fd.W, fd.H, wkhk);
-            sbx[i] = make_float4(b.x, b.y, b.w, b.h);
-        }
-        bx = sbx;
-        ksrc = gkeys;
-    } else {
-        for (int i = tid; i < n; i += kThreads) {
-            const pd_box b = decode(keys[i], fd.W, fd.H, wkhk);
-            gbx[i] = make_float4(b.x, b.y, b.w, b.h);
-        }
-        bx = gbx;
-        ksrc = keys;
-    }
-    if (tid == 0) {
-        s_ok = 1;
-        s_bx_smem = bx != gbx;
-    }
-    }
-    }
-    cluster.sync();  // the leader's candidates, flags and boxes are in place
-    if (!(leader ? s_ok : *cluster.map_shared_rank(&s_ok, 0))) {
         cluster.sync();  // nobody leaves while another rank reads its shared memory
         return;
     }
-    const int n = leader ? n_cand : *cluster.map_shared_rank(&n_cand, 0);
+    int np = 1;
+    while (np < n) np <<= 1;
+    if (big) {
+        // keys and boxes in global memory: every rank sorts and decodes a share
+        for (int i = n + rank * kThreads + tid; i < np; i += C * kThreads) keys[i] = ~0ull;
+        cluster.sync();
+        // the boxes region (cap float4s) is free until the decode below
+        sort_large(keys, reinterpret_cast<unsigned long long *>(gbx), np, skeys, tid, rank, C,
+                   [&] { cluster.sync(); });
+        for (int i = rank * kThreads + tid; i < n; i += C * kThreads) {
+            const pd_box b = decode(keys[i], fd.W, fd.H, wkhk);
+            gbx[i] = make_float4(b.x, b.y, b.w, b.h);
+        }
+        if (leader) {
+            for (int i = tid; i < n; i += kThreads) supp[i] = 0;
+            if (tid == 0) s_bx_smem = 0;
+        }
+    } else if (leader) {
+        for (int i = n + tid; i < np; i += kThreads) keys[i] = ~0ull;
+        __syncthreads();
+        bitonic_sort_smem(keys, np, tid);
+        for (int i = tid; i < n; i += kThreads) supp[i] = 0;
+        __syncthreads();
+        // Decoded boxes: in shared memory when they fit in the key region (the
+        // keys then move to the global scratch, where only kept ones are read
+        // again), otherwise in the global scratch. Each greedy pass reads every
+        // remaining box, so keeping them on chip shortens every pass.
+        if (2 * n <= cap_pow2) {
+            unsigned long long *gkeys = reinterpret_cast<unsigned long long *>(gbx);
+            for (int i = tid; i < n; i += kThreads) gkeys[i] = keys[i];
+            __syncthreads();
+            float4 *sbx = reinterpret_cast<float4 *>(keys);
+            for (int i = tid; i < n; i += kThreads) {  // each thread re-reads only its own writes
+                const pd_box b = decode(gkeys[i], fd.W, fd.H, wkhk);
+                sbx[i] = make_float4(b.x, b.y, b.w, b.h);
+            }
+            bx = sbx;
+            ksrc = gkeys;
+        } else {
+            for (int i = tid; i < n; i += kThreads) {
+                const pd_box b = decode(keys[i], fd.W, fd.H, wkhk);
+                gbx[i] = make_float4(b.x, b.y, b.w, b.h);
+            }
+        }
+        if (tid == 0) s_bx_smem = bx != gbx;
+    }
+    cluster.sync();  // the leader's candidates, flags and boxes are in place
     // the flags and the boxes of the walk: the leader's own, or read remotely
     uint8_t *fl = leader ? supp : cluster.map_shared_rank(supp, 0);
     if (!leader && *cluster.map_shared_rank(&s_bx_smem, 0))
