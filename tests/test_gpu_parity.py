@@ -505,3 +505,33 @@ def test_repeated_batch_shape_replays_graph_with_new_frames(template):
                 assert np.array_equal(f.boxes(i), boxes[i])
         finally:
             f.close()
+
+
+def test_results_do_not_depend_on_batch_size(template):
+    """The batch size sets the launch shapes: the cells kernel's strip height
+    (2 to 32 cell rows) and the CTAs per frame of the NMS cluster (8, 4, 2, 1
+    on a 152-SM GPU). Frame 0's score maps and boxes must not change."""
+    from paper_1611_01642_gb300 import build as bld
+    bld.build()
+    w, b = template
+    n_max = 128
+    imgs = [synth.make_scene(1242, 375, 2, i) for i in range(n_max)]
+    d = pd.Detector(w, b, pyr_factor=float(np.float32(1.05)), max_frames=n_max, max_width=1242, max_height=375)
+    try:
+        frames = [torch.from_numpy(im).cuda() for im in imgs]
+        ref_maps = ref_boxes = None
+        for n in (1, 20, 40, n_max):
+            d.detect(frames[:n])
+            assert d.sync() == pd.PD_OK, pd.pd_last_error(d.h)
+            maps = [m.clone() for m in d.score_maps(0)]
+            boxes = d.boxes(0)
+            if ref_maps is None:
+                ref_maps, ref_boxes = maps, boxes
+                assert len(ref_boxes) > 0
+                continue
+            assert len(maps) == len(ref_maps)
+            for a, r in zip(maps, ref_maps):
+                assert torch.equal(a, r), n
+            assert np.array_equal(boxes, ref_boxes), n
+    finally:
+        d.close()
