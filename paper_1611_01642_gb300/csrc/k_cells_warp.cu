@@ -2,29 +2,33 @@
 // (Section 4.2, Algorithms 1-2; Section 4.3, Algorithms 4-5), one warp per
 // strip of cells, four pixel columns per lane.
 //
-// A strip is 15 cells wide and up to kStripTiles cell tiles (8 cell rows
-// each) tall (the planner takes shorter strips for small batches). Its warp walks the 128 pixel columns [8 cx0 - 4, 8 cx0 + 124)
-// (the strip and the 4 columns on each side whose HOG votes still reach it):
-// lane t owns columns 8 cx0 - 4 + 4t .. + 3, which lie in one cell (strip
-// cell (t - 1) / 2; lanes 0 and 31 lie in the neighbouring strips). The warp
-// walks the pixel rows from the top in bands of 8: band k covers the rows
-// [8 (cy0 + k) - 4, 8 (cy0 + k) + 4), which vote only into cell rows
-// cy0 + k - 1 and cy0 + k, so after band k cell row cy0 + k - 1 is final and
-// the warp writes it out. The warps of a CTA never wait for each other, and
-// a tall strip walks the 4-row vertical halo of a band only once per strip.
+// Persistent warps (4 per CTA, independent of each other) take strips from a
+// queue, tallest first. A strip is 15 cells wide and up to kStripTiles cell
+// tiles (8 cell rows each) tall; the planner takes shorter strips, down to 2
+// cell rows, when a batch is small. Its warp walks the 128 pixel columns
+// [8 cx0 - 4, 8 cx0 + 124) (the strip and the 4 columns on each side whose
+// HOG votes still reach it): lane t owns columns 8 cx0 - 4 + 4t .. + 3, which
+// lie in one cell (strip cell (t - 1) / 2; lanes 0 and 31 lie in the
+// neighbouring strips). The warp walks the pixel rows from the top in bands
+// of 8: band k covers the rows [8 (cy0 + k) - 4, 8 (cy0 + k) + 4), which vote
+// only into cell rows cy0 + k - 1 and cy0 + k, so after band k cell row
+// cy0 + k - 1 is final and the warp writes it out. A tall strip walks the
+// 4-row vertical halo of a band once per strip.
 //
 // Per row a lane loads three aligned 32-bit words of the level row (its own
 // 4 bytes and its neighbours'; byte loads clamped to the level at its left
-// and right edges) and keeps the rows above and below in registers. For its
-// 4 pixels:
+// and right edges), one row pair ahead, and keeps the rows above and below
+// in registers. For its 4 pixels:
 //  * LBP (Algorithm 1) on packed bytes. For bytes n, c: n >= c exactly when
 //    the subtraction n - c does not borrow out of bit 7, which is the
 //    majority of (n7, not c7, bit 7 of (n | 0x80) - (c & 0x7f)); one
 //    subtraction and one 3-input logic operation compare 4 pixels with one
 //    neighbour, and the 8 comparison words fold into 4 codes. A 256-entry
 //    table gives each code's uniform bin as an 8-bit counter of a word of the
-//    cell's counts (shared-memory integer atomics, exact and order
-//    independent; counts <= 64; Algorithm 2).
+//    lane's own counters ([word][lane] layout: the shared-memory atomics never
+//    collide; exact and order independent; Algorithm 2). A cell's counts are
+//    the sum of its two lanes' counters (each <= 32), written out after the
+//    band's first 4 rows, which complete cell row cy0 + k - 1.
 //  * HOG (Algorithm 4). One byte permute and two dp2a (weights +1, -1) give
 //    the central differences of two pixels; the accumulator 0x4B400000 makes
 //    the 32-bit result the float 1.5 * 2^23 + g, so one subtraction turns it
@@ -43,14 +47,17 @@
 //    wrap), which the epilogue folds back: the loop needs no wrap logic.
 //    The slots of lane t's 4 columns sit at 4t + (j ^ ((t >> 3) & 3)), so
 //    that a warp's data-dependent scatter hits 32 distinct banks and the
-//    epilogue reads them with one 16-byte load.
-// Epilogue of cell row r: each lane forms, per bin, the weighted sums of its
-// 4 columns for its own cell and for the neighbouring cell they reach; three
-// shuffles add the 4 lanes that reach a cell (fixed order: deterministic).
-// The LBP counts go out bin-plane by bin-plane, one byte per cell, lanes on
-// consecutive cells (coalesced). At the top and bottom of a level the votes
-// of the clamped cell row (Algorithm 5's interpolation clamped into the
-// grid) are added into the first and last row before they are written.
+//    epilogue reads them with one 16-byte load. Rows outside the cell grid
+//    vote with weight 0 and count nothing (no branch).
+// HOG epilogue of cell row r: each lane forms, per bin, the weighted sums of
+// its 4 columns for its own cell and for the neighbouring cell they reach;
+// three shuffles add the 4 lanes that reach a cell (fixed order:
+// deterministic). The LBP counts go out bin-plane by bin-plane, one byte per
+// cell, lanes on consecutive cells (coalesced). At the top and bottom of a
+// level the votes of the clamped cell row (Algorithm 5's interpolation
+// clamped into the grid) are added into the first and last row before they
+// are written. The result does not depend on the strip height: every cell
+// row sums its votes in the same order.
 //
 // Sparse path: c_flag marks the 15 x 8-cell tiles to compute; a band is
 // walked when one of its two cell rows lies in a marked tile, and a cell
