@@ -31,20 +31,26 @@
 //    band's first 4 rows, which complete cell row cy0 + k - 1.
 //  * HOG (Algorithm 4). One byte permute and two dp2a (weights +1, -1) give
 //    the central differences of two pixels; the accumulator 0x4B400000 makes
-//    the 32-bit result the float 1.5 * 2^23 + g, so one subtraction turns it
-//    into g. Magnitude sqrt(gx^2 + gy^2); unsigned orientation in bin units
-//    (degrees / 20) from the octant reduction z = min / max in [0, 1] and an
-//    odd polynomial z P(z^2) of degree 13 fitted to atan on [0, 1] (weighted
+//    the 32-bit result the float 1.5 * 2^23 + g, so one multiply-add turns it
+//    into g / 2 (exact). Magnitude sqrt(gx^2 + gy^2); unsigned orientation in
+//    bin units (degrees / 20): the angle phi of (|gx|, |gy|) is 45 degrees +
+//    atan(t) with t = (|gy| - |gx|) / (|gy| + |gx|) in [-1, 1], where an odd
+//    polynomial t P(t^2) of degree 13 fitted to atan on [0, 1] (weighted
 //    least squares on Chebyshev nodes, scaled to bin units; error < 1e-6
-//    bin). The vote is linear between the two nearest of the 9 bins and
-//    between the two cell rows of the band (weights (7.5 - k) / 8 and
-//    (k + 0.5) / 8 for band row k), and bilinear on x through the columns'
-//    weights in the epilogue. floor(theta / 20deg - 0.5) comes from rounding
-//    theta - 1 by adding 1.5 * 2^23 (a tie gives the other neighbour with
-//    weight 1, the same votes); the float's bits are the bin number plus a
-//    constant, so they index the column's vote slots directly. There are 11
-//    slots per column, slot s holding bin (s - 1) mod 9 (bin -1 and bin 9
-//    wrap), which the epilogue folds back: the loop needs no wrap logic.
+//    bin) holds; theta is phi or 180 degrees - phi as the signs of gx and gy
+//    agree or not (one sign flip, no branch). The vote is linear between the
+//    two nearest of the 9 bins and between the two cell rows of the band
+//    (weights (7.5 - k) / 8 and (k + 0.5) / 8 for band row k), and bilinear
+//    on x through the columns' weights in the epilogue.
+//    floor(theta / 20deg - 0.5) comes from rounding 2 (theta - 1) to an even
+//    integer by adding 3 * 2^23, where floats are spaced by 2 (a tie gives
+//    the other neighbour with weight 1, the same votes); the residual e in
+//    [-1, 1] gives the lower and upper bins' weights (1 - e) / 2 and
+//    (1 + e) / 2 with one multiply-add each, and the float's bits are the
+//    bin number plus a constant, so they index the column's vote slots
+//    directly. There are 11 slots per column, slot s holding bin
+//    (s - 1) mod 9 (bin -1 and bin 9 wrap), which the epilogue folds back:
+//    the loop needs no wrap logic.
 //    The slots of lane t's 4 columns sit at 4t + (j ^ ((t >> 3) & 3)), so
 //    that a warp's data-dependent scatter hits 32 distinct banks and the
 //    epilogue reads them with one 16-byte load. Rows outside the cell grid
@@ -78,8 +84,10 @@ constexpr int kSlots = kHogBins + 2;             // vote slots per column (bins 
 constexpr int kRingStride = kSlots * kSCols;     // floats per open cell row
 constexpr int kCntWords = (kLbpBins + 3) / 4;    // words of four 8-bit counters per cell
 constexpr uint32_t kHi = 0x80808080u;
-constexpr float kMagic = 12582912.0f;            // 1.5 * 2^23
+constexpr float kMagic = 12582912.0f;            // 1.5 * 2^23: dp2a accumulator
 constexpr uint32_t kMagicBits = 0x4B400000u;
+constexpr float kMagic2 = 25165824.0f;           // 3 * 2^23 (spacing 2): rounds to even integers
+constexpr uint32_t kMagic2Bits = 0x4BC00000u;
 
 struct WarpSmem {
     float R[2 * kRingStride];       // HOG vote slots of the 2 open cell rows
@@ -121,16 +129,17 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
-// atan(z) * 9/pi / z as a polynomial in s = z^2 (z in [0, 1]): the fitted
-// coefficients scaled to 20-degree bins.
-__device__ __forceinline__ float atan_bins_poly(float s) {
-    float p = 0.019514326006174088f;
-    p = fmaf(p, s, -0.09626893699169159f);
-    p = fmaf(p, s, 0.22810496389865875f);
-    p = fmaf(p, s, -0.3791072964668274f);
-    p = fmaf(p, s, 0.5674521327018738f);
-    p = fmaf(p, s, -0.9544723033905029f);
-    return fmaf(p, s, 2.8647778034210205f);
+// 2 atan(z) * 9/pi / z as a polynomial in s = z^2 (|z| <= 1): the fitted
+// coefficients scaled to 20-degree bins and doubled (exact: every step of
+// the evaluation scales by 2).
+__device__ __forceinline__ float atan_bins2_poly(float s) {
+    float p = 2.0f * 0.019514326006174088f;
+    p = fmaf(p, s, 2.0f * -0.09626893699169159f);
+    p = fmaf(p, s, 2.0f * 0.22810496389865875f);
+    p = fmaf(p, s, 2.0f * -0.3791072964668274f);
+    p = fmaf(p, s, 2.0f * 0.5674521327018738f);
+    p = fmaf(p, s, 2.0f * -0.9544723033905029f);
+    return fmaf(p, s, 2.0f * 2.8647778034210205f);
 }
 
 template <class F, int... I>
@@ -189,7 +198,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
         // float index of slot 0 of pixel j's column, less the bias of the rounded angle's bits
         uint32_t vb[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) vb[j] = (uint32_t)(4 * lane + (j ^ sw)) + 128u - kMagicBits * 128u;
+        for (int j = 0; j < 4; ++j) vb[j] = (uint32_t)(4 * lane + (j ^ sw)) + 128u - kMagic2Bits * 128u;
         // epilogue x-weights by slot position p (column j = p ^ sw): own cell, neighbour cell
         float wo[4], wn[4];
         {
@@ -258,29 +267,30 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
                                     dp2a_diff_lo(Q23, (int)kMagicBits), dp2a_diff_hi(Q23, (int)kMagicBits)};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const float fx = __int_as_float(gxb[j]) - kMagic, fy = __int_as_float(gyb[j]) - kMagic;
-                    const float mag = sqrt_approx(fmaf(fx, fx, fy * fy));
-                    const float ax = fabsf(fx), ay = fabsf(fy);
-                    // mx is 0 or >= 1: the 1e-30 only turns 0 / 0 into 0
-                    const float z = fminf(ax, ay) * rcp_approx(fmaxf(ax, ay) + 1e-30f);
-                    const float pz = atan_bins_poly(z * z);
-                    // theta = phi, 4.5 - phi (steep), 9 - phi (opposite signs), 4.5 + phi (both);
-                    // the vote position is theta - 0.5, rounded below through theta - 1
-                    const bool steep = ay > ax;
-                    const bool mirror = (int)(__float_as_uint(fx) ^ __float_as_uint(fy)) < 0;
-                    const float zs = (steep != mirror) ? -z : z;
-                    const float off = steep ? 3.5f : (mirror ? 8.0f : -1.0f);
-                    const float tm1 = fmaf(pz, zs, off);
-                    const float t = tm1 + kMagic;
-                    const float o1 = (tm1 + 0.5f) - (t - kMagic);
-                    const int oa = (int)((uint32_t)__float_as_int(t) * 128u + va[j]);
+                    // half gradients, exact: (1.5 * 2^23 + g) / 2 - 0.75 * 2^23
+                    const float hx = fmaf(__int_as_float(gxb[j]), 0.5f, -0.5f * kMagic);
+                    const float hy = fmaf(__int_as_float(gyb[j]), 0.5f, -0.5f * kMagic);
+                    const float hm = sqrt_approx(fmaf(hx, hx, hy * hy));  // magnitude / 2
+                    const float ax = fabsf(hx), ay = fabsf(hy);
+                    // phi = atan(ay / ax) = 45deg + atan(t), t = (ay - ax) / (ay + ax) in [-1, 1];
+                    // ax + ay is 0 or >= 0.5: the 1e-30 only turns 0 / 0 into 0
+                    const float t = (ay - ax) * rcp_approx(ax + ay + 1e-30f);
+                    const float u = fmaf(-t, atan_bins2_poly(t * t), 4.5f);  // 2 (4.5 - phi) in bins, in [0, 9]
+                    // theta = phi (same signs) or 9 - phi (opposite signs); the vote position is
+                    // theta - 0.5, rounded below through theta - 1: p2 = 2 (theta - 1) = 7 -/+ u
+                    const uint32_t flip = (__float_as_uint(hx) ^ __float_as_uint(hy)) & 0x80000000u;
+                    const float p2 = 7.0f - __uint_as_float(__float_as_uint(u) ^ flip);
+                    const float r2 = p2 + kMagic2;                // 2 round(theta - 1) + 3 * 2^23
+                    const float e2 = p2 - (r2 - kMagic2);         // 2 (theta - 1 - round(...)), in [-1, 1]
+                    const int oa = (int)((uint32_t)__float_as_int(r2) * 128u + va[j]);
                     float *v = Wm.R + oa;
-                    float *u = Wm.R + (oa + dB);
-                    const float mo1 = mag * o1, mo0 = mag - mo1;
+                    float *w = Wm.R + (oa + dB);
+                    // upper / lower bin: magnitude times (1 +/- e2) / 2
+                    const float mo1 = fmaf(hm, e2, hm), mo0 = fmaf(-hm, e2, hm);
                     v[0] = fmaf(mo0, wa, v[0]);
                     v[kSCols] = fmaf(mo1, wa, v[kSCols]);
-                    u[0] = fmaf(mo0, wb, u[0]);
-                    u[kSCols] = fmaf(mo1, wb, u[kSCols]);
+                    w[0] = fmaf(mo0, wb, w[0]);
+                    w[kSCols] = fmaf(mo1, wb, w[kSCols]);
                 }
             }
             if (kLbp) {
