@@ -36,6 +36,8 @@
 // only for the rare pairs in the band.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "pd_internal.h"
 
 namespace pd {
@@ -47,6 +49,9 @@ constexpr int kMaxCandidatesBig = 65536;  // keys in global scratch
 constexpr int kMaxBoxes = 16384;
 constexpr int kBatch = 64;                // greedy walk: candidates resolved per block-wide step
 constexpr int kGrid = 32;                 // culling grid: kGrid x kGrid cells over the frame
+constexpr int kCountBlocks = 32;          // blocks per frame counting its candidates
+static_assert(nms_sched_ints(1) == 2 + kCountBlocks, "scheduling scratch: ticket, then per frame its order slot and counts");
+constexpr int kOrderMax = 16384;          // frames the order kernel sorts (more: drawn in index order)
 static_assert(kThreads == 16 * kBatch, "pairwise matrix: 16 threads per batch member");
 static_assert(kThreads == kGrid * kGrid, "one culling cell per thread");
 
@@ -347,11 +352,13 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
                                                   const float *__restrict__ scores, float threshold,
                                                   float iou_thr, int cap, float4 *__restrict__ scratch,
                                                   pd_box *__restrict__ boxes, int max_boxes,
-                                                  int32_t *__restrict__ counts) {
+                                                  int32_t *__restrict__ counts, int n_frames,
+                                                  const int *__restrict__ order, int *__restrict__ queue) {
     extern __shared__ unsigned long long skeys[];  // [cap_pow2] keys (small caps), cap bytes of flags, kept list
     __shared__ int n_cand;
     __shared__ int2 wkhk[PD_MAX_LEVELS];  // level sizes of this frame
     __shared__ int s_done, s_bx_smem;  // leader's state: walk over; boxes on chip
+    __shared__ int s_frame;            // the frame this cluster works on (-1: none left)
     // A frame is one cluster of C CTAs (C = 1 without a cluster launch). Every
     // rank collects a share of the frame's candidates into the leader's list;
     // with large caps (keys in global memory) every rank also sorts and
@@ -360,344 +367,423 @@ __global__ void __launch_bounds__(kThreads) k_nms(const FrameDesc *__restrict__ 
     // 1/C share of each suppression pass, reading the leader's flags and
     // boxes through distributed shared memory. All ranks pass the same
     // cluster barriers: what comes next is read from the leader after one.
+    // Without a queue, cluster i takes frame i. With one (more frames than
+    // clusters that fit on the GPU), the clusters are persistent: the leader
+    // draws the next ticket, takes that frame of `order` (heaviest first)
+    // and writes it into every rank's s_frame before the barrier that starts
+    // the frame, so all ranks work on the same frame and stop together.
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     const int C = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
     const bool leader = rank == 0;
-    const int f = blockIdx.x / C, tid = threadIdx.x;
-    const FrameDesc fd = frames[f];
+    const int tid = threadIdx.x;
     int cap_pow2 = 1;
     while (cap_pow2 < cap) cap_pow2 <<= 1;
     const bool big = cap > kMaxCandidates;
-    float4 *gbx = scratch + (size_t)f * nms_scratch_float4s(cap);
-    unsigned long long *keys = big ? reinterpret_cast<unsigned long long *>(gbx + cap) : skeys;
-    uint8_t *supp = reinterpret_cast<uint8_t *>(big ? skeys : skeys + cap_pow2);
-    const float4 *bx = gbx;
-    const unsigned long long *ksrc = keys;
-    for (int k = tid; k < fd.n_levels; k += kThreads) {
-        const LevelDesc L = levels[fd.first_level + k];
-        wkhk[k] = make_int2(L.Wk, L.Hk);
-    }
-    if (tid == 0 && leader) n_cand = 0;
-    cluster.sync();  // the leader's counter is zero
-    {
-        // every rank scans its share of the windows (every C-th run of
-        // kThreads * kUnroll of a level) and appends to the leader's list
-        int *cnt = leader ? &n_cand : cluster.map_shared_rank(&n_cand, 0);
-        unsigned long long *kw = big ? keys : leader ? skeys : cluster.map_shared_rank(skeys, 0);
-        for (int k = 0; k < fd.n_levels; ++k) {
+    if (queue) cluster.sync();  // every CTA of the cluster runs before the leader writes into it
+    for (int pass = 0;; ++pass) {
+        if (queue) {
+            if (leader && tid == 0) {
+                const int t = atomicAdd(queue, 1);
+                const int fr = t < n_frames ? (order ? order[t] : t) : -1;
+                for (int r = 0; r < C; ++r) *cluster.map_shared_rank(&s_frame, r) = fr;
+                n_cand = 0;
+            }
+        } else if (tid == 0) {
+            s_frame = pass == 0 ? (int)(blockIdx.x / C) : -1;
+            if (leader) n_cand = 0;
+        }
+        cluster.sync();  // every rank knows the frame; the leader's counter is zero
+        const int f = s_frame;
+        if (f < 0) return;  // the same value in every rank: all leave together
+        const FrameDesc fd = frames[f];
+        float4 *gbx = scratch + (size_t)f * nms_scratch_float4s(cap);
+        unsigned long long *keys = big ? reinterpret_cast<unsigned long long *>(gbx + cap) : skeys;
+        uint8_t *supp = reinterpret_cast<uint8_t *>(big ? skeys : skeys + cap_pow2);
+        const float4 *bx = gbx;
+        const unsigned long long *ksrc = keys;
+        for (int k = tid; k < fd.n_levels; k += kThreads) {
             const LevelDesc L = levels[fd.first_level + k];
-            const int n = L.rows * L.cols;
-            const float *sc = scores + L.score_off;
-            // warp-aggregated appends; kUnroll independent loads per thread are in
-            // flight before any of them is used (the scan is latency-bound otherwise)
-            constexpr int kUnroll = 8;
-            for (int i0 = rank * kThreads * kUnroll; i0 < n; i0 += C * kThreads * kUnroll) {
-                float sv[kUnroll];
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    const int i = i0 + u * kThreads + tid;
-                    sv[u] = i < n ? __ldg(sc + i) : 0.f;
-                }
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    const int i = i0 + u * kThreads + tid;
-                    if (i0 + u * kThreads >= n) break;  // block-uniform
-                    const float s = sv[u];
-                    const bool hit = i < n && s > threshold;
-                    const unsigned m = __ballot_sync(0xffffffffu, hit);
-                    int base = 0;
-                    if ((tid & 31) == 0 && m) base = atomicAdd(cnt, __popc(m));
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    if (hit) {
-                        const int idx = base + __popc(m & ((1u << (tid & 31)) - 1u));
-                        if (idx < cap) {
-                            const int wy = i / L.cols;
-                            kw[idx] = make_key(s, k, wy, i - wy * L.cols);
+            wkhk[k] = make_int2(L.Wk, L.Hk);
+        }
+        {
+            // every rank scans its share of the windows (every C-th run of
+            // kThreads * kUnroll of a level) and appends to the leader's list
+            int *cnt = leader ? &n_cand : cluster.map_shared_rank(&n_cand, 0);
+            unsigned long long *kw = big ? keys : leader ? skeys : cluster.map_shared_rank(skeys, 0);
+            for (int k = 0; k < fd.n_levels; ++k) {
+                const LevelDesc L = levels[fd.first_level + k];
+                const int n = L.rows * L.cols;
+                const float *sc = scores + L.score_off;
+                // warp-aggregated appends; kUnroll independent loads per thread are in
+                // flight before any of them is used (the scan is latency-bound otherwise)
+                constexpr int kUnroll = 8;
+                for (int i0 = rank * kThreads * kUnroll; i0 < n; i0 += C * kThreads * kUnroll) {
+                    float sv[kUnroll];
+    #pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        const int i = i0 + u * kThreads + tid;
+                        sv[u] = i < n ? __ldg(sc + i) : 0.f;
+                    }
+    #pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        const int i = i0 + u * kThreads + tid;
+                        if (i0 + u * kThreads >= n) break;  // block-uniform
+                        const float s = sv[u];
+                        const bool hit = i < n && s > threshold;
+                        const unsigned m = __ballot_sync(0xffffffffu, hit);
+                        int base = 0;
+                        if ((tid & 31) == 0 && m) base = atomicAdd(cnt, __popc(m));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (hit) {
+                            const int idx = base + __popc(m & ((1u << (tid & 31)) - 1u));
+                            if (idx < cap) {
+                                const int wy = i / L.cols;
+                                kw[idx] = make_key(s, k, wy, i - wy * L.cols);
+                            }
                         }
                     }
                 }
             }
         }
-    }
-    cluster.sync();  // every rank's candidates are in
-    const int n = leader ? n_cand : *cluster.map_shared_rank(&n_cand, 0);
-    if (n > cap) {
-        if (leader && tid == 0) {
-            counts[2 * f] = 0;
-            counts[2 * f + 1] = -n;
-        }
-        cluster.sync();  // nobody leaves while another rank reads its shared memory
-        return;
-    }
-    int np = 1;
-    while (np < n) np <<= 1;
-    if (big) {
-        // keys and boxes in global memory: every rank sorts and decodes a share
-        for (int i = n + rank * kThreads + tid; i < np; i += C * kThreads) keys[i] = ~0ull;
-        cluster.sync();
-        // the boxes region (cap float4s) is free until the decode below
-        sort_large(keys, reinterpret_cast<unsigned long long *>(gbx), np, skeys, tid, rank, C,
-                   [&] { cluster.sync(); });
-        for (int i = rank * kThreads + tid; i < n; i += C * kThreads) {
-            const pd_box b = decode(keys[i], fd.W, fd.H, wkhk);
-            gbx[i] = make_float4(b.x, b.y, b.w, b.h);
-        }
-        if (leader) {
-            for (int i = tid; i < n; i += kThreads) supp[i] = 0;
-            if (tid == 0) s_bx_smem = 0;
-        }
-    } else if (leader) {
-        for (int i = n + tid; i < np; i += kThreads) keys[i] = ~0ull;
-        __syncthreads();
-        bitonic_sort_smem(keys, np, tid);
-        for (int i = tid; i < n; i += kThreads) supp[i] = 0;
-        __syncthreads();
-        // Decoded boxes: in shared memory when they fit in the key region (the
-        // keys then move to the global scratch, where only kept ones are read
-        // again), otherwise in the global scratch. Each greedy pass reads every
-        // remaining box, so keeping them on chip shortens every pass.
-        if (2 * n <= cap_pow2) {
-            unsigned long long *gkeys = reinterpret_cast<unsigned long long *>(gbx);
-            for (int i = tid; i < n; i += kThreads) gkeys[i] = keys[i];
-            __syncthreads();
-            float4 *sbx = reinterpret_cast<float4 *>(keys);
-            for (int i = tid; i < n; i += kThreads) {  // each thread re-reads only its own writes
-                const pd_box b = decode(gkeys[i], fd.W, fd.H, wkhk);
-                sbx[i] = make_float4(b.x, b.y, b.w, b.h);
+        cluster.sync();  // every rank's candidates are in
+        const int n = leader ? n_cand : *cluster.map_shared_rank(&n_cand, 0);
+        if (n > cap) {
+            if (leader && tid == 0) {
+                counts[2 * f] = 0;
+                counts[2 * f + 1] = -n;
             }
-            bx = sbx;
-            ksrc = gkeys;
-        } else {
-            for (int i = tid; i < n; i += kThreads) {
+            cluster.sync();  // nobody moves on while another rank reads its shared memory
+            continue;
+        }
+        int np = 1;
+        while (np < n) np <<= 1;
+        if (big) {
+            // keys and boxes in global memory: every rank sorts and decodes a share
+            for (int i = n + rank * kThreads + tid; i < np; i += C * kThreads) keys[i] = ~0ull;
+            cluster.sync();
+            // the boxes region (cap float4s) is free until the decode below
+            sort_large(keys, reinterpret_cast<unsigned long long *>(gbx), np, skeys, tid, rank, C,
+                       [&] { cluster.sync(); });
+            for (int i = rank * kThreads + tid; i < n; i += C * kThreads) {
                 const pd_box b = decode(keys[i], fd.W, fd.H, wkhk);
                 gbx[i] = make_float4(b.x, b.y, b.w, b.h);
             }
-        }
-        if (tid == 0) s_bx_smem = bx != gbx;
-    }
-    cluster.sync();  // the leader's candidates, flags and boxes are in place
-    // the flags and the boxes of the walk: the leader's own, or read remotely
-    uint8_t *fl = leader ? supp : cluster.map_shared_rank(supp, 0);
-    if (!leader && *cluster.map_shared_rank(&s_bx_smem, 0))
-        bx = cluster.map_shared_rank(reinterpret_cast<float4 *>(keys), 0);
-    // Greedy walk in batches. All threads find the next (up to) 64 candidates
-    // not yet suppressed, in order (1024 positions per round), and copy their
-    // boxes to shared memory; all threads compute the batch's pairwise
-    // suppression bits (4 pairs each); warp 0 resolves the members (a member
-    // is kept iff no kept member before it suppresses it: the candidates
-    // between members are already suppressed) and copies the kept boxes to
-    // shared memory; then every thread suppresses the later candidates against
-    // them. Same decisions as the sequential definition, with ~64x fewer
-    // block-wide barriers.
-    //
-    // Culling (IoU threshold >= 0.5): if IoU(A, B) > 0.5 then A's centre lies
-    // in B (were it outside B on one axis, A and B would overlap on at most
-    // half of A's extent there, so inter <= |A| / 2, and inter > (|A| + |B|)
-    // / 3 would need |B| < |A| / 2 while inter <= |B| needs |B| > |A| / 2).
-    // Each batch records, for every cell of a 32 x 32 grid over the frame,
-    // which of its kept boxes cover the cell (one cell of margin for
-    // rounding); a candidate is tested only against the kept boxes that cover
-    // its centre's cell (no test at all when none does).
-    __shared__ int batch[kBatch];
-    __shared__ float4 bbx[kBatch], kbx[kBatch];
-    __shared__ unsigned long long bcol[kBatch];  // member b: bit a set iff a < b and a suppresses b
-    __shared__ int n_batch, n_keep, kept_total, scan_pos;
-    __shared__ int wcnt[kThreads / 32];
-    __shared__ unsigned long long cmask[kGrid * kGrid];  // culling grid: kept boxes covering each cell
-    __shared__ int4 krect[kBatch];                       // kept boxes' cell ranges x0, x1, y0, y1
-    int *kept_idx = reinterpret_cast<int *>(supp + ((cap + 15) & ~15));
-    const int warp = tid >> 5, lane = tid & 31;
-    const bool cull = iou_thr >= 0.5f;
-    const float gsx = (float)kGrid / (float)fd.W, gsy = (float)kGrid / (float)fd.H;
-    if (tid == 0 && leader) {
-        kept_total = 0;
-        scan_pos = 0;
-    }
-    __syncthreads();
-    while (true) {
-        if (leader) {
-            // ---- the next batch: the first kBatch alive candidates at or after scan_pos
-            {
-                int cnt = 0, pos = scan_pos;
-                while (cnt < kBatch && pos < n) {
-                    const int j = pos + tid;
-                    const bool alive = j < n && !fl[j];
-                    const unsigned m = __ballot_sync(0xffffffffu, alive);
-                    if (lane == 0) wcnt[warp] = __popc(m);
-                    __syncthreads();
-                    int before = 0, total = 0;
-#pragma unroll 8
-                    for (int w = 0; w < kThreads / 32; ++w) {
-                        const int c = wcnt[w];
-                        before += w < warp ? c : 0;
-                        total += c;
-                    }
-                    const int slot = cnt + before + __popc(m & ((1u << lane) - 1u));
-                    if (alive && slot < kBatch) {
-                        batch[slot] = j;
-                        bbx[slot] = bx[j];
-                        if (slot == kBatch - 1) scan_pos = j + 1;  // stop right after the last member
-                    }
-                    if (cnt + total < kBatch && tid == 0) scan_pos = min(pos + kThreads, n);
-                    cnt = min(cnt + total, kBatch);
-                    pos += kThreads;
-                    __syncthreads();  // wcnt reused by the next round; scan_pos, batch visible
-                }
-                if (tid == 0) n_batch = cnt;
+            if (leader) {
+                for (int i = tid; i < n; i += kThreads) supp[i] = 0;
+                if (tid == 0) s_bx_smem = 0;
             }
+        } else if (leader) {
+            for (int i = n + tid; i < np; i += kThreads) keys[i] = ~0ull;
             __syncthreads();
-            const int nb = n_batch;
-            if (nb > 0) {
+            bitonic_sort_smem(keys, np, tid);
+            for (int i = tid; i < n; i += kThreads) supp[i] = 0;
+            __syncthreads();
+            // Decoded boxes: in shared memory when they fit in the key region (the
+            // keys then move to the global scratch, where only kept ones are read
+            // again), otherwise in the global scratch. Each greedy pass reads every
+            // remaining box, so keeping them on chip shortens every pass.
+            if (2 * n <= cap_pow2) {
+                unsigned long long *gkeys = reinterpret_cast<unsigned long long *>(gbx);
+                for (int i = tid; i < n; i += kThreads) gkeys[i] = keys[i];
+                __syncthreads();
+                float4 *sbx = reinterpret_cast<float4 *>(keys);
+                for (int i = tid; i < n; i += kThreads) {  // each thread re-reads only its own writes
+                    const pd_box b = decode(gkeys[i], fd.W, fd.H, wkhk);
+                    sbx[i] = make_float4(b.x, b.y, b.w, b.h);
+                }
+                bx = sbx;
+                ksrc = gkeys;
+            } else {
+                for (int i = tid; i < n; i += kThreads) {
+                    const pd_box b = decode(keys[i], fd.W, fd.H, wkhk);
+                    gbx[i] = make_float4(b.x, b.y, b.w, b.h);
+                }
+            }
+            if (tid == 0) s_bx_smem = bx != gbx;
+        }
+        cluster.sync();  // the leader's candidates, flags and boxes are in place
+        // the flags and the boxes of the walk: the leader's own, or read remotely
+        uint8_t *fl = leader ? supp : cluster.map_shared_rank(supp, 0);
+        if (!leader && *cluster.map_shared_rank(&s_bx_smem, 0))
+            bx = cluster.map_shared_rank(reinterpret_cast<float4 *>(keys), 0);
+        // Greedy walk in batches. All threads find the next (up to) 64 candidates
+        // not yet suppressed, in order (1024 positions per round), and copy their
+        // boxes to shared memory; all threads compute the batch's pairwise
+        // suppression bits (4 pairs each); warp 0 resolves the members (a member
+        // is kept iff no kept member before it suppresses it: the candidates
+        // between members are already suppressed) and copies the kept boxes to
+        // shared memory; then every thread suppresses the later candidates against
+        // them. Same decisions as the sequential definition, with ~64x fewer
+        // block-wide barriers.
+        //
+        // Culling (IoU threshold >= 0.5): if IoU(A, B) > 0.5 then A's centre lies
+        // in B (were it outside B on one axis, A and B would overlap on at most
+        // half of A's extent there, so inter <= |A| / 2, and inter > (|A| + |B|)
+        // / 3 would need |B| < |A| / 2 while inter <= |B| needs |B| > |A| / 2).
+        // Each batch records, for every cell of a 32 x 32 grid over the frame,
+        // which of its kept boxes cover the cell (one cell of margin for
+        // rounding); a candidate is tested only against the kept boxes that cover
+        // its centre's cell (no test at all when none does).
+        __shared__ int batch[kBatch];
+        __shared__ float4 bbx[kBatch], kbx[kBatch];
+        __shared__ unsigned long long bcol[kBatch];  // member b: bit a set iff a < b and a suppresses b
+        __shared__ int n_batch, n_keep, kept_total, scan_pos;
+        __shared__ int wcnt[kThreads / 32];
+        __shared__ unsigned long long cmask[kGrid * kGrid];  // culling grid: kept boxes covering each cell
+        __shared__ int4 krect[kBatch];                       // kept boxes' cell ranges x0, x1, y0, y1
+        int *kept_idx = reinterpret_cast<int *>(supp + ((cap + 15) & ~15));
+        const int warp = tid >> 5, lane = tid & 31;
+        const bool cull = iou_thr >= 0.5f;
+        const float gsx = (float)kGrid / (float)fd.W, gsy = (float)kGrid / (float)fd.H;
+        if (tid == 0 && leader) {
+            kept_total = 0;
+            scan_pos = 0;
+        }
+        __syncthreads();
+        while (true) {
+            if (leader) {
+                // ---- the next batch: the first kBatch alive candidates at or after scan_pos
                 {
-                    // member b = tid / 16 is tested against members a = 4 (tid % 16) .. + 3
-                    // (a < b); the 16 threads of a member OR their bits together
-                    const int b = tid >> 4, a0 = (tid & 15) * 4;
-                    unsigned long long bits = 0;
-                    if (b < nb) {
-                        const float4 bb = bbx[b];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int a = a0 + q;
-                            if (a < b && suppresses(bbx[a], bb, iou_thr)) bits |= 1ull << a;
+                    int cnt = 0, pos = scan_pos;
+                    while (cnt < kBatch && pos < n) {
+                        const int j = pos + tid;
+                        const bool alive = j < n && !fl[j];
+                        const unsigned m = __ballot_sync(0xffffffffu, alive);
+                        if (lane == 0) wcnt[warp] = __popc(m);
+                        __syncthreads();
+                        int before = 0, total = 0;
+    #pragma unroll 8
+                        for (int w = 0; w < kThreads / 32; ++w) {
+                            const int c = wcnt[w];
+                            before += w < warp ? c : 0;
+                            total += c;
                         }
+                        const int slot = cnt + before + __popc(m & ((1u << lane) - 1u));
+                        if (alive && slot < kBatch) {
+                            batch[slot] = j;
+                            bbx[slot] = bx[j];
+                            if (slot == kBatch - 1) scan_pos = j + 1;  // stop right after the last member
+                        }
+                        if (cnt + total < kBatch && tid == 0) scan_pos = min(pos + kThreads, n);
+                        cnt = min(cnt + total, kBatch);
+                        pos += kThreads;
+                        __syncthreads();  // wcnt reused by the next round; scan_pos, batch visible
                     }
-#pragma unroll
-                    for (int o = 8; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
-                    if ((tid & 15) == 0 && b < kBatch) bcol[b] = bits;
+                    if (tid == 0) n_batch = cnt;
                 }
                 __syncthreads();
-                if (warp == 0) {
-                    // Resolve in rounds: a member is dropped once a kept member
-                    // suppresses it, and kept once every member that could suppress it
-                    // is decided and none of them is kept. This reaches the in-order
-                    // result (induction on the member index) in as many rounds as the
-                    // longest chain of suppressions.
-                    const unsigned long long all = nb == 64 ? ~0ull : ((1ull << nb) - 1ull);
-                    const unsigned long long c0 = bcol[lane], c1 = bcol[lane + 32];
-                    unsigned long long keep = 0, decided = ~all;
-                    while (decided != ~0ull) {
-                        const bool k0 = !((decided >> lane) & 1ull) && !(c0 & keep) && !(c0 & ~decided);
-                        const bool d0 = k0 || (!((decided >> lane) & 1ull) && (c0 & keep));
-                        const bool k1 = !((decided >> (lane + 32)) & 1ull) && !(c1 & keep) && !(c1 & ~decided);
-                        const bool d1 = k1 || (!((decided >> (lane + 32)) & 1ull) && (c1 & keep));
-                        keep |= (unsigned long long)__ballot_sync(0xffffffffu, k0) |
-                                ((unsigned long long)__ballot_sync(0xffffffffu, k1) << 32);
-                        decided |= (unsigned long long)__ballot_sync(0xffffffffu, d0) |
-                                   ((unsigned long long)__ballot_sync(0xffffffffu, d1) << 32);
+                const int nb = n_batch;
+                if (nb > 0) {
+                    {
+                        // member b = tid / 16 is tested against members a = 4 (tid % 16) .. + 3
+                        // (a < b); the 16 threads of a member OR their bits together
+                        const int b = tid >> 4, a0 = (tid & 15) * 4;
+                        unsigned long long bits = 0;
+                        if (b < nb) {
+                            const float4 bb = bbx[b];
+    #pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const int a = a0 + q;
+                                if (a < b && suppresses(bbx[a], bb, iou_thr)) bits |= 1ull << a;
+                            }
+                        }
+    #pragma unroll
+                        for (int o = 8; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
+                        if ((tid & 15) == 0 && b < kBatch) bcol[b] = bits;
                     }
-                    // the cap on kept boxes: only the first (max_boxes - kept so far) in order
-                    const int kt = kept_total;
-                    const int room = max_boxes - kt;
-                    while (__popcll(keep) > room) keep &= ~(1ull << (63 - __clzll(keep)));
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int m = lane + 32 * h;
-                        if (m < nb && ((keep >> m) & 1ull)) {
-                            const int r = __popcll(keep & ((1ull << m) - 1ull));
-                            kept_idx[kt + r] = batch[m];
-                            kbx[r] = bbx[m];
+                    __syncthreads();
+                    if (warp == 0) {
+                        // Resolve in rounds: a member is dropped once a kept member
+                        // suppresses it, and kept once every member that could suppress it
+                        // is decided and none of them is kept. This reaches the in-order
+                        // result (induction on the member index) in as many rounds as the
+                        // longest chain of suppressions.
+                        const unsigned long long all = nb == 64 ? ~0ull : ((1ull << nb) - 1ull);
+                        const unsigned long long c0 = bcol[lane], c1 = bcol[lane + 32];
+                        unsigned long long keep = 0, decided = ~all;
+                        while (decided != ~0ull) {
+                            const bool k0 = !((decided >> lane) & 1ull) && !(c0 & keep) && !(c0 & ~decided);
+                            const bool d0 = k0 || (!((decided >> lane) & 1ull) && (c0 & keep));
+                            const bool k1 = !((decided >> (lane + 32)) & 1ull) && !(c1 & keep) && !(c1 & ~decided);
+                            const bool d1 = k1 || (!((decided >> (lane + 32)) & 1ull) && (c1 & keep));
+                            keep |= (unsigned long long)__ballot_sync(0xffffffffu, k0) |
+                                    ((unsigned long long)__ballot_sync(0xffffffffu, k1) << 32);
+                            decided |= (unsigned long long)__ballot_sync(0xffffffffu, d0) |
+                                       ((unsigned long long)__ballot_sync(0xffffffffu, d1) << 32);
+                        }
+                        // the cap on kept boxes: only the first (max_boxes - kept so far) in order
+                        const int kt = kept_total;
+                        const int room = max_boxes - kt;
+                        while (__popcll(keep) > room) keep &= ~(1ull << (63 - __clzll(keep)));
+    #pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int m = lane + 32 * h;
+                            if (m < nb && ((keep >> m) & 1ull)) {
+                                const int r = __popcll(keep & ((1ull << m) - 1ull));
+                                kept_idx[kt + r] = batch[m];
+                                kbx[r] = bbx[m];
+                            }
+                        }
+                        if (lane == 0) {
+                            n_keep = __popcll(keep);
+                            kept_total = kt + __popcll(keep);
                         }
                     }
-                    if (lane == 0) {
-                        n_keep = __popcll(keep);
-                        kept_total = kt + __popcll(keep);
+                }
+                __syncthreads();
+                if (tid == 0) s_done = nb == 0 || kept_total >= max_boxes;
+            }
+            cluster.sync();  // the batch is resolved (or the walk is over)
+            if (leader ? s_done : *cluster.map_shared_rank(&s_done, 0)) break;
+            int nk, sp;
+            if (leader) {
+                nk = n_keep;
+                sp = scan_pos;
+            } else {  // the kept boxes of the batch and the scan start, from the leader
+                nk = *cluster.map_shared_rank(&n_keep, 0);
+                sp = *cluster.map_shared_rank(&scan_pos, 0);
+                const float4 *lk = cluster.map_shared_rank(kbx, 0);
+                for (int k = tid; k < nk; k += kThreads) kbx[k] = lk[k];
+                __syncthreads();
+            }
+            if (cull) {
+                // grid cells under each kept box, with one cell of margin; then per
+                // cell (one per thread) the set of kept boxes that cover it
+                if (tid < nk) {
+                    const float4 b = kbx[tid];
+                    krect[tid] = make_int4(max((int)floorf(b.x * gsx) - 1, 0),
+                                           min((int)floorf((b.x + b.z) * gsx) + 1, kGrid - 1),
+                                           max((int)floorf(b.y * gsy) - 1, 0),
+                                           min((int)floorf((b.y + b.w) * gsy) + 1, kGrid - 1));
+                }
+                __syncthreads();
+                const int cx = tid & (kGrid - 1), cy = tid / kGrid;
+                unsigned long long m = 0ull;
+                for (int k = 0; k < nk; ++k) {
+                    const int4 r = krect[k];
+                    if (cx >= r.x && cx <= r.y && cy >= r.z && cy <= r.w) m |= 1ull << k;
+                }
+                cmask[tid] = m;
+                __syncthreads();
+            }
+            int j = sp + rank * kThreads + tid;  // this rank's share: every C-th run of kThreads
+            float4 bnext = j < n ? bx[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (; j < n; j += C * kThreads) {
+                // the next box is loaded while this one is tested (global for large caps)
+                const float4 bj = bnext;
+                if (j + C * kThreads < n) bnext = bx[j + C * kThreads];
+                if (fl[j]) continue;
+                bool hit = false;
+                if (cull) {
+                    // only the kept boxes that cover the centre's cell can suppress it
+                    const int cx = min(max((int)floorf((bj.x + 0.5f * bj.z) * gsx), 0), kGrid - 1);
+                    const int cy = min(max((int)floorf((bj.y + 0.5f * bj.w) * gsy), 0), kGrid - 1);
+                    unsigned long long m = cmask[cy * kGrid + cx];
+                    while (m && !hit) {
+                        const int k = __ffsll((long long)m) - 1;
+                        m &= m - 1ull;
+                        hit = suppresses(kbx[k], bj, iou_thr);
+                    }
+                } else {
+                    for (int k = 0; k < nk && !hit; k += 4) {
+                        // four tests in flight (kept boxes past nk repeat the first one)
+                        const bool h0 = suppresses(kbx[k], bj, iou_thr);
+                        const bool h1 = suppresses(kbx[k + 1 < nk ? k + 1 : 0], bj, iou_thr);
+                        const bool h2 = suppresses(kbx[k + 2 < nk ? k + 2 : 0], bj, iou_thr);
+                        const bool h3 = suppresses(kbx[k + 3 < nk ? k + 3 : 0], bj, iou_thr);
+                        hit = h0 || h1 || h2 || h3;
                     }
                 }
+                if (hit) fl[j] = 1;
             }
-            __syncthreads();
-            if (tid == 0) s_done = nb == 0 || kept_total >= max_boxes;
+            cluster.sync();  // every rank's share of the pass is done
         }
-        cluster.sync();  // the batch is resolved (or the walk is over)
-        if (leader ? s_done : *cluster.map_shared_rank(&s_done, 0)) break;
-        int nk, sp;
-        if (leader) {
-            nk = n_keep;
-            sp = scan_pos;
-        } else {  // the kept boxes of the batch and the scan start, from the leader
-            nk = *cluster.map_shared_rank(&n_keep, 0);
-            sp = *cluster.map_shared_rank(&scan_pos, 0);
-            const float4 *lk = cluster.map_shared_rank(kbx, 0);
-            for (int k = tid; k < nk; k += kThreads) kbx[k] = lk[k];
-            __syncthreads();
+        cluster.sync();  // nobody moves on while another rank reads its shared memory
+        if (!leader) continue;
+        const int kept = kept_total;
+        pd_box *out = boxes + (size_t)f * max_boxes;
+        for (int k = tid; k < kept; k += kThreads) {
+            const int c = kept_idx[k];
+            const unsigned long long key = ksrc[c];
+            const float4 bc = bx[c];
+            const uint32_t hi = (uint32_t)(key >> 32), lo = (uint32_t)key;
+            const uint32_t ord = ~hi;
+            pd_box b;
+            b.x = bc.x;
+            b.y = bc.y;
+            b.w = bc.z;
+            b.h = bc.w;
+            b.score = __uint_as_float((ord & 0x80000000u) ? (ord ^ 0x80000000u) : ~ord);
+            b.level = (int)(lo >> 24);
+            b.wy = (int)((lo >> 12) & 4095);
+            b.wx = (int)(lo & 4095);
+            out[k] = b;
         }
-        if (cull) {
-            // grid cells under each kept box, with one cell of margin; then per
-            // cell (one per thread) the set of kept boxes that cover it
-            if (tid < nk) {
-                const float4 b = kbx[tid];
-                krect[tid] = make_int4(max((int)floorf(b.x * gsx) - 1, 0),
-                                       min((int)floorf((b.x + b.z) * gsx) + 1, kGrid - 1),
-                                       max((int)floorf(b.y * gsy) - 1, 0),
-                                       min((int)floorf((b.y + b.w) * gsy) + 1, kGrid - 1));
-            }
-            __syncthreads();
-            const int cx = tid & (kGrid - 1), cy = tid / kGrid;
-            unsigned long long m = 0ull;
-            for (int k = 0; k < nk; ++k) {
-                const int4 r = krect[k];
-                if (cx >= r.x && cx <= r.y && cy >= r.z && cy <= r.w) m |= 1ull << k;
-            }
-            cmask[tid] = m;
-            __syncthreads();
+        if (tid == 0) {
+            counts[2 * f] = kept;
+            counts[2 * f + 1] = n;
         }
-        int j = sp + rank * kThreads + tid;  // this rank's share: every C-th run of kThreads
-        float4 bnext = j < n ? bx[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-        for (; j < n; j += C * kThreads) {
-            // the next box is loaded while this one is tested (global for large caps)
-            const float4 bj = bnext;
-            if (j + C * kThreads < n) bnext = bx[j + C * kThreads];
-            if (fl[j]) continue;
-            bool hit = false;
-            if (cull) {
-                // only the kept boxes that cover the centre's cell can suppress it
-                const int cx = min(max((int)floorf((bj.x + 0.5f * bj.z) * gsx), 0), kGrid - 1);
-                const int cy = min(max((int)floorf((bj.y + 0.5f * bj.w) * gsy), 0), kGrid - 1);
-                unsigned long long m = cmask[cy * kGrid + cx];
-                while (m && !hit) {
-                    const int k = __ffsll((long long)m) - 1;
-                    m &= m - 1ull;
-                    hit = suppresses(kbx[k], bj, iou_thr);
-                }
-            } else {
-                for (int k = 0; k < nk && !hit; k += 4) {
-                    // four tests in flight (kept boxes past nk repeat the first one)
-                    const bool h0 = suppresses(kbx[k], bj, iou_thr);
-                    const bool h1 = suppresses(kbx[k + 1 < nk ? k + 1 : 0], bj, iou_thr);
-                    const bool h2 = suppresses(kbx[k + 2 < nk ? k + 2 : 0], bj, iou_thr);
-                    const bool h3 = suppresses(kbx[k + 3 < nk ? k + 3 : 0], bj, iou_thr);
-                    hit = h0 || h1 || h2 || h3;
-                }
-            }
-            if (hit) fl[j] = 1;
-        }
-        cluster.sync();  // every rank's share of the pass is done
     }
-    cluster.sync();  // nobody leaves while another rank reads its shared memory
-    if (!leader) return;
-    const int kept = kept_total;
-    pd_box *out = boxes + (size_t)f * max_boxes;
-    for (int k = tid; k < kept; k += kThreads) {
-        const int c = kept_idx[k];
-        const unsigned long long key = ksrc[c];
-        const float4 bc = bx[c];
-        const uint32_t hi = (uint32_t)(key >> 32), lo = (uint32_t)key;
-        const uint32_t ord = ~hi;
-        pd_box b;
-        b.x = bc.x;
-        b.y = bc.y;
-        b.w = bc.z;
-        b.h = bc.w;
-        b.score = __uint_as_float((ord & 0x80000000u) ? (ord ^ 0x80000000u) : ~ord);
-        b.level = (int)(lo >> 24);
-        b.wy = (int)((lo >> 12) & 4095);
-        b.wx = (int)(lo & 4095);
-        out[k] = b;
+}
+
+// Candidates per frame for the order of the persistent clusters. A frame's
+// score maps lie back to back (its levels in order); block x of frame y
+// counts the scores above the threshold in every kCountBlocks-th run of
+// 4 x 256 of them, four loads in flight per thread.
+__global__ void __launch_bounds__(256) k_nms_count(const FrameDesc *__restrict__ frames,
+                                                   const LevelDesc *__restrict__ levels,
+                                                   const float *__restrict__ scores, float threshold,
+                                                   int *__restrict__ partial) {
+    const int f = blockIdx.y;
+    const FrameDesc fd = frames[f];
+    int c = 0;
+    if (fd.n_levels > 0) {
+        const LevelDesc &a = levels[fd.first_level], &z = levels[fd.first_level + fd.n_levels - 1];
+        const float *sc = scores + a.score_off;
+        const int n = (int)(z.score_off + (int64_t)z.rows * z.cols - a.score_off);
+        constexpr int kU = 4;
+        for (int i0 = blockIdx.x * 256 * kU + threadIdx.x; i0 < n; i0 += kCountBlocks * 256 * kU) {
+            float v[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) v[u] = i0 + u * 256 < n ? __ldg(sc + i0 + u * 256) : -INFINITY;
+#pragma unroll
+            for (int u = 0; u < kU; ++u) c += v[u] > threshold;
+        }
     }
-    if (tid == 0) {
-        counts[2 * f] = kept;
-        counts[2 * f + 1] = n;
+    c = __reduce_add_sync(0xffffffffu, c);
+    __shared__ int ws[8];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < 8; ++w) t += ws[w];
+        partial[f * kCountBlocks + blockIdx.x] = t;
     }
+}
+
+// The frames by candidates, most first (ties: lower frame first), and the
+// ticket counter reset. One CTA, a bitonic sort of n_frames keys.
+__global__ void __launch_bounds__(kThreads) k_nms_order(const int *__restrict__ partial, int n_frames,
+                                                        int *__restrict__ order, int *__restrict__ queue) {
+    extern __shared__ unsigned long long okeys[];
+    const int tid = threadIdx.x;
+    int np = 1;
+    while (np < n_frames) np <<= 1;
+    for (int i = tid; i < np; i += kThreads) {
+        unsigned long long key = ~0ull;
+        if (i < n_frames) {
+            int c = 0;
+            for (int b = 0; b < kCountBlocks; ++b) c += partial[i * kCountBlocks + b];
+            key = ((unsigned long long)(uint32_t)(0x7fffffff - c) << 32) | (uint32_t)i;
+        }
+        okeys[i] = key;
+    }
+    __syncthreads();
+    bitonic_sort_smem(okeys, np, tid);
+    __syncthreads();
+    for (int t = tid; t < n_frames; t += kThreads) order[t] = (int)(uint32_t)okeys[t];
+    if (tid == 0) *queue = 0;
 }
 
 size_t nms_smem(int cap, int max_boxes) {
@@ -714,12 +800,24 @@ size_t nms_smem(int cap, int max_boxes) {
 
 namespace {
 int g_nms_max_cluster = 1;  // largest cluster of k_nms CTAs the device can hold (1, 2, 4 or 8)
+int g_nms_active[4] = {1, 0, 0, 0};  // clusters of 1, 2, 4, 8 CTAs that fit on the device at once
+
+int log2_cluster(int c) { return c == 8 ? 3 : c == 4 ? 2 : c == 2 ? 1 : 0; }
 }  // namespace
 
 cudaError_t init_nms() {
     const int smem = (int)nms_smem(kMaxCandidates, kMaxBoxes);
-    const cudaError_t e = cudaFuncSetAttribute(k_nms, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(k_nms, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_nms_order, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kOrderMax * (int)sizeof(unsigned long long));
     if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nms, kThreads, (size_t)smem)) != cudaSuccess)
+        return e;
+    g_nms_active[0] = std::max(sms * per_sm, 1);
     g_nms_max_cluster = 1;
     for (int c = 8; c >= 2; c >>= 1) {
         cudaLaunchConfig_t cfg = {};
@@ -735,38 +833,72 @@ cudaError_t init_nms() {
         cfg.numAttrs = 1;
         int n = 0;
         if (cudaOccupancyMaxActiveClusters(&n, k_nms, &cfg) == cudaSuccess && n > 0) {
-            g_nms_max_cluster = c;
-            break;
+            g_nms_active[log2_cluster(c)] = n;
+            g_nms_max_cluster = std::max(g_nms_max_cluster, c);
+        } else {
+            g_nms_active[log2_cluster(c)] = 0;
+            (void)cudaGetLastError();  // a refused size is not an error
         }
-        (void)cudaGetLastError();  // a refused size is not an error: try a smaller one
     }
     return cudaSuccess;
 }
 
-int nms_cluster_for(int n_frames, int sm_count) {
+int nms_cluster_for(int n_frames, int sm_count, int max_cand) {
     // the CTAs of a frame share its suppression passes; only while every CTA
-    // still gets an SM of its own (one 1024-thread CTA per SM)
+    // still gets an SM of its own (one 1024-thread CTA per SM), or, for large
+    // candidate lists, while two rounds of clusters cover the frames (the
+    // clusters then draw the frames heaviest first)
+    const int64_t budget = (max_cand > kMaxCandidates ? 2 : 1) * (int64_t)sm_count;
     int c = 1;
-    while (2 * c <= g_nms_max_cluster && (int64_t)n_frames * 2 * c <= sm_count) c *= 2;
+    while (2 * c <= g_nms_max_cluster && g_nms_active[log2_cluster(2 * c)] > 0 && (int64_t)n_frames * 2 * c <= budget)
+        c *= 2;
     return c;
+}
+
+bool nms_persistent(int n_frames, int cluster) { return n_frames > g_nms_active[log2_cluster(cluster)]; }
+
+int nms_launches(int n_frames, int cluster) {
+    if (n_frames <= 0) return 0;
+    return nms_persistent(n_frames, cluster) && n_frames <= kOrderMax ? 3 : 1;
 }
 
 cudaError_t launch_nms(cudaStream_t s, const FrameDesc *d_frames, const LevelDesc *d_levels,
                        int n_frames, const float *scores, float threshold, float iou,
                        float4 *scratch, int max_cand, pd_box *boxes, int max_boxes,
-                       int32_t *counts, int cluster) {
+                       int32_t *counts, int cluster, int *sched) {
     if (n_frames <= 0) return cudaSuccess;
     if (max_cand < 1 || max_cand > kMaxCandidatesBig || max_boxes < 1 || max_boxes > kMaxBoxes ||
         cluster < 1 || cluster > 8 || (cluster & (cluster - 1)))
         return cudaErrorInvalidValue;
     const size_t smem = nms_smem(max_cand, max_boxes);
+    // more frames than clusters that fit at once: persistent clusters over a
+    // ticket queue, frames ordered by their candidate counts (most first)
+    int *queue = nullptr, *order = nullptr;
+    int n_clusters = n_frames;
+    if (sched && nms_persistent(n_frames, cluster)) {
+        queue = sched;
+        n_clusters = g_nms_active[log2_cluster(cluster)];
+        if (n_frames <= kOrderMax) {
+            order = sched + 1;
+            int *partial = order + n_frames;
+            k_nms_count<<<dim3(kCountBlocks, n_frames), 256, 0, s>>>(d_frames, d_levels, scores, threshold,
+                                                                       partial);
+            int np = 1;
+            while (np < n_frames) np <<= 1;
+            k_nms_order<<<1, kThreads, (size_t)np * sizeof(unsigned long long), s>>>(partial, n_frames, order,
+                                                                                     queue);
+        } else {
+            const cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), s);
+            if (e != cudaSuccess) return e;
+        }
+    }
     if (cluster == 1) {
-        k_nms<<<n_frames, kThreads, smem, s>>>(d_frames, d_levels, scores, threshold, iou, max_cand, scratch,
-                                               boxes, max_boxes, counts);
+        k_nms<<<n_clusters, kThreads, smem, s>>>(d_frames, d_levels, scores, threshold, iou, max_cand, scratch,
+                                                 boxes, max_boxes, counts, n_frames, order, queue);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(n_frames * cluster);
+    cfg.gridDim = dim3(n_clusters * cluster);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
@@ -778,7 +910,7 @@ cudaError_t launch_nms(cudaStream_t s, const FrameDesc *d_frames, const LevelDes
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_nms, d_frames, d_levels, scores, threshold, iou, max_cand, scratch, boxes,
-                              max_boxes, counts);
+                              max_boxes, counts, n_frames, (const int *)order, queue);
 }
 
 // ---------------------------------------------------------------------------

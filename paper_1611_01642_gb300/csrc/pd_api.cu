@@ -289,6 +289,7 @@ struct pd_handle {
     CUtensorMap hog_map[kSvmShapes]{}, lbp_map[kSvmShapes]{};
     CUtensorMap tc_hog_map{}, tc_lbp_map{};  // the same planes for the tensor-core K4
     int *d_queue = nullptr;                  // [2]: K4's and K2+K3's item counters (zeroed before each launch)
+    int *d_nms_sched = nullptr;              // NMS ticket counter, frame order and candidate counts
     int sm_count = 1;
     float tile_cost[kSvmShapes] = {kDefaultTileCost[0], kDefaultTileCost[1], kDefaultTileCost[2],
                                    kDefaultTileCost[3], kDefaultTileCost[4], kDefaultTileCost[5],
@@ -920,7 +921,7 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
         {(int64_t)kLbpBins * h->atlas.lbp_plane, 0},               // 5 lbp atlas
         {h->score_cap * 4, 0},                                     // 6 scores
         {(int64_t)params->max_frames * params->max_boxes_per_frame * (int64_t)sizeof(pd_box), 0},  // 7
-        {(int64_t)params->max_frames * 2 * 4 + 16, 0},             // 8 counts + error word
+        {(int64_t)params->max_frames * 2 * 4 + 16, 0},             // 8 counts + error word + item counters
         {h->frames_cap, 0},                                        // 9 host-input frames
         {(int64_t)params->max_frames * (int64_t)nms_scratch_float4s(params->max_candidates_per_frame) * 16,
          0},                                                                        // 10 NMS scratch
@@ -928,6 +929,7 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
         {(int64_t)rows * P * 4, 0},                                                 // 12 head values
         {h->score_cap * 4, 0},                                                      // 13 window logits
         {2 * h->flag_cap * 4, 0},                                                   // 14 tile flags
+        {(int64_t)nms_sched_ints(params->max_frames) * 4, 0},                       // 15 NMS frame order
     };
     int64_t total = 0;
     for (auto &pt : parts) {
@@ -957,6 +959,7 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
     h->logits = reinterpret_cast<float *>(h->arena + parts[13].off);
     h->s_flag = reinterpret_cast<uint32_t *>(h->arena + parts[14].off);
     h->c_flag = h->s_flag + h->flag_cap;
+    h->d_nms_sched = reinterpret_cast<int *>(h->arena + parts[15].off);
     h->proposal = params->use_proposal != 0;
     h->tau = params->keep_logit_threshold;
 
@@ -1114,7 +1117,9 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
         if (timed) PD_CUDA(h, record(h->stage_ev[3], q));
         PD_CUDA(h, launch_nms(q, df, dl, n_frames, h->d_scores, h->p.threshold, h->p.nms_iou,
                               h->d_nms_scratch, h->p.max_candidates_per_frame, h->m_boxes,
-                              h->p.max_boxes_per_frame, h->m_counts, nms_cluster_for(n_frames, h->sm_count)));
+                              h->p.max_boxes_per_frame, h->m_counts,
+                              nms_cluster_for(n_frames, h->sm_count, h->p.max_candidates_per_frame),
+                              h->d_nms_sched));
         if (timed) PD_CUDA(h, record(h->stage_ev[4], q));
         return PD_OK;
     };
@@ -1146,7 +1151,8 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
     }
     PD_CUDA(h, cudaEventRecord(h->graph_done, s));
     h->last_launches = (p.r_items.empty() ? 0 : 1) + (p.c_items.empty() ? 0 : 1) +
-                       (p.s_items.empty() ? 0 : 1) + (n_frames > 0 ? 1 : 0) +
+                       (p.s_items.empty() ? 0 : 1) +
+                       nms_launches(n_frames, nms_cluster_for(n_frames, h->sm_count, h->p.max_candidates_per_frame)) +
                        (h->proposal ? (p.cnn_items.empty() ? 0 : 1) + (p.levels.empty() ? 0 : 1) +
                                           (p.s_items.empty() ? 0 : 1)
                                     : 0);
@@ -1635,7 +1641,8 @@ int pd_nms_maps(pd_handle *h, void *stream, const float *d_scores, int n_levels,
     if (r != PD_OK) return r;
     PD_CUDA(h, launch_nms(s, dptr<FrameDesc>(h, o.frames), dptr<LevelDesc>(h, o.levels), 1, d_scores,
                           h->p.threshold, h->p.nms_iou, h->d_nms_scratch, h->p.max_candidates_per_frame,
-                          d_boxes, max_boxes, d_counts, nms_cluster_for(1, h->sm_count)));
+                          d_boxes, max_boxes, d_counts,
+                          nms_cluster_for(1, h->sm_count, h->p.max_candidates_per_frame)));
     return PD_OK;
 }
 

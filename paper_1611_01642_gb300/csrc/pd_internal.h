@@ -153,11 +153,20 @@ __host__ __device__ inline size_t nms_scratch_float4s(int cap) {
 }
 // cluster: CTAs per frame (1, 2, 4 or 8; a thread-block cluster that shares
 // the frame's suppression passes); nms_cluster_for picks it for a batch.
+// sched: nms_sched_ints(n_frames) ints of device scratch, or null. With it,
+// a batch of more frames than clusters that fit on the GPU at once runs on
+// persistent clusters that take the frames by a ticket queue, most
+// candidates first (two more kernels count and order them); without it,
+// one cluster per frame.
 cudaError_t launch_nms(cudaStream_t s, const FrameDesc *d_frames, const LevelDesc *d_levels,
                        int n_frames, const float *scores, float threshold, float iou,
                        float4 *scratch, int max_cand, pd_box *boxes, int max_boxes,
-                       int32_t *counts, int cluster = 1);
-int nms_cluster_for(int n_frames, int sm_count);
+                       int32_t *counts, int cluster = 1, int *sched = nullptr);
+int nms_cluster_for(int n_frames, int sm_count, int max_cand);
+// launch_nms with sched runs the persistent form (count, order, NMS kernels)
+bool nms_persistent(int n_frames, int cluster);
+int nms_launches(int n_frames, int cluster);  // kernels launch_nms with sched starts
+constexpr size_t nms_sched_ints(int n_frames) { return 1 + 33 * (size_t)n_frames; }
 
 // ---- the paper's kernel schemes (comparison with the fused kernels)
 size_t scheme_cells_scratch(int Wk, int Hk);

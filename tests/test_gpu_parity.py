@@ -509,22 +509,31 @@ def test_repeated_batch_shape_replays_graph_with_new_frames(template):
 
 def test_results_do_not_depend_on_batch_size(template):
     """The batch size sets the launch shapes: the cells kernel's strip height
-    (2 to 32 cell rows) and the CTAs per frame of the NMS cluster (8, 4, 2, 1
-    on a 152-SM GPU). Frame 0's score maps and boxes must not change."""
+    (2 to 32 cell rows), the CTAs per frame of the NMS cluster (8, 4, 2, 1
+    on a 152-SM GPU) and, with more frames than SMs, persistent NMS CTAs
+    that take the frames most-candidates-first. Frame 0's score maps and
+    boxes must not change, nor any frame's boxes between the last two batches."""
     from paper_1611_01642_gb300 import build as bld
     bld.build()
     w, b = template
-    n_max = 128
-    imgs = [synth.make_scene(1242, 375, 2, i) for i in range(n_max)]
-    d = pd.Detector(w, b, pyr_factor=float(np.float32(1.05)), max_frames=n_max, max_width=1242, max_height=375)
+    n_big = torch.cuda.get_device_properties(0).multi_processor_count + 8
+    imgs = [synth.make_scene(1242, 375, 2, i) for i in range(n_big)]
+    d = pd.Detector(w, b, pyr_factor=float(np.float32(1.05)), max_frames=n_big, max_width=1242, max_height=375)
     try:
         frames = [torch.from_numpy(im).cuda() for im in imgs]
         ref_maps = ref_boxes = None
-        for n in (1, 20, 40, n_max):
+        for n in (1, 20, 40, 128, n_big):
             d.detect(frames[:n])
             assert d.sync() == pd.PD_OK, pd.pd_last_error(d.h)
             maps = [m.clone() for m in d.score_maps(0)]
             boxes = d.boxes(0)
+            if n == 128:
+                all128 = [(d.boxes(i), pd.pd_frame_candidates(d.h, i)) for i in range(128)]
+            if n == n_big:
+                assert pd.pd_last_launch_count(d.h) == 6  # pyramid, cells, K4, count, order, NMS
+                for i in range(128):
+                    assert pd.pd_frame_candidates(d.h, i) == all128[i][1], i
+                    assert np.array_equal(d.boxes(i), all128[i][0]), i
             if ref_maps is None:
                 ref_maps, ref_boxes = maps, boxes
                 assert len(ref_boxes) > 0
