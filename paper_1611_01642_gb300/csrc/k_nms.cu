@@ -1,7 +1,12 @@
 // K5 -- non-maximum suppression (refinement stage of Section 3, run on the
 // host in the paper; greedy IoU suppression here, on the device).
 //
-// One CTA (1024 threads) per frame:
+// One CTA (1024 threads) per frame, or a thread-block cluster of 2-8 CTAs
+// that share its collection, large sorts and suppression passes when the
+// batch leaves SMs free. A batch of more frames than clusters that fit on the
+// GPU at once runs on persistent clusters that draw frames from a ticket
+// queue, most candidates first (a counting kernel and a one-CTA sort set the
+// order), so the heaviest frames do not start last. Per frame:
 //  1. collects every window of every level with score > threshold into a
 //     shared-memory key list (64-bit keys: the float score mapped to an
 //     order-reversing integer in the high word, level/wy/wx in the low word,
