@@ -35,7 +35,6 @@ namespace pd {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
 constexpr int kTW = kResizeTW;                 // 128 source columns per tile
 constexpr int kTH = kResizeTH;                 // 32 source rows per tile
 constexpr int kTP = 176;                       // staged byte row pitch (>= kResizeBW + 8, 16-byte multiple)
@@ -73,7 +72,7 @@ __device__ __forceinline__ uint32_t pack4(uint32_t o0, uint32_t o1, uint32_t o2,
 
 // kCG column groups per warp task; the warp's lanes are kCG groups x kRS row slices.
 template <int kCG>
-__global__ void __launch_bounds__(kThreads, 5) k_resize(const FrameDesc *__restrict__ frames,
+__global__ void __launch_bounds__(kThreads, 6) k_resize(const FrameDesc *__restrict__ frames,
                                                         const LevelDesc *__restrict__ levels,
                                                         const int32_t *__restrict__ tabs,
                                                         uint8_t *__restrict__ pyr,
@@ -91,7 +90,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_resize(const FrameDesc *__restr
 
     const ResizeItem it = items[blockIdx.x];
     const FrameDesc fd = frames[it.frame];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int n = fd.n_levels;
     const int tcx = it.x0 / kTW, tcy = it.y0 / kTH;
 
