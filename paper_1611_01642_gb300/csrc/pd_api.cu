@@ -406,19 +406,54 @@ void plan_tc(std::vector<TcItem> &out, int li, int rows, int cols, int chunk) {
 
 // K2+K3 strips of every level of a plan, tallest first (the warps take them
 // in this order, so the queue ends with the short ones). A strip is
-// kStripTiles cell tiles tall, or shorter (down to 2 cell rows) when the
-// plan would give fewer strips than the device holds warps: a warp alone on
-// an SM exposes every latency, so small batches take more, shorter strips.
-// The strip height does not change the result (every cell row sums its
-// votes in the same order).
+// kStripTiles cell tiles tall, or shorter (down to 2 cell rows) when a
+// small plan would otherwise leave warps idle in its last round. The strip
+// height does not change the result (every cell row sums its votes in the
+// same order).
 void plan_strips(Plan &p, int resident_warps) {
-    auto count = [&](int rows) {
-        int64_t n = 0;
-        for (const LevelDesc &L : p.levels) n += (int64_t)L.ctx * ((L.Hc + rows - 1) / rows);
-        return n;
+    // A strip of r cell rows costs r + 1 bands of 8 pixel rows (one band of
+    // halo), and the persistent warps take strips, tallest first, until none
+    // is left. Of the heights 32, 16, ..., 2 the planner takes the one whose
+    // schedule ends first, a shorter one only if it ends at least 3% sooner:
+    // with many rounds of strips per warp that is 32 (least halo); with few,
+    // a shorter height evens out the last round. The schedule (each strip to
+    // the warp that is free first) is simulated when 32-row strips make fewer
+    // than 16 rounds; warps are counted per integer time, so it is linear.
+    const int R = std::max(resident_warps, 1);
+    auto heights = [&](int rows) {
+        std::vector<int> h;
+        for (const LevelDesc &L : p.levels) {
+            if (L.Hc <= 0) continue;
+            for (int cy = 0; cy < L.Hc; cy += rows) h.insert(h.end(), L.ctx, std::min(rows, L.Hc - cy));
+        }
+        std::sort(h.begin(), h.end(), std::greater<int>());
+        return h;
+    };
+    auto makespan = [&](const std::vector<int> &h) {
+        std::vector<int64_t> free_at(1, R);  // free_at[t]: warps that become free at time t
+        size_t t = 0, end = 0;
+        for (const int r : h) {
+            while (free_at[t] == 0) ++t;
+            --free_at[t];
+            const size_t e = t + (size_t)r + 1;
+            if (e >= free_at.size()) free_at.resize(e + 1, 0);
+            ++free_at[e];
+            end = std::max(end, e);
+        }
+        return (int64_t)end;
     };
     int rows = kCellTH * kStripTiles;
-    while (rows > 2 && count(rows) < resident_warps) rows /= 2;
+    std::vector<int> h = heights(rows);
+    if ((int64_t)h.size() < 16 * (int64_t)R) {
+        int64_t best = makespan(h);
+        for (int r = rows / 2; r >= 2; r /= 2) {
+            const int64_t t = makespan(heights(r));
+            if (100 * t <= 97 * best) {
+                best = t;
+                rows = r;
+            }
+        }
+    }
     p.strips.clear();
     for (int li = 0; li < (int)p.levels.size(); ++li) {
         const LevelDesc &L = p.levels[li];
