@@ -631,6 +631,11 @@ def run_c1(args, pd, torch, w, b):
     frame = [torch.from_numpy(img).cuda()]
     stream = torch.cuda.current_stream()
     try:
+        # launch shapes for this workload (a single small frame: short tensor-core items cut the
+        # score kernel's walk), measured by the autotuner like the main line's
+        from paper_1611_01642_gb300 import autotune
+        tuning = (pd.pd_get_tuning(det.h) if args.no_autotune else
+                  autotune.apply_default(det, frame, w, b, f12))
         for _ in range(20):
             det.detect(frame)
             det.sync()
@@ -651,7 +656,7 @@ def run_c1(args, pd, torch, w, b):
     return {"workload": "1 x 320x240 u8 frame (scene recipe 1: 3 silhouettes of 64..128 px), pyramid factor 1.2 "
                         f"({n_levels} levels), plain HOG+LBP+SVM+NMS", "latency_ms_median": med,
             "latency_ms_p10": float(np.percentile(ms, 10)), "latency_ms_p90": float(np.percentile(ms, 90)),
-            "frames_per_s": 1e3 / med, "boxes": boxes, "replays": args.c1_replays,
+            "frames_per_s": 1e3 / med, "boxes": boxes, "replays": args.c1_replays, "launch_shapes": tuning,
             "timing": "device-resident frame, graph replay, CUDA events per detect (L2 not flushed)"}
 
 

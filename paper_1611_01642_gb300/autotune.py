@@ -38,7 +38,7 @@ from . import (PD_FLAG_STAGE_TIMING, PD_FLAG_SVM_FP32, PD_OK, TILE_SHAPE_DIMS, T
                pd_get_tile_costs, pd_get_tuning, pd_set_tile_costs, pd_set_tuning, pd_stage_times)
 
 K1_GROUPS = (4, 8, 16)
-TC_ITEM_ROWS = (16, 24, 32, 48, 64)
+TC_ITEM_ROWS = (8, 16, 24, 32, 48, 64)
 
 
 def _cache_path() -> str:
