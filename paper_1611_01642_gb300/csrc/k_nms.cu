@@ -810,13 +810,13 @@ int g_nms_active[4] = {1, 0, 0, 0};  // clusters of 1, 2, 4, 8 CTAs that fit on 
 int log2_cluster(int c) { return c == 8 ? 3 : c == 4 ? 2 : c == 2 ? 1 : 0; }
 }  // namespace
 
-cudaError_t init_nms() {
+cudaError_t init_nms(bool occupancy) {
     const int smem = (int)nms_smem(kMaxCandidates, kMaxBoxes);
     cudaError_t e = cudaFuncSetAttribute(k_nms, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_nms_order, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kOrderMax * (int)sizeof(unsigned long long));
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || !occupancy) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
@@ -1006,7 +1006,7 @@ extern "C" int pd_nms_noalloc(void *stream, const float *d_scores, int n_levels,
     // address right after a device reset or on a new primary context.
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_nms_scratch) != cudaSuccess || !p) return PD_ECUDA;
-    if (init_nms() != cudaSuccess) return PD_ECUDA;
+    if (init_nms(false) != cudaSuccess) return PD_ECUDA;  // one cluster-less CTA: no occupancy table
     NoAllocScratch *scratch = reinterpret_cast<NoAllocScratch *>(p);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     k_nms_noalloc_setup<<<1, 128, 0, s>>>(g, scratch);

@@ -104,7 +104,7 @@ struct CellAtlas {
 // One-time per-device kernel attribute set-up (dynamic shared memory opt-in).
 cudaError_t init_cells();
 cudaError_t init_svm();
-cudaError_t init_nms();
+cudaError_t init_nms(bool occupancy = true);  // occupancy: also the clusters that fit (for the launch policy)
 cudaError_t init_resize();
 
 // Kernel launchers (host functions defined next to their kernels).
