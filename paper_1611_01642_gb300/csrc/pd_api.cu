@@ -418,36 +418,46 @@ void plan_strips(Plan &p, int resident_warps) {
     // with many rounds of strips per warp that is 32 (least halo); with few,
     // a shorter height evens out the last round. The schedule (each strip to
     // the warp that is free first) is simulated when 32-row strips make fewer
-    // than 16 rounds; warps are counted per integer time, so it is linear.
-    const int R = std::max(resident_warps, 1);
-    auto heights = [&](int rows) {
-        std::vector<int> h;
+    // than 16 rounds, from the histogram of strip heights with warps counted
+    // per integer time (strips of one height go to the free warps in bulk).
+    constexpr int kMaxRows = kCellTH * kStripTiles;
+    const int64_t R = std::max(resident_warps, 1);
+    auto histogram = [&](int rows, int64_t (&n)[kMaxRows + 1]) {
+        int64_t total = 0;
+        for (int r = 0; r <= kMaxRows; ++r) n[r] = 0;
         for (const LevelDesc &L : p.levels) {
             if (L.Hc <= 0) continue;
-            for (int cy = 0; cy < L.Hc; cy += rows) h.insert(h.end(), L.ctx, std::min(rows, L.Hc - cy));
+            n[rows] += (int64_t)L.ctx * (L.Hc / rows);
+            n[L.Hc % rows] += L.Hc % rows ? L.ctx : 0;
+            total += (int64_t)L.ctx * ((L.Hc + rows - 1) / rows);
         }
-        std::sort(h.begin(), h.end(), std::greater<int>());
-        return h;
+        return total;
     };
-    auto makespan = [&](const std::vector<int> &h) {
+    auto makespan = [&](int rows) {
+        int64_t n[kMaxRows + 1];
+        histogram(rows, n);
         std::vector<int64_t> free_at(1, R);  // free_at[t]: warps that become free at time t
         size_t t = 0, end = 0;
-        for (const int r : h) {
-            while (free_at[t] == 0) ++t;
-            --free_at[t];
-            const size_t e = t + (size_t)r + 1;
-            if (e >= free_at.size()) free_at.resize(e + 1, 0);
-            ++free_at[e];
-            end = std::max(end, e);
+        for (int r = kMaxRows; r >= 1; --r) {
+            for (int64_t left = n[r]; left > 0;) {
+                while (free_at[t] == 0) ++t;
+                const int64_t k = std::min(free_at[t], left);
+                const size_t e = t + (size_t)r + 1;
+                if (e >= free_at.size()) free_at.resize(e + 1, 0);
+                free_at[t] -= k;
+                free_at[e] += k;
+                left -= k;
+                end = std::max(end, e);
+            }
         }
         return (int64_t)end;
     };
-    int rows = kCellTH * kStripTiles;
-    std::vector<int> h = heights(rows);
-    if ((int64_t)h.size() < 16 * (int64_t)R) {
-        int64_t best = makespan(h);
+    int rows = kMaxRows;
+    int64_t n32[kMaxRows + 1];
+    if (histogram(rows, n32) < 16 * R) {
+        int64_t best = makespan(rows);
         for (int r = rows / 2; r >= 2; r /= 2) {
-            const int64_t t = makespan(heights(r));
+            const int64_t t = makespan(r);
             if (100 * t <= 97 * best) {
                 best = t;
                 rows = r;
