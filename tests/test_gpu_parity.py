@@ -544,3 +544,40 @@ def test_results_do_not_depend_on_batch_size(template):
             assert np.array_equal(boxes, ref_boxes), n
     finally:
         d.close()
+
+
+def test_batch_beyond_the_nms_frame_order(template):
+    """16,400 frames of 64x128 (one window each; the seeded training crops,
+    half of them positive): more frames than the NMS order kernel sorts
+    (16,384), so the persistent NMS CTAs draw the frames in index order.
+    Every frame's boxes and candidate count equal those of the same frame in
+    a 100-frame batch (one CTA per frame)."""
+    from paper_1611_01642_gb300 import build as bld
+    bld.build()
+    w, b = template
+    n_big, n_small = 16400, 100
+    pos, neg = synth.make_training_crops(seed=3, n_pos=64, n_neg=64)
+    crops = [np.ascontiguousarray(c) for pair in zip(pos, neg) for c in pair]
+    imgs = [crops[i % len(crops)] for i in range(n_big)]
+    frames = [torch.from_numpy(im).cuda() for im in imgs]
+    small = pd.Detector(w, b, pyr_factor=F105, max_frames=n_small, max_width=64, max_height=128,
+                        max_candidates_per_frame=64)
+    big = pd.Detector(w, b, pyr_factor=F105, max_frames=n_big, max_width=64, max_height=128,
+                      max_candidates_per_frame=64)
+    try:
+        big.detect(frames)
+        assert big.sync() == pd.PD_OK, pd.pd_last_error(big.h)
+        assert pd.pd_last_launch_count(big.h) == 4  # pyramid, cells, K4, NMS (no count / order)
+        n_boxes = 0
+        for s0 in (0, 8200, n_big - n_small):
+            small.detect(frames[s0:s0 + n_small])
+            assert small.sync() == pd.PD_OK
+            for i in range(n_small):
+                assert pd.pd_frame_candidates(big.h, s0 + i) == pd.pd_frame_candidates(small.h, i), s0 + i
+                bb = big.boxes(s0 + i)
+                assert np.array_equal(bb, small.boxes(i)), s0 + i
+                n_boxes += len(bb)
+        assert n_boxes > 0
+    finally:
+        small.close()
+        big.close()
