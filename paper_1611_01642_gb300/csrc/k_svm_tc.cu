@@ -342,7 +342,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_svm_tc(const __grid_constant__ CUtensorMap hog_map, const __grid_constant__ CUtensorMap lbp_map,
              const LevelDesc *__restrict__ levels, const TcItem *__restrict__ items, int n_items,
              int *__restrict__ queue, const float *__restrict__ wt, float bias, float clip,
-             float *__restrict__ scores, const uint32_t *__restrict__ c_flag, unsigned *__restrict__ err) {
+             float *__restrict__ scores, const uint32_t *__restrict__ c_flag, unsigned *__restrict__ err,
+             const CUtensorMap *__restrict__ level_maps) {
     using Slot = SlotT<HP>;
     using TcSmem = TcSmemT<HP>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -544,8 +545,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                                  "r"((uint32_t)(sizeof(float) * HP * kHogX + kLbpBins * kLbpX))
                                  : "memory");
-                    tma_3d(&sl.hog[0][0], &hog_map, bar, it.wx0, L.cell_row + ra + u, 0);
-                    tma_3d(&sl.lbp[0][0], &lbp_map, bar, xl, L.cell_row + ra + u, 0);
+                    tma_3d(&sl.hog[0][0], level_maps ? level_maps + 2 * L.tc_map : &hog_map, bar, it.wx0,
+                           L.cell_row + ra + u, 0);
+                    tma_3d(&sl.lbp[0][0], level_maps ? level_maps + 2 * L.tc_map + 1 : &lbp_map, bar, xl,
+                           L.cell_row + ra + u, 0);
                     issued = idx + 1;
                 };
                 if (ctrl)
@@ -655,15 +658,18 @@ int svm_tc_smem_bytes(int hog_planes) {
 cudaError_t launch_svm_tc(cudaStream_t s, const CUtensorMap &hog_map, const CUtensorMap &lbp_map,
                           const LevelDesc *d_levels, const TcItem *d_items, int n_items, int *d_queue, int grid,
                           const float *d_w, float bias, float clip, float *scores, const uint32_t *c_flag,
-                          unsigned *d_err, int hog_planes) {
+                          unsigned *d_err, int hog_planes, const CUtensorMap *level_maps) {
     if (n_items <= 0) return cudaSuccess;
+    if (reinterpret_cast<uintptr_t>(level_maps) & 63) return cudaErrorInvalidValue;
     grid = grid < n_items ? grid : n_items;
     if (hog_planes == 4 * kHogBins)
         k_svm_tc<4 * kHogBins><<<grid, kThreads, sizeof(TcSmemT<4 * kHogBins>), s>>>(
-            hog_map, lbp_map, d_levels, d_items, n_items, d_queue, d_w, bias, clip, scores, c_flag, d_err);
+            hog_map, lbp_map, d_levels, d_items, n_items, d_queue, d_w, bias, clip, scores, c_flag, d_err,
+            level_maps);
     else
         k_svm_tc<kHogBins><<<grid, kThreads, sizeof(TcSmemT<kHogBins>), s>>>(
-            hog_map, lbp_map, d_levels, d_items, n_items, d_queue, d_w, bias, clip, scores, c_flag, d_err);
+            hog_map, lbp_map, d_levels, d_items, n_items, d_queue, d_w, bias, clip, scores, c_flag, d_err,
+            level_maps);
     return cudaGetLastError();
 }
 

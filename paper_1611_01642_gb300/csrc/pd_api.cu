@@ -67,6 +67,7 @@ struct Plan {
     std::vector<TcItem> t_items;
     std::vector<CnnItem> cnn_items;
     std::vector<int32_t> tabs;
+    std::vector<int32_t> tc_widths;  // tensor-core K4: level widths (cells) with a pair of maps
     int tc_rows = kTcChunk;  // tensor-core K4 window rows per item (tuning; kept by clear())
     int64_t pyr_bytes = 0;
     int64_t score_floats = 0;
@@ -86,6 +87,7 @@ struct Plan {
         t_items.clear();
         cnn_items.clear();
         tabs.clear();
+        tc_widths.clear();
         pyr_bytes = score_floats = 0;
         atlas_rows = max_wc = 0;
     }
@@ -93,7 +95,7 @@ struct Plan {
 
 // Byte offsets of the plan's sections inside the packed descriptor block.
 struct Packed {
-    int64_t frames, levels, r_items, c_items, strips, s_items, t_items, cnn_items, tabs, tmaps, total;
+    int64_t frames, levels, r_items, c_items, strips, s_items, t_items, cnn_items, tabs, tmaps, tc_maps, total;
 };
 
 Packed pack_layout(const Plan &p) {
@@ -115,6 +117,8 @@ Packed pack_layout(const Plan &p) {
     o.tabs = take((int64_t)p.tabs.size() * sizeof(int32_t));
     off = round_up(off, 64);  // tensor maps: 64-byte aligned
     o.tmaps = take(p.cnn_items.empty() ? 0 : (int64_t)p.levels.size() * sizeof(CUtensorMap));
+    off = round_up(off, 64);
+    o.tc_maps = take(2 * (int64_t)p.tc_widths.size() * sizeof(CUtensorMap));
     o.total = off;
     return o;
 }
@@ -200,10 +204,10 @@ void build_lbp_bin_table(uint8_t table[256]) {
 
 int encode_plane_map(CUtensorMap *map, void *base, CUtensorMapDataType dtype, int elem_bytes,
                      int64_t pitch, int64_t rows, int64_t planes, int64_t plane_stride_elems,
-                     uint32_t box_x, uint32_t box_y, uint32_t box_planes) {
+                     uint32_t box_x, uint32_t box_y, uint32_t box_planes, int64_t width) {
     auto fn = get_encode();
     if (!fn) return PD_ECUDA;
-    cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)rows, (cuuint64_t)planes};
+    cuuint64_t dims[3] = {(cuuint64_t)(width > 0 ? width : pitch), (cuuint64_t)rows, (cuuint64_t)planes};
     cuuint64_t strides[2] = {(cuuint64_t)(pitch * elem_bytes), (cuuint64_t)(plane_stride_elems * elem_bytes)};
     cuuint32_t box[3] = {box_x, box_y, box_planes};
     cuuint32_t estr[3] = {1, 1, 1};
@@ -563,6 +567,7 @@ void plan_level(Plan &p, int frame, int level, int W, int H, int Wk, int Hk, int
                 int32_t img_pitch, const LevelDesc *share = nullptr,
                 const float *tile_cost = kDefaultTileCost) {
     LevelDesc L{};
+    L.tc_map = -1;
     L.img_off = img_off;
     L.img_pitch = img_pitch;
     L.frame = frame;
@@ -665,6 +670,34 @@ bool params_ok(const pd_params *p) {
            !((p->flags & PD_FLAG_HOG_PER_BLOCK) && (p->flags & (PD_FLAG_SVM_FP32 | PD_FLAG_LBP_ONLY)));
 }
 
+int encode_tc_maps(CUtensorMap *hog_map, CUtensorMap *lbp_map, const float *hog, const uint8_t *lbp, int64_t pitch,
+                   int64_t rows, int64_t hog_plane, int64_t lbp_plane, int hog_planes = kHogBins,
+                   int64_t width = 0) {
+    if (encode_plane_map(hog_map, const_cast<float *>(hog), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, pitch, rows,
+                         hog_planes, hog_plane, 112, 1, hog_planes, width) != PD_OK ||
+        encode_plane_map(lbp_map, const_cast<uint8_t *>(lbp), CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, pitch, rows,
+                         kLbpBins, lbp_plane, 128, 1, kLbpBins, width) != PD_OK)
+        return PD_ECUDA;
+    return PD_OK;
+}
+
+// Tensor-core K4: one pair of cell-plane maps per distinct level width, so
+// that a box reaching past a level's right edge reads zeros (TMA fill) and
+// not the atlas row's padding from memory (the windows that use those cells
+// are not stored).
+void assign_tc_maps(Plan &p) {
+    p.tc_widths.clear();
+    std::map<int32_t, int32_t> index;
+    for (LevelDesc &L : p.levels) {
+        auto it = index.find(L.Wc);
+        if (it == index.end()) {
+            it = index.emplace(L.Wc, (int32_t)p.tc_widths.size()).first;
+            p.tc_widths.push_back(L.Wc);
+        }
+        L.tc_map = it->second;
+    }
+}
+
 // Packs the plan into the pinned staging buffer and sends it to the device.
 int upload_plan(pd_handle *h, cudaStream_t s, const Plan &p, Packed &o, const uint8_t *pyr_base = nullptr) {
     o = pack_layout(p);
@@ -682,6 +715,12 @@ int upload_plan(pd_handle *h, cudaStream_t s, const Plan &p, Packed &o, const ui
     put(o.t_items, p.t_items.data(), p.t_items.size() * sizeof(TcItem));
     put(o.cnn_items, p.cnn_items.data(), p.cnn_items.size() * sizeof(CnnItem));
     put(o.tabs, p.tabs.data(), p.tabs.size() * sizeof(int32_t));
+    for (size_t k = 0; k < p.tc_widths.size(); ++k) {
+        CUtensorMap *maps = reinterpret_cast<CUtensorMap *>(h->h_desc + o.tc_maps) + 2 * k;
+        if (encode_tc_maps(&maps[0], &maps[1], h->atlas.hog, h->atlas.lbp, h->atlas.pitch, h->atlas.rows,
+                           h->atlas.hog_plane, h->atlas.lbp_plane, hog_planes_of(h->p.flags), p.tc_widths[k]) != PD_OK)
+            return fail(h, PD_ECUDA, "cell-plane tensor map");
+    }
     if (!p.cnn_items.empty()) {
         CUtensorMap *maps = reinterpret_cast<CUtensorMap *>(h->h_desc + o.tmaps);
         for (size_t k = 0; k < p.levels.size(); ++k) {
@@ -713,16 +752,6 @@ int encode_svm_maps(CUtensorMap *hog_maps, CUtensorMap *lbp_maps, const float *h
 
 // The tensor-core K4's maps: one cell row of a 112-cell strip of the 9 (or,
 // per-block HOG, 36) HOG planes, and of a 128-cell strip of the 59 LBP planes.
-int encode_tc_maps(CUtensorMap *hog_map, CUtensorMap *lbp_map, const float *hog, const uint8_t *lbp, int64_t pitch,
-                   int64_t rows, int64_t hog_plane, int64_t lbp_plane, int hog_planes = kHogBins) {
-    if (encode_plane_map(hog_map, const_cast<float *>(hog), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, pitch, rows,
-                         hog_planes, hog_plane, 112, 1, hog_planes) != PD_OK ||
-        encode_plane_map(lbp_map, const_cast<uint8_t *>(lbp), CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, pitch, rows,
-                         kLbpBins, lbp_plane, 128, 1, kLbpBins) != PD_OK)
-        return PD_ECUDA;
-    return PD_OK;
-}
-
 // Round to the nearest bfloat16 (ties to even): 8 significant bits of the
 // exact value, as a float.
 float bf16_round_host(double a) {
@@ -932,6 +961,7 @@ int pd_create(const pd_params *params, const float *svm_w, float svm_b, pd_handl
             cnn_bound += (int64_t)((L.Hc + kCnnTile - 1) / kCnnTile) * ((L.Wc + kCnnTile - 1) / kCnnTile);
         h->flag_cap = F * std::max<int64_t>(s_bound, (int64_t)one.c_items.size()) + 64;
         h->desc_cap = round_up(F * (int64_t)one.levels.size() * (int64_t)sizeof(CUtensorMap), 64) + 128 +
+                      round_up(2 * (int64_t)std::max(worst.max_wc, 1) * (int64_t)sizeof(CUtensorMap), 64) + 64 +
                       round_up(F * cnn_bound * (int64_t)sizeof(CnnItem), 16) +
                       round_up(F * (int64_t)sizeof(FrameDesc), 16) +
                       round_up(F * (int64_t)one.levels.size() * (int64_t)sizeof(LevelDesc), 16) +
@@ -1101,6 +1131,7 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
         }
         order_tc(p.t_items);
         plan_strips(p, h->sm_count * kStripWarpsPerSm);
+        if (!(h->p.flags & PD_FLAG_SVM_FP32)) assign_tc_maps(p);
         if (p.atlas_rows > h->atlas.rows || p.pyr_bytes > h->pyr_cap || p.score_floats > h->score_cap ||
             (int64_t)p.s_items.size() > h->flag_cap || (int64_t)p.c_items.size() > h->flag_cap)
             return fail(h, PD_EINVAL, "batch exceeds the arena");
@@ -1157,7 +1188,8 @@ int pd_detect(pd_handle *h, void *stream, int n_frames, const uint8_t *const *d_
             PD_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), q));
             PD_CUDA(h, launch_svm_tc(q, h->tc_hog_map, h->tc_lbp_map, dl, dptr<TcItem>(h, o.t_items),
                                      (int)p.t_items.size(), h->d_queue, h->sm_count, h->d_w, h->bias,
-                                     h->p.l2hys_clip, h->d_scores, cf, h->d_err, hog_planes_of(h->p.flags)));
+                                     h->p.l2hys_clip, h->d_scores, cf, h->d_err, hog_planes_of(h->p.flags),
+                                     p.tc_widths.empty() ? nullptr : dptr<CUtensorMap>(h, o.tc_maps)));
         }
         if (timed) PD_CUDA(h, record(h->stage_ev[3], q));
         PD_CUDA(h, launch_nms(q, df, dl, n_frames, h->d_scores, h->p.threshold, h->p.nms_iou,

@@ -55,6 +55,8 @@ struct LevelDesc {
     int32_t rspan;      // K1 source bytes a tile row needs for this level (<= kResizeBW)
     int32_t xq_off;     // K1 column quads: per group one word, byte i = quad index of column i
     int32_t hsrc;       // proposal: index (in this table) of the level whose head map this level uses
+    int32_t tc_map;     // tensor-core K4: pair (HOG, LBP) of cell-plane maps whose x extent is this
+                        // level's width (index into the plan's map table; -1: none)
 };
 
 // Work items (one CTA each).
@@ -139,10 +141,13 @@ cudaError_t launch_svm(cudaStream_t s, const CUtensorMap *hog_maps, const CUtens
 // 112 x 1 x hog_planes (f32; 9, or 36 for per-block HOG) and 128 x 1 x 59 (u8).
 cudaError_t init_svm_tc();
 int svm_tc_smem_bytes(int hog_planes = kHogBins);
+// level_maps: null, or 2 maps per entry of LevelDesc::tc_map (HOG, LBP) in device
+// memory (64-byte aligned) whose x extent is the level's width, so that a box
+// reaching past it reads zeros instead of the atlas row's padding.
 cudaError_t launch_svm_tc(cudaStream_t s, const CUtensorMap &hog_map, const CUtensorMap &lbp_map,
                           const LevelDesc *d_levels, const TcItem *d_items, int n_items, int *d_queue, int grid,
                           const float *d_w, float bias, float clip, float *scores, const uint32_t *c_flag,
-                          unsigned *d_err, int hog_planes = kHogBins);
+                          unsigned *d_err, int hog_planes = kHogBins, const CUtensorMap *level_maps = nullptr);
 // Per-frame NMS scratch (float4 units) for a candidate cap: the decoded
 // boxes, plus the sort keys when the cap is above 16,384 (shared memory
 // holds them below).
@@ -243,10 +248,11 @@ cudaError_t launch_cnn(cudaStream_t s, const LevelDesc *d_levels, int n_levels, 
 cudaError_t launch_train_step(cudaStream_t s, const TrainArgs &a);
 cudaError_t launch_round_params(cudaStream_t s, const float *master, float *wr);
 
-// Encodes a 3-D tiled tensor map over plane-major cell planes.
+// Encodes a 3-D tiled tensor map over plane-major cell planes; x extent: the
+// row pitch, or width when it is positive (boxes reaching past it read zeros).
 int encode_plane_map(CUtensorMap *map, void *base, CUtensorMapDataType dtype, int elem_bytes,
                      int64_t pitch, int64_t rows, int64_t planes, int64_t plane_stride_elems,
-                     uint32_t box_x, uint32_t box_y, uint32_t box_planes);
+                     uint32_t box_x, uint32_t box_y, uint32_t box_planes, int64_t width = 0);
 
 // Host-side tables.
 void build_lbp_bin_table(uint8_t table[256]);
