@@ -25,8 +25,9 @@
 //     suppressed: all threads compute the batch's pairwise suppression bits,
 //     warp 0 resolves the batch (kept iff no kept earlier member suppresses
 //     it), and all threads then suppress the later candidates against the
-//     batch's kept members (their boxes staged in shared memory). This takes the same decisions as the one-at-a-time greedy
-//     walk (candidates between batch members are already suppressed).
+//     batch's kept members (their boxes staged in shared memory). This
+//     takes the same decisions as the one-at-a-time greedy walk (candidates
+//     between batch members are already suppressed).
 // The IoU test first evaluates the IoU in float. For boxes of this detector
 // (width >= 64, height >= 128, coordinates < 8192) the float value is within
 // 7e-5 of the exact one: each coordinate sum or difference is off by at most
@@ -55,7 +56,8 @@ constexpr int kMaxBoxes = 16384;
 constexpr int kBatch = 64;                // greedy walk: candidates resolved per block-wide step
 constexpr int kGrid = 32;                 // culling grid: kGrid x kGrid cells over the frame
 constexpr int kCountBlocks = 32;          // blocks per frame counting its candidates
-static_assert(nms_sched_ints(1) == 2 + kCountBlocks, "scheduling scratch: ticket, then per frame its order slot and counts");
+static_assert(nms_sched_ints(1) == 2 + kCountBlocks,
+              "scheduling scratch: the ticket, then per frame its order slot and counts");
 constexpr int kOrderMax = 16384;          // frames the order kernel sorts (more: drawn in index order)
 static_assert(kThreads == 16 * kBatch, "pairwise matrix: 16 threads per batch member");
 static_assert(kThreads == kGrid * kGrid, "one culling cell per thread");

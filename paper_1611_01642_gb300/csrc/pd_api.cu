@@ -1315,7 +1315,8 @@ int pd_get_tile_costs(const pd_handle *h, float *cost) {
 // ----------------------------------------------------------------------------- learned proposal
 
 int pd_cnn_set_params(pd_handle *h, const float *params, int n) {
-    if (!h || !params || n != kCnnParams) return h ? fail(h, PD_EINVAL, "expected %d parameters", kCnnParams) : PD_EINVAL;
+    if (!h || !params || n != kCnnParams)
+        return h ? fail(h, PD_EINVAL, "expected %d parameters", kCnnParams) : PD_EINVAL;
     for (int i = 0; i < n; ++i)
         if (!std::isfinite(params[i])) return fail(h, PD_EINVAL, "parameter %d is not finite", i);
     PD_CUDA(h, cudaDeviceSynchronize());
@@ -1370,8 +1371,8 @@ int pd_cnn_forward(pd_handle *h, void *stream, const uint8_t *d_level, int Wk, i
     int r = upload_plan(h, s, p, o, d_level);
     if (r != PD_OK) return r;
     PD_CUDA(h, launch_cnn(s, dptr<LevelDesc>(h, o.levels), p.levels[0].rows > 0 ? 1 : 0,
-                          dptr<CUtensorMap>(h, o.tmaps), dptr<CnnItem>(h, o.cnn_items), (int)p.cnn_items.size(), cnn_weights(h), d_h, h_pitch,
-                          d_logits, max_pool_tiles(p), h->d_err));
+                          dptr<CUtensorMap>(h, o.tmaps), dptr<CnnItem>(h, o.cnn_items), (int)p.cnn_items.size(),
+                          cnn_weights(h), d_h, h_pitch, d_logits, max_pool_tiles(p), h->d_err));
     return PD_OK;
 }
 
@@ -1743,7 +1744,8 @@ int pd_scheme_cells(pd_handle *h, void *stream, int scheme, const uint8_t *d_lev
     if (!h) return PD_EINVAL;
     const int Wc = Wk / 8, Hc = Hk / 8;
     const bool lbp_s = scheme == PD_SCHEME_LBP_NAIVE || scheme == PD_SCHEME_LBP_SCALABLE;
-    const bool hog_s = scheme == PD_SCHEME_HOG_GLOBAL || scheme == PD_SCHEME_HOG_LOCAL || scheme == PD_SCHEME_HOG_SHARED;
+    const bool hog_s =
+        scheme == PD_SCHEME_HOG_GLOBAL || scheme == PD_SCHEME_HOG_LOCAL || scheme == PD_SCHEME_HOG_SHARED;
     if (!(lbp_s || hog_s) || !d_level || Wk < 1 || Hk < 1 || pitch < Wk || cell_pitch < Wc ||
         (lbp_s && (!d_lbp || lbp_plane < (int64_t)Hc * cell_pitch)) ||
         (hog_s && (!d_hog || hog_plane < (int64_t)Hc * cell_pitch)))
