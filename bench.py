@@ -670,6 +670,11 @@ def run_c3(args, pd, torch, flush, w, b, pool):
     det = pd.Detector(w, b, pyr_factor=FACTOR, max_frames=len(frames), max_width=1920, max_height=1080,
                       flags=pd.PD_FLAG_STAGE_TIMING)
     try:
+        # launch shapes picked by the autotuner on this batch (the configuration's "tiles picked
+        # by the project's autotuner")
+        from paper_1611_01642_gb300 import autotune
+        tuning = (pd.pd_get_tuning(det.h) if args.no_autotune else
+                  autotune.apply_default(det, frames, w, b, FACTOR))
         ms, st = time_detector(det, frames, flush, args.c3_steps, pd, torch)
         levels = sorted({len(det.levels(f)) for f in range(len(frames))})
     finally:
@@ -680,7 +685,8 @@ def run_c3(args, pd, torch, flush, w, b, pool):
                         "HOG+LBP+SVM+NMS",
             "frames_per_s": len(frames) / (ms / 1e3), "ms_per_step": ms, "px_per_ns": px / (ms * 1e6),
             "stage_ms_per_step": dict(zip(["pyramid", "cells", "norm_svm", "nms"], map(float, st[:4]))),
-            "steps": args.c3_steps, "l2": "flushed (256 MB write) before every timed step"}
+            "steps": args.c3_steps, "launch_shapes": tuning,
+            "l2": "flushed (256 MB write) before every timed step"}
 
 
 def run_gpu(args):
